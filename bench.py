@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the robust reference governor on one GB300 (or N replicas).
+
+Workload: the closed-loop RG run with 1,024 disturbance scenarios and a
+2,000-step RK4 horizon (dt = 0.01 s) on the FC3 fuel-cell air-path model, the
+reference a seeded 8-level staircase over 50..300 A held 125 updates per
+level.  One benchmark step is one closed-loop update: redraw the scenarios,
+run the robust RG search (speculative bisection, N_kappa = 12, binary32
+rollouts with a binary64 recheck of near-zero slacks), move the simulated
+plant one step.  W warm-up updates run first; the K timed updates are the
+next K of the same run.
+
+Printed (rank 0): one JSON line.  value = RG updates/s over all ranks, device
+time (CUDA events on the library's stream, inputs resident in HBM, L2 flushed
+between timed steps).  e2e = the same through the host-buffer C-ABI calls
+(rrg_sample_scenarios + rrg_step + rrg_plant_step, host copies included).
+roofline = the binary32 rollout kernel's achieved FP32 rate vs the FP32 FMA
+peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz.  cpu_baseline = the
+FP64 CPU oracle (plain joint bisection) on a bounded prefix of the same run.
+
+--impl reference times that oracle alone (the CPU arm) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RG updates/s & trajectory-steps/s at stated kappa tol; FP32+adjoint vs plain FP64 bisect"
+UNIT = "RG updates/s"
+N_SCEN, HORIZON, N_BISECT, M_CAND = 1024, 2000, 12, 64
+SEED, V0 = 1, 100.0
+RECHECK_EPS_REL = 1e-6
+# algorithmic binary32 flops of one trajectory step (4 right-hand sides of 27,
+# 3 stage points of 6, the RK4 combination of 18, the disturbance add of 3,
+# output, slack, finiteness and running min of 6); counted from the source
+FLOPS_PER_STEP = 153
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="updates of the plain FP64 bisection comparator")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(W, K):
+    return {
+        "workload": "closed-loop robust RG on FC3: N_sim=1024 scenarios, horizon 2000 RK4 steps "
+                    "(dt=0.01 s), staircase r (8 levels over 50..300 A, seed 1, 125 updates/level), "
+                    "timed updates [%d, %d) of the 1000-update run" % (W, W + K),
+        "search": "speculative bisection (Alg. 1 result), N_kappa=12, 64 candidates/round",
+        "kappa_tol": 2.0 ** -11,
+        "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
+        "l2": "256 MB written between timed steps",
+    }
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_index is not None:
+            cmd += ["-i", str(gpu_index)]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU side --
+def cpu_oracle_closed_loop(x0, r_seq, seconds, cores):
+    """Times the FP64 oracle's closed loop (plain joint bisection) on a
+    bounded prefix of the run; returns (updates/s, updates, seconds, kappas)."""
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    p = inputs.fc3_params()
+    c = O.cfg(H=HORIZON, N=N_SCEN)
+    t0 = time.perf_counter()
+    v, kap, fl, xs = O.closed_loop(p, c, x0, V0, r_seq[:1], SEED, 0, inputs.DIST_AMP, inputs.DIST_AMP,
+                                   search=0, n_kappa=N_BISECT, nthreads=cores)
+    one = time.perf_counter() - t0
+    more = max(0, min(len(r_seq) - 1, int(seconds / max(one, 1e-3)) - 1))
+    kaps = list(kap)
+    if more:
+        t1 = time.perf_counter()
+        v2, kap2, fl2, xs2 = O.closed_loop(p, c, xs[1], v[0], r_seq[1:1 + more], SEED, 1, inputs.DIST_AMP,
+                                           inputs.DIST_AMP, search=0, n_kappa=N_BISECT, nthreads=cores)
+        kaps += list(kap2)
+        total = one + (time.perf_counter() - t1)
+    else:
+        total = one
+    n = 1 + more
+    return n / total, n, total, kaps
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    p = inputs.fc3_params()
+    W, K = args.warmup, args.steps
+    r_seq = inputs.staircase(W + K, 8, 125, SEED)
+    x0 = O.equilibrium(p, V0)
+    cores = os.cpu_count() or 1
+    c = O.cfg(H=HORIZON, N=N_SCEN)
+    amp = inputs.DIST_AMP
+    v, kap, fl, xs = O.closed_loop(p, c, x0, V0, r_seq[:W], SEED, 0, amp, amp, search=0, n_kappa=N_BISECT,
+                                   nthreads=cores) if W else (None, None, None, [x0])
+    xw, vw = (xs[-1], v[-1]) if W else (x0, V0)
+    t0 = time.perf_counter()
+    O.closed_loop(p, c, xw, vw, r_seq[W:W + K], SEED, W, amp, amp, search=0, n_kappa=N_BISECT,
+                  nthreads=cores)
+    dt = time.perf_counter() - t0
+    val = K / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(W, K), search="plain joint bisection (Alg. 1 on all scenarios)",
+                       precision="binary64", l2="n/a (CPU)"),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "updates [%d, %d) of the closed loop, FP64 CPU oracle, %d threads"
+                                   % (W, W + K, cores)},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- GPU side --
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+
+    p = inputs.fc3_params()
+    W, K = args.warmup, args.steps
+    T = W + K
+    seed = SEED + 1000 * rank          # replicas run independent closed loops
+    r_seq = inputs.staircase(T, 8, 125, SEED)
+    amp = np.array(inputs.DIST_AMP)
+    stream = torch.cuda.Stream()
+    cfg = R.rrg_config_default(horizon=HORIZON, n_scenarios=N_SCEN, max_candidates=M_CAND,
+                               n_bisect=N_BISECT, search=R.SEARCH_SPEC_BISECT,
+                               precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
+                               recheck_eps_rel=RECHECK_EPS_REL)
+    g = R.Governor(p, cfg, stream)
+    x0, _ = g.equilibrium(V0)
+    dev = torch.device("cuda", local)
+    d_r = torch.tensor(r_seq, dtype=torch.float64, device=dev)
+    d_v = torch.zeros(T, dtype=torch.float64, device=dev)
+    d_k = torch.zeros(T, dtype=torch.float64, device=dev)
+    d_f = torch.zeros(T, dtype=torch.int32, device=dev)
+    d_x = torch.zeros(3 * (T + 1), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    # warm-up updates (also initialises the loop state on the device)
+    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, W, seed, 0, amp, False, d_v, d_k, d_f, d_x)
+    torch.cuda.synchronize()
+    g.reset_stats()
+    g.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(float(i))                       # L2 flush, outside the timed window
+            evs[i][0].record(stream)
+            R.rrg_closed_loop_dev(g.h, None, 0.0, d_r, 1, seed, 0, amp, False, d_v, d_k, d_f, d_x)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    st = g.stats()
+    g.set_profiling(False)
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    kap_dev = d_k.cpu().numpy()
+    flags_dev = d_f.cpu().numpy()
+    x_dev = d_x.cpu().numpy().reshape(T + 1, 3)
+    value = world * K / total_s
+
+    # executed and nominal trajectory-steps of the timed updates
+    exec_steps = st["lane_steps"]
+    fp32_steps = st["lane_steps"] - st["lane_steps_fp64"]
+    avg_roll_ms = st["rollout_ms"] / max(1, st["timed_rollouts"])
+    roll_launches = max(1, st["timed_rollouts"])
+    achieved = (fp32_steps / roll_launches) * FLOPS_PER_STEP / (avg_roll_ms * 1e-3) / 1e12
+
+    out = None
+    if rank == 0:
+        # e2e: the same updates through the host-buffer C ABI, on a fresh handle
+        g2 = R.Governor(p, cfg, stream)
+        x, v = x0.copy(), V0
+        for t in range(W):
+            g2.sample_scenarios(seed, t)
+            v, _, _ = g2.step(x, r_seq[t], v)
+            x = g2.plant_step(x, v, seed, t, amp)
+        e2e_s, kap_e2e = 0.0, []
+        for t in range(W, T):
+            flush.fill_(float(t))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2.sample_scenarios(seed, t)
+            v, kk, _ = g2.step(x, r_seq[t], v)
+            x = g2.plant_step(x, v, seed, t, amp)
+            e2e_s += time.perf_counter() - t0
+            kap_e2e.append(kk)
+        g2.close()
+
+        # plain FP64 bisection on the same GPU, same updates
+        nf = min(args.fp64_steps, K)
+        fp64 = None
+        if nf > 0:
+            cfg64 = R.rrg_config_default(horizon=HORIZON, n_scenarios=N_SCEN, max_candidates=M_CAND,
+                                         n_bisect=N_BISECT, search=R.SEARCH_BISECT, precision=R.FP64,
+                                         early_exit=R.EXIT_CANDIDATE)
+            g3 = R.Governor(p, cfg64, stream)
+            ms64, kap64 = [], []
+            v_dev = d_v.cpu().numpy()
+            for t in range(W, W + nf):
+                g3.sample_scenarios(seed, t)
+                flush.fill_(0.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, kk, _ = g3.step(x_dev[t], r_seq[t], v_dev[t - 1] if t else V0)
+                ms64.append(1e3 * (time.perf_counter() - t0))
+                kap64.append(kk)
+            g3.close()
+            fp64 = {"value": 1e3 / statistics.mean(ms64), "unit": UNIT, "ms_per_update": statistics.mean(ms64),
+                    "updates": nf, "kappa_equal_to_fp32_recheck": bool(np.all(np.array(kap64) == kap_dev[W:W + nf]))}
+
+        cpu = None
+        if not args.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            from oracle import oracle as O
+            x0o = O.equilibrium(p, V0)
+            cval, cn, cs, ckap = cpu_oracle_closed_loop(x0o, inputs.staircase(1000, 8, 125, SEED),
+                                                        args.cpu_seconds, cores)
+            cpu = {"value": cval, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "first %d updates of the same closed loop (seed %d), FP64 plain joint "
+                             "bisection, %.1f s" % (cn, SEED, cs)}
+            # rank 0's replica starts from the same state and scenarios: kappas must agree
+            nk = min(cn, T)
+            cpu["kappa_equal_to_gpu"] = bool(np.all(np.array(ckap[:nk]) == kap_dev[:nk]))
+
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(W, K),
+            "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
+                                       "executed_per_update": exec_steps / K},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "rollout_kernel<float>",
+                         "avg_launch_ms": avg_roll_ms, "launches": st["timed_rollouts"],
+                         "flops_per_traj_step": FLOPS_PER_STEP,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 40 + 96,
+                    "d2h_bytes_per_step": 20 + 24,
+                    "kappa_equal_to_device_run": bool(np.all(np.array(kap_e2e) == kap_dev[W:T]))},
+            "gpu_launches": st["launches"],
+            "clocks": clk,
+            "fp64_bisect_gpu": fp64,
+            "rechecked_trajectories": st["rechecked"],
+            "no_admissible_updates": int(np.sum(flags_dev[W:T] & 1)),
+            "kappa_mean": float(np.mean(kap_dev[W:T])),
+        }
+    g.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * rrg.h -- C ABI of librrg, a single-GPU (sm_103a) implementation of the
+ * scenario-based robust reference governor (RG) of Ossareh, Shayne &
+ * Chevalier, "CPU- and GPU-Based Parallelization of the Robust Reference
+ * Governor" (arXiv 2510.08288).
+ *
+ * What one RG update computes (Sec. II-III):
+ *   given the measured state x_t, the previous governed reference v_{t-1} and
+ *   the desired reference r_t, find the largest kappa in [0, 1] such that the
+ *   governed reference v = v_{t-1} + kappa (r_t - v_{t-1})            (Eq. 2)
+ *   keeps the predicted output y_j = h(x_j, v) in Y = { y >= y_min } for
+ *   j = 0..j* along x_{j+1} = f(x_j, v) + d_j^k for every one of N_sim
+ *   sampled disturbance sequences d^k                          (Eq. 3, Eq. 4)
+ *   and keeps the steady-state output in the tightened set      (Eq. 3),
+ *   by bisection (Alg. 1 / Alg. 2) or by the parallel grid of Alg. 3 (Eq. 5).
+ *
+ * Model: FC3, the library's third-order fuel-cell air-path closed loop with
+ * states x = [p_ca (Pa), w_cp (rad/s), p_sm (Pa)] and setpoint v = stack
+ * current (A) (the paper's Sec. IV-A names these states and the OER >= 1.9
+ * output constraint; its own equations are not published in the paper).
+ * f is one classical RK4 step of size dt (Sec. IV-A: 0.01 s).
+ *
+ * Conventions for every entry point:
+ *   - Return value: RRG_OK (0) or one of the RRG_E* codes below.  On error,
+ *     rrg_last_error(h) returns a message owned by the handle (valid until
+ *     the next call on that handle); for a failed rrg_create, rrg_last_error
+ *     (NULL) returns the calling thread's last creation error.
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ *   - Host pointers ("host") are owned by the caller and are read or written
+ *     synchronously before the call returns.  Device pointers ("device", the
+ *     *_dev entry points) must point to memory of the handle's device; those
+ *     calls only enqueue work on the handle's stream and return at once.
+ *   - Scenario arrays use the layout d[(i*H + j)*N + k]: component i in
+ *     state order, step j = 0..H-1, scenario k = 0..N-1 (k fastest).
+ *   - No entry point falls back to a CPU implementation.
+ */
+#ifndef RRG_H
+#define RRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------- */
+#define RRG_OK        0
+#define RRG_EINVAL    1   /* an argument is out of range or not finite   */
+#define RRG_ENOMEM    2   /* device or host allocation failed            */
+#define RRG_ECUDA     3   /* a CUDA runtime call failed                  */
+#define RRG_ETIMEOUT  4   /* a bounded device-side wait gave up          */
+#define RRG_ENOTIMPL  5   /* the requested option is not implemented     */
+
+/* ---- search strategies (rrg_config.search) --------------------------- */
+#define RRG_SEARCH_BISECT      0  /* Alg. 1 on the joint all-scenario predicate:
+                                     one candidate per round, n_bisect rounds */
+#define RRG_SEARCH_GRID        1  /* Alg. 3 / Eq. 5: M = max_candidates points */
+#define RRG_SEARCH_KSECTION    2  /* repeated grid: round 1 is Alg. 3, later
+                                     rounds put M points strictly inside the
+                                     bracket (kappa_i*, kappa_i*+1); n_rounds */
+#define RRG_SEARCH_SPEC_BISECT 3  /* same result as RRG_SEARCH_BISECT: each
+                                     round evaluates every node of the next
+                                     levels of Alg. 1's bisection tree that
+                                     fit in max_candidates, then follows
+                                     Alg. 1's path through their outcomes */
+
+/* ---- arithmetic of the rollouts (rrg_config.precision) --------------- */
+#define RRG_FP64          0  /* all rollouts in binary64                    */
+#define RRG_FP32          1  /* all rollouts in binary32                    */
+#define RRG_FP32_RECHECK  2  /* binary32 rollouts; any trajectory whose FP32
+                                min slack lies within recheck_eps_rel * y_min
+                                of zero is rolled out again in binary64 and
+                                the binary64 decision replaces it            */
+
+/* ---- early termination (rrg_config.early_exit) ----------------------- */
+#define RRG_EXIT_NONE       0  /* every trajectory runs all H steps          */
+#define RRG_EXIT_LANE       1  /* a trajectory stops at its first violation
+                                  (Sec. III-B/C)                             */
+#define RRG_EXIT_CANDIDATE  2  /* additionally, all trajectories of a
+                                  candidate stop once one of them violates   */
+
+#define RRG_NPARAM 27         /* length of the FC3 parameter vector          */
+#define RRG_MAX_CANDIDATES 1024
+
+/* FC3 parameter vector layout (SI units):
+ *  0 p_atm   1 T_atm   2 T_st    3 R_a     4 V_sm    5 V_ca    6 k_sm
+ *  7 k_ca    8 n_cell  9 faraday 10 M_O2   11 x_O2   12 gamma  13 c_p
+ * 14 eta_cp 15 J_cp   16 eta_cm 17 k_t    18 k_v    19 R_cm   20 a_w
+ * 21 a_p    22 lam_ref 23 K_p   24 c0     25 c1     26 c2                   */
+
+typedef struct {
+    double  dt;              /* RK4 step, s (> 0)                             */
+    int32_t horizon;         /* H = j*: outputs checked at j = 0..H (>= 1)    */
+    int32_t n_scenarios;     /* N_sim (>= 1)                                  */
+    int32_t max_candidates;  /* candidates per round, 1..RRG_MAX_CANDIDATES;
+                                the grid size M for GRID and KSECTION         */
+    int32_t n_bisect;        /* N_kappa of Alg. 1 (>= 1)                      */
+    int32_t n_rounds;        /* KSECTION rounds (>= 1)                        */
+    int32_t search;          /* RRG_SEARCH_*                                  */
+    int32_t precision;       /* RRG_FP64 / RRG_FP32 / RRG_FP32_RECHECK        */
+    int32_t early_exit;      /* RRG_EXIT_*                                    */
+    int32_t ss_check;        /* 1: require y_ss(v) >= y_min + eps_ss (y_c -
+                                y_min) (Eq. 3, steady-state tightening)       */
+    double  y_min;           /* output constraint y >= y_min (Sec. IV-A: 1.9) */
+    double  eps_ss;          /* epsilon of (1 - eps) Y, in [0, 1)             */
+    double  y_c;             /* nominal output the tightening shrinks towards */
+    double  recheck_eps_rel; /* FP64 recheck band, relative to y_min          */
+    double  dist_amp[3];     /* scenario disturbance half-ranges (Sec. IV-A:
+                                50 Pa, 10 rad/s, 50 Pa)                       */
+} rrg_config;
+
+typedef struct rrg_ctx *rrg_handle;
+
+/* Counters kept by a handle since creation or the last rrg_reset_stats. */
+typedef struct {
+    uint64_t launches;          /* kernels this handle launched               */
+    uint64_t rollout_launches;  /* of which rollout kernels                   */
+    uint64_t lane_steps;        /* RK4 steps executed over all trajectories   */
+    uint64_t lane_steps_fp64;   /* of which in binary64                       */
+    uint64_t rechecked;         /* trajectories re-run in binary64            */
+    uint64_t rounds;            /* search rounds enqueued                     */
+    double   rollout_ms;        /* summed device time of rollout launches
+                                   (only while profiling is on)               */
+    double   recheck_ms;        /* same for recheck launches                  */
+    uint64_t timed_rollouts;    /* rollout launches covered by rollout_ms     */
+} rrg_stats;
+
+/* Fills *cfg with the defaults of the paper's fuel-cell experiment: dt 0.01,
+ * H 500, N 32, M 32, N_kappa 12, 3 rounds, SPEC_BISECT, FP32_RECHECK,
+ * EXIT_CANDIDATE, ss_check 1, y_min 1.9, eps_ss 0.05, y_c 2.2, recheck band
+ * 1e-6, amplitudes (50, 10, 50).  Never fails. */
+void rrg_config_default(rrg_config *cfg);
+
+/* Creates a governor on the current CUDA device.
+ *   model_params  host, n_params doubles in the FC3 layout above; copied.
+ *   cfg           host; copied.  Validated: RRG_EINVAL on a bad field.
+ *   cuda_stream   a cudaStream_t of the current device; all work of the
+ *                 handle goes there.  NULL: the handle creates (and later
+ *                 destroys) a private non-blocking stream of its own.
+ *   out           host; receives the handle.
+ * Allocates all device memory the handle needs (about 36 H N bytes of
+ * scenarios plus O(max_candidates * N) bytes of per-candidate and recheck
+ * buffers).  RRG_ENOMEM / RRG_ECUDA on failure (nothing leaks). */
+int rrg_create(const double *model_params, int n_params, const rrg_config *cfg,
+               void *cuda_stream, rrg_handle *out);
+
+/* Releases every resource of h (after synchronising its stream).  NULL is
+ * accepted.  Returns RRG_ECUDA if the stream reported an error. */
+int rrg_destroy(rrg_handle h);
+
+const char *rrg_last_error(rrg_handle h);
+
+/* Draws the N scenario sequences of one RG update on the device (Sec. II-C:
+ * scenarios are redrawn at every RG time step; Alg. 3 step 2):
+ * d_j^k[i] = a_i (2u - 1), u = (w_i >> 11) 2^-53 with (w_0, w_1, w_2, w_3) =
+ * Philox4x64-10(counter = (j, k, update_index, 0), key = (seed, 0)).
+ * Asynchronous on the handle's stream. */
+int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index);
+
+/* Loads explicit scenarios instead: d host, 3*H*N doubles (layout above).
+ * The binary32 copy is the round-to-nearest of each value.  Synchronous. */
+int rrg_set_scenarios(rrg_handle h, const double *d);
+
+/* Copies the current scenarios (binary64, layout above, 3*H*N doubles) to the
+ * host buffer d.  Synchronous. */
+int rrg_get_scenarios(rrg_handle h, double *d);
+
+/* Evaluates m candidate kappas on the current scenarios (Alg. 3 parallel
+ * steps 1-3 for given kappas, Eq. 5's P).  Host buffers:
+ *   x_t[3], v_prev, r_t   the RG inputs (finite; v values must be > 0)
+ *   kappas[m]             each in [0, 1]; 1 <= m <= max_candidates
+ *   admissible[m]  out    1 iff the steady-state check passes and every
+ *                         scenario's trajectory keeps y >= y_min at j=0..H
+ *   min_slack[m]   out    (optional, NULL) min over scenarios and steps of
+ *                         y_j - y_min; NaN when the steady-state check fails
+ *                         (no rollout is run); with early exit on, for an
+ *                         inadmissible candidate it is only an upper bound
+ *   P[m*N]         out    (optional, NULL) P[i*N + k] = 1 iff candidate i is
+ *                         admissible for scenario k; when P is requested the
+ *                         candidate-level early exit is not used
+ * Synchronous. */
+int rrg_eval_candidates(rrg_handle h, const double *x_t, double v_prev, double r_t,
+                        const double *kappas, int m, uint8_t *admissible,
+                        double *min_slack, uint8_t *P);
+
+/* One robust RG update with the configured search on the current scenarios.
+ * Host in: x_t[3], r_t, v_prev.  Host out: *v_t (Eq. 2 applied to the chosen
+ * kappa, evaluated as v_prev + kappa * (r_t - v_prev) without fused
+ * multiply-add), *kappa, *flags (bit 0: no evaluated candidate was admissible,
+ * so kappa = 0 and v_t = v_prev; bit 1: inputs were rejected on the device).
+ * Synchronous. */
+int rrg_step(rrg_handle h, const double *x_t, double r_t, double v_prev,
+             double *v_t, double *kappa, int32_t *flags);
+
+/* Same as rrg_step with device pointers: d_x_t[3], *d_r_t, *d_v_prev in;
+ * *d_v_t, *d_kappa, *d_flags out.  Asynchronous; nothing is copied to or from
+ * the host, so it can be enqueued back to back or captured in a CUDA graph. */
+int rrg_step_dev(rrg_handle h, const double *d_x_t, const double *d_r_t,
+                 const double *d_v_prev, double *d_v_t, double *d_kappa,
+                 int32_t *d_flags);
+
+/* Equilibrium of FC3 at constant setpoint v (Sec. II-A's equilibrium
+ * manifold) and its output y_ss(v), in binary64 on the device.  Host out.
+ * RRG_EINVAL if v is not positive and finite or no equilibrium is found. */
+int rrg_equilibrium(rrg_handle h, double v, double *x_eq, double *y_ss);
+
+/* Closed loop of Fig. 1 with a simulated plant, T updates, all on the device:
+ * for t = 0..T-1: sample scenarios (seed, t0 + t); RG update with r_seq[t];
+ * plant step x_{t+1} = RK4(x_t, v_t) + d_plant, d_plant drawn like the
+ * scenarios from Philox4x64-10(counter = (0, 0, t0 + t, 1), key = (seed, 0))
+ * with half-ranges plant_amp[3].
+ *   host in:  x0[3], v0, r_seq[T], plant_amp[3]
+ *   host out: v_out[T], kappa_out[T], flags_out[T], x_out[3*(T+1)] (x_out[0..2]
+ *             = x0).  Any output pointer may be NULL.
+ *   use_graph: 1 replays one captured CUDA graph per update, 0 launches the
+ *             kernels of each update directly.
+ * Synchronous. */
+int rrg_closed_loop(rrg_handle h, const double *x0, double v0, const double *r_seq,
+                    int T, uint64_t seed, uint64_t t0, const double *plant_amp,
+                    int use_graph, double *v_out, double *kappa_out,
+                    int32_t *flags_out, double *x_out);
+
+/* Device-pointer form of rrg_closed_loop: d_r_seq[T] in; d_v_out[T],
+ * d_kappa_out[T], d_flags_out[T], d_x_out[3*(T+1)] out (d_x_out[0..2] is
+ * written with x0).  x0, v0 and plant_amp are host values.  Asynchronous.
+ * x0 == NULL continues the loop where the previous call on this handle left
+ * it: state, v_{t-1} and the update counter t carry over, r_seq and the
+ * outputs are indexed by that running t (so they must cover every update of
+ * the run), and the scenarios of update t use update index t0 + t. */
+int rrg_closed_loop_dev(rrg_handle h, const double *x0, double v0, const double *d_r_seq,
+                        int T, uint64_t seed, uint64_t t0, const double *plant_amp,
+                        int use_graph, double *d_v_out, double *d_kappa_out,
+                        int32_t *d_flags_out, double *d_x_out);
+
+/* One plant step of the closed loop above with host buffers: x_next =
+ * RK4(x_t, v_t) + d_plant(seed, t).  Synchronous. */
+int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, uint64_t t,
+                   const double *plant_amp, double *x_next);
+
+/* Profiling: while on, every rollout and recheck launch is bracketed by CUDA
+ * events on the handle's stream and their durations are summed into
+ * rrg_stats.rollout_ms / recheck_ms. */
+int rrg_set_profiling(rrg_handle h, int on);
+
+/* Reads the counters (synchronises the handle's stream).  Host out. */
+int rrg_get_stats(rrg_handle h, rrg_stats *out);
+int rrg_reset_stats(rrg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RRG_H */

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -19,7 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rrg_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_LIB = os.path.join(_HERE, "liboracle.%s.so" % platform.machine())
 _lock = threading.Lock()
 _lib = None
 

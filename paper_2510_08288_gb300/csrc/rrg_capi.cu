@@ -1,0 +1,684 @@
+// rrg_capi.cu -- host side of the C ABI declared in include/rrg.h: handle
+// life cycle, argument validation, device memory, and the fixed launch
+// sequence of one RG update (see rrg_kernels.cu).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "rrg_device.cuh"
+#include "rrg_internal.h"
+
+using namespace rrg;
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+struct rrg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  rrg_config cfg{};
+  double params[RRG_NPARAM]{};
+  Fc3K<double> k64h{};
+  Fc3K<float> k32h{};
+  SearchCfg scfg{};
+  Launch L{};
+  // device memory
+  double* params_dev = nullptr;
+  Fc3K<double>* k64_dev = nullptr;
+  Fc3K<float>* k32_dev = nullptr;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  SearchState* st = nullptr;
+  double* cand_kappa = nullptr;
+  double* cand_v = nullptr;
+  CandK<double>* cand_k64 = nullptr;
+  CandK<float>* cand_k32 = nullptr;
+  int32_t* cand_ok = nullptr;
+  int32_t* cand_dead = nullptr;
+  int32_t* cand_ss = nullptr;
+  unsigned long long* cand_min = nullptr;
+  uint32_t* recheck_list = nullptr;
+  uint32_t* recheck_count = nullptr;
+  DevStats* stats = nullptr;
+  uint8_t* P_dev = nullptr;
+  double* io_dev = nullptr;     // [0..2] x, [3] r, [4] v, [5..8] out, [8] amp.. see offsets
+  int32_t* flag_dev = nullptr;  // [0] flags, [1] status
+  double* kap_dev = nullptr;    // [m_cap] kappas in, [m_cap] min slack out
+  uint8_t* adm_dev = nullptr;
+  LoopState* loop = nullptr;
+  // closed-loop I/O staging (grown on demand)
+  double* cl_dev = nullptr;
+  size_t cl_cap = 0;
+  // pinned host staging
+  double* io_h = nullptr;
+  int32_t* flag_h = nullptr;
+  // counters and profiling
+  uint64_t launches = 0, rollout_launches = 0, rounds = 0;
+  bool profiling = false;
+  bool capturing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_roll, ev_rec;
+  double rollout_ms = 0.0, recheck_ms = 0.0;
+  uint64_t timed_rollouts = 0;
+  std::string err;
+};
+
+namespace {
+
+// io_dev / io_h offsets (doubles)
+constexpr int IO_X = 0, IO_R = 3, IO_V = 4, IO_OUT = 5, IO_AMP = 9, IO_LEN = 12;
+
+int set_err(rrg_ctx* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf; else g_create_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return set_err(h, RRG_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+int validate_cfg(const rrg_config* c) {
+  if (!c) return set_err(nullptr, RRG_EINVAL, "cfg is NULL");
+  if (!(c->dt > 0.0) || !is_fin(c->dt)) return set_err(nullptr, RRG_EINVAL, "dt must be > 0");
+  if (c->horizon < 1) return set_err(nullptr, RRG_EINVAL, "horizon must be >= 1");
+  if (c->n_scenarios < 1) return set_err(nullptr, RRG_EINVAL, "n_scenarios must be >= 1");
+  if (c->max_candidates < 1 || c->max_candidates > RRG_MAX_CANDIDATES)
+    return set_err(nullptr, RRG_EINVAL, "max_candidates must be in [1, %d]", RRG_MAX_CANDIDATES);
+  if (c->n_bisect < 1 || c->n_bisect > 60)
+    return set_err(nullptr, RRG_EINVAL, "n_bisect must be in [1, 60]");
+  if (c->n_rounds < 1 || c->n_rounds > 64)
+    return set_err(nullptr, RRG_EINVAL, "n_rounds must be in [1, 64]");
+  if (c->search < RRG_SEARCH_BISECT || c->search > RRG_SEARCH_SPEC_BISECT)
+    return set_err(nullptr, RRG_EINVAL, "unknown search %d", c->search);
+  if ((c->search == RRG_SEARCH_GRID || c->search == RRG_SEARCH_KSECTION) && c->max_candidates < 2)
+    return set_err(nullptr, RRG_EINVAL, "grid searches need max_candidates >= 2");
+  if (c->precision < RRG_FP64 || c->precision > RRG_FP32_RECHECK)
+    return set_err(nullptr, RRG_EINVAL, "unknown precision %d", c->precision);
+  if (c->early_exit < RRG_EXIT_NONE || c->early_exit > RRG_EXIT_CANDIDATE)
+    return set_err(nullptr, RRG_EINVAL, "unknown early_exit %d", c->early_exit);
+  if (!is_fin(c->y_min) || !is_fin(c->y_c) || !is_fin(c->eps_ss) || c->eps_ss < 0.0 ||
+      c->eps_ss >= 1.0)
+    return set_err(nullptr, RRG_EINVAL, "y_min, y_c must be finite and eps_ss in [0, 1)");
+  if (!is_fin(c->recheck_eps_rel) || c->recheck_eps_rel < 0.0)
+    return set_err(nullptr, RRG_EINVAL, "recheck_eps_rel must be >= 0");
+  for (int i = 0; i < 3; ++i)
+    if (!is_fin(c->dist_amp[i]) || c->dist_amp[i] < 0.0)
+      return set_err(nullptr, RRG_EINVAL, "dist_amp must be finite and >= 0");
+  const unsigned long long lanes =
+      static_cast<unsigned long long>(c->max_candidates) * static_cast<unsigned long long>(c->n_scenarios);
+  if (lanes >= (1ull << 32)) return set_err(nullptr, RRG_EINVAL, "max_candidates * n_scenarios >= 2^32");
+  return RRG_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T) + 16);
+}
+
+void free_all(rrg_ctx* h) {
+  void* ptrs[] = {h->params_dev, h->k64_dev, h->k32_dev, h->d64, h->d32, h->st, h->cand_kappa,
+                  h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
+                  h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
+                  h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->io_h) cudaFreeHost(h->io_h);
+  if (h->flag_h) cudaFreeHost(h->flag_h);
+  for (auto& e : h->ev_free) cudaEventDestroy(e);
+  for (auto& pr : h->ev_roll) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto& pr : h->ev_rec) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+void fill_launch(rrg_ctx* h) {
+  Launch& L = h->L;
+  const rrg_config& c = h->cfg;
+  L.stream = h->stream;
+  L.N = c.n_scenarios;
+  L.H = c.horizon;
+  L.precision = c.precision;
+  L.early_exit = c.early_exit;
+  L.m_cap = c.max_candidates;
+  L.dt = c.dt;
+  L.y_min = c.y_min;
+  L.eps_abs = c.precision == RRG_FP32_RECHECK ? c.recheck_eps_rel * std::fabs(c.y_min) : 0.0;
+  L.scfg = h->scfg;
+  L.params = h->params_dev;
+  L.k64_dev = h->k64_dev;
+  L.k32_dev = h->k32_dev;
+  L.k64_host = &h->k64h;
+  L.k32_host = &h->k32h;
+  L.d64 = h->d64;
+  L.d32 = h->d32;
+  L.st = h->st;
+  L.cand_kappa = h->cand_kappa;
+  L.cand_v = h->cand_v;
+  L.cand_k64 = h->cand_k64;
+  L.cand_k32 = h->cand_k32;
+  L.cand_ok = h->cand_ok;
+  L.cand_dead = h->cand_dead;
+  L.cand_ss = h->cand_ss;
+  L.cand_min = h->cand_min;
+  L.recheck_list = h->recheck_list;
+  L.recheck_count = h->recheck_count;
+  L.stats = h->stats;
+  L.P = nullptr;
+  L.recheck_blocks = 2 * 152;
+}
+
+cudaEvent_t take_event(rrg_ctx* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Rollout of the current round (+ recheck in FP32_RECHECK mode).
+int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit) {
+  const bool timed = h->profiling && !h->capturing;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (timed) { a = take_event(h); b = take_event(h); }
+  if (a && b) CK(cudaEventRecord(a, h->stream));
+  const bool fp64 = h->cfg.precision == RRG_FP64;
+  CK(launch_rollout(L, width, fp64, early_exit, h->cfg.precision == RRG_FP32_RECHECK));
+  if (a && b) {
+    CK(cudaEventRecord(b, h->stream));
+    h->ev_roll.emplace_back(a, b);
+  }
+  h->launches++;
+  h->rollout_launches++;
+  if (h->cfg.precision == RRG_FP32_RECHECK) {
+    cudaEvent_t c = nullptr, d = nullptr;
+    if (timed) { c = take_event(h); d = take_event(h); }
+    if (c && d) CK(cudaEventRecord(c, h->stream));
+    CK(launch_recheck(L, early_exit));
+    if (c && d) {
+      CK(cudaEventRecord(d, h->stream));
+      h->ev_rec.emplace_back(c, d);
+    }
+    h->launches++;
+  }
+  return RRG_OK;
+}
+
+// The search of one RG update on already-sampled scenarios.
+int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
+                   const unsigned long long* t_dev, const double* d_vp, double* d_vt,
+                   double* d_kappa, int32_t* d_flags) {
+  const Launch& L = h->L;
+  CK(launch_search_begin(L, d_x, d_r, t_dev, d_vp));
+  h->launches++;
+  const int R = search_round_count(h->scfg);
+  for (int r = 0; r < R; ++r) {
+    const int width = search_round_width(h->scfg, r);
+    int rc = enqueue_round_work(h, L, width, h->cfg.early_exit);
+    if (rc != RRG_OK) return rc;
+    CK(launch_search_next(L, d_vt, d_kappa, d_flags));
+    h->launches++;
+    h->rounds++;
+  }
+  return RRG_OK;
+}
+
+bool x_ok(const double* x) { return x && is_fin(x[0]) && is_fin(x[1]) && is_fin(x[2]); }
+
+}  // namespace
+
+extern "C" {
+
+void rrg_config_default(rrg_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof *c);
+  c->dt = 0.01;
+  c->horizon = 500;
+  c->n_scenarios = 32;
+  c->max_candidates = 32;
+  c->n_bisect = 12;
+  c->n_rounds = 3;
+  c->search = RRG_SEARCH_SPEC_BISECT;
+  c->precision = RRG_FP32_RECHECK;
+  c->early_exit = RRG_EXIT_CANDIDATE;
+  c->ss_check = 1;
+  c->y_min = 1.9;
+  c->eps_ss = 0.05;
+  c->y_c = 2.2;
+  c->recheck_eps_rel = 1e-6;
+  c->dist_amp[0] = 50.0;
+  c->dist_amp[1] = 10.0;
+  c->dist_amp[2] = 50.0;
+}
+
+const char* rrg_last_error(rrg_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, void* cuda_stream,
+               rrg_handle* out) {
+  g_create_error.clear();
+  if (!out) return set_err(nullptr, RRG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!model_params || n_params != RRG_NPARAM)
+    return set_err(nullptr, RRG_EINVAL, "model_params must hold %d values", RRG_NPARAM);
+  for (int i = 0; i < RRG_NPARAM; ++i)
+    if (!is_fin(model_params[i])) return set_err(nullptr, RRG_EINVAL, "model_params[%d] not finite", i);
+  int rc = validate_cfg(cfg);
+  if (rc != RRG_OK) return rc;
+
+  rrg_ctx* h = new (std::nothrow) rrg_ctx();
+  if (!h) return set_err(nullptr, RRG_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  std::memcpy(h->params, model_params, sizeof h->params);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+      h->own_stream = e == cudaSuccess;
+    }
+  }
+  const rrg_config& c = h->cfg;
+  const size_t N = c.n_scenarios, H = c.horizon, M = c.max_candidates;
+  const size_t HN3 = 3 * H * N;
+#define ALLOC(ptr, n)                                                   \
+  if (e == cudaSuccess) {                                               \
+    e = dalloc(&h->ptr, (n));                                           \
+    if (e != cudaSuccess) { cudaGetLastError(); }                       \
+  }
+  ALLOC(params_dev, RRG_NPARAM);
+  ALLOC(k64_dev, 1);
+  ALLOC(k32_dev, 1);
+  ALLOC(d64, HN3);
+  ALLOC(d32, HN3);
+  ALLOC(st, 1);
+  ALLOC(cand_kappa, M);
+  ALLOC(cand_v, M);
+  ALLOC(cand_k64, M);
+  ALLOC(cand_k32, M);
+  ALLOC(cand_ok, M);
+  ALLOC(cand_dead, M);
+  ALLOC(cand_ss, M);
+  ALLOC(cand_min, M);
+  ALLOC(recheck_list, M * N);
+  ALLOC(recheck_count, 1);
+  ALLOC(stats, 1);
+  ALLOC(io_dev, IO_LEN);
+  ALLOC(flag_dev, 4);
+  ALLOC(kap_dev, 2 * M);
+  ALLOC(adm_dev, M);
+  ALLOC(loop, 1);
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->io_h), IO_LEN * sizeof(double) + 2 * M * sizeof(double) + M);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->flag_h), 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(SearchState), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d64, 0, HN3 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, HN3 * sizeof(float), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_fold_constants(h->params_dev, h->k64_dev, h->k32_dev, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h->k64h, h->k64_dev, sizeof h->k64h, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h->k32h, h->k32_dev, sizeof h->k32h, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? RRG_ENOMEM : RRG_ECUDA;
+    set_err(nullptr, code, "rrg_create: %s", cudaGetErrorString(e));
+    free_all(h);
+    delete h;
+    return code;
+  }
+  h->launches = 1;
+  SearchCfg& s = h->scfg;
+  s.search = c.search;
+  s.m_cap = c.search == RRG_SEARCH_BISECT ? 1 : c.max_candidates;
+  s.n_bisect = c.n_bisect;
+  s.n_rounds = c.n_rounds;
+  s.ss_check = c.ss_check;
+  s.y_min = c.y_min;
+  s.eps_ss = c.eps_ss;
+  s.y_c = c.y_c;
+  fill_launch(h);
+  *out = h;
+  return RRG_OK;
+}
+
+int rrg_destroy(rrg_handle h) {
+  if (!h) return RRG_OK;
+  int rc = RRG_OK;
+  {
+    DeviceGuard g(h->device);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = RRG_ECUDA;
+    free_all(h);
+  }
+  delete h;
+  return rc;
+}
+
+int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index) {
+  if (!h) return RRG_EINVAL;
+  DeviceGuard g(h->device);
+  CK(launch_sample(h->L, seed, update_index, nullptr, h->cfg.dist_amp));
+  h->launches++;
+  return RRG_OK;
+}
+
+int rrg_set_scenarios(rrg_handle h, const double* d) {
+  if (!h) return RRG_EINVAL;
+  if (!d) return set_err(h, RRG_EINVAL, "d is NULL");
+  DeviceGuard g(h->device);
+  const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
+  CK(cudaMemcpyAsync(h->d64, d, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_round_scenarios(h->L));
+  h->launches++;
+  CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
+}
+
+int rrg_get_scenarios(rrg_handle h, double* d) {
+  if (!h) return RRG_EINVAL;
+  if (!d) return set_err(h, RRG_EINVAL, "d is NULL");
+  DeviceGuard g(h->device);
+  const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
+  CK(cudaMemcpyAsync(d, h->d64, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
+}
+
+int rrg_eval_candidates(rrg_handle h, const double* x_t, double v_prev, double r_t,
+                        const double* kappas, int m, uint8_t* admissible, double* min_slack,
+                        uint8_t* P) {
+  if (!h) return RRG_EINVAL;
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite and v_prev, r_t > 0");
+  if (!kappas || !admissible || m < 1 || m > h->cfg.max_candidates)
+    return set_err(h, RRG_EINVAL, "need 1 <= m <= max_candidates and non-NULL kappas/admissible");
+  for (int i = 0; i < m; ++i)
+    if (!(kappas[i] >= 0.0 && kappas[i] <= 1.0))
+      return set_err(h, RRG_EINVAL, "kappas[%d] outside [0, 1]", i);
+  DeviceGuard g(h->device);
+  const int M = h->cfg.max_candidates;
+  double* kap_h = h->io_h + IO_LEN;
+  uint8_t* adm_h = reinterpret_cast<uint8_t*>(h->io_h + IO_LEN + 2 * M);
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  std::memcpy(kap_h, kappas, m * sizeof(double));
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, IO_LEN * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->kap_dev, kap_h, m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  Launch L = h->L;
+  int early = h->cfg.early_exit;
+  if (P) {
+    if (!h->P_dev) CK(cudaMalloc(reinterpret_cast<void**>(&h->P_dev),
+                                 static_cast<size_t>(M) * h->cfg.n_scenarios));
+    L.P = h->P_dev;
+    if (early > RRG_EXIT_LANE) early = RRG_EXIT_LANE;
+  }
+  CK(launch_eval_prepare(L, h->io_dev + IO_X, v_prev, r_t, h->kap_dev, m));
+  h->launches++;
+  int rc = enqueue_round_work(h, L, m, early);
+  if (rc != RRG_OK) return rc;
+  CK(launch_eval_finish(L, m, h->adm_dev, h->kap_dev + M));
+  h->launches++;
+  CK(cudaMemcpyAsync(adm_h, h->adm_dev, m, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(kap_h + M, h->kap_dev + M, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (P)
+    CK(cudaMemcpyAsync(P, h->P_dev, static_cast<size_t>(m) * h->cfg.n_scenarios,
+                       cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(admissible, adm_h, m);
+  if (min_slack) std::memcpy(min_slack, kap_h + M, m * sizeof(double));
+  return RRG_OK;
+}
+
+int rrg_step(rrg_handle h, const double* x_t, double r_t, double v_prev, double* v_t,
+             double* kappa, int32_t* flags) {
+  if (!h) return RRG_EINVAL;
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite and v_prev, r_t > 0");
+  DeviceGuard g(h->device);
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  h->io_h[IO_R] = r_t;
+  h->io_h[IO_V] = v_prev;
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, 5 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_search(h, h->io_dev + IO_X, h->io_dev + IO_R, nullptr, h->io_dev + IO_V,
+                          h->io_dev + IO_OUT, h->io_dev + IO_OUT + 1, h->flag_dev);
+  if (rc != RRG_OK) return rc;
+  CK(cudaMemcpyAsync(h->io_h + IO_OUT, h->io_dev + IO_OUT, 2 * sizeof(double),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->flag_h, h->flag_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (v_t) *v_t = h->io_h[IO_OUT];
+  if (kappa) *kappa = h->io_h[IO_OUT + 1];
+  if (flags) *flags = h->flag_h[0];
+  return RRG_OK;
+}
+
+int rrg_step_dev(rrg_handle h, const double* d_x_t, const double* d_r_t, const double* d_v_prev,
+                 double* d_v_t, double* d_kappa, int32_t* d_flags) {
+  if (!h) return RRG_EINVAL;
+  if (!d_x_t || !d_r_t || !d_v_prev) return set_err(h, RRG_EINVAL, "input pointers must be non-NULL");
+  DeviceGuard g(h->device);
+  return enqueue_search(h, d_x_t, d_r_t, nullptr, d_v_prev, d_v_t, d_kappa, d_flags);
+}
+
+int rrg_equilibrium(rrg_handle h, double v, double* x_eq, double* y_ss) {
+  if (!h) return RRG_EINVAL;
+  if (!is_fin(v) || !(v > 0.0)) return set_err(h, RRG_EINVAL, "v must be finite and > 0");
+  DeviceGuard g(h->device);
+  CK(launch_equilibrium(h->L, v, h->io_dev + IO_OUT, h->flag_dev + 1));
+  h->launches++;
+  CK(cudaMemcpyAsync(h->io_h + IO_OUT, h->io_dev + IO_OUT, 4 * sizeof(double),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->flag_h + 1, h->flag_dev + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->flag_h[1] != 0) return set_err(h, RRG_EINVAL, "no equilibrium found for v = %g", v);
+  if (x_eq) std::memcpy(x_eq, h->io_h + IO_OUT, 3 * sizeof(double));
+  if (y_ss) *y_ss = h->io_h[IO_OUT + 3];
+  return RRG_OK;
+}
+
+int rrg_plant_step(rrg_handle h, const double* x_t, double v_t, uint64_t seed, uint64_t t,
+                   const double* plant_amp, double* x_next) {
+  if (!h) return RRG_EINVAL;
+  if (!x_ok(x_t) || !is_fin(v_t) || !x_ok(plant_amp) || !x_next)
+    return set_err(h, RRG_EINVAL, "x_t, v_t, plant_amp must be finite and x_next non-NULL");
+  DeviceGuard g(h->device);
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  h->io_h[IO_V] = v_t;
+  std::memcpy(h->io_h + IO_AMP, plant_amp, 3 * sizeof(double));
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, IO_LEN * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_plant(h->L, h->io_dev + IO_X, h->io_dev + IO_V, seed, t, nullptr, h->io_dev + IO_AMP,
+                  h->io_dev + IO_OUT));
+  h->launches++;
+  CK(cudaMemcpyAsync(h->io_h + IO_OUT, h->io_dev + IO_OUT, 3 * sizeof(double),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(x_next, h->io_h + IO_OUT, 3 * sizeof(double));
+  return RRG_OK;
+}
+
+int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double* d_r_seq, int T,
+                        uint64_t seed, uint64_t t0, const double* plant_amp, int use_graph,
+                        double* d_v_out, double* d_kappa_out, int32_t* d_flags_out,
+                        double* d_x_out) {
+  if (!h) return RRG_EINVAL;
+  if ((x0 && (!x_ok(x0) || !is_fin(v0) || !(v0 > 0.0))) || !x_ok(plant_amp) || !d_r_seq || T < 0)
+    return set_err(h, RRG_EINVAL, "x0, v0, plant_amp must be finite, v0 > 0, T >= 0, r_seq non-NULL");
+  DeviceGuard g(h->device);
+  std::memcpy(h->io_h + IO_AMP, plant_amp, 3 * sizeof(double));
+  CK(cudaMemcpyAsync(h->io_dev + IO_AMP, h->io_h + IO_AMP, 3 * sizeof(double),
+                     cudaMemcpyHostToDevice, h->stream));
+  if (x0) {
+    CK(launch_loop_init(h->L, h->loop, x0, v0, d_x_out));
+    h->launches++;
+  }
+  if (T == 0) return RRG_OK;
+  const double* amp = h->io_dev + IO_AMP;
+  auto enqueue_update = [&]() -> int {
+    CK(launch_sample(h->L, seed, t0, &h->loop->t, h->cfg.dist_amp));
+    h->launches++;
+    int rc = enqueue_search(h, h->loop->x, d_r_seq, &h->loop->t, &h->loop->v_prev, nullptr,
+                            nullptr, nullptr);
+    if (rc != RRG_OK) return rc;
+    CK(launch_loop_end(h->L, h->loop, seed, t0, amp, d_v_out, d_kappa_out, d_flags_out, d_x_out));
+    h->launches++;
+    return RRG_OK;
+  };
+  if (!use_graph) {
+    for (int t = 0; t < T; ++t) {
+      int rc = enqueue_update();
+      if (rc != RRG_OK) return rc;
+    }
+    return RRG_OK;
+  }
+  // Capture one update and replay it T times; the update index lives on the
+  // device (loop->t), so every replay works on the next time step.
+  const uint64_t launches0 = h->launches, rl0 = h->rollout_launches, rounds0 = h->rounds;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  int rc = enqueue_update();
+  h->capturing = false;
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+  if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+  const uint64_t per = h->launches - launches0, rl_per = h->rollout_launches - rl0,
+                 rd_per = h->rounds - rounds0;
+  h->launches = launches0;
+  h->rollout_launches = rl0;
+  h->rounds = rounds0;
+  for (int t = 0; t < T; ++t) {
+    ce = cudaGraphLaunch(exec, h->stream);
+    if (ce != cudaSuccess) break;
+    h->launches += per;
+    h->rollout_launches += rl_per;
+    h->rounds += rd_per;
+  }
+  cudaGraphExecDestroy(exec);
+  if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+  return RRG_OK;
+}
+
+int rrg_closed_loop(rrg_handle h, const double* x0, double v0, const double* r_seq, int T,
+                    uint64_t seed, uint64_t t0, const double* plant_amp, int use_graph,
+                    double* v_out, double* kappa_out, int32_t* flags_out, double* x_out) {
+  if (!h) return RRG_EINVAL;
+  if (T < 0 || (T > 0 && !r_seq)) return set_err(h, RRG_EINVAL, "T >= 0 and r_seq non-NULL");
+  DeviceGuard g(h->device);
+  // staging: r[T], v[T], kappa[T], x[3(T+1)], flags[T] (as int32 in doubles)
+  const size_t need = static_cast<size_t>(T) * 3 + 3 * (static_cast<size_t>(T) + 1) + T + 4;
+  if (need > h->cl_cap) {
+    if (h->cl_dev) cudaFree(h->cl_dev);
+    h->cl_dev = nullptr;
+    h->cl_cap = 0;
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->cl_dev), need * sizeof(double)));
+    h->cl_cap = need;
+  }
+  double* d_r = h->cl_dev;
+  double* d_v = d_r + T;
+  double* d_k = d_v + T;
+  double* d_x = d_k + T;
+  int32_t* d_f = reinterpret_cast<int32_t*>(d_x + 3 * (static_cast<size_t>(T) + 1));
+  if (T > 0)
+    CK(cudaMemcpyAsync(d_r, r_seq, T * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  int rc = rrg_closed_loop_dev(h, x0, v0, d_r, T, seed, t0, plant_amp, use_graph, d_v, d_k, d_f, d_x);
+  if (rc != RRG_OK) return rc;
+  if (v_out && T) CK(cudaMemcpyAsync(v_out, d_v, T * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (kappa_out && T)
+    CK(cudaMemcpyAsync(kappa_out, d_k, T * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (flags_out && T)
+    CK(cudaMemcpyAsync(flags_out, d_f, T * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (x_out)
+    CK(cudaMemcpyAsync(x_out, d_x, 3 * (static_cast<size_t>(T) + 1) * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
+}
+
+int rrg_set_profiling(rrg_handle h, int on) {
+  if (!h) return RRG_EINVAL;
+  h->profiling = on != 0;
+  return RRG_OK;
+}
+
+int rrg_get_stats(rrg_handle h, rrg_stats* out) {
+  if (!h || !out) return RRG_EINVAL;
+  DeviceGuard g(h->device);
+  DevStats ds{};
+  CK(cudaMemcpyAsync(&ds, h->stats, sizeof ds, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& pr : h->ev_roll) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    h->rollout_ms += ms;
+    h->timed_rollouts++;
+    h->ev_free.push_back(pr.first);
+    h->ev_free.push_back(pr.second);
+  }
+  h->ev_roll.clear();
+  for (auto& pr : h->ev_rec) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    h->recheck_ms += ms;
+    h->ev_free.push_back(pr.first);
+    h->ev_free.push_back(pr.second);
+  }
+  h->ev_rec.clear();
+  out->launches = h->launches;
+  out->rollout_launches = h->rollout_launches;
+  out->lane_steps = ds.lane_steps;
+  out->lane_steps_fp64 = ds.lane_steps_fp64;
+  out->rechecked = ds.rechecked;
+  out->rounds = h->rounds;
+  out->rollout_ms = h->rollout_ms;
+  out->recheck_ms = h->recheck_ms;
+  out->timed_rollouts = h->timed_rollouts;
+  return RRG_OK;
+}
+
+int rrg_reset_stats(rrg_handle h) {
+  if (!h) return RRG_EINVAL;
+  DeviceGuard g(h->device);
+  rrg_stats tmp;
+  int rc = rrg_get_stats(h, &tmp);  // drains pending events
+  if (rc != RRG_OK) return rc;
+  CK(cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->launches = h->rollout_launches = h->rounds = 0;
+  h->rollout_ms = h->recheck_ms = 0.0;
+  h->timed_rollouts = 0;
+  return RRG_OK;
+}
+
+}  // extern "C"

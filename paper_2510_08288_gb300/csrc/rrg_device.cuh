@@ -1,0 +1,135 @@
+// rrg_device.cuh -- device-side building blocks of the robust reference
+// governor: the FC3 closed-loop right-hand side and output, the RK4 step,
+// the Philox4x64-10 scenario generator and order-preserving keys for
+// atomic minima.  Included by rrg_kernels.cu only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rrg {
+
+// ---------------------------------------------------------------------------
+// FC3 constants.  The state is kept in gauge coordinates
+//   q = [p_ca - p_atm, w_cp, p_sm - p_atm]
+// so that the pressure differences that set every flow (and the output) are
+// formed from numbers of the size of the differences, not of ~1e5 Pa: in
+// binary32 this keeps about 3 more significant bits in the slack.  All
+// constants are folded once per handle in binary64 and rounded once.
+template <typename T>
+struct Fc3K {
+  T inv_p_atm;   // 1 / p_atm
+  T a_w, a_p;    // compressor map W_cp = a_w w - a_p q_sm
+  T k_sm, k_ca;  // orifice and outlet coefficients
+  T e;           // (gamma - 1) / gamma
+  T C_cp;        // c_p T_atm / eta_cp
+  T C_m;         // eta_cm k_t / R_cm
+  T k_v;         // back-EMF constant
+  T K_p;         // controller gain on the air-flow error
+  T RT_Vca;      // R_a T_st / V_ca
+  T RT_Vsm;      // R_a T_st / V_sm
+  T inv_J;       // 1 / J_cp
+};
+
+// Per-candidate constants (functions of the governed setpoint v = I only).
+template <typename T>
+struct CandK {
+  T W_o2;     // O2 consumed, M_O2 n_cell I / (4 F)
+  T V0;       // v_ff(I) + K_p W_ref(I): motor voltage at zero flow error
+  T y_scale;  // x_O2 k_sm / W_o2: OER per pascal of p_sm - p_ca
+};
+
+template <typename T> __device__ __forceinline__ T pow_e(T x, T e);
+template <> __device__ __forceinline__ float pow_e<float>(float x, float e) { return __powf(x, e); }
+template <> __device__ __forceinline__ double pow_e<double>(double x, double e) { return pow(x, e); }
+
+template <typename T> __device__ __forceinline__ T div_fast(T a, T b);
+template <> __device__ __forceinline__ float div_fast<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double div_fast<double>(double a, double b) { return a / b; }
+
+// dq/dt of the FC3 closed loop (mass balances of the cathode and supply
+// manifold, torque balance of the compressor shaft under a feed-forward +
+// proportional air-flow controller).
+template <typename T>
+__device__ __forceinline__ void fc3_rhs(const Fc3K<T>& K, const CandK<T>& C,
+                                        T q_ca, T w, T q_sm,
+                                        T& d_ca, T& d_w, T& d_sm) {
+  const T W_cp = K.a_w * w - K.a_p * q_sm;
+  const T W_sm = K.k_sm * (q_sm - q_ca);
+  const T W_ca = K.k_ca * q_ca;
+  const T pr_e = pow_e<T>(T(1) + q_sm * K.inv_p_atm, K.e) - T(1);
+  const T tau_cp = div_fast<T>(K.C_cp * pr_e * W_cp, w);
+  const T tau_cm = K.C_m * ((C.V0 - K.K_p * W_cp) - K.k_v * w);
+  d_ca = K.RT_Vca * (W_sm - W_ca - C.W_o2);
+  d_w = (tau_cm - tau_cp) * K.inv_J;
+  d_sm = K.RT_Vsm * (W_cp - W_sm);
+}
+
+// Oxygen excess ratio y = h(x, v).
+template <typename T>
+__device__ __forceinline__ T fc3_output(const CandK<T>& C, T q_ca, T q_sm) {
+  return C.y_scale * (q_sm - q_ca);
+}
+
+// One classical RK4 step of size dt, in place.
+template <typename T>
+__device__ __forceinline__ void rk4_step(const Fc3K<T>& K, const CandK<T>& C, T dt,
+                                         T& q_ca, T& w, T& q_sm) {
+  const T h2 = T(0.5) * dt, h6 = dt / T(6);
+  T a1, b1, c1, a2, b2, c2, a3, b3, c3, a4, b4, c4;
+  fc3_rhs<T>(K, C, q_ca, w, q_sm, a1, b1, c1);
+  fc3_rhs<T>(K, C, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, a2, b2, c2);
+  fc3_rhs<T>(K, C, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, a3, b3, c3);
+  fc3_rhs<T>(K, C, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, a4, b4, c4);
+  q_ca += h6 * ((a1 + a4) + T(2) * (a2 + a3));
+  w += h6 * ((b1 + b4) + T(2) * (b2 + b3));
+  q_sm += h6 * ((c1 + c4) + T(2) * (c2 + c3));
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10, written from Salmon et al., "Parallel random numbers: as easy
+// as 1, 2, 3" (SC'11): per round two 64x64 -> 128-bit products, words
+// permuted and xored with the key; the key advances by a Weyl sequence.
+struct U64x4 { uint64_t w[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                               uint64_t c3, uint64_t k0, uint64_t k1) {
+  constexpr uint64_t kM0 = 0xD2E7470EE14C6C93ull, kM1 = 0xCA5A826395121157ull;
+  constexpr uint64_t kW0 = 0x9E3779B97F4A7C15ull, kW1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += kW0; k1 += kW1; }
+    const uint64_t hi0 = __umul64hi(kM0, c0), lo0 = kM0 * c0;
+    const uint64_t hi1 = __umul64hi(kM1, c2), lo1 = kM1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  U64x4 o;
+  o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+  return o;
+}
+
+// a (2u - 1) with u the top 53 bits of w scaled to [0, 1).
+__device__ __forceinline__ double uniform_sym(uint64_t w, double a) {
+  const double u = __dmul_rn(static_cast<double>(w >> 11), 0x1.0p-53);
+  return __dmul_rn(a, __dsub_rn(__dmul_rn(2.0, u), 1.0));
+}
+
+// ---------------------------------------------------------------------------
+// Order-preserving 64-bit key of a double (for atomicMin); NaN must be mapped
+// by the caller.
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dunkey(unsigned long long k) {
+  return (k >> 63) ? __longlong_as_double(static_cast<long long>(k & 0x7FFFFFFFFFFFFFFFull))
+                   : __longlong_as_double(static_cast<long long>(~k));
+}
+
+// Eq. 2 evaluated as written, without fused multiply-add.
+__device__ __forceinline__ double governed(double v_prev, double r, double kappa) {
+  return __dadd_rn(v_prev, __dmul_rn(kappa, __dsub_rn(r, v_prev)));
+}
+
+}  // namespace rrg

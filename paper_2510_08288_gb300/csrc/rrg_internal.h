@@ -1,0 +1,130 @@
+// rrg_internal.h -- types shared by the kernels (rrg_kernels.cu) and the
+// host side of the C ABI (rrg_capi.cu).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rrg.h"
+
+namespace rrg {
+
+template <typename T> struct Fc3K;
+template <typename T> struct CandK;
+
+// FC3 parameter indices (the layout documented in rrg.h).
+enum ParamIdx {
+  P_P_ATM = 0, P_T_ATM, P_T_ST, P_R_A, P_V_SM, P_V_CA, P_K_SM, P_K_CA,
+  P_N_CELL, P_FARADAY, P_M_O2, P_X_O2, P_GAMMA, P_C_P, P_ETA_CP, P_J_CP,
+  P_ETA_CM, P_K_T, P_K_V, P_R_CM, P_A_W, P_A_P, P_LAM_REF, P_K_P,
+  P_C0, P_C1, P_C2, P_COUNT
+};
+static_assert(P_COUNT == RRG_NPARAM, "parameter layout");
+
+constexpr int kMaxTreeNodes = 2 * RRG_MAX_CANDIDATES;
+
+// Device-resident state of one RG update's search (one per handle).
+struct SearchState {
+  double x[3];        // x_t (absolute coordinates)
+  double v_prev, r;   // v_{t-1}, r_t
+  double lo, hi;      // bisection bracket / k-section bracket
+  double kappa;       // next kappa Alg. 1 would test
+  double kappa_opt;   // best admissible kappa so far
+  int32_t iter;       // Alg. 1 iterations consumed
+  int32_t any;        // some evaluated candidate was admissible
+  int32_t done;       // search finished; outputs written
+  int32_t flags;      // RRG flags of the result
+  int32_t m;          // candidates of the current round
+  int32_t depth;      // tree levels of the current round (bisection)
+  int32_t round;      // rounds finished
+  int32_t invalid;    // inputs rejected on the device
+  double v_t_out;     // governed reference of the finished search
+  int32_t slot_of_node[kMaxTreeNodes];  // bisection tree: heap node -> slot
+};
+
+// Device counters of a handle.
+struct DevStats {
+  unsigned long long lane_steps;
+  unsigned long long lane_steps_fp64;
+  unsigned long long rechecked;
+};
+
+// Closed-loop device state.
+struct LoopState {
+  double x[3];
+  double v_prev;
+  unsigned long long t;   // updates done since the loop started
+};
+
+// Search configuration passed by value to the search kernels.
+struct SearchCfg {
+  int search;        // RRG_SEARCH_*
+  int m_cap;         // candidates per round
+  int n_bisect;      // N_kappa
+  int n_rounds;      // k-section rounds
+  int ss_check;
+  double y_min, eps_ss, y_c;
+};
+
+// Everything a launch needs; filled by the host side from the handle.
+struct Launch {
+  cudaStream_t stream;
+  int N, H, precision, early_exit, m_cap;
+  double dt, y_min, eps_abs;
+  SearchCfg scfg;
+  const double* params;         // [RRG_NPARAM]
+  const Fc3K<double>* k64_dev;  // folded constants (device copy)
+  const Fc3K<float>* k32_dev;
+  const void* k64_host;         // host copies, passed by value to rollouts
+  const void* k32_host;
+  double* d64;                  // scenarios [3][H][N]
+  float* d32;
+  SearchState* st;
+  double* cand_kappa;
+  double* cand_v;
+  CandK<double>* cand_k64;
+  CandK<float>* cand_k32;
+  int32_t* cand_ok;    // AND of the round's trajectory decisions
+  int32_t* cand_dead;  // set once the candidate is known to fail
+  int32_t* cand_ss;    // steady-state check passed
+  unsigned long long* cand_min;
+  uint32_t* recheck_list;
+  uint32_t* recheck_count;
+  DevStats* stats;
+  uint8_t* P;                   // optional
+  int recheck_blocks;
+};
+
+// ---- kernel launchers (rrg_kernels.cu) --------------------------------
+cudaError_t launch_fold_constants(const double* params, Fc3K<double>* k64, Fc3K<float>* k32,
+                                  cudaStream_t s);
+size_t fc3k_size(bool fp64);
+cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
+                          const unsigned long long* t_dev, const double* amp);
+cudaError_t launch_round_scenarios(const Launch& L);
+cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
+                                const unsigned long long* t_dev, const double* d_v_prev);
+cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa,
+                               int32_t* d_flags);
+cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
+                                const double* d_kappas, int m);
+cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d_min_slack);
+cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
+                           bool recheck_classify);
+cudaError_t launch_recheck(const Launch& L, int early_exit);
+cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_t* d_status);
+cudaError_t launch_plant(const Launch& L, const double* d_x, const double* d_v, uint64_t seed,
+                         uint64_t base, const unsigned long long* t_dev, const double* amp_dev,
+                         double* d_x_next);
+cudaError_t launch_loop_end(const Launch& L, LoopState* ls, uint64_t seed, uint64_t t0,
+                            const double* amp_dev, double* d_v_out, double* d_kappa_out,
+                            int32_t* d_flags_out, double* d_x_out);
+cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, double v0,
+                             double* d_x_out);
+
+// Number of search rounds each strategy enqueues (host-side schedule).
+int search_round_count(const SearchCfg& c);
+// Largest candidate count of any round of the schedule.
+int search_round_width(const SearchCfg& c, int round);
+
+}  // namespace rrg

@@ -1,0 +1,757 @@
+// rrg_kernels.cu -- CUDA kernels of the robust reference governor update.
+//
+// One RG update (Alg. 3 and the bisection of Alg. 1/2, on the joint
+// all-scenario predicate) is a fixed sequence of launches on one stream:
+//
+//   sample_kernel            d_j^k for all (j, k)            (Sec. II-C)
+//   search_begin_kernel      round-1 candidates, v_i (Eq. 2), steady-state
+//                            check y_ss(v_i) (Eq. 3)
+//   { rollout_kernel<T>      one thread per (candidate i, scenario k): RK4
+//                            rollout with the output check at every step and
+//                            early exit (Alg. 3 steps 2-3), warp AND / min of
+//                            the per-trajectory results into per-candidate
+//                            flags and min slack (Eq. 5 reduced on the device)
+//     recheck_kernel         binary64 re-run of near-zero-slack trajectories
+//     search_next_kernel  }  decide (Alg. 1 / Alg. 3 / k-section), build the
+//                            next round's candidates or write the result
+//
+// Nothing returns to the host between rounds; the whole update can be
+// captured in a CUDA graph.
+#include <cfloat>
+#include <cmath>
+
+#include "rrg_device.cuh"
+#include "rrg_internal.h"
+
+namespace rrg {
+
+constexpr int kRollThreads = 128;
+constexpr int kSearchThreads = 256;
+
+template <typename T> __device__ __forceinline__ T max_finite();
+template <> __device__ __forceinline__ float max_finite<float>() { return FLT_MAX; }
+template <> __device__ __forceinline__ double max_finite<double>() { return DBL_MAX; }
+template <typename T> __device__ __forceinline__ T inf_v();
+template <> __device__ __forceinline__ float inf_v<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double inf_v<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+size_t fc3k_size(bool fp64) { return fp64 ? sizeof(Fc3K<double>) : sizeof(Fc3K<float>); }
+
+// ---------------------------------------------------------------------------
+// Constant folding (once per handle).
+__global__ void fold_constants_kernel(const double* __restrict__ P, Fc3K<double>* k64,
+                                      Fc3K<float>* k32) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Fc3K<double> K;
+  K.inv_p_atm = 1.0 / P[P_P_ATM];
+  K.a_w = P[P_A_W];
+  K.a_p = P[P_A_P];
+  K.k_sm = P[P_K_SM];
+  K.k_ca = P[P_K_CA];
+  K.e = (P[P_GAMMA] - 1.0) / P[P_GAMMA];
+  K.C_cp = P[P_C_P] * P[P_T_ATM] / P[P_ETA_CP];
+  K.C_m = P[P_ETA_CM] * P[P_K_T] / P[P_R_CM];
+  K.k_v = P[P_K_V];
+  K.K_p = P[P_K_P];
+  K.RT_Vca = P[P_R_A] * P[P_T_ST] / P[P_V_CA];
+  K.RT_Vsm = P[P_R_A] * P[P_T_ST] / P[P_V_SM];
+  K.inv_J = 1.0 / P[P_J_CP];
+  *k64 = K;
+  Fc3K<float> F;
+  F.inv_p_atm = static_cast<float>(K.inv_p_atm);
+  F.a_w = static_cast<float>(K.a_w);
+  F.a_p = static_cast<float>(K.a_p);
+  F.k_sm = static_cast<float>(K.k_sm);
+  F.k_ca = static_cast<float>(K.k_ca);
+  F.e = static_cast<float>(K.e);
+  F.C_cp = static_cast<float>(K.C_cp);
+  F.C_m = static_cast<float>(K.C_m);
+  F.k_v = static_cast<float>(K.k_v);
+  F.K_p = static_cast<float>(K.K_p);
+  F.RT_Vca = static_cast<float>(K.RT_Vca);
+  F.RT_Vsm = static_cast<float>(K.RT_Vsm);
+  F.inv_J = static_cast<float>(K.inv_J);
+  *k32 = F;
+}
+
+cudaError_t launch_fold_constants(const double* params, Fc3K<double>* k64, Fc3K<float>* k32,
+                                  cudaStream_t s) {
+  fold_constants_kernel<<<1, 32, 0, s>>>(params, k64, k32);
+  return cudaGetLastError();
+}
+
+// Constants of the closed loop at setpoint I (binary64).
+__device__ __forceinline__ CandK<double> cand_consts(const double* __restrict__ P, double I) {
+  CandK<double> C;
+  C.W_o2 = P[P_M_O2] * P[P_N_CELL] * I / (4.0 * P[P_FARADAY]);
+  const double W_ref = P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
+  C.V0 = P[P_C0] + P[P_C1] * I + P[P_C2] * I * I + P[P_K_P] * W_ref;
+  C.y_scale = P[P_X_O2] * P[P_K_SM] / C.W_o2;
+  return C;
+}
+
+// ---------------------------------------------------------------------------
+// Equilibrium manifold (Sec. II-A).  At rest the cathode balance fixes the
+// cathode gauge pressure from the air flow W, the orifice fixes the supply
+// manifold pressure and the compressor map the speed, leaving the shaft
+// torque balance g(W) = 0.  g decreases in W; it is bracketed on
+// [W_o2, 2 lam_ref W_o2 / x_O2 * 2^n] and solved by the Illinois variant of
+// regula falsi (Dowell & Jarratt, BIT 11, 1971).
+__device__ double eq_torque(const Fc3K<double>& K, const double* __restrict__ P,
+                            const CandK<double>& C, double W, double q[3]) {
+  q[0] = (W - C.W_o2) / P[P_K_CA];
+  q[2] = q[0] + W / P[P_K_SM];
+  q[1] = (W + P[P_A_P] * q[2]) / P[P_A_W];
+  double a, b, c;
+  fc3_rhs<double>(K, C, q[0], q[1], q[2], a, b, c);
+  return b;
+}
+
+__device__ int equilibrium_dev(const Fc3K<double>& K, const double* __restrict__ P, double I,
+                               double q[3], double* y_ss) {
+  if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
+  const CandK<double> C = cand_consts(P, I);
+  double lo = C.W_o2, hi = 2.0 * P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
+  double glo = eq_torque(K, P, C, lo, q);
+  double ghi = eq_torque(K, P, C, hi, q);
+  for (int it = 0; it < 60 && ghi > 0.0; ++it) {
+    hi *= 2.0;
+    ghi = eq_torque(K, P, C, hi, q);
+  }
+  if (!(glo > 0.0) || !(ghi < 0.0)) return -2;
+  int side = 0;
+  double W = 0.5 * (lo + hi), W_last = lo;
+  for (int it = 0; it < 200; ++it) {
+    W = (lo * ghi - hi * glo) / (ghi - glo);
+    if (!(W > lo && W < hi)) W = 0.5 * (lo + hi);
+    const double g = eq_torque(K, P, C, W, q);
+    if (g == 0.0) break;
+    if (g > 0.0) {
+      lo = W; glo = g;
+      if (side == 1) ghi *= 0.5;
+      side = 1;
+    } else {
+      hi = W; ghi = g;
+      if (side == -1) glo *= 0.5;
+      side = -1;
+    }
+    if (fabs(W - W_last) <= 2e-16 * W || hi - lo <= 2e-16 * hi) break;
+    W_last = W;
+  }
+  eq_torque(K, P, C, W, q);
+  *y_ss = fc3_output<double>(C, q[0], q[2]);
+  return 0;
+}
+
+__global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<double>* k64,
+                                   double v, double* out4, int32_t* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double q[3], y = 0.0;
+  const int rc = equilibrium_dev(*k64, P, v, q, &y);
+  out4[0] = q[0] + P[P_P_ATM];
+  out4[1] = q[1];
+  out4[2] = q[2] + P[P_P_ATM];
+  out4[3] = y;
+  *status = rc;
+}
+
+cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_t* d_status) {
+  equilibrium_kernel<<<1, 32, 0, L.stream>>>(L.params, L.k64_dev, v, d_out4, d_status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Scenario sampling: one thread per (j, k), coalesced over k.
+__global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32, int N, int H,
+                              uint64_t seed, uint64_t base, const unsigned long long* t_dev,
+                              double a0, double a1, double a2) {
+  const uint64_t upd = base + (t_dev ? *t_dev : 0ull);
+  const size_t HN = static_cast<size_t>(H) * N;
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
+    const uint64_t j = q / static_cast<uint64_t>(N), k = q - j * static_cast<uint64_t>(N);
+    const U64x4 w = philox4x64_10(j, k, upd, 0ull, seed, 0ull);
+    const double x0 = uniform_sym(w.w[0], a0);
+    const double x1 = uniform_sym(w.w[1], a1);
+    const double x2 = uniform_sym(w.w[2], a2);
+    d64[q] = x0;
+    d64[HN + q] = x1;
+    d64[2 * HN + q] = x2;
+    d32[q] = static_cast<float>(x0);
+    d32[HN + q] = static_cast<float>(x1);
+    d32[2 * HN + q] = static_cast<float>(x2);
+  }
+}
+
+static int grid_for(size_t n, int threads, int cap) {
+  size_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > static_cast<size_t>(cap)) b = cap;
+  return static_cast<int>(b);
+}
+
+cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
+                          const unsigned long long* t_dev, const double* amp) {
+  const size_t n = static_cast<size_t>(L.H) * L.N;
+  sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(
+      L.d64, L.d32, L.N, L.H, seed, base, t_dev, amp[0], amp[1], amp[2]);
+  return cudaGetLastError();
+}
+
+__global__ void round_scenarios_kernel(const double* __restrict__ d64, float* __restrict__ d32,
+                                       size_t n) {
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += stride)
+    d32[q] = static_cast<float>(d64[q]);
+}
+
+cudaError_t launch_round_scenarios(const Launch& L) {
+  const size_t n = 3 * static_cast<size_t>(L.H) * L.N;
+  round_scenarios_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.d32, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One trajectory: x_0 = x_t, x_{j+1} = RK4(x_j, v) + d_j, slack s_j =
+// h(x_j, v) - y_min at j = 0..H; a non-finite state or output counts as
+// s = -inf.  Stops when s < thr (thr = -inf: never), and, every 32 steps,
+// when *dead is set.  Returns min_j s_j; *steps receives the RK4 steps done.
+template <typename T>
+__device__ __forceinline__ T checked_slack(const CandK<T>& C, T q_ca, T w, T q_sm, T y_min) {
+  const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
+  const T z = q_ca + w + q_sm;
+  return (fabs(z) <= max_finite<T>() && fabs(s) <= max_finite<T>()) ? s : -inf_v<T>();
+}
+
+template <typename T>
+__device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
+                                      const T* __restrict__ d, int k, int N, int H,
+                                      T q_ca, T w, T q_sm, T dt, T y_min, T thr,
+                                      const volatile int32_t* dead, unsigned* steps) {
+  T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+  T smin = s;
+  bool stop = (s < thr) || (H == 0);
+  int j = 0;
+  const size_t HN = static_cast<size_t>(H) * N;
+  const T* dp = d + k;
+  while (!stop) {
+    const T d0 = __ldg(dp), d1 = __ldg(dp + HN), d2 = __ldg(dp + 2 * HN);
+    dp += N;
+    rk4_step<T>(K, C, dt, q_ca, w, q_sm);
+    q_ca += d0;
+    w += d1;
+    q_sm += d2;
+    ++j;
+    s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    smin = fmin(smin, s);
+    stop = (s < thr) || (j == H);
+    if (dead != nullptr && !stop && (j & 31) == 0) stop = (*dead != 0);
+  }
+  *steps = static_cast<unsigned>(j);
+  return smin;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One thread per (candidate i = blockIdx.y, scenario k).  classify = 1 is the
+// binary32 pass of RRG_FP32_RECHECK: trajectories whose min slack lies in
+// [-eps, eps) are appended to the recheck list and decided later in binary64.
+template <typename T>
+__global__ void __launch_bounds__(kRollThreads)
+rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d,
+               const CandK<T>* __restrict__ cand, int early_exit, int classify) {
+  const int i = blockIdx.y;
+  if (i >= L.st->m) return;
+  const int N = L.N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = k < N;
+  if (!L.cand_ss[i]) {
+    // steady-state check failed: the whole row of P is 0, no rollout
+    if (L.P != nullptr && active) L.P[static_cast<size_t>(i) * N + k] = 0;
+    return;
+  }
+  volatile int32_t* dead = L.cand_dead + i;
+  const bool cand_stop = early_exit == RRG_EXIT_CANDIDATE;
+  if (cand_stop) {
+    // another block may already have found a violation; read once per warp so
+    // the warp leaves (or stays) as a whole before the warp reductions below
+    const int dead0 = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? *dead : 0, 0);
+    if (dead0) return;
+  }
+  const CandK<T> C = cand[i];
+  const T eps = static_cast<T>(L.eps_abs);
+  const T thr = early_exit != RRG_EXIT_NONE ? (classify ? -eps : T(0)) : -inf_v<T>();
+
+  T smin = inf_v<T>();
+  unsigned steps = 0;
+  if (active) {
+    const double p_atm = L.params[P_P_ATM];
+    smin = run_lane<T>(K, C, d, k, N, L.H, static_cast<T>(L.st->x[0] - p_atm),
+                       static_cast<T>(L.st->x[1]), static_cast<T>(L.st->x[2] - p_atm),
+                       static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+                       cand_stop ? dead : nullptr, &steps);
+    if (cand_stop && smin < thr) *dead = 1;
+  }
+  bool lane_ok = true, uncertain = false;
+  double contrib = static_cast<double>(inf_v<T>());
+  if (active) {
+    if (classify) {
+      if (smin >= eps) {
+        contrib = smin;
+      } else if (smin < -eps) {
+        lane_ok = false;
+        contrib = smin;
+      } else {
+        uncertain = true;
+      }
+    } else {
+      lane_ok = smin >= T(0);
+      contrib = smin;
+    }
+  }
+  if (uncertain && *dead == 0) {
+    const uint32_t slot = atomicAdd(L.recheck_count, 1u);
+    L.recheck_list[slot] = static_cast<uint32_t>(i) * static_cast<uint32_t>(N) + static_cast<uint32_t>(k);
+  }
+  if (L.P != nullptr && active) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
+
+  const bool all_ok = __all_sync(0xffffffffu, lane_ok);
+  const double wmin = warp_min(contrib);
+  const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
+  if ((threadIdx.x & 31) == 0) {
+    if (!all_ok) L.cand_ok[i] = 0;
+    if (wmin < static_cast<double>(inf_v<T>())) atomicMin(L.cand_min + i, dkey(wmin));
+    if (wsteps) {
+      atomicAdd(&L.stats->lane_steps, static_cast<unsigned long long>(wsteps));
+      if (sizeof(T) == 8) atomicAdd(&L.stats->lane_steps_fp64, static_cast<unsigned long long>(wsteps));
+    }
+  }
+}
+
+cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
+                           bool recheck_classify) {
+  dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
+  if (use_fp64) {
+    rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(
+        L, *static_cast<const Fc3K<double>*>(L.k64_host), L.d64, L.cand_k64, early_exit, 0);
+  } else {
+    rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(
+        L, *static_cast<const Fc3K<float>*>(L.k32_host), L.d32, L.cand_k32, early_exit,
+        recheck_classify ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+// Binary64 re-run of the trajectories the binary32 pass could not decide.
+__global__ void __launch_bounds__(64)
+recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
+  const uint32_t count = *L.recheck_count;
+  const int N = L.N;
+  const double p_atm = L.params[P_P_ATM];
+  const double thr = early_exit != RRG_EXIT_NONE ? 0.0 : -inf_v<double>();
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    const uint32_t idx = L.recheck_list[e];
+    const int i = static_cast<int>(idx / static_cast<uint32_t>(N));
+    const int k = static_cast<int>(idx - static_cast<uint32_t>(i) * static_cast<uint32_t>(N));
+    // a failed candidate needs no more decisions, unless P asks for every entry
+    if (L.P == nullptr && !L.cand_ok[i]) continue;
+    unsigned steps = 0;
+    const double smin = run_lane<double>(K, L.cand_k64[i], L.d64, k, N, L.H, L.st->x[0] - p_atm,
+                                         L.st->x[1], L.st->x[2] - p_atm, L.dt, L.y_min, thr,
+                                         nullptr, &steps);
+    const bool ok = smin >= 0.0;
+    if (!ok) L.cand_ok[i] = 0;
+    if (L.P != nullptr) L.P[static_cast<size_t>(i) * N + k] = ok ? 1 : 0;
+    atomicMin(L.cand_min + i, dkey(smin));
+    atomicAdd(&L.stats->lane_steps, static_cast<unsigned long long>(steps));
+    atomicAdd(&L.stats->lane_steps_fp64, static_cast<unsigned long long>(steps));
+    atomicAdd(&L.stats->rechecked, 1ull);
+  }
+}
+
+cudaError_t launch_recheck(const Launch& L, int early_exit) {
+  recheck_kernel<<<L.recheck_blocks, 64, 0, L.stream>>>(
+      L, *static_cast<const Fc3K<double>*>(L.k64_host), early_exit);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Search.  Thread 0 of a single block runs the decision logic; the block then
+// prepares the round's candidates in parallel (v_i by Eq. 2, constants, the
+// steady-state check of Eq. 3 by one equilibrium solve per candidate).
+
+// Bisection tree of Alg. 1 from the state (lo, hi, kappa): heap node 1 is
+// the next kappa to test; node 2n is the state after "infeasible" at node n
+// (hi <- kappa), node 2n+1 after "feasible" (lo <- kappa); a feasible
+// kappa = 1 ends Alg. 1, so the right subtree of a kappa = 1 node is empty.
+__device__ int tree_count(bool root_is_one, int d) {
+  return root_is_one ? (1 << (d - 1)) : ((1 << d) - 1);
+}
+
+__device__ int choose_depth(const SearchState* s, const SearchCfg& c) {
+  const int remaining = c.n_bisect - s->iter;
+  const bool one = s->kappa == 1.0;
+  int d = 1;
+  while (d + 1 <= remaining && d + 1 <= 11 && tree_count(one, d + 1) <= c.m_cap) ++d;
+  return d;
+}
+
+__device__ int build_tree(SearchState* s, double* cand_kappa, int depth) {
+  int count = 0;
+  const int nodes = 1 << depth;
+  for (int n = 1; n < nodes; ++n) {
+    const int lev = 31 - __clz(n);
+    double lo = s->lo, hi = s->hi, k = s->kappa;
+    bool valid = true;
+    for (int b = lev - 1; b >= 0; --b) {
+      if ((n >> b) & 1) {
+        if (k == 1.0) { valid = false; break; }
+        lo = k;
+      } else {
+        hi = k;
+      }
+      k = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    }
+    if (valid) {
+      s->slot_of_node[n] = count;
+      cand_kappa[count++] = k;
+    } else {
+      s->slot_of_node[n] = -1;
+    }
+  }
+  return count;
+}
+
+// Follows Alg. 1's path through the evaluated tree.
+__device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* cand_ok) {
+  int n = 1;
+  for (int lev = 0; lev < s->depth; ++lev) {
+    const int slot = s->slot_of_node[n];
+    if (slot < 0) break;  // cannot happen: the path only visits valid nodes
+    const double k = s->kappa;
+    s->iter += 1;
+    if (cand_ok[slot]) {
+      s->kappa_opt = k;
+      s->any = 1;
+      if (k == 1.0) { s->done = 1; return; }
+      s->lo = k;
+      n = 2 * n + 1;
+    } else {
+      s->hi = k;
+      n = 2 * n;
+    }
+    s->kappa = __dmul_rn(__dadd_rn(s->lo, s->hi), 0.5);
+    if (s->iter >= c.n_bisect) { s->done = 1; return; }
+  }
+}
+
+__device__ int grid_points(double* cand_kappa, int M) {
+  for (int i = 0; i < M; ++i)
+    cand_kappa[i] = __ddiv_rn(static_cast<double>(i), static_cast<double>(M - 1));
+  return M;
+}
+
+__device__ int interior_points(double* cand_kappa, int M, double lo, double hi) {
+  const double w = __dsub_rn(hi, lo);
+  for (int i = 0; i < M; ++i)
+    cand_kappa[i] = __dadd_rn(lo, __ddiv_rn(__dmul_rn(w, static_cast<double>(i + 1)),
+                                            static_cast<double>(M + 1)));
+  return M;
+}
+
+// Prepares the first round after the inputs were stored; returns m.
+__device__ int first_round(SearchState* s, const SearchCfg& c, double* cand_kappa) {
+  s->lo = 0.0; s->hi = 1.0; s->kappa = 1.0; s->kappa_opt = 0.0;
+  s->iter = 0; s->any = 0; s->done = 0; s->flags = 0; s->round = 0;
+  if (c.search == RRG_SEARCH_GRID || c.search == RRG_SEARCH_KSECTION)
+    return grid_points(cand_kappa, c.m_cap);
+  s->depth = choose_depth(s, c);
+  return build_tree(s, cand_kappa, s->depth);
+}
+
+// Decides from the evaluated round and prepares the next; returns next m.
+__device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa,
+                          const int32_t* cand_ok) {
+  const int m = s->m;
+  if (c.search == RRG_SEARCH_BISECT || c.search == RRG_SEARCH_SPEC_BISECT) {
+    walk_tree(s, c, cand_ok);
+    s->round += 1;
+    if (s->done) return 0;
+    s->depth = choose_depth(s, c);
+    return build_tree(s, cand_kappa, s->depth);
+  }
+  int best = -1;
+  for (int i = 0; i < m; ++i)
+    if (cand_ok[i]) best = i;
+  if (c.search == RRG_SEARCH_GRID) {
+    if (best >= 0) { s->kappa_opt = cand_kappa[best]; s->any = 1; }
+    s->round += 1;
+    s->done = 1;
+    return 0;
+  }
+  // k-section
+  if (s->round == 0) {
+    if (best < 0) { s->done = 1; s->round = 1; return 0; }
+    s->any = 1;
+    s->kappa_opt = cand_kappa[best];
+    if (best == m - 1) { s->done = 1; s->round = 1; return 0; }
+    s->lo = cand_kappa[best];
+    s->hi = cand_kappa[best + 1];
+  } else if (best < 0) {
+    s->hi = cand_kappa[0];
+  } else {
+    s->kappa_opt = cand_kappa[best];
+    s->lo = cand_kappa[best];
+    if (best < m - 1) s->hi = cand_kappa[best + 1];
+  }
+  s->round += 1;
+  if (s->round >= c.n_rounds) { s->done = 1; return 0; }
+  return interior_points(cand_kappa, c.m_cap, s->lo, s->hi);
+}
+
+__device__ void prepare_candidates(const Launch& L, int m) {
+  const SearchState* s = L.st;
+  const Fc3K<double> K = *L.k64_dev;
+  const double thr_ss =
+      __dadd_rn(L.scfg.y_min, __dmul_rn(L.scfg.eps_ss, __dsub_rn(L.scfg.y_c, L.scfg.y_min)));
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double v = governed(s->v_prev, s->r, L.cand_kappa[i]);
+    L.cand_v[i] = v;
+    const CandK<double> C = cand_consts(L.params, v);
+    L.cand_k64[i] = C;
+    CandK<float> F;
+    F.W_o2 = static_cast<float>(C.W_o2);
+    F.V0 = static_cast<float>(C.V0);
+    F.y_scale = static_cast<float>(C.y_scale);
+    L.cand_k32[i] = F;
+    int ok = 1;
+    if (L.scfg.ss_check) {
+      double q[3], y_ss = 0.0;
+      ok = (equilibrium_dev(K, L.params, v, q, &y_ss) == 0) && (y_ss >= thr_ss);
+    }
+    L.cand_ok[i] = ok;
+    L.cand_ss[i] = ok;
+    L.cand_dead[i] = ok ? 0 : 1;
+    L.cand_min[i] = dkey(inf_v<double>());
+  }
+  if (threadIdx.x == 0) *L.recheck_count = 0u;
+}
+
+__device__ void write_result(SearchState* s, double* v_t, double* kappa, int32_t* flags) {
+  s->flags = (s->any ? 0 : 1) | (s->invalid ? 2 : 0);
+  const double kap = s->invalid ? 0.0 : s->kappa_opt;
+  const double v = s->invalid ? s->v_prev : governed(s->v_prev, s->r, kap);
+  s->kappa_opt = kap;
+  s->v_t_out = v;
+  if (v_t) *v_t = v;
+  if (kappa) *kappa = kap;
+  if (flags) *flags = s->flags;
+}
+
+__global__ void __launch_bounds__(kSearchThreads)
+search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double* __restrict__ d_r,
+                    const unsigned long long* t_dev, const double* __restrict__ d_v_prev) {
+  __shared__ int m_sh;
+  SearchState* s = L.st;
+  if (threadIdx.x == 0) {
+    const double x0 = d_x[0], x1 = d_x[1], x2 = d_x[2];
+    const double r = d_r[t_dev ? *t_dev : 0ull];
+    const double vp = *d_v_prev;
+    s->x[0] = x0; s->x[1] = x1; s->x[2] = x2;
+    s->r = r;
+    s->v_prev = vp;
+    const bool fin = fabs(x0) <= DBL_MAX && fabs(x1) <= DBL_MAX && fabs(x2) <= DBL_MAX &&
+                     fabs(r) <= DBL_MAX && fabs(vp) <= DBL_MAX;
+    s->invalid = (!fin || !(vp > 0.0) || !(r > 0.0)) ? 1 : 0;
+    int m = first_round(s, L.scfg, L.cand_kappa);
+    if (s->invalid) { s->done = 1; m = 0; }
+    s->m = m;
+    m_sh = m;
+  }
+  __syncthreads();
+  prepare_candidates(L, m_sh);
+}
+
+__global__ void __launch_bounds__(kSearchThreads)
+search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
+  __shared__ int m_sh;
+  SearchState* s = L.st;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    if (!s->done) m = next_round(s, L.scfg, L.cand_kappa, L.cand_ok);
+    if (s->done) {
+      m = 0;
+      write_result(s, v_t, kappa, flags);
+    }
+    s->m = m;
+    m_sh = m;
+  }
+  __syncthreads();
+  if (m_sh > 0) prepare_candidates(L, m_sh);
+}
+
+cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
+                                const unsigned long long* t_dev, const double* d_v_prev) {
+  search_begin_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa, int32_t* d_flags) {
+  search_next_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_v_t, d_kappa, d_flags);
+  return cudaGetLastError();
+}
+
+// Explicit candidates (rrg_eval_candidates).
+__global__ void __launch_bounds__(kSearchThreads)
+eval_prepare_kernel(const Launch L, const double* __restrict__ d_x, double v_prev, double r,
+                    const double* __restrict__ d_kappas, int m) {
+  SearchState* s = L.st;
+  if (threadIdx.x == 0) {
+    s->x[0] = d_x[0]; s->x[1] = d_x[1]; s->x[2] = d_x[2];
+    s->v_prev = v_prev;
+    s->r = r;
+    s->m = m;
+    s->done = 0;
+    s->invalid = 0;
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) L.cand_kappa[i] = d_kappas[i];
+  __syncthreads();
+  prepare_candidates(L, m);
+}
+
+__global__ void eval_finish_kernel(const Launch L, int m, uint8_t* adm, double* min_slack) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const bool ss_failed = !L.cand_ss[i];
+    adm[i] = L.cand_ok[i] ? 1 : 0;
+    if (min_slack) min_slack[i] = ss_failed ? __longlong_as_double(0x7ff8000000000000ll)
+                                            : dunkey(L.cand_min[i]);
+  }
+}
+
+cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
+                                const double* d_kappas, int m) {
+  eval_prepare_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, v_prev, r, d_kappas, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d_min_slack) {
+  eval_finish_kernel<<<grid_for(m, 128, 64), 128, 0, L.stream>>>(L, m, d_adm, d_min_slack);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Simulated plant of the closed loop (Fig. 1) and the loop bookkeeping.
+__device__ void plant_step(const Launch& L, const double* x, double v, uint64_t seed, uint64_t upd,
+                           const double* amp, double* x_next) {
+  const Fc3K<double> K = *L.k64_dev;
+  const CandK<double> C = cand_consts(L.params, v);
+  const double p_atm = L.params[P_P_ATM];
+  double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm;
+  rk4_step<double>(K, C, L.dt, q_ca, w, q_sm);
+  const U64x4 r = philox4x64_10(0ull, 0ull, upd, 1ull, seed, 0ull);
+  x_next[0] = (q_ca + p_atm) + uniform_sym(r.w[0], amp[0]);
+  x_next[1] = w + uniform_sym(r.w[1], amp[1]);
+  x_next[2] = (q_sm + p_atm) + uniform_sym(r.w[2], amp[2]);
+}
+
+__global__ void plant_kernel(const Launch L, const double* d_x, const double* d_v, uint64_t seed,
+                             uint64_t base, const unsigned long long* t_dev, const double* amp,
+                             double* x_next) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double x[3] = {d_x[0], d_x[1], d_x[2]}, xn[3];
+  plant_step(L, x, *d_v, seed, base + (t_dev ? *t_dev : 0ull), amp, xn);
+  x_next[0] = xn[0]; x_next[1] = xn[1]; x_next[2] = xn[2];
+}
+
+cudaError_t launch_plant(const Launch& L, const double* d_x, const double* d_v, uint64_t seed,
+                         uint64_t base, const unsigned long long* t_dev, const double* amp_dev,
+                         double* d_x_next) {
+  plant_kernel<<<1, 32, 0, L.stream>>>(L, d_x, d_v, seed, base, t_dev, amp_dev, d_x_next);
+  return cudaGetLastError();
+}
+
+__global__ void loop_init_kernel(LoopState* ls, double x0, double x1, double x2, double v0,
+                                 double* x_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ls->x[0] = x0; ls->x[1] = x1; ls->x[2] = x2;
+  ls->v_prev = v0;
+  ls->t = 0ull;
+  if (x_out) { x_out[0] = x0; x_out[1] = x1; x_out[2] = x2; }
+}
+
+cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, double v0,
+                             double* d_x_out) {
+  loop_init_kernel<<<1, 32, 0, L.stream>>>(ls, x0[0], x0[1], x0[2], v0, d_x_out);
+  return cudaGetLastError();
+}
+
+// After the search of update t: record v_t, kappa, flags; move the plant one
+// step under v_t; v_prev <- v_t; t <- t + 1.
+__global__ void loop_end_kernel(const Launch L, LoopState* ls, uint64_t seed, uint64_t t0,
+                                const double* amp, double* v_out, double* kappa_out,
+                                int32_t* flags_out, double* x_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const SearchState* s = L.st;
+  const unsigned long long t = ls->t;
+  const double v = s->v_t_out;
+  if (v_out) v_out[t] = v;
+  if (kappa_out) kappa_out[t] = s->kappa_opt;
+  if (flags_out) flags_out[t] = s->flags;
+  double xn[3];
+  plant_step(L, ls->x, v, seed, t0 + t, amp, xn);
+  ls->x[0] = xn[0]; ls->x[1] = xn[1]; ls->x[2] = xn[2];
+  ls->v_prev = v;
+  ls->t = t + 1;
+  if (x_out) {
+    x_out[3 * (t + 1) + 0] = xn[0];
+    x_out[3 * (t + 1) + 1] = xn[1];
+    x_out[3 * (t + 1) + 2] = xn[2];
+  }
+}
+
+cudaError_t launch_loop_end(const Launch& L, LoopState* ls, uint64_t seed, uint64_t t0,
+                            const double* amp_dev, double* d_v_out, double* d_kappa_out,
+                            int32_t* d_flags_out, double* d_x_out) {
+  loop_end_kernel<<<1, 32, 0, L.stream>>>(L, ls, seed, t0, amp_dev, d_v_out, d_kappa_out,
+                                          d_flags_out, d_x_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Host-side schedule of rounds (mirrors choose_depth / tree_count above).
+static int host_tree_count(bool one, int d) { return one ? (1 << (d - 1)) : ((1 << d) - 1); }
+
+int search_round_count(const SearchCfg& c) {
+  if (c.search == RRG_SEARCH_GRID) return 1;
+  if (c.search == RRG_SEARCH_KSECTION) return c.n_rounds;
+  int iter = 0, rounds = 0;
+  bool one = true;
+  while (iter < c.n_bisect) {
+    int d = 1;
+    while (d + 1 <= c.n_bisect - iter && d + 1 <= 11 && host_tree_count(one, d + 1) <= c.m_cap) ++d;
+    iter += d;
+    one = false;
+    ++rounds;
+  }
+  return rounds;
+}
+
+int search_round_width(const SearchCfg& c, int round) {
+  if (c.search == RRG_SEARCH_GRID || c.search == RRG_SEARCH_KSECTION) return c.m_cap;
+  int iter = 0;
+  bool one = true;
+  for (int r = 0; iter < c.n_bisect; ++r) {
+    int d = 1;
+    while (d + 1 <= c.n_bisect - iter && d + 1 <= 11 && host_tree_count(one, d + 1) <= c.m_cap) ++d;
+    if (r == round) return host_tree_count(one, d);
+    iter += d;
+    one = false;
+  }
+  return 1;
+}
+
+}  // namespace rrg

@@ -1,0 +1,305 @@
+"""Python binding of librrg (include/rrg.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all
+computation runs in the library's CUDA kernels.  There is no CPU fallback:
+if librrg.so is missing or fails to load, importing this module raises.
+
+PyTorch is used only as a provider of device memory and streams for the
+``*_dev`` entry points (tensors are passed by ``data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librrg.so")
+
+RRG_OK, RRG_EINVAL, RRG_ENOMEM, RRG_ECUDA, RRG_ETIMEOUT, RRG_ENOTIMPL = range(6)
+SEARCH_BISECT, SEARCH_GRID, SEARCH_KSECTION, SEARCH_SPEC_BISECT = range(4)
+FP64, FP32, FP32_RECHECK = range(3)
+EXIT_NONE, EXIT_LANE, EXIT_CANDIDATE = range(3)
+NPARAM = 27
+MAX_CANDIDATES = 1024
+FLAG_NONE_ADMISSIBLE = 1
+FLAG_INVALID_INPUT = 2
+
+_d, _i32, _u64, _p = ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p
+
+
+class RrgConfig(ctypes.Structure):
+    """Mirror of rrg_config."""
+
+    _fields_ = [
+        ("dt", _d), ("horizon", _i32), ("n_scenarios", _i32), ("max_candidates", _i32),
+        ("n_bisect", _i32), ("n_rounds", _i32), ("search", _i32), ("precision", _i32),
+        ("early_exit", _i32), ("ss_check", _i32), ("y_min", _d), ("eps_ss", _d), ("y_c", _d),
+        ("recheck_eps_rel", _d), ("dist_amp", _d * 3),
+    ]
+
+
+class RrgStats(ctypes.Structure):
+    """Mirror of rrg_stats."""
+
+    _fields_ = [
+        ("launches", _u64), ("rollout_launches", _u64), ("lane_steps", _u64),
+        ("lane_steps_fp64", _u64), ("rechecked", _u64), ("rounds", _u64),
+        ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64),
+    ]
+
+
+class RrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("librrg error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librrg.so not built (%s); run paper_2510_08288_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "rrg_config_default": (None, [P(RrgConfig)]),
+        "rrg_create": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, P(_p)]),
+        "rrg_destroy": (ctypes.c_int, [_p]),
+        "rrg_last_error": (ctypes.c_char_p, [_p]),
+        "rrg_sample_scenarios": (ctypes.c_int, [_p, _u64, _u64]),
+        "rrg_set_scenarios": (ctypes.c_int, [_p, _p]),
+        "rrg_get_scenarios": (ctypes.c_int, [_p, _p]),
+        "rrg_eval_candidates": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, _p, _p, _p]),
+        "rrg_step": (ctypes.c_int, [_p, _p, _d, _d, _p, _p, _p]),
+        "rrg_step_dev": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _p]),
+        "rrg_equilibrium": (ctypes.c_int, [_p, _d, _p, _p]),
+        "rrg_closed_loop": (ctypes.c_int, [_p, _p, _d, _p, ctypes.c_int, _u64, _u64, _p, ctypes.c_int,
+                                           _p, _p, _p, _p]),
+        "rrg_closed_loop_dev": (ctypes.c_int, [_p, _p, _d, _p, ctypes.c_int, _u64, _u64, _p,
+                                               ctypes.c_int, _p, _p, _p, _p]),
+        "rrg_plant_step": (ctypes.c_int, [_p, _p, _d, _u64, _u64, _p, _p]),
+        "rrg_set_profiling": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
+        "rrg_reset_stats": (ctypes.c_int, [_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def rrg_config_default(**overrides) -> RrgConfig:
+    """rrg_config_default, then named field overrides (dist_amp as a 3-sequence)."""
+    c = RrgConfig()
+    lib.rrg_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        if k == "dist_amp":
+            c.dist_amp = (_d * 3)(*[float(x) for x in v])
+        elif hasattr(c, k):
+            setattr(c, k, v)
+        else:
+            raise KeyError(k)
+    return c
+
+
+def rrg_last_error(h=None) -> str:
+    s = lib.rrg_last_error(h)
+    return s.decode() if s else ""
+
+
+def _check(rc, h=None):
+    if rc != RRG_OK:
+        raise RrgError(rc, rrg_last_error(h))
+
+
+def _tensor_ptr(t):
+    """Device address of a torch tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def rrg_create(params, cfg: RrgConfig, stream=None):
+    p = _f64(params)
+    h = _p()
+    rc = lib.rrg_create(_ptr(p), int(p.shape[0]), ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
+def rrg_destroy(h):
+    _check(lib.rrg_destroy(h))
+
+
+def rrg_sample_scenarios(h, seed, update_index):
+    _check(lib.rrg_sample_scenarios(h, int(seed), int(update_index)), h)
+
+
+def rrg_set_scenarios(h, d):
+    d = _f64(d)
+    _check(lib.rrg_set_scenarios(h, _ptr(d)), h)
+
+
+def rrg_get_scenarios(h, n_scenarios, horizon):
+    d = np.zeros((3, horizon, n_scenarios))
+    _check(lib.rrg_get_scenarios(h, _ptr(d)), h)
+    return d
+
+
+def rrg_eval_candidates(h, x_t, v_prev, r_t, kappas, want_P=False, n_scenarios=None):
+    x, k = _f64(x_t), _f64(kappas)
+    m = k.shape[0]
+    adm = np.zeros(m, dtype=np.uint8)
+    ms = np.zeros(m)
+    P = np.zeros((m, n_scenarios), dtype=np.uint8) if want_P else None
+    rc = lib.rrg_eval_candidates(h, _ptr(x), float(v_prev), float(r_t), _ptr(k), m, _ptr(adm), _ptr(ms),
+                                 _ptr(P) if P is not None else None)
+    _check(rc, h)
+    return adm, ms, P
+
+
+def rrg_step(h, x_t, r_t, v_prev):
+    x = _f64(x_t)
+    v, kap, fl = _d(0.0), _d(0.0), _i32(0)
+    _check(lib.rrg_step(h, _ptr(x), float(r_t), float(v_prev), ctypes.byref(v), ctypes.byref(kap),
+                        ctypes.byref(fl)), h)
+    return v.value, kap.value, fl.value
+
+
+def rrg_step_dev(h, d_x_t, d_r_t, d_v_prev, d_v_t, d_kappa, d_flags):
+    _check(lib.rrg_step_dev(h, _tensor_ptr(d_x_t), _tensor_ptr(d_r_t), _tensor_ptr(d_v_prev),
+                            _tensor_ptr(d_v_t), _tensor_ptr(d_kappa), _tensor_ptr(d_flags)), h)
+
+
+def rrg_equilibrium(h, v):
+    x = np.zeros(3)
+    y = _d(0.0)
+    _check(lib.rrg_equilibrium(h, float(v), _ptr(x), ctypes.byref(y)), h)
+    return x, y.value
+
+
+def rrg_closed_loop(h, x0, v0, r_seq, seed, t0, plant_amp, use_graph=True):
+    x0, r, amp = _f64(x0), _f64(r_seq), _f64(plant_amp)
+    T = r.shape[0]
+    v = np.zeros(T)
+    kap = np.zeros(T)
+    fl = np.zeros(T, dtype=np.int32)
+    xs = np.zeros((T + 1, 3))
+    _check(lib.rrg_closed_loop(h, _ptr(x0), float(v0), _ptr(r), T, int(seed), int(t0), _ptr(amp),
+                               int(bool(use_graph)), _ptr(v), _ptr(kap), _ptr(fl), _ptr(xs)), h)
+    return v, kap, fl, xs
+
+
+def rrg_closed_loop_dev(h, x0, v0, d_r_seq, T, seed, t0, plant_amp, use_graph, d_v_out, d_kappa_out,
+                        d_flags_out, d_x_out):
+    x0, amp = _f64(x0), _f64(plant_amp)
+    _check(lib.rrg_closed_loop_dev(h, _ptr(x0), float(v0), _tensor_ptr(d_r_seq), int(T), int(seed),
+                                   int(t0), _ptr(amp), int(bool(use_graph)), _tensor_ptr(d_v_out),
+                                   _tensor_ptr(d_kappa_out), _tensor_ptr(d_flags_out),
+                                   _tensor_ptr(d_x_out)), h)
+
+
+def rrg_plant_step(h, x_t, v_t, seed, t, plant_amp):
+    x, amp = _f64(x_t), _f64(plant_amp)
+    out = np.zeros(3)
+    _check(lib.rrg_plant_step(h, _ptr(x), float(v_t), int(seed), int(t), _ptr(amp), _ptr(out)), h)
+    return out
+
+
+def rrg_set_profiling(h, on):
+    _check(lib.rrg_set_profiling(h, int(bool(on))), h)
+
+
+def rrg_get_stats(h) -> dict:
+    s = RrgStats()
+    _check(lib.rrg_get_stats(h, ctypes.byref(s)), h)
+    return {name: getattr(s, name) for name, _ in RrgStats._fields_}
+
+
+def rrg_reset_stats(h):
+    _check(lib.rrg_reset_stats(h), h)
+
+
+@dataclass
+class Governor:
+    """Owning wrapper of one rrg handle (create on construction, destroy on close)."""
+
+    params: np.ndarray
+    cfg: RrgConfig
+    stream: object = None
+
+    def __post_init__(self):
+        self.h = rrg_create(self.params, self.cfg, self.stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rrg_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sample_scenarios(self, seed, update_index):
+        rrg_sample_scenarios(self.h, seed, update_index)
+
+    def set_scenarios(self, d):
+        rrg_set_scenarios(self.h, d)
+
+    def get_scenarios(self):
+        return rrg_get_scenarios(self.h, self.cfg.n_scenarios, self.cfg.horizon)
+
+    def eval_candidates(self, x_t, v_prev, r_t, kappas, want_P=False):
+        return rrg_eval_candidates(self.h, x_t, v_prev, r_t, kappas, want_P, self.cfg.n_scenarios)
+
+    def step(self, x_t, r_t, v_prev):
+        return rrg_step(self.h, x_t, r_t, v_prev)
+
+    def equilibrium(self, v):
+        return rrg_equilibrium(self.h, v)
+
+    def closed_loop(self, x0, v0, r_seq, seed, t0, plant_amp, use_graph=True):
+        return rrg_closed_loop(self.h, x0, v0, r_seq, seed, t0, plant_amp, use_graph)
+
+    def plant_step(self, x_t, v_t, seed, t, plant_amp):
+        return rrg_plant_step(self.h, x_t, v_t, seed, t, plant_amp)
+
+    def stats(self):
+        return rrg_get_stats(self.h)
+
+    def reset_stats(self):
+        rrg_reset_stats(self.h)
+
+    def set_profiling(self, on):
+        rrg_set_profiling(self.h, on)

@@ -1,0 +1,330 @@
+"""GPU-vs-oracle parity of the robust reference governor, through the C ABI.
+
+Every test here needs a GB300 and the built librrg.so.  The oracle is the
+sequential FP64 C implementation under oracle/; both sides get the same seeded
+inputs (the same Philox counters, or explicit arrays from the inputs module).
+
+Tolerances:
+  - integer results (admissibility flags, P entries, kappa on the dyadic or
+    grid points, v_t) must be identical;
+  - binary64 slacks agree to 1e-9 relative (the two sides round in different
+    orders; over 2,000 contractive RK4 steps the drift stays ~1e-13);
+  - binary32 slacks agree with binary64 to the band SLACK32_TOL, and
+    admissibility decisions of the plain FP32 path may differ only where the
+    binary64 slack is inside that band; with FP32_RECHECK they are identical
+    whenever the band covers the measured binary32 error.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_08288_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SLACK64_RTOL = 1e-9
+SLACK32_TOL = 2e-4        # absolute OER units; measured max error is reported by test_fp32_error_band
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import rrg
+    return rrg
+
+
+def _cfg(R, N, H, **kw):
+    base = dict(horizon=H, n_scenarios=N, max_candidates=32, n_bisect=12, n_rounds=3,
+                search=R.SEARCH_SPEC_BISECT, precision=R.FP64, early_exit=R.EXIT_CANDIDATE)
+    base.update(kw)
+    return R.rrg_config_default(**base)
+
+
+def _ocfg(orc, N, H, early_exit=1, **kw):
+    return orc.cfg(H=H, N=N, early_exit=early_exit, **kw)
+
+
+# ------------------------------------------------------------------ pieces --
+def test_scenarios_bit_exact(R, orc, params):
+    """Philox4x64-10 on the device draws exactly the oracle's d_j^k."""
+    for N, H, seed, upd in ((32, 500, 0, 0), (37, 61, 5, 123456789), (1, 1, 2**63 + 1, 7)):
+        with R.Governor(params, _cfg(R, N, H)) as g:
+            g.sample_scenarios(seed, upd)
+            got = g.get_scenarios()
+        want = orc.sample_disturbances(seed, upd, N, H, inputs.DIST_AMP)
+        np.testing.assert_array_equal(got, want)
+
+
+def test_set_scenarios_roundtrip(R, params):
+    d = inputs.uniform_disturbances(29, 17, seed=3)
+    with R.Governor(params, _cfg(R, 29, 17)) as g:
+        g.set_scenarios(d)
+        np.testing.assert_array_equal(g.get_scenarios(), d)
+
+
+@pytest.mark.parametrize("I", [50.0, 77.7, 100.0, 175.0, 250.0, 300.0])
+def test_equilibrium(R, orc, params, I):
+    """Equilibrium manifold (Sec. II-A): device Illinois solve vs oracle bisection."""
+    with R.Governor(params, _cfg(R, 4, 4)) as g:
+        x, y = g.equilibrium(I)
+    xo = orc.equilibrium(params, I)
+    np.testing.assert_allclose(x, xo, rtol=1e-11)
+    assert y == pytest.approx(orc.output(params, xo, I), rel=1e-11)
+
+
+def test_equilibrium_rejects_bad_setpoint(R, params):
+    with R.Governor(params, _cfg(R, 4, 4)) as g:
+        for v in (0.0, -5.0, float("nan"), float("inf")):
+            with pytest.raises(R.RrgError):
+                g.equilibrium(v)
+
+
+# --------------------------------------------------------- candidate eval --
+def _eval_both(R, orc, params, N, H, kappas, prec, early, v_prev=100.0, r=250.0, seed=0,
+               want_P=True, x_t=None, **ckw):
+    if x_t is None:
+        x_t = orc.equilibrium(params, v_prev)
+    with R.Governor(params, _cfg(R, N, H, precision=prec, early_exit=early,
+                                 max_candidates=max(len(kappas), 2), **ckw)) as g:
+        g.sample_scenarios(seed, 0)
+        adm, ms, P = g.eval_candidates(x_t, v_prev, r, kappas, want_P=want_P)
+        st = g.stats()
+    d = orc.sample_disturbances(seed, 0, N, H, inputs.DIST_AMP)
+    oc = _ocfg(orc, N, H, early_exit=0, **{k: v for k, v in ckw.items() if k in ("y_min", "ss_check", "eps_ss", "y_c")})
+    a_o, ms_o, P_o, _ = orc.eval_candidates(params, oc, x_t, v_prev, r, kappas, d, want_P=True)
+    return (adm, ms, P, st), (a_o, ms_o, P_o)
+
+
+@pytest.mark.parametrize("N,H", [(32, 500), (37, 200), (129, 64), (1, 1), (300, 33)])
+@pytest.mark.parametrize("early", [0, 1, 2])
+def test_eval_fp64_matches_oracle(R, orc, params, N, H, early):
+    """Alg. 3 steps 1-3 in binary64: identical P and decisions, slacks to 1e-9."""
+    kappas = np.array([0.0, 0.03, 0.08, 0.1, 0.1025, 0.11, 0.3, 1.0])
+    (adm, ms, P, _), (a_o, ms_o, P_o) = _eval_both(R, orc, params, N, H, kappas, R.FP64, early,
+                                                   want_P=True)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+    ok = a_o == 1
+    np.testing.assert_allclose(ms[ok], ms_o[ok], rtol=SLACK64_RTOL, atol=1e-12)
+    if early == 0:
+        np.testing.assert_allclose(ms, ms_o, rtol=SLACK64_RTOL, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,H", [(32, 500), (129, 300)])
+def test_eval_fp32_within_band(R, orc, params, N, H):
+    """Plain binary32: slack error inside the band; decisions differ only
+    where the binary64 slack is inside it."""
+    kappas = np.linspace(0.0, 0.2, 21)
+    (adm, ms, P, _), (a_o, ms_o, P_o) = _eval_both(R, orc, params, N, H, kappas, R.FP32, 0)
+    assert np.max(np.abs(ms - ms_o)) < SLACK32_TOL
+    differ = adm != a_o
+    assert np.all(np.abs(ms_o[differ]) < SLACK32_TOL)
+
+
+@pytest.mark.parametrize("N,H", [(32, 500), (129, 300), (1000, 120)])
+def test_eval_fp32_recheck_is_exact(R, orc, params, N, H):
+    """Binary32 bulk + binary64 recheck of the near-zero lanes decides exactly
+    like the binary64 oracle (the band is wide enough to cover binary32 error)."""
+    kappas = np.linspace(0.09, 0.115, 26)
+    (adm, ms, P, st), (a_o, ms_o, P_o) = _eval_both(
+        R, orc, params, N, H, kappas, R.FP32_RECHECK, 1, recheck_eps_rel=SLACK32_TOL / 1.9)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+    assert st["rechecked"] >= 1
+
+
+def test_steady_state_failure_rows(R, orc, params):
+    """Candidates failing the steady-state check (Eq. 3) get an all-zero P row
+    and a NaN min slack; the oracle agrees on the row."""
+    kappas = np.array([0.0, 0.5, 1.0])
+    ckw = dict(eps_ss=0.9, y_c=2.23378)  # threshold 2.2004: OER_ss(60 A) passes, (170, 280 A) fail
+    (adm, ms, P, _), (a_o, ms_o, P_o) = _eval_both(R, orc, params, 16, 50, kappas, R.FP64, 1,
+                                                   v_prev=60.0, r=280.0, **ckw)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+    for i in range(3):
+        ss = orc.ss_ok(params, orc.cfg(eps_ss=0.9, y_c=2.23378), orc.governed(60.0, 280.0, kappas[i]))
+        if not ss:
+            assert np.isnan(ms[i]) and not P[i].any()
+    assert not all(orc.ss_ok(params, orc.cfg(eps_ss=0.9, y_c=2.23378), orc.governed(60.0, 280.0, k))
+                   for k in kappas)
+
+
+def test_fp32_error_band(R, orc, params):
+    """Measures max |s32 - s64| over full-horizon trajectories (no early exit)
+    of the 1,024 x 2,000 closed-loop workload at kappas near the boundary and
+    asserts it is inside the band the recheck tests use."""
+    N, H = 1024, 2000
+    kappas = np.array([0.0, 0.1, 0.102, 0.104, 0.2])
+    x_t = orc.equilibrium(params, 100.0)
+    errs = []
+    for prec in (R.FP32, R.FP64):
+        with R.Governor(params, _cfg(R, N, H, precision=prec, early_exit=0, max_candidates=8)) as g:
+            g.sample_scenarios(1, 0)
+            errs.append(g.eval_candidates(x_t, 100.0, 250.0, kappas)[1])
+    err = np.max(np.abs(errs[0] - errs[1]))
+    print("max |s32 - s64| (min over scenarios) = %.3e" % err)
+    assert err < SLACK32_TOL
+
+
+# ------------------------------------------------------------- searches ----
+SEARCHES = ("bisect", "spec", "grid", "ksection")
+
+
+def _oracle_search(orc, params, kind, x_t, v_prev, r, d, N, H, M, n_bisect=12, rounds=3, **kw):
+    c = orc.cfg(H=H, N=N, **kw)
+    if kind in ("bisect", "spec"):
+        return orc.bisect_joint(params, c, x_t, v_prev, r, n_bisect, d)
+    if kind == "grid":
+        return orc.alg3(params, c, x_t, v_prev, r, M, d)
+    return orc.ksection(params, c, x_t, v_prev, r, M, rounds, d)
+
+
+def _gpu_search(R, kind):
+    return {"bisect": R.SEARCH_BISECT, "spec": R.SEARCH_SPEC_BISECT, "grid": R.SEARCH_GRID,
+            "ksection": R.SEARCH_KSECTION}[kind]
+
+
+@pytest.mark.parametrize("kind", SEARCHES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32_recheck"])
+@pytest.mark.parametrize("case", [(100.0, 250.0), (100.0, 112.0), (200.0, 60.0), (150.0, 150.0),
+                                  (55.0, 300.0)])
+def test_step_matches_oracle(R, orc, params, kind, prec, case):
+    """One robust RG update: kappa, v_t and flags equal the oracle's Alg. 1
+    (joint predicate), Alg. 3 or k-section on the same scenarios."""
+    v_prev, r = case
+    N, H, M = 32, 500, 16
+    x_t = orc.equilibrium(params, v_prev)
+    p = R.FP64 if prec == "fp64" else R.FP32_RECHECK
+    cfg = _cfg(R, N, H, search=_gpu_search(R, kind), precision=p, max_candidates=M,
+               recheck_eps_rel=SLACK32_TOL / 1.9)
+    with R.Governor(params, cfg) as g:
+        g.sample_scenarios(0, 0)
+        v_t, kap, fl = g.step(x_t, r, v_prev)
+    d = orc.sample_disturbances(0, 0, N, H, inputs.DIST_AMP)
+    k_o, f_o = _oracle_search(orc, params, kind, x_t, v_prev, r, d, N, H, M)
+    assert kap == k_o and fl == f_o
+    assert v_t == v_prev + kap * (r - v_prev)
+    assert 0.0 <= kap <= 1.0
+    if r == v_prev:
+        assert kap == 1.0
+
+
+@pytest.mark.parametrize("m_cap", [1, 2, 3, 7, 64, 1024])
+def test_spec_bisect_equals_bisect_for_any_width(R, orc, params, m_cap):
+    """Evaluating several levels of Alg. 1's tree per round changes nothing:
+    the result equals plain bisection for every candidate budget."""
+    N, H = 24, 300
+    x_t = orc.equilibrium(params, 120.0)
+    d = orc.sample_disturbances(9, 4, N, H, inputs.DIST_AMP)
+    for r in (290.0, 140.0, 130.0):
+        k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, 120.0, r, 14, d)
+        cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, max_candidates=m_cap, n_bisect=14)
+        with R.Governor(params, cfg) as g:
+            g.sample_scenarios(9, 4)
+            _, kap, fl = g.step(x_t, r, 120.0)
+        assert kap == k_o and fl == f_o
+
+
+def test_nothing_admissible_holds(R, orc, params):
+    """y_min above every reachable OER: kappa = 0, v_t = v_prev, flag bit 0."""
+    x_t = orc.equilibrium(params, 100.0)
+    for kind in SEARCHES:
+        cfg = _cfg(R, 8, 30, search=_gpu_search(R, kind), y_min=5.0, max_candidates=9)
+        with R.Governor(params, cfg) as g:
+            g.sample_scenarios(1, 0)
+            v_t, kap, fl = g.step(x_t, 200.0, 100.0)
+        assert (v_t, kap, fl) == (100.0, 0.0, 1)
+
+
+def test_host_input_validation(R, orc, params):
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, _cfg(R, 8, 30)) as g:
+        g.sample_scenarios(1, 0)
+        for bad in ((np.array([np.nan, 1, 1]), 200.0, 100.0), (x_t, np.inf, 100.0), (x_t, 200.0, -1.0)):
+            with pytest.raises(R.RrgError) as e:
+                g.step(*bad)
+            assert e.value.code == R.RRG_EINVAL
+        with pytest.raises(R.RrgError):
+            g.eval_candidates(x_t, 100.0, 200.0, [1.5])
+        with pytest.raises(R.RrgError):
+            g.eval_candidates(x_t, 100.0, 200.0, np.zeros(33))
+
+
+def test_step_dev_flags_invalid_input_on_device(R, orc, params):
+    """The device-pointer update rejects a non-finite x_t on the device:
+    kappa = 0, v_t = v_prev, flag bit 1, and the handle stays usable."""
+    import torch
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, _cfg(R, 8, 30)) as g:
+        g.sample_scenarios(1, 0)
+        dx = torch.tensor([np.nan, x_t[1], x_t[2]], dtype=torch.float64, device="cuda")
+        dr = torch.tensor([200.0], dtype=torch.float64, device="cuda")
+        dv = torch.tensor([100.0], dtype=torch.float64, device="cuda")
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        fl = torch.zeros(1, dtype=torch.int32, device="cuda")
+        R.rrg_step_dev(g.h, dx, dr, dv, out[0:1], out[1:2], fl)
+        torch.cuda.synchronize()
+        assert out[0].item() == 100.0 and out[1].item() == 0.0 and fl.item() & 2
+        v_t, kap, f = g.step(x_t, 200.0, 100.0)
+        assert f == 0 and 0 < kap < 1
+
+
+# --------------------------------------------------------- closed loop -----
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("kind", ["spec", "ksection"])
+def test_closed_loop_matches_oracle(R, orc, params, use_graph, kind):
+    """Fig. 1 closed loop for 6 updates on a staircase reference: every
+    kappa, v_t and flag equal the oracle's; states agree to 1e-10."""
+    N, H, T = 16, 150, 6
+    r_seq = inputs.staircase(T, 3, 2, seed=1)
+    x0 = orc.equilibrium(params, 100.0)
+    amp = inputs.DIST_AMP
+    cfg = _cfg(R, N, H, search=_gpu_search(R, kind), precision=R.FP32_RECHECK, max_candidates=16,
+               recheck_eps_rel=SLACK32_TOL / 1.9)
+    with R.Governor(params, cfg) as g:
+        v, kap, fl, xs = g.closed_loop(x0, 100.0, r_seq, 11, 5, amp, use_graph=use_graph)
+    search = 0 if kind == "spec" else 2
+    vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 100.0, r_seq, 11, 5, amp, amp,
+                                     search=search, n_kappa=12, M=16, rounds=3)
+    np.testing.assert_array_equal(kap, ko)
+    np.testing.assert_array_equal(v, vo)
+    np.testing.assert_array_equal(fl, fo)
+    np.testing.assert_allclose(xs, xo, rtol=1e-10)
+
+
+def test_plant_step_matches_oracle(R, orc, params):
+    x = orc.equilibrium(params, 120.0)
+    with R.Governor(params, _cfg(R, 4, 4)) as g:
+        got = g.plant_step(x, 180.0, 3, 9, inputs.DIST_AMP)
+    want = orc.rk4_step(params, x, 180.0, 0.01) + orc.plant_disturbance(3, 9, inputs.DIST_AMP)
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+# ------------------------------------------- full-size closed-loop workload --
+def test_full_size_update_matches_oracle(R, orc, params):
+    """The benchmark's configuration (N = 1,024 scenarios, horizon 2,000,
+    FP32 + FP64 recheck, speculative bisection, 64 candidates per round):
+    the GPU update equals the oracle's joint bisection on the same scenarios,
+    and sampled P entries equal the oracle's per-trajectory decisions."""
+    w = inputs.WORKLOADS["closed_loop"]
+    N, H = w["N"], w["H"]
+    x_t = orc.equilibrium(params, 100.0)
+    cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=R.FP32_RECHECK, max_candidates=64,
+               recheck_eps_rel=w["recheck_eps_rel"])
+    with R.Governor(params, cfg) as g:
+        g.sample_scenarios(w["seed"], 0)
+        v_t, kap, fl = g.step(x_t, 250.0, 100.0)
+        kap_probe = np.array([kap, min(1.0, kap + 2.0 ** -11), 0.05])
+        adm, ms, P = g.eval_candidates(x_t, 100.0, 250.0, kap_probe, want_P=True)
+    d = orc.sample_disturbances(w["seed"], 0, N, H, inputs.DIST_AMP)
+    k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, 100.0, 250.0, 12, d, nthreads=8)
+    assert kap == k_o and fl == f_o
+    rng = np.random.default_rng(0)
+    for k in rng.choice(N, size=48, replace=False):
+        for i, kk in enumerate(kap_probe):
+            s, _ = orc.rollout(params, orc.cfg(H=H, N=N, early_exit=1), x_t, orc.governed(100.0, 250.0, kk), d, k)
+            assert P[i, k] == (1 if s >= 0 else 0)
