@@ -49,20 +49,23 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--fp64-steps", type=int, default=3, help="updates of the plain FP64 bisection comparator")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scenarios", type=int, default=N_SCEN, help="smaller cases for profiling only")
+    ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     return ap.parse_args()
 
 
-def workload_config(W, K):
+def workload_config(W, K, N=N_SCEN, H=HORIZON):
     return {
-        "workload": "closed-loop robust RG on FC3: N_sim=1024 scenarios, horizon 2000 RK4 steps "
+        "workload": "closed-loop robust RG on FC3: N_sim=%d scenarios, horizon %d RK4 steps "
                     "(dt=0.01 s), staircase r (8 levels over 50..300 A, seed 1, 125 updates/level), "
-                    "timed updates [%d, %d) of the 1000-update run" % (W, W + K),
+                    "timed updates [%d, %d) of the 1000-update run" % (N, H, W, W + K),
         "search": "speculative bisection (Alg. 1 result), N_kappa=12, 64 candidates/round",
         "kappa_tol": 2.0 ** -11,
         "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
@@ -176,6 +179,37 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- GPU side --
+def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev):
+    """The timed updates again through the host-buffer entry points
+    (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle; every
+    call copies its inputs from and its results to host memory."""
+    import numpy as np
+    import torch
+    g2 = R.Governor(p, cfg, stream)
+    x, v = x0.copy(), V0
+    for t in range(W):
+        g2.sample_scenarios(seed, t)
+        v, _, _ = g2.step(x, r_seq[t], v)
+        x = g2.plant_step(x, v, seed, t, amp)
+    e2e_s, kap_e2e = 0.0, []
+    for t in range(W, T):
+        flush.fill_(float(t))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2.sample_scenarios(seed, t)
+        v, kk, _ = g2.step(x, r_seq[t], v)
+        x = g2.plant_step(x, v, seed, t, amp)
+        e2e_s += time.perf_counter() - t0
+        kap_e2e.append(kk)
+    g2.close()
+    K = T - W
+    # bytes copied per update: rrg_step sends x_t, r_t, v_prev (40 B) and
+    # returns v_t, kappa, flags (20 B); rrg_plant_step sends its 12-double
+    # staging block (96 B) and returns x_{t+1} (24 B)
+    return {"value": K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 40 + 96, "d2h_bytes_per_step": 20 + 24,
+            "kappa_equal_to_device_run": bool(np.all(np.array(kap_e2e) == kap_dev[W:T]))}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -201,7 +235,8 @@ def run_gpu(args):
     r_seq = inputs.staircase(T, 8, 125, SEED)
     amp = np.array(inputs.DIST_AMP)
     stream = torch.cuda.Stream()
-    cfg = R.rrg_config_default(horizon=HORIZON, n_scenarios=N_SCEN, max_candidates=M_CAND,
+    NS, HZ = args.scenarios, args.horizon
+    cfg = R.rrg_config_default(horizon=HZ, n_scenarios=NS, max_candidates=M_CAND,
                                n_bisect=N_BISECT, search=R.SEARCH_SPEC_BISECT,
                                precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
                                recheck_eps_rel=RECHECK_EPS_REL)
@@ -257,29 +292,15 @@ def run_gpu(args):
     out = None
     if rank == 0:
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
-        g2 = R.Governor(p, cfg, stream)
-        x, v = x0.copy(), V0
-        for t in range(W):
-            g2.sample_scenarios(seed, t)
-            v, _, _ = g2.step(x, r_seq[t], v)
-            x = g2.plant_step(x, v, seed, t, amp)
-        e2e_s, kap_e2e = 0.0, []
-        for t in range(W, T):
-            flush.fill_(float(t))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g2.sample_scenarios(seed, t)
-            v, kk, _ = g2.step(x, r_seq[t], v)
-            x = g2.plant_step(x, v, seed, t, amp)
-            e2e_s += time.perf_counter() - t0
-            kap_e2e.append(kk)
-        g2.close()
+        e2e = None
+        if not args.no_e2e:
+            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev)
 
         # plain FP64 bisection on the same GPU, same updates
         nf = min(args.fp64_steps, K)
         fp64 = None
         if nf > 0:
-            cfg64 = R.rrg_config_default(horizon=HORIZON, n_scenarios=N_SCEN, max_candidates=M_CAND,
+            cfg64 = R.rrg_config_default(horizon=HZ, n_scenarios=NS, max_candidates=M_CAND,
                                          n_bisect=N_BISECT, search=R.SEARCH_BISECT, precision=R.FP64,
                                          early_exit=R.EXIT_CANDIDATE)
             g3 = R.Governor(p, cfg64, stream)
@@ -298,7 +319,7 @@ def run_gpu(args):
                     "updates": nf, "kappa_equal_to_fp32_recheck": bool(np.all(np.array(kap64) == kap_dev[W:W + nf]))}
 
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and (NS, HZ) == (N_SCEN, HORIZON):
             cores = os.cpu_count() or 1
             from oracle import oracle as O
             x0o = O.equilibrium(p, V0)
@@ -315,7 +336,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(W, K),
+            "config": workload_config(W, K, NS, HZ),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -325,9 +346,7 @@ def run_gpu(args):
                          "flops_per_traj_step": FLOPS_PER_STEP,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
             "cpu_baseline": cpu,
-            "e2e": {"value": K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 40 + 96,
-                    "d2h_bytes_per_step": 20 + 24,
-                    "kappa_equal_to_device_run": bool(np.all(np.array(kap_e2e) == kap_dev[W:T]))},
+            "e2e": e2e,
             "gpu_launches": st["launches"],
             "clocks": clk,
             "fp64_bisect_gpu": fp64,
