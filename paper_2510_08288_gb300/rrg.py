@@ -215,8 +215,10 @@ def rrg_closed_loop(h, x0, v0, r_seq, seed, t0, plant_amp, use_graph=True):
 
 def rrg_closed_loop_dev(h, x0, v0, d_r_seq, T, seed, t0, plant_amp, use_graph, d_v_out, d_kappa_out,
                         d_flags_out, d_x_out):
-    x0, amp = _f64(x0), _f64(plant_amp)
-    _check(lib.rrg_closed_loop_dev(h, _ptr(x0), float(v0), _tensor_ptr(d_r_seq), int(T), int(seed),
+    amp = _f64(plant_amp)
+    x0 = _f64(x0) if x0 is not None else None      # None: continue the previous loop
+    _check(lib.rrg_closed_loop_dev(h, _ptr(x0) if x0 is not None else None, float(v0),
+                                   _tensor_ptr(d_r_seq), int(T), int(seed),
                                    int(t0), _ptr(amp), int(bool(use_graph)), _tensor_ptr(d_v_out),
                                    _tensor_ptr(d_kappa_out), _tensor_ptr(d_flags_out),
                                    _tensor_ptr(d_x_out)), h)

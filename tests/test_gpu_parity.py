@@ -328,3 +328,35 @@ def test_full_size_update_matches_oracle(R, orc, params):
         for i, kk in enumerate(kap_probe):
             s, _ = orc.rollout(params, orc.cfg(H=H, N=N, early_exit=1), x_t, orc.governed(100.0, 250.0, kk), d, k)
             assert P[i, k] == (1 if s >= 0 else 0)
+
+
+def test_closed_loop_continuation_equals_one_run(R, orc, params):
+    """rrg_closed_loop_dev with x0 = NULL continues the previous run: 2 + 1 + 1
+    updates give exactly the same trajectory as one call of 4 updates."""
+    import torch
+    N, H, T = 16, 100, 4
+    r_seq = inputs.staircase(T, 2, 2, seed=4)
+    x0 = orc.equilibrium(params, 90.0)
+    amp = np.array(inputs.DIST_AMP)
+    cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=R.FP32_RECHECK, max_candidates=16,
+               recheck_eps_rel=SLACK32_TOL / 1.9)
+    outs = []
+    for pieces in ((4,), (2, 1, 1)):
+        with R.Governor(params, cfg) as g:
+            dev = torch.device("cuda")
+            d_r = torch.tensor(r_seq, dtype=torch.float64, device=dev)
+            d_v = torch.zeros(T, dtype=torch.float64, device=dev)
+            d_k = torch.zeros(T, dtype=torch.float64, device=dev)
+            d_f = torch.zeros(T, dtype=torch.int32, device=dev)
+            d_x = torch.zeros(3 * (T + 1), dtype=torch.float64, device=dev)
+            first = True
+            for n in pieces:
+                R.rrg_closed_loop_dev(g.h, x0 if first else None, 90.0, d_r, n, 7, 3, amp, not first,
+                                      d_v, d_k, d_f, d_x)
+                first = False
+            torch.cuda.synchronize()
+            outs.append((d_v.cpu().numpy(), d_k.cpu().numpy(), d_x.cpu().numpy()))
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+    vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 90.0, r_seq, 7, 3, amp, amp, search=0)
+    np.testing.assert_array_equal(outs[0][1], ko)
