@@ -18,11 +18,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "librrg.so")
-STAMP = os.path.join(BUILD, "librrg.stamp")
 SOURCES = ("rrg_kernels.cu", "rrg_capi.cu")
 HEADERS = ("rrg_device.cuh", "rrg_internal.h")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+# -ftz=true: the binary32 rollouts never meet subnormal values, and flushing
+# lets lg2/ex2/rcp issue as single MUFU operations on the critical path
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr"]
 
 
@@ -40,13 +41,18 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str = None,
+          build_dir: str = None) -> str:
+    """Compiles and links librrg.so (or `out`, with objects in `build_dir`)."""
+    lib_path = out or LIB
+    bdir = build_dir or BUILD
+    stamp = os.path.join(bdir, "librrg.stamp")
+    os.makedirs(bdir, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "rrg.h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(bdir, src + ".o")
         if force or _stale(o, [s] + hdrs):
             jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, *extra_flags, "-c", s, "-o", o])
 
@@ -61,16 +67,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(BUILD, s + ".o") for s in SOURCES]
+    objs = [os.path.join(bdir, s + ".o") for s in SOURCES]
     # the stamp records which machine linked librrg.so, so a library copied
     # from another architecture is relinked from this machine's objects
-    if force or jobs or _stale(LIB, objs) or not os.path.exists(STAMP):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib_path, objs) or not os.path.exists(stamp):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-        with open(STAMP, "w") as f:
+        os.replace(tmp, lib_path)
+        with open(stamp, "w") as f:
             f.write(platform.machine() + "\n")
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

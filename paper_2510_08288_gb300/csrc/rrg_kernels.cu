@@ -94,9 +94,11 @@ __device__ __forceinline__ CandK<double> cand_consts(const double* __restrict__ 
 // Equilibrium manifold (Sec. II-A).  At rest the cathode balance fixes the
 // cathode gauge pressure from the air flow W, the orifice fixes the supply
 // manifold pressure and the compressor map the speed, leaving the shaft
-// torque balance g(W) = 0.  g decreases in W; it is bracketed on
-// [W_o2, 2 lam_ref W_o2 / x_O2 * 2^n] and solved by the Illinois variant of
-// regula falsi (Dowell & Jarratt, BIT 11, 1971).
+// torque balance g(W) = 0, with g decreasing in W and g(W_o2) > 0.  The root
+// lies close to the controller's target flow W_ref = lam_ref W_o2 / x_O2, so
+// a secant iteration started there converges in a handful of binary64
+// evaluations; every iterate is kept inside a sign-change bracket and a
+// step that leaves it is replaced by bisection.
 __device__ double eq_torque(const Fc3K<double>& K, const double* __restrict__ P,
                             const CandK<double>& C, double W, double q[3]) {
   q[0] = (W - C.W_o2) / P[P_K_CA];
@@ -111,32 +113,33 @@ __device__ int equilibrium_dev(const Fc3K<double>& K, const double* __restrict__
                                double q[3], double* y_ss) {
   if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
   const CandK<double> C = cand_consts(P, I);
-  double lo = C.W_o2, hi = 2.0 * P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
-  double glo = eq_torque(K, P, C, lo, q);
-  double ghi = eq_torque(K, P, C, hi, q);
-  for (int it = 0; it < 60 && ghi > 0.0; ++it) {
-    hi *= 2.0;
-    ghi = eq_torque(K, P, C, hi, q);
+  double lo = C.W_o2;
+  if (!(eq_torque(K, P, C, lo, q) > 0.0)) return -2;
+  double hi = DBL_MAX;
+  // two starting points around the target flow
+  double x0 = P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
+  double g0 = eq_torque(K, P, C, x0, q);
+  if (g0 > 0.0) lo = x0; else hi = x0;
+  double x1 = x0 * (g0 > 0.0 ? 1.001 : 0.999);
+  double g1 = eq_torque(K, P, C, x1, q);
+  if (g1 > 0.0) { if (x1 > lo) lo = x1; } else if (x1 < hi) hi = x1;
+  // make sure the bracket is closed before bisection can be needed
+  for (int it = 0; it < 60 && hi == DBL_MAX; ++it) {
+    const double xt = 2.0 * lo;
+    if (eq_torque(K, P, C, xt, q) > 0.0) lo = xt; else hi = xt;
   }
-  if (!(glo > 0.0) || !(ghi < 0.0)) return -2;
-  int side = 0;
-  double W = 0.5 * (lo + hi), W_last = lo;
-  for (int it = 0; it < 200; ++it) {
-    W = (lo * ghi - hi * glo) / (ghi - glo);
-    if (!(W > lo && W < hi)) W = 0.5 * (lo + hi);
-    const double g = eq_torque(K, P, C, W, q);
-    if (g == 0.0) break;
-    if (g > 0.0) {
-      lo = W; glo = g;
-      if (side == 1) ghi *= 0.5;
-      side = 1;
-    } else {
-      hi = W; ghi = g;
-      if (side == -1) glo *= 0.5;
-      side = -1;
-    }
-    if (fabs(W - W_last) <= 2e-16 * W || hi - lo <= 2e-16 * hi) break;
-    W_last = W;
+  if (hi == DBL_MAX) return -2;
+  double W = x1;
+  for (int it = 0; it < 100; ++it) {
+    double x2 = x1 - g1 * (x1 - x0) / (g1 - g0);
+    if (!(x2 > lo && x2 < hi)) x2 = 0.5 * (lo + hi);
+    const double g2 = eq_torque(K, P, C, x2, q);
+    W = x2;
+    if (g2 == 0.0) break;
+    if (g2 > 0.0) lo = x2; else hi = x2;
+    if (fabs(x2 - x1) <= 1e-15 * x2 || hi - lo <= 4e-16 * hi) break;
+    x0 = x1; g0 = g1;
+    x1 = x2; g1 = g2;
   }
   eq_torque(K, P, C, W, q);
   *y_ss = fc3_output<double>(C, q[0], q[2]);
@@ -214,8 +217,20 @@ cudaError_t launch_round_scenarios(const Launch& L) {
 // ---------------------------------------------------------------------------
 // One trajectory: x_0 = x_t, x_{j+1} = RK4(x_j, v) + d_j, slack s_j =
 // h(x_j, v) - y_min at j = 0..H; a non-finite state or output counts as
-// s = -inf.  Stops when s < thr (thr = -inf: never), and, every 32 steps,
-// when *dead is set.  Returns min_j s_j; *steps receives the RK4 steps done.
+// s = -inf.  Stops when s < thr (thr = -inf: never) and, checked once per
+// block of kPrefetch steps, when *dead is set.  Returns min_j s_j; *steps
+// receives the RK4 steps done.
+//
+// The disturbances of step j are loaded kPrefetch steps ahead into a small
+// register ring, so the L2 latency of the three loads (larger than one RK4
+// step on a two-die GB300) overlaps the arithmetic of the steps in between.
+// The candidate's dead flag is read at the start of a block and used at its
+// end, for the same reason.
+#ifndef RRG_PREFETCH
+#define RRG_PREFETCH 4
+#endif
+constexpr int kPrefetch = RRG_PREFETCH;
+
 template <typename T>
 __device__ __forceinline__ T checked_slack(const CandK<T>& C, T q_ca, T w, T q_sm, T y_min) {
   const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
@@ -230,22 +245,48 @@ __device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
                                       const volatile int32_t* dead, unsigned* steps) {
   T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
   T smin = s;
-  bool stop = (s < thr) || (H == 0);
   int j = 0;
-  const size_t HN = static_cast<size_t>(H) * N;
-  const T* dp = d + k;
-  while (!stop) {
-    const T d0 = __ldg(dp), d1 = __ldg(dp + HN), d2 = __ldg(dp + 2 * HN);
-    dp += N;
-    rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-    q_ca += d0;
-    w += d1;
-    q_sm += d2;
-    ++j;
-    s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
-    smin = fmin(smin, s);
-    stop = (s < thr) || (j == H);
-    if (dead != nullptr && !stop && (j & 31) == 0) stop = (*dead != 0);
+  if (!(s < thr) && H > 0) {
+    const size_t HN = static_cast<size_t>(H) * N;
+    T r0[kPrefetch], r1[kPrefetch], r2[kPrefetch];
+    const T* pf = d + k;  // next step to prefetch
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      if (u < H) {
+        r0[u] = __ldg(pf);
+        r1[u] = __ldg(pf + HN);
+        r2[u] = __ldg(pf + 2 * HN);
+      } else {
+        r0[u] = r1[u] = r2[u] = T(0);
+      }
+      pf += N;
+    }
+    bool stop = false;
+    while (!stop) {
+      const int dead_now = dead != nullptr ? *dead : 0;
+#pragma unroll
+      for (int u = 0; u < kPrefetch; ++u) {
+        const T e0 = r0[u], e1 = r1[u], e2 = r2[u];
+        if (j + kPrefetch < H) {
+          r0[u] = __ldg(pf);
+          r1[u] = __ldg(pf + HN);
+          r2[u] = __ldg(pf + 2 * HN);
+        }
+        pf += N;
+        rk4_step<T>(K, C, dt, q_ca, w, q_sm);
+        q_ca += e0;
+        w += e1;
+        q_sm += e2;
+        ++j;
+        s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+        smin = fmin(smin, s);
+        if ((s < thr) || (j == H)) {
+          stop = true;
+          break;
+        }
+      }
+      if (dead_now != 0) stop = true;
+    }
   }
   *steps = static_cast<unsigned>(j);
   return smin;

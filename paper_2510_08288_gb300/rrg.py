@@ -16,7 +16,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librrg.so")
+LIB_PATH = os.environ.get("RRG_LIBRARY") or os.path.join(_HERE, "librrg.so")
 
 RRG_OK, RRG_EINVAL, RRG_ENOMEM, RRG_ECUDA, RRG_ETIMEOUT, RRG_ENOTIMPL = range(6)
 SEARCH_BISECT, SEARCH_GRID, SEARCH_KSECTION, SEARCH_SPEC_BISECT = range(4)
