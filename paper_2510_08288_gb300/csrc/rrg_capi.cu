@@ -24,14 +24,10 @@ struct rrg_ctx {
   bool own_stream = false;
   rrg_config cfg{};
   double params[RRG_NPARAM]{};
-  Fc3K<double> k64h{};
-  Fc3K<float> k32h{};
   SearchCfg scfg{};
   Launch L{};
   // device memory
   double* params_dev = nullptr;
-  Fc3K<double>* k64_dev = nullptr;
-  Fc3K<float>* k32_dev = nullptr;
   double* d64 = nullptr;
   float* d32 = nullptr;
   SearchState* st = nullptr;
@@ -141,7 +137,7 @@ cudaError_t dalloc(T** p, size_t n) {
 }
 
 void free_all(rrg_ctx* h) {
-  void* ptrs[] = {h->params_dev, h->k64_dev, h->k32_dev, h->d64, h->d32, h->st, h->cand_kappa,
+  void* ptrs[] = {h->params_dev, h->d64, h->d32, h->st, h->cand_kappa,
                   h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev};
@@ -169,10 +165,7 @@ void fill_launch(rrg_ctx* h) {
   L.eps_abs = c.precision == RRG_FP32_RECHECK ? c.recheck_eps_rel * std::fabs(c.y_min) : 0.0;
   L.scfg = h->scfg;
   L.params = h->params_dev;
-  L.k64_dev = h->k64_dev;
-  L.k32_dev = h->k32_dev;
-  L.k64_host = &h->k64h;
-  L.k32_host = &h->k32h;
+  fold_constants(h->params, &L.k64, &L.k32);
   L.d64 = h->d64;
   L.d32 = h->d32;
   L.st = h->st;
@@ -313,8 +306,6 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
     if (e != cudaSuccess) { cudaGetLastError(); }                       \
   }
   ALLOC(params_dev, RRG_NPARAM);
-  ALLOC(k64_dev, 1);
-  ALLOC(k32_dev, 1);
   ALLOC(d64, HN3);
   ALLOC(d32, HN3);
   ALLOC(st, 1);
@@ -343,11 +334,6 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, HN3 * sizeof(float), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = launch_fold_constants(h->params_dev, h->k64_dev, h->k32_dev, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&h->k64h, h->k64_dev, sizeof h->k64h, cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&h->k32h, h->k32_dev, sizeof h->k32h, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? RRG_ENOMEM : RRG_ECUDA;
@@ -356,7 +342,6 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
     delete h;
     return code;
   }
-  h->launches = 1;
   SearchCfg& s = h->scfg;
   s.search = c.search;
   s.m_cap = c.search == RRG_SEARCH_BISECT ? 1 : c.max_candidates;

@@ -9,8 +9,7 @@
 
 namespace rrg {
 
-template <typename T> struct Fc3K;
-template <typename T> struct CandK;
+#include "rrg_device.cuh"
 
 // FC3 parameter indices (the layout documented in rrg.h).
 enum ParamIdx {
@@ -72,11 +71,9 @@ struct Launch {
   int N, H, precision, early_exit, m_cap;
   double dt, y_min, eps_abs;
   SearchCfg scfg;
-  const double* params;         // [RRG_NPARAM]
-  const Fc3K<double>* k64_dev;  // folded constants (device copy)
-  const Fc3K<float>* k32_dev;
-  const void* k64_host;         // host copies, passed by value to rollouts
-  const void* k32_host;
+  const double* params;         // [RRG_NPARAM] (device)
+  Fc3K<double> k64;             // folded model constants, passed by value
+  Fc3K<float> k32;
   double* d64;                  // scenarios [3][H][N]
   float* d32;
   SearchState* st;
@@ -95,10 +92,11 @@ struct Launch {
   int recheck_blocks;
 };
 
+// Folds the FC3 parameter vector into the constants the kernels use
+// (binary64, then rounded once to binary32).
+void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32);
+
 // ---- kernel launchers (rrg_kernels.cu) --------------------------------
-cudaError_t launch_fold_constants(const double* params, Fc3K<double>* k64, Fc3K<float>* k32,
-                                  cudaStream_t s);
-size_t fc3k_size(bool fp64);
 cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
                           const unsigned long long* t_dev, const double* amp);
 cudaError_t launch_round_scenarios(const Launch& L);

@@ -35,13 +35,10 @@ template <typename T> __device__ __forceinline__ T inf_v();
 template <> __device__ __forceinline__ float inf_v<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double inf_v<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
 
-size_t fc3k_size(bool fp64) { return fp64 ? sizeof(Fc3K<double>) : sizeof(Fc3K<float>); }
-
 // ---------------------------------------------------------------------------
-// Constant folding (once per handle).
-__global__ void fold_constants_kernel(const double* __restrict__ P, Fc3K<double>* k64,
-                                      Fc3K<float>* k32) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Constant folding (once per handle, on the host; no fused multiply-add can
+// occur in these products and quotients, so host and device would agree).
+void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32) {
   Fc3K<double> K;
   K.inv_p_atm = 1.0 / P[P_P_ATM];
   K.a_w = P[P_A_W];
@@ -72,12 +69,6 @@ __global__ void fold_constants_kernel(const double* __restrict__ P, Fc3K<double>
   F.RT_Vsm = static_cast<float>(K.RT_Vsm);
   F.inv_J = static_cast<float>(K.inv_J);
   *k32 = F;
-}
-
-cudaError_t launch_fold_constants(const double* params, Fc3K<double>* k64, Fc3K<float>* k32,
-                                  cudaStream_t s) {
-  fold_constants_kernel<<<1, 32, 0, s>>>(params, k64, k32);
-  return cudaGetLastError();
 }
 
 // Constants of the closed loop at setpoint I (binary64).
@@ -146,11 +137,11 @@ __device__ int equilibrium_dev(const Fc3K<double>& K, const double* __restrict__
   return 0;
 }
 
-__global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<double>* k64,
+__global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<double> k64,
                                    double v, double* out4, int32_t* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double q[3], y = 0.0;
-  const int rc = equilibrium_dev(*k64, P, v, q, &y);
+  const int rc = equilibrium_dev(k64, P, v, q, &y);
   out4[0] = q[0] + P[P_P_ATM];
   out4[1] = q[1];
   out4[2] = q[2] + P[P_P_ATM];
@@ -159,7 +150,7 @@ __global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<doub
 }
 
 cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_t* d_status) {
-  equilibrium_kernel<<<1, 32, 0, L.stream>>>(L.params, L.k64_dev, v, d_out4, d_status);
+  equilibrium_kernel<<<1, 32, 0, L.stream>>>(L.params, L.k64, v, d_out4, d_status);
   return cudaGetLastError();
 }
 
@@ -377,12 +368,11 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
                            bool recheck_classify) {
   dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
   if (use_fp64) {
-    rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(
-        L, *static_cast<const Fc3K<double>*>(L.k64_host), L.d64, L.cand_k64, early_exit, 0);
+    rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.cand_k64,
+                                                                early_exit, 0);
   } else {
-    rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(
-        L, *static_cast<const Fc3K<float>*>(L.k32_host), L.d32, L.cand_k32, early_exit,
-        recheck_classify ? 1 : 0);
+    rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.cand_k32,
+                                                               early_exit, recheck_classify ? 1 : 0);
   }
   return cudaGetLastError();
 }
@@ -415,8 +405,7 @@ recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
 }
 
 cudaError_t launch_recheck(const Launch& L, int early_exit) {
-  recheck_kernel<<<L.recheck_blocks, 64, 0, L.stream>>>(
-      L, *static_cast<const Fc3K<double>*>(L.k64_host), early_exit);
+  recheck_kernel<<<L.recheck_blocks, 64, 0, L.stream>>>(L, L.k64, early_exit);
   return cudaGetLastError();
 }
 
@@ -556,7 +545,7 @@ __device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa
 
 __device__ void prepare_candidates(const Launch& L, int m) {
   const SearchState* s = L.st;
-  const Fc3K<double> K = *L.k64_dev;
+  const Fc3K<double>& K = L.k64;
   const double thr_ss =
       __dadd_rn(L.scfg.y_min, __dmul_rn(L.scfg.eps_ss, __dsub_rn(L.scfg.y_c, L.scfg.y_min)));
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -688,7 +677,7 @@ cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d
 // Simulated plant of the closed loop (Fig. 1) and the loop bookkeeping.
 __device__ void plant_step(const Launch& L, const double* x, double v, uint64_t seed, uint64_t upd,
                            const double* amp, double* x_next) {
-  const Fc3K<double> K = *L.k64_dev;
+  const Fc3K<double>& K = L.k64;
   const CandK<double> C = cand_consts(L.params, v);
   const double p_atm = L.params[P_P_ATM];
   double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm;
