@@ -246,6 +246,52 @@ int rrg_set_profiling(rrg_handle h, int on);
 int rrg_get_stats(rrg_handle h, rrg_stats *out);
 int rrg_reset_stats(rrg_handle h);
 
+/* ---- allocation-free candidate evaluation ---------------------------
+ * The paper has no counterpart of this entry point.  It is for callers that
+ * must not allocate device memory once they run: a fixed-rate control task
+ * (the governor's natural home) where an allocation can block for an
+ * unbounded time or fail once device memory is fragmented, or a host program
+ * that hands all device memory out from its own pool and does not allow a
+ * library to call cudaMalloc.  Such a caller cannot create a handle
+ * (rrg_create allocates), so this call needs none.
+ *
+ * It computes what rrg_eval_candidates computes (without P) for m kappas on
+ * scenarios the caller already holds on the device:
+ *   model_params   host, RRG_NPARAM doubles; cfg host (validated like
+ *                  rrg_create; search and n_rounds are ignored)
+ *   cuda_stream    stream to enqueue on (NULL: the legacy default stream)
+ *   d_scen64       device, 3*H*N doubles (layout above); needed unless
+ *                  cfg->precision == RRG_FP32
+ *   d_scen32       device, 3*H*N floats, the binary32 copy; needed unless
+ *                  cfg->precision == RRG_FP64
+ *   d_x_t          device, 3 doubles; v_prev, r_t by value (finite, > 0)
+ *   d_kappas       device, m doubles, each in [0, 1] (not checked: device data)
+ *   d_admissible   device out, m bytes; d_min_slack device out, m doubles or
+ *                  NULL (same meaning as in rrg_eval_candidates)
+ * Its only working memory is one file-scope device array of
+ * RRG_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * holds until the process exits.  Limits: 1 <= m <= RRG_STATIC_MAX_CANDIDATES
+ * (and <= cfg->max_candidates) and m * n_scenarios <= RRG_STATIC_MAX_LANES;
+ * beyond them the call returns RRG_EINVAL and rrg_last_error(NULL) says which
+ * limit was hit.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  It only enqueues work (asynchronous).
+ *
+ * The first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  Every call uses the same scratch, which
+ * keeps the last call's contents; each call re-initialises everything it
+ * reads, but calls that may overlap on the GPU (on different streams, or from
+ * host threads without ordering between them) race on the scratch and their
+ * results are undefined.  Errors: RRG_EINVAL, RRG_ECUDA. */
+#define RRG_STATIC_MAX_CANDIDATES 64
+#define RRG_STATIC_MAX_LANES 131072
+#define RRG_STATIC_SCRATCH_BYTES (1u << 20)
+int rrg_eval_candidates_static(const double *model_params, int n_params, const rrg_config *cfg,
+                               void *cuda_stream, const double *d_scen64, const float *d_scen32,
+                               const double *d_x_t, double v_prev, double r_t,
+                               const double *d_kappas, int m, uint8_t *d_admissible,
+                               double *d_min_slack);
+
 #ifdef __cplusplus
 }
 #endif

@@ -667,3 +667,9 @@ int rrg_reset_stats(rrg_handle h) {
 }
 
 }  // extern "C"
+
+namespace rrg {
+// Used by the handle-less entry point in rrg_static.cu.
+int check_config(const rrg_config* c) { return validate_cfg(c); }
+void set_thread_error(const char* msg) { g_create_error = msg; }
+}  // namespace rrg

@@ -7,9 +7,9 @@
 
 #include "../../include/rrg.h"
 
-namespace rrg {
-
 #include "rrg_device.cuh"
+
+namespace rrg {
 
 // FC3 parameter indices (the layout documented in rrg.h).
 enum ParamIdx {
@@ -119,6 +119,11 @@ cudaError_t launch_loop_end(const Launch& L, LoopState* ls, uint64_t seed, uint6
                             int32_t* d_flags_out, double* d_x_out);
 cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, double v0,
                              double* d_x_out);
+
+// Configuration check shared with the handle-less entry point (rrg_capi.cu);
+// on failure the message is readable with rrg_last_error(NULL).
+int check_config(const rrg_config* c);
+void set_thread_error(const char* msg);
 
 // Number of search rounds each strategy enqueues (host-side schedule).
 int search_round_count(const SearchCfg& c);

@@ -1,0 +1,175 @@
+// rrg_static.cu -- rrg_eval_candidates_static: candidate evaluation that
+// allocates nothing.  Its working memory is one file-scope device array of
+// fixed size; everything else is the caller's.  The paper has no counterpart
+// of this entry point: it exists for callers that cannot allocate device
+// memory while they run (see include/rrg.h).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "rrg_internal.h"
+
+namespace rrg {
+namespace {
+
+constexpr int kStaticMaxCand = RRG_STATIC_MAX_CANDIDATES;
+constexpr size_t kStaticMaxLanes = RRG_STATIC_MAX_LANES;
+
+// Layout of the scratch array (byte offsets, each 256-byte aligned).
+constexpr size_t align256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
+constexpr size_t kOffState = 0;
+constexpr size_t kOffParams = kOffState + align256(sizeof(SearchState));
+constexpr size_t kOffKappa = kOffParams + align256(RRG_NPARAM * sizeof(double));
+constexpr size_t kOffV = kOffKappa + align256(kStaticMaxCand * sizeof(double));
+constexpr size_t kOffK64 = kOffV + align256(kStaticMaxCand * sizeof(double));
+constexpr size_t kOffK32 = kOffK64 + align256(kStaticMaxCand * sizeof(CandK<double>));
+constexpr size_t kOffOk = kOffK32 + align256(kStaticMaxCand * sizeof(CandK<float>));
+constexpr size_t kOffDead = kOffOk + align256(kStaticMaxCand * sizeof(int32_t));
+constexpr size_t kOffSs = kOffDead + align256(kStaticMaxCand * sizeof(int32_t));
+constexpr size_t kOffMin = kOffSs + align256(kStaticMaxCand * sizeof(int32_t));
+constexpr size_t kOffCount = kOffMin + align256(kStaticMaxCand * sizeof(unsigned long long));
+constexpr size_t kOffStats = kOffCount + align256(sizeof(uint32_t));
+constexpr size_t kOffList = kOffStats + align256(sizeof(DevStats));
+constexpr size_t kScratchBytes = kOffList + align256(kStaticMaxLanes * sizeof(uint32_t));
+static_assert(kScratchBytes <= RRG_STATIC_SCRATCH_BYTES, "scratch layout exceeds its stated size");
+
+// The scratch itself: held by every device that loads the library.
+__device__ __align__(256) unsigned char g_rrg_static_scratch[RRG_STATIC_SCRATCH_BYTES];
+
+struct ParamBlock { double v[RRG_NPARAM]; };
+
+// Writes the parameter vector (passed by value) into the scratch and clears
+// the scratch's step counters.
+__global__ void static_params_kernel(ParamBlock pb, double* params, DevStats* stats) {
+  const int i = threadIdx.x;
+  if (i < RRG_NPARAM) params[i] = pb.v[i];
+  if (i == 0) {
+    stats->lane_steps = 0ull;
+    stats->lane_steps_fp64 = 0ull;
+    stats->rechecked = 0ull;
+  }
+}
+
+// Device address of the scratch on each device, looked up once per device.
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+unsigned char* g_scratch_ptr[kMaxDevices] = {};
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_thread_error(buf);
+  return code;
+}
+
+int scratch_for_current_device(unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(RRG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(RRG_EINVAL, "device ordinal %d not supported", dev);
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_rrg_static_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(RRG_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return RRG_OK;
+}
+
+}  // namespace
+}  // namespace rrg
+
+using namespace rrg;
+
+extern "C" int rrg_eval_candidates_static(const double* model_params, int n_params,
+                                          const rrg_config* cfg, void* cuda_stream,
+                                          const double* d_scen64, const float* d_scen32,
+                                          const double* d_x_t, double v_prev, double r_t,
+                                          const double* d_kappas, int m, uint8_t* d_admissible,
+                                          double* d_min_slack) {
+  if (!model_params || n_params != RRG_NPARAM)
+    return fail(RRG_EINVAL, "model_params must hold %d values", RRG_NPARAM);
+  for (int i = 0; i < RRG_NPARAM; ++i)
+    if (!std::isfinite(model_params[i])) return fail(RRG_EINVAL, "model_params[%d] not finite", i);
+  int rc = check_config(cfg);
+  if (rc != RRG_OK) return rc;
+  if (m < 1 || m > cfg->max_candidates || m > kStaticMaxCand)
+    return fail(RRG_EINVAL, "m = %d: the allocation-free evaluation takes 1..%d candidates "
+                "(and at most max_candidates)", m, kStaticMaxCand);
+  const size_t lanes = static_cast<size_t>(m) * static_cast<size_t>(cfg->n_scenarios);
+  if (lanes > kStaticMaxLanes)
+    return fail(RRG_EINVAL, "m * n_scenarios = %zu exceeds the scratch limit of %zu trajectories",
+                lanes, kStaticMaxLanes);
+  if (!std::isfinite(v_prev) || !std::isfinite(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
+    return fail(RRG_EINVAL, "v_prev and r_t must be finite and > 0");
+  if (!d_x_t || !d_kappas || !d_admissible)
+    return fail(RRG_EINVAL, "d_x_t, d_kappas and d_admissible must be non-NULL");
+  const bool need64 = cfg->precision != RRG_FP32, need32 = cfg->precision != RRG_FP64;
+  if ((need64 && !d_scen64) || (need32 && !d_scen32))
+    return fail(RRG_EINVAL, "precision %d needs the %s scenario array(s)", cfg->precision,
+                cfg->precision == RRG_FP64 ? "binary64" : (cfg->precision == RRG_FP32 ? "binary32" : "binary64 and binary32"));
+
+  unsigned char* base = nullptr;
+  rc = scratch_for_current_device(&base);
+  if (rc != RRG_OK) return rc;
+
+  Launch L{};
+  L.stream = static_cast<cudaStream_t>(cuda_stream);
+  L.N = cfg->n_scenarios;
+  L.H = cfg->horizon;
+  L.precision = cfg->precision;
+  L.early_exit = cfg->early_exit;
+  L.m_cap = m;
+  L.dt = cfg->dt;
+  L.y_min = cfg->y_min;
+  L.eps_abs = cfg->precision == RRG_FP32_RECHECK ? cfg->recheck_eps_rel * std::fabs(cfg->y_min) : 0.0;
+  L.scfg.search = cfg->search;
+  L.scfg.m_cap = m;
+  L.scfg.n_bisect = cfg->n_bisect;
+  L.scfg.n_rounds = cfg->n_rounds;
+  L.scfg.ss_check = cfg->ss_check;
+  L.scfg.y_min = cfg->y_min;
+  L.scfg.eps_ss = cfg->eps_ss;
+  L.scfg.y_c = cfg->y_c;
+  fold_constants(model_params, &L.k64, &L.k32);
+  L.params = reinterpret_cast<double*>(base + kOffParams);
+  L.d64 = const_cast<double*>(d_scen64);
+  L.d32 = const_cast<float*>(d_scen32);
+  L.st = reinterpret_cast<SearchState*>(base + kOffState);
+  L.cand_kappa = reinterpret_cast<double*>(base + kOffKappa);
+  L.cand_v = reinterpret_cast<double*>(base + kOffV);
+  L.cand_k64 = reinterpret_cast<CandK<double>*>(base + kOffK64);
+  L.cand_k32 = reinterpret_cast<CandK<float>*>(base + kOffK32);
+  L.cand_ok = reinterpret_cast<int32_t*>(base + kOffOk);
+  L.cand_dead = reinterpret_cast<int32_t*>(base + kOffDead);
+  L.cand_ss = reinterpret_cast<int32_t*>(base + kOffSs);
+  L.cand_min = reinterpret_cast<unsigned long long*>(base + kOffMin);
+  L.recheck_count = reinterpret_cast<uint32_t*>(base + kOffCount);
+  L.stats = reinterpret_cast<DevStats*>(base + kOffStats);
+  L.recheck_list = reinterpret_cast<uint32_t*>(base + kOffList);
+  L.P = nullptr;
+  L.recheck_blocks = 2 * 152;
+
+  ParamBlock pb;
+  std::memcpy(pb.v, model_params, sizeof pb.v);
+  static_params_kernel<<<1, 32, 0, L.stream>>>(pb, const_cast<double*>(L.params), L.stats);
+  cudaError_t e = cudaGetLastError();
+  // the prepare kernel rewrites every per-candidate flag, key and the recheck
+  // count, so nothing left in the scratch by an earlier call is read
+  if (e == cudaSuccess) e = launch_eval_prepare(L, d_x_t, v_prev, r_t, d_kappas, m);
+  if (e == cudaSuccess)
+    e = launch_rollout(L, m, cfg->precision == RRG_FP64, cfg->early_exit,
+                       cfg->precision == RRG_FP32_RECHECK);
+  if (e == cudaSuccess && cfg->precision == RRG_FP32_RECHECK) e = launch_recheck(L, cfg->early_exit);
+  if (e == cudaSuccess) e = launch_eval_finish(L, m, d_admissible, d_min_slack);
+  if (e != cudaSuccess) return fail(RRG_ECUDA, "launch: %s", cudaGetErrorString(e));
+  return RRG_OK;
+}

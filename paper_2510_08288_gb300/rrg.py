@@ -82,6 +82,8 @@ def _load():
         "rrg_set_profiling": (ctypes.c_int, [_p, ctypes.c_int]),
         "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
         "rrg_reset_stats": (ctypes.c_int, [_p]),
+        "rrg_eval_candidates_static": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, _p, _p, _p, _d,
+                                                      _d, _p, ctypes.c_int, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -243,6 +245,17 @@ def rrg_get_stats(h) -> dict:
 
 def rrg_reset_stats(h):
     _check(lib.rrg_reset_stats(h), h)
+
+
+def rrg_eval_candidates_static(params, cfg: RrgConfig, stream, d_scen64, d_scen32, d_x_t, v_prev, r_t,
+                               d_kappas, m, d_admissible, d_min_slack=None):
+    """Allocation-free evaluation on caller-owned device buffers (see rrg.h);
+    asynchronous on `stream` (None: the legacy default stream)."""
+    p = _f64(params)
+    _check(lib.rrg_eval_candidates_static(_ptr(p), int(p.shape[0]), ctypes.byref(cfg), _stream_ptr(stream),
+                                          _tensor_ptr(d_scen64), _tensor_ptr(d_scen32), _tensor_ptr(d_x_t),
+                                          float(v_prev), float(r_t), _tensor_ptr(d_kappas), int(m),
+                                          _tensor_ptr(d_admissible), _tensor_ptr(d_min_slack)), None)
 
 
 @dataclass
