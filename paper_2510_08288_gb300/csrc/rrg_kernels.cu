@@ -218,7 +218,7 @@ cudaError_t launch_round_scenarios(const Launch& L) {
 // The candidate's dead flag is read at the start of a block and used at its
 // end, for the same reason.
 #ifndef RRG_PREFETCH
-#define RRG_PREFETCH 4
+#define RRG_PREFETCH 8
 #endif
 constexpr int kPrefetch = RRG_PREFETCH;
 
