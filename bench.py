@@ -38,6 +38,7 @@ UNIT = "RG updates/s"
 N_SCEN, HORIZON, N_BISECT, M_CAND = 1024, 2000, 12, 64
 SEED, V0 = 1, 100.0
 RECHECK_EPS_REL = 1e-6
+PROBE_STEPS = 128
 # algorithmic binary32 flops of one trajectory step (4 right-hand sides of 27,
 # 3 stage points of 6, the RK4 combination of 18, the disturbance add of 3,
 # output, slack, finiteness and running min of 6); counted from the source
@@ -58,15 +59,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scenarios", type=int, default=N_SCEN, help="smaller cases for profiling only")
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
+    ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
+                    help="steps of the probe that pipelines the first two bisection rounds (0: off)")
     return ap.parse_args()
 
 
-def workload_config(W, K, N=N_SCEN, H=HORIZON):
+def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS):
     return {
         "workload": "closed-loop robust RG on FC3: N_sim=%d scenarios, horizon %d RK4 steps "
                     "(dt=0.01 s), staircase r (8 levels over 50..300 A, seed 1, 125 updates/level), "
                     "timed updates [%d, %d) of the 1000-update run" % (N, H, W, W + K),
-        "search": "speculative bisection (Alg. 1 result), N_kappa=12, 64 candidates/round",
+        "search": "speculative bisection (Alg. 1 result), N_kappa=12, 64 candidates/round, "
+                  "first two rounds pipelined after a %d-step probe" % probe,
         "kappa_tol": 2.0 ** -11,
         "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
         "l2": "256 MB written between timed steps",
@@ -239,7 +243,7 @@ def run_gpu(args):
     cfg = R.rrg_config_default(horizon=HZ, n_scenarios=NS, max_candidates=M_CAND,
                                n_bisect=N_BISECT, search=R.SEARCH_SPEC_BISECT,
                                precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
-                               recheck_eps_rel=RECHECK_EPS_REL)
+                               recheck_eps_rel=RECHECK_EPS_REL, probe_steps=args.probe_steps)
     g = R.Governor(p, cfg, stream)
     x0, _ = g.equilibrium(V0)
     dev = torch.device("cuda", local)
@@ -336,7 +340,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(W, K, NS, HZ),
+            "config": workload_config(W, K, NS, HZ, args.probe_steps),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -351,6 +355,7 @@ def run_gpu(args):
             "clocks": clk,
             "fp64_bisect_gpu": fp64,
             "rechecked_trajectories": st["rechecked"],
+            "pipeline_repairs": st["repairs"],
             "no_admissible_updates": int(np.sum(flags_dev[W:T] & 1)),
             "kappa_mean": float(np.mean(kap_dev[W:T])),
         }

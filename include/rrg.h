@@ -107,6 +107,15 @@ typedef struct {
     double  recheck_eps_rel; /* FP64 recheck band, relative to y_min          */
     double  dist_amp[3];     /* scenario disturbance half-ranges (Sec. IV-A:
                                 50 Pa, 10 rad/s, 50 Pa)                       */
+    int32_t probe_steps;     /* RRG_SEARCH_SPEC_BISECT only; > 0 pipelines its
+                                first two rounds: round 1 runs its first
+                                probe_steps steps, round 2's tree is built from
+                                those provisional outcomes and runs while round
+                                1 finishes; round 1 is then re-walked with its
+                                final outcomes and, if any decision changed,
+                                round 2 is redone (counted in rrg_stats.repairs).
+                                The result is always Alg. 1's.  0 = off;
+                                ignored when >= horizon                       */
 } rrg_config;
 
 typedef struct rrg_ctx *rrg_handle;
@@ -123,12 +132,14 @@ typedef struct {
                                    (only while profiling is on)               */
     double   recheck_ms;        /* same for recheck launches                  */
     uint64_t timed_rollouts;    /* rollout launches covered by rollout_ms     */
+    uint64_t repairs;           /* pipelined rounds redone after a provisional
+                                   outcome turned out wrong                   */
 } rrg_stats;
 
 /* Fills *cfg with the defaults of the paper's fuel-cell experiment: dt 0.01,
  * H 500, N 32, M 32, N_kappa 12, 3 rounds, SPEC_BISECT, FP32_RECHECK,
  * EXIT_CANDIDATE, ss_check 1, y_min 1.9, eps_ss 0.05, y_c 2.2, recheck band
- * 1e-6, amplitudes (50, 10, 50).  Never fails. */
+ * 1e-6, amplitudes (50, 10, 50), probe_steps 128.  Never fails. */
 void rrg_config_default(rrg_config *cfg);
 
 /* Creates a governor on the current CUDA device.

@@ -42,6 +42,7 @@ struct rrg_ctx {
   uint32_t* recheck_list = nullptr;
   uint32_t* recheck_count = nullptr;
   DevStats* stats = nullptr;
+  void* lane_state = nullptr;
   uint8_t* P_dev = nullptr;
   double* io_dev = nullptr;     // [0..2] x, [3] r, [4] v, [5..8] out, [8] amp.. see offsets
   int32_t* flag_dev = nullptr;  // [0] flags, [1] status
@@ -125,9 +126,10 @@ int validate_cfg(const rrg_config* c) {
   for (int i = 0; i < 3; ++i)
     if (!is_fin(c->dist_amp[i]) || c->dist_amp[i] < 0.0)
       return set_err(nullptr, RRG_EINVAL, "dist_amp must be finite and >= 0");
+  if (c->probe_steps < 0) return set_err(nullptr, RRG_EINVAL, "probe_steps must be >= 0");
   const unsigned long long lanes =
-      static_cast<unsigned long long>(c->max_candidates) * static_cast<unsigned long long>(c->n_scenarios);
-  if (lanes >= (1ull << 32)) return set_err(nullptr, RRG_EINVAL, "max_candidates * n_scenarios >= 2^32");
+      2ull * static_cast<unsigned long long>(c->max_candidates) * static_cast<unsigned long long>(c->n_scenarios);
+  if (lanes >= (1ull << 32)) return set_err(nullptr, RRG_EINVAL, "2 * max_candidates * n_scenarios >= 2^32");
   return RRG_OK;
 }
 
@@ -140,7 +142,7 @@ void free_all(rrg_ctx* h) {
   void* ptrs[] = {h->params_dev, h->d64, h->d32, h->st, h->cand_kappa,
                   h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
-                  h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev};
+                  h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->io_h) cudaFreeHost(h->io_h);
@@ -182,6 +184,8 @@ void fill_launch(rrg_ctx* h) {
   L.stats = h->stats;
   L.P = nullptr;
   L.recheck_blocks = 2 * 152;
+  L.probe_steps = c.probe_steps;
+  L.lane_state = h->lane_state;
 }
 
 cudaEvent_t take_event(rrg_ctx* h) {
@@ -195,8 +199,9 @@ cudaEvent_t take_event(rrg_ctx* h) {
   return e;
 }
 
-// Rollout of the current round (+ recheck in FP32_RECHECK mode).
-int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit) {
+// Rollout of the current round (+ recheck in FP32_RECHECK mode unless the
+// launch is a probe, whose lanes are not decided yet).
+int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit, bool recheck = true) {
   const bool timed = h->profiling && !h->capturing;
   cudaEvent_t a = nullptr, b = nullptr;
   if (timed) { a = take_event(h); b = take_event(h); }
@@ -209,7 +214,7 @@ int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit) {
   }
   h->launches++;
   h->rollout_launches++;
-  if (h->cfg.precision == RRG_FP32_RECHECK) {
+  if (recheck && h->cfg.precision == RRG_FP32_RECHECK) {
     cudaEvent_t c = nullptr, d = nullptr;
     if (timed) { c = take_event(h); d = take_event(h); }
     if (c && d) CK(cudaEventRecord(c, h->stream));
@@ -223,20 +228,50 @@ int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit) {
   return RRG_OK;
 }
 
-// The search of one RG update on already-sampled scenarios.
+// The search of one RG update on already-sampled scenarios.  Each search
+// kernel decides on the device and names the slots the following prepare
+// launch sets up; the host only enqueues the fixed sequence.
 int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
                    const unsigned long long* t_dev, const double* d_vp, double* d_vt,
                    double* d_kappa, int32_t* d_flags) {
   const Launch& L = h->L;
+  const SearchCfg& c = h->scfg;
+  const int R = search_round_count(c);
   CK(launch_search_begin(L, d_x, d_r, t_dev, d_vp));
-  h->launches++;
-  const int R = search_round_count(h->scfg);
-  for (int r = 0; r < R; ++r) {
-    const int width = search_round_width(h->scfg, r);
+  CK(launch_prepare(L, search_round_width(c, 0)));
+  h->launches += 2;
+  int r0 = 0;
+  const bool pipe = search_pipelined(c, h->cfg.horizon);
+  if (pipe) {
+    // probe of round 1, then round 1's remainder together with round 2; the
+    // rounds after it only do work when the validation found a wrong guess
+    const int w0 = search_round_width(c, 0), w1 = search_round_width(c, 1);
+    int rc = enqueue_round_work(h, L, w0, h->cfg.early_exit, false);
+    if (rc != RRG_OK) return rc;
+    CK(launch_search_mid(L));
+    CK(launch_prepare(L, w1));
+    h->launches += 2;
+    rc = enqueue_round_work(h, L, w0 + w1, h->cfg.early_exit);
+    if (rc != RRG_OK) return rc;
+    CK(launch_search_next(L, d_vt, d_kappa, d_flags));
+    h->launches++;
+    if (R > 1) {
+      CK(launch_prepare(L, w1));
+      h->launches++;
+    }
+    h->rounds++;
+    r0 = 1;
+  }
+  for (int r = r0; r < R; ++r) {
+    const int width = pipe ? search_round_width(c, 1) : search_round_width(c, r);
     int rc = enqueue_round_work(h, L, width, h->cfg.early_exit);
     if (rc != RRG_OK) return rc;
     CK(launch_search_next(L, d_vt, d_kappa, d_flags));
     h->launches++;
+    if (r + 1 < R) {
+      CK(launch_prepare(L, pipe ? search_round_width(c, 1) : search_round_width(c, r + 1)));
+      h->launches++;
+    }
     h->rounds++;
   }
   return RRG_OK;
@@ -268,6 +303,7 @@ void rrg_config_default(rrg_config* c) {
   c->dist_amp[0] = 50.0;
   c->dist_amp[1] = 10.0;
   c->dist_amp[2] = 50.0;
+  c->probe_steps = 128;
 }
 
 const char* rrg_last_error(rrg_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -309,15 +345,20 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   ALLOC(d64, HN3);
   ALLOC(d32, HN3);
   ALLOC(st, 1);
-  ALLOC(cand_kappa, M);
-  ALLOC(cand_v, M);
-  ALLOC(cand_k64, M);
-  ALLOC(cand_k32, M);
-  ALLOC(cand_ok, M);
-  ALLOC(cand_dead, M);
-  ALLOC(cand_ss, M);
-  ALLOC(cand_min, M);
-  ALLOC(recheck_list, M * N);
+  // two slot ranges: a pipelined round and the round after it run together
+  ALLOC(cand_kappa, 2 * M);
+  ALLOC(cand_v, 2 * M);
+  ALLOC(cand_k64, 2 * M);
+  ALLOC(cand_k32, 2 * M);
+  ALLOC(cand_ok, 2 * M);
+  ALLOC(cand_dead, 2 * M);
+  ALLOC(cand_ss, 2 * M);
+  ALLOC(cand_min, 2 * M);
+  ALLOC(recheck_list, 2 * M * N);
+  if (e == cudaSuccess && c.search == RRG_SEARCH_SPEC_BISECT && c.probe_steps > 0) {
+    e = cudaMalloc(&h->lane_state, M * N * sizeof(LaneState<double>));
+    if (e != cudaSuccess) cudaGetLastError();
+  }
   ALLOC(recheck_count, 1);
   ALLOC(stats, 1);
   ALLOC(io_dev, IO_LEN);
@@ -348,6 +389,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   s.n_bisect = c.n_bisect;
   s.n_rounds = c.n_rounds;
   s.ss_check = c.ss_check;
+  s.probe_steps = c.search == RRG_SEARCH_SPEC_BISECT ? c.probe_steps : 0;
   s.y_min = c.y_min;
   s.eps_ss = c.eps_ss;
   s.y_c = c.y_c;
@@ -426,7 +468,8 @@ int rrg_eval_candidates(rrg_handle h, const double* x_t, double v_prev, double r
     if (early > RRG_EXIT_LANE) early = RRG_EXIT_LANE;
   }
   CK(launch_eval_prepare(L, h->io_dev + IO_X, v_prev, r_t, h->kap_dev, m));
-  h->launches++;
+  CK(launch_prepare(L, m));
+  h->launches += 2;
   int rc = enqueue_round_work(h, L, m, early);
   if (rc != RRG_OK) return rc;
   CK(launch_eval_finish(L, m, h->adm_dev, h->kap_dev + M));
@@ -649,6 +692,7 @@ int rrg_get_stats(rrg_handle h, rrg_stats* out) {
   out->rollout_ms = h->rollout_ms;
   out->recheck_ms = h->recheck_ms;
   out->timed_rollouts = h->timed_rollouts;
+  out->repairs = ds.repairs;
   return RRG_OK;
 }
 

@@ -22,6 +22,28 @@ static_assert(P_COUNT == RRG_NPARAM, "parameter layout");
 
 constexpr int kMaxTreeNodes = 2 * RRG_MAX_CANDIDATES;
 
+// What the blocks of one rollout launch do with their candidate slot.
+enum SegMode : int32_t {
+  SEG_FULL = 0,      // steps 0..H
+  SEG_PROBE = 1,     // steps 0..probe_steps; survivors save their state
+  SEG_CONTINUE = 2,  // resume a probed trajectory at probe_steps, run to H
+};
+
+// A launch covers up to two slot ranges: blockIdx.y < seg[0].count maps to
+// slot seg[0].base + y, the next seg[1].count rows to seg[1].base + ...
+struct Seg {
+  int32_t mode, count, base;
+};
+
+// Saved state of a probed trajectory (status 0: still running, continue it;
+// 1: finished in the probe and already reduced).
+template <typename T>
+struct LaneState {
+  T q[3];
+  T smin;
+  int32_t status;
+};
+
 // Device-resident state of one RG update's search (one per handle).
 struct SearchState {
   double x[3];        // x_t (absolute coordinates)
@@ -38,7 +60,20 @@ struct SearchState {
   int32_t round;      // rounds finished
   int32_t invalid;    // inputs rejected on the device
   double v_t_out;     // governed reference of the finished search
-  int32_t slot_of_node[kMaxTreeNodes];  // bisection tree: heap node -> slot
+  Seg seg[2];         // what the next rollout launch runs
+  int32_t prep_base;  // slots the next prepare launch fills: prep_base ..
+  int32_t prep_m;     //   prep_base + prep_m - 1
+  // pipelined first round of the speculative bisection: the round is probed,
+  // the next tree is built from the provisional outcomes, and both run
+  // together; the real outcomes are compared with the provisional ones
+  int32_t probe;      // 1 while a probed round awaits validation
+  int32_t depth1;     // levels of the tree built from provisional outcomes
+  int32_t prov_len, prov_done;
+  uint32_t prov_bits;
+  double w_lo, w_hi, w_kappa, w_kopt;  // search state before the probed round
+  int32_t w_iter, w_any;
+  int32_t slot_of_node[kMaxTreeNodes];   // bisection tree: heap node -> slot
+  int32_t slot_of_node1[kMaxTreeNodes];  // tree of the pipelined second round
 };
 
 // Device counters of a handle.
@@ -46,6 +81,7 @@ struct DevStats {
   unsigned long long lane_steps;
   unsigned long long lane_steps_fp64;
   unsigned long long rechecked;
+  unsigned long long repairs;   // probed rounds whose provisional outcome was wrong
 };
 
 // Closed-loop device state.
@@ -62,6 +98,7 @@ struct SearchCfg {
   int n_bisect;      // N_kappa
   int n_rounds;      // k-section rounds
   int ss_check;
+  int probe_steps;   // > 0: pipeline the first two bisection rounds
   double y_min, eps_ss, y_c;
 };
 
@@ -90,6 +127,8 @@ struct Launch {
   DevStats* stats;
   uint8_t* P;                   // optional
   int recheck_blocks;
+  int probe_steps;              // steps of a SEG_PROBE segment
+  void* lane_state;             // LaneState<T>[m_cap * N] for probed rounds
 };
 
 // Folds the FC3 parameter vector into the constants the kernels use
@@ -104,6 +143,10 @@ cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double
                                 const unsigned long long* t_dev, const double* d_v_prev);
 cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa,
                                int32_t* d_flags);
+cudaError_t launch_search_mid(const Launch& L);
+// Candidate set-up for the slots the last search kernel chose: one block per
+// candidate (the binary64 equilibrium solves spread over the SMs).
+cudaError_t launch_prepare(const Launch& L, int width);
 cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
                                 const double* d_kappas, int m);
 cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d_min_slack);
@@ -127,7 +170,9 @@ void set_thread_error(const char* msg);
 
 // Number of search rounds each strategy enqueues (host-side schedule).
 int search_round_count(const SearchCfg& c);
-// Largest candidate count of any round of the schedule.
+// Candidate count of round `round` of the schedule.
 int search_round_width(const SearchCfg& c, int round);
+// True when the first two rounds are pipelined (probe + continue).
+bool search_pipelined(const SearchCfg& c, int horizon);
 
 }  // namespace rrg

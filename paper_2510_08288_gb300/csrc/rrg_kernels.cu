@@ -229,21 +229,38 @@ __device__ __forceinline__ T checked_slack(const CandK<T>& C, T q_ca, T w, T q_s
   return (fabs(z) <= max_finite<T>() && fabs(s) <= max_finite<T>()) ? s : -inf_v<T>();
 }
 
+// Lane outcome of run_lane.
+enum LaneEnd : int { LANE_REACHED_END = 0, LANE_VIOLATED = 1, LANE_STOPPED = 2 };
+
+// Steps j0+1..j_end of one trajectory, from the state (q_ca, w, q_sm) at
+// step j0 (updated in place); with j0 = 0 the output at step 0 is checked
+// first (for j0 > 0 it was checked by the run that stopped there).  smin_in
+// is the min slack so far.
 template <typename T>
 __device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
-                                      const T* __restrict__ d, int k, int N, int H,
-                                      T q_ca, T w, T q_sm, T dt, T y_min, T thr,
-                                      const volatile int32_t* dead, unsigned* steps) {
-  T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
-  T smin = s;
-  int j = 0;
-  if (!(s < thr) && H > 0) {
+                                      const T* __restrict__ d, int k, int N, int H, int j0,
+                                      int j_end, T& q_ca, T& w, T& q_sm, T smin_in, T dt, T y_min,
+                                      T thr, const volatile int32_t* dead, unsigned* steps,
+                                      int* end) {
+  T smin = smin_in;
+  int j = j0;
+  int how = LANE_REACHED_END;
+  bool go = j < j_end;
+  if (j0 == 0) {
+    const T s0 = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    smin = fmin(smin, s0);
+    if (s0 < thr) {
+      how = LANE_VIOLATED;
+      go = false;
+    }
+  }
+  if (go) {
     const size_t HN = static_cast<size_t>(H) * N;
     T r0[kPrefetch], r1[kPrefetch], r2[kPrefetch];
-    const T* pf = d + k;  // next step to prefetch
+    const T* pf = d + static_cast<size_t>(j0) * N + k;  // next step to prefetch
 #pragma unroll
     for (int u = 0; u < kPrefetch; ++u) {
-      if (u < H) {
+      if (j0 + u < j_end) {
         r0[u] = __ldg(pf);
         r1[u] = __ldg(pf + HN);
         r2[u] = __ldg(pf + 2 * HN);
@@ -258,7 +275,7 @@ __device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
 #pragma unroll
       for (int u = 0; u < kPrefetch; ++u) {
         const T e0 = r0[u], e1 = r1[u], e2 = r2[u];
-        if (j + kPrefetch < H) {
+        if (j + kPrefetch < j_end) {
           r0[u] = __ldg(pf);
           r1[u] = __ldg(pf + HN);
           r2[u] = __ldg(pf + 2 * HN);
@@ -269,17 +286,26 @@ __device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
         w += e1;
         q_sm += e2;
         ++j;
-        s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+        const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
         smin = fmin(smin, s);
-        if ((s < thr) || (j == H)) {
+        if (s < thr) {
+          how = LANE_VIOLATED;
+          stop = true;
+          break;
+        }
+        if (j == j_end) {
           stop = true;
           break;
         }
       }
-      if (dead_now != 0) stop = true;
+      if (!stop && dead_now != 0) {
+        how = LANE_STOPPED;
+        stop = true;
+      }
     }
   }
-  *steps = static_cast<unsigned>(j);
+  *steps = static_cast<unsigned>(j - j0);
+  *end = how;
   return smin;
 }
 
@@ -289,15 +315,28 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
-// One thread per (candidate i = blockIdx.y, scenario k).  classify = 1 is the
-// binary32 pass of RRG_FP32_RECHECK: trajectories whose min slack lies in
-// [-eps, eps) are appended to the recheck list and decided later in binary64.
+// One thread per (candidate slot, scenario k); blockIdx.y picks the slot
+// through the state's two segments.  classify = 1 is the binary32 pass of
+// RRG_FP32_RECHECK: trajectories whose final min slack lies in [-eps, eps)
+// are appended to the recheck list and decided later in binary64.  A
+// SEG_PROBE lane that survives its probe steps saves its state and reports
+// nothing yet; the SEG_CONTINUE lane of the next launch finishes it.
 template <typename T>
 __global__ void __launch_bounds__(kRollThreads)
 rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d,
                const CandK<T>* __restrict__ cand, int early_exit, int classify) {
-  const int i = blockIdx.y;
-  if (i >= L.st->m) return;
+  const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
+  const int y = blockIdx.y;
+  int mode, i;
+  if (y < s0.count) {
+    mode = s0.mode;
+    i = s0.base + y;
+  } else if (y - s0.count < s1.count) {
+    mode = s1.mode;
+    i = s1.base + (y - s0.count);
+  } else {
+    return;
+  }
   const int N = L.N;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = k < N;
@@ -320,17 +359,50 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d,
 
   T smin = inf_v<T>();
   unsigned steps = 0;
+  bool final_lane = active;  // this launch decides the lane
   if (active) {
+    LaneState<T>* ls = mode == SEG_FULL ? nullptr
+                                        : static_cast<LaneState<T>*>(L.lane_state) +
+                                              static_cast<size_t>(i) * N + k;
     const double p_atm = L.params[P_P_ATM];
-    smin = run_lane<T>(K, C, d, k, N, L.H, static_cast<T>(L.st->x[0] - p_atm),
-                       static_cast<T>(L.st->x[1]), static_cast<T>(L.st->x[2] - p_atm),
-                       static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
-                       cand_stop ? dead : nullptr, &steps);
-    if (cand_stop && smin < thr) *dead = 1;
+    T q_ca = static_cast<T>(L.st->x[0] - p_atm), w = static_cast<T>(L.st->x[1]),
+      q_sm = static_cast<T>(L.st->x[2] - p_atm);
+    T smin0 = inf_v<T>();
+    int j0 = 0;
+    if (mode == SEG_CONTINUE) {
+      const LaneState<T> st = *ls;
+      if (st.status != 0) {
+        final_lane = false;  // finished and reduced in the probe
+      } else {
+        q_ca = st.q[0];
+        w = st.q[1];
+        q_sm = st.q[2];
+        smin0 = st.smin;
+        j0 = L.probe_steps;
+      }
+    }
+    if (final_lane) {
+      const int j_end = mode == SEG_PROBE ? L.probe_steps : L.H;
+      int end = LANE_REACHED_END;
+      smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, smin0,
+                         static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+                         cand_stop ? dead : nullptr, &steps, &end);
+      if (cand_stop && smin < thr) *dead = 1;
+      if (mode == SEG_PROBE) {
+        LaneState<T> o;
+        o.q[0] = q_ca;
+        o.q[1] = w;
+        o.q[2] = q_sm;
+        o.smin = smin;
+        o.status = end == LANE_REACHED_END ? 0 : 1;
+        *ls = o;
+        if (end == LANE_REACHED_END) final_lane = false;
+      }
+    }
   }
   bool lane_ok = true, uncertain = false;
   double contrib = static_cast<double>(inf_v<T>());
-  if (active) {
+  if (final_lane) {
     if (classify) {
       if (smin >= eps) {
         contrib = smin;
@@ -349,7 +421,7 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d,
     const uint32_t slot = atomicAdd(L.recheck_count, 1u);
     L.recheck_list[slot] = static_cast<uint32_t>(i) * static_cast<uint32_t>(N) + static_cast<uint32_t>(k);
   }
-  if (L.P != nullptr && active) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
+  if (L.P != nullptr && final_lane) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
 
   const bool all_ok = __all_sync(0xffffffffu, lane_ok);
   const double wmin = warp_min(contrib);
@@ -391,9 +463,11 @@ recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
     // a failed candidate needs no more decisions, unless P asks for every entry
     if (L.P == nullptr && !L.cand_ok[i]) continue;
     unsigned steps = 0;
-    const double smin = run_lane<double>(K, L.cand_k64[i], L.d64, k, N, L.H, L.st->x[0] - p_atm,
-                                         L.st->x[1], L.st->x[2] - p_atm, L.dt, L.y_min, thr,
-                                         nullptr, &steps);
+    int end = 0;
+    double q_ca = L.st->x[0] - p_atm, w = L.st->x[1], q_sm = L.st->x[2] - p_atm;
+    const double smin = run_lane<double>(K, L.cand_k64[i], L.d64, k, N, L.H, 0, L.H, q_ca, w, q_sm,
+                                         inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps,
+                                         &end);
     const bool ok = smin >= 0.0;
     if (!ok) L.cand_ok[i] = 0;
     if (L.P != nullptr) L.P[static_cast<size_t>(i) * N + k] = ok ? 1 : 0;
@@ -430,7 +504,10 @@ __device__ int choose_depth(const SearchState* s, const SearchCfg& c) {
   return d;
 }
 
-__device__ int build_tree(SearchState* s, double* cand_kappa, int depth) {
+// Puts the valid nodes of the depth-`depth` tree into slots base, base+1, ...
+// (kappas in cand_kappa[slot]); slot_map[node] = slot or -1.  Returns the count.
+__device__ int build_tree(const SearchState* s, int32_t* slot_map, double* cand_kappa, int base,
+                          int depth) {
   int count = 0;
   const int nodes = 1 << depth;
   for (int n = 1; n < nodes; ++n) {
@@ -447,27 +524,35 @@ __device__ int build_tree(SearchState* s, double* cand_kappa, int depth) {
       k = __dmul_rn(__dadd_rn(lo, hi), 0.5);
     }
     if (valid) {
-      s->slot_of_node[n] = count;
-      cand_kappa[count++] = k;
+      slot_map[n] = base + count;
+      cand_kappa[base + count] = k;
+      ++count;
     } else {
-      s->slot_of_node[n] = -1;
+      slot_map[n] = -1;
     }
   }
   return count;
 }
 
-// Follows Alg. 1's path through the evaluated tree.
-__device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* cand_ok) {
+// Follows Alg. 1's path through an evaluated tree of `depth` levels, one
+// iteration per level; bit l of *bits is the outcome at level l, *len the
+// number of levels walked.
+__device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* slot_map, int depth,
+                          const int32_t* cand_ok, uint32_t* bits, int* len) {
   int n = 1;
-  for (int lev = 0; lev < s->depth; ++lev) {
-    const int slot = s->slot_of_node[n];
+  uint32_t b = 0;
+  int l = 0;
+  for (int lev = 0; lev < depth; ++lev) {
+    const int slot = slot_map[n];
     if (slot < 0) break;  // cannot happen: the path only visits valid nodes
     const double k = s->kappa;
     s->iter += 1;
+    ++l;
     if (cand_ok[slot]) {
+      b |= 1u << lev;
       s->kappa_opt = k;
       s->any = 1;
-      if (k == 1.0) { s->done = 1; return; }
+      if (k == 1.0) { s->done = 1; break; }
       s->lo = k;
       n = 2 * n + 1;
     } else {
@@ -475,8 +560,10 @@ __device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* can
       n = 2 * n;
     }
     s->kappa = __dmul_rn(__dadd_rn(s->lo, s->hi), 0.5);
-    if (s->iter >= c.n_bisect) { s->done = 1; return; }
+    if (s->iter >= c.n_bisect) { s->done = 1; break; }
   }
+  *bits = b;
+  *len = l;
 }
 
 __device__ int grid_points(double* cand_kappa, int M) {
@@ -493,14 +580,30 @@ __device__ int interior_points(double* cand_kappa, int M, double lo, double hi) 
   return M;
 }
 
+__device__ void set_segments(SearchState* s, int mode0, int count0, int base0, int mode1,
+                             int count1, int base1) {
+  s->seg[0].mode = mode0; s->seg[0].count = count0; s->seg[0].base = base0;
+  s->seg[1].mode = mode1; s->seg[1].count = count1; s->seg[1].base = base1;
+}
+
+__device__ void save_walk_start(SearchState* s) {
+  s->w_lo = s->lo; s->w_hi = s->hi; s->w_kappa = s->kappa; s->w_kopt = s->kappa_opt;
+  s->w_iter = s->iter; s->w_any = s->any;
+}
+
+__device__ void restore_walk_start(SearchState* s) {
+  s->lo = s->w_lo; s->hi = s->w_hi; s->kappa = s->w_kappa; s->kappa_opt = s->w_kopt;
+  s->iter = s->w_iter; s->any = s->w_any; s->done = 0;
+}
+
 // Prepares the first round after the inputs were stored; returns m.
 __device__ int first_round(SearchState* s, const SearchCfg& c, double* cand_kappa) {
   s->lo = 0.0; s->hi = 1.0; s->kappa = 1.0; s->kappa_opt = 0.0;
-  s->iter = 0; s->any = 0; s->done = 0; s->flags = 0; s->round = 0;
+  s->iter = 0; s->any = 0; s->done = 0; s->flags = 0; s->round = 0; s->probe = 0;
   if (c.search == RRG_SEARCH_GRID || c.search == RRG_SEARCH_KSECTION)
     return grid_points(cand_kappa, c.m_cap);
   s->depth = choose_depth(s, c);
-  return build_tree(s, cand_kappa, s->depth);
+  return build_tree(s, s->slot_of_node, cand_kappa, 0, s->depth);
 }
 
 // Decides from the evaluated round and prepares the next; returns next m.
@@ -508,11 +611,13 @@ __device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa
                           const int32_t* cand_ok) {
   const int m = s->m;
   if (c.search == RRG_SEARCH_BISECT || c.search == RRG_SEARCH_SPEC_BISECT) {
-    walk_tree(s, c, cand_ok);
+    uint32_t bits;
+    int len;
+    walk_tree(s, c, s->slot_of_node, s->depth, cand_ok, &bits, &len);
     s->round += 1;
     if (s->done) return 0;
     s->depth = choose_depth(s, c);
-    return build_tree(s, cand_kappa, s->depth);
+    return build_tree(s, s->slot_of_node, cand_kappa, 0, s->depth);
   }
   int best = -1;
   for (int i = 0; i < m; ++i)
@@ -543,32 +648,45 @@ __device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa
   return interior_points(cand_kappa, c.m_cap, s->lo, s->hi);
 }
 
-__device__ void prepare_candidates(const Launch& L, int m) {
+// Candidate slot i: v_i by Eq. 2, constants, the steady-state check of
+// Eq. 3 and fresh flags.
+__device__ void prepare_slot(const Launch& L, int i) {
   const SearchState* s = L.st;
   const Fc3K<double>& K = L.k64;
   const double thr_ss =
       __dadd_rn(L.scfg.y_min, __dmul_rn(L.scfg.eps_ss, __dsub_rn(L.scfg.y_c, L.scfg.y_min)));
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double v = governed(s->v_prev, s->r, L.cand_kappa[i]);
-    L.cand_v[i] = v;
-    const CandK<double> C = cand_consts(L.params, v);
-    L.cand_k64[i] = C;
-    CandK<float> F;
-    F.W_o2 = static_cast<float>(C.W_o2);
-    F.V0 = static_cast<float>(C.V0);
-    F.y_scale = static_cast<float>(C.y_scale);
-    L.cand_k32[i] = F;
-    int ok = 1;
-    if (L.scfg.ss_check) {
-      double q[3], y_ss = 0.0;
-      ok = (equilibrium_dev(K, L.params, v, q, &y_ss) == 0) && (y_ss >= thr_ss);
-    }
-    L.cand_ok[i] = ok;
-    L.cand_ss[i] = ok;
-    L.cand_dead[i] = ok ? 0 : 1;
-    L.cand_min[i] = dkey(inf_v<double>());
+  const double v = governed(s->v_prev, s->r, L.cand_kappa[i]);
+  L.cand_v[i] = v;
+  const CandK<double> C = cand_consts(L.params, v);
+  L.cand_k64[i] = C;
+  CandK<float> F;
+  F.W_o2 = static_cast<float>(C.W_o2);
+  F.V0 = static_cast<float>(C.V0);
+  F.y_scale = static_cast<float>(C.y_scale);
+  L.cand_k32[i] = F;
+  int ok = 1;
+  if (L.scfg.ss_check) {
+    double q[3], y_ss = 0.0;
+    ok = (equilibrium_dev(K, L.params, v, q, &y_ss) == 0) && (y_ss >= thr_ss);
   }
-  if (threadIdx.x == 0) *L.recheck_count = 0u;
+  L.cand_ok[i] = ok;
+  L.cand_ss[i] = ok;
+  L.cand_dead[i] = ok ? 0 : 1;
+  L.cand_min[i] = dkey(inf_v<double>());
+}
+
+// One block per candidate slot of the round the search kernel just set up;
+// block 0 also empties the recheck list.
+__global__ void __launch_bounds__(32) prepare_kernel(const Launch L) {
+  const SearchState* s = L.st;
+  if (threadIdx.x != 0) return;
+  if (blockIdx.x == 0) *L.recheck_count = 0u;
+  if (static_cast<int>(blockIdx.x) < s->prep_m) prepare_slot(L, s->prep_base + blockIdx.x);
+}
+
+cudaError_t launch_prepare(const Launch& L, int width) {
+  prepare_kernel<<<width > 0 ? width : 1, 32, 0, L.stream>>>(L);
+  return cudaGetLastError();
 }
 
 __device__ void write_result(SearchState* s, double* v_t, double* kappa, int32_t* flags) {
@@ -582,10 +700,10 @@ __device__ void write_result(SearchState* s, double* v_t, double* kappa, int32_t
   if (flags) *flags = s->flags;
 }
 
-__global__ void __launch_bounds__(kSearchThreads)
+__global__ void __launch_bounds__(32)
 search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double* __restrict__ d_r,
-                    const unsigned long long* t_dev, const double* __restrict__ d_v_prev) {
-  __shared__ int m_sh;
+                    const unsigned long long* t_dev, const double* __restrict__ d_v_prev,
+                    int pipeline) {
   SearchState* s = L.st;
   if (threadIdx.x == 0) {
     const double x0 = d_x[0], x1 = d_x[1], x2 = d_x[2];
@@ -600,38 +718,103 @@ search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double
     int m = first_round(s, L.scfg, L.cand_kappa);
     if (s->invalid) { s->done = 1; m = 0; }
     s->m = m;
-    m_sh = m;
+    if (pipeline && m > 0) {
+      save_walk_start(s);
+      s->probe = 1;
+      set_segments(s, SEG_PROBE, m, 0, SEG_FULL, 0, 0);
+    } else {
+      set_segments(s, SEG_FULL, m, 0, SEG_FULL, 0, 0);
+    }
+    s->prep_base = 0;
+    s->prep_m = m;
   }
-  __syncthreads();
-  prepare_candidates(L, m_sh);
 }
 
-__global__ void __launch_bounds__(kSearchThreads)
+// Between the probe of round 1 and the launch that finishes it: walk round
+// 1's tree with the provisional outcomes (a node is provisionally admissible
+// while none of its trajectories has violated yet), build round 2's tree
+// from where that walk ends (slots m_cap..), and let the next launch both
+// continue round 1 and run round 2.
+__global__ void __launch_bounds__(32)
+search_mid_kernel(const Launch L) {
+  SearchState* s = L.st;
+  if (threadIdx.x == 0) {
+    int m1 = 0;
+    if (s->probe && !s->done) {
+      const int m0 = s->m;
+      restore_walk_start(s);
+      uint32_t bits;
+      int len;
+      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len);
+      s->prov_bits = bits;
+      s->prov_len = len;
+      s->prov_done = s->done;
+      s->done = 0;
+      if (!s->prov_done) {
+        s->depth1 = choose_depth(s, L.scfg);
+        m1 = build_tree(s, s->slot_of_node1, L.cand_kappa, L.scfg.m_cap, s->depth1);
+      }
+      set_segments(s, SEG_CONTINUE, m0, 0, SEG_FULL, m1, L.scfg.m_cap);
+    }
+    s->prep_base = L.scfg.m_cap;
+    s->prep_m = m1;
+  }
+}
+
+__global__ void __launch_bounds__(32)
 search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
-  __shared__ int m_sh;
   SearchState* s = L.st;
   if (threadIdx.x == 0) {
     int m = 0;
-    if (!s->done) m = next_round(s, L.scfg, L.cand_kappa, L.cand_ok);
+    if (!s->done && s->probe) {
+      // validate the pipelined pair: walk round 1 again with the final
+      // outcomes; only if every decision matches the provisional walk does
+      // round 2's tree continue Alg. 1's path
+      s->probe = 0;
+      restore_walk_start(s);
+      uint32_t bits;
+      int len;
+      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len);
+      s->round += 1;
+      const bool same = bits == s->prov_bits && len == s->prov_len && s->done == s->prov_done;
+      if (same && !s->done) {
+        walk_tree(s, L.scfg, s->slot_of_node1, s->depth1, L.cand_ok, &bits, &len);
+        s->round += 1;
+      } else if (!same) {
+        L.stats->repairs += 1ull;
+      }
+      if (!s->done) {
+        s->depth = choose_depth(s, L.scfg);
+        m = build_tree(s, s->slot_of_node, L.cand_kappa, 0, s->depth);
+      }
+    } else if (!s->done) {
+      m = next_round(s, L.scfg, L.cand_kappa, L.cand_ok);
+    }
     if (s->done) {
       m = 0;
       write_result(s, v_t, kappa, flags);
     }
     s->m = m;
-    m_sh = m;
+    set_segments(s, SEG_FULL, m, 0, SEG_FULL, 0, 0);
+    s->prep_base = 0;
+    s->prep_m = m;
   }
-  __syncthreads();
-  if (m_sh > 0) prepare_candidates(L, m_sh);
 }
 
 cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
                                 const unsigned long long* t_dev, const double* d_v_prev) {
-  search_begin_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev);
+  const int pipeline = search_pipelined(L.scfg, L.H) ? 1 : 0;
+  search_begin_kernel<<<1, 32, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev, pipeline);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_search_mid(const Launch& L) {
+  search_mid_kernel<<<1, 32, 0, L.stream>>>(L);
   return cudaGetLastError();
 }
 
 cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa, int32_t* d_flags) {
-  search_next_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_v_t, d_kappa, d_flags);
+  search_next_kernel<<<1, 32, 0, L.stream>>>(L, d_v_t, d_kappa, d_flags);
   return cudaGetLastError();
 }
 
@@ -647,10 +830,12 @@ eval_prepare_kernel(const Launch L, const double* __restrict__ d_x, double v_pre
     s->m = m;
     s->done = 0;
     s->invalid = 0;
+    s->probe = 0;
+    set_segments(s, SEG_FULL, m, 0, SEG_FULL, 0, 0);
+    s->prep_base = 0;
+    s->prep_m = m;
   }
   for (int i = threadIdx.x; i < m; i += blockDim.x) L.cand_kappa[i] = d_kappas[i];
-  __syncthreads();
-  prepare_candidates(L, m);
 }
 
 __global__ void eval_finish_kernel(const Launch L, int m, uint8_t* adm, double* min_slack) {
@@ -768,6 +953,11 @@ int search_round_count(const SearchCfg& c) {
     ++rounds;
   }
   return rounds;
+}
+
+bool search_pipelined(const SearchCfg& c, int horizon) {
+  return c.search == RRG_SEARCH_SPEC_BISECT && c.probe_steps > 0 && c.probe_steps < horizon &&
+         search_round_count(c) >= 2;
 }
 
 int search_round_width(const SearchCfg& c, int round) {

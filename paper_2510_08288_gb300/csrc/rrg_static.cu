@@ -165,6 +165,7 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
   // the prepare kernel rewrites every per-candidate flag, key and the recheck
   // count, so nothing left in the scratch by an earlier call is read
   if (e == cudaSuccess) e = launch_eval_prepare(L, d_x_t, v_prev, r_t, d_kappas, m);
+  if (e == cudaSuccess) e = launch_prepare(L, m);
   if (e == cudaSuccess)
     e = launch_rollout(L, m, cfg->precision == RRG_FP64, cfg->early_exit,
                        cfg->precision == RRG_FP32_RECHECK);

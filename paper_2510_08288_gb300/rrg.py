@@ -37,7 +37,7 @@ class RrgConfig(ctypes.Structure):
         ("dt", _d), ("horizon", _i32), ("n_scenarios", _i32), ("max_candidates", _i32),
         ("n_bisect", _i32), ("n_rounds", _i32), ("search", _i32), ("precision", _i32),
         ("early_exit", _i32), ("ss_check", _i32), ("y_min", _d), ("eps_ss", _d), ("y_c", _d),
-        ("recheck_eps_rel", _d), ("dist_amp", _d * 3),
+        ("recheck_eps_rel", _d), ("dist_amp", _d * 3), ("probe_steps", _i32),
     ]
 
 
@@ -47,7 +47,7 @@ class RrgStats(ctypes.Structure):
     _fields_ = [
         ("launches", _u64), ("rollout_launches", _u64), ("lane_steps", _u64),
         ("lane_steps_fp64", _u64), ("rechecked", _u64), ("rounds", _u64),
-        ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64),
+        ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64), ("repairs", _u64),
     ]
 
 

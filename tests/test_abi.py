@@ -42,7 +42,7 @@ def test_binding_names_match_header():
 def test_config_struct_layout_matches_header():
     """The ctypes mirror has the size of the C struct (checked via offsets)."""
     from paper_2510_08288_gb300 import rrg as R
-    assert ctypes.sizeof(R.RrgConfig) == 8 + 9 * 4 + 4 + 4 * 8 + 3 * 8
+    assert ctypes.sizeof(R.RrgConfig) == 8 + 9 * 4 + 4 + 4 * 8 + 3 * 8 + 8
     assert R.RrgConfig.y_min.offset == 48
 
 

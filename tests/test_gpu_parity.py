@@ -360,3 +360,28 @@ def test_closed_loop_continuation_equals_one_run(R, orc, params):
         np.testing.assert_array_equal(a, b)
     vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 90.0, r_seq, 7, 3, amp, amp, search=0)
     np.testing.assert_array_equal(outs[0][1], ko)
+
+
+@pytest.mark.parametrize("probe", [0, 1, 8, 128, 499, 500])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_recheck"])
+def test_pipelined_spec_bisect_equals_bisect(R, orc, params, probe, prec):
+    """Pipelining the first two speculative-bisection rounds (round 2 built
+    from round 1's first `probe` steps) never changes the result: a wrong
+    provisional outcome is detected and round 2 redone.  probe = 1 forces
+    such repairs; probe >= H switches pipelining off."""
+    N, H = 48, 500
+    p = R.FP64 if prec == "fp64" else R.FP32_RECHECK
+    repairs = 0
+    for v_prev, r in ((100.0, 250.0), (100.0, 112.0), (220.0, 290.0), (180.0, 60.0)):
+        x_t = orc.equilibrium(params, v_prev)
+        d = orc.sample_disturbances(2, 1, N, H, inputs.DIST_AMP)
+        k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, v_prev, r, 12, d)
+        cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=p, max_candidates=64,
+                   probe_steps=probe, recheck_eps_rel=SLACK32_TOL / 1.9)
+        with R.Governor(params, cfg) as g:
+            g.sample_scenarios(2, 1)
+            v_t, kap, fl = g.step(x_t, r, v_prev)
+            repairs += g.stats()["repairs"]
+        assert kap == k_o and fl == f_o, (v_prev, r, kap, k_o)
+    if probe == 1:
+        assert repairs > 0
