@@ -251,25 +251,34 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
     CK(launch_search_mid(L));
     CK(launch_prepare(L, w1));
     h->launches += 2;
-    rc = enqueue_round_work(h, L, w0 + w1, h->cfg.early_exit);
+    // rows: the <= 11 path nodes of round 1 that continue, then round 2
+    rc = enqueue_round_work(h, L, (w0 < 11 ? w0 : 11) + w1, h->cfg.early_exit);
     if (rc != RRG_OK) return rc;
     CK(launch_search_next(L, d_vt, d_kappa, d_flags));
     h->launches++;
-    if (R > 1) {
-      CK(launch_prepare(L, w1));
-      h->launches++;
-    }
     h->rounds++;
-    r0 = 1;
+    // after a wrong provisional outcome the search resumes from the level
+    // where it went wrong; these rounds do nothing when it went right
+    const int extra = search_extra_rounds(c), wx = search_extra_width(c);
+    for (int r = 0; r < extra; ++r) {
+      CK(launch_prepare(L, wx));
+      h->launches++;
+      rc = enqueue_round_work(h, L, wx, h->cfg.early_exit);
+      if (rc != RRG_OK) return rc;
+      CK(launch_search_next(L, d_vt, d_kappa, d_flags));
+      h->launches++;
+      h->rounds++;
+    }
+    return RRG_OK;
   }
   for (int r = r0; r < R; ++r) {
-    const int width = pipe ? search_round_width(c, 1) : search_round_width(c, r);
+    const int width = search_round_width(c, r);
     int rc = enqueue_round_work(h, L, width, h->cfg.early_exit);
     if (rc != RRG_OK) return rc;
     CK(launch_search_next(L, d_vt, d_kappa, d_flags));
     h->launches++;
     if (r + 1 < R) {
-      CK(launch_prepare(L, pipe ? search_round_width(c, 1) : search_round_width(c, r + 1)));
+      CK(launch_prepare(L, search_round_width(c, r + 1)));
       h->launches++;
     }
     h->rounds++;

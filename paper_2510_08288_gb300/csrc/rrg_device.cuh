@@ -109,10 +109,19 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
   return o;
 }
 
-// a (2u - 1) with u the top 53 bits of w scaled to [0, 1).
+// a (2u - 1) with u the top 53 bits of w scaled to [0, 1).  2u - 1 equals
+// t 2^-52 exactly for the integer t = (w >> 11) - 2^52, and a 2^-52 is exact,
+// so (a 2^-52) t rounds the same real number once: one conversion and one
+// binary64 multiply instead of four operations on GB300's narrow FP64 pipe.
+// (For a below 2^-960, a 2^-52 would lose bits to underflow; such tiny
+// half-ranges take the four-operation form.)
 __device__ __forceinline__ double uniform_sym(uint64_t w, double a) {
-  const double u = __dmul_rn(static_cast<double>(w >> 11), 0x1.0p-53);
-  return __dmul_rn(a, __dsub_rn(__dmul_rn(2.0, u), 1.0));
+  if (a < 0x1.0p-960) {
+    const double u = __dmul_rn(static_cast<double>(w >> 11), 0x1.0p-53);
+    return __dmul_rn(a, __dsub_rn(__dmul_rn(2.0, u), 1.0));
+  }
+  const long long t = static_cast<long long>(w >> 11) - (1ll << 52);
+  return __dmul_rn(__ll2double_rn(t), __dmul_rn(a, 0x1.0p-52));
 }
 
 // ---------------------------------------------------------------------------

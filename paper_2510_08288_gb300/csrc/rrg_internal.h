@@ -26,7 +26,8 @@ constexpr int kMaxTreeNodes = 2 * RRG_MAX_CANDIDATES;
 enum SegMode : int32_t {
   SEG_FULL = 0,      // steps 0..H
   SEG_PROBE = 1,     // steps 0..probe_steps; survivors save their state
-  SEG_CONTINUE = 2,  // resume a probed trajectory at probe_steps, run to H
+  SEG_CONTINUE = 2,  // resume a probed trajectory at probe_steps, run to H;
+                     // row y continues slot cont_slot[y]
 };
 
 // A launch covers up to two slot ranges: blockIdx.y < seg[0].count maps to
@@ -70,6 +71,7 @@ struct SearchState {
   int32_t depth1;     // levels of the tree built from provisional outcomes
   int32_t prov_len, prov_done;
   uint32_t prov_bits;
+  int32_t cont_slot[16];  // the probed round's slots on the provisional path
   double w_lo, w_hi, w_kappa, w_kopt;  // search state before the probed round
   int32_t w_iter, w_any;
   int32_t slot_of_node[kMaxTreeNodes];   // bisection tree: heap node -> slot
@@ -174,5 +176,10 @@ int search_round_count(const SearchCfg& c);
 int search_round_width(const SearchCfg& c, int round);
 // True when the first two rounds are pipelined (probe + continue).
 bool search_pipelined(const SearchCfg& c, int horizon);
+// Standard rounds enqueued after a pipelined pair (enough to finish the
+// search from any level a wrong provisional outcome can send it back to),
+// and the candidate width they need.
+int search_extra_rounds(const SearchCfg& c);
+int search_extra_width(const SearchCfg& c);
 
 }  // namespace rrg

@@ -330,7 +330,7 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d,
   int mode, i;
   if (y < s0.count) {
     mode = s0.mode;
-    i = s0.base + y;
+    i = mode == SEG_CONTINUE ? L.st->cont_slot[y] : s0.base + y;
   } else if (y - s0.count < s1.count) {
     mode = s1.mode;
     i = s1.base + (y - s0.count);
@@ -537,18 +537,31 @@ __device__ int build_tree(const SearchState* s, int32_t* slot_map, double* cand_
 // Follows Alg. 1's path through an evaluated tree of `depth` levels, one
 // iteration per level; bit l of *bits is the outcome at level l, *len the
 // number of levels walked.
+// With `visited`, the slots of the path are recorded; with `expect`, the
+// walk stops right after the first level whose outcome differs from bit l of
+// *expect (*diverged is then set): beyond it the path leaves the nodes whose
+// outcomes are known.
 __device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* slot_map, int depth,
-                          const int32_t* cand_ok, uint32_t* bits, int* len) {
+                          const int32_t* cand_ok, uint32_t* bits, int* len,
+                          int32_t* visited = nullptr, const uint32_t* expect = nullptr,
+                          bool* diverged = nullptr) {
   int n = 1;
   uint32_t b = 0;
   int l = 0;
+  if (diverged) *diverged = false;
   for (int lev = 0; lev < depth; ++lev) {
     const int slot = slot_map[n];
     if (slot < 0) break;  // cannot happen: the path only visits valid nodes
+    if (visited) visited[lev] = slot;
     const double k = s->kappa;
     s->iter += 1;
     ++l;
-    if (cand_ok[slot]) {
+    const bool ok = cand_ok[slot] != 0;
+    if (expect && ok != (((*expect >> lev) & 1u) != 0)) {
+      *diverged = true;
+      depth = lev + 1;  // apply this level's decision, then stop
+    }
+    if (ok) {
       b |= 1u << lev;
       s->kappa_opt = k;
       s->any = 1;
@@ -742,10 +755,11 @@ search_mid_kernel(const Launch L) {
     int m1 = 0;
     if (s->probe && !s->done) {
       const int m0 = s->m;
+      (void)m0;
       restore_walk_start(s);
       uint32_t bits;
       int len;
-      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len);
+      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len, s->cont_slot);
       s->prov_bits = bits;
       s->prov_len = len;
       s->prov_done = s->done;
@@ -754,7 +768,9 @@ search_mid_kernel(const Launch L) {
         s->depth1 = choose_depth(s, L.scfg);
         m1 = build_tree(s, s->slot_of_node1, L.cand_kappa, L.scfg.m_cap, s->depth1);
       }
-      set_segments(s, SEG_CONTINUE, m0, 0, SEG_FULL, m1, L.scfg.m_cap);
+      // only the nodes on the provisional path are finished: no other node
+      // of round 1 can be read by a walk that agrees with the provisional one
+      set_segments(s, SEG_CONTINUE, len, 0, SEG_FULL, m1, L.scfg.m_cap);
     }
     s->prep_base = L.scfg.m_cap;
     s->prep_m = m1;
@@ -774,13 +790,15 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
       restore_walk_start(s);
       uint32_t bits;
       int len;
-      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len);
+      bool diverged = false;
+      const uint32_t expect = s->prov_bits;
+      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len, nullptr, &expect,
+                &diverged);
       s->round += 1;
-      const bool same = bits == s->prov_bits && len == s->prov_len && s->done == s->prov_done;
-      if (same && !s->done) {
+      if (!diverged && !s->done) {
         walk_tree(s, L.scfg, s->slot_of_node1, s->depth1, L.cand_ok, &bits, &len);
         s->round += 1;
-      } else if (!same) {
+      } else if (diverged) {
         L.stats->repairs += 1ull;
       }
       if (!s->done) {
@@ -958,6 +976,21 @@ int search_round_count(const SearchCfg& c) {
 bool search_pipelined(const SearchCfg& c, int horizon) {
   return c.search == RRG_SEARCH_SPEC_BISECT && c.probe_steps > 0 && c.probe_steps < horizon &&
          search_round_count(c) >= 2;
+}
+
+static int host_max_depth(const SearchCfg& c) {
+  int d = 1;
+  while (d + 1 <= 11 && host_tree_count(false, d + 1) <= c.m_cap) ++d;
+  return d;
+}
+
+int search_extra_rounds(const SearchCfg& c) {
+  const int d = host_max_depth(c);
+  return (c.n_bisect - 1 + d - 1) / d;
+}
+
+int search_extra_width(const SearchCfg& c) {
+  return host_tree_count(false, host_max_depth(c));
 }
 
 int search_round_width(const SearchCfg& c, int round) {
