@@ -9,6 +9,8 @@
 
 namespace rrg {
 
+constexpr int kPowDegree = 10;
+
 // ---------------------------------------------------------------------------
 // FC3 constants.  The state is kept in gauge coordinates
 //   q = [p_ca - p_atm, w_cp, p_sm - p_atm]
@@ -29,6 +31,10 @@ struct Fc3K {
   T RT_Vca;      // R_a T_st / V_ca
   T RT_Vsm;      // R_a T_st / V_sm
   T inv_J;       // 1 / J_cp
+  // binary32 path only: (1 + u)^e - 1 on [pw_lo, pw_hi] as a polynomial in
+  // z = (u - pw_mid) pw_inv_half (see pow_e_m1 below)
+  T pw_c[kPowDegree + 1];
+  T pw_mid, pw_inv_half, pw_lo, pw_hi;
 };
 
 // Per-candidate constants (functions of the governed setpoint v = I only).
@@ -39,9 +45,35 @@ struct CandK {
   T y_scale;  // x_O2 k_sm / W_o2: OER per pascal of p_sm - p_ca
 };
 
-template <typename T> __device__ __forceinline__ T pow_e(T x, T e);
-template <> __device__ __forceinline__ float pow_e<float>(float x, float e) { return __powf(x, e); }
-template <> __device__ __forceinline__ double pow_e<double>(double x, double e) { return pow(x, e); }
+// (1 + u)^e - 1, the compressor's isentropic temperature-ratio term.
+// binary64: pow.  binary32: inside [pw_lo, pw_hi] (the pressure range of
+// operation with margin) the degree-10 Chebyshev interpolant of the function
+// (interpolation at Chebyshev points of the first kind, converted to the
+// power basis once per handle on the host), evaluated by Estrin's scheme: its
+// dependency chain is five multiply-adds instead of two MUFU operations and a
+// multiply, and its error (interpolation 6e-10, binary32 evaluation ~3e-8)
+// is below __powf's.  Outside the interval it falls back to __powf.
+template <typename T> struct Fc3K;
+template <typename T>
+__device__ __forceinline__ T pow_e_m1(const Fc3K<T>& K, T u);
+
+template <>
+__device__ __forceinline__ double pow_e_m1<double>(const Fc3K<double>& K, double u) {
+  return pow(1.0 + u, K.e) - 1.0;
+}
+
+template <>
+__device__ __forceinline__ float pow_e_m1<float>(const Fc3K<float>& K, float u) {
+  if (!(u >= K.pw_lo && u <= K.pw_hi)) return __powf(1.0f + u, K.e) - 1.0f;
+  const float* c = K.pw_c;
+  const float z = (u - K.pw_mid) * K.pw_inv_half;
+  const float z2 = z * z, z4 = z2 * z2, z8 = z4 * z4;
+  const float p01 = fmaf(c[1], z, c[0]), p23 = fmaf(c[3], z, c[2]);
+  const float p45 = fmaf(c[5], z, c[4]), p67 = fmaf(c[7], z, c[6]);
+  const float p89 = fmaf(c[9], z, c[8]);
+  const float q0 = fmaf(p23, z2, p01), q1 = fmaf(p67, z2, p45), q2 = fmaf(c[10], z2, p89);
+  return fmaf(q2, z8, fmaf(q1, z4, q0));
+}
 
 template <typename T> __device__ __forceinline__ T div_fast(T a, T b);
 template <> __device__ __forceinline__ float div_fast<float>(float a, float b) { return __fdividef(a, b); }
@@ -57,7 +89,7 @@ __device__ __forceinline__ void fc3_rhs(const Fc3K<T>& K, const CandK<T>& C,
   const T W_cp = K.a_w * w - K.a_p * q_sm;
   const T W_sm = K.k_sm * (q_sm - q_ca);
   const T W_ca = K.k_ca * q_ca;
-  const T pr_e = pow_e<T>(T(1) + q_sm * K.inv_p_atm, K.e) - T(1);
+  const T pr_e = pow_e_m1<T>(K, q_sm * K.inv_p_atm);
   const T tau_cp = div_fast<T>(K.C_cp * pr_e * W_cp, w);
   const T tau_cm = K.C_m * ((C.V0 - K.K_p * W_cp) - K.k_v * w);
   d_ca = K.RT_Vca * (W_sm - W_ca - C.W_o2);
