@@ -9,8 +9,6 @@
 
 namespace rrg {
 
-constexpr int kPowDegree = 10;
-
 // ---------------------------------------------------------------------------
 // FC3 constants.  The state is kept in gauge coordinates
 //   q = [p_ca - p_atm, w_cp, p_sm - p_atm]
@@ -31,10 +29,6 @@ struct Fc3K {
   T RT_Vca;      // R_a T_st / V_ca
   T RT_Vsm;      // R_a T_st / V_sm
   T inv_J;       // 1 / J_cp
-  // binary32 path only: (1 + u)^e - 1 on [pw_lo, pw_hi] as a polynomial in
-  // z = (u - pw_mid) pw_inv_half (see pow_e_m1 below)
-  T pw_c[kPowDegree + 1];
-  T pw_mid, pw_inv_half, pw_lo, pw_hi;
 };
 
 // Per-candidate constants (functions of the governed setpoint v = I only).
@@ -45,14 +39,11 @@ struct CandK {
   T y_scale;  // x_O2 k_sm / W_o2: OER per pascal of p_sm - p_ca
 };
 
-// (1 + u)^e - 1, the compressor's isentropic temperature-ratio term.
-// binary64: pow.  binary32: inside [pw_lo, pw_hi] (the pressure range of
-// operation with margin) the degree-10 Chebyshev interpolant of the function
-// (interpolation at Chebyshev points of the first kind, converted to the
-// power basis once per handle on the host), evaluated by Estrin's scheme: its
-// dependency chain is five multiply-adds instead of two MUFU operations and a
-// multiply, and its error (interpolation 6e-10, binary32 evaluation ~3e-8)
-// is below __powf's.  Outside the interval it falls back to __powf.
+// (1 + u)^e - 1, the compressor's isentropic temperature-ratio term: pow in
+// binary64, the MUFU-based __powf in binary32.  (A degree-10 Chebyshev
+// interpolant evaluated by Estrin's scheme was measured slower on GB300: a
+// warp running one trajectory is issue-bound, and the polynomial costs more
+// instructions than the two MUFU operations it would replace.)
 template <typename T> struct Fc3K;
 template <typename T>
 __device__ __forceinline__ T pow_e_m1(const Fc3K<T>& K, T u);
@@ -64,15 +55,7 @@ __device__ __forceinline__ double pow_e_m1<double>(const Fc3K<double>& K, double
 
 template <>
 __device__ __forceinline__ float pow_e_m1<float>(const Fc3K<float>& K, float u) {
-  if (!(u >= K.pw_lo && u <= K.pw_hi)) return __powf(1.0f + u, K.e) - 1.0f;
-  const float* c = K.pw_c;
-  const float z = (u - K.pw_mid) * K.pw_inv_half;
-  const float z2 = z * z, z4 = z2 * z2, z8 = z4 * z4;
-  const float p01 = fmaf(c[1], z, c[0]), p23 = fmaf(c[3], z, c[2]);
-  const float p45 = fmaf(c[5], z, c[4]), p67 = fmaf(c[7], z, c[6]);
-  const float p89 = fmaf(c[9], z, c[8]);
-  const float q0 = fmaf(p23, z2, p01), q1 = fmaf(p67, z2, p45), q2 = fmaf(c[10], z2, p89);
-  return fmaf(q2, z8, fmaf(q1, z4, q0));
+  return __powf(1.0f + u, K.e) - 1.0f;
 }
 
 template <typename T> __device__ __forceinline__ T div_fast(T a, T b);

@@ -38,37 +38,6 @@ template <> __device__ __forceinline__ double inf_v<double>() { return __longlon
 // ---------------------------------------------------------------------------
 // Constant folding (once per handle, on the host; no fused multiply-add can
 // occur in these products and quotients, so host and device would agree).
-// Chebyshev interpolant of (1 + u)^e - 1 on [lo, hi] at the n + 1 Chebyshev
-// points of the first kind, x_k = cos(pi (k + 1/2) / (n + 1)), as power-basis
-// coefficients of z = (u - mid) / half: the discrete Chebyshev transform
-// gives the Chebyshev coefficients, the recurrence T_{j+1} = 2 z T_j - T_{j-1}
-// expands them.
-static void chebyshev_pow_m1(double e, double lo, double hi, double* mono) {
-  const int n = kPowDegree;
-  const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
-  const double pi = 3.14159265358979323846;
-  double y[kPowDegree + 1], xk[kPowDegree + 1], cheb[kPowDegree + 1];
-  for (int k = 0; k <= n; ++k) {
-    xk[k] = std::cos(pi * (k + 0.5) / (n + 1));
-    y[k] = std::pow(1.0 + mid + half * xk[k], e) - 1.0;
-  }
-  for (int j = 0; j <= n; ++j) {
-    double acc = 0.0;
-    for (int k = 0; k <= n; ++k) acc += y[k] * std::cos(j * pi * (k + 0.5) / (n + 1));
-    cheb[j] = (j == 0 ? 1.0 : 2.0) * acc / (n + 1);
-  }
-  double Tm[kPowDegree + 1] = {0}, T0[kPowDegree + 1] = {0}, T1[kPowDegree + 1] = {0};
-  for (int i = 0; i <= n; ++i) mono[i] = 0.0;
-  T0[0] = 1.0;             // T_0 = 1
-  T1[1] = 1.0;             // T_1 = z
-  for (int i = 0; i <= n; ++i) mono[i] += cheb[0] * T0[i] + cheb[1] * T1[i];
-  for (int j = 2; j <= n; ++j) {
-    for (int i = 0; i <= n; ++i) Tm[i] = -T0[i] + (i > 0 ? 2.0 * T1[i - 1] : 0.0);
-    for (int i = 0; i <= n; ++i) mono[i] += cheb[j] * Tm[i];
-    for (int i = 0; i <= n; ++i) { T0[i] = T1[i]; T1[i] = Tm[i]; }
-  }
-}
-
 void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32) {
   Fc3K<double> K{};
   K.inv_p_atm = 1.0 / P[P_P_ATM];
@@ -84,23 +53,8 @@ void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32) {
   K.RT_Vca = P[P_R_A] * P[P_T_ST] / P[P_V_CA];
   K.RT_Vsm = P[P_R_A] * P[P_T_ST] / P[P_V_SM];
   K.inv_J = 1.0 / P[P_J_CP];
-  // gauge supply-manifold pressure over p_atm spans about [0, 0.77] in
-  // operation (states within 10 % of any equilibrium from 50 to 300 A)
-  const double lo = -0.1, hi = 1.0;
-  double mono[kPowDegree + 1];
-  chebyshev_pow_m1(K.e, lo, hi, mono);
-  for (int i = 0; i <= kPowDegree; ++i) K.pw_c[i] = mono[i];
-  K.pw_mid = 0.5 * (lo + hi);
-  K.pw_inv_half = 2.0 / (hi - lo);
-  K.pw_lo = lo;
-  K.pw_hi = hi;
   *k64 = K;
   Fc3K<float> F{};
-  for (int i = 0; i <= kPowDegree; ++i) F.pw_c[i] = static_cast<float>(mono[i]);
-  F.pw_mid = static_cast<float>(K.pw_mid);
-  F.pw_inv_half = static_cast<float>(K.pw_inv_half);
-  F.pw_lo = static_cast<float>(lo);
-  F.pw_hi = static_cast<float>(hi);
   F.inv_p_atm = static_cast<float>(K.inv_p_atm);
   F.a_w = static_cast<float>(K.a_w);
   F.a_p = static_cast<float>(K.a_p);
@@ -136,50 +90,64 @@ __device__ __forceinline__ CandK<double> cand_consts(const double* __restrict__ 
 // a secant iteration started there converges in a handful of binary64
 // evaluations; every iterate is kept inside a sign-change bracket and a
 // step that leaves it is replaced by bisection.
-__device__ double eq_torque(const Fc3K<double>& K, const double* __restrict__ P,
-                            const CandK<double>& C, double W, double q[3]) {
-  q[0] = (W - C.W_o2) / P[P_K_CA];
-  q[2] = q[0] + W / P[P_K_SM];
-  q[1] = (W + P[P_A_P] * q[2]) / P[P_A_W];
-  double a, b, c;
-  fc3_rhs<double>(K, C, q[0], q[1], q[2], a, b, c);
+template <typename T>
+__device__ T eq_torque(const Fc3K<T>& K, const CandK<T>& C, T inv_k_ca, T inv_k_sm, T a_p,
+                       T inv_a_w, T W, T q[3]) {
+  q[0] = (W - C.W_o2) * inv_k_ca;
+  q[2] = q[0] + W * inv_k_sm;
+  q[1] = (W + a_p * q[2]) * inv_a_w;
+  T a, b, c;
+  fc3_rhs<T>(K, C, q[0], q[1], q[2], a, b, c);
   return b;
 }
 
-__device__ int equilibrium_dev(const Fc3K<double>& K, const double* __restrict__ P, double I,
-                               double q[3], double* y_ss) {
+template <typename T> __device__ __forceinline__ T eq_tol();
+template <> __device__ __forceinline__ double eq_tol<double>() { return 1e-15; }
+template <> __device__ __forceinline__ float eq_tol<float>() { return 2e-7f; }
+
+// Returns 0 and the gauge state q, output *y_ss at the equilibrium, or < 0.
+template <typename T>
+__device__ int equilibrium_dev(const Fc3K<T>& K, const double* __restrict__ P, double I, T q[3],
+                               T* y_ss) {
   if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
-  const CandK<double> C = cand_consts(P, I);
-  double lo = C.W_o2;
-  if (!(eq_torque(K, P, C, lo, q) > 0.0)) return -2;
-  double hi = DBL_MAX;
+  const CandK<double> Cd = cand_consts(P, I);
+  CandK<T> C;
+  C.W_o2 = static_cast<T>(Cd.W_o2);
+  C.V0 = static_cast<T>(Cd.V0);
+  C.y_scale = static_cast<T>(Cd.y_scale);
+  const T ikca = static_cast<T>(1.0 / P[P_K_CA]), iksm = static_cast<T>(1.0 / P[P_K_SM]);
+  const T a_p = static_cast<T>(P[P_A_P]), iaw = static_cast<T>(1.0 / P[P_A_W]);
+  const T big = static_cast<T>(1e30);
+  T lo = C.W_o2;
+  if (!(eq_torque<T>(K, C, ikca, iksm, a_p, iaw, lo, q) > T(0))) return -2;
+  T hi = big;
   // two starting points around the target flow
-  double x0 = P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
-  double g0 = eq_torque(K, P, C, x0, q);
-  if (g0 > 0.0) lo = x0; else hi = x0;
-  double x1 = x0 * (g0 > 0.0 ? 1.001 : 0.999);
-  double g1 = eq_torque(K, P, C, x1, q);
-  if (g1 > 0.0) { if (x1 > lo) lo = x1; } else if (x1 < hi) hi = x1;
+  T x0 = static_cast<T>(P[P_LAM_REF] * Cd.W_o2 / P[P_X_O2]);
+  T g0 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x0, q);
+  if (g0 > T(0)) lo = x0; else hi = x0;
+  T x1 = x0 * (g0 > T(0) ? T(1.001) : T(0.999));
+  T g1 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x1, q);
+  if (g1 > T(0)) { if (x1 > lo) lo = x1; } else if (x1 < hi) hi = x1;
   // make sure the bracket is closed before bisection can be needed
-  for (int it = 0; it < 60 && hi == DBL_MAX; ++it) {
-    const double xt = 2.0 * lo;
-    if (eq_torque(K, P, C, xt, q) > 0.0) lo = xt; else hi = xt;
+  for (int it = 0; it < 60 && hi == big; ++it) {
+    const T xt = T(2) * lo;
+    if (eq_torque<T>(K, C, ikca, iksm, a_p, iaw, xt, q) > T(0)) lo = xt; else hi = xt;
   }
-  if (hi == DBL_MAX) return -2;
-  double W = x1;
+  if (hi == big) return -2;
+  T W = x1;
   for (int it = 0; it < 100; ++it) {
-    double x2 = x1 - g1 * (x1 - x0) / (g1 - g0);
-    if (!(x2 > lo && x2 < hi)) x2 = 0.5 * (lo + hi);
-    const double g2 = eq_torque(K, P, C, x2, q);
+    T x2 = x1 - g1 * (x1 - x0) / (g1 - g0);
+    if (!(x2 > lo && x2 < hi)) x2 = T(0.5) * (lo + hi);
+    const T g2 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x2, q);
     W = x2;
-    if (g2 == 0.0) break;
-    if (g2 > 0.0) lo = x2; else hi = x2;
-    if (fabs(x2 - x1) <= 1e-15 * x2 || hi - lo <= 4e-16 * hi) break;
+    if (g2 == T(0)) break;
+    if (g2 > T(0)) lo = x2; else hi = x2;
+    if (fabs(x2 - x1) <= eq_tol<T>() * x2 || hi - lo <= T(0.4) * eq_tol<T>() * hi) break;
     x0 = x1; g0 = g1;
     x1 = x2; g1 = g2;
   }
-  eq_torque(K, P, C, W, q);
-  *y_ss = fc3_output<double>(C, q[0], q[2]);
+  eq_torque<T>(K, C, ikca, iksm, a_p, iaw, W, q);
+  *y_ss = fc3_output<T>(C, q[0], q[2]);
   return 0;
 }
 
@@ -187,7 +155,7 @@ __global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<doub
                                    double v, double* out4, int32_t* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double q[3], y = 0.0;
-  const int rc = equilibrium_dev(k64, P, v, q, &y);
+  const int rc = equilibrium_dev<double>(k64, P, v, q, &y);
   out4[0] = q[0] + P[P_P_ATM];
   out4[1] = q[1];
   out4[2] = q[2] + P[P_P_ATM];
@@ -563,34 +531,54 @@ __device__ int choose_depth(const SearchState* s, const SearchCfg& c) {
   return d;
 }
 
-// Puts the valid nodes of the depth-`depth` tree into slots base, base+1, ...
-// (kappas in cand_kappa[slot]); slot_map[node] = slot or -1.  Returns the count.
-__device__ int build_tree(const SearchState* s, int32_t* slot_map, double* cand_kappa, int base,
-                          int depth) {
-  int count = 0;
-  const int nodes = 1 << depth;
-  for (int n = 1; n < nodes; ++n) {
+// Tree construction is split: the deciding thread records what to build
+// (build_tree returns the node count, known in closed form) and, after a
+// barrier, the whole block writes the nodes (build_tree_block), one node per
+// thread: each node's kappa is a short chain of binary64 operations and
+// GB300's binary64 latency makes a serial loop over up to 2,047 nodes slow.
+struct TreeReq {
+  int pending, which, base, depth;
+  double lo, hi, kappa;
+};
+__shared__ TreeReq g_tree_req;
+
+__device__ int build_tree(const SearchState* s, int which, int base, int depth) {
+  g_tree_req.pending = 1;
+  g_tree_req.which = which;
+  g_tree_req.base = base;
+  g_tree_req.depth = depth;
+  g_tree_req.lo = s->lo;
+  g_tree_req.hi = s->hi;
+  g_tree_req.kappa = s->kappa;
+  return tree_count(s->kappa == 1.0, depth);
+}
+
+// Heap node n of the requested tree goes to slot base + (its rank among the
+// valid nodes in heap order): with a kappa = 1 root the valid nodes are the
+// root and its left subtree, so level L >= 1 starts at rank 2^(L-1).
+__device__ void build_tree_block(const Launch& L) {
+  const TreeReq r = g_tree_req;
+  if (!r.pending) return;
+  int32_t* map = r.which ? L.st->slot_of_node1 : L.st->slot_of_node;
+  const bool one = r.kappa == 1.0;
+  const int nodes = 1 << r.depth;
+  for (int n = threadIdx.x + 1; n < nodes; n += blockDim.x) {
     const int lev = 31 - __clz(n);
-    double lo = s->lo, hi = s->hi, k = s->kappa;
-    bool valid = true;
+    const int off = n - (1 << lev);
+    const bool valid = !one || lev == 0 || off < (1 << (lev - 1));
+    if (!valid) {
+      map[n] = -1;
+      continue;
+    }
+    double lo = r.lo, hi = r.hi, k = r.kappa;
     for (int b = lev - 1; b >= 0; --b) {
-      if ((n >> b) & 1) {
-        if (k == 1.0) { valid = false; break; }
-        lo = k;
-      } else {
-        hi = k;
-      }
+      if ((n >> b) & 1) lo = k; else hi = k;
       k = __dmul_rn(__dadd_rn(lo, hi), 0.5);
     }
-    if (valid) {
-      slot_map[n] = base + count;
-      cand_kappa[base + count] = k;
-      ++count;
-    } else {
-      slot_map[n] = -1;
-    }
+    const int rank = !one ? n - 1 : (lev == 0 ? 0 : (1 << (lev - 1)) + off);
+    map[n] = r.base + rank;
+    L.cand_kappa[r.base + rank] = k;
   }
-  return count;
 }
 
 // Follows Alg. 1's path through an evaluated tree of `depth` levels, one
@@ -675,7 +663,7 @@ __device__ int first_round(SearchState* s, const SearchCfg& c, double* cand_kapp
   if (c.search == RRG_SEARCH_GRID || c.search == RRG_SEARCH_KSECTION)
     return grid_points(cand_kappa, c.m_cap);
   s->depth = choose_depth(s, c);
-  return build_tree(s, s->slot_of_node, cand_kappa, 0, s->depth);
+  return build_tree(s, 0, 0, s->depth);
 }
 
 // Decides from the evaluated round and prepares the next; returns next m.
@@ -689,7 +677,7 @@ __device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa
     s->round += 1;
     if (s->done) return 0;
     s->depth = choose_depth(s, c);
-    return build_tree(s, s->slot_of_node, cand_kappa, 0, s->depth);
+    return build_tree(s, 0, 0, s->depth);
   }
   int best = -1;
   for (int i = 0; i < m; ++i)
@@ -738,8 +726,16 @@ __device__ void prepare_slot(const Launch& L, int i) {
   L.cand_k32[i] = F;
   int ok = 1;
   if (L.scfg.ss_check) {
-    double q[3], y_ss = 0.0;
-    ok = (equilibrium_dev(K, L.params, v, q, &y_ss) == 0) && (y_ss >= thr_ss);
+    // binary32 solve first; it decides unless y_ss lands within 1e-4 of the
+    // threshold (its error is ~1e-6), in which case binary64 decides
+    float q32[3], y32 = 0.0f;
+    const int rc32 = equilibrium_dev<float>(L.k32, L.params, v, q32, &y32);
+    if (rc32 == 0 && fabs(static_cast<double>(y32) - thr_ss) > 1e-4 * (1.0 + fabs(thr_ss))) {
+      ok = static_cast<double>(y32) >= thr_ss;
+    } else {
+      double q[3], y_ss = 0.0;
+      ok = (equilibrium_dev<double>(K, L.params, v, q, &y_ss) == 0) && (y_ss >= thr_ss);
+    }
   }
   L.cand_ok[i] = ok;
   L.cand_ss[i] = ok;
@@ -772,11 +768,13 @@ __device__ void write_result(SearchState* s, double* v_t, double* kappa, int32_t
   if (flags) *flags = s->flags;
 }
 
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kSearchThreads)
 search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double* __restrict__ d_r,
                     const unsigned long long* t_dev, const double* __restrict__ d_v_prev,
                     int pipeline) {
   SearchState* s = L.st;
+  if (threadIdx.x == 0) g_tree_req.pending = 0;
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double x0 = d_x[0], x1 = d_x[1], x2 = d_x[2];
     const double r = d_r[t_dev ? *t_dev : 0ull];
@@ -800,6 +798,8 @@ search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double
     s->prep_base = 0;
     s->prep_m = m;
   }
+  __syncthreads();
+  build_tree_block(L);
 }
 
 // Between the probe of round 1 and the launch that finishes it: walk round
@@ -807,9 +807,11 @@ search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double
 // while none of its trajectories has violated yet), build round 2's tree
 // from where that walk ends (slots m_cap..), and let the next launch both
 // continue round 1 and run round 2.
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kSearchThreads)
 search_mid_kernel(const Launch L) {
   SearchState* s = L.st;
+  if (threadIdx.x == 0) g_tree_req.pending = 0;
+  __syncthreads();
   if (threadIdx.x == 0) {
     int m1 = 0;
     if (s->probe && !s->done) {
@@ -825,7 +827,7 @@ search_mid_kernel(const Launch L) {
       s->done = 0;
       if (!s->prov_done) {
         s->depth1 = choose_depth(s, L.scfg);
-        m1 = build_tree(s, s->slot_of_node1, L.cand_kappa, L.scfg.m_cap, s->depth1);
+        m1 = build_tree(s, 1, L.scfg.m_cap, s->depth1);
       }
       // only the nodes on the provisional path are finished: no other node
       // of round 1 can be read by a walk that agrees with the provisional one
@@ -834,11 +836,15 @@ search_mid_kernel(const Launch L) {
     s->prep_base = L.scfg.m_cap;
     s->prep_m = m1;
   }
+  __syncthreads();
+  build_tree_block(L);
 }
 
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kSearchThreads)
 search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
   SearchState* s = L.st;
+  if (threadIdx.x == 0) g_tree_req.pending = 0;
+  __syncthreads();
   if (threadIdx.x == 0) {
     int m = 0;
     if (!s->done && s->probe) {
@@ -862,7 +868,7 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
       }
       if (!s->done) {
         s->depth = choose_depth(s, L.scfg);
-        m = build_tree(s, s->slot_of_node, L.cand_kappa, 0, s->depth);
+        m = build_tree(s, 0, 0, s->depth);
       }
     } else if (!s->done) {
       m = next_round(s, L.scfg, L.cand_kappa, L.cand_ok);
@@ -876,22 +882,24 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
     s->prep_base = 0;
     s->prep_m = m;
   }
+  __syncthreads();
+  build_tree_block(L);
 }
 
 cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
                                 const unsigned long long* t_dev, const double* d_v_prev) {
   const int pipeline = search_pipelined(L.scfg, L.H) ? 1 : 0;
-  search_begin_kernel<<<1, 32, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev, pipeline);
+  search_begin_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev, pipeline);
   return cudaGetLastError();
 }
 
 cudaError_t launch_search_mid(const Launch& L) {
-  search_mid_kernel<<<1, 32, 0, L.stream>>>(L);
+  search_mid_kernel<<<1, kSearchThreads, 0, L.stream>>>(L);
   return cudaGetLastError();
 }
 
 cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa, int32_t* d_flags) {
-  search_next_kernel<<<1, 32, 0, L.stream>>>(L, d_v_t, d_kappa, d_flags);
+  search_next_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_v_t, d_kappa, d_flags);
   return cudaGetLastError();
 }
 
