@@ -281,6 +281,25 @@ def run_gpu(args):
         t = torch.tensor([total_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
+    # the same K updates again through the cached one-update CUDA graph (the
+    # library's closed-loop replay mode), on a fresh handle from the same start
+    gg = R.Governor(p, cfg, stream)
+    gd_v, gd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
+    gd_f, gd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
+    R.rrg_closed_loop_dev(gg.h, x0, V0, d_r, W, seed, 0, amp, True, gd_v, gd_k, gd_f, gd_x)
+    gevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(float(i))
+            gevs[i][0].record(stream)
+            R.rrg_closed_loop_dev(gg.h, None, 0.0, d_r, 1, seed, 0, amp, True, gd_v, gd_k, gd_f, gd_x)
+            gevs[i][1].record(stream)
+    torch.cuda.synchronize()
+    graph_s = sum(a.elapsed_time(b) for a, b in gevs) / 1e3
+    graph_same = bool(torch.equal(gd_k, d_k))
+    gg.close()
+
     kap_dev = d_k.cpu().numpy()
     flags_dev = d_f.cpu().numpy()
     x_dev = d_x.cpu().numpy().reshape(T + 1, 3)
@@ -351,6 +370,8 @@ def run_gpu(args):
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "graph_replay": {"value": world * K / graph_s, "unit": UNIT, "ms_per_step": 1e3 * graph_s / K,
+                             "kappa_equal_to_direct_launches": graph_same},
             "gpu_launches": st["launches"],
             "clocks": clk,
             "fp64_bisect_gpu": fp64,

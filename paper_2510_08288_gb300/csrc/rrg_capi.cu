@@ -30,6 +30,18 @@ struct rrg_ctx {
   double* params_dev = nullptr;
   double* d64 = nullptr;
   float* d32 = nullptr;
+  double* d64b = nullptr;       // second scenario pair, allocated by the first closed loop
+  float* d32b = nullptr;
+  cudaStream_t side = nullptr;  // samples update t+1 while update t runs
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool cl_next_ready = false;   // the closed loop's next update is already sampled
+  uint64_t cl_seed = 0, cl_t0 = 0;
+  // the captured one-update graph of the last closed loop, reused while the
+  // run's pointers and indices stay the same
+  cudaGraphExec_t cl_exec = nullptr;
+  const void* cl_key[6] = {};
+  uint64_t cl_key_seed = 0, cl_key_t0 = 0;
+  uint64_t cl_per = 0, cl_rl_per = 0, cl_rd_per = 0;
   SearchState* st = nullptr;
   double* cand_kappa = nullptr;
   double* cand_v = nullptr;
@@ -139,7 +151,7 @@ cudaError_t dalloc(T** p, size_t n) {
 }
 
 void free_all(rrg_ctx* h) {
-  void* ptrs[] = {h->params_dev, h->d64, h->d32, h->st, h->cand_kappa,
+  void* ptrs[] = {h->params_dev, h->d64, h->d32, h->d64b, h->d32b, h->st, h->cand_kappa,
                   h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state};
@@ -150,6 +162,10 @@ void free_all(rrg_ctx* h) {
   for (auto& e : h->ev_free) cudaEventDestroy(e);
   for (auto& pr : h->ev_roll) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto& pr : h->ev_rec) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (h->cl_exec) cudaGraphExecDestroy(h->cl_exec);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -233,11 +249,11 @@ int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit, b
 // launch sets up; the host only enqueues the fixed sequence.
 int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
                    const unsigned long long* t_dev, const double* d_vp, double* d_vt,
-                   double* d_kappa, int32_t* d_flags) {
+                   double* d_kappa, int32_t* d_flags, long long buf_base = -1) {
   const Launch& L = h->L;
   const SearchCfg& c = h->scfg;
   const int R = search_round_count(c);
-  CK(launch_search_begin(L, d_x, d_r, t_dev, d_vp));
+  CK(launch_search_begin(L, d_x, d_r, t_dev, d_vp, buf_base));
   CK(launch_prepare(L, search_round_width(c, 0)));
   h->launches += 2;
   int r0 = 0;
@@ -569,25 +585,53 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
   if ((x0 && (!x_ok(x0) || !is_fin(v0) || !(v0 > 0.0))) || !x_ok(plant_amp) || !d_r_seq || T < 0)
     return set_err(h, RRG_EINVAL, "x0, v0, plant_amp must be finite, v0 > 0, T >= 0, r_seq non-NULL");
   DeviceGuard g(h->device);
+  // the second scenario pair and the side stream, on first use
+  if (!h->d64b) {
+    const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->d64b), n * sizeof(double)));
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->d32b), n * sizeof(float)));
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    h->L.d64b = h->d64b;
+    h->L.d32b = h->d32b;
+  }
   std::memcpy(h->io_h + IO_AMP, plant_amp, 3 * sizeof(double));
   CK(cudaMemcpyAsync(h->io_dev + IO_AMP, h->io_h + IO_AMP, 3 * sizeof(double),
                      cudaMemcpyHostToDevice, h->stream));
   if (x0) {
     CK(launch_loop_init(h->L, h->loop, x0, v0, d_x_out));
     h->launches++;
+    h->cl_next_ready = false;
   }
   if (T == 0) return RRG_OK;
   const double* amp = h->io_dev + IO_AMP;
+  const Launch& L = h->L;
+  // scenarios of the first update of this call, unless the previous call of
+  // the same run already drew them
+  if (!(h->cl_next_ready && h->cl_seed == seed && h->cl_t0 == t0)) {
+    CK(launch_sample(L, seed, t0, &h->loop->t, h->cfg.dist_amp, true));
+    h->launches++;
+  }
+  // one update: draw update t+1 on the side stream (into the other pair)
+  // while update t searches and moves the plant on the main stream
   auto enqueue_update = [&]() -> int {
-    CK(launch_sample(h->L, seed, t0, &h->loop->t, h->cfg.dist_amp));
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    CK(launch_sample(L, seed, t0 + 1, &h->loop->t, h->cfg.dist_amp, true, h->side));
+    CK(cudaEventRecord(h->ev_join, h->side));
     h->launches++;
     int rc = enqueue_search(h, h->loop->x, d_r_seq, &h->loop->t, &h->loop->v_prev, nullptr,
-                            nullptr, nullptr);
+                            nullptr, nullptr, static_cast<long long>(t0));
     if (rc != RRG_OK) return rc;
-    CK(launch_loop_end(h->L, h->loop, seed, t0, amp, d_v_out, d_kappa_out, d_flags_out, d_x_out));
+    CK(launch_loop_end(L, h->loop, seed, t0, amp, d_v_out, d_kappa_out, d_flags_out, d_x_out));
     h->launches++;
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     return RRG_OK;
   };
+  h->cl_seed = seed;
+  h->cl_t0 = t0;
+  h->cl_next_ready = true;
   if (!use_graph) {
     for (int t = 0; t < T; ++t) {
       int rc = enqueue_update();
@@ -596,34 +640,48 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
     return RRG_OK;
   }
   // Capture one update and replay it T times; the update index lives on the
-  // device (loop->t), so every replay works on the next time step.
-  const uint64_t launches0 = h->launches, rl0 = h->rollout_launches, rounds0 = h->rounds;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  h->capturing = true;
-  int rc = enqueue_update();
-  h->capturing = false;
-  cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
-  if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-  if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-  const uint64_t per = h->launches - launches0, rl_per = h->rollout_launches - rl0,
-                 rd_per = h->rounds - rounds0;
-  h->launches = launches0;
-  h->rollout_launches = rl0;
-  h->rounds = rounds0;
-  for (int t = 0; t < T; ++t) {
-    ce = cudaGraphLaunch(exec, h->stream);
-    if (ce != cudaSuccess) break;
-    h->launches += per;
-    h->rollout_launches += rl_per;
-    h->rounds += rd_per;
+  // device (loop->t), so every replay works on the next time step.  The
+  // instantiated graph is kept for later calls of the same run.
+  const void* key[6] = {d_r_seq, d_v_out, d_kappa_out, d_flags_out, d_x_out, h->loop};
+  const bool hit = h->cl_exec != nullptr && std::memcmp(key, h->cl_key, sizeof key) == 0 &&
+                   h->cl_key_seed == seed && h->cl_key_t0 == t0;
+  if (!hit) {
+    if (h->cl_exec) {
+      cudaGraphExecDestroy(h->cl_exec);
+      h->cl_exec = nullptr;
+    }
+    const uint64_t launches0 = h->launches, rl0 = h->rollout_launches, rounds0 = h->rounds;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    int rc = enqueue_update();
+    h->capturing = false;
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&h->cl_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      h->cl_exec = nullptr;
+      return set_err(h, RRG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    }
+    h->cl_per = h->launches - launches0;
+    h->cl_rl_per = h->rollout_launches - rl0;
+    h->cl_rd_per = h->rounds - rounds0;
+    h->launches = launches0;
+    h->rollout_launches = rl0;
+    h->rounds = rounds0;
+    std::memcpy(h->cl_key, key, sizeof key);
+    h->cl_key_seed = seed;
+    h->cl_key_t0 = t0;
   }
-  cudaGraphExecDestroy(exec);
-  if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+  for (int t = 0; t < T; ++t) {
+    const cudaError_t ce = cudaGraphLaunch(h->cl_exec, h->stream);
+    if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+    h->launches += h->cl_per;
+    h->rollout_launches += h->cl_rl_per;
+    h->rounds += h->cl_rd_per;
+  }
   return RRG_OK;
 }
 

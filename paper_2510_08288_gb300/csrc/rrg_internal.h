@@ -61,6 +61,7 @@ struct SearchState {
   int32_t round;      // rounds finished
   int32_t invalid;    // inputs rejected on the device
   double v_t_out;     // governed reference of the finished search
+  int32_t buf;        // scenario pair of the current update (0: d64/d32, 1: d64b/d32b)
   Seg seg[2];         // what the next rollout launch runs
   int32_t prep_base;  // slots the next prepare launch fills: prep_base ..
   int32_t prep_m;     //   prep_base + prep_m - 1
@@ -115,6 +116,8 @@ struct Launch {
   Fc3K<float> k32;
   double* d64;                  // scenarios [3][H][N]
   float* d32;
+  double* d64b;                 // second pair for closed loops (sampling of update t+1
+  float* d32b;                  //   overlaps update t), or nullptr
   SearchState* st;
   double* cand_kappa;
   double* cand_v;
@@ -138,11 +141,16 @@ struct Launch {
 void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32);
 
 // ---- kernel launchers (rrg_kernels.cu) --------------------------------
+// dual: write the pair (base + *t_dev) & 1 (closed loops with two pairs)
 cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
-                          const unsigned long long* t_dev, const double* amp);
+                          const unsigned long long* t_dev, const double* amp, bool dual = false,
+                          cudaStream_t stream = nullptr);
 cudaError_t launch_round_scenarios(const Launch& L);
+// buf_base >= 0: the update index is buf_base + *t_dev and selects the
+// scenario pair by its parity; otherwise pair 0
 cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
-                                const unsigned long long* t_dev, const double* d_v_prev);
+                                const unsigned long long* t_dev, const double* d_v_prev,
+                                long long buf_base = -1);
 cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa,
                                int32_t* d_flags);
 cudaError_t launch_search_mid(const Launch& L);

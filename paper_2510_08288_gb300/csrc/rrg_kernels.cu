@@ -170,10 +170,15 @@ cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_
 
 // ---------------------------------------------------------------------------
 // Scenario sampling: one thread per (j, k), coalesced over k.
-__global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32, int N, int H,
+__global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
+                              double* __restrict__ d64b, float* __restrict__ d32b, int N, int H,
                               uint64_t seed, uint64_t base, const unsigned long long* t_dev,
                               double a0, double a1, double a2) {
   const uint64_t upd = base + (t_dev ? *t_dev : 0ull);
+  if (d64b != nullptr && (upd & 1ull)) {
+    d64 = d64b;
+    d32 = d32b;
+  }
   const size_t HN = static_cast<size_t>(H) * N;
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
@@ -199,10 +204,12 @@ static int grid_for(size_t n, int threads, int cap) {
 }
 
 cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
-                          const unsigned long long* t_dev, const double* amp) {
+                          const unsigned long long* t_dev, const double* amp, bool dual,
+                          cudaStream_t stream) {
   const size_t n = static_cast<size_t>(L.H) * L.N;
-  sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(
-      L.d64, L.d32, L.N, L.H, seed, base, t_dev, amp[0], amp[1], amp[2]);
+  sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, stream ? stream : L.stream>>>(
+      L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
+      amp[0], amp[1], amp[2]);
   return cudaGetLastError();
 }
 
@@ -350,8 +357,10 @@ __device__ __forceinline__ double warp_min(double v) {
 // nothing yet; the SEG_CONTINUE lane of the next launch finishes it.
 template <typename T>
 __global__ void __launch_bounds__(kRollThreads)
-rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d,
-               const CandK<T>* __restrict__ cand, int early_exit, int classify) {
+rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
+               const T* __restrict__ d_pair1, const CandK<T>* __restrict__ cand, int early_exit,
+               int classify) {
+  const T* __restrict__ d = L.st->buf ? d_pair1 : d_pair0;
   const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
   const int y = blockIdx.y;
   int mode, i;
@@ -467,11 +476,12 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
                            bool recheck_classify) {
   dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
   if (use_fp64) {
-    rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.cand_k64,
-                                                                early_exit, 0);
+    rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.d64b,
+                                                                L.cand_k64, early_exit, 0);
   } else {
-    rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.cand_k32,
-                                                               early_exit, recheck_classify ? 1 : 0);
+    rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.d32b,
+                                                               L.cand_k32, early_exit,
+                                                               recheck_classify ? 1 : 0);
   }
   return cudaGetLastError();
 }
@@ -492,7 +502,8 @@ recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
     unsigned steps = 0;
     int end = 0;
     double q_ca = L.st->x[0] - p_atm, w = L.st->x[1], q_sm = L.st->x[2] - p_atm;
-    const double smin = run_lane<double>(K, L.cand_k64[i], L.d64, k, N, L.H, 0, L.H, q_ca, w, q_sm,
+    const double smin = run_lane<double>(K, L.cand_k64[i], L.st->buf ? L.d64b : L.d64, k, N, L.H,
+                                         0, L.H, q_ca, w, q_sm,
                                          inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps,
                                          &end);
     const bool ok = smin >= 0.0;
@@ -771,7 +782,7 @@ __device__ void write_result(SearchState* s, double* v_t, double* kappa, int32_t
 __global__ void __launch_bounds__(kSearchThreads)
 search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double* __restrict__ d_r,
                     const unsigned long long* t_dev, const double* __restrict__ d_v_prev,
-                    int pipeline) {
+                    int pipeline, long long buf_base) {
   SearchState* s = L.st;
   if (threadIdx.x == 0) g_tree_req.pending = 0;
   __syncthreads();
@@ -782,6 +793,9 @@ search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double
     s->x[0] = x0; s->x[1] = x1; s->x[2] = x2;
     s->r = r;
     s->v_prev = vp;
+    s->buf = (buf_base >= 0 && t_dev != nullptr && L.d64b != nullptr)
+                 ? static_cast<int>((static_cast<unsigned long long>(buf_base) + *t_dev) & 1ull)
+                 : 0;
     const bool fin = fabs(x0) <= DBL_MAX && fabs(x1) <= DBL_MAX && fabs(x2) <= DBL_MAX &&
                      fabs(r) <= DBL_MAX && fabs(vp) <= DBL_MAX;
     s->invalid = (!fin || !(vp > 0.0) || !(r > 0.0)) ? 1 : 0;
@@ -887,9 +901,11 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
 }
 
 cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
-                                const unsigned long long* t_dev, const double* d_v_prev) {
+                                const unsigned long long* t_dev, const double* d_v_prev,
+                                long long buf_base) {
   const int pipeline = search_pipelined(L.scfg, L.H) ? 1 : 0;
-  search_begin_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev, pipeline);
+  search_begin_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, d_r, t_dev, d_v_prev, pipeline,
+                                                          buf_base);
   return cudaGetLastError();
 }
 
@@ -916,6 +932,7 @@ eval_prepare_kernel(const Launch L, const double* __restrict__ d_x, double v_pre
     s->done = 0;
     s->invalid = 0;
     s->probe = 0;
+    s->buf = 0;
     set_segments(s, SEG_FULL, m, 0, SEG_FULL, 0, 0);
     s->prep_base = 0;
     s->prep_m = m;
