@@ -165,6 +165,11 @@ const char *rrg_last_error(rrg_handle h);
  * scenarios are redrawn at every RG time step; Alg. 3 step 2):
  * d_j^k[i] = a_i (2u - 1), u = (w_i >> 11) 2^-53 with (w_0, w_1, w_2, w_3) =
  * Philox4x64-10(counter = (j, k, update_index, 0), key = (seed, 0)).
+ * With precision RRG_FP32 or RRG_FP32_RECHECK only the binary32 copy used by
+ * the binary32 rollouts is drawn, from the top 24 bits of the same words:
+ * RN32((w_i >> 40) - 2^23) a_i 2^-23) (within a_i 2^-23 plus one rounding of
+ * the binary64 value); the binary64 values are regenerated from the same
+ * counters wherever they are needed (recheck, rrg_get_scenarios).
  * Asynchronous on the handle's stream. */
 int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index);
 

@@ -400,6 +400,9 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, HN3 * sizeof(float), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
+  fill_launch(h);
+  // the zero scenarios are explicit values (marks pair 0's binary64 array valid)
+  if (e == cudaSuccess) e = launch_round_scenarios(h->L);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? RRG_ENOMEM : RRG_ECUDA;
@@ -460,6 +463,8 @@ int rrg_get_scenarios(rrg_handle h, double* d) {
   if (!d) return set_err(h, RRG_EINVAL, "d is NULL");
   DeviceGuard g(h->device);
   const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
+  CK(launch_materialize64(h->L));
+  h->launches++;
   CK(cudaMemcpyAsync(d, h->d64, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return RRG_OK;

@@ -45,6 +45,16 @@ struct LaneState {
   int32_t status;
 };
 
+// Origin of a scenario pair.  In the binary32 modes the sampler writes only
+// the binary32 copy; the binary64 values (needed by the few rechecked
+// trajectories) are regenerated from the same Philox counters on demand.
+struct ScenSrc {
+  int32_t d64_valid;     // 1: the binary64 array holds the values
+  int32_t pad;
+  unsigned long long seed, update;
+  double amp[3];
+};
+
 // Device-resident state of one RG update's search (one per handle).
 struct SearchState {
   double x[3];        // x_t (absolute coordinates)
@@ -62,6 +72,7 @@ struct SearchState {
   int32_t invalid;    // inputs rejected on the device
   double v_t_out;     // governed reference of the finished search
   int32_t buf;        // scenario pair of the current update (0: d64/d32, 1: d64b/d32b)
+  ScenSrc src[2];     // where each pair's binary64 values are
   Seg seg[2];         // what the next rollout launch runs
   int32_t prep_base;  // slots the next prepare launch fills: prep_base ..
   int32_t prep_m;     //   prep_base + prep_m - 1
@@ -141,10 +152,14 @@ struct Launch {
 void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32);
 
 // ---- kernel launchers (rrg_kernels.cu) --------------------------------
-// dual: write the pair (base + *t_dev) & 1 (closed loops with two pairs)
+// dual: write the pair (base + *t_dev) & 1 (closed loops with two pairs).
+// In the binary32 modes only the binary32 copy is written.
 cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
                           const unsigned long long* t_dev, const double* amp, bool dual = false,
                           cudaStream_t stream = nullptr);
+// Fills pair 0's binary64 array from its Philox counters if it was sampled
+// lazily (no-op otherwise).
+cudaError_t launch_materialize64(const Launch& L);
 cudaError_t launch_round_scenarios(const Launch& L);
 // buf_base >= 0: the update index is buf_base + *t_dev and selects the
 // scenario pair by its parity; otherwise pair 0

@@ -170,29 +170,55 @@ cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_
 
 // ---------------------------------------------------------------------------
 // Scenario sampling: one thread per (j, k), coalesced over k.
+//
+// binary64 values: d = a (2u - 1), u = (w >> 11) 2^-53 (bit-exact with the
+// definition in rrg.h).  binary32 copy in the binary32 modes: from the top 24
+// bits of the same word, d32 = RN32((u24 - 2^23) a 2^-23); it differs from
+// the binary64 value by less than a 2^-23 plus one binary32 rounding, far
+// inside the binary32 rollout's own error, and needs no binary64 arithmetic
+// (GB300's binary64 pipe is narrow).
+__device__ __forceinline__ float uniform_sym32(uint64_t w, float a_scaled) {
+  const int t = static_cast<int>(w >> 40) - (1 << 23);
+  return __fmul_rn(__int2float_rn(t), a_scaled);
+}
+
 __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
                               double* __restrict__ d64b, float* __restrict__ d32b, int N, int H,
                               uint64_t seed, uint64_t base, const unsigned long long* t_dev,
-                              double a0, double a1, double a2) {
+                              double a0, double a1, double a2, int write64, SearchState* st) {
   const uint64_t upd = base + (t_dev ? *t_dev : 0ull);
-  if (d64b != nullptr && (upd & 1ull)) {
+  const int pair = (d64b != nullptr && (upd & 1ull)) ? 1 : 0;
+  if (pair) {
     d64 = d64b;
     d32 = d32b;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ScenSrc src;
+    src.d64_valid = write64;
+    src.pad = 0;
+    src.seed = seed;
+    src.update = upd;
+    src.amp[0] = a0;
+    src.amp[1] = a1;
+    src.amp[2] = a2;
+    st->src[pair] = src;
+  }
   const size_t HN = static_cast<size_t>(H) * N;
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const float s0 = static_cast<float>(a0 * 0x1.0p-23), s1 = static_cast<float>(a1 * 0x1.0p-23),
+              s2 = static_cast<float>(a2 * 0x1.0p-23);
   for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
     const uint64_t j = q / static_cast<uint64_t>(N), k = q - j * static_cast<uint64_t>(N);
     const U64x4 w = philox4x64_10(j, k, upd, 0ull, seed, 0ull);
-    const double x0 = uniform_sym(w.w[0], a0);
-    const double x1 = uniform_sym(w.w[1], a1);
-    const double x2 = uniform_sym(w.w[2], a2);
-    d64[q] = x0;
-    d64[HN + q] = x1;
-    d64[2 * HN + q] = x2;
-    d32[q] = static_cast<float>(x0);
-    d32[HN + q] = static_cast<float>(x1);
-    d32[2 * HN + q] = static_cast<float>(x2);
+    if (write64) {
+      d64[q] = uniform_sym(w.w[0], a0);
+      d64[HN + q] = uniform_sym(w.w[1], a1);
+      d64[2 * HN + q] = uniform_sym(w.w[2], a2);
+    } else {
+      d32[q] = uniform_sym32(w.w[0], s0);
+      d32[HN + q] = uniform_sym32(w.w[1], s1);
+      d32[2 * HN + q] = uniform_sym32(w.w[2], s2);
+    }
   }
 }
 
@@ -207,14 +233,39 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
                           const unsigned long long* t_dev, const double* amp, bool dual,
                           cudaStream_t stream) {
   const size_t n = static_cast<size_t>(L.H) * L.N;
+  const int write64 = L.precision == RRG_FP64 ? 1 : 0;
   sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, stream ? stream : L.stream>>>(
       L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
-      amp[0], amp[1], amp[2]);
+      amp[0], amp[1], amp[2], write64, L.st);
+  return cudaGetLastError();
+}
+
+// Writes pair 0's binary64 values from Philox when the pair was sampled in a
+// binary32 mode (its binary64 array is then stale).
+__global__ void materialize64_kernel(double* __restrict__ d64, int N, int H,
+                                     const SearchState* st) {
+  const ScenSrc src = st->src[0];
+  if (src.d64_valid) return;
+  const size_t HN = static_cast<size_t>(H) * N;
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
+    const uint64_t j = q / static_cast<uint64_t>(N), k = q - j * static_cast<uint64_t>(N);
+    const U64x4 w = philox4x64_10(j, k, src.update, 0ull, src.seed, 0ull);
+    d64[q] = uniform_sym(w.w[0], src.amp[0]);
+    d64[HN + q] = uniform_sym(w.w[1], src.amp[1]);
+    d64[2 * HN + q] = uniform_sym(w.w[2], src.amp[2]);
+  }
+}
+
+cudaError_t launch_materialize64(const Launch& L) {
+  const size_t n = static_cast<size_t>(L.H) * L.N;
+  materialize64_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.N, L.H, L.st);
   return cudaGetLastError();
 }
 
 __global__ void round_scenarios_kernel(const double* __restrict__ d64, float* __restrict__ d32,
-                                       size_t n) {
+                                       size_t n, SearchState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->src[0].d64_valid = 1;
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += stride)
     d32[q] = static_cast<float>(d64[q]);
@@ -222,7 +273,7 @@ __global__ void round_scenarios_kernel(const double* __restrict__ d64, float* __
 
 cudaError_t launch_round_scenarios(const Launch& L) {
   const size_t n = 3 * static_cast<size_t>(L.H) * L.N;
-  round_scenarios_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.d32, n);
+  round_scenarios_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.d32, n, L.st);
   return cudaGetLastError();
 }
 
@@ -486,6 +537,34 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
   return cudaGetLastError();
 }
 
+// One binary64 trajectory whose disturbances are regenerated from their
+// Philox counters step by step (the pair was sampled in a binary32 mode, so
+// its binary64 array was never written).  Same contract as run_lane over
+// steps 1..H with early exit at s < thr.
+__device__ double run_lane_philox(const Fc3K<double>& K, const CandK<double>& C,
+                                  const ScenSrc& src, int k, int H, double q_ca, double w,
+                                  double q_sm, double dt, double y_min, double thr,
+                                  unsigned* steps) {
+  double smin = checked_slack<double>(C, q_ca, w, q_sm, y_min);
+  int j = 0;
+  if (!(smin < thr)) {
+    while (j < H) {
+      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
+                                    0ull, src.seed, 0ull);
+      rk4_step<double>(K, C, dt, q_ca, w, q_sm);
+      q_ca += uniform_sym(r.w[0], src.amp[0]);
+      w += uniform_sym(r.w[1], src.amp[1]);
+      q_sm += uniform_sym(r.w[2], src.amp[2]);
+      ++j;
+      const double s = checked_slack<double>(C, q_ca, w, q_sm, y_min);
+      smin = fmin(smin, s);
+      if (s < thr) break;
+    }
+  }
+  *steps = static_cast<unsigned>(j);
+  return smin;
+}
+
 // Binary64 re-run of the trajectories the binary32 pass could not decide.
 __global__ void __launch_bounds__(64)
 recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
@@ -493,6 +572,8 @@ recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
   const int N = L.N;
   const double p_atm = L.params[P_P_ATM];
   const double thr = early_exit != RRG_EXIT_NONE ? 0.0 : -inf_v<double>();
+  const int buf = L.st->buf;
+  const ScenSrc src = L.st->src[buf];
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
     const uint32_t idx = L.recheck_list[e];
     const int i = static_cast<int>(idx / static_cast<uint32_t>(N));
@@ -500,12 +581,16 @@ recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
     // a failed candidate needs no more decisions, unless P asks for every entry
     if (L.P == nullptr && !L.cand_ok[i]) continue;
     unsigned steps = 0;
-    int end = 0;
-    double q_ca = L.st->x[0] - p_atm, w = L.st->x[1], q_sm = L.st->x[2] - p_atm;
-    const double smin = run_lane<double>(K, L.cand_k64[i], L.st->buf ? L.d64b : L.d64, k, N, L.H,
-                                         0, L.H, q_ca, w, q_sm,
-                                         inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps,
-                                         &end);
+    double smin;
+    if (src.d64_valid) {
+      int end = 0;
+      double q_ca = L.st->x[0] - p_atm, w = L.st->x[1], q_sm = L.st->x[2] - p_atm;
+      smin = run_lane<double>(K, L.cand_k64[i], buf ? L.d64b : L.d64, k, N, L.H, 0, L.H, q_ca, w,
+                              q_sm, inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps, &end);
+    } else {
+      smin = run_lane_philox(K, L.cand_k64[i], src, k, L.H, L.st->x[0] - p_atm, L.st->x[1],
+                             L.st->x[2] - p_atm, L.dt, L.y_min, thr, &steps);
+    }
     const bool ok = smin >= 0.0;
     if (!ok) L.cand_ok[i] = 0;
     if (L.P != nullptr) L.P[static_cast<size_t>(i) * N + k] = ok ? 1 : 0;

@@ -42,10 +42,13 @@ struct ParamBlock { double v[RRG_NPARAM]; };
 
 // Writes the parameter vector (passed by value) into the scratch and clears
 // the scratch's step counters.
-__global__ void static_params_kernel(ParamBlock pb, double* params, DevStats* stats) {
+__global__ void static_params_kernel(ParamBlock pb, double* params, DevStats* stats,
+                                     SearchState* st) {
   const int i = threadIdx.x;
   if (i < RRG_NPARAM) params[i] = pb.v[i];
   if (i == 0) {
+    st->src[0].d64_valid = 1;  // the caller's binary64 array holds the values
+    st->src[1].d64_valid = 1;
     stats->lane_steps = 0ull;
     stats->lane_steps_fp64 = 0ull;
     stats->rechecked = 0ull;
@@ -160,7 +163,7 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
 
   ParamBlock pb;
   std::memcpy(pb.v, model_params, sizeof pb.v);
-  static_params_kernel<<<1, 32, 0, L.stream>>>(pb, const_cast<double*>(L.params), L.stats);
+  static_params_kernel<<<1, 32, 0, L.stream>>>(pb, const_cast<double*>(L.params), L.stats, L.st);
   cudaError_t e = cudaGetLastError();
   // the prepare kernel rewrites every per-candidate flag, key and the recheck
   // count, so nothing left in the scratch by an earlier call is read

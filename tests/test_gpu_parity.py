@@ -58,6 +58,17 @@ def test_scenarios_bit_exact(R, orc, params):
         np.testing.assert_array_equal(got, want)
 
 
+def test_lazily_sampled_scenarios_materialize_bit_exact(R, orc, params):
+    """In the binary32 modes the sampler writes only the binary32 copy; the
+    binary64 values rrg_get_scenarios returns are regenerated from the same
+    Philox counters and equal the oracle's draw bit for bit."""
+    for prec in (R.FP32, R.FP32_RECHECK):
+        with R.Governor(params, _cfg(R, 40, 33, precision=prec)) as g:
+            g.sample_scenarios(77, 5)
+            got = g.get_scenarios()
+        np.testing.assert_array_equal(got, orc.sample_disturbances(77, 5, 40, 33, inputs.DIST_AMP))
+
+
 def test_set_scenarios_roundtrip(R, params):
     d = inputs.uniform_disturbances(29, 17, seed=3)
     with R.Governor(params, _cfg(R, 29, 17)) as g:
