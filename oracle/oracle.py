@@ -93,6 +93,10 @@ def lib():
         L.orc_closed_loop.argtypes = [_p, ctypes.POINTER(OrcCfg), _p, _d, _p, _int, _u64, _u64,
                                       _p, _p, _int, _int, _int, _int, _int, _p, _p, _p, _p]
         L.orc_closed_loop.restype = _i64
+        L.orc_min_slack_argmin.argtypes = [_p, ctypes.POINTER(OrcCfg), _p, _d, _p, ctypes.POINTER(_i64),
+                                           ctypes.POINTER(_i64)]
+        L.orc_min_slack_argmin.restype = _d
+        L.orc_slack_grad.argtypes = [_p, ctypes.POINTER(OrcCfg), _p, _d, _d, _d, _p, _i64, _i64, _p, _p]
         _lib = L
     return _lib
 
@@ -270,3 +274,24 @@ def closed_loop(p, c, x0, v0, r_seq, seed, t0, amp, plant_amp, search=0, n_kappa
                           int(t0), _ptr(amp), _ptr(plant_amp), int(search), int(n_kappa), int(M),
                           int(rounds), int(nthreads), _ptr(v), _ptr(kap), _ptr(fl), _ptr(xs))
     return v, kap, fl, xs
+
+
+def min_slack_argmin(p, c, x0, I, d=None):
+    """min over scenarios and steps of the slack (full horizon) and its argmin (k, j)."""
+    p, x0 = _f64(p), _f64(x0)
+    dd = _f64(d) if d is not None else None
+    kk, jj = _i64(0), _i64(0)
+    g = lib().orc_min_slack_argmin(_ptr(p), ctypes.byref(c), _ptr(x0), float(I),
+                                   _ptr(dd) if dd is not None else None, ctypes.byref(kk), ctypes.byref(jj))
+    return g, kk.value, jj.value
+
+
+def slack_grad(p, c, x_t, v_prev, r, kappa, d, k, jstar):
+    """Complex-step gradient of s_jstar^k w.r.t. (kappa, x_t[3], theta[27]); returns (s, grad[31])."""
+    p, x_t = _f64(p), _f64(x_t)
+    dd = _f64(d) if d is not None else None
+    grad = np.zeros(4 + p.shape[0])
+    s = ctypes.c_double(0.0)
+    lib().orc_slack_grad(_ptr(p), ctypes.byref(c), _ptr(x_t), float(v_prev), float(r), float(kappa),
+                         _ptr(dd) if dd is not None else None, int(k), int(jstar), _ptr(grad), ctypes.byref(s))
+    return s.value, grad

@@ -550,3 +550,116 @@ int64_t orc_closed_loop(const double *p, const orc_cfg *c, const double *x0, dou
     free(d);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Gradient of the robust objective g(kappa) = min over scenarios k and steps
+ * j of the slack s_j^k (the quantity the admissibility test thresholds at 0),
+ * at its argmin (k*, j*), with respect to kappa, x_t and every model
+ * parameter.  The oracle computes it by the complex-step method (Squire &
+ * Trapp, SIAM Review 40, 1998; Martins, Sturdza & Alonso, ACM TOMS 29, 2003):
+ * f'(a) = Im f(a + i h) / h for analytic f, with no subtraction error, so it is
+ * an independent check of the CUDA path's hand-written discrete adjoint. */
+#include <complex.h>
+
+typedef double complex cplx;
+
+static void fc3_rhs_cs(const cplx *p, const cplx *x, cplx cur, cplx *dx)
+{
+    cplx p_ca = x[0], w = x[1], p_sm = x[2];
+    cplx W_cp = p[O_A_W] * w - p[O_A_P] * (p_sm - p[O_P_ATM]);
+    cplx W_sm = p[O_K_SM] * (p_sm - p_ca);
+    cplx W_ca = p[O_K_CA] * (p_ca - p[O_P_ATM]);
+    cplx W_o2 = p[O_M_O2] * p[O_N_CELL] * cur / (4.0 * p[O_FARADAY]);
+    cplx e = (p[O_GAMMA] - 1.0) / p[O_GAMMA];
+    cplx Pi = p_sm / p[O_P_ATM];
+    cplx tau_cp = p[O_C_P] * p[O_T_ATM] / p[O_ETA_CP] * (cpow(Pi, e) - 1.0) * W_cp / w;
+    cplx W_ref = p[O_LAM_REF] * W_o2 / p[O_X_O2];
+    cplx v_cm = p[O_C0] + p[O_C1] * cur + p[O_C2] * cur * cur + p[O_K_P] * (W_ref - W_cp);
+    cplx tau_cm = p[O_ETA_CM] * p[O_K_T] * (v_cm - p[O_K_V] * w) / p[O_R_CM];
+    cplx RT = p[O_R_A] * p[O_T_ST];
+    dx[0] = RT / p[O_V_CA] * (W_sm - W_ca - W_o2);
+    dx[1] = (tau_cm - tau_cp) / p[O_J_CP];
+    dx[2] = RT / p[O_V_SM] * (W_cp - W_sm);
+}
+
+static cplx fc3_output_cs(const cplx *p, const cplx *x, cplx cur)
+{
+    cplx W_sm = p[O_K_SM] * (x[2] - x[0]);
+    return p[O_X_O2] * W_sm / (p[O_M_O2] * p[O_N_CELL] * cur / (4.0 * p[O_FARADAY]));
+}
+
+static void rk4_step_cs(const cplx *p, const cplx *x, cplx cur, double dt, cplx *xn)
+{
+    cplx k1[3], k2[3], k3[3], k4[3], t[3];
+    int i;
+    fc3_rhs_cs(p, x, cur, k1);
+    for (i = 0; i < 3; i++) t[i] = x[i] + 0.5 * dt * k1[i];
+    fc3_rhs_cs(p, t, cur, k2);
+    for (i = 0; i < 3; i++) t[i] = x[i] + 0.5 * dt * k2[i];
+    fc3_rhs_cs(p, t, cur, k3);
+    for (i = 0; i < 3; i++) t[i] = x[i] + dt * k3[i];
+    fc3_rhs_cs(p, t, cur, k4);
+    for (i = 0; i < 3; i++)
+        xn[i] = x[i] + (dt / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* s_jstar of scenario k with every input allowed to carry an imaginary part. */
+static cplx slack_cs(const cplx *p, const orc_cfg *c, const cplx *x0, cplx cur, const double *d,
+                     int64_t k, int64_t jstar)
+{
+    cplx x[3] = { x0[0], x0[1], x0[2] }, xn[3];
+    int64_t j;
+    int i;
+    for (j = 0; j < jstar; j++) {
+        rk4_step_cs(p, x, cur, c->dt, xn);
+        for (i = 0; i < 3; i++)
+            x[i] = xn[i] + (d ? d[((int64_t)i * c->H + j) * c->N + k] : 0.0);
+    }
+    return fc3_output_cs(p, x, cur) - c->y_min;
+}
+
+/* min over k, j of s_j^k over the full horizon (no early exit); the argmin is
+ * the first (k, then j) attaining it.  Returns the min. */
+double orc_min_slack_argmin(const double *p, const orc_cfg *c, const double *x0, double cur,
+                            const double *d, int64_t *k_out, int64_t *j_out)
+{
+    double best = INFINITY;
+    int64_t kb = -1, jb = -1, k, j;
+    for (k = 0; k < c->N; k++) {
+        double x[3] = { x0[0], x0[1], x0[2] }, xn[3];
+        for (j = 0; j <= c->H; j++) {
+            double s = orc_fc3_output(p, x, cur) - c->y_min;
+            int i;
+            if (s < best) { best = s; kb = k; jb = j; }
+            if (j == c->H) break;
+            orc_rk4_step(p, x, cur, c->dt, xn);
+            for (i = 0; i < 3; i++) x[i] = xn[i] + (d ? d[((int64_t)i * c->H + j) * c->N + k] : 0.0);
+        }
+    }
+    if (k_out) *k_out = kb;
+    if (j_out) *j_out = jb;
+    return best;
+}
+
+/* grad[0] = ds/dkappa, grad[1..3] = ds/dx_t, grad[4..4+NPARAM) = ds/dtheta
+ * for s = s_jstar^k at kappa (v = v_prev + kappa (r - v_prev)).  Complex
+ * step of size 1e-30 per direction. */
+void orc_slack_grad(const double *p, const orc_cfg *c, const double *x_t, double v_prev, double r,
+                    double kappa, const double *d, int64_t k, int64_t jstar, double *grad,
+                    double *s_out)
+{
+    const double h = 1e-30;
+    cplx pc[O_NPARAM], xc[3];
+    int dir, i;
+    for (dir = 0; dir < 4 + O_NPARAM; dir++) {
+        cplx kap = kappa, s;
+        for (i = 0; i < O_NPARAM; i++) pc[i] = p[i];
+        for (i = 0; i < 3; i++) xc[i] = x_t[i];
+        if (dir == 0) kap += _Complex_I * h;
+        else if (dir < 4) xc[dir - 1] += _Complex_I * h;
+        else pc[dir - 4] += _Complex_I * h;
+        s = slack_cs(pc, c, xc, v_prev + kap * (r - v_prev), d, k, jstar);
+        grad[dir] = cimag(s) / h;
+        if (dir == 0 && s_out) *s_out = creal(s);
+    }
+}
