@@ -45,6 +45,22 @@ PROBE_STEPS = 128
 FLOPS_PER_STEP = 153
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes per rollout launch on this workload (ncu, profiles/
+# rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the kernel
+# sources are the ones profiled
+TRAFFIC_PER_LAUNCH = 25.73e6 / 4
+TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "b79ddbecf5448196b9243cfbb88ab40ccdc7bc13",
+                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "d45d11c95e959aca39fe4cb352a5a835de5a70cf"}
+
+
+def measured_traffic():
+    """The profiled DRAM bytes per launch, or None if the kernel changed."""
+    import hashlib
+    for rel, sha in TRAFFIC_SOURCES.items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    return TRAFFIC_PER_LAUNCH
 
 
 def parse():
@@ -363,7 +379,8 @@ def run_gpu(args):
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": measured_traffic() if (NS, HZ) == (N_SCEN, HORIZON) else None,
                          "kernel": "rollout_kernel<float>",
                          "avg_launch_ms": avg_roll_ms, "launches": st["timed_rollouts"],
                          "flops_per_traj_step": FLOPS_PER_STEP,

@@ -253,6 +253,38 @@ int rrg_closed_loop_dev(rrg_handle h, const double *x0, double v0, const double 
 int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, uint64_t t,
                    const double *plant_amp, double *x_next);
 
+/* Gradient of the robust objective g(kappa) = min over scenarios k and steps
+ * j = 0..H of s_j^k = h(x_j^k, v) - y_min on the current scenarios, with
+ * v = v_prev + kappa (r_t - v_prev) (Eq. 2) and x_{j+1} = RK4(x_j, v) + d_j^k
+ * over the full horizon (Eq. 4; Alg. 3's admissibility test is g >= 0 plus
+ * the steady-state check).  The derivative is taken at the argmin (k*, j*)
+ * (first k, then first j, attaining the min; a subgradient where the argmin
+ * is not unique) by the discrete adjoint of the RK4 recursion: the forward
+ * pass saves every trajectory's state every `checkpoint` steps, the reverse
+ * pass recomputes one checkpoint segment at a time.  Host in: x_t[3]
+ * (finite), v_prev, r_t (> 0), kappa in [0, 1], checkpoint >= 1, precision
+ * RRG_FP64 or RRG_FP32 (arithmetic of both passes).  Host out (each may be
+ * NULL): *g, grad[31] = (dg/dkappa, dg/dx_t[3], dg/dtheta[27] in the FC3
+ * parameter layout), *k_star, *j_star.  Synchronous. */
+int rrg_slack_gradient(rrg_handle h, const double *x_t, double v_prev, double r_t, double kappa,
+                       int checkpoint, int precision, double *g, double *grad, int64_t *k_star,
+                       int64_t *j_star);
+
+/* Safeguarded Newton search for the largest admissible kappa on the current
+ * scenarios, driven by rrg_slack_gradient: kappa = 1 is tried first (as in
+ * Alg. 1), then Newton steps on g(kappa) = 0 inside a bracket [lo, hi] with
+ * lo admissible and hi not (steady-state check and g >= 0), bisection when a
+ * step leaves the bracket, until hi - lo <= tol or max_iter gradients.  The
+ * final bracket is then judged by rrg_eval_candidates (the handle's own
+ * admissibility test).  Host out: *kappa = lo (0 if nothing admissible),
+ * *flags (bit 0: nothing admissible found; bit 2: the bracket check failed:
+ * lo not admissible, hi admissible, or the bracket still wider than tol),
+ * *iterations (gradient evaluations).  Needs max_candidates >= 2.
+ * Synchronous. */
+int rrg_newton_search(rrg_handle h, const double *x_t, double r_t, double v_prev, double tol,
+                      int max_iter, int checkpoint, int precision, double *kappa, int32_t *flags,
+                      int32_t *iterations);
+
 /* Profiling: while on, every rollout and recheck launch is bracketed by CUDA
  * events on the handle's stream and their durations are summed into
  * rrg_stats.rollout_ms / recheck_ms. */

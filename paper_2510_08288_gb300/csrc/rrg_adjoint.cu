@@ -1,0 +1,381 @@
+// rrg_adjoint.cu -- discrete adjoint of the robust RG objective.
+//
+// g(kappa) = min over scenarios k and steps j = 0..H of the slack
+// s_j^k = h(x_j^k, v) - y_min, v = v_prev + kappa (r - v_prev) (Eq. 2), with
+// x_{j+1} = RK4(x_j, v) + d_j^k (Eq. 4): the admissibility test of Alg. 3
+// is g >= 0 (without the steady-state part).  Its derivative at the argmin
+// (k*, j*) (a subgradient where the argmin is not unique) is obtained by the
+// reverse (adjoint) sweep of the RK4 recursion of trajectory k* from j* back
+// to 0:
+//   forward  adjoint_forward_kernel: one thread per scenario, full horizon,
+//            the state saved every `checkpoint` steps, per-lane min and argmin;
+//   argmin   adjoint_argmin_kernel: the first (k, then j) attaining the min;
+//   reverse  adjoint_reverse_kernel: one thread; each checkpoint segment is
+//            recomputed forward into local memory, then swept backwards with
+//            the vector-Jacobian products of the FC3 right-hand side; the
+//            adjoints of the folded constants are mapped to the 27 model
+//            parameters, to x_t and (through the setpoint) to kappa.
+#include <cfloat>
+#include <cmath>
+
+#include "rrg_device.cuh"
+#include "rrg_internal.h"
+
+namespace rrg {
+
+namespace {
+
+// Adjoints of the constants the right-hand side and output read.
+template <typename T>
+struct ConstAdj {
+  T a_w, a_p, k_sm, k_ca, e, C_cp, C_m, k_v, K_p, RT_Vca, RT_Vsm, inv_J, inv_p_atm;
+  T W_o2, V0, y_scale;
+};
+
+// Vector-Jacobian product of fc3_rhs at q with output adjoint (b_ca, b_w,
+// b_sm): adds J^T b to (qb_ca, qb_w, qb_sm) and the constants' adjoints to g.
+template <typename T>
+__device__ void fc3_rhs_vjp(const Fc3K<T>& K, const CandK<T>& C, T q_ca, T w, T q_sm, T b_ca,
+                            T b_w, T b_sm, T& qb_ca, T& qb_w, T& qb_sm, ConstAdj<T>& g) {
+  // forward intermediates (as in fc3_rhs)
+  const T W_cp = K.a_w * w - K.a_p * q_sm;
+  const T W_sm = K.k_sm * (q_sm - q_ca);
+  const T W_ca = K.k_ca * q_ca;
+  const T Pi = T(1) + q_sm * K.inv_p_atm;
+  const T Pe = pow(Pi, K.e);
+  const T pr = Pe - T(1);
+  const T inv_w = T(1) / w;
+  const T tau_cp = K.C_cp * pr * W_cp * inv_w;
+  const T v_cm = C.V0 - K.K_p * W_cp;
+  const T tau_cm = K.C_m * (v_cm - K.k_v * w);
+  // d_ca = RT_Vca (W_sm - W_ca - W_o2)
+  g.RT_Vca += b_ca * (W_sm - W_ca - C.W_o2);
+  T Wsm_b = K.RT_Vca * b_ca;
+  const T Wca_b = -K.RT_Vca * b_ca;
+  g.W_o2 += -K.RT_Vca * b_ca;
+  // d_w = (tau_cm - tau_cp) inv_J
+  g.inv_J += b_w * (tau_cm - tau_cp);
+  const T tcm_b = K.inv_J * b_w, tcp_b = -K.inv_J * b_w;
+  // d_sm = RT_Vsm (W_cp - W_sm)
+  g.RT_Vsm += b_sm * (W_cp - W_sm);
+  T Wcp_b = K.RT_Vsm * b_sm;
+  Wsm_b += -K.RT_Vsm * b_sm;
+  // tau_cm = C_m (v_cm - k_v w)
+  g.C_m += tcm_b * (v_cm - K.k_v * w);
+  const T vcm_b = K.C_m * tcm_b;
+  T w_b = -K.C_m * K.k_v * tcm_b;
+  g.k_v += -K.C_m * w * tcm_b;
+  // v_cm = V0 - K_p W_cp
+  g.V0 += vcm_b;
+  g.K_p += -W_cp * vcm_b;
+  Wcp_b += -K.K_p * vcm_b;
+  // tau_cp = C_cp pr W_cp / w
+  g.C_cp += tcp_b * pr * W_cp * inv_w;
+  const T pr_b = tcp_b * K.C_cp * W_cp * inv_w;
+  Wcp_b += tcp_b * K.C_cp * pr * inv_w;
+  w_b += -tcp_b * tau_cp * inv_w;
+  // pr = Pi^e - 1
+  g.e += pr_b * Pe * log(Pi);
+  const T Pi_b = pr_b * K.e * Pe / Pi;
+  // Pi = 1 + q_sm inv_p_atm
+  T qsm_b = Pi_b * K.inv_p_atm;
+  g.inv_p_atm += Pi_b * q_sm;
+  // W_ca = k_ca q_ca
+  g.k_ca += Wca_b * q_ca;
+  T qca_b = K.k_ca * Wca_b;
+  // W_sm = k_sm (q_sm - q_ca)
+  g.k_sm += Wsm_b * (q_sm - q_ca);
+  qsm_b += K.k_sm * Wsm_b;
+  qca_b += -K.k_sm * Wsm_b;
+  // W_cp = a_w w - a_p q_sm
+  g.a_w += Wcp_b * w;
+  g.a_p += -Wcp_b * q_sm;
+  w_b += K.a_w * Wcp_b;
+  qsm_b += -K.a_p * Wcp_b;
+  qb_ca += qca_b;
+  qb_w += w_b;
+  qb_sm += qsm_b;
+}
+
+// Adjoint of one RK4 step q+ = q + dt/6 (k1 + 2 k2 + 2 k3 + k4) (+ d): given
+// the adjoint (l0, l1, l2) of q+, overwrites it with the adjoint of q.
+template <typename T>
+__device__ void rk4_step_vjp(const Fc3K<T>& K, const CandK<T>& C, T dt, T q_ca, T w, T q_sm,
+                             T& l0, T& l1, T& l2, ConstAdj<T>& g) {
+  const T h2 = T(0.5) * dt, h6 = dt / T(6);
+  // forward stages
+  T a1, b1, c1, a2, b2, c2, a3, b3, c3;
+  fc3_rhs<T>(K, C, q_ca, w, q_sm, a1, b1, c1);
+  const T y2_0 = q_ca + h2 * a1, y2_1 = w + h2 * b1, y2_2 = q_sm + h2 * c1;
+  fc3_rhs<T>(K, C, y2_0, y2_1, y2_2, a2, b2, c2);
+  const T y3_0 = q_ca + h2 * a2, y3_1 = w + h2 * b2, y3_2 = q_sm + h2 * c2;
+  fc3_rhs<T>(K, C, y3_0, y3_1, y3_2, a3, b3, c3);
+  const T y4_0 = q_ca + dt * a3, y4_1 = w + dt * b3, y4_2 = q_sm + dt * c3;
+  // reverse
+  T q0 = l0, q1 = l1, q2 = l2;                  // identity part
+  T k1_0 = h6 * l0, k1_1 = h6 * l1, k1_2 = h6 * l2;
+  T k2_0 = T(2) * h6 * l0, k2_1 = T(2) * h6 * l1, k2_2 = T(2) * h6 * l2;
+  T k3_0 = T(2) * h6 * l0, k3_1 = T(2) * h6 * l1, k3_2 = T(2) * h6 * l2;
+  const T k4_0 = h6 * l0, k4_1 = h6 * l1, k4_2 = h6 * l2;
+  T y0 = 0, y1 = 0, y2 = 0;
+  fc3_rhs_vjp<T>(K, C, y4_0, y4_1, y4_2, k4_0, k4_1, k4_2, y0, y1, y2, g);
+  q0 += y0; q1 += y1; q2 += y2;
+  k3_0 += dt * y0; k3_1 += dt * y1; k3_2 += dt * y2;
+  y0 = y1 = y2 = 0;
+  fc3_rhs_vjp<T>(K, C, y3_0, y3_1, y3_2, k3_0, k3_1, k3_2, y0, y1, y2, g);
+  q0 += y0; q1 += y1; q2 += y2;
+  k2_0 += h2 * y0; k2_1 += h2 * y1; k2_2 += h2 * y2;
+  y0 = y1 = y2 = 0;
+  fc3_rhs_vjp<T>(K, C, y2_0, y2_1, y2_2, k2_0, k2_1, k2_2, y0, y1, y2, g);
+  q0 += y0; q1 += y1; q2 += y2;
+  k1_0 += h2 * y0; k1_1 += h2 * y1; k1_2 += h2 * y2;
+  y0 = y1 = y2 = 0;
+  fc3_rhs_vjp<T>(K, C, q_ca, w, q_sm, k1_0, k1_1, k1_2, y0, y1, y2, g);
+  l0 = q0 + y0;
+  l1 = q1 + y1;
+  l2 = q2 + y2;
+}
+
+template <typename T>
+__device__ __forceinline__ Fc3K<T> konst(const Launch& L);
+template <>
+__device__ __forceinline__ Fc3K<double> konst<double>(const Launch& L) { return L.k64; }
+template <>
+__device__ __forceinline__ Fc3K<float> konst<float>(const Launch& L) { return L.k32; }
+
+template <typename T>
+__device__ CandK<T> cand_of(const double* P, double I) {
+  const double W_o2 = P[P_M_O2] * P[P_N_CELL] * I / (4.0 * P[P_FARADAY]);
+  CandK<T> C;
+  C.W_o2 = static_cast<T>(W_o2);
+  C.V0 = static_cast<T>(P[P_C0] + P[P_C1] * I + P[P_C2] * I * I +
+                        P[P_K_P] * P[P_LAM_REF] * W_o2 / P[P_X_O2]);
+  C.y_scale = static_cast<T>(P[P_X_O2] * P[P_K_SM] / W_o2);
+  return C;
+}
+
+// Forward: one thread per scenario, full horizon; state saved at j = 0, C,
+// 2C, ... (j < H) into ckpt[(k * nseg + c) * 3 + i]; per-lane min slack and
+// the first step attaining it.  The binary64 scenarios are read and rounded
+// to T.
+template <typename T>
+__global__ void __launch_bounds__(128)
+adjoint_forward_kernel(const Launch L, const double* __restrict__ d, const double* __restrict__ x_t,
+                       double v_prev, double r, double kappa, int checkpoint,
+                       double* __restrict__ ckpt, double* __restrict__ lane_min,
+                       int* __restrict__ lane_arg) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = L.N, H = L.H;
+  if (k >= N) return;
+  const double v = governed(v_prev, r, kappa);
+  const Fc3K<T> K = konst<T>(L);
+  const CandK<T> C = cand_of<T>(L.params, v);
+  const double p_atm = L.params[P_P_ATM];
+  T q_ca = static_cast<T>(x_t[0] - p_atm), w = static_cast<T>(x_t[1]),
+    q_sm = static_cast<T>(x_t[2] - p_atm);
+  const T dt = static_cast<T>(L.dt), y_min = static_cast<T>(L.y_min);
+  const int nseg = H / checkpoint + 1;
+  const size_t HN = static_cast<size_t>(H) * N;
+  T smin = fc3_output<T>(C, q_ca, q_sm) - y_min;
+  int arg = 0;
+  for (int j = 0; j < H; ++j) {
+    if (j % checkpoint == 0) {
+      double* c = ckpt + (static_cast<size_t>(k) * nseg + j / checkpoint) * 3;
+      c[0] = q_ca; c[1] = w; c[2] = q_sm;
+    }
+    const size_t o = static_cast<size_t>(j) * N + k;
+    const T e0 = static_cast<T>(d[o]), e1 = static_cast<T>(d[HN + o]),
+            e2 = static_cast<T>(d[2 * HN + o]);
+    rk4_step<T>(K, C, dt, q_ca, w, q_sm);
+    q_ca += e0; w += e1; q_sm += e2;
+    const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
+    if (s < smin) { smin = s; arg = j + 1; }
+  }
+  lane_min[k] = static_cast<double>(smin);
+  lane_arg[k] = arg;
+}
+
+__global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
+                                      const int* __restrict__ lane_arg, int N, double* out_g,
+                                      long long* out_k, long long* out_j) {
+  __shared__ double sv[256];
+  __shared__ int sk[256];
+  double best = INFINITY;
+  int bk = 0x7fffffff;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const double s = lane_min[k];
+    if (s < best || (s == best && k < bk)) { best = s; bk = k; }
+  }
+  sv[threadIdx.x] = best;
+  sk[threadIdx.x] = bk;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double s = sv[threadIdx.x + o];
+      const int kk = sk[threadIdx.x + o];
+      if (s < sv[threadIdx.x] || (s == sv[threadIdx.x] && kk < sk[threadIdx.x])) {
+        sv[threadIdx.x] = s;
+        sk[threadIdx.x] = kk;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *out_g = sv[0];
+    *out_k = sk[0];
+    *out_j = (sk[0] >= 0 && sk[0] < N) ? lane_arg[sk[0]] : 0;
+  }
+}
+
+// Reverse sweep of trajectory k* from j* to 0 (one thread), then the chain
+// rule from the folded constants to the model parameters and kappa.
+// seg: scratch of checkpoint * 3 values for the recomputed segment.
+// out[0] = dg/dkappa, out[1..3] = dg/dx_t, out[4..4+NPARAM) = dg/dtheta.
+template <typename T>
+__global__ void adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
+                                       double v_prev, double r, double kappa, int checkpoint,
+                                       const double* __restrict__ ckpt, const long long* kj,
+                                       T* __restrict__ seg, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double v = governed(v_prev, r, kappa);
+  const int N = L.N, H = L.H;
+  const int k = static_cast<int>(kj[0]), jstar = static_cast<int>(kj[1]);
+  const Fc3K<T> K = konst<T>(L);
+  const CandK<T> C = cand_of<T>(L.params, v);
+  const double* P = L.params;
+  const T dt = static_cast<T>(L.dt);
+  const int nseg = H / checkpoint + 1;
+  const size_t HN = static_cast<size_t>(H) * N;
+  ConstAdj<T> g{};
+  // the state at j*: recompute from its checkpoint
+  T q_ca, w, q_sm;
+  {
+    int c = jstar / checkpoint;
+    const int last = (H - 1) / checkpoint;  // last stored checkpoint
+    if (c > last) c = last;
+    const double* cp = ckpt + (static_cast<size_t>(k) * nseg + c) * 3;
+    q_ca = static_cast<T>(cp[0]); w = static_cast<T>(cp[1]); q_sm = static_cast<T>(cp[2]);
+    for (int j = c * checkpoint; j < jstar; ++j) {
+      const size_t o = static_cast<size_t>(j) * N + k;
+      rk4_step<T>(K, C, dt, q_ca, w, q_sm);
+      q_ca += static_cast<T>(d[o]);
+      w += static_cast<T>(d[HN + o]);
+      q_sm += static_cast<T>(d[2 * HN + o]);
+    }
+  }
+  // output at j*: s = y_scale (q_sm - q_ca) - y_min
+  g.y_scale += q_sm - q_ca;
+  T l0 = -C.y_scale, l1 = T(0), l2 = C.y_scale;
+  // backwards over the segments that end at or before j*
+  for (int c = (jstar - 1) / checkpoint; jstar > 0 && c >= 0; --c) {
+    const int j0 = c * checkpoint;
+    const int j1 = (j0 + checkpoint < jstar) ? j0 + checkpoint : jstar;  // steps j0..j1-1
+    const double* cp = ckpt + (static_cast<size_t>(k) * nseg + c) * 3;
+    T a = static_cast<T>(cp[0]), b = static_cast<T>(cp[1]), e = static_cast<T>(cp[2]);
+    for (int j = j0; j < j1; ++j) {
+      T* sj = seg + static_cast<size_t>(j - j0) * 3;
+      sj[0] = a; sj[1] = b; sj[2] = e;
+      const size_t o = static_cast<size_t>(j) * N + k;
+      rk4_step<T>(K, C, dt, a, b, e);
+      a += static_cast<T>(d[o]);
+      b += static_cast<T>(d[HN + o]);
+      e += static_cast<T>(d[2 * HN + o]);
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      const T* sj = seg + static_cast<size_t>(j - j0) * 3;
+      rk4_step_vjp<T>(K, C, dt, sj[0], sj[1], sj[2], l0, l1, l2, g);
+    }
+  }
+  // chain rule to the parameter vector (binary64)
+  double th[RRG_NPARAM];
+  for (int i = 0; i < RRG_NPARAM; ++i) th[i] = 0.0;
+  const double I = v;
+  const double W_o2 = P[P_M_O2] * P[P_N_CELL] * I / (4.0 * P[P_FARADAY]);
+  const double y_scale = P[P_X_O2] * P[P_K_SM] / W_o2;
+  const double lam = P[P_LAM_REF], xo2 = P[P_X_O2], Kp = P[P_K_P];
+  const double gamma = P[P_GAMMA];
+  th[P_A_W] += g.a_w;
+  th[P_A_P] += g.a_p;
+  th[P_K_SM] += g.k_sm + static_cast<double>(g.y_scale) * y_scale / P[P_K_SM];
+  th[P_K_CA] += g.k_ca;
+  th[P_GAMMA] += static_cast<double>(g.e) / (gamma * gamma);
+  {
+    const double Ccp = P[P_C_P] * P[P_T_ATM] / P[P_ETA_CP], gc = g.C_cp;
+    th[P_C_P] += gc * P[P_T_ATM] / P[P_ETA_CP];
+    th[P_T_ATM] += gc * P[P_C_P] / P[P_ETA_CP];
+    th[P_ETA_CP] += -gc * Ccp / P[P_ETA_CP];
+  }
+  {
+    const double Cm = P[P_ETA_CM] * P[P_K_T] / P[P_R_CM], gc = g.C_m;
+    th[P_ETA_CM] += gc * P[P_K_T] / P[P_R_CM];
+    th[P_K_T] += gc * P[P_ETA_CM] / P[P_R_CM];
+    th[P_R_CM] += -gc * Cm / P[P_R_CM];
+  }
+  th[P_K_V] += g.k_v;
+  th[P_K_P] += g.K_p;
+  {
+    const double RTa = P[P_R_A] * P[P_T_ST] / P[P_V_CA], RTs = P[P_R_A] * P[P_T_ST] / P[P_V_SM];
+    const double ga = g.RT_Vca, gs = g.RT_Vsm;
+    th[P_R_A] += ga * P[P_T_ST] / P[P_V_CA] + gs * P[P_T_ST] / P[P_V_SM];
+    th[P_T_ST] += ga * P[P_R_A] / P[P_V_CA] + gs * P[P_R_A] / P[P_V_SM];
+    th[P_V_CA] += -ga * RTa / P[P_V_CA];
+    th[P_V_SM] += -gs * RTs / P[P_V_SM];
+  }
+  th[P_J_CP] += -static_cast<double>(g.inv_J) / (P[P_J_CP] * P[P_J_CP]);
+  // p_atm: through 1/p_atm and through q_0 = x_t - p_atm (pressures)
+  th[P_P_ATM] += -static_cast<double>(g.inv_p_atm) / (P[P_P_ATM] * P[P_P_ATM]) -
+                 static_cast<double>(l0) - static_cast<double>(l2);
+  // candidate constants
+  const double gV0 = g.V0, gy = g.y_scale;
+  const double gW = static_cast<double>(g.W_o2) + gV0 * Kp * lam / xo2 - gy * y_scale / W_o2;
+  th[P_M_O2] += gW * W_o2 / P[P_M_O2];
+  th[P_N_CELL] += gW * W_o2 / P[P_N_CELL];
+  th[P_FARADAY] += -gW * W_o2 / P[P_FARADAY];
+  th[P_C0] += gV0;
+  th[P_C1] += gV0 * I;
+  th[P_C2] += gV0 * I * I;
+  th[P_K_P] += gV0 * lam * W_o2 / xo2;
+  th[P_LAM_REF] += gV0 * Kp * W_o2 / xo2;
+  th[P_X_O2] += -gV0 * Kp * lam * W_o2 / (xo2 * xo2) + gy * y_scale / xo2;
+  const double dI = gW * W_o2 / I + gV0 * (P[P_C1] + 2.0 * P[P_C2] * I);
+  out[0] = dI * (r - v_prev);
+  out[1] = l0;
+  out[2] = l1;
+  out[3] = l2;
+  for (int i = 0; i < RRG_NPARAM; ++i) out[4 + i] = th[i];
+}
+
+}  // namespace
+
+// Host side: enqueue forward, argmin and reverse on the handle's stream.
+// ckpt: N * (H / checkpoint + 1) * 3 doubles; lane_min/lane_arg: N each;
+// seg: checkpoint * 3 doubles; d_kj: 2; d_out: 1 + 3 + RRG_NPARAM.
+cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
+                           double kappa, int checkpoint, double* ckpt, double* lane_min,
+                           int* lane_arg, double* seg, double* d_g, long long* d_kj,
+                           double* d_out) {
+  const int blocks = (L.N + 127) / 128;
+  if (fp64) {
+    adjoint_forward_kernel<double><<<blocks, 128, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
+                                                                 checkpoint, ckpt, lane_min, lane_arg);
+  } else {
+    adjoint_forward_kernel<float><<<blocks, 128, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
+                                                                checkpoint, ckpt, lane_min, lane_arg);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adjoint_argmin_kernel<<<1, 256, 0, L.stream>>>(lane_min, lane_arg, L.N, d_g, d_kj, d_kj + 1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (fp64) {
+    adjoint_reverse_kernel<double><<<1, 32, 0, L.stream>>>(L, L.d64, v_prev, r, kappa, checkpoint,
+                                                           ckpt, d_kj, seg, d_out);
+  } else {
+    adjoint_reverse_kernel<float><<<1, 32, 0, L.stream>>>(L, L.d64, v_prev, r, kappa, checkpoint,
+                                                          ckpt, d_kj, reinterpret_cast<float*>(seg),
+                                                          d_out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rrg

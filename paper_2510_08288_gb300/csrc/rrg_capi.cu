@@ -36,6 +36,14 @@ struct rrg_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool cl_next_ready = false;   // the closed loop's next update is already sampled
   uint64_t cl_seed = 0, cl_t0 = 0;
+  // adjoint buffers (allocated on first use)
+  double* adj_ckpt = nullptr;
+  size_t adj_ckpt_cap = 0;
+  double* adj_lane_min = nullptr;
+  int* adj_lane_arg = nullptr;
+  double* adj_seg = nullptr;
+  int adj_seg_cap = 0;
+  double* adj_out = nullptr;   // [0] g, [1..2] k*, j* (as long long), [3..] gradient
   // the captured one-update graph of the last closed loop, reused while the
   // run's pointers and indices stay the same
   cudaGraphExec_t cl_exec = nullptr;
@@ -154,7 +162,8 @@ void free_all(rrg_ctx* h) {
   void* ptrs[] = {h->params_dev, h->d64, h->d32, h->d64b, h->d32b, h->st, h->cand_kappa,
                   h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
-                  h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state};
+                  h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state,
+                  h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->io_h) cudaFreeHost(h->io_h);
@@ -723,6 +732,127 @@ int rrg_closed_loop(rrg_handle h, const double* x0, double v0, const double* r_s
     CK(cudaMemcpyAsync(x_out, d_x, 3 * (static_cast<size_t>(T) + 1) * sizeof(double),
                        cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
+}
+
+int rrg_slack_gradient(rrg_handle h, const double* x_t, double v_prev, double r_t, double kappa,
+                       int checkpoint, int precision, double* g, double* grad, int64_t* k_star,
+                       int64_t* j_star) {
+  if (!h) return RRG_EINVAL;
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite and v_prev, r_t > 0");
+  if (!(kappa >= 0.0 && kappa <= 1.0)) return set_err(h, RRG_EINVAL, "kappa outside [0, 1]");
+  if (checkpoint < 1 || checkpoint > 1 << 16)
+    return set_err(h, RRG_EINVAL, "checkpoint must be in [1, 65536]");
+  if (precision != RRG_FP64 && precision != RRG_FP32)
+    return set_err(h, RRG_EINVAL, "precision must be RRG_FP64 or RRG_FP32");
+  DeviceGuard gd(h->device);
+  const size_t N = h->cfg.n_scenarios, H = h->cfg.horizon;
+  const size_t need = N * (H / checkpoint + 1) * 3;
+  if (need > h->adj_ckpt_cap) {
+    if (h->adj_ckpt) cudaFree(h->adj_ckpt);
+    h->adj_ckpt = nullptr;
+    h->adj_ckpt_cap = 0;
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_ckpt), need * sizeof(double)));
+    h->adj_ckpt_cap = need;
+  }
+  if (!h->adj_lane_min) {
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_lane_min), N * sizeof(double)));
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_lane_arg), N * sizeof(int)));
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_out), (3 + 4 + RRG_NPARAM) * sizeof(double)));
+  }
+  if (checkpoint > h->adj_seg_cap) {
+    if (h->adj_seg) cudaFree(h->adj_seg);
+    h->adj_seg = nullptr;
+    h->adj_seg_cap = 0;
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_seg), static_cast<size_t>(checkpoint) * 3 * sizeof(double)));
+    h->adj_seg_cap = checkpoint;
+  }
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_materialize64(h->L));
+  CK(launch_adjoint(h->L, precision == RRG_FP64, h->io_dev + IO_X, v_prev, r_t, kappa, checkpoint,
+                    h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
+                    reinterpret_cast<long long*>(h->adj_out + 1), h->adj_out + 3));
+  h->launches += 4;
+  double out[3 + 4 + RRG_NPARAM];
+  CK(cudaMemcpyAsync(out, h->adj_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  long long kj[2];
+  std::memcpy(kj, out + 1, sizeof kj);
+  if (g) *g = out[0];
+  if (k_star) *k_star = kj[0];
+  if (j_star) *j_star = kj[1];
+  if (grad) std::memcpy(grad, out + 3, (4 + RRG_NPARAM) * sizeof(double));
+  return RRG_OK;
+}
+
+int rrg_newton_search(rrg_handle h, const double* x_t, double r_t, double v_prev, double tol,
+                      int max_iter, int checkpoint, int precision, double* kappa, int32_t* flags,
+                      int32_t* iterations) {
+  if (!h) return RRG_EINVAL;
+  if (!(tol > 0.0) || max_iter < 1) return set_err(h, RRG_EINVAL, "tol > 0 and max_iter >= 1 needed");
+  if (h->cfg.max_candidates < 2)
+    return set_err(h, RRG_EINVAL, "the bracket check needs max_candidates >= 2");
+  const double thr_ss = h->cfg.y_min + h->cfg.eps_ss * (h->cfg.y_c - h->cfg.y_min);
+  // admissible(k): steady-state check (device equilibrium) and g >= 0
+  auto ss_ok = [&](double k, bool* ok) -> int {
+    if (!h->cfg.ss_check) { *ok = true; return RRG_OK; }
+    double x[3], y = 0.0;
+    const double v = v_prev + k * (r_t - v_prev);
+    const int rc = rrg_equilibrium(h, v, x, &y);
+    if (rc == RRG_EINVAL) { *ok = false; return RRG_OK; }
+    if (rc != RRG_OK) return rc;
+    *ok = y >= thr_ss;
+    return RRG_OK;
+  };
+  int32_t it = 0;
+  // Alg. 1 starts with kappa = 1, judged by the handle's own evaluation
+  const double one = 1.0;
+  uint8_t adm_one = 0;
+  int rc = rrg_eval_candidates(h, x_t, v_prev, r_t, &one, 1, &adm_one, nullptr, nullptr);
+  if (rc != RRG_OK) return rc;
+  if (adm_one) {
+    if (kappa) *kappa = 1.0;
+    if (flags) *flags = 0;
+    if (iterations) *iterations = 0;
+    return RRG_OK;
+  }
+  // like Alg. 1, kappa = 0 is never tested: it is the hold returned when no
+  // tested kappa is admissible
+  double lo = 0.0, hi = 1.0, k = 0.5;
+  bool any = false;
+  while (it < max_iter && hi - lo > tol) {
+    double g = 0.0, grad[4 + RRG_NPARAM];
+    int64_t ks, js;
+    rc = rrg_slack_gradient(h, x_t, v_prev, r_t, k, checkpoint, precision, &g, grad, &ks, &js);
+    if (rc != RRG_OK) return rc;
+    ++it;
+    bool ok = false;
+    rc = ss_ok(k, &ok);
+    if (rc != RRG_OK) return rc;
+    const bool adm = ok && g >= 0.0;
+    if (adm) { lo = k; any = true; } else { hi = k; }
+    // Newton step on g(kappa) = 0 (g decreases through the boundary); fall
+    // back to the bracket midpoint when the step leaves the bracket
+    double kn = (grad[0] < 0.0 && ok) ? k - g / grad[0] : 0.5 * (lo + hi);
+    if (!(kn > lo && kn < hi)) kn = 0.5 * (lo + hi);
+    // a root approached from one side: step just across it to close the bracket
+    if (adm && kn - lo < 0.25 * tol) kn = lo + 0.5 * tol;
+    if (!adm && hi - kn < 0.25 * tol) kn = hi - 0.5 * tol;
+    if (kn <= lo || kn >= hi) kn = 0.5 * (lo + hi);
+    k = kn;
+  }
+  // the bracket as plain bisection judges it: lo admissible, hi not
+  int32_t fl = any ? 0 : 1;
+  const double br[2] = {lo, hi};
+  uint8_t a[2] = {0, 0};
+  rc = rrg_eval_candidates(h, x_t, v_prev, r_t, br, 2, a, nullptr, nullptr);
+  if (rc != RRG_OK) return rc;
+  if ((lo > 0.0 && !a[0]) || a[1] || hi - lo > tol) fl |= 4;
+  if (kappa) *kappa = any ? lo : 0.0;
+  if (flags) *flags = fl;
+  if (iterations) *iterations = it;
   return RRG_OK;
 }
 

@@ -188,6 +188,12 @@ cudaError_t launch_loop_end(const Launch& L, LoopState* ls, uint64_t seed, uint6
 cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, double v0,
                              double* d_x_out);
 
+// Discrete adjoint of the min-slack objective (rrg_adjoint.cu).
+cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
+                           double kappa, int checkpoint, double* ckpt, double* lane_min,
+                           int* lane_arg, double* seg, double* d_g, long long* d_kj,
+                           double* d_out);
+
 // Configuration check shared with the handle-less entry point (rrg_capi.cu);
 // on failure the message is readable with rrg_last_error(NULL).
 int check_config(const rrg_config* c);

@@ -82,6 +82,10 @@ def _load():
         "rrg_set_profiling": (ctypes.c_int, [_p, ctypes.c_int]),
         "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
         "rrg_reset_stats": (ctypes.c_int, [_p]),
+        "rrg_slack_gradient": (ctypes.c_int, [_p, _p, _d, _d, _d, ctypes.c_int, ctypes.c_int, _p, _p,
+                                              P(ctypes.c_int64), P(ctypes.c_int64)]),
+        "rrg_newton_search": (ctypes.c_int, [_p, _p, _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             _p, _p, _p]),
         "rrg_eval_candidates_static": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, _p, _p, _p, _d,
                                                       _d, _p, ctypes.c_int, _p, _p]),
     }
@@ -233,6 +237,29 @@ def rrg_plant_step(h, x_t, v_t, seed, t, plant_amp):
     return out
 
 
+def rrg_slack_gradient(h, x_t, v_prev, r_t, kappa, checkpoint=50, precision=FP64):
+    """(g, grad[31], k*, j*): min slack over scenarios and steps and its
+    gradient w.r.t. (kappa, x_t[3], theta[27]) by the discrete adjoint."""
+    x = _f64(x_t)
+    g = _d(0.0)
+    grad = np.zeros(4 + NPARAM)
+    ks, js = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.rrg_slack_gradient(h, _ptr(x), float(v_prev), float(r_t), float(kappa), int(checkpoint),
+                                  int(precision), ctypes.byref(g), _ptr(grad), ctypes.byref(ks),
+                                  ctypes.byref(js)), h)
+    return g.value, grad, ks.value, js.value
+
+
+def rrg_newton_search(h, x_t, r_t, v_prev, tol=2.0 ** -19, max_iter=40, checkpoint=50, precision=FP64):
+    """(kappa, flags, iterations) of the adjoint-driven Newton search."""
+    x = _f64(x_t)
+    k, fl, it = _d(0.0), _i32(0), _i32(0)
+    _check(lib.rrg_newton_search(h, _ptr(x), float(r_t), float(v_prev), float(tol), int(max_iter),
+                                 int(checkpoint), int(precision), ctypes.byref(k), ctypes.byref(fl),
+                                 ctypes.byref(it)), h)
+    return k.value, fl.value, it.value
+
+
 def rrg_set_profiling(h, on):
     _check(lib.rrg_set_profiling(h, int(bool(on))), h)
 
@@ -309,6 +336,12 @@ class Governor:
 
     def plant_step(self, x_t, v_t, seed, t, plant_amp):
         return rrg_plant_step(self.h, x_t, v_t, seed, t, plant_amp)
+
+    def slack_gradient(self, x_t, v_prev, r_t, kappa, checkpoint=50, precision=FP64):
+        return rrg_slack_gradient(self.h, x_t, v_prev, r_t, kappa, checkpoint, precision)
+
+    def newton_search(self, x_t, r_t, v_prev, tol=2.0 ** -19, max_iter=40, checkpoint=50, precision=FP64):
+        return rrg_newton_search(self.h, x_t, r_t, v_prev, tol, max_iter, checkpoint, precision)
 
     def stats(self):
         return rrg_get_stats(self.h)
