@@ -26,8 +26,9 @@ def R():
 
 
 def _gov(R, params, N, H, **kw):
-    cfg = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=16, precision=R.FP64, **kw)
-    return R.Governor(params, cfg)
+    base = dict(horizon=H, n_scenarios=N, max_candidates=16, precision=R.FP64)
+    base.update(kw)
+    return R.Governor(params, R.rrg_config_default(**base))
 
 
 @pytest.mark.parametrize("checkpoint", [1, 7, 50, 1000])
