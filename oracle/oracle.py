@@ -97,6 +97,8 @@ def lib():
                                            ctypes.POINTER(_i64)]
         L.orc_min_slack_argmin.restype = _d
         L.orc_slack_grad.argtypes = [_p, ctypes.POINTER(OrcCfg), _p, _d, _d, _d, _p, _i64, _i64, _p, _p]
+        L.orc_sample_param_multipliers.argtypes = [_u64, _u64, _i64, _d, ctypes.c_uint32, _p]
+        L.orc_set_param_multipliers.argtypes = [_p]
         _lib = L
     return _lib
 
@@ -295,3 +297,24 @@ def slack_grad(p, c, x_t, v_prev, r, kappa, d, k, jstar):
     lib().orc_slack_grad(_ptr(p), ctypes.byref(c), _ptr(x_t), float(v_prev), float(r), float(kappa),
                          _ptr(dd) if dd is not None else None, int(k), int(jstar), _ptr(grad), ctypes.byref(s))
     return s.value, grad
+
+
+def sample_param_multipliers(seed, update, N, rho, mask):
+    """Per-scenario parameter multipliers m[k, p] (parametric uncertainty workload)."""
+    m = np.zeros((N, nparam()))
+    lib().orc_sample_param_multipliers(int(seed), int(update), int(N), float(rho), int(mask), _ptr(m))
+    return m
+
+
+class param_multipliers:
+    """Context manager: evaluations inside use scenario k's parameters p * m[k]."""
+
+    def __init__(self, m):
+        self.m = None if m is None else np.ascontiguousarray(np.asarray(m, dtype=np.float64))
+
+    def __enter__(self):
+        lib().orc_set_param_multipliers(_ptr(self.m) if self.m is not None else None)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_param_multipliers(None)

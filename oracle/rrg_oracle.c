@@ -26,6 +26,9 @@
  *   searches           pinned: brute-force dyadic grid vs bisection,
  *                      Alg. 1 == Alg. 2 with d = 0 and N = 1, scenario
  *                      monotonicity, early-exit invariance.
+ *   param multipliers  pinned: range, moments and mask of the draws, words
+ *                      from the numpy-pinned Philox stream 2, and scenario
+ *                      k's rollout equal to the nominal rollout of theta m^k.
  */
 #include <math.h>
 #include <pthread.h>
@@ -151,7 +154,7 @@ void orc_philox4x64_10(const uint64_t *ctr, const uint64_t *key, uint64_t *out)
 }
 
 /* Counter streams: word 3 of the counter selects what is drawn. */
-enum { STREAM_SCENARIO = 0, STREAM_PLANT = 1 };
+enum { STREAM_SCENARIO = 0, STREAM_PLANT = 1, STREAM_PARAM = 2 };
 
 /* Uniform on [-a, a): top 53 bits of a Philox word as u in [0, 1). */
 static double uniform_sym(uint64_t w, double a)
@@ -178,6 +181,38 @@ void orc_sample_disturbances(uint64_t seed, uint64_t update, int64_t N, int64_t 
         }
     }
 }
+
+/* Parametric uncertainty: scenario k of update t sees the model parameters
+ * theta_p m_p^k, m_p^k = 1 + rho (2u - 1) uniform on [1 - rho, 1 + rho] for
+ * every parameter p set in `mask` (bit p) and 1 otherwise; u from word p % 4
+ * of Philox4x64-10(counter = (p / 4, k, t, 2), key = (seed, 0)).
+ * Output m[k * nparam + p]. */
+void orc_sample_param_multipliers(uint64_t seed, uint64_t update, int64_t N, double rho,
+                                  uint32_t mask, double *m)
+{
+    uint64_t key[2] = { seed, 0 };
+    int64_t k;
+    int p;
+    for (k = 0; k < N; k++) {
+        for (p = 0; p < O_NPARAM; p++) {
+            double mult = 1.0;
+            if (mask & (1u << p)) {
+                uint64_t ctr[4] = { (uint64_t)(p / 4), (uint64_t)k, update, STREAM_PARAM };
+                uint64_t w[4];
+                orc_philox4x64_10(ctr, key, w);
+                mult = 1.0 + uniform_sym(w[p % 4], rho);
+            }
+            m[k * O_NPARAM + p] = mult;
+        }
+    }
+}
+
+/* Multipliers the evaluations below apply to scenario k's parameters
+ * (NULL: every scenario sees the nominal parameters).  The steady-state check
+ * always uses the nominal parameters. */
+static const double *g_param_mult = NULL;
+
+void orc_set_param_multipliers(const double *m) { g_param_mult = m; }
 
 /* Disturbance acting on the simulated plant at closed-loop step t (Eq. 4). */
 void orc_plant_disturbance(uint64_t seed, uint64_t t, const double *amp, double *d3)
@@ -262,12 +297,19 @@ int orc_ss_ok(const double *p, const orc_cfg *c, double I)
  * x_{j+1} = RK4(x_j, v) + d_j^k; slack s_j = h(x_j, v) - y_min at
  * j = 0..H.  Returns min_j s_j, -inf if any state or output is not finite.
  * d == NULL means the disturbance-free model of Eq. 1. */
-double orc_rollout(const double *p, const orc_cfg *c, const double *x0, double I,
+double orc_rollout(const double *p_nominal, const orc_cfg *c, const double *x0, double I,
                    const double *d, int64_t k, int64_t *steps_out)
 {
     double x[3] = { x0[0], x0[1], x0[2] }, xn[3];
     double smin = INFINITY;
     int64_t j, steps = 0;
+    double pk[O_NPARAM];
+    const double *p = p_nominal;
+    if (g_param_mult) {
+        int i;
+        for (i = 0; i < O_NPARAM; i++) pk[i] = p_nominal[i] * g_param_mult[k * O_NPARAM + i];
+        p = pk;
+    }
     for (j = 0; j <= c->H; j++) {
         double s = orc_fc3_output(p, x, I) - c->y_min;
         int i;

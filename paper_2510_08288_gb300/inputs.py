@@ -58,6 +58,8 @@ FC3_DEFAULTS = {
 
 # Parameters perturbed per scenario in the parametric-uncertainty workload.
 FC3_UNCERTAIN = ("k_sm", "k_ca", "eta_cp", "J_cp", "a_w", "a_p", "eta_cm", "R_cm")
+FC3_UNCERTAIN_MASK = sum(1 << FC3_PARAM_NAMES.index(n) for n in FC3_UNCERTAIN)
+PARAM_UNC_REL = 0.10            # +-10 % per uncertain parameter
 
 DIST_AMP = (50.0, 10.0, 50.0)   # +-50 Pa, +-10 rad/s, +-50 Pa (Sec. IV-A)
 DT = 0.01                       # s (Sec. IV-A)

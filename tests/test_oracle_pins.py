@@ -344,3 +344,59 @@ def test_non_finite_state_is_a_violation(orc, params):
     c = orc.cfg(H=10, N=1)
     s, _ = orc.rollout(params, c, [np.nan, 3000.0, 120000.0], 100.0)
     assert s == -np.inf
+
+
+# --------------------------------------------------- parametric uncertainty --
+def test_param_multipliers_range_moments_and_mask(orc):
+    """Per-scenario multipliers m_p^k uniform on [1 - rho, 1 + rho) for every
+    uncertain parameter, exactly 1 for the rest; i.i.d. over k and p; redrawn
+    with the update index; nested in N."""
+    rho, mask = 0.1, inputs.FC3_UNCERTAIN_MASK
+    m = orc.sample_param_multipliers(7, 3, 4096, rho, mask)
+    unc = np.array([(mask >> p) & 1 for p in range(orc.nparam())], dtype=bool)
+    assert unc.sum() == len(inputs.FC3_UNCERTAIN)
+    np.testing.assert_array_equal(m[:, ~unc], 1.0)
+    mu = m[:, unc]
+    assert mu.min() >= 1.0 - rho and mu.max() < 1.0 + rho
+    assert np.all(np.abs(mu.mean(axis=0) - 1.0) < 0.006)
+    assert np.all(np.abs(mu.var(axis=0) / (rho * rho / 3.0) - 1.0) < 0.08)
+    # distinct parameters of one scenario are not the same draw
+    c = np.corrcoef(mu.T)
+    assert np.max(np.abs(c - np.eye(c.shape[0]))) < 0.06
+    np.testing.assert_array_equal(orc.sample_param_multipliers(7, 3, 100, rho, mask), m[:100])
+    assert not np.any(orc.sample_param_multipliers(7, 4, 100, rho, mask)[:, unc] == m[:100, unc])
+    np.testing.assert_array_equal(orc.sample_param_multipliers(7, 3, 64, 0.0, mask), 1.0)
+
+
+def test_param_multiplier_words_from_philox(orc):
+    """m_p^k comes from word p % 4 of the Philox block at counter
+    (p / 4, k, update, 2): the stream-2 blocks, pinned to numpy's Philox
+    above, mapped to 1 + rho (2u - 1) with u the top 53 bits over 2^53."""
+    rho, seed, upd = 0.25, 99, 12
+    m = orc.sample_param_multipliers(seed, upd, 5, rho, (1 << orc.nparam()) - 1)
+    for k in range(5):
+        for p in range(orc.nparam()):
+            w = int(orc.philox4x64_10([p // 4, k, upd, 2], [seed, 0])[p % 4])
+            u = (w >> 11) / 2.0**53
+            assert m[k, p] == 1.0 + rho * (2.0 * u - 1.0)
+
+
+def test_param_multipliers_scale_scenario_parameters(orc, params):
+    """With multipliers loaded, scenario k's rollout is the nominal rollout of
+    the model with parameters theta * m^k (only scenario k's row is used),
+    and leaving the context restores the nominal model."""
+    N, H = 6, 120
+    c = orc.cfg(H=H, N=N, early_exit=0)
+    x = orc.equilibrium(params, 120.0)
+    d = orc.sample_disturbances(1, 0, N, H, inputs.DIST_AMP)
+    m = orc.sample_param_multipliers(1, 0, N, 0.1, inputs.FC3_UNCERTAIN_MASK)
+    nominal = [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)]
+    with orc.param_multipliers(m):
+        scaled = [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)]
+    direct = [orc.rollout(params * m[k], c, x, 180.0, d, k)[0] for k in range(N)]
+    assert scaled == direct
+    assert all(a != b for a, b in zip(scaled, nominal))
+    assert [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)] == nominal
+    # multipliers of one make no difference
+    with orc.param_multipliers(np.ones_like(m)):
+        assert [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)] == nominal
