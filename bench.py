@@ -19,6 +19,13 @@ peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz.  cpu_baseline = the
 FP64 CPU oracle (plain joint bisection) on a bounded prefix of the same run.
 
 --impl reference times that oracle alone (the CPU arm) on the same workload.
+
+--workload sweep: the large-sweep workload instead, one RG update per step
+(k-section with 16 kappa candidates per round, 3 rounds, binary32 rollouts
+with the binary64 recheck) over N_sim = 1,024 ... 65,536 scenarios, each with
+per-step disturbances and per-scenario parametric uncertainty (+-10 % on the
+uncertain FC3 parameters), horizon 5,000 steps; one JSON line with
+trajectory-steps/s per N.
 """
 from __future__ import annotations
 
@@ -45,6 +52,10 @@ PROBE_STEPS = 128
 FLOPS_PER_STEP = 153
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+# large sweep: N_sim 1K..64K, 16 candidates, horizon 5,000, parametric uncertainty
+SWEEP_N = (1024, 2048, 4096, 8192, 16384, 32768, 65536)
+SWEEP_H, SWEEP_M, SWEEP_ROUNDS = 5000, 16, 3
+SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # DRAM bytes per rollout launch on this workload (ncu, profiles/
 # rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the kernel
 # sources are the ones profiled
@@ -77,6 +88,11 @@ def parse():
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
                     help="steps of the probe that pipelines the first two bisection rounds (0: off)")
+    ap.add_argument("--workload", choices=("closed_loop", "sweep"), default="closed_loop")
+    ap.add_argument("--sweep-n", type=str, default=",".join(str(n) for n in SWEEP_N),
+                    help="scenario counts of the sweep")
+    ap.add_argument("--param-unc-rel", type=float, default=None,
+                    help="sweep: half-range of the parameter multipliers (default 0.1; 0 = nominal model)")
     return ap.parse_args()
 
 
@@ -406,10 +422,155 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ sweep --
+SWEEP_METRIC = "trajectory-steps/s vs scenario count (large sweep, FP32 + FP64 recheck)"
+
+
+def sweep_config(ns, W, K):
+    return {"workload": "large sweep on FC3: one robust RG update per step, N_sim in %s, k-section "
+                        "with %d kappa candidates per round, %d rounds, horizon %d RK4 steps (dt=0.01 s), "
+                        "per-step disturbances plus per-scenario parametric uncertainty +-10%% on k_ca, "
+                        "eta_cp, J_cp, eta_cm, R_cm, a_w, a_p; x_t at the %g A equilibrium, r_t = %g A; "
+                        "scenarios redrawn every step (update index = step)"
+                        % (list(ns), SWEEP_M, SWEEP_ROUNDS, SWEEP_H, SWEEP_CASE[0], SWEEP_CASE[1]),
+            "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
+            "timed": "steps [%d, %d) per N" % (W, W + K), "l2": "256 MB written between timed steps"}
+
+
+def sweep_cpu(p, seconds, cores):
+    """The FP64 oracle on a bounded sample of the sweep workload: the 16
+    candidates of a k-section round on the first n scenarios (n sized to
+    ~seconds), full horizon with early exit at a trajectory's first
+    violation; trajectory-steps/s."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    v_prev, r = SWEEP_CASE
+    x_t = O.equilibrium(p, v_prev)
+    kappas = np.linspace(0.0, 1.0, SWEEP_M)
+    n = 16
+    while True:
+        c = O.cfg(H=SWEEP_H, N=n)
+        d = O.sample_disturbances(SEED, 0, n, SWEEP_H, inputs.DIST_AMP)
+        m = O.sample_param_multipliers(SEED, 0, n, inputs.PARAM_UNC_REL, inputs.FC3_UNCERTAIN_MASK)
+        t0 = time.perf_counter()
+        with O.param_multipliers(m):
+            _, _, _, steps = O.eval_candidates(p, c, x_t, v_prev, r, kappas, d, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= 4096:
+            return {"value": steps / dt, "unit": "trajectory-steps/s", "cores": cores, "kind": "oracle",
+                    "sample": "%d scenarios x %d candidates x horizon %d, FP64, %.1f s" % (n, SWEEP_M, SWEEP_H, dt)}
+        n *= 2
+
+
+def run_sweep(args):
+    import numpy as np
+    import torch
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = inputs.fc3_params()
+    W, K = args.warmup, args.steps
+    ns = [int(x) for x in args.sweep_n.split(",") if x]
+    rho = inputs.PARAM_UNC_REL if args.param_unc_rel is None else args.param_unc_rel
+    v_prev, r = SWEEP_CASE
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    clocks = ClockSampler()
+    for N in ns:
+        cfg = R.rrg_config_default(horizon=SWEEP_H, n_scenarios=N, max_candidates=SWEEP_M,
+                                   n_rounds=SWEEP_ROUNDS, search=R.SEARCH_KSECTION,
+                                   precision=R.FP32_RECHECK,
+                                   early_exit=R.EXIT_CANDIDATE, recheck_eps_rel=RECHECK_EPS_REL,
+                                   param_unc_rel=rho, param_unc_mask=inputs.FC3_UNCERTAIN_MASK)
+        g = R.Governor(p, cfg, stream)
+        x_t, _ = g.equilibrium(v_prev)
+        d_x = torch.tensor(x_t, dtype=torch.float64, device=dev)
+        d_r = torch.tensor([r], dtype=torch.float64, device=dev)
+        d_vp = torch.tensor([v_prev], dtype=torch.float64, device=dev)
+        d_out = torch.zeros(2 * (W + K), dtype=torch.float64, device=dev)
+        d_fl = torch.zeros(W + K, dtype=torch.int32, device=dev)
+        for t in range(W):
+            g.sample_scenarios(SEED, t)
+            R.rrg_step_dev(g.h, d_x, d_r, d_vp, d_out[2 * t:2 * t + 1], d_out[2 * t + 1:2 * t + 2], d_fl[t:t + 1])
+        torch.cuda.synchronize()
+        g.reset_stats()
+        g.set_profiling(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        with torch.cuda.stream(stream):
+            for i in range(K):
+                t = W + i
+                flush.fill_(float(t))
+                evs[i][0].record(stream)
+                g.sample_scenarios(SEED, t)
+                R.rrg_step_dev(g.h, d_x, d_r, d_vp, d_out[2 * t:2 * t + 1], d_out[2 * t + 1:2 * t + 2],
+                               d_fl[t:t + 1])
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        secs = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        st = g.stats()
+        g.set_profiling(False)
+        fp32_steps = st["lane_steps"] - st["lane_steps_fp64"]
+        avg_roll_ms = st["rollout_ms"] / max(1, st["timed_rollouts"])
+        achieved = (fp32_steps / max(1, st["timed_rollouts"])) * FLOPS_PER_STEP / (avg_roll_ms * 1e-3) / 1e12
+        kap = d_out.cpu().numpy()[1::2][W:]
+        flags = d_fl.cpu().numpy()[W:]
+        # the same first timed update in plain binary64 (same search), small N only
+        fp64 = None
+        if N <= 8192:
+            cfg64 = R.rrg_config_default(horizon=SWEEP_H, n_scenarios=N, max_candidates=SWEEP_M,
+                                         n_rounds=SWEEP_ROUNDS, search=R.SEARCH_KSECTION, precision=R.FP64,
+                                         early_exit=R.EXIT_CANDIDATE, param_unc_rel=rho,
+                                         param_unc_mask=inputs.FC3_UNCERTAIN_MASK)
+            g64 = R.Governor(p, cfg64, stream)
+            g64.sample_scenarios(SEED, W)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, k64, _ = g64.step(x_t, r, v_prev)
+            fp64 = {"ms_per_update": 1e3 * (time.perf_counter() - t0), "kappa_equal": bool(k64 == kap[0])}
+            g64.close()
+        rows.append({"n_scenarios": N, "updates_per_s": K / secs, "ms_per_update": 1e3 * secs / K,
+                     "trajectory_steps_per_s": st["lane_steps"] / secs,
+                     "nominal_trajectory_steps_per_update": SWEEP_ROUNDS * SWEEP_M * N * SWEEP_H,
+                     "executed_trajectory_steps_per_update": st["lane_steps"] / K,
+                     "rollout_tflops": achieved, "rollout_frac": achieved / FP32_PEAK_TFLOPS,
+                     "rollout_avg_launch_ms": avg_roll_ms, "rechecked": st["rechecked"],
+                     "gpu_launches": st["launches"], "kappa": [float(x) for x in kap],
+                     "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64})
+        g.close()
+        del d_x, d_r, d_vp, d_out, d_fl
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    top = rows[-1]
+    cpu = None if args.no_cpu_baseline else sweep_cpu(p, args.cpu_seconds, os.cpu_count() or 1)
+    out = {
+        "metric": SWEEP_METRIC, "value": top["trajectory_steps_per_s"], "unit": "trajectory-steps/s",
+        "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": top["ms_per_update"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(sweep_config(ns, W, K), param_unc_rel=rho),
+        "roofline": {"bound": "alu", "achieved": top["rollout_tflops"], "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": top["rollout_frac"], "traffic": None,
+                     "kernel": "rollout_kernel<float, parametric>", "n_scenarios": top["n_scenarios"],
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
+        "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
+        "gpu_launches": top["gpu_launches"],
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

@@ -116,7 +116,28 @@ typedef struct {
                                 round 2 is redone (counted in rrg_stats.repairs).
                                 The result is always Alg. 1's.  0 = off;
                                 ignored when >= horizon                       */
+    double  param_unc_rel;   /* parametric uncertainty (the sampled model
+                                uncertainties of Sec. I next to the
+                                disturbances of Eq. 4); 0 = off, else in
+                                (0, 1): scenario k of an update sees every
+                                parameter p set in param_unc_mask scaled by
+                                m_p^k = 1 + rho (2u - 1), rho = param_unc_rel,
+                                u = (w >> 11) 2^-53 with w word p % 4 of
+                                Philox4x64-10(counter = (p / 4, k,
+                                update_index, 2), key = (seed, 0)); drawn with
+                                the disturbances by rrg_sample_scenarios.  The
+                                rollouts, rechecks and the adjoint use theta_p
+                                m_p^k (pressures measured from scenario k's
+                                p_atm); the steady-state check (Eq. 3) and the
+                                simulated plant keep the nominal theta.       */
+    uint32_t param_unc_mask; /* bit p: parameter p is uncertain (bits below
+                                RRG_NPARAM only)                             */
 } rrg_config;
+
+/* FC3 parameters perturbed by default: k_ca, eta_cp, J_cp, eta_cm, R_cm,
+ * a_w, a_p (the air path's dynamics; k_sm, which also scales the OER output
+ * map, stays nominal). */
+#define RRG_PARAM_UNC_MASK_FC3 0x0039c080u
 
 typedef struct rrg_ctx *rrg_handle;
 
@@ -139,7 +160,9 @@ typedef struct {
 /* Fills *cfg with the defaults of the paper's fuel-cell experiment: dt 0.01,
  * H 500, N 32, M 32, N_kappa 12, 3 rounds, SPEC_BISECT, FP32_RECHECK,
  * EXIT_CANDIDATE, ss_check 1, y_min 1.9, eps_ss 0.05, y_c 2.2, recheck band
- * 1e-6, amplitudes (50, 10, 50), probe_steps 128.  Never fails. */
+ * 1e-6, amplitudes (50, 10, 50), probe_steps 128, no parametric
+ * uncertainty (param_unc_rel 0, param_unc_mask RRG_PARAM_UNC_MASK_FC3).
+ * Never fails. */
 void rrg_config_default(rrg_config *cfg);
 
 /* Creates a governor on the current CUDA device.
@@ -172,6 +195,18 @@ const char *rrg_last_error(rrg_handle h);
  * counters wherever they are needed (recheck, rrg_get_scenarios).
  * Asynchronous on the handle's stream. */
 int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index);
+
+/* Copies the per-scenario parameter multipliers of the current scenarios,
+ * m[k * RRG_NPARAM + p], to host m (N * RRG_NPARAM doubles; all 1 when
+ * param_unc_rel = 0 or before the first draw).  Synchronous. */
+int rrg_get_param_multipliers(rrg_handle h, double *m);
+
+/* Loads explicit multipliers m[k * RRG_NPARAM + p] (host, N * RRG_NPARAM
+ * doubles, each finite and > 0; parameters outside param_unc_mask are used
+ * as given too).  RRG_EINVAL unless the handle was created with
+ * param_unc_rel > 0.  The next rrg_sample_scenarios overwrites them.
+ * Synchronous. */
+int rrg_set_param_multipliers(rrg_handle h, const double *m);
 
 /* Loads explicit scenarios instead: d host, 3*H*N doubles (layout above).
  * The binary32 copy is the round-to-nearest of each value.  Synchronous. */
@@ -265,7 +300,9 @@ int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, u
  * (finite), v_prev, r_t (> 0), kappa in [0, 1], checkpoint >= 1, precision
  * RRG_FP64 or RRG_FP32 (arithmetic of both passes).  Host out (each may be
  * NULL): *g, grad[31] = (dg/dkappa, dg/dx_t[3], dg/dtheta[27] in the FC3
- * parameter layout), *k_star, *j_star.  Synchronous. */
+ * parameter layout), *k_star, *j_star.  Under parametric uncertainty
+ * scenario k runs with theta_p m_p^k and dg/dtheta is with respect to the
+ * nominal theta.  Synchronous. */
 int rrg_slack_gradient(rrg_handle h, const double *x_t, double v_prev, double r_t, double kappa,
                        int checkpoint, int precision, double *g, double *grad, int64_t *k_star,
                        int64_t *j_star);
@@ -330,7 +367,9 @@ int rrg_reset_stats(rrg_handle h);
  * keeps the last call's contents; each call re-initialises everything it
  * reads, but calls that may overlap on the GPU (on different streams, or from
  * host threads without ordering between them) race on the scratch and their
- * results are undefined.  Errors: RRG_EINVAL, RRG_ECUDA. */
+ * results are undefined.  Parametric uncertainty is not available here
+ * (param_unc_rel != 0: RRG_ENOTIMPL).  Errors: RRG_EINVAL, RRG_ENOTIMPL,
+ * RRG_ECUDA. */
 #define RRG_STATIC_MAX_CANDIDATES 64
 #define RRG_STATIC_MAX_LANES 131072
 #define RRG_STATIC_SCRATCH_BYTES (1u << 20)

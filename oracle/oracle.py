@@ -91,7 +91,8 @@ def lib():
                                    ctypes.POINTER(_int), _int]
         L.orc_ksection.restype = _d
         L.orc_closed_loop.argtypes = [_p, ctypes.POINTER(OrcCfg), _p, _d, _p, _int, _u64, _u64,
-                                      _p, _p, _int, _int, _int, _int, _int, _p, _p, _p, _p]
+                                      _p, _p, _int, _int, _int, _int, _int, _d, ctypes.c_uint32,
+                                      _p, _p, _p, _p]
         L.orc_closed_loop.restype = _i64
         L.orc_min_slack_argmin.argtypes = [_p, ctypes.POINTER(OrcCfg), _p, _d, _p, ctypes.POINTER(_i64),
                                            ctypes.POINTER(_i64)]
@@ -264,8 +265,9 @@ def ksection(p, c, x_t, v_prev, r, M, rounds, d, nthreads=1):
 
 
 def closed_loop(p, c, x0, v0, r_seq, seed, t0, amp, plant_amp, search=0, n_kappa=12, M=32,
-                rounds=2, nthreads=1):
-    """Closed loop of Fig. 1 under the robust RG; returns (v[T], kappa[T], flags[T], x[T+1,3])."""
+                rounds=2, nthreads=1, param_unc_rel=0.0, param_unc_mask=0):
+    """Closed loop of Fig. 1 under the robust RG; returns (v[T], kappa[T], flags[T], x[T+1,3]).
+    param_unc_rel > 0: each update's scenarios also draw parameter multipliers."""
     p, x0, r_seq, amp, plant_amp = _f64(p), _f64(x0), _f64(r_seq), _f64(amp), _f64(plant_amp)
     T = r_seq.shape[0]
     v = np.zeros(T)
@@ -274,7 +276,8 @@ def closed_loop(p, c, x0, v0, r_seq, seed, t0, amp, plant_amp, search=0, n_kappa
     xs = np.zeros((T + 1, 3))
     lib().orc_closed_loop(_ptr(p), ctypes.byref(c), _ptr(x0), float(v0), _ptr(r_seq), T, int(seed),
                           int(t0), _ptr(amp), _ptr(plant_amp), int(search), int(n_kappa), int(M),
-                          int(rounds), int(nthreads), _ptr(v), _ptr(kap), _ptr(fl), _ptr(xs))
+                          int(rounds), int(nthreads), float(param_unc_rel), int(param_unc_mask),
+                          _ptr(v), _ptr(kap), _ptr(fl), _ptr(xs))
     return v, kap, fl, xs
 
 

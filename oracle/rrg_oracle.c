@@ -568,10 +568,13 @@ double orc_ksection(const double *p, const orc_cfg *c, const double *x_t, double
 int64_t orc_closed_loop(const double *p, const orc_cfg *c, const double *x0, double v0,
                         const double *r_seq, int T, uint64_t seed, uint64_t t0,
                         const double *amp, const double *plant_amp, int search,
-                        int n_kappa, int M, int rounds, int nthreads,
+                        int n_kappa, int M, int rounds, int nthreads, double param_unc_rel,
+                        uint32_t param_unc_mask,
                         double *v_out, double *kappa_out, int *flags_out, double *x_out)
 {
     double *d = (double *)malloc(sizeof(double) * (size_t)(3 * c->H * c->N));
+    double *m = param_unc_rel > 0.0 ? (double *)malloc(sizeof(double) * (size_t)(c->N * O_NPARAM))
+                                    : NULL;
     double x[3] = { x0[0], x0[1], x0[2] }, v = v0;
     int t, i;
     memcpy(x_out, x0, sizeof(double) * 3);
@@ -579,9 +582,17 @@ int64_t orc_closed_loop(const double *p, const orc_cfg *c, const double *x0, dou
         double kap, xn[3], dp[3];
         int fl = 0;
         orc_sample_disturbances(seed, t0 + (uint64_t)t, c->N, c->H, amp, d);
+        /* scenario k of this update also draws its parameter multipliers;
+         * the plant below runs the nominal model */
+        if (m) {
+            orc_sample_param_multipliers(seed, t0 + (uint64_t)t, c->N, param_unc_rel,
+                                         param_unc_mask, m);
+            orc_set_param_multipliers(m);
+        }
         if (search == 0) kap = orc_bisect_joint(p, c, x, v, r_seq[t], n_kappa, d, &fl, nthreads);
         else if (search == 1) kap = orc_alg3(p, c, x, v, r_seq[t], M, d, &fl, nthreads);
         else kap = orc_ksection(p, c, x, v, r_seq[t], M, rounds, d, &fl, nthreads);
+        if (m) orc_set_param_multipliers(NULL);
         v = orc_governed(v, r_seq[t], kap);
         v_out[t] = v; kappa_out[t] = kap; flags_out[t] = fl;
         orc_rk4_step(p, x, v, c->dt, xn);
@@ -590,6 +601,7 @@ int64_t orc_closed_loop(const double *p, const orc_cfg *c, const double *x0, dou
         memcpy(x_out + 3 * (t + 1), x, sizeof(double) * 3);
     }
     free(d);
+    free(m);
     return 0;
 }
 
@@ -649,9 +661,15 @@ static void rk4_step_cs(const cplx *p, const cplx *x, cplx cur, double dt, cplx 
 static cplx slack_cs(const cplx *p, const orc_cfg *c, const cplx *x0, cplx cur, const double *d,
                      int64_t k, int64_t jstar)
 {
-    cplx x[3] = { x0[0], x0[1], x0[2] }, xn[3];
+    cplx x[3] = { x0[0], x0[1], x0[2] }, xn[3], pk[O_NPARAM];
     int64_t j;
     int i;
+    if (g_param_mult) {
+        /* scenario k's parameters theta m^k (the derivative stays the one
+         * with respect to the nominal theta) */
+        for (i = 0; i < O_NPARAM; i++) pk[i] = p[i] * g_param_mult[k * O_NPARAM + i];
+        p = pk;
+    }
     for (j = 0; j < jstar; j++) {
         rk4_step_cs(p, x, cur, c->dt, xn);
         for (i = 0; i < 3; i++)
@@ -667,8 +685,15 @@ double orc_min_slack_argmin(const double *p, const orc_cfg *c, const double *x0,
 {
     double best = INFINITY;
     int64_t kb = -1, jb = -1, k, j;
+    const double *p_nominal = p;
+    double pk[O_NPARAM];
     for (k = 0; k < c->N; k++) {
         double x[3] = { x0[0], x0[1], x0[2] }, xn[3];
+        if (g_param_mult) {
+            int i;
+            for (i = 0; i < O_NPARAM; i++) pk[i] = p_nominal[i] * g_param_mult[k * O_NPARAM + i];
+            p = pk;
+        }
         for (j = 0; j <= c->H; j++) {
             double s = orc_fc3_output(p, x, cur) - c->y_min;
             int i;

@@ -136,12 +136,22 @@ __device__ void rk4_step_vjp(const Fc3K<T>& K, const CandK<T>& C, T dt, T q_ca, 
   l2 = q2 + y2;
 }
 
+// Parameters of scenario k: theta, or theta_p m_p^k under parametric
+// uncertainty (multipliers of scenario pair 0).
+__device__ __forceinline__ void scenario_params(const Launch& L, int k, double* Pk) {
+  for (int p = 0; p < RRG_NPARAM; ++p)
+    Pk[p] = L.pmul ? __dmul_rn(L.params[p], L.pmul[static_cast<size_t>(k) * RRG_NPARAM + p])
+                   : L.params[p];
+}
+
 template <typename T>
-__device__ __forceinline__ Fc3K<T> konst(const Launch& L);
-template <>
-__device__ __forceinline__ Fc3K<double> konst<double>(const Launch& L) { return L.k64; }
-template <>
-__device__ __forceinline__ Fc3K<float> konst<float>(const Launch& L) { return L.k32; }
+__device__ __forceinline__ Fc3K<T> konst(const double* Pk) {
+  Fc3K<double> k64;
+  Fc3K<float> k32;
+  fold_constants(Pk, &k64, &k32);
+  if constexpr (sizeof(T) == 8) return k64;
+  else return k32;
+}
 
 template <typename T>
 __device__ CandK<T> cand_of(const double* P, double I) {
@@ -168,9 +178,11 @@ adjoint_forward_kernel(const Launch L, const double* __restrict__ d, const doubl
   const int N = L.N, H = L.H;
   if (k >= N) return;
   const double v = governed(v_prev, r, kappa);
-  const Fc3K<T> K = konst<T>(L);
-  const CandK<T> C = cand_of<T>(L.params, v);
-  const double p_atm = L.params[P_P_ATM];
+  double Pk[RRG_NPARAM];
+  scenario_params(L, k, Pk);
+  const Fc3K<T> K = konst<T>(Pk);
+  const CandK<T> C = cand_of<T>(Pk, v);
+  const double p_atm = Pk[P_P_ATM];
   T q_ca = static_cast<T>(x_t[0] - p_atm), w = static_cast<T>(x_t[1]),
     q_sm = static_cast<T>(x_t[2] - p_atm);
   const T dt = static_cast<T>(L.dt), y_min = static_cast<T>(L.y_min);
@@ -240,9 +252,10 @@ __global__ void adjoint_reverse_kernel(const Launch L, const double* __restrict_
   const double v = governed(v_prev, r, kappa);
   const int N = L.N, H = L.H;
   const int k = static_cast<int>(kj[0]), jstar = static_cast<int>(kj[1]);
-  const Fc3K<T> K = konst<T>(L);
-  const CandK<T> C = cand_of<T>(L.params, v);
-  const double* P = L.params;
+  double P[RRG_NPARAM];
+  scenario_params(L, k, P);
+  const Fc3K<T> K = konst<T>(P);
+  const CandK<T> C = cand_of<T>(P, v);
   const T dt = static_cast<T>(L.dt);
   const int nseg = H / checkpoint + 1;
   const size_t HN = static_cast<size_t>(H) * N;
@@ -342,7 +355,9 @@ __global__ void adjoint_reverse_kernel(const Launch L, const double* __restrict_
   out[1] = l0;
   out[2] = l1;
   out[3] = l2;
-  for (int i = 0; i < RRG_NPARAM; ++i) out[4 + i] = th[i];
+  // theta'_p = theta_p m_p^{k*}: back to the nominal parameters
+  for (int i = 0; i < RRG_NPARAM; ++i)
+    out[4 + i] = L.pmul ? th[i] * L.pmul[static_cast<size_t>(k) * RRG_NPARAM + i] : th[i];
 }
 
 }  // namespace

@@ -32,6 +32,8 @@ struct rrg_ctx {
   float* d32 = nullptr;
   double* d64b = nullptr;       // second scenario pair, allocated by the first closed loop
   float* d32b = nullptr;
+  double* pmul = nullptr;       // parameter multipliers of each pair (parametric uncertainty)
+  double* pmulb = nullptr;
   cudaStream_t side = nullptr;  // samples update t+1 while update t runs
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool cl_next_ready = false;   // the closed loop's next update is already sampled
@@ -147,6 +149,10 @@ int validate_cfg(const rrg_config* c) {
     if (!is_fin(c->dist_amp[i]) || c->dist_amp[i] < 0.0)
       return set_err(nullptr, RRG_EINVAL, "dist_amp must be finite and >= 0");
   if (c->probe_steps < 0) return set_err(nullptr, RRG_EINVAL, "probe_steps must be >= 0");
+  if (!is_fin(c->param_unc_rel) || c->param_unc_rel < 0.0 || c->param_unc_rel >= 1.0)
+    return set_err(nullptr, RRG_EINVAL, "param_unc_rel must be in [0, 1)");
+  if (c->param_unc_mask >> RRG_NPARAM)
+    return set_err(nullptr, RRG_EINVAL, "param_unc_mask has bits at or above RRG_NPARAM");
   const unsigned long long lanes =
       2ull * static_cast<unsigned long long>(c->max_candidates) * static_cast<unsigned long long>(c->n_scenarios);
   if (lanes >= (1ull << 32)) return set_err(nullptr, RRG_EINVAL, "2 * max_candidates * n_scenarios >= 2^32");
@@ -163,7 +169,8 @@ void free_all(rrg_ctx* h) {
                   h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state,
-                  h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out};
+                  h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
+                  h->pmul, h->pmulb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->io_h) cudaFreeHost(h->io_h);
@@ -211,6 +218,10 @@ void fill_launch(rrg_ctx* h) {
   L.recheck_blocks = 2 * 152;
   L.probe_steps = c.probe_steps;
   L.lane_state = h->lane_state;
+  L.pmul = h->pmul;
+  L.pmulb = h->pmulb;
+  L.punc_rho = c.param_unc_rel;
+  L.punc_mask = c.param_unc_mask;
 }
 
 cudaEvent_t take_event(rrg_ctx* h) {
@@ -338,6 +349,8 @@ void rrg_config_default(rrg_config* c) {
   c->dist_amp[1] = 10.0;
   c->dist_amp[2] = 50.0;
   c->probe_steps = 128;
+  c->param_unc_rel = 0.0;
+  c->param_unc_mask = RRG_PARAM_UNC_MASK_FC3;
 }
 
 const char* rrg_last_error(rrg_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -400,6 +413,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   ALLOC(kap_dev, 2 * M);
   ALLOC(adm_dev, M);
   ALLOC(loop, 1);
+  if (c.param_unc_rel > 0.0) ALLOC(pmul, N * RRG_NPARAM);
 #undef ALLOC
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->io_h), IO_LEN * sizeof(double) + 2 * M * sizeof(double) + M);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->flag_h), 4 * sizeof(int32_t));
@@ -412,6 +426,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   fill_launch(h);
   // the zero scenarios are explicit values (marks pair 0's binary64 array valid)
   if (e == cudaSuccess) e = launch_round_scenarios(h->L);
+  if (e == cudaSuccess && h->pmul) e = launch_fill(h->L, h->pmul, N * RRG_NPARAM, 1.0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? RRG_ENOMEM : RRG_ECUDA;
@@ -463,6 +478,35 @@ int rrg_set_scenarios(rrg_handle h, const double* d) {
   CK(cudaMemcpyAsync(h->d64, d, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(launch_round_scenarios(h->L));
   h->launches++;
+  CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
+}
+
+int rrg_get_param_multipliers(rrg_handle h, double* m) {
+  if (!h) return RRG_EINVAL;
+  if (!m) return set_err(h, RRG_EINVAL, "m is NULL");
+  DeviceGuard g(h->device);
+  const size_t n = static_cast<size_t>(h->cfg.n_scenarios) * RRG_NPARAM;
+  if (!h->pmul) {
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t q = 0; q < n; ++q) m[q] = 1.0;
+    return RRG_OK;
+  }
+  CK(cudaMemcpyAsync(m, h->pmul, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
+}
+
+int rrg_set_param_multipliers(rrg_handle h, const double* m) {
+  if (!h) return RRG_EINVAL;
+  if (!m) return set_err(h, RRG_EINVAL, "m is NULL");
+  if (!h->pmul) return set_err(h, RRG_EINVAL, "the handle has no parametric uncertainty (param_unc_rel = 0)");
+  const size_t n = static_cast<size_t>(h->cfg.n_scenarios) * RRG_NPARAM;
+  for (size_t q = 0; q < n; ++q)
+    if (!is_fin(m[q]) || !(m[q] > 0.0))
+      return set_err(h, RRG_EINVAL, "m[%zu] must be finite and > 0", q);
+  DeviceGuard g(h->device);
+  CK(cudaMemcpyAsync(h->pmul, m, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return RRG_OK;
 }
@@ -599,16 +643,23 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
   if ((x0 && (!x_ok(x0) || !is_fin(v0) || !(v0 > 0.0))) || !x_ok(plant_amp) || !d_r_seq || T < 0)
     return set_err(h, RRG_EINVAL, "x0, v0, plant_amp must be finite, v0 > 0, T >= 0, r_seq non-NULL");
   DeviceGuard g(h->device);
-  // the second scenario pair and the side stream, on first use
-  if (!h->d64b) {
+  // the second scenario pair and the side stream, on first use (each piece
+  // is retried until all exist; the launch descriptor sees none before)
+  if (!h->L.d64b) {
     const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->d64b), n * sizeof(double)));
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->d32b), n * sizeof(float)));
-    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    if (!h->d64b) CK(cudaMalloc(reinterpret_cast<void**>(&h->d64b), n * sizeof(double)));
+    if (!h->d32b) CK(cudaMalloc(reinterpret_cast<void**>(&h->d32b), n * sizeof(float)));
+    if (h->pmul && !h->pmulb) {
+      const size_t np = static_cast<size_t>(h->cfg.n_scenarios) * RRG_NPARAM;
+      CK(cudaMalloc(reinterpret_cast<void**>(&h->pmulb), np * sizeof(double)));
+      CK(launch_fill(h->L, h->pmulb, np, 1.0));
+    }
+    if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     h->L.d64b = h->d64b;
     h->L.d32b = h->d32b;
+    h->L.pmulb = h->pmulb;
   }
   std::memcpy(h->io_h + IO_AMP, plant_amp, 3 * sizeof(double));
   CK(cudaMemcpyAsync(h->io_dev + IO_AMP, h->io_h + IO_AMP, 3 * sizeof(double),

@@ -145,11 +145,70 @@ struct Launch {
   int recheck_blocks;
   int probe_steps;              // steps of a SEG_PROBE segment
   void* lane_state;             // LaneState<T>[m_cap * N] for probed rounds
+  // parametric uncertainty: per-scenario parameter multipliers m[k * NPARAM
+  // + p] of each scenario pair (nullptr when off)
+  double* pmul;
+  double* pmulb;
+  double punc_rho;
+  uint32_t punc_mask;
 };
 
 // Folds the FC3 parameter vector into the constants the kernels use
-// (binary64, then rounded once to binary32).
-void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32);
+// (binary64, then rounded once to binary32).  Only products and quotients
+// occur, so no multiply-add can be fused and host and device agree bit for
+// bit.  Called once per handle on the host and, under parametric
+// uncertainty, once per trajectory on the device.
+__host__ __device__ inline void fold_constants(const double* P, Fc3K<double>* k64,
+                                               Fc3K<float>* k32) {
+  Fc3K<double> K{};
+  K.inv_p_atm = 1.0 / P[P_P_ATM];
+  K.a_w = P[P_A_W];
+  K.a_p = P[P_A_P];
+  K.k_sm = P[P_K_SM];
+  K.k_ca = P[P_K_CA];
+  K.e = (P[P_GAMMA] - 1.0) / P[P_GAMMA];
+  K.C_cp = P[P_C_P] * P[P_T_ATM] / P[P_ETA_CP];
+  K.C_m = P[P_ETA_CM] * P[P_K_T] / P[P_R_CM];
+  K.k_v = P[P_K_V];
+  K.K_p = P[P_K_P];
+  K.RT_Vca = P[P_R_A] * P[P_T_ST] / P[P_V_CA];
+  K.RT_Vsm = P[P_R_A] * P[P_T_ST] / P[P_V_SM];
+  K.inv_J = 1.0 / P[P_J_CP];
+  *k64 = K;
+  Fc3K<float> F{};
+  F.inv_p_atm = static_cast<float>(K.inv_p_atm);
+  F.a_w = static_cast<float>(K.a_w);
+  F.a_p = static_cast<float>(K.a_p);
+  F.k_sm = static_cast<float>(K.k_sm);
+  F.k_ca = static_cast<float>(K.k_ca);
+  F.e = static_cast<float>(K.e);
+  F.C_cp = static_cast<float>(K.C_cp);
+  F.C_m = static_cast<float>(K.C_m);
+  F.k_v = static_cast<float>(K.k_v);
+  F.K_p = static_cast<float>(K.K_p);
+  F.RT_Vca = static_cast<float>(K.RT_Vca);
+  F.RT_Vsm = static_cast<float>(K.RT_Vsm);
+  F.inv_J = static_cast<float>(K.inv_J);
+  *k32 = F;
+}
+
+// Constants of the closed loop at setpoint I (binary64).
+__device__ __forceinline__ CandK<double> cand_consts(const double* __restrict__ P, double I) {
+  CandK<double> C;
+  C.W_o2 = P[P_M_O2] * P[P_N_CELL] * I / (4.0 * P[P_FARADAY]);
+  const double W_ref = P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
+  C.V0 = P[P_C0] + P[P_C1] * I + P[P_C2] * I * I + P[P_K_P] * W_ref;
+  C.y_scale = P[P_X_O2] * P[P_K_SM] / C.W_o2;
+  return C;
+}
+
+__device__ __forceinline__ CandK<float> cand_round(const CandK<double>& C) {
+  CandK<float> F;
+  F.W_o2 = static_cast<float>(C.W_o2);
+  F.V0 = static_cast<float>(C.V0);
+  F.y_scale = static_cast<float>(C.y_scale);
+  return F;
+}
 
 // ---- kernel launchers (rrg_kernels.cu) --------------------------------
 // dual: write the pair (base + *t_dev) & 1 (closed loops with two pairs).
@@ -161,6 +220,7 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
 // lazily (no-op otherwise).
 cudaError_t launch_materialize64(const Launch& L);
 cudaError_t launch_round_scenarios(const Launch& L);
+cudaError_t launch_fill(const Launch& L, double* a, size_t n, double v);
 // buf_base >= 0: the update index is buf_base + *t_dev and selects the
 // scenario pair by its parity; otherwise pair 0
 cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,

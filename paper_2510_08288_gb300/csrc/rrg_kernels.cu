@@ -36,52 +36,6 @@ template <> __device__ __forceinline__ float inf_v<float>() { return __int_as_fl
 template <> __device__ __forceinline__ double inf_v<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
 
 // ---------------------------------------------------------------------------
-// Constant folding (once per handle, on the host; no fused multiply-add can
-// occur in these products and quotients, so host and device would agree).
-void fold_constants(const double* P, Fc3K<double>* k64, Fc3K<float>* k32) {
-  Fc3K<double> K{};
-  K.inv_p_atm = 1.0 / P[P_P_ATM];
-  K.a_w = P[P_A_W];
-  K.a_p = P[P_A_P];
-  K.k_sm = P[P_K_SM];
-  K.k_ca = P[P_K_CA];
-  K.e = (P[P_GAMMA] - 1.0) / P[P_GAMMA];
-  K.C_cp = P[P_C_P] * P[P_T_ATM] / P[P_ETA_CP];
-  K.C_m = P[P_ETA_CM] * P[P_K_T] / P[P_R_CM];
-  K.k_v = P[P_K_V];
-  K.K_p = P[P_K_P];
-  K.RT_Vca = P[P_R_A] * P[P_T_ST] / P[P_V_CA];
-  K.RT_Vsm = P[P_R_A] * P[P_T_ST] / P[P_V_SM];
-  K.inv_J = 1.0 / P[P_J_CP];
-  *k64 = K;
-  Fc3K<float> F{};
-  F.inv_p_atm = static_cast<float>(K.inv_p_atm);
-  F.a_w = static_cast<float>(K.a_w);
-  F.a_p = static_cast<float>(K.a_p);
-  F.k_sm = static_cast<float>(K.k_sm);
-  F.k_ca = static_cast<float>(K.k_ca);
-  F.e = static_cast<float>(K.e);
-  F.C_cp = static_cast<float>(K.C_cp);
-  F.C_m = static_cast<float>(K.C_m);
-  F.k_v = static_cast<float>(K.k_v);
-  F.K_p = static_cast<float>(K.K_p);
-  F.RT_Vca = static_cast<float>(K.RT_Vca);
-  F.RT_Vsm = static_cast<float>(K.RT_Vsm);
-  F.inv_J = static_cast<float>(K.inv_J);
-  *k32 = F;
-}
-
-// Constants of the closed loop at setpoint I (binary64).
-__device__ __forceinline__ CandK<double> cand_consts(const double* __restrict__ P, double I) {
-  CandK<double> C;
-  C.W_o2 = P[P_M_O2] * P[P_N_CELL] * I / (4.0 * P[P_FARADAY]);
-  const double W_ref = P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
-  C.V0 = P[P_C0] + P[P_C1] * I + P[P_C2] * I * I + P[P_K_P] * W_ref;
-  C.y_scale = P[P_X_O2] * P[P_K_SM] / C.W_o2;
-  return C;
-}
-
-// ---------------------------------------------------------------------------
 // Equilibrium manifold (Sec. II-A).  At rest the cathode balance fixes the
 // cathode gauge pressure from the air flow W, the orifice fixes the supply
 // manifold pressure and the compressor map the speed, leaving the shaft
@@ -182,15 +136,35 @@ __device__ __forceinline__ float uniform_sym32(uint64_t w, float a_scaled) {
   return __fmul_rn(__int2float_rn(t), a_scaled);
 }
 
+// Parametric uncertainty: multiplier m_p^k = 1 + rho (2u - 1) of parameter p
+// in scenario k for every p set in mask (1 for the rest), u from word p % 4 of
+// the Philox block at counter (p / 4, k, update, 2).
+constexpr int kParamGroups = (RRG_NPARAM + 3) / 4;
+
+__device__ __forceinline__ void sample_param_group(double* __restrict__ pm, uint64_t k, int g,
+                                                   uint64_t upd, uint64_t seed, double rho,
+                                                   uint32_t mask) {
+  const U64x4 w = philox4x64_10(static_cast<uint64_t>(g), k, upd, 2ull, seed, 0ull);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int p = 4 * g + b;
+    if (p < RRG_NPARAM)
+      pm[k * RRG_NPARAM + p] = ((mask >> p) & 1u) ? __dadd_rn(1.0, uniform_sym(w.w[b], rho)) : 1.0;
+  }
+}
+
 __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
                               double* __restrict__ d64b, float* __restrict__ d32b, int N, int H,
                               uint64_t seed, uint64_t base, const unsigned long long* t_dev,
-                              double a0, double a1, double a2, int write64, SearchState* st) {
+                              double a0, double a1, double a2, int write64, SearchState* st,
+                              double* __restrict__ pm, double* __restrict__ pmb, double rho,
+                              uint32_t mask) {
   const uint64_t upd = base + (t_dev ? *t_dev : 0ull);
   const int pair = (d64b != nullptr && (upd & 1ull)) ? 1 : 0;
   if (pair) {
     d64 = d64b;
     d32 = d32b;
+    pm = pmb;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ScenSrc src;
@@ -220,6 +194,13 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
       d32[2 * HN + q] = uniform_sym32(w.w[2], s2);
     }
   }
+  if (pm != nullptr) {
+    const size_t G = static_cast<size_t>(N) * kParamGroups;
+    for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < G; q += stride) {
+      const uint64_t k = q / kParamGroups;
+      sample_param_group(pm, k, static_cast<int>(q - k * kParamGroups), upd, seed, rho, mask);
+    }
+  }
 }
 
 static int grid_for(size_t n, int threads, int cap) {
@@ -236,7 +217,19 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
   const int write64 = L.precision == RRG_FP64 ? 1 : 0;
   sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, stream ? stream : L.stream>>>(
       L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
-      amp[0], amp[1], amp[2], write64, L.st);
+      amp[0], amp[1], amp[2], write64, L.st, L.pmul, dual ? L.pmulb : nullptr, L.punc_rho,
+      L.punc_mask);
+  return cudaGetLastError();
+}
+
+__global__ void fill_kernel(double* __restrict__ a, size_t n, double v) {
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += stride)
+    a[q] = v;
+}
+
+cudaError_t launch_fill(const Launch& L, double* a, size_t n, double v) {
+  fill_kernel<<<grid_for(n, 256, 152 * 4), 256, 0, L.stream>>>(a, n, v);
   return cudaGetLastError();
 }
 
@@ -394,6 +387,30 @@ __device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
   return smin;
 }
 
+// Scenario k's model under parametric uncertainty: the parameters theta_p
+// m_p^k folded like the nominal ones, and the candidate constants at v.
+// Returns the scenario's p_atm (the origin of its gauge coordinates).
+template <typename T>
+__device__ __forceinline__ double scenario_model(const double* __restrict__ P,
+                                                 const double* __restrict__ m_k, double v,
+                                                 Fc3K<T>& K, CandK<T>& C) {
+  double Pk[RRG_NPARAM];
+#pragma unroll
+  for (int p = 0; p < RRG_NPARAM; ++p) Pk[p] = __dmul_rn(P[p], m_k[p]);
+  Fc3K<double> k64;
+  Fc3K<float> k32;
+  fold_constants(Pk, &k64, &k32);
+  const CandK<double> c64 = cand_consts(Pk, v);
+  if constexpr (sizeof(T) == 8) {
+    K = k64;
+    C = c64;
+  } else {
+    K = k32;
+    C = cand_round(c64);
+  }
+  return Pk[P_P_ATM];
+}
+
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -405,12 +422,14 @@ __device__ __forceinline__ double warp_min(double v) {
 // RRG_FP32_RECHECK: trajectories whose final min slack lies in [-eps, eps)
 // are appended to the recheck list and decided later in binary64.  A
 // SEG_PROBE lane that survives its probe steps saves its state and reports
-// nothing yet; the SEG_CONTINUE lane of the next launch finishes it.
-template <typename T>
-__global__ void __launch_bounds__(kRollThreads)
-rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
-               const T* __restrict__ d_pair1, const CandK<T>* __restrict__ cand, int early_exit,
-               int classify) {
+// nothing yet; the SEG_CONTINUE lane of the next launch finishes it.  PU:
+// parametric uncertainty, each lane folds its scenario's own model constants.
+template <typename T, bool PU>
+__device__ __forceinline__ void rollout_body(const Launch& L, const Fc3K<T>& K0,
+                                             const T* __restrict__ d_pair0,
+                                             const T* __restrict__ d_pair1,
+                                             const CandK<T>* __restrict__ cand, int early_exit,
+                                             int classify) {
   const T* __restrict__ d = L.st->buf ? d_pair1 : d_pair0;
   const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
   const int y = blockIdx.y;
@@ -440,7 +459,8 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
     const int dead0 = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? *dead : 0, 0);
     if (dead0) return;
   }
-  const CandK<T> C = cand[i];
+  CandK<T> C = cand[i];
+  Fc3K<T> K = K0;
   const T eps = static_cast<T>(L.eps_abs);
   const T thr = early_exit != RRG_EXIT_NONE ? (classify ? -eps : T(0)) : -inf_v<T>();
 
@@ -451,7 +471,11 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
     LaneState<T>* ls = mode == SEG_FULL ? nullptr
                                         : static_cast<LaneState<T>*>(L.lane_state) +
                                               static_cast<size_t>(i) * N + k;
-    const double p_atm = L.params[P_P_ATM];
+    double p_atm = L.params[P_P_ATM];
+    if constexpr (PU)
+      p_atm = scenario_model<T>(L.params,
+                                (L.st->buf ? L.pmulb : L.pmul) + static_cast<size_t>(k) * RRG_NPARAM,
+                                L.cand_v[i], K, C);
     T q_ca = static_cast<T>(L.st->x[0] - p_atm), w = static_cast<T>(L.st->x[1]),
       q_sm = static_cast<T>(L.st->x[2] - p_atm);
     T smin0 = inf_v<T>();
@@ -523,16 +547,48 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kRollThreads)
+rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
+               const T* __restrict__ d_pair1, const CandK<T>* __restrict__ cand, int early_exit,
+               int classify) {
+  rollout_body<T, false>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
+}
+
+// Parametric uncertainty: the per-lane constants need about 30 more
+// registers; the binary32 kernel is held to the register budget of
+// RRG_PU_MIN_BLOCKS resident blocks per SM.  Measured on GB300 (65,536
+// scenarios x 16 candidates x 5,000 steps): 4 blocks at 128 registers ran
+// 7 % faster than 5 blocks at 96 registers with spills.
+#ifndef RRG_PU_MIN_BLOCKS
+#define RRG_PU_MIN_BLOCKS 4
+#endif
+template <typename T>
+__global__ void __launch_bounds__(kRollThreads, sizeof(T) == 4 ? RRG_PU_MIN_BLOCKS : 1)
+rollout_pu_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
+                  const T* __restrict__ d_pair1, const CandK<T>* __restrict__ cand, int early_exit,
+                  int classify) {
+  rollout_body<T, true>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
+}
+
 cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
                            bool recheck_classify) {
   dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
+  const int cls = recheck_classify ? 1 : 0;
   if (use_fp64) {
-    rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.d64b,
-                                                                L.cand_k64, early_exit, 0);
+    if (L.pmul)
+      rollout_pu_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.d64b,
+                                                                     L.cand_k64, early_exit, 0);
+    else
+      rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.d64b,
+                                                                  L.cand_k64, early_exit, 0);
   } else {
-    rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.d32b,
-                                                               L.cand_k32, early_exit,
-                                                               recheck_classify ? 1 : 0);
+    if (L.pmul)
+      rollout_pu_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.d32b,
+                                                                    L.cand_k32, early_exit, cls);
+    else
+      rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.d32b,
+                                                                 L.cand_k32, early_exit, cls);
   }
   return cudaGetLastError();
 }
@@ -567,7 +623,7 @@ __device__ double run_lane_philox(const Fc3K<double>& K, const CandK<double>& C,
 
 // Binary64 re-run of the trajectories the binary32 pass could not decide.
 __global__ void __launch_bounds__(64)
-recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
+recheck_kernel(const Launch L, const Fc3K<double> K0, int early_exit) {
   const uint32_t count = *L.recheck_count;
   const int N = L.N;
   const double p_atm = L.params[P_P_ATM];
@@ -582,14 +638,21 @@ recheck_kernel(const Launch L, const Fc3K<double> K, int early_exit) {
     if (L.P == nullptr && !L.cand_ok[i]) continue;
     unsigned steps = 0;
     double smin;
+    Fc3K<double> K = K0;
+    CandK<double> C = L.cand_k64[i];
+    double p_atm_k = p_atm;
+    const double* pm = buf ? L.pmulb : L.pmul;
+    if (pm != nullptr)
+      p_atm_k = scenario_model<double>(L.params, pm + static_cast<size_t>(k) * RRG_NPARAM,
+                                       L.cand_v[i], K, C);
     if (src.d64_valid) {
       int end = 0;
-      double q_ca = L.st->x[0] - p_atm, w = L.st->x[1], q_sm = L.st->x[2] - p_atm;
-      smin = run_lane<double>(K, L.cand_k64[i], buf ? L.d64b : L.d64, k, N, L.H, 0, L.H, q_ca, w,
-                              q_sm, inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps, &end);
+      double q_ca = L.st->x[0] - p_atm_k, w = L.st->x[1], q_sm = L.st->x[2] - p_atm_k;
+      smin = run_lane<double>(K, C, buf ? L.d64b : L.d64, k, N, L.H, 0, L.H, q_ca, w, q_sm,
+                              inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps, &end);
     } else {
-      smin = run_lane_philox(K, L.cand_k64[i], src, k, L.H, L.st->x[0] - p_atm, L.st->x[1],
-                             L.st->x[2] - p_atm, L.dt, L.y_min, thr, &steps);
+      smin = run_lane_philox(K, C, src, k, L.H, L.st->x[0] - p_atm_k, L.st->x[1],
+                             L.st->x[2] - p_atm_k, L.dt, L.y_min, thr, &steps);
     }
     const bool ok = smin >= 0.0;
     if (!ok) L.cand_ok[i] = 0;
@@ -815,11 +878,7 @@ __device__ void prepare_slot(const Launch& L, int i) {
   L.cand_v[i] = v;
   const CandK<double> C = cand_consts(L.params, v);
   L.cand_k64[i] = C;
-  CandK<float> F;
-  F.W_o2 = static_cast<float>(C.W_o2);
-  F.V0 = static_cast<float>(C.V0);
-  F.y_scale = static_cast<float>(C.y_scale);
-  L.cand_k32[i] = F;
+  L.cand_k32[i] = cand_round(C);
   int ok = 1;
   if (L.scfg.ss_check) {
     // binary32 solve first; it decides unless y_ss lands within 1e-4 of the

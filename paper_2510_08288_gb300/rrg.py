@@ -38,6 +38,7 @@ class RrgConfig(ctypes.Structure):
         ("n_bisect", _i32), ("n_rounds", _i32), ("search", _i32), ("precision", _i32),
         ("early_exit", _i32), ("ss_check", _i32), ("y_min", _d), ("eps_ss", _d), ("y_c", _d),
         ("recheck_eps_rel", _d), ("dist_amp", _d * 3), ("probe_steps", _i32),
+        ("param_unc_rel", _d), ("param_unc_mask", ctypes.c_uint32),
     ]
 
 
@@ -70,6 +71,8 @@ def _load():
         "rrg_sample_scenarios": (ctypes.c_int, [_p, _u64, _u64]),
         "rrg_set_scenarios": (ctypes.c_int, [_p, _p]),
         "rrg_get_scenarios": (ctypes.c_int, [_p, _p]),
+        "rrg_get_param_multipliers": (ctypes.c_int, [_p, _p]),
+        "rrg_set_param_multipliers": (ctypes.c_int, [_p, _p]),
         "rrg_eval_candidates": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, _p, _p, _p]),
         "rrg_step": (ctypes.c_int, [_p, _p, _d, _d, _p, _p, _p]),
         "rrg_step_dev": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _p]),
@@ -173,6 +176,17 @@ def rrg_get_scenarios(h, n_scenarios, horizon):
     d = np.zeros((3, horizon, n_scenarios))
     _check(lib.rrg_get_scenarios(h, _ptr(d)), h)
     return d
+
+
+def rrg_get_param_multipliers(h, n_scenarios):
+    m = np.zeros((n_scenarios, NPARAM))
+    _check(lib.rrg_get_param_multipliers(h, _ptr(m)), h)
+    return m
+
+
+def rrg_set_param_multipliers(h, m):
+    m = _f64(m)
+    _check(lib.rrg_set_param_multipliers(h, _ptr(m)), h)
 
 
 def rrg_eval_candidates(h, x_t, v_prev, r_t, kappas, want_P=False, n_scenarios=None):
@@ -321,6 +335,12 @@ class Governor:
 
     def get_scenarios(self):
         return rrg_get_scenarios(self.h, self.cfg.n_scenarios, self.cfg.horizon)
+
+    def get_param_multipliers(self):
+        return rrg_get_param_multipliers(self.h, self.cfg.n_scenarios)
+
+    def set_param_multipliers(self, m):
+        rrg_set_param_multipliers(self.h, m)
 
     def eval_candidates(self, x_t, v_prev, r_t, kappas, want_P=False):
         return rrg_eval_candidates(self.h, x_t, v_prev, r_t, kappas, want_P, self.cfg.n_scenarios)

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -39,11 +40,36 @@ def test_binding_names_match_header():
         assert hasattr(R, n), n
 
 
-def test_config_struct_layout_matches_header():
-    """The ctypes mirror has the size of the C struct (checked via offsets)."""
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a struct of include/rrg.h, as the C compiler
+    lays it out (gcc, the host ABI the binding runs on)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    inc = os.path.join(ROOT, "include")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rrg.h"', 'int main(void) {',
+             '  printf("%%zu\\n", sizeof(%s));' % struct]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["RrgConfig", "RrgStats"])
+def test_struct_layout_matches_c_compiler(name, tmp_path):
+    """The ctypes mirrors have the C compiler's size and field offsets."""
     from paper_2510_08288_gb300 import rrg as R
-    assert ctypes.sizeof(R.RrgConfig) == 8 + 9 * 4 + 4 + 4 * 8 + 3 * 8 + 8
-    assert R.RrgConfig.y_min.offset == 48
+    cls = getattr(R, name)
+    struct = {"RrgConfig": "rrg_config", "RrgStats": "rrg_stats"}[name]
+    fields = [f[0] for f in cls._fields_]
+    size, offs = _c_layout(struct, fields, tmp_path)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
 
 
 def test_config_defaults_and_create_validation_without_gpu():
@@ -61,6 +87,25 @@ def test_config_defaults_and_create_validation_without_gpu():
         R.rrg_create(inputs.fc3_params()[:5], c)
     with pytest.raises(R.RrgError):
         R.rrg_create(inputs.fc3_params(), R.rrg_config_default(search=R.SEARCH_GRID, max_candidates=1))
+    # parametric uncertainty: rho in [0, 1), mask within the parameter vector
+    assert c.param_unc_rel == 0.0 and c.param_unc_mask == inputs.FC3_UNCERTAIN_MASK
+    for kw in (dict(param_unc_rel=1.0), dict(param_unc_rel=-0.1), dict(param_unc_rel=float("nan")),
+               dict(param_unc_rel=0.1, param_unc_mask=1 << 27)):
+        with pytest.raises(R.RrgError) as e:
+            R.rrg_create(inputs.fc3_params(), R.rrg_config_default(**kw))
+        assert e.value.code == R.RRG_EINVAL and "param_unc" in str(e.value)
+
+
+def test_static_entry_rejects_parametric_uncertainty_without_gpu():
+    """The allocation-free entry point has no multiplier storage: it refuses
+    param_unc_rel != 0 before touching the device."""
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+    p = np.ascontiguousarray(inputs.fc3_params())
+    cfg = R.rrg_config_default(param_unc_rel=0.1)
+    rc = R.lib.rrg_eval_candidates_static(p.ctypes.data_as(ctypes.c_void_p), 27, ctypes.byref(cfg), None,
+                                          None, None, None, 100.0, 200.0, None, 1, None, None)
+    assert rc == R.RRG_ENOTIMPL and "parametric" in R.rrg_last_error(None)
 
 
 def test_oracle_and_library_share_no_code():

@@ -389,7 +389,7 @@ def test_param_multipliers_scale_scenario_parameters(orc, params):
     c = orc.cfg(H=H, N=N, early_exit=0)
     x = orc.equilibrium(params, 120.0)
     d = orc.sample_disturbances(1, 0, N, H, inputs.DIST_AMP)
-    m = orc.sample_param_multipliers(1, 0, N, 0.1, inputs.FC3_UNCERTAIN_MASK)
+    m = orc.sample_param_multipliers(1, 0, N, 0.1, (1 << orc.nparam()) - 1)
     nominal = [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)]
     with orc.param_multipliers(m):
         scaled = [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)]
