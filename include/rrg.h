@@ -379,6 +379,69 @@ int rrg_eval_candidates_static(const double *model_params, int n_params, const r
                                const double *d_kappas, int m, uint8_t *d_admissible,
                                double *d_min_slack);
 
+/* ------------------------------------------------------------------------ */
+/* Batched instances: S independent robust RG problems (instance s with its
+ * own N_s scenarios and horizon H_s) that share the model, dt, the search and
+ * its settings, advanced together by one fixed launch sequence per update.
+ * The trajectories of all instances' candidates are tiles (instance,
+ * candidate, block of scenarios) of one persistent rollout launch per search
+ * round, taken from a queue in longest-horizon-first order.  Instance s draws
+ * its scenarios exactly as rrg_sample_scenarios with seed + s (mod 2^64), and
+ * its simulated plant disturbance as rrg_plant_step with seed + s.  Search:
+ * RRG_SEARCH_GRID (Alg. 3) or RRG_SEARCH_KSECTION with max_candidates per
+ * instance and round; precision RRG_FP32_RECHECK; no parametric uncertainty
+ * (otherwise RRG_ENOTIMPL).  Each instance's result equals rrg_step's for
+ * the same inputs and scenarios. */
+#define RRG_BATCH_MAX_INSTANCES 1024
+#define RRG_BATCH_VARIANTS 6   /* rollout variants: lanes per tile {64, 128,
+                                  256} x disturbance prefetch depth {8, 16} */
+typedef struct rrg_batch_ctx *rrg_batch_handle;
+
+/* cfg as for rrg_create (n_scenarios and horizon are ignored); n_scenarios
+ * and horizons: host arrays of n_instances values >= 1; sum over instances of
+ * max_candidates * N_s must be below 2^31.  Allocates 12 sum(H_s N_s) bytes of
+ * scenarios plus O(sum M N_s) bytes of recheck list. */
+int rrg_batch_create(const double *model_params, int n_params, const rrg_config *cfg,
+                     int n_instances, const int32_t *n_scenarios, const int32_t *horizons,
+                     void *cuda_stream, rrg_batch_handle *out);
+int rrg_batch_destroy(rrg_batch_handle h);
+const char *rrg_batch_last_error(rrg_batch_handle h);
+
+/* One update of every instance from device inputs: d_x[3 S] (instance s at
+ * 3 s), d_r[S], d_v_prev[S]; draws the scenarios of update_index, searches,
+ * and writes d_v_t[S], d_kappa[S], d_flags[S] (each may be NULL; flags as
+ * rrg_step).  An instance with non-finite or non-positive inputs holds
+ * (kappa 0, flag bit 1).  Asynchronous on the handle's stream. */
+int rrg_batch_step_dev(rrg_batch_handle h, const double *d_x, const double *d_r,
+                       const double *d_v_prev, uint64_t seed, uint64_t update_index,
+                       double *d_v_t, double *d_kappa, int32_t *d_flags);
+
+/* T closed-loop updates of every instance on the device (as
+ * rrg_closed_loop_dev per instance): d_x0[3 S], d_v0[S] start the loop (NULL
+ * d_x0: continue the previous call's loop), d_r_seq[t S + s] (t counted from
+ * the loop start), plant_amp host[3]; outputs at [t S + s] (d_x_out at
+ * [((t + 1) S + s) 3], the start at t = 0), each may be NULL.  use_graph: one
+ * update is captured once and replayed (the graph is kept while pointers,
+ * seed, t0 and the rollout variant stay the same).  Asynchronous. */
+int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double *d_x0, const double *d_v0,
+                              const double *d_r_seq, int T, uint64_t seed, uint64_t t0,
+                              const double *plant_amp, int use_graph, double *d_v_out,
+                              double *d_kappa_out, int32_t *d_flags_out, double *d_x_out);
+
+/* Autotuner: runs 1 + repeats updates on the given inputs with each rollout
+ * variant, times the rollout launches (CUDA events), keeps the fastest and
+ * returns it in *variant_out; ms_out (optional, RRG_BATCH_VARIANTS doubles)
+ * receives each variant's mean rollout time per update.  Results do not
+ * depend on the variant.  Synchronous. */
+int rrg_batch_autotune(rrg_batch_handle h, const double *d_x, const double *d_r,
+                       const double *d_v_prev, uint64_t seed, uint64_t update_index, int repeats,
+                       int *variant_out, double *ms_out);
+int rrg_batch_set_variant(rrg_batch_handle h, int variant);
+int rrg_batch_get_variant(rrg_batch_handle h, int *variant, int *tile_lanes, int *prefetch);
+int rrg_batch_set_profiling(rrg_batch_handle h, int on);
+int rrg_batch_get_stats(rrg_batch_handle h, rrg_stats *out);
+int rrg_batch_reset_stats(rrg_batch_handle h);
+
 #ifdef __cplusplus
 }
 #endif

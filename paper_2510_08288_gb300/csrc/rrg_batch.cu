@@ -1,0 +1,994 @@
+// rrg_batch.cu -- many independent robust RG problems in one set of launches.
+//
+// S instances, each with its own scenario count N_s and horizon H_s, share
+// the model and the search settings.  One update of all of them is a fixed
+// launch sequence (CUDA-graph capturable):
+//
+//   batch_sample_kernel      d_j^k of every instance (grid y = instance)
+//   batch_begin_kernel       inputs, round-1 candidates (Alg. 3 grid, Eq. 5),
+//                            the round's tile list
+//   { batch_prepare_kernel   v_i (Eq. 2), candidate constants, steady-state
+//                            check (Eq. 3); one thread per (instance, slot)
+//     batch_rollout_kernel   persistent: each CTA takes the next tile
+//                            (instance, candidate, block of scenarios) from a
+//                            queue ordered longest horizon first, and runs
+//                            its trajectories as the single-problem rollout
+//     batch_recheck_kernel   binary64 re-run of near-zero-slack lanes
+//     batch_decide_kernel }  Alg. 3 / k-section decision per instance, the
+//                            next round's candidates and tile list
+//   batch_plant_kernel       simulated plants (closed loop only)
+//
+// The tile queue is one atomic counter; a CTA never waits for another.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "rrg_device.cuh"
+#include "rrg_internal.h"
+#include "rrg_lane.cuh"
+
+namespace rrg {
+namespace {
+
+constexpr int kMaxInst = RRG_BATCH_MAX_INSTANCES;
+constexpr int kDecideThreads = 1024;
+static_assert(kMaxInst <= kDecideThreads, "one decision thread per instance");
+
+struct BInst {
+  int32_t N, H;
+  long long off;  // element offset of the instance's [3][H][N] binary32 scenarios
+};
+
+struct BState {
+  double x[3];
+  double v_prev, r;
+  double lo, hi, kappa_opt;
+  double v_out;
+  int32_t m, round, any, done, invalid, flags;
+  unsigned long long seed, update;
+};
+
+struct BCfg {
+  int S, M, n_rounds, search, ss_check, early_exit;
+  double dt, y_min, eps_ss, y_c, eps_abs;
+  double amp[3];
+};
+
+struct BLaunch {
+  cudaStream_t stream;
+  BCfg c;
+  const double* params;
+  Fc3K<double> k64;
+  Fc3K<float> k32;
+  RhsU<double> u64;
+  RhsU<float> u32;
+  const BInst* inst;
+  const int32_t* order;  // instances, longest horizon (then most scenarios) first
+  BState* st;
+  float* d32;
+  double* cand_kappa;
+  double* cand_v;
+  RhsC<double>* cand_c64;
+  RhsC<float>* cand_c32;
+  int32_t* cand_ok;
+  int32_t* cand_dead;
+  int32_t* cand_ss;
+  unsigned long long* cand_min;
+  int32_t* tile_base;  // [S + 1] over `order`
+  uint32_t* queue;     // [0] next tile, [1] tiles of the round
+  uint2* recheck_list; // (slot, k)
+  uint32_t* recheck_count;
+  unsigned long long recheck_cap;
+  DevStats* stats;
+  unsigned long long* t_dev;  // closed-loop update counter
+};
+
+// ---------------------------------------------------------------------------
+// Sampling: instance s draws with key (seed + s, 0) and the counters of the
+// single-problem sampler; only the binary32 copy is stored (the recheck
+// regenerates binary64 values from the same counters).
+__global__ void batch_sample_kernel(const BLaunch B, uint64_t seed, uint64_t base) {
+  const int s = blockIdx.y;
+  const BInst I = B.inst[s];
+  const uint64_t upd = base + (B.t_dev ? *B.t_dev : 0ull);
+  const uint64_t key = seed + static_cast<uint64_t>(s);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    B.st[s].seed = key;
+    B.st[s].update = upd;
+  }
+  const size_t HN = static_cast<size_t>(I.H) * I.N;
+  float* d = B.d32 + I.off;
+  const float s0 = static_cast<float>(B.c.amp[0] * 0x1.0p-23),
+              s1 = static_cast<float>(B.c.amp[1] * 0x1.0p-23),
+              s2 = static_cast<float>(B.c.amp[2] * 0x1.0p-23);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
+    const uint64_t j = q / static_cast<uint64_t>(I.N), k = q - j * static_cast<uint64_t>(I.N);
+    const U64x4 w = philox4x64_10(j, k, upd, 0ull, key, 0ull);
+    d[q] = uniform_sym32(w.w[0], s0);
+    d[HN + q] = uniform_sym32(w.w[1], s1);
+    d[2 * HN + q] = uniform_sym32(w.w[2], s2);
+  }
+}
+
+// Tile list of the next round: instance order[o] contributes m x ceil(N / tile)
+// tiles; block-wide inclusive scan (blockDim = kDecideThreads >= S).
+__device__ void build_tiles(const BLaunch& B, int tile) {
+  __shared__ int sc[kDecideThreads];
+  const int o = threadIdx.x;
+  int cnt = 0;
+  if (o < B.c.S) {
+    const int s = B.order[o];
+    const BState& st = B.st[s];
+    cnt = (st.done ? 0 : st.m) * ((B.inst[s].N + tile - 1) / tile);
+  }
+  sc[o] = cnt;
+  __syncthreads();
+  for (int d = 1; d < kDecideThreads; d <<= 1) {
+    const int v = o >= d ? sc[o - d] : 0;
+    __syncthreads();
+    sc[o] += v;
+    __syncthreads();
+  }
+  if (o < B.c.S) B.tile_base[o + 1] = sc[o];
+  if (o == 0) {
+    B.tile_base[0] = 0;
+    B.queue[0] = 0u;
+    B.queue[1] = static_cast<uint32_t>(sc[B.c.S - 1]);
+    *B.recheck_count = 0u;
+  }
+}
+
+// Round 1: inputs (device arrays; NULL x / v_prev: the closed loop's state),
+// Alg. 3's grid, the tile list.  r is read at r[t * S + s] (t = the loop
+// counter, 0 without one).
+__global__ void __launch_bounds__(kDecideThreads)
+batch_begin_kernel(const BLaunch B, const double* __restrict__ d_x, const double* __restrict__ d_r,
+                   const double* __restrict__ d_vp, int tile) {
+  const int s = threadIdx.x;
+  const unsigned long long t = B.t_dev ? *B.t_dev : 0ull;
+  if (s < B.c.S) {
+    BState& st = B.st[s];
+    if (d_x) {
+      st.x[0] = d_x[3 * s];
+      st.x[1] = d_x[3 * s + 1];
+      st.x[2] = d_x[3 * s + 2];
+    }
+    if (d_vp) st.v_prev = d_vp[s];
+    st.r = d_r[t * static_cast<unsigned long long>(B.c.S) + s];
+    const bool ok = isfinite(st.x[0]) && isfinite(st.x[1]) && isfinite(st.x[2]) &&
+                    isfinite(st.v_prev) && isfinite(st.r) && st.v_prev > 0.0 && st.r > 0.0;
+    st.invalid = ok ? 0 : 1;
+    st.lo = 0.0;
+    st.hi = 1.0;
+    st.kappa_opt = 0.0;
+    st.any = 0;
+    st.round = 0;
+    st.flags = 0;
+    st.done = ok ? 0 : 1;
+    st.m = ok ? grid_points(B.cand_kappa + static_cast<size_t>(s) * B.c.M, B.c.M) : 0;
+  }
+  __syncthreads();
+  build_tiles(B, tile);
+}
+
+// v_i, candidate constants and the steady-state check of one (instance, slot).
+__global__ void batch_prepare_kernel(const BLaunch B) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = B.c.M;
+  const int s = idx / M, i = idx - s * M;
+  if (s >= B.c.S) return;
+  const BState& st = B.st[s];
+  if (st.done || i >= st.m) return;
+  const size_t slot = static_cast<size_t>(s) * M + i;
+  const double v = governed(st.v_prev, st.r, B.cand_kappa[slot]);
+  B.cand_v[slot] = v;
+  const CandK<double> C = cand_consts(B.params, v);
+  fold_rhs_cand(B.k64, C, B.cand_c64 + slot, B.cand_c32 + slot);
+  int ok = 1;
+  if (B.c.ss_check) {
+    const double thr = __dadd_rn(B.c.y_min, __dmul_rn(B.c.eps_ss, __dsub_rn(B.c.y_c, B.c.y_min)));
+    float q32[3], y32 = 0.0f;
+    const int rc32 = equilibrium_dev<float>(B.k32, B.params, v, q32, &y32);
+    if (rc32 == 0 && fabs(static_cast<double>(y32) - thr) > 1e-4 * (1.0 + fabs(thr))) {
+      ok = static_cast<double>(y32) >= thr;
+    } else {
+      double q[3], y_ss = 0.0;
+      ok = (equilibrium_dev<double>(B.k64, B.params, v, q, &y_ss) == 0) && (y_ss >= thr);
+    }
+  }
+  B.cand_ok[slot] = ok;
+  B.cand_ss[slot] = ok;
+  B.cand_dead[slot] = ok ? 0 : 1;
+  B.cand_min[slot] = dkey(inf_v<double>());
+}
+
+// One tile: lanes k of candidate slot (s, i), binary32 rollouts classified
+// for the binary64 recheck, reduced into the candidate's flags.  Called by
+// every thread of the CTA; returns are warp- or CTA-uniform.
+template <int PF>
+__device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k) {
+  const BInst I = B.inst[s];
+  const size_t slot = static_cast<size_t>(s) * B.c.M + i;
+  if (!B.cand_ss[slot]) return;
+  volatile int32_t* dead = B.cand_dead + slot;
+  const bool cand_stop = B.c.early_exit == RRG_EXIT_CANDIDATE;
+  if (cand_stop) {
+    const int dead0 = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? *dead : 0, 0);
+    if (dead0) return;
+  }
+  const bool active = k < I.N;
+  const float eps = static_cast<float>(B.c.eps_abs);
+  const float thr = B.c.early_exit != RRG_EXIT_NONE ? -eps : -inf_v<float>();
+  float smin = inf_v<float>();
+  unsigned steps = 0;
+  if (active) {
+    const BState& st = B.st[s];
+    const double p_atm = B.params[P_P_ATM];
+    float q_ca = static_cast<float>(st.x[0] - p_atm), w = static_cast<float>(st.x[1]),
+          q_sm = static_cast<float>(st.x[2] - p_atm);
+    int end = LANE_REACHED_END;
+    smin = run_lane<float, PF>(B.u32, B.cand_c32[slot], B.d32 + I.off, k, I.N, I.H, 0, I.H, q_ca,
+                               w, q_sm, inf_v<float>(), static_cast<float>(B.c.dt),
+                               static_cast<float>(B.c.y_min), thr, cand_stop ? dead : nullptr,
+                               &steps, &end);
+    if (cand_stop && smin < thr) *dead = 1;
+  }
+  bool lane_ok = true, uncertain = false;
+  double contrib = static_cast<double>(inf_v<float>());
+  if (active) {
+    if (smin >= eps) {
+      contrib = smin;
+    } else if (smin < -eps) {
+      lane_ok = false;
+      contrib = smin;
+    } else {
+      uncertain = true;
+    }
+  }
+  if (uncertain && *dead == 0) {
+    const uint32_t e = atomicAdd(B.recheck_count, 1u);
+    if (e < B.recheck_cap) B.recheck_list[e] = make_uint2(static_cast<uint32_t>(slot), static_cast<uint32_t>(k));
+  }
+  const bool all_ok = __all_sync(0xffffffffu, lane_ok);
+  const double wmin = warp_min(contrib);
+  const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
+  if ((threadIdx.x & 31) == 0) {
+    if (!all_ok) B.cand_ok[slot] = 0;
+    if (wmin < static_cast<double>(inf_v<float>())) atomicMin(B.cand_min + slot, dkey(wmin));
+    if (wsteps) atomicAdd(&B.stats->lane_steps, static_cast<unsigned long long>(wsteps));
+  }
+}
+
+// Persistent rollout: each CTA takes tiles from the queue until none is left.
+template <int TILE, int PF>
+__global__ void __launch_bounds__(TILE) batch_rollout_kernel(const BLaunch B) {
+  __shared__ int sh[3];
+  const uint32_t total = B.queue[1];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(B.queue, 1u);
+      int s = -1, i = 0, b = 0;
+      if (t < total) {
+        // tile_base[lo] <= t < tile_base[hi]; instances without tiles have
+        // equal bases and are skipped by taking the last such lo
+        int lo = 0, hi = B.c.S;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (static_cast<uint32_t>(B.tile_base[mid]) <= t) lo = mid; else hi = mid;
+        }
+        s = B.order[lo];
+        const int nb = (B.inst[s].N + TILE - 1) / TILE;
+        const int local = static_cast<int>(t) - B.tile_base[lo];
+        i = local / nb;
+        b = local - i * nb;
+      }
+      sh[0] = s;
+      sh[1] = i;
+      sh[2] = b;
+    }
+    __syncthreads();
+    const int s = sh[0], i = sh[1], b = sh[2];
+    __syncthreads();
+    if (s < 0) return;
+    batch_tile<PF>(B, s, i, b * TILE + static_cast<int>(threadIdx.x));
+  }
+}
+
+// Binary64 re-run (disturbances regenerated from the Philox counters).
+__global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
+  const uint32_t count = min(*B.recheck_count, static_cast<uint32_t>(B.recheck_cap));
+  const double p_atm = B.params[P_P_ATM];
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    const uint2 en = B.recheck_list[e];
+    const size_t slot = en.x;
+    const int k = static_cast<int>(en.y);
+    if (!B.cand_ok[slot]) continue;
+    const int s = static_cast<int>(slot / B.c.M);
+    const BState& st = B.st[s];
+    ScenSrc src;
+    src.d64_valid = 0;
+    src.pad = 0;
+    src.seed = st.seed;
+    src.update = st.update;
+    src.amp[0] = B.c.amp[0];
+    src.amp[1] = B.c.amp[1];
+    src.amp[2] = B.c.amp[2];
+    unsigned steps = 0;
+    const double smin = run_lane_philox(B.u64, B.cand_c64[slot], src, k, B.inst[s].H,
+                                        st.x[0] - p_atm, st.x[1], st.x[2] - p_atm, B.c.dt,
+                                        B.c.y_min,
+                                        B.c.early_exit != RRG_EXIT_NONE ? 0.0 : -inf_v<double>(),
+                                        &steps);
+    if (!(smin >= 0.0)) B.cand_ok[slot] = 0;
+    atomicMin(B.cand_min + slot, dkey(smin));
+    atomicAdd(&B.stats->lane_steps, static_cast<unsigned long long>(steps));
+    atomicAdd(&B.stats->lane_steps_fp64, static_cast<unsigned long long>(steps));
+    atomicAdd(&B.stats->rechecked, 1ull);
+  }
+}
+
+// Alg. 3 / k-section decision from the evaluated round (as the
+// single-problem search), the next round's candidates and tiles; `final`
+// also writes every instance's result at index t * S + s.
+__global__ void __launch_bounds__(kDecideThreads)
+batch_decide_kernel(const BLaunch B, int final, int tile, double* __restrict__ v_out,
+                    double* __restrict__ k_out, int32_t* __restrict__ f_out) {
+  const int s = threadIdx.x;
+  const int M = B.c.M;
+  if (s < B.c.S) {
+    BState& st = B.st[s];
+    double* kap = B.cand_kappa + static_cast<size_t>(s) * M;
+    const int32_t* ok = B.cand_ok + static_cast<size_t>(s) * M;
+    if (!st.done && st.m > 0) {
+      const int m = st.m;
+      int best = -1;
+      for (int i = 0; i < m; ++i)
+        if (ok[i]) best = i;
+      int next = 0;
+      if (B.c.search == RRG_SEARCH_GRID) {
+        if (best >= 0) { st.kappa_opt = kap[best]; st.any = 1; }
+        st.done = 1;
+      } else if (st.round == 0 && (best < 0 || best == m - 1)) {
+        if (best >= 0) { st.kappa_opt = kap[best]; st.any = 1; }
+        st.done = 1;
+      } else {
+        if (st.round == 0) {
+          st.any = 1;
+          st.kappa_opt = kap[best];
+          st.lo = kap[best];
+          st.hi = kap[best + 1];
+        } else if (best < 0) {
+          st.hi = kap[0];
+        } else {
+          st.kappa_opt = kap[best];
+          st.lo = kap[best];
+          if (best < m - 1) st.hi = kap[best + 1];
+        }
+        if (st.round + 1 >= B.c.n_rounds) st.done = 1;
+        else next = interior_points(kap, M, st.lo, st.hi);
+      }
+      st.round += 1;
+      st.m = st.done ? 0 : next;
+    }
+    if (final) {
+      st.done = 1;
+      st.m = 0;
+      st.flags = (st.any ? 0 : 1) | (st.invalid ? 2 : 0);
+      const double kk = st.invalid ? 0.0 : st.kappa_opt;
+      st.kappa_opt = kk;
+      st.v_out = st.invalid ? st.v_prev : governed(st.v_prev, st.r, kk);
+      const unsigned long long o =
+          (B.t_dev ? *B.t_dev : 0ull) * static_cast<unsigned long long>(B.c.S) + s;
+      if (v_out) v_out[o] = st.v_out;
+      if (k_out) k_out[o] = kk;
+      if (f_out) f_out[o] = st.flags;
+    }
+  }
+  __syncthreads();
+  build_tiles(B, tile);
+}
+
+// Simulated plants: x_{t+1} = RK4(x_t, v_t) + d_plant(seed + s, update),
+// then the loop counter advances (one block).
+__global__ void __launch_bounds__(kDecideThreads)
+batch_plant_kernel(const BLaunch B, uint64_t seed, uint64_t base, const double* __restrict__ amp,
+                   double* __restrict__ x_out) {
+  const int s = threadIdx.x;
+  const unsigned long long t = *B.t_dev;
+  if (s < B.c.S) {
+    BState& st = B.st[s];
+    const double v = st.v_out;
+    const double p_atm = B.params[P_P_ATM];
+    double q_ca = st.x[0] - p_atm, w = st.x[1], q_sm = st.x[2] - p_atm;
+    const CandK<double> C = cand_consts(B.params, v);
+    rk4_step<double>(B.k64, C, B.c.dt, q_ca, w, q_sm);
+    const U64x4 r = philox4x64_10(0ull, 0ull, base + t, 1ull, seed + static_cast<uint64_t>(s), 0ull);
+    st.x[0] = (q_ca + p_atm) + uniform_sym(r.w[0], amp[0]);
+    st.x[1] = w + uniform_sym(r.w[1], amp[1]);
+    st.x[2] = (q_sm + p_atm) + uniform_sym(r.w[2], amp[2]);
+    st.v_prev = v;
+    if (x_out) {
+      double* xo = x_out + ((t + 1) * static_cast<unsigned long long>(B.c.S) + s) * 3;
+      xo[0] = st.x[0];
+      xo[1] = st.x[1];
+      xo[2] = st.x[2];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *B.t_dev = t + 1;
+}
+
+__global__ void batch_loop_init_kernel(const BLaunch B, const double* __restrict__ x0,
+                                       const double* __restrict__ v0, double* __restrict__ x_out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *B.t_dev = 0ull;
+  if (s >= B.c.S) return;
+  BState& st = B.st[s];
+  st.x[0] = x0[3 * s];
+  st.x[1] = x0[3 * s + 1];
+  st.x[2] = x0[3 * s + 2];
+  st.v_prev = v0[s];
+  if (x_out) {
+    x_out[3 * s] = st.x[0];
+    x_out[3 * s + 1] = st.x[1];
+    x_out[3 * s + 2] = st.x[2];
+  }
+}
+
+// Rollout variants the autotuner chooses from: threads (= scenario lanes)
+// per tile, and the disturbance prefetch depth.
+struct Variant {
+  int tile, pf;
+  void (*kernel)(const BLaunch);
+};
+const Variant kVariants[RRG_BATCH_VARIANTS] = {
+    {64, 8, batch_rollout_kernel<64, 8>},   {64, 16, batch_rollout_kernel<64, 16>},
+    {128, 8, batch_rollout_kernel<128, 8>}, {128, 16, batch_rollout_kernel<128, 16>},
+    {256, 8, batch_rollout_kernel<256, 8>}, {256, 16, batch_rollout_kernel<256, 16>},
+};
+
+}  // namespace
+}  // namespace rrg
+
+using namespace rrg;
+
+struct rrg_batch_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  rrg_config cfg{};
+  double params[RRG_NPARAM]{};
+  BLaunch B{};
+  std::vector<BInst> inst;
+  int variant = 3;             // 128 lanes per tile, prefetch 16
+  int grid[RRG_BATCH_VARIANTS]{};
+  size_t lanes = 0;            // sum of M N_s
+  // device memory
+  double* params_dev = nullptr;
+  BInst* inst_dev = nullptr;
+  int32_t* order_dev = nullptr;
+  BState* st = nullptr;
+  float* d32 = nullptr;
+  double* cand_kappa = nullptr;
+  double* cand_v = nullptr;
+  RhsC<double>* cand_c64 = nullptr;
+  RhsC<float>* cand_c32 = nullptr;
+  int32_t* cand_ok = nullptr;
+  int32_t* cand_dead = nullptr;
+  int32_t* cand_ss = nullptr;
+  unsigned long long* cand_min = nullptr;
+  int32_t* tile_base = nullptr;
+  uint32_t* queue = nullptr;
+  uint2* recheck_list = nullptr;
+  uint32_t* recheck_count = nullptr;
+  DevStats* stats = nullptr;
+  unsigned long long* t_dev = nullptr;
+  double* amp_dev = nullptr;
+  double* io_h = nullptr;      // pinned staging for the plant amplitudes
+  // graph of one closed-loop update
+  cudaGraphExec_t cl_exec = nullptr;
+  const void* cl_key[5] = {};
+  uint64_t cl_key_seed = 0, cl_key_t0 = 0;
+  int cl_key_variant = -1;
+  uint64_t cl_per = 0, cl_rl_per = 0;
+  // counters and profiling
+  uint64_t launches = 0, rollout_launches = 0, rounds = 0;
+  bool profiling = false, capturing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_roll;
+  double rollout_ms = 0.0;
+  uint64_t timed_rollouts = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+int bset_err(rrg_batch_ctx* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf; else g_batch_create_error = buf;
+  return code;
+}
+
+#define BCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return bset_err(h, RRG_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+struct BDeviceGuard {
+  int prev = -1;
+  explicit BDeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~BDeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+void bfree_all(rrg_batch_ctx* h) {
+  void* ptrs[] = {h->params_dev, h->inst_dev, h->order_dev, h->st, h->d32, h->cand_kappa,
+                  h->cand_v, h->cand_c64, h->cand_c32, h->cand_ok, h->cand_dead, h->cand_ss,
+                  h->cand_min, h->tile_base, h->queue, h->recheck_list, h->recheck_count,
+                  h->stats, h->t_dev, h->amp_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->io_h) cudaFreeHost(h->io_h);
+  for (auto& e : h->ev_free) cudaEventDestroy(e);
+  for (auto& pr : h->ev_roll) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (h->cl_exec) cudaGraphExecDestroy(h->cl_exec);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+cudaEvent_t btake_event(rrg_batch_ctx* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Folds the timed rollout launches into rollout_ms (after a synchronize).
+void bcollect(rrg_batch_ctx* h) {
+  for (auto& pr : h->ev_roll) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+      h->rollout_ms += ms;
+      h->timed_rollouts++;
+    }
+    h->ev_free.push_back(pr.first);
+    h->ev_free.push_back(pr.second);
+  }
+  h->ev_roll.clear();
+}
+
+int enqueue_rollout(rrg_batch_ctx* h) {
+  const Variant& v = kVariants[h->variant];
+  const bool timed = h->profiling && !h->capturing;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (timed) {
+    a = btake_event(h);
+    b = btake_event(h);
+    if (a && b) BCK(cudaEventRecord(a, h->stream));
+  }
+  v.kernel<<<h->grid[h->variant], v.tile, 0, h->stream>>>(h->B);
+  BCK(cudaGetLastError());
+  if (timed && a && b) {
+    BCK(cudaEventRecord(b, h->stream));
+    h->ev_roll.emplace_back(a, b);
+  }
+  h->launches++;
+  h->rollout_launches++;
+  return RRG_OK;
+}
+
+// One update of every instance: sample, then the rounds of the search.
+int enqueue_update(rrg_batch_ctx* h, const double* d_x, const double* d_r, const double* d_vp,
+                   uint64_t seed, uint64_t base, double* v_out, double* k_out, int32_t* f_out) {
+  const BLaunch& B = h->B;
+  const int S = B.c.S;
+  const int tile = kVariants[h->variant].tile;
+  int maxhn_blocks = 1;
+  for (const BInst& I : h->inst) {
+    const size_t hn = static_cast<size_t>(I.H) * I.N;
+    maxhn_blocks = std::max(maxhn_blocks, static_cast<int>(std::min<size_t>((hn + 255) / 256, 64)));
+  }
+  batch_sample_kernel<<<dim3(maxhn_blocks, S), 256, 0, h->stream>>>(B, seed, base);
+  BCK(cudaGetLastError());
+  batch_begin_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, d_x, d_r, d_vp, tile);
+  BCK(cudaGetLastError());
+  h->launches += 2;
+  const int rounds = B.c.search == RRG_SEARCH_GRID ? 1 : B.c.n_rounds;
+  const int prep_blocks = (S * B.c.M + 127) / 128;
+  for (int r = 0; r < rounds; ++r) {
+    batch_prepare_kernel<<<prep_blocks, 128, 0, h->stream>>>(B);
+    BCK(cudaGetLastError());
+    int rc = enqueue_rollout(h);
+    if (rc != RRG_OK) return rc;
+    batch_recheck_kernel<<<2 * 152, 64, 0, h->stream>>>(B);
+    BCK(cudaGetLastError());
+    const int final = r == rounds - 1;
+    batch_decide_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, final, tile, v_out, k_out, f_out);
+    BCK(cudaGetLastError());
+    h->launches += 3;
+    h->rounds++;
+  }
+  return RRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rrg_batch_create(const double* model_params, int n_params, const rrg_config* cfg,
+                     int n_instances, const int32_t* n_scenarios, const int32_t* horizons,
+                     void* cuda_stream, rrg_batch_handle* out) {
+  g_batch_create_error.clear();
+  rrg_batch_ctx* h = nullptr;
+  if (!out) return bset_err(h, RRG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!model_params || n_params != RRG_NPARAM)
+    return bset_err(h, RRG_EINVAL, "model_params must hold %d values", RRG_NPARAM);
+  for (int i = 0; i < RRG_NPARAM; ++i)
+    if (!std::isfinite(model_params[i])) return bset_err(h, RRG_EINVAL, "model_params[%d] not finite", i);
+  int rc = check_config(cfg);
+  if (rc != RRG_OK) return bset_err(h, rc, "%s", rrg_last_error(nullptr));
+  if (cfg->search != RRG_SEARCH_GRID && cfg->search != RRG_SEARCH_KSECTION)
+    return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_SEARCH_GRID or RRG_SEARCH_KSECTION");
+  if (cfg->precision != RRG_FP32_RECHECK)
+    return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_FP32_RECHECK");
+  if (cfg->param_unc_rel != 0.0)
+    return bset_err(h, RRG_ENOTIMPL, "batched instances have no parametric uncertainty");
+  if (n_instances < 1 || n_instances > kMaxInst)
+    return bset_err(h, RRG_EINVAL, "n_instances must be in [1, %d]", kMaxInst);
+  if (!n_scenarios || !horizons) return bset_err(h, RRG_EINVAL, "n_scenarios and horizons must be non-NULL");
+  const int M = cfg->max_candidates;
+  std::vector<BInst> inst(n_instances);
+  unsigned long long lanes = 0, elems = 0;
+  for (int s = 0; s < n_instances; ++s) {
+    if (n_scenarios[s] < 1 || horizons[s] < 1)
+      return bset_err(h, RRG_EINVAL, "instance %d: n_scenarios and horizon must be >= 1", s);
+    inst[s].N = n_scenarios[s];
+    inst[s].H = horizons[s];
+    inst[s].off = static_cast<long long>(elems);
+    const unsigned long long e = 3ull * static_cast<unsigned long long>(horizons[s]) *
+                                 static_cast<unsigned long long>(n_scenarios[s]);
+    elems += (e + 31ull) & ~31ull;  // 128-byte aligned blocks
+    lanes += static_cast<unsigned long long>(M) * static_cast<unsigned long long>(n_scenarios[s]);
+  }
+  if (lanes >= (1ull << 31)) return bset_err(h, RRG_EINVAL, "sum of max_candidates * n_scenarios >= 2^31");
+
+  h = new (std::nothrow) rrg_batch_ctx();
+  if (!h) return bset_err(nullptr, RRG_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  h->inst = inst;
+  h->lanes = lanes;
+  std::memcpy(h->params, model_params, sizeof h->params);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+      h->own_stream = e == cudaSuccess;
+    }
+  }
+  const size_t S = n_instances, SM = S * M;
+  auto alloc = [&](auto** p, size_t n) {
+    if (e == cudaSuccess) {
+      e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(**p) + 16);
+      if (e != cudaSuccess) cudaGetLastError();
+    }
+  };
+  alloc(&h->params_dev, RRG_NPARAM);
+  alloc(&h->inst_dev, S);
+  alloc(&h->order_dev, S);
+  alloc(&h->st, S);
+  alloc(&h->d32, static_cast<size_t>(elems));
+  alloc(&h->cand_kappa, SM);
+  alloc(&h->cand_v, SM);
+  alloc(&h->cand_c64, SM);
+  alloc(&h->cand_c32, SM);
+  alloc(&h->cand_ok, SM);
+  alloc(&h->cand_dead, SM);
+  alloc(&h->cand_ss, SM);
+  alloc(&h->cand_min, SM);
+  alloc(&h->tile_base, S + 1);
+  alloc(&h->queue, 2);
+  alloc(&h->recheck_list, static_cast<size_t>(lanes));
+  alloc(&h->recheck_count, 1);
+  alloc(&h->stats, 1);
+  alloc(&h->t_dev, 1);
+  alloc(&h->amp_dev, 3);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->io_h), 4 * sizeof(double));
+  // longest horizon first, then most scenarios (a longest-processing-time
+  // order for the tile queue)
+  std::vector<int32_t> order(S);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (inst[a].H != inst[b].H) return inst[a].H > inst[b].H;
+    return inst[a].N > inst[b].N;
+  });
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->inst_dev, inst.data(), S * sizeof(BInst), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->order_dev, order.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, S * sizeof(BState), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->t_dev, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, static_cast<size_t>(elems) * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  int nsm = 152;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  for (int v = 0; v < RRG_BATCH_VARIANTS && e == cudaSuccess; ++v) {
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kVariants[v].kernel, kVariants[v].tile, 0);
+    h->grid[v] = std::max(1, per) * nsm;
+  }
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? RRG_ENOMEM : RRG_ECUDA;
+    bset_err(nullptr, code, "rrg_batch_create: %s", cudaGetErrorString(e));
+    bfree_all(h);
+    delete h;
+    return code;
+  }
+  BLaunch& B = h->B;
+  B.stream = h->stream;
+  B.c.S = n_instances;
+  B.c.M = M;
+  B.c.n_rounds = cfg->n_rounds;
+  B.c.search = cfg->search;
+  B.c.ss_check = cfg->ss_check;
+  B.c.early_exit = cfg->early_exit;
+  B.c.dt = cfg->dt;
+  B.c.y_min = cfg->y_min;
+  B.c.eps_ss = cfg->eps_ss;
+  B.c.y_c = cfg->y_c;
+  B.c.eps_abs = cfg->recheck_eps_rel * std::fabs(cfg->y_min);
+  for (int i = 0; i < 3; ++i) B.c.amp[i] = cfg->dist_amp[i];
+  B.params = h->params_dev;
+  fold_constants(h->params, &B.k64, &B.k32);
+  fold_rhs(B.k64, &B.u64, &B.u32);
+  B.inst = h->inst_dev;
+  B.order = h->order_dev;
+  B.st = h->st;
+  B.d32 = h->d32;
+  B.cand_kappa = h->cand_kappa;
+  B.cand_v = h->cand_v;
+  B.cand_c64 = h->cand_c64;
+  B.cand_c32 = h->cand_c32;
+  B.cand_ok = h->cand_ok;
+  B.cand_dead = h->cand_dead;
+  B.cand_ss = h->cand_ss;
+  B.cand_min = h->cand_min;
+  B.tile_base = h->tile_base;
+  B.queue = h->queue;
+  B.recheck_list = h->recheck_list;
+  B.recheck_count = h->recheck_count;
+  B.recheck_cap = lanes;
+  B.stats = h->stats;
+  B.t_dev = nullptr;
+  *out = h;
+  return RRG_OK;
+}
+
+int rrg_batch_destroy(rrg_batch_handle h) {
+  if (!h) return RRG_OK;
+  int rc = RRG_OK;
+  {
+    BDeviceGuard g(h->device);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = RRG_ECUDA;
+    bfree_all(h);
+  }
+  delete h;
+  return rc;
+}
+
+const char* rrg_batch_last_error(rrg_batch_handle h) {
+  return h ? h->err.c_str() : g_batch_create_error.c_str();
+}
+
+int rrg_batch_step_dev(rrg_batch_handle h, const double* d_x, const double* d_r,
+                       const double* d_v_prev, uint64_t seed, uint64_t update_index,
+                       double* d_v_t, double* d_kappa, int32_t* d_flags) {
+  if (!h) return RRG_EINVAL;
+  if (!d_x || !d_r || !d_v_prev) return bset_err(h, RRG_EINVAL, "d_x, d_r and d_v_prev must be non-NULL");
+  BDeviceGuard g(h->device);
+  h->B.t_dev = nullptr;
+  return enqueue_update(h, d_x, d_r, d_v_prev, seed, update_index, d_v_t, d_kappa, d_flags);
+}
+
+int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double* d_x0, const double* d_v0,
+                              const double* d_r_seq, int T, uint64_t seed, uint64_t t0,
+                              const double* plant_amp, int use_graph, double* d_v_out,
+                              double* d_kappa_out, int32_t* d_flags_out, double* d_x_out) {
+  if (!h) return RRG_EINVAL;
+  if (T < 0 || !d_r_seq || !plant_amp || (d_x0 && !d_v0))
+    return bset_err(h, RRG_EINVAL, "T >= 0, d_r_seq and plant_amp non-NULL, d_v0 with d_x0");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(plant_amp[i]) || plant_amp[i] < 0.0)
+      return bset_err(h, RRG_EINVAL, "plant_amp must be finite and >= 0");
+  BDeviceGuard g(h->device);
+  h->B.t_dev = h->t_dev;
+  std::memcpy(h->io_h, plant_amp, 3 * sizeof(double));
+  BCK(cudaMemcpyAsync(h->amp_dev, h->io_h, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (d_x0) {
+    batch_loop_init_kernel<<<(h->B.c.S + 127) / 128, 128, 0, h->stream>>>(h->B, d_x0, d_v0, d_x_out);
+    BCK(cudaGetLastError());
+    h->launches++;
+  }
+  auto one = [&]() -> int {
+    int rc = enqueue_update(h, nullptr, d_r_seq, nullptr, seed, t0, d_v_out, d_kappa_out, d_flags_out);
+    if (rc != RRG_OK) return rc;
+    batch_plant_kernel<<<1, kDecideThreads, 0, h->stream>>>(h->B, seed, t0, h->amp_dev, d_x_out);
+    BCK(cudaGetLastError());
+    h->launches++;
+    return RRG_OK;
+  };
+  if (!use_graph) {
+    for (int t = 0; t < T; ++t) {
+      int rc = one();
+      if (rc != RRG_OK) return rc;
+    }
+    return RRG_OK;
+  }
+  const void* key[5] = {d_r_seq, d_v_out, d_kappa_out, d_flags_out, d_x_out};
+  const bool hit = h->cl_exec && std::memcmp(key, h->cl_key, sizeof key) == 0 &&
+                   h->cl_key_seed == seed && h->cl_key_t0 == t0 && h->cl_key_variant == h->variant;
+  if (!hit) {
+    if (h->cl_exec) {
+      cudaGraphExecDestroy(h->cl_exec);
+      h->cl_exec = nullptr;
+    }
+    const uint64_t l0 = h->launches, r0 = h->rollout_launches, rd0 = h->rounds;
+    cudaGraph_t graph = nullptr;
+    BCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    int rc = one();
+    h->capturing = false;
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ce != cudaSuccess) return bset_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&h->cl_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      h->cl_exec = nullptr;
+      return bset_err(h, RRG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    }
+    h->cl_per = h->launches - l0;
+    h->cl_rl_per = h->rollout_launches - r0;
+    h->launches = l0;
+    h->rollout_launches = r0;
+    h->rounds = rd0;
+    std::memcpy(h->cl_key, key, sizeof key);
+    h->cl_key_seed = seed;
+    h->cl_key_t0 = t0;
+    h->cl_key_variant = h->variant;
+  }
+  for (int t = 0; t < T; ++t) {
+    const cudaError_t ce = cudaGraphLaunch(h->cl_exec, h->stream);
+    if (ce != cudaSuccess) return bset_err(h, RRG_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+    h->launches += h->cl_per;
+    h->rollout_launches += h->cl_rl_per;
+    h->rounds += h->cfg.search == RRG_SEARCH_GRID ? 1 : h->cfg.n_rounds;
+  }
+  return RRG_OK;
+}
+
+int rrg_batch_set_variant(rrg_batch_handle h, int variant) {
+  if (!h) return RRG_EINVAL;
+  if (variant < 0 || variant >= RRG_BATCH_VARIANTS)
+    return bset_err(h, RRG_EINVAL, "variant must be in [0, %d)", RRG_BATCH_VARIANTS);
+  h->variant = variant;
+  return RRG_OK;
+}
+
+int rrg_batch_get_variant(rrg_batch_handle h, int* variant, int* tile_lanes, int* prefetch) {
+  if (!h) return RRG_EINVAL;
+  if (variant) *variant = h->variant;
+  if (tile_lanes) *tile_lanes = kVariants[h->variant].tile;
+  if (prefetch) *prefetch = kVariants[h->variant].pf;
+  return RRG_OK;
+}
+
+int rrg_batch_autotune(rrg_batch_handle h, const double* d_x, const double* d_r,
+                       const double* d_v_prev, uint64_t seed, uint64_t update_index, int repeats,
+                       int* variant_out, double* ms_out) {
+  if (!h) return RRG_EINVAL;
+  if (!d_x || !d_r || !d_v_prev || repeats < 1)
+    return bset_err(h, RRG_EINVAL, "d_x, d_r, d_v_prev non-NULL and repeats >= 1");
+  BDeviceGuard g(h->device);
+  h->B.t_dev = nullptr;
+  const bool prof = h->profiling;
+  const double ms0 = h->rollout_ms;
+  const uint64_t n0 = h->timed_rollouts;
+  BCK(cudaStreamSynchronize(h->stream));
+  bcollect(h);
+  double best = 0.0;
+  int best_v = h->variant;
+  for (int v = 0; v < RRG_BATCH_VARIANTS; ++v) {
+    h->variant = v;
+    h->profiling = true;
+    double total = 0.0;
+    for (int rep = 0; rep <= repeats; ++rep) {
+      const double before = h->rollout_ms;
+      int rc = enqueue_update(h, d_x, d_r, d_v_prev, seed, update_index, nullptr, nullptr, nullptr);
+      if (rc != RRG_OK) { h->profiling = prof; return rc; }
+      BCK(cudaStreamSynchronize(h->stream));
+      bcollect(h);
+      if (rep > 0) total += h->rollout_ms - before;  // the first run warms up
+    }
+    const double ms = total / repeats;
+    if (ms_out) ms_out[v] = ms;
+    if (v == 0 || ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  h->variant = best_v;
+  h->profiling = prof;
+  h->rollout_ms = ms0;
+  h->timed_rollouts = n0;
+  if (variant_out) *variant_out = best_v;
+  return RRG_OK;
+}
+
+int rrg_batch_set_profiling(rrg_batch_handle h, int on) {
+  if (!h) return RRG_EINVAL;
+  h->profiling = on != 0;
+  return RRG_OK;
+}
+
+int rrg_batch_get_stats(rrg_batch_handle h, rrg_stats* out) {
+  if (!h || !out) return RRG_EINVAL;
+  BDeviceGuard g(h->device);
+  BCK(cudaStreamSynchronize(h->stream));
+  bcollect(h);
+  DevStats d{};
+  BCK(cudaMemcpy(&d, h->stats, sizeof d, cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof *out);
+  out->launches = h->launches;
+  out->rollout_launches = h->rollout_launches;
+  out->lane_steps = d.lane_steps;
+  out->lane_steps_fp64 = d.lane_steps_fp64;
+  out->rechecked = d.rechecked;
+  out->rounds = h->rounds;
+  out->rollout_ms = h->rollout_ms;
+  out->recheck_ms = 0.0;
+  out->timed_rollouts = h->timed_rollouts;
+  out->repairs = 0;
+  return RRG_OK;
+}
+
+int rrg_batch_reset_stats(rrg_batch_handle h) {
+  if (!h) return RRG_EINVAL;
+  BDeviceGuard g(h->device);
+  BCK(cudaStreamSynchronize(h->stream));
+  bcollect(h);
+  BCK(cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream));
+  BCK(cudaStreamSynchronize(h->stream));
+  h->launches = h->rollout_launches = h->rounds = 0;
+  h->rollout_ms = 0.0;
+  h->timed_rollouts = 0;
+  return RRG_OK;
+}
+
+}  // extern "C"

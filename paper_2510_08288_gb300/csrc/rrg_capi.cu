@@ -55,8 +55,8 @@ struct rrg_ctx {
   SearchState* st = nullptr;
   double* cand_kappa = nullptr;
   double* cand_v = nullptr;
-  CandK<double>* cand_k64 = nullptr;
-  CandK<float>* cand_k32 = nullptr;
+  RhsC<double>* cand_c64 = nullptr;
+  RhsC<float>* cand_c32 = nullptr;
   int32_t* cand_ok = nullptr;
   int32_t* cand_dead = nullptr;
   int32_t* cand_ss = nullptr;
@@ -166,7 +166,7 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_all(rrg_ctx* h) {
   void* ptrs[] = {h->params_dev, h->d64, h->d32, h->d64b, h->d32b, h->st, h->cand_kappa,
-                  h->cand_v, h->cand_k64, h->cand_k32, h->cand_ok, h->cand_dead, h->cand_ss,
+                  h->cand_v, h->cand_c64, h->cand_c32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state,
                   h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
@@ -200,13 +200,14 @@ void fill_launch(rrg_ctx* h) {
   L.scfg = h->scfg;
   L.params = h->params_dev;
   fold_constants(h->params, &L.k64, &L.k32);
+  fold_rhs(L.k64, &L.u64, &L.u32);
   L.d64 = h->d64;
   L.d32 = h->d32;
   L.st = h->st;
   L.cand_kappa = h->cand_kappa;
   L.cand_v = h->cand_v;
-  L.cand_k64 = h->cand_k64;
-  L.cand_k32 = h->cand_k32;
+  L.cand_c64 = h->cand_c64;
+  L.cand_c32 = h->cand_c32;
   L.cand_ok = h->cand_ok;
   L.cand_dead = h->cand_dead;
   L.cand_ss = h->cand_ss;
@@ -395,8 +396,8 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   // two slot ranges: a pipelined round and the round after it run together
   ALLOC(cand_kappa, 2 * M);
   ALLOC(cand_v, 2 * M);
-  ALLOC(cand_k64, 2 * M);
-  ALLOC(cand_k32, 2 * M);
+  ALLOC(cand_c64, 2 * M);
+  ALLOC(cand_c32, 2 * M);
   ALLOC(cand_ok, 2 * M);
   ALLOC(cand_dead, 2 * M);
   ALLOC(cand_ss, 2 * M);

@@ -125,6 +125,8 @@ struct Launch {
   const double* params;         // [RRG_NPARAM] (device)
   Fc3K<double> k64;             // folded model constants, passed by value
   Fc3K<float> k32;
+  RhsU<double> u64;             // the rollout's multiplied-out constants
+  RhsU<float> u32;
   double* d64;                  // scenarios [3][H][N]
   float* d32;
   double* d64b;                 // second pair for closed loops (sampling of update t+1
@@ -132,8 +134,8 @@ struct Launch {
   SearchState* st;
   double* cand_kappa;
   double* cand_v;
-  CandK<double>* cand_k64;
-  CandK<float>* cand_k32;
+  RhsC<double>* cand_c64;       // per-slot rollout constants of the candidate
+  RhsC<float>* cand_c32;
   int32_t* cand_ok;    // AND of the round's trajectory decisions
   int32_t* cand_dead;  // set once the candidate is known to fail
   int32_t* cand_ss;    // steady-state check passed
@@ -192,13 +194,16 @@ __host__ __device__ inline void fold_constants(const double* P, Fc3K<double>* k6
   *k32 = F;
 }
 
-// Constants of the closed loop at setpoint I (binary64).
+// Constants of the closed loop at setpoint I (binary64; every operation
+// rounded separately, so each call site computes the same bits).
 __device__ __forceinline__ CandK<double> cand_consts(const double* __restrict__ P, double I) {
   CandK<double> C;
-  C.W_o2 = P[P_M_O2] * P[P_N_CELL] * I / (4.0 * P[P_FARADAY]);
-  const double W_ref = P[P_LAM_REF] * C.W_o2 / P[P_X_O2];
-  C.V0 = P[P_C0] + P[P_C1] * I + P[P_C2] * I * I + P[P_K_P] * W_ref;
-  C.y_scale = P[P_X_O2] * P[P_K_SM] / C.W_o2;
+  C.W_o2 = __ddiv_rn(__dmul_rn(__dmul_rn(P[P_M_O2], P[P_N_CELL]), I), __dmul_rn(4.0, P[P_FARADAY]));
+  const double W_ref = __ddiv_rn(__dmul_rn(P[P_LAM_REF], C.W_o2), P[P_X_O2]);
+  const double v_ff = __dadd_rn(__dadd_rn(P[P_C0], __dmul_rn(P[P_C1], I)),
+                                __dmul_rn(__dmul_rn(P[P_C2], I), I));
+  C.V0 = __dadd_rn(v_ff, __dmul_rn(P[P_K_P], W_ref));
+  C.y_scale = __ddiv_rn(__dmul_rn(P[P_X_O2], P[P_K_SM]), C.W_o2);
   return C;
 }
 
@@ -208,6 +213,49 @@ __device__ __forceinline__ CandK<float> cand_round(const CandK<double>& C) {
   F.V0 = static_cast<float>(C.V0);
   F.y_scale = static_cast<float>(C.y_scale);
   return F;
+}
+
+// The multiplied-out constants of the rollout right-hand side (products of
+// the folded binary64 constants, each rounded once to binary32).
+__host__ __device__ inline void fold_rhs(const Fc3K<double>& K, RhsU<double>* u64, RhsU<float>* u32) {
+  RhsU<double> U;
+  U.a1 = K.RT_Vca * K.k_sm;
+  U.a2 = K.RT_Vca * K.k_ca;
+  U.a_w = K.a_w;
+  U.a_p = K.a_p;
+  U.RT_Vsm = K.RT_Vsm;
+  U.b3 = K.RT_Vsm * K.k_sm;
+  U.inv_p_atm = K.inv_p_atm;
+  U.e = K.e;
+  U.e1 = K.C_m * K.K_p * K.inv_J;
+  U.e2 = K.C_m * K.k_v * K.inv_J;
+  U.e3 = K.C_cp * K.inv_J;
+  *u64 = U;
+  RhsU<float> F;
+  F.a1 = static_cast<float>(U.a1);
+  F.a2 = static_cast<float>(U.a2);
+  F.a_w = static_cast<float>(U.a_w);
+  F.a_p = static_cast<float>(U.a_p);
+  F.RT_Vsm = static_cast<float>(U.RT_Vsm);
+  F.b3 = static_cast<float>(U.b3);
+  F.inv_p_atm = static_cast<float>(U.inv_p_atm);
+  F.e = static_cast<float>(U.e);
+  F.e1 = static_cast<float>(U.e1);
+  F.e2 = static_cast<float>(U.e2);
+  F.e3 = static_cast<float>(U.e3);
+  *u32 = F;
+}
+
+__host__ __device__ inline void fold_rhs_cand(const Fc3K<double>& K, const CandK<double>& C,
+                                              RhsC<double>* c64, RhsC<float>* c32) {
+  RhsC<double> R;
+  R.a3 = K.RT_Vca * C.W_o2;
+  R.e0 = K.C_m * C.V0 * K.inv_J;
+  R.y_scale = C.y_scale;
+  *c64 = R;
+  c32->a3 = static_cast<float>(R.a3);
+  c32->e0 = static_cast<float>(R.e0);
+  c32->y_scale = static_cast<float>(R.y_scale);
 }
 
 // ---- kernel launchers (rrg_kernels.cu) --------------------------------

@@ -22,88 +22,12 @@
 
 #include "rrg_device.cuh"
 #include "rrg_internal.h"
+#include "rrg_lane.cuh"
 
 namespace rrg {
 
 constexpr int kRollThreads = 128;
 constexpr int kSearchThreads = 256;
-
-template <typename T> __device__ __forceinline__ T max_finite();
-template <> __device__ __forceinline__ float max_finite<float>() { return FLT_MAX; }
-template <> __device__ __forceinline__ double max_finite<double>() { return DBL_MAX; }
-template <typename T> __device__ __forceinline__ T inf_v();
-template <> __device__ __forceinline__ float inf_v<float>() { return __int_as_float(0x7f800000); }
-template <> __device__ __forceinline__ double inf_v<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
-
-// ---------------------------------------------------------------------------
-// Equilibrium manifold (Sec. II-A).  At rest the cathode balance fixes the
-// cathode gauge pressure from the air flow W, the orifice fixes the supply
-// manifold pressure and the compressor map the speed, leaving the shaft
-// torque balance g(W) = 0, with g decreasing in W and g(W_o2) > 0.  The root
-// lies close to the controller's target flow W_ref = lam_ref W_o2 / x_O2, so
-// a secant iteration started there converges in a handful of binary64
-// evaluations; every iterate is kept inside a sign-change bracket and a
-// step that leaves it is replaced by bisection.
-template <typename T>
-__device__ T eq_torque(const Fc3K<T>& K, const CandK<T>& C, T inv_k_ca, T inv_k_sm, T a_p,
-                       T inv_a_w, T W, T q[3]) {
-  q[0] = (W - C.W_o2) * inv_k_ca;
-  q[2] = q[0] + W * inv_k_sm;
-  q[1] = (W + a_p * q[2]) * inv_a_w;
-  T a, b, c;
-  fc3_rhs<T>(K, C, q[0], q[1], q[2], a, b, c);
-  return b;
-}
-
-template <typename T> __device__ __forceinline__ T eq_tol();
-template <> __device__ __forceinline__ double eq_tol<double>() { return 1e-15; }
-template <> __device__ __forceinline__ float eq_tol<float>() { return 2e-7f; }
-
-// Returns 0 and the gauge state q, output *y_ss at the equilibrium, or < 0.
-template <typename T>
-__device__ int equilibrium_dev(const Fc3K<T>& K, const double* __restrict__ P, double I, T q[3],
-                               T* y_ss) {
-  if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
-  const CandK<double> Cd = cand_consts(P, I);
-  CandK<T> C;
-  C.W_o2 = static_cast<T>(Cd.W_o2);
-  C.V0 = static_cast<T>(Cd.V0);
-  C.y_scale = static_cast<T>(Cd.y_scale);
-  const T ikca = static_cast<T>(1.0 / P[P_K_CA]), iksm = static_cast<T>(1.0 / P[P_K_SM]);
-  const T a_p = static_cast<T>(P[P_A_P]), iaw = static_cast<T>(1.0 / P[P_A_W]);
-  const T big = static_cast<T>(1e30);
-  T lo = C.W_o2;
-  if (!(eq_torque<T>(K, C, ikca, iksm, a_p, iaw, lo, q) > T(0))) return -2;
-  T hi = big;
-  // two starting points around the target flow
-  T x0 = static_cast<T>(P[P_LAM_REF] * Cd.W_o2 / P[P_X_O2]);
-  T g0 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x0, q);
-  if (g0 > T(0)) lo = x0; else hi = x0;
-  T x1 = x0 * (g0 > T(0) ? T(1.001) : T(0.999));
-  T g1 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x1, q);
-  if (g1 > T(0)) { if (x1 > lo) lo = x1; } else if (x1 < hi) hi = x1;
-  // make sure the bracket is closed before bisection can be needed
-  for (int it = 0; it < 60 && hi == big; ++it) {
-    const T xt = T(2) * lo;
-    if (eq_torque<T>(K, C, ikca, iksm, a_p, iaw, xt, q) > T(0)) lo = xt; else hi = xt;
-  }
-  if (hi == big) return -2;
-  T W = x1;
-  for (int it = 0; it < 100; ++it) {
-    T x2 = x1 - g1 * (x1 - x0) / (g1 - g0);
-    if (!(x2 > lo && x2 < hi)) x2 = T(0.5) * (lo + hi);
-    const T g2 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x2, q);
-    W = x2;
-    if (g2 == T(0)) break;
-    if (g2 > T(0)) lo = x2; else hi = x2;
-    if (fabs(x2 - x1) <= eq_tol<T>() * x2 || hi - lo <= T(0.4) * eq_tol<T>() * hi) break;
-    x0 = x1; g0 = g1;
-    x1 = x2; g1 = g2;
-  }
-  eq_torque<T>(K, C, ikca, iksm, a_p, iaw, W, q);
-  *y_ss = fc3_output<T>(C, q[0], q[2]);
-  return 0;
-}
 
 __global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<double> k64,
                                    double v, double* out4, int32_t* status) {
@@ -131,10 +55,6 @@ cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_
 // the binary64 value by less than a 2^-23 plus one binary32 rounding, far
 // inside the binary32 rollout's own error, and needs no binary64 arithmetic
 // (GB300's binary64 pipe is narrow).
-__device__ __forceinline__ float uniform_sym32(uint64_t w, float a_scaled) {
-  const int t = static_cast<int>(w >> 40) - (1 << 23);
-  return __fmul_rn(__int2float_rn(t), a_scaled);
-}
 
 // Parametric uncertainty: multiplier m_p^k = 1 + rho (2u - 1) of parameter p
 // in scenario k for every p set in mask (1 for the rest), u from word p % 4 of
@@ -270,153 +190,6 @@ cudaError_t launch_round_scenarios(const Launch& L) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// One trajectory: x_0 = x_t, x_{j+1} = RK4(x_j, v) + d_j, slack s_j =
-// h(x_j, v) - y_min at j = 0..H; a non-finite state or output counts as
-// s = -inf.  Stops when s < thr (thr = -inf: never) and, checked once per
-// block of kPrefetch steps, when *dead is set.  Returns min_j s_j; *steps
-// receives the RK4 steps done.
-//
-// The disturbances of step j are loaded kPrefetch steps ahead into a small
-// register ring, so the L2 latency of the three loads (larger than one RK4
-// step on a two-die GB300) overlaps the arithmetic of the steps in between.
-// The candidate's dead flag is read at the start of a block and used at its
-// end, for the same reason.
-#ifndef RRG_PREFETCH
-#define RRG_PREFETCH 8
-#endif
-constexpr int kPrefetch = RRG_PREFETCH;
-
-template <typename T>
-__device__ __forceinline__ T checked_slack(const CandK<T>& C, T q_ca, T w, T q_sm, T y_min) {
-  const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
-  const T z = q_ca + w + q_sm;
-  return (fabs(z) <= max_finite<T>() && fabs(s) <= max_finite<T>()) ? s : -inf_v<T>();
-}
-
-// Lane outcome of run_lane.
-enum LaneEnd : int { LANE_REACHED_END = 0, LANE_VIOLATED = 1, LANE_STOPPED = 2 };
-
-// Steps j0+1..j_end of one trajectory, from the state (q_ca, w, q_sm) at
-// step j0 (updated in place); with j0 = 0 the output at step 0 is checked
-// first (for j0 > 0 it was checked by the run that stopped there).  smin_in
-// is the min slack so far.
-template <typename T>
-__device__ __forceinline__ T run_lane(const Fc3K<T>& K, const CandK<T>& C,
-                                      const T* __restrict__ d, int k, int N, int H, int j0,
-                                      int j_end, T& q_ca, T& w, T& q_sm, T smin_in, T dt, T y_min,
-                                      T thr, const volatile int32_t* dead, unsigned* steps,
-                                      int* end) {
-  T smin = smin_in;
-  int j = j0;
-  int how = LANE_REACHED_END;
-  bool go = j < j_end;
-  if (j0 == 0) {
-    const T s0 = checked_slack<T>(C, q_ca, w, q_sm, y_min);
-    smin = fmin(smin, s0);
-    if (s0 < thr) {
-      how = LANE_VIOLATED;
-      go = false;
-    }
-  }
-  if (go) {
-    const size_t HN = static_cast<size_t>(H) * N;
-    T r0[kPrefetch], r1[kPrefetch], r2[kPrefetch];
-    const T* pf = d + static_cast<size_t>(j0) * N + k;  // next step to prefetch
-#pragma unroll
-    for (int u = 0; u < kPrefetch; ++u) {
-      if (j0 + u < j_end) {
-        r0[u] = __ldg(pf);
-        r1[u] = __ldg(pf + HN);
-        r2[u] = __ldg(pf + 2 * HN);
-      } else {
-        r0[u] = r1[u] = r2[u] = T(0);
-      }
-      pf += N;
-    }
-    bool stop = false;
-    // Whole blocks of kPrefetch steps run without a per-step exit branch: the
-    // running min is tested once per block.  A lane that violates inside a
-    // block runs to the block's end; that only lowers its min slack, so no
-    // decision changes.  The last, partial block steps one at a time.
-    while (!stop && j + kPrefetch <= j_end) {
-      const int dead_now = dead != nullptr ? *dead : 0;
-#pragma unroll
-      for (int u = 0; u < kPrefetch; ++u) {
-        const T e0 = r0[u], e1 = r1[u], e2 = r2[u];
-        if (j + kPrefetch < j_end) {
-          r0[u] = __ldg(pf);
-          r1[u] = __ldg(pf + HN);
-          r2[u] = __ldg(pf + 2 * HN);
-        }
-        pf += N;
-        rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-        q_ca += e0;
-        w += e1;
-        q_sm += e2;
-        ++j;
-        smin = fmin(smin, checked_slack<T>(C, q_ca, w, q_sm, y_min));
-      }
-      if (smin < thr) {
-        how = LANE_VIOLATED;
-        stop = true;
-      } else if (dead_now != 0 && j < j_end) {
-        how = LANE_STOPPED;
-        stop = true;
-      }
-    }
-    const T* dp = d + static_cast<size_t>(j) * N + k;
-    while (!stop && j < j_end) {
-      const T e0 = __ldg(dp), e1 = __ldg(dp + HN), e2 = __ldg(dp + 2 * HN);
-      dp += N;
-      rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-      q_ca += e0;
-      w += e1;
-      q_sm += e2;
-      ++j;
-      const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
-      smin = fmin(smin, s);
-      if (s < thr) {
-        how = LANE_VIOLATED;
-        stop = true;
-      }
-    }
-  }
-  *steps = static_cast<unsigned>(j - j0);
-  *end = how;
-  return smin;
-}
-
-// Scenario k's model under parametric uncertainty: the parameters theta_p
-// m_p^k folded like the nominal ones, and the candidate constants at v.
-// Returns the scenario's p_atm (the origin of its gauge coordinates).
-template <typename T>
-__device__ __forceinline__ double scenario_model(const double* __restrict__ P,
-                                                 const double* __restrict__ m_k, double v,
-                                                 Fc3K<T>& K, CandK<T>& C) {
-  double Pk[RRG_NPARAM];
-#pragma unroll
-  for (int p = 0; p < RRG_NPARAM; ++p) Pk[p] = __dmul_rn(P[p], m_k[p]);
-  Fc3K<double> k64;
-  Fc3K<float> k32;
-  fold_constants(Pk, &k64, &k32);
-  const CandK<double> c64 = cand_consts(Pk, v);
-  if constexpr (sizeof(T) == 8) {
-    K = k64;
-    C = c64;
-  } else {
-    K = k32;
-    C = cand_round(c64);
-  }
-  return Pk[P_P_ATM];
-}
-
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 // One thread per (candidate slot, scenario k); blockIdx.y picks the slot
 // through the state's two segments.  classify = 1 is the binary32 pass of
 // RRG_FP32_RECHECK: trajectories whose final min slack lies in [-eps, eps)
@@ -425,10 +198,10 @@ __device__ __forceinline__ double warp_min(double v) {
 // nothing yet; the SEG_CONTINUE lane of the next launch finishes it.  PU:
 // parametric uncertainty, each lane folds its scenario's own model constants.
 template <typename T, bool PU>
-__device__ __forceinline__ void rollout_body(const Launch& L, const Fc3K<T>& K0,
+__device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
                                              const T* __restrict__ d_pair0,
                                              const T* __restrict__ d_pair1,
-                                             const CandK<T>* __restrict__ cand, int early_exit,
+                                             const RhsC<T>* __restrict__ cand, int early_exit,
                                              int classify) {
   const T* __restrict__ d = L.st->buf ? d_pair1 : d_pair0;
   const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
@@ -459,8 +232,8 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const Fc3K<T>& K0,
     const int dead0 = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? *dead : 0, 0);
     if (dead0) return;
   }
-  CandK<T> C = cand[i];
-  Fc3K<T> K = K0;
+  RhsC<T> C = cand[i];
+  RhsU<T> K = K0;
   const T eps = static_cast<T>(L.eps_abs);
   const T thr = early_exit != RRG_EXIT_NONE ? (classify ? -eps : T(0)) : -inf_v<T>();
 
@@ -549,8 +322,8 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const Fc3K<T>& K0,
 
 template <typename T>
 __global__ void __launch_bounds__(kRollThreads)
-rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
-               const T* __restrict__ d_pair1, const CandK<T>* __restrict__ cand, int early_exit,
+rollout_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0,
+               const T* __restrict__ d_pair1, const RhsC<T>* __restrict__ cand, int early_exit,
                int classify) {
   rollout_body<T, false>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
 }
@@ -565,8 +338,8 @@ rollout_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
 #endif
 template <typename T>
 __global__ void __launch_bounds__(kRollThreads, sizeof(T) == 4 ? RRG_PU_MIN_BLOCKS : 1)
-rollout_pu_kernel(const Launch L, const Fc3K<T> K, const T* __restrict__ d_pair0,
-                  const T* __restrict__ d_pair1, const CandK<T>* __restrict__ cand, int early_exit,
+rollout_pu_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0,
+                  const T* __restrict__ d_pair1, const RhsC<T>* __restrict__ cand, int early_exit,
                   int classify) {
   rollout_body<T, true>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
 }
@@ -577,53 +350,25 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
   const int cls = recheck_classify ? 1 : 0;
   if (use_fp64) {
     if (L.pmul)
-      rollout_pu_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.d64b,
-                                                                     L.cand_k64, early_exit, 0);
+      rollout_pu_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.u64, L.d64, L.d64b,
+                                                                     L.cand_c64, early_exit, 0);
     else
-      rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.k64, L.d64, L.d64b,
-                                                                  L.cand_k64, early_exit, 0);
+      rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.u64, L.d64, L.d64b,
+                                                                  L.cand_c64, early_exit, 0);
   } else {
     if (L.pmul)
-      rollout_pu_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.d32b,
-                                                                    L.cand_k32, early_exit, cls);
+      rollout_pu_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b,
+                                                                    L.cand_c32, early_exit, cls);
     else
-      rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.k32, L.d32, L.d32b,
-                                                                 L.cand_k32, early_exit, cls);
+      rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b,
+                                                                 L.cand_c32, early_exit, cls);
   }
   return cudaGetLastError();
 }
 
-// One binary64 trajectory whose disturbances are regenerated from their
-// Philox counters step by step (the pair was sampled in a binary32 mode, so
-// its binary64 array was never written).  Same contract as run_lane over
-// steps 1..H with early exit at s < thr.
-__device__ double run_lane_philox(const Fc3K<double>& K, const CandK<double>& C,
-                                  const ScenSrc& src, int k, int H, double q_ca, double w,
-                                  double q_sm, double dt, double y_min, double thr,
-                                  unsigned* steps) {
-  double smin = checked_slack<double>(C, q_ca, w, q_sm, y_min);
-  int j = 0;
-  if (!(smin < thr)) {
-    while (j < H) {
-      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
-                                    0ull, src.seed, 0ull);
-      rk4_step<double>(K, C, dt, q_ca, w, q_sm);
-      q_ca += uniform_sym(r.w[0], src.amp[0]);
-      w += uniform_sym(r.w[1], src.amp[1]);
-      q_sm += uniform_sym(r.w[2], src.amp[2]);
-      ++j;
-      const double s = checked_slack<double>(C, q_ca, w, q_sm, y_min);
-      smin = fmin(smin, s);
-      if (s < thr) break;
-    }
-  }
-  *steps = static_cast<unsigned>(j);
-  return smin;
-}
-
 // Binary64 re-run of the trajectories the binary32 pass could not decide.
 __global__ void __launch_bounds__(64)
-recheck_kernel(const Launch L, const Fc3K<double> K0, int early_exit) {
+recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
   const uint32_t count = *L.recheck_count;
   const int N = L.N;
   const double p_atm = L.params[P_P_ATM];
@@ -638,8 +383,8 @@ recheck_kernel(const Launch L, const Fc3K<double> K0, int early_exit) {
     if (L.P == nullptr && !L.cand_ok[i]) continue;
     unsigned steps = 0;
     double smin;
-    Fc3K<double> K = K0;
-    CandK<double> C = L.cand_k64[i];
+    RhsU<double> K = K0;
+    RhsC<double> C = L.cand_c64[i];
     double p_atm_k = p_atm;
     const double* pm = buf ? L.pmulb : L.pmul;
     if (pm != nullptr)
@@ -665,7 +410,7 @@ recheck_kernel(const Launch L, const Fc3K<double> K0, int early_exit) {
 }
 
 cudaError_t launch_recheck(const Launch& L, int early_exit) {
-  recheck_kernel<<<L.recheck_blocks, 64, 0, L.stream>>>(L, L.k64, early_exit);
+  recheck_kernel<<<L.recheck_blocks, 64, 0, L.stream>>>(L, L.u64, early_exit);
   return cudaGetLastError();
 }
 
@@ -785,20 +530,6 @@ __device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* slo
   *len = l;
 }
 
-__device__ int grid_points(double* cand_kappa, int M) {
-  for (int i = 0; i < M; ++i)
-    cand_kappa[i] = __ddiv_rn(static_cast<double>(i), static_cast<double>(M - 1));
-  return M;
-}
-
-__device__ int interior_points(double* cand_kappa, int M, double lo, double hi) {
-  const double w = __dsub_rn(hi, lo);
-  for (int i = 0; i < M; ++i)
-    cand_kappa[i] = __dadd_rn(lo, __ddiv_rn(__dmul_rn(w, static_cast<double>(i + 1)),
-                                            static_cast<double>(M + 1)));
-  return M;
-}
-
 __device__ void set_segments(SearchState* s, int mode0, int count0, int base0, int mode1,
                              int count1, int base1) {
   s->seg[0].mode = mode0; s->seg[0].count = count0; s->seg[0].base = base0;
@@ -877,8 +608,7 @@ __device__ void prepare_slot(const Launch& L, int i) {
   const double v = governed(s->v_prev, s->r, L.cand_kappa[i]);
   L.cand_v[i] = v;
   const CandK<double> C = cand_consts(L.params, v);
-  L.cand_k64[i] = C;
-  L.cand_k32[i] = cand_round(C);
+  fold_rhs_cand(K, C, L.cand_c64 + i, L.cand_c32 + i);
   int ok = 1;
   if (L.scfg.ss_check) {
     // binary32 solve first; it decides unless y_ss lands within 1e-4 of the

@@ -1,0 +1,308 @@
+// rrg_lane.cuh -- device code shared by the single-problem kernels
+// (rrg_kernels.cu) and the batched kernels (rrg_batch.cu): the trajectory
+// loop with its constraint check, the binary64 re-run from Philox counters,
+// the equilibrium solve of the steady-state check, per-scenario model
+// constants and the k-section grids.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+
+#include "rrg_device.cuh"
+#include "rrg_internal.h"
+
+namespace rrg {
+
+template <typename T> __device__ __forceinline__ T max_finite();
+template <> __device__ __forceinline__ float max_finite<float>() { return FLT_MAX; }
+template <> __device__ __forceinline__ double max_finite<double>() { return DBL_MAX; }
+template <typename T> __device__ __forceinline__ T inf_v();
+template <> __device__ __forceinline__ float inf_v<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double inf_v<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+// ---------------------------------------------------------------------------
+// Equilibrium manifold (Sec. II-A).  At rest the cathode balance fixes the
+// cathode gauge pressure from the air flow W, the orifice fixes the supply
+// manifold pressure and the compressor map the speed, leaving the shaft
+// torque balance g(W) = 0, with g decreasing in W and g(W_o2) > 0.  The root
+// lies close to the controller's target flow W_ref = lam_ref W_o2 / x_O2, so
+// a secant iteration started there converges in a handful of binary64
+// evaluations; every iterate is kept inside a sign-change bracket and a
+// step that leaves it is replaced by bisection.
+template <typename T>
+__device__ __forceinline__ T eq_torque(const Fc3K<T>& K, const CandK<T>& C, T inv_k_ca, T inv_k_sm, T a_p,
+                       T inv_a_w, T W, T q[3]) {
+  q[0] = (W - C.W_o2) * inv_k_ca;
+  q[2] = q[0] + W * inv_k_sm;
+  q[1] = (W + a_p * q[2]) * inv_a_w;
+  T a, b, c;
+  fc3_rhs<T>(K, C, q[0], q[1], q[2], a, b, c);
+  return b;
+}
+
+template <typename T> __device__ __forceinline__ T eq_tol();
+template <> __device__ __forceinline__ double eq_tol<double>() { return 1e-15; }
+template <> __device__ __forceinline__ float eq_tol<float>() { return 2e-7f; }
+
+// Returns 0 and the gauge state q, output *y_ss at the equilibrium, or < 0.
+template <typename T>
+__device__ __forceinline__ int equilibrium_dev(const Fc3K<T>& K, const double* __restrict__ P, double I, T q[3],
+                               T* y_ss) {
+  if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
+  const CandK<double> Cd = cand_consts(P, I);
+  CandK<T> C;
+  C.W_o2 = static_cast<T>(Cd.W_o2);
+  C.V0 = static_cast<T>(Cd.V0);
+  C.y_scale = static_cast<T>(Cd.y_scale);
+  const T ikca = static_cast<T>(1.0 / P[P_K_CA]), iksm = static_cast<T>(1.0 / P[P_K_SM]);
+  const T a_p = static_cast<T>(P[P_A_P]), iaw = static_cast<T>(1.0 / P[P_A_W]);
+  const T big = static_cast<T>(1e30);
+  T lo = C.W_o2;
+  if (!(eq_torque<T>(K, C, ikca, iksm, a_p, iaw, lo, q) > T(0))) return -2;
+  T hi = big;
+  // two starting points around the target flow
+  T x0 = static_cast<T>(P[P_LAM_REF] * Cd.W_o2 / P[P_X_O2]);
+  T g0 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x0, q);
+  if (g0 > T(0)) lo = x0; else hi = x0;
+  T x1 = x0 * (g0 > T(0) ? T(1.001) : T(0.999));
+  T g1 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x1, q);
+  if (g1 > T(0)) { if (x1 > lo) lo = x1; } else if (x1 < hi) hi = x1;
+  // make sure the bracket is closed before bisection can be needed
+  for (int it = 0; it < 60 && hi == big; ++it) {
+    const T xt = T(2) * lo;
+    if (eq_torque<T>(K, C, ikca, iksm, a_p, iaw, xt, q) > T(0)) lo = xt; else hi = xt;
+  }
+  if (hi == big) return -2;
+  T W = x1;
+  for (int it = 0; it < 100; ++it) {
+    T x2 = x1 - g1 * (x1 - x0) / (g1 - g0);
+    if (!(x2 > lo && x2 < hi)) x2 = T(0.5) * (lo + hi);
+    const T g2 = eq_torque<T>(K, C, ikca, iksm, a_p, iaw, x2, q);
+    W = x2;
+    if (g2 == T(0)) break;
+    if (g2 > T(0)) lo = x2; else hi = x2;
+    if (fabs(x2 - x1) <= eq_tol<T>() * x2 || hi - lo <= T(0.4) * eq_tol<T>() * hi) break;
+    x0 = x1; g0 = g1;
+    x1 = x2; g1 = g2;
+  }
+  eq_torque<T>(K, C, ikca, iksm, a_p, iaw, W, q);
+  *y_ss = fc3_output<T>(C, q[0], q[2]);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// One trajectory: x_0 = x_t, x_{j+1} = RK4(x_j, v) + d_j, slack s_j =
+// h(x_j, v) - y_min at j = 0..H; a non-finite state or output counts as
+// s = -inf.  Stops when s < thr (thr = -inf: never) and, checked once per
+// block of kPrefetch steps, when *dead is set.  Returns min_j s_j; *steps
+// receives the RK4 steps done.
+//
+// The disturbances of step j are loaded kPrefetch steps ahead into a small
+// register ring, so the L2 latency of the three loads (larger than one RK4
+// step on a two-die GB300) overlaps the arithmetic of the steps in between.
+// The candidate's dead flag is read at the start of a block and used at its
+// end, for the same reason.
+#ifndef RRG_PREFETCH
+#define RRG_PREFETCH 8
+#endif
+constexpr int kPrefetch = RRG_PREFETCH;
+
+template <typename T>
+__device__ __forceinline__ T checked_slack(const RhsC<T>& C, T q_ca, T w, T q_sm, T y_min) {
+  const T s = C.y_scale * (q_sm - q_ca) - y_min;
+  const bool fin = fabs(q_ca) <= max_finite<T>() && fabs(w) <= max_finite<T>() &&
+                   fabs(q_sm) <= max_finite<T>() && fabs(s) <= max_finite<T>();
+  return fin ? s : -inf_v<T>();
+}
+
+// a b + c rounded once; never simplified (x 0 + c is NaN for x = inf or NaN).
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Lane outcome of run_lane.
+enum LaneEnd : int { LANE_REACHED_END = 0, LANE_VIOLATED = 1, LANE_STOPPED = 2 };
+
+// Steps j0+1..j_end of one trajectory, from the state (q_ca, w, q_sm) at
+// step j0 (updated in place); with j0 = 0 the output at step 0 is checked
+// first (for j0 > 0 it was checked by the run that stopped there).  smin_in
+// is the min slack so far.
+template <typename T, int PF = kPrefetch>
+__device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
+                                      const T* __restrict__ d, int k, int N, int H, int j0,
+                                      int j_end, T& q_ca, T& w, T& q_sm, T smin_in, T dt, T y_min,
+                                      T thr, const volatile int32_t* dead, unsigned* steps,
+                                      int* end) {
+  T smin = smin_in;
+  int j = j0;
+  int how = LANE_REACHED_END;
+  bool go = j < j_end;
+  if (j0 == 0) {
+    const T s0 = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    smin = fmin(smin, s0);
+    if (s0 < thr) {
+      how = LANE_VIOLATED;
+      go = false;
+    }
+  }
+  if (go) {
+    const size_t HN = static_cast<size_t>(H) * N;
+    T r0[PF], r1[PF], r2[PF];
+    const T* pf = d + static_cast<size_t>(j0) * N + k;  // next step to prefetch
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      if (j0 + u < j_end) {
+        r0[u] = __ldg(pf);
+        r1[u] = __ldg(pf + HN);
+        r2[u] = __ldg(pf + 2 * HN);
+      } else {
+        r0[u] = r1[u] = r2[u] = T(0);
+      }
+      pf += N;
+    }
+    bool stop = false;
+    // Whole blocks of PF steps (PF = prefetch depth) run without a per-step exit branch: the
+    // running min is tested once per block.  A lane that violates inside a
+    // block runs to the block's end; that only lowers its min slack, so no
+    // decision changes.  The last, partial block steps one at a time.
+    //
+    // Finiteness is also settled once per block: nf = sum of s_j 0 stays 0
+    // while every slack is finite and turns NaN (for good) at the first that
+    // is not; a non-finite state component is tested at the block's end,
+    // since it contaminates every component through the next right-hand side
+    // (every derivative reads W_cp or s) and NaN and inf never return to a
+    // finite value through +, -, x and / by a finite or NaN operand.  Either
+    // makes the lane's min slack -inf, as a per-step test would.
+    while (!stop && j + PF <= j_end) {
+      const int dead_now = dead != nullptr ? *dead : 0;
+      T nf = T(0);
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const T e0 = r0[u], e1 = r1[u], e2 = r2[u];
+        if (j + PF < j_end) {
+          r0[u] = __ldg(pf);
+          r1[u] = __ldg(pf + HN);
+          r2[u] = __ldg(pf + 2 * HN);
+        }
+        pf += N;
+        rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm);
+        q_ca += e0;
+        w += e1;
+        q_sm += e2;
+        ++j;
+        const T s = C.y_scale * (q_sm - q_ca) - y_min;
+        smin = fmin(smin, s);
+        nf = fma_rn(s, T(0), nf);
+      }
+      nf = fma_rn(q_ca, T(0), fma_rn(w, T(0), fma_rn(q_sm, T(0), nf)));
+      if (nf != nf) smin = -inf_v<T>();
+      if (smin < thr) {
+        how = LANE_VIOLATED;
+        stop = true;
+      } else if (dead_now != 0 && j < j_end) {
+        how = LANE_STOPPED;
+        stop = true;
+      }
+    }
+    const T* dp = d + static_cast<size_t>(j) * N + k;
+    while (!stop && j < j_end) {
+      const T e0 = __ldg(dp), e1 = __ldg(dp + HN), e2 = __ldg(dp + 2 * HN);
+      dp += N;
+      rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm);
+      q_ca += e0;
+      w += e1;
+      q_sm += e2;
+      ++j;
+      const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+      smin = fmin(smin, s);
+      if (s < thr) {
+        how = LANE_VIOLATED;
+        stop = true;
+      }
+    }
+  }
+  *steps = static_cast<unsigned>(j - j0);
+  *end = how;
+  return smin;
+}
+
+// Scenario k's model under parametric uncertainty: the parameters theta_p
+// m_p^k folded like the nominal ones, and the candidate constants at v.
+// Returns the scenario's p_atm (the origin of its gauge coordinates).
+template <typename T>
+__device__ __forceinline__ double scenario_model(const double* __restrict__ P,
+                                                 const double* __restrict__ m_k, double v,
+                                                 RhsU<T>& U, RhsC<T>& C) {
+  double Pk[RRG_NPARAM];
+#pragma unroll
+  for (int p = 0; p < RRG_NPARAM; ++p) Pk[p] = __dmul_rn(P[p], m_k[p]);
+  Fc3K<double> k64;
+  Fc3K<float> k32;
+  fold_constants(Pk, &k64, &k32);
+  const CandK<double> c64 = cand_consts(Pk, v);
+  RhsU<double> u64;
+  RhsU<float> u32;
+  RhsC<double> r64;
+  RhsC<float> r32;
+  fold_rhs(k64, &u64, &u32);
+  fold_rhs_cand(k64, c64, &r64, &r32);
+  if constexpr (sizeof(T) == 8) {
+    U = u64;
+    C = r64;
+  } else {
+    U = u32;
+    C = r32;
+  }
+  return Pk[P_P_ATM];
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One binary64 trajectory whose disturbances are regenerated from their
+// Philox counters step by step (the pair was sampled in a binary32 mode, so
+// its binary64 array was never written).  Same contract as run_lane over
+// steps 1..H with early exit at s < thr.
+__device__ __forceinline__ double run_lane_philox(const RhsU<double>& K, const RhsC<double>& C,
+                                  const ScenSrc& src, int k, int H, double q_ca, double w,
+                                  double q_sm, double dt, double y_min, double thr,
+                                  unsigned* steps) {
+  double smin = checked_slack<double>(C, q_ca, w, q_sm, y_min);
+  int j = 0;
+  if (!(smin < thr)) {
+    while (j < H) {
+      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
+                                    0ull, src.seed, 0ull);
+      rk4_step_fast<double>(K, C, dt, q_ca, w, q_sm);
+      q_ca += uniform_sym(r.w[0], src.amp[0]);
+      w += uniform_sym(r.w[1], src.amp[1]);
+      q_sm += uniform_sym(r.w[2], src.amp[2]);
+      ++j;
+      const double s = checked_slack<double>(C, q_ca, w, q_sm, y_min);
+      smin = fmin(smin, s);
+      if (s < thr) break;
+    }
+  }
+  *steps = static_cast<unsigned>(j);
+  return smin;
+}
+
+// k-section grids (Alg. 3 / Eq. 5 for round 1; M points strictly inside the
+// bracket for the later rounds).
+__device__ __forceinline__ int grid_points(double* cand_kappa, int M) {
+  for (int i = 0; i < M; ++i)
+    cand_kappa[i] = __ddiv_rn(static_cast<double>(i), static_cast<double>(M - 1));
+  return M;
+}
+
+__device__ __forceinline__ int interior_points(double* cand_kappa, int M, double lo, double hi) {
+  const double w = __dsub_rn(hi, lo);
+  for (int i = 0; i < M; ++i)
+    cand_kappa[i] = __dadd_rn(lo, __ddiv_rn(__dmul_rn(w, static_cast<double>(i + 1)),
+                                            static_cast<double>(M + 1)));
+  return M;
+}
+
+}  // namespace rrg

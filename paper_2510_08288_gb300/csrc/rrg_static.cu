@@ -24,8 +24,8 @@ constexpr size_t kOffParams = kOffState + align256(sizeof(SearchState));
 constexpr size_t kOffKappa = kOffParams + align256(RRG_NPARAM * sizeof(double));
 constexpr size_t kOffV = kOffKappa + align256(kStaticMaxCand * sizeof(double));
 constexpr size_t kOffK64 = kOffV + align256(kStaticMaxCand * sizeof(double));
-constexpr size_t kOffK32 = kOffK64 + align256(kStaticMaxCand * sizeof(CandK<double>));
-constexpr size_t kOffOk = kOffK32 + align256(kStaticMaxCand * sizeof(CandK<float>));
+constexpr size_t kOffK32 = kOffK64 + align256(kStaticMaxCand * sizeof(RhsC<double>));
+constexpr size_t kOffOk = kOffK32 + align256(kStaticMaxCand * sizeof(RhsC<float>));
 constexpr size_t kOffDead = kOffOk + align256(kStaticMaxCand * sizeof(int32_t));
 constexpr size_t kOffSs = kOffDead + align256(kStaticMaxCand * sizeof(int32_t));
 constexpr size_t kOffMin = kOffSs + align256(kStaticMaxCand * sizeof(int32_t));
@@ -146,14 +146,15 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
   L.scfg.eps_ss = cfg->eps_ss;
   L.scfg.y_c = cfg->y_c;
   fold_constants(model_params, &L.k64, &L.k32);
+  fold_rhs(L.k64, &L.u64, &L.u32);
   L.params = reinterpret_cast<double*>(base + kOffParams);
   L.d64 = const_cast<double*>(d_scen64);
   L.d32 = const_cast<float*>(d_scen32);
   L.st = reinterpret_cast<SearchState*>(base + kOffState);
   L.cand_kappa = reinterpret_cast<double*>(base + kOffKappa);
   L.cand_v = reinterpret_cast<double*>(base + kOffV);
-  L.cand_k64 = reinterpret_cast<CandK<double>*>(base + kOffK64);
-  L.cand_k32 = reinterpret_cast<CandK<float>*>(base + kOffK32);
+  L.cand_c64 = reinterpret_cast<RhsC<double>*>(base + kOffK64);
+  L.cand_c32 = reinterpret_cast<RhsC<float>*>(base + kOffK32);
   L.cand_ok = reinterpret_cast<int32_t*>(base + kOffOk);
   L.cand_dead = reinterpret_cast<int32_t*>(base + kOffDead);
   L.cand_ss = reinterpret_cast<int32_t*>(base + kOffSs);

@@ -120,6 +120,21 @@ def state_perturbation(n: int, seed: int, rel: float = 0.1) -> np.ndarray:
     return rng.uniform(1.0 - rel, 1.0 + rel, size=(n, 3))
 
 
+def batched_instances(S: int, seed: int, N_lo: int = 64, N_hi: int = 8192, H_lo: int = 200,
+                      H_hi: int = 4000, rel: float = 0.1):
+    """S independent RG problems (seeded): scenario counts log-uniform on
+    [N_lo, N_hi], horizons uniform on {H_lo..H_hi}, (v_prev, r) uniform over
+    the operating range, and per-state factors uniform on [1 - rel, 1 + rel]
+    that the caller applies to the equilibrium of v_prev to get x_0."""
+    rng = np.random.default_rng(seed)
+    N = np.rint(np.exp(rng.uniform(np.log(N_lo), np.log(N_hi), size=S))).astype(np.int32)
+    H = rng.integers(H_lo, H_hi + 1, size=S).astype(np.int32)
+    v_prev = rng.uniform(I_MIN, I_MAX, size=S)
+    r = rng.uniform(I_MIN, I_MAX, size=S)
+    xfac = rng.uniform(1.0 - rel, 1.0 + rel, size=(S, 3))
+    return {"N": np.clip(N, N_lo, N_hi), "H": H, "v_prev": v_prev, "r": r, "xfac": xfac}
+
+
 def random_problems(n: int, seed: int):
     """(v_prev, r) pairs drawn uniformly over the operating range."""
     rng = np.random.default_rng(seed)

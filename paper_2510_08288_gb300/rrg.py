@@ -91,6 +91,18 @@ def _load():
                                              _p, _p, _p]),
         "rrg_eval_candidates_static": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, _p, _p, _p, _d,
                                                       _d, _p, ctypes.c_int, _p, _p]),
+        "rrg_batch_create": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), ctypes.c_int, _p, _p, _p, P(_p)]),
+        "rrg_batch_destroy": (ctypes.c_int, [_p]),
+        "rrg_batch_last_error": (ctypes.c_char_p, [_p]),
+        "rrg_batch_step_dev": (ctypes.c_int, [_p, _p, _p, _p, _u64, _u64, _p, _p, _p]),
+        "rrg_batch_closed_loop_dev": (ctypes.c_int, [_p, _p, _p, _p, ctypes.c_int, _u64, _u64, _p, ctypes.c_int,
+                                                     _p, _p, _p, _p]),
+        "rrg_batch_autotune": (ctypes.c_int, [_p, _p, _p, _p, _u64, _u64, ctypes.c_int, P(ctypes.c_int), _p]),
+        "rrg_batch_set_variant": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_batch_get_variant": (ctypes.c_int, [_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
+        "rrg_batch_set_profiling": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_batch_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
+        "rrg_batch_reset_stats": (ctypes.c_int, [_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -371,3 +383,174 @@ class Governor:
 
     def set_profiling(self, on):
         rrg_set_profiling(self.h, on)
+
+
+# ---------------------------------------------------------------- batched --
+BATCH_VARIANTS = 6
+
+
+def rrg_batch_last_error(h=None) -> str:
+    e = lib.rrg_batch_last_error(h)
+    return e.decode() if e else ""
+
+
+def _bcheck(rc, h=None):
+    if rc != RRG_OK:
+        raise RrgError(rc, rrg_batch_last_error(h))
+
+
+def rrg_batch_create(params, cfg: RrgConfig, n_scenarios, horizons, stream=None):
+    p = _f64(params)
+    ns = np.ascontiguousarray(np.asarray(n_scenarios, dtype=np.int32))
+    hz = np.ascontiguousarray(np.asarray(horizons, dtype=np.int32))
+    if ns.shape != hz.shape:
+        raise ValueError("n_scenarios and horizons differ in length")
+    h = _p()
+    _bcheck(lib.rrg_batch_create(_ptr(p), int(p.shape[0]), ctypes.byref(cfg), int(ns.shape[0]), _ptr(ns),
+                                 _ptr(hz), _stream_ptr(stream), ctypes.byref(h)), None)
+    return h
+
+
+def rrg_batch_destroy(h):
+    _bcheck(lib.rrg_batch_destroy(h))
+
+
+def rrg_batch_step_dev(h, d_x, d_r, d_v_prev, seed, update_index, d_v_t=None, d_kappa=None, d_flags=None):
+    _bcheck(lib.rrg_batch_step_dev(h, _tensor_ptr(d_x), _tensor_ptr(d_r), _tensor_ptr(d_v_prev), int(seed),
+                                   int(update_index), _tensor_ptr(d_v_t), _tensor_ptr(d_kappa),
+                                   _tensor_ptr(d_flags)), h)
+
+
+def rrg_batch_closed_loop_dev(h, d_x0, d_v0, d_r_seq, T, seed, t0, plant_amp, use_graph, d_v_out=None,
+                              d_kappa_out=None, d_flags_out=None, d_x_out=None):
+    amp = _f64(plant_amp)
+    _bcheck(lib.rrg_batch_closed_loop_dev(h, _tensor_ptr(d_x0), _tensor_ptr(d_v0), _tensor_ptr(d_r_seq), int(T),
+                                          int(seed), int(t0), _ptr(amp), int(bool(use_graph)),
+                                          _tensor_ptr(d_v_out), _tensor_ptr(d_kappa_out),
+                                          _tensor_ptr(d_flags_out), _tensor_ptr(d_x_out)), h)
+
+
+def rrg_batch_autotune(h, d_x, d_r, d_v_prev, seed, update_index, repeats=2):
+    """(chosen variant, mean rollout ms per update of each variant)."""
+    v = ctypes.c_int(0)
+    ms = np.zeros(BATCH_VARIANTS)
+    _bcheck(lib.rrg_batch_autotune(h, _tensor_ptr(d_x), _tensor_ptr(d_r), _tensor_ptr(d_v_prev), int(seed),
+                                   int(update_index), int(repeats), ctypes.byref(v), _ptr(ms)), h)
+    return v.value, ms
+
+
+def rrg_batch_set_variant(h, variant):
+    _bcheck(lib.rrg_batch_set_variant(h, int(variant)), h)
+
+
+def rrg_batch_get_variant(h):
+    """(variant, lanes per tile, prefetch depth)."""
+    v, t, f = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _bcheck(lib.rrg_batch_get_variant(h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(f)), h)
+    return v.value, t.value, f.value
+
+
+def rrg_batch_set_profiling(h, on):
+    _bcheck(lib.rrg_batch_set_profiling(h, int(bool(on))), h)
+
+
+def rrg_batch_get_stats(h) -> dict:
+    st = RrgStats()
+    _bcheck(lib.rrg_batch_get_stats(h, ctypes.byref(st)), h)
+    return {name: getattr(st, name) for name, _ in RrgStats._fields_}
+
+
+def rrg_batch_reset_stats(h):
+    _bcheck(lib.rrg_batch_reset_stats(h), h)
+
+
+class BatchGovernor:
+    """Owning wrapper of a batched handle; the host-array methods stage
+    through torch device tensors (argument marshalling only)."""
+
+    def __init__(self, params, cfg: RrgConfig, n_scenarios, horizons, stream=None):
+        self.params = _f64(params)
+        self.cfg = cfg
+        self.n_scenarios = np.asarray(n_scenarios, dtype=np.int32)
+        self.horizons = np.asarray(horizons, dtype=np.int32)
+        self.S = int(self.n_scenarios.shape[0])
+        self.stream = stream
+        self.h = rrg_batch_create(self.params, cfg, self.n_scenarios, self.horizons, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rrg_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, dtype=None):
+        import torch
+        if dtype is None:
+            dtype = torch.float64
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+    def _sync(self):
+        import torch
+        if self.stream is not None:
+            self.stream.synchronize()
+        torch.cuda.synchronize()
+
+    def step(self, x, r, v_prev, seed, update_index):
+        """One update from host arrays x[S, 3], r[S], v_prev[S]: (v_t, kappa, flags)."""
+        import torch
+        dx, dr, dv = self._dev(np.asarray(x).reshape(-1)), self._dev(r), self._dev(v_prev)
+        ov = torch.zeros(self.S, dtype=torch.float64, device="cuda")
+        ok = torch.zeros_like(ov)
+        of = torch.zeros(self.S, dtype=torch.int32, device="cuda")
+        self._sync()
+        rrg_batch_step_dev(self.h, dx, dr, dv, seed, update_index, ov, ok, of)
+        self._sync()
+        return ov.cpu().numpy(), ok.cpu().numpy(), of.cpu().numpy()
+
+    def closed_loop(self, x0, v0, r_seq, seed, t0, plant_amp, use_graph=True):
+        """T updates from host arrays: x0[S, 3], v0[S], r_seq[T, S]; returns
+        (v[T, S], kappa[T, S], flags[T, S], x[T + 1, S, 3])."""
+        import torch
+        r_seq = np.asarray(r_seq, dtype=np.float64)
+        T = int(r_seq.shape[0])
+        dx0, dv0, dr = self._dev(np.asarray(x0).reshape(-1)), self._dev(v0), self._dev(r_seq.reshape(-1))
+        ov = torch.zeros(T * self.S, dtype=torch.float64, device="cuda")
+        ok = torch.zeros_like(ov)
+        of = torch.zeros(T * self.S, dtype=torch.int32, device="cuda")
+        ox = torch.zeros((T + 1) * self.S * 3, dtype=torch.float64, device="cuda")
+        self._sync()
+        rrg_batch_closed_loop_dev(self.h, dx0, dv0, dr, T, seed, t0, plant_amp, use_graph, ov, ok, of, ox)
+        self._sync()
+        return (ov.cpu().numpy().reshape(T, self.S), ok.cpu().numpy().reshape(T, self.S),
+                of.cpu().numpy().reshape(T, self.S), ox.cpu().numpy().reshape(T + 1, self.S, 3))
+
+    def autotune(self, x, r, v_prev, seed, update_index, repeats=2):
+        dx, dr, dv = self._dev(np.asarray(x).reshape(-1)), self._dev(r), self._dev(v_prev)
+        self._sync()
+        return rrg_batch_autotune(self.h, dx, dr, dv, seed, update_index, repeats)
+
+    def set_variant(self, v):
+        rrg_batch_set_variant(self.h, v)
+
+    def get_variant(self):
+        return rrg_batch_get_variant(self.h)
+
+    def stats(self):
+        return rrg_batch_get_stats(self.h)
+
+    def reset_stats(self):
+        rrg_batch_reset_stats(self.h)
+
+    def set_profiling(self, on):
+        rrg_batch_set_profiling(self.h, on)

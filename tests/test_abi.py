@@ -119,3 +119,28 @@ def test_oracle_and_library_share_no_code():
     for f in ("rrg.py", "build.py", "inputs.py"):
         assert "import oracle" not in open(os.path.join(ROOT, "paper_2510_08288_gb300", f)).read()
         assert "from oracle" not in open(os.path.join(ROOT, "paper_2510_08288_gb300", f)).read()
+
+
+def test_batch_create_validation_without_gpu():
+    """The batched entry point rejects bad shapes and unsupported options
+    before any device work."""
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+    p = inputs.fc3_params()
+    ok = R.rrg_config_default(search=R.SEARCH_KSECTION, precision=R.FP32_RECHECK)
+    cases = [
+        (ok, [10, 0], [5, 5], R.RRG_EINVAL),
+        (ok, [10], [0], R.RRG_EINVAL),
+        (ok, [], [], R.RRG_EINVAL),
+        (ok, [1] * 1025, [1] * 1025, R.RRG_EINVAL),
+        (R.rrg_config_default(search=R.SEARCH_BISECT, precision=R.FP32_RECHECK), [4], [4], R.RRG_ENOTIMPL),
+        (R.rrg_config_default(search=R.SEARCH_GRID, precision=R.FP64), [4], [4], R.RRG_ENOTIMPL),
+        (R.rrg_config_default(search=R.SEARCH_GRID, precision=R.FP32_RECHECK, param_unc_rel=0.1), [4], [4],
+         R.RRG_ENOTIMPL),
+        (R.rrg_config_default(search=R.SEARCH_GRID, precision=R.FP32_RECHECK, max_candidates=1024), [2 ** 21], [4],
+         R.RRG_EINVAL),
+    ]
+    for cfg, ns, hz, code in cases:
+        with pytest.raises(R.RrgError) as e:
+            R.rrg_batch_create(p, cfg, ns, hz)
+        assert e.value.code == code, (ns, hz, str(e.value))

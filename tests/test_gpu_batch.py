@@ -1,0 +1,162 @@
+"""Batched instances (many independent RG problems in one persistent launch
+per round) against the oracle, through the C ABI.
+
+Instance s draws its scenarios with seed + s, so each instance's result must
+equal the oracle's Alg. 3 or k-section on that instance's own draw; the
+batch's binary32 rollouts with the binary64 recheck decide like binary64
+whenever the band covers the binary32 error (same tolerances as the
+single-problem tests: identical kappa, v_t and flags).
+"""
+import numpy as np
+import pytest
+
+from paper_2510_08288_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BAND = 2e-4 / 1.9
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import rrg
+    return rrg
+
+
+def _problem(orc, params, S, seed, **kw):
+    b = inputs.batched_instances(S, seed, **kw)
+    x = np.array([orc.equilibrium(params, b["v_prev"][s]) * b["xfac"][s] for s in range(S)])
+    return b, x
+
+
+def _cfg(R, M, search, **kw):
+    base = dict(max_candidates=M, n_rounds=3, search=search, precision=R.FP32_RECHECK,
+                early_exit=R.EXIT_CANDIDATE, recheck_eps_rel=BAND)
+    base.update(kw)
+    return R.rrg_config_default(**base)
+
+
+def _oracle(orc, params, kind, x, v_prev, r, d, N, H, M, rounds=3):
+    c = orc.cfg(H=H, N=N)
+    if kind == "grid":
+        return orc.alg3(params, c, x, v_prev, r, M, d)
+    return orc.ksection(params, c, x, v_prev, r, M, rounds, d)
+
+
+@pytest.mark.parametrize("kind", ["ksection", "grid"])
+@pytest.mark.parametrize("M", [2, 7, 32])
+def test_batch_step_matches_oracle(R, orc, params, kind, M):
+    S, seed, upd = 9, 7, 3
+    b, x = _problem(orc, params, S, 5, N_lo=1, N_hi=300, H_lo=1, H_hi=250)
+    search = R.SEARCH_KSECTION if kind == "ksection" else R.SEARCH_GRID
+    with R.BatchGovernor(params, _cfg(R, M, search), b["N"], b["H"]) as g:
+        v, k, f = g.step(x, b["r"], b["v_prev"], seed, upd)
+    for s in range(S):
+        N, H = int(b["N"][s]), int(b["H"][s])
+        d = orc.sample_disturbances(seed + s, upd, N, H, inputs.DIST_AMP)
+        ko, fo = _oracle(orc, params, kind, x[s], b["v_prev"][s], b["r"][s], d, N, H, M)
+        assert (k[s], f[s]) == (ko, fo), s
+        assert v[s] == orc.governed(b["v_prev"][s], b["r"][s], ko)
+
+
+def test_batch_uneven_sizes_and_invalid_instance(R, orc, params):
+    """Very uneven instances (1 .. 3,000 scenarios, horizons 1 .. 900), one
+    with a non-finite state (holds with flag bit 1), one with r = v_prev."""
+    N = np.array([1, 3000, 64, 129, 1, 700, 2], dtype=np.int32)
+    H = np.array([900, 50, 1, 333, 2, 120, 600], dtype=np.int32)
+    S = N.shape[0]
+    v_prev = np.array([100.0, 150.0, 60.0, 220.0, 80.0, 120.0, 290.0])
+    r = np.array([250.0, 160.0, 300.0, 100.0, 80.0, 200.0, 60.0])
+    x = np.array([orc.equilibrium(params, v) for v in v_prev])
+    x[2, 1] = np.nan
+    with R.BatchGovernor(params, _cfg(R, 16, R.SEARCH_KSECTION), N, H) as g:
+        v, k, f = g.step(x, r, v_prev, 11, 0)
+    assert f[2] & 2 and k[2] == 0.0 and v[2] == v_prev[2]
+    for s in range(S):
+        if s == 2:
+            continue
+        d = orc.sample_disturbances(11 + s, 0, int(N[s]), int(H[s]), inputs.DIST_AMP)
+        ko, fo = _oracle(orc, params, "ksection", x[s], v_prev[s], r[s], d, int(N[s]), int(H[s]), 16)
+        assert (k[s], f[s]) == (ko, fo), s
+    assert k[4] == 1.0
+
+
+def test_all_rollout_variants_agree_and_autotune_picks_one(R, orc, params):
+    S = 12
+    b, x = _problem(orc, params, S, 9, N_lo=16, N_hi=2000, H_lo=50, H_hi=400)
+    with R.BatchGovernor(params, _cfg(R, 16, R.SEARCH_KSECTION), b["N"], b["H"]) as g:
+        outs = []
+        for var in range(R.BATCH_VARIANTS):
+            g.set_variant(var)
+            assert g.get_variant()[0] == var
+            outs.append(g.step(x, b["r"], b["v_prev"], 3, 1))
+        best, ms = g.autotune(x, b["r"], b["v_prev"], 3, 1, repeats=1)
+        assert 0 <= best < R.BATCH_VARIANTS and g.get_variant()[0] == best
+        assert np.all(ms > 0) and ms[best] == ms.min()
+        after = g.step(x, b["r"], b["v_prev"], 3, 1)
+    for o in outs[1:] + [after]:
+        for a, c in zip(outs[0], o):
+            np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_closed_loop_matches_oracle(R, orc, params, use_graph):
+    """T closed-loop updates of every instance (plants included) equal the
+    oracle's closed loop of each instance with seed + s; a continued loop
+    (two calls) equals one call."""
+    S, T, M, seed, t0 = 5, 4, 8, 21, 2
+    b, x0 = _problem(orc, params, S, 13, N_lo=4, N_hi=200, H_lo=20, H_hi=160)
+    r_seq = np.stack([inputs.staircase(T, 2, 2, seed=40 + s) for s in range(S)], axis=1)
+    amp = inputs.DIST_AMP
+    with R.BatchGovernor(params, _cfg(R, M, R.SEARCH_KSECTION), b["N"], b["H"]) as g:
+        v, k, f, xs = g.closed_loop(x0, b["v_prev"], r_seq, seed, t0, amp, use_graph=use_graph)
+    for s in range(S):
+        c = orc.cfg(H=int(b["H"][s]), N=int(b["N"][s]))
+        vo, ko, fo, xo = orc.closed_loop(params, c, x0[s], b["v_prev"][s], r_seq[:, s], seed + s, t0, amp, amp,
+                                         search=2, M=M, rounds=3)
+        np.testing.assert_array_equal(k[:, s], ko)
+        np.testing.assert_array_equal(f[:, s], fo)
+        np.testing.assert_array_equal(v[:, s], vo)
+        np.testing.assert_allclose(xs[:, s], xo, rtol=1e-10)
+
+
+def test_batch_closed_loop_continues(R, orc, params):
+    import torch
+    S, T, M, seed = 4, 4, 8, 5
+    b, x0 = _problem(orc, params, S, 17, N_lo=4, N_hi=100, H_lo=20, H_hi=100)
+    r_seq = np.stack([inputs.staircase(T, 2, 2, seed=60 + s) for s in range(S)], axis=1)
+    amp = inputs.DIST_AMP
+    cfg = _cfg(R, M, R.SEARCH_KSECTION)
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        one = g.closed_loop(x0, b["v_prev"], r_seq, seed, 0, amp)
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+        dr = dev(r_seq.reshape(-1))
+        ov = torch.zeros(T * S, dtype=torch.float64, device="cuda")
+        ok = torch.zeros_like(ov)
+        of = torch.zeros(T * S, dtype=torch.int32, device="cuda")
+        ox = torch.zeros((T + 1) * S * 3, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        R.rrg_batch_closed_loop_dev(g.h, dev(x0.reshape(-1)), dev(b["v_prev"]), dr, 2, seed, 0, amp, True,
+                                    ov, ok, of, ox)
+        R.rrg_batch_closed_loop_dev(g.h, None, None, dr, 2, seed, 0, amp, True, ov, ok, of, ox)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ok.cpu().numpy().reshape(T, S), one[1])
+        np.testing.assert_array_equal(ox.cpu().numpy().reshape(T + 1, S, 3), one[3])
+
+
+def test_batch_stats_count_steps(R, orc, params):
+    S = 3
+    b, x = _problem(orc, params, S, 23, N_lo=10, N_hi=50, H_lo=10, H_hi=40)
+    with R.BatchGovernor(params, _cfg(R, 4, R.SEARCH_GRID, early_exit=R.EXIT_NONE), b["N"], b["H"]) as g:
+        g.set_profiling(True)
+        g.step(x, b["r"], b["v_prev"], 1, 0)
+        st = g.stats()
+    # no early exit: every candidate that passes the steady-state check runs N H steps
+    assert st["lane_steps"] - st["lane_steps_fp64"] <= int(np.sum(4 * b["N"] * b["H"]))
+    assert st["rollout_launches"] == 1 and st["timed_rollouts"] == 1 and st["rollout_ms"] > 0
