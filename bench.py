@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
                     help="steps of the probe that pipelines the first two bisection rounds (0: off)")
-    ap.add_argument("--workload", choices=("closed_loop", "sweep"), default="closed_loop")
+    ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch"), default="closed_loop")
+    ap.add_argument("--instances", type=int, default=BATCH_S, help="batch: number of RG instances")
     ap.add_argument("--sweep-n", type=str, default=",".join(str(n) for n in SWEEP_N),
                     help="scenario counts of the sweep")
     ap.add_argument("--param-unc-rel", type=float, default=None,
@@ -424,6 +425,160 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ batch --
+BATCH_S, BATCH_M, BATCH_ROUNDS, BATCH_SEED = 256, 32, 3, 2
+BATCH_METRIC = "RG updates/s (instance updates, batched) & trajectory-steps/s; FP32 + FP64 recheck"
+
+
+def batch_config(S, W, K, variant):
+    return {"workload": "batched instances on FC3: %d independent RG problems advanced together per step "
+                        "(closed loop with plants), scenario counts log-uniform on [64, 8192], horizons "
+                        "uniform on {200..4000} (seed %d), x_0 = equilibrium of v_prev x U[0.9, 1.1] per "
+                        "state, v_prev and r per instance uniform on 50..300 A; k-section with %d candidates "
+                        "per round, %d rounds; one persistent rollout launch per round" %
+                        (S, BATCH_SEED, BATCH_M, BATCH_ROUNDS),
+            "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
+            "timed": "updates [%d, %d) of the graph-replayed closed loop" % (W, W + K),
+            "rollout_variant": variant, "l2": "256 MB written between timed steps"}
+
+
+def batch_inputs(R, p, S):
+    import numpy as np
+    from paper_2510_08288_gb300 import inputs
+    b = inputs.batched_instances(S, BATCH_SEED)
+    with R.Governor(p, R.rrg_config_default(horizon=1, n_scenarios=1, max_candidates=2)) as g1:
+        x0 = np.array([g1.equilibrium(v)[0] for v in b["v_prev"]]) * b["xfac"]
+    return b, x0
+
+
+def batch_cpu(p, b, x0, r, seconds, cores):
+    """The FP64 oracle's k-section on a bounded sample: whole instances (the
+    shortest first) for one update each, until about `seconds` are spent."""
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    order = sorted(range(len(b["N"])), key=lambda s: int(b["N"][s]) * int(b["H"][s]))
+    done, t_total = 0, 0.0
+    for s in order:
+        N, H = int(b["N"][s]), int(b["H"][s])
+        d = O.sample_disturbances(SEED + s, 0, N, H, inputs.DIST_AMP)
+        t0 = time.perf_counter()
+        O.ksection(p, O.cfg(H=H, N=N), x0[s], b["v_prev"][s], r[s], BATCH_M, BATCH_ROUNDS, d, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if t_total > seconds:
+            break
+    return {"value": done / t_total, "unit": "RG updates/s (instance updates)", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d instances (smallest N*H first: biased towards cheap ones), one update each, "
+                      "FP64 k-section, %.1f s" % (done, len(b["N"]), t_total)}
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    p = inputs.fc3_params()
+    S, W, K = args.instances, args.warmup, args.steps
+    K2 = min(K, 5)        # extra updates without the graph, for the kernel timing
+    T = W + K + K2
+    b, x0 = batch_inputs(R, p, S)
+    r = b["r"]
+    r_seq = np.tile(r, (T, 1))
+    amp = np.array(inputs.DIST_AMP)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    cfg = R.rrg_config_default(max_candidates=BATCH_M, n_rounds=BATCH_ROUNDS, search=R.SEARCH_KSECTION,
+                               precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
+                               recheck_eps_rel=RECHECK_EPS_REL)
+    g = R.BatchGovernor(p, cfg, b["N"], b["H"], stream)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    dx0, dv0, dr = d(x0.reshape(-1)), d(b["v_prev"]), d(r_seq.reshape(-1))
+    torch.cuda.synchronize()
+    best, tune_ms = R.rrg_batch_autotune(g.h, dx0, d(r), dv0, SEED, 0, 1)
+    dv = torch.zeros(T * S, dtype=torch.float64, device=dev)
+    dk = torch.zeros_like(dv)
+    df = torch.zeros(T * S, dtype=torch.int32, device=dev)
+    dxo = torch.zeros((T + 1) * S * 3, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    R.rrg_batch_closed_loop_dev(g.h, dx0, dv0, dr, W, SEED, 0, amp, True, dv, dk, df, dxo)
+    torch.cuda.synchronize()
+    g.reset_stats()
+    g.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            R.rrg_batch_closed_loop_dev(g.h, None, None, dr, 1, SEED, 0, amp, True, dv, dk, df, dxo)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(c) for a, c in evs) / 1e3
+    st = g.stats()
+    # graph replays cannot time single kernels: K2 more updates with direct
+    # launches give the rollout kernel's duration (CUDA events in the library)
+    g.reset_stats()
+    R.rrg_batch_closed_loop_dev(g.h, None, None, dr, K2, SEED, 0, amp, False, dv, dk, df, dxo)
+    st2 = g.stats()
+    g.set_profiling(False)
+    kap = dk.cpu().numpy().reshape(T, S)
+    flags = df.cpu().numpy().reshape(T, S)
+    fp32_steps = st2["lane_steps"] - st2["lane_steps_fp64"]
+    avg_roll_ms = st2["rollout_ms"] / max(1, st2["timed_rollouts"])
+    achieved = (fp32_steps / max(1, st2["timed_rollouts"])) * FLOPS_PER_STEP / (avg_roll_ms * 1e-3) / 1e12
+    variant = R.rrg_batch_get_variant(g.h)
+    # e2e: the same K updates through the host-array call (copies included),
+    # on a fresh handle that first replays the warm-up updates
+    e2e = None
+    if not args.no_e2e:
+        g2 = R.BatchGovernor(p, cfg, b["N"], b["H"], stream)
+        g2.set_variant(variant[0])
+        xw = dxo.cpu().numpy().reshape(T + 1, S, 3)[W]
+        vw = dv.cpu().numpy().reshape(T, S)[W - 1] if W else b["v_prev"]
+        t0 = time.perf_counter()
+        v2, k2, f2, x2 = g2.closed_loop(xw, vw, r_seq[W:W + K], SEED, W, amp)
+        e2e_s = time.perf_counter() - t0
+        g2.close()
+        e2e = {"value": S * K / e2e_s, "unit": "RG updates/s (instance updates)",
+               # per call: x_0, v_0 and the K x S references in; v, kappa,
+               # flags and the K + 1 states out
+               "h2d_bytes_per_step": (4 * S * 8) // K + S * 8,
+               "d2h_bytes_per_step": S * (8 + 8 + 4) + ((K + 1) * S * 3 * 8) // K,
+               "kappa_equal_to_device_run": bool(np.array_equal(k2, kap[W:W + K]))}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = batch_cpu(p, b, x0, r, args.cpu_seconds, os.cpu_count() or 1)
+    g.close()
+    out = {
+        "metric": BATCH_METRIC, "value": S * K / secs, "unit": "RG updates/s (instance updates)", "n_gpus": 1,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": batch_config(S, W, K, {"index": variant[0], "tile_lanes": variant[1], "prefetch": variant[2]}),
+        "trajectory_steps_per_s": {"executed": st["lane_steps"] / secs, "executed_per_step": st["lane_steps"] / K},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "batch_rollout_kernel<%d, %d>" % (variant[1], variant[2]),
+                     "avg_launch_ms": avg_roll_ms, "launches": st2["timed_rollouts"],
+                     "timing": "%d direct-launch updates after the timed ones" % K2,
+                     "flops_per_traj_step": FLOPS_PER_STEP,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
+        "autotune_rollout_ms": [float(x) for x in tune_ms],
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": st["launches"],
+        "rechecked_trajectories": st["rechecked"],
+        "no_admissible_fraction": float(np.mean(flags[W:W + K] & 1)),
+        "kappa_mean": float(np.mean(kap[W:W + K])),
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ sweep --
 SWEEP_METRIC = "trajectory-steps/s vs scenario count (large sweep, FP32 + FP64 recheck)"
 
@@ -573,6 +728,8 @@ def main():
         return run_reference(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

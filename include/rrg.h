@@ -372,7 +372,7 @@ int rrg_reset_stats(rrg_handle h);
  * RRG_ECUDA. */
 #define RRG_STATIC_MAX_CANDIDATES 64
 #define RRG_STATIC_MAX_LANES 131072
-#define RRG_STATIC_SCRATCH_BYTES (1u << 20)
+#define RRG_STATIC_SCRATCH_BYTES (2u << 20)
 int rrg_eval_candidates_static(const double *model_params, int n_params, const rrg_config *cfg,
                                void *cuda_stream, const double *d_scen64, const float *d_scen32,
                                const double *d_x_t, double v_prev, double r_t,

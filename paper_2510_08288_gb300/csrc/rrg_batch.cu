@@ -84,6 +84,7 @@ struct BLaunch {
   int32_t* tile_base;  // [S + 1] over `order`
   uint32_t* queue;     // [0] next tile, [1] tiles of the round
   uint2* recheck_list; // (slot, k)
+  uint32_t* recheck_jlast;  // the recheck runs steps 0..jlast
   uint32_t* recheck_count;
   unsigned long long recheck_cap;
   DevStats* stats;
@@ -229,6 +230,7 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
   const float thr = B.c.early_exit != RRG_EXIT_NONE ? -eps : -inf_v<float>();
   float smin = inf_v<float>();
   unsigned steps = 0;
+  int jlast = -1;
   if (active) {
     const BState& st = B.st[s];
     const double p_atm = B.params[P_P_ATM];
@@ -238,7 +240,7 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
     smin = run_lane<float, PF>(B.u32, B.cand_c32[slot], B.d32 + I.off, k, I.N, I.H, 0, I.H, q_ca,
                                w, q_sm, inf_v<float>(), static_cast<float>(B.c.dt),
                                static_cast<float>(B.c.y_min), thr, cand_stop ? dead : nullptr,
-                               &steps, &end);
+                               &steps, &end, eps, &jlast);
     if (cand_stop && smin < thr) *dead = 1;
   }
   bool lane_ok = true, uncertain = false;
@@ -255,7 +257,10 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
   }
   if (uncertain && *dead == 0) {
     const uint32_t e = atomicAdd(B.recheck_count, 1u);
-    if (e < B.recheck_cap) B.recheck_list[e] = make_uint2(static_cast<uint32_t>(slot), static_cast<uint32_t>(k));
+    if (e < B.recheck_cap) {
+      B.recheck_list[e] = make_uint2(static_cast<uint32_t>(slot), static_cast<uint32_t>(k));
+      B.recheck_jlast[e] = static_cast<uint32_t>(jlast);
+    }
   }
   const bool all_ok = __all_sync(0xffffffffu, lane_ok);
   const double wmin = warp_min(contrib);
@@ -302,7 +307,8 @@ __global__ void __launch_bounds__(TILE) batch_rollout_kernel(const BLaunch B) {
   }
 }
 
-// Binary64 re-run (disturbances regenerated from the Philox counters).
+// Binary64 re-run (disturbances regenerated from the Philox counters) over
+// steps 0..jlast of each listed lane.
 __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
   const uint32_t count = min(*B.recheck_count, static_cast<uint32_t>(B.recheck_cap));
   const double p_atm = B.params[P_P_ATM];
@@ -322,7 +328,8 @@ __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
     src.amp[1] = B.c.amp[1];
     src.amp[2] = B.c.amp[2];
     unsigned steps = 0;
-    const double smin = run_lane_philox(B.u64, B.cand_c64[slot], src, k, B.inst[s].H,
+    const double smin = run_lane_philox(B.u64, B.cand_c64[slot], src, k,
+                                        min(static_cast<int>(B.recheck_jlast[e]), B.inst[s].H),
                                         st.x[0] - p_atm, st.x[1], st.x[2] - p_atm, B.c.dt,
                                         B.c.y_min,
                                         B.c.early_exit != RRG_EXIT_NONE ? 0.0 : -inf_v<double>(),
@@ -488,6 +495,7 @@ struct rrg_batch_ctx {
   int32_t* tile_base = nullptr;
   uint32_t* queue = nullptr;
   uint2* recheck_list = nullptr;
+  uint32_t* recheck_jlast = nullptr;
   uint32_t* recheck_count = nullptr;
   DevStats* stats = nullptr;
   unsigned long long* t_dev = nullptr;
@@ -542,7 +550,8 @@ struct BDeviceGuard {
 void bfree_all(rrg_batch_ctx* h) {
   void* ptrs[] = {h->params_dev, h->inst_dev, h->order_dev, h->st, h->d32, h->cand_kappa,
                   h->cand_v, h->cand_c64, h->cand_c32, h->cand_ok, h->cand_dead, h->cand_ss,
-                  h->cand_min, h->tile_base, h->queue, h->recheck_list, h->recheck_count,
+                  h->cand_min, h->tile_base, h->queue, h->recheck_list, h->recheck_jlast,
+                  h->recheck_count,
                   h->stats, h->t_dev, h->amp_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -712,6 +721,7 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   alloc(&h->tile_base, S + 1);
   alloc(&h->queue, 2);
   alloc(&h->recheck_list, static_cast<size_t>(lanes));
+  alloc(&h->recheck_jlast, static_cast<size_t>(lanes));
   alloc(&h->recheck_count, 1);
   alloc(&h->stats, 1);
   alloc(&h->t_dev, 1);
@@ -782,6 +792,7 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   B.tile_base = h->tile_base;
   B.queue = h->queue;
   B.recheck_list = h->recheck_list;
+  B.recheck_jlast = h->recheck_jlast;
   B.recheck_count = h->recheck_count;
   B.recheck_cap = lanes;
   B.stats = h->stats;

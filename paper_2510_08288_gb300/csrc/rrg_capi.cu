@@ -62,6 +62,7 @@ struct rrg_ctx {
   int32_t* cand_ss = nullptr;
   unsigned long long* cand_min = nullptr;
   uint32_t* recheck_list = nullptr;
+  uint32_t* recheck_jlast = nullptr;
   uint32_t* recheck_count = nullptr;
   DevStats* stats = nullptr;
   void* lane_state = nullptr;
@@ -167,7 +168,7 @@ cudaError_t dalloc(T** p, size_t n) {
 void free_all(rrg_ctx* h) {
   void* ptrs[] = {h->params_dev, h->d64, h->d32, h->d64b, h->d32b, h->st, h->cand_kappa,
                   h->cand_v, h->cand_c64, h->cand_c32, h->cand_ok, h->cand_dead, h->cand_ss,
-                  h->cand_min, h->recheck_list, h->recheck_count, h->stats, h->P_dev, h->io_dev,
+                  h->cand_min, h->recheck_list, h->recheck_jlast, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state,
                   h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
                   h->pmul, h->pmulb};
@@ -213,6 +214,7 @@ void fill_launch(rrg_ctx* h) {
   L.cand_ss = h->cand_ss;
   L.cand_min = h->cand_min;
   L.recheck_list = h->recheck_list;
+  L.recheck_jlast = h->recheck_jlast;
   L.recheck_count = h->recheck_count;
   L.stats = h->stats;
   L.P = nullptr;
@@ -403,6 +405,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   ALLOC(cand_ss, 2 * M);
   ALLOC(cand_min, 2 * M);
   ALLOC(recheck_list, 2 * M * N);
+  ALLOC(recheck_jlast, 2 * M * N);
   if (e == cudaSuccess && c.search == RRG_SEARCH_SPEC_BISECT && c.probe_steps > 0) {
     e = cudaMalloc(&h->lane_state, M * N * sizeof(LaneState<double>));
     if (e != cudaSuccess) cudaGetLastError();

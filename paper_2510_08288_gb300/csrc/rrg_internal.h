@@ -43,6 +43,7 @@ struct LaneState {
   T q[3];
   T smin;
   int32_t status;
+  int32_t jlast;  // last step with slack below the recheck band so far (-1: none)
 };
 
 // Origin of a scenario pair.  In the binary32 modes the sampler writes only
@@ -141,6 +142,7 @@ struct Launch {
   int32_t* cand_ss;    // steady-state check passed
   unsigned long long* cand_min;
   uint32_t* recheck_list;
+  uint32_t* recheck_jlast;      // per entry: the recheck runs steps 0..jlast
   uint32_t* recheck_count;
   DevStats* stats;
   uint8_t* P;                   // optional

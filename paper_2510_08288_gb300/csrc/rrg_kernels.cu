@@ -239,6 +239,8 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
 
   T smin = inf_v<T>();
   unsigned steps = 0;
+  int jlast = -1;
+  const T band = classify ? eps : -inf_v<T>();
   bool final_lane = active;  // this launch decides the lane
   if (active) {
     LaneState<T>* ls = mode == SEG_FULL ? nullptr
@@ -262,6 +264,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
         w = st.q[1];
         q_sm = st.q[2];
         smin0 = st.smin;
+        jlast = st.jlast;
         j0 = L.probe_steps;
       }
     }
@@ -270,7 +273,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
       int end = LANE_REACHED_END;
       smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, smin0,
                          static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
-                         cand_stop ? dead : nullptr, &steps, &end);
+                         cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
       if (cand_stop && smin < thr) *dead = 1;
       if (mode == SEG_PROBE) {
         LaneState<T> o;
@@ -279,6 +282,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
         o.q[2] = q_sm;
         o.smin = smin;
         o.status = end == LANE_REACHED_END ? 0 : 1;
+        o.jlast = jlast;
         *ls = o;
         if (end == LANE_REACHED_END) final_lane = false;
       }
@@ -304,6 +308,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
   if (uncertain && *dead == 0) {
     const uint32_t slot = atomicAdd(L.recheck_count, 1u);
     L.recheck_list[slot] = static_cast<uint32_t>(i) * static_cast<uint32_t>(N) + static_cast<uint32_t>(k);
+    L.recheck_jlast[slot] = static_cast<uint32_t>(jlast);
   }
   if (L.P != nullptr && final_lane) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
 
@@ -366,7 +371,8 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
   return cudaGetLastError();
 }
 
-// Binary64 re-run of the trajectories the binary32 pass could not decide.
+// Binary64 re-run of the trajectories the binary32 pass could not decide,
+// over steps 0..jlast of each (the later steps were decided in binary32).
 __global__ void __launch_bounds__(64)
 recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
   const uint32_t count = *L.recheck_count;
@@ -377,6 +383,7 @@ recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
   const ScenSrc src = L.st->src[buf];
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
     const uint32_t idx = L.recheck_list[e];
+    const int j_end = min(static_cast<int>(L.recheck_jlast[e]), L.H);
     const int i = static_cast<int>(idx / static_cast<uint32_t>(N));
     const int k = static_cast<int>(idx - static_cast<uint32_t>(i) * static_cast<uint32_t>(N));
     // a failed candidate needs no more decisions, unless P asks for every entry
@@ -393,10 +400,12 @@ recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
     if (src.d64_valid) {
       int end = 0;
       double q_ca = L.st->x[0] - p_atm_k, w = L.st->x[1], q_sm = L.st->x[2] - p_atm_k;
-      smin = run_lane<double>(K, C, buf ? L.d64b : L.d64, k, N, L.H, 0, L.H, q_ca, w, q_sm,
-                              inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps, &end);
+      int jl = -1;
+      smin = run_lane<double>(K, C, buf ? L.d64b : L.d64, k, N, L.H, 0, j_end, q_ca, w, q_sm,
+                              inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps, &end,
+                              -inf_v<double>(), &jl);
     } else {
-      smin = run_lane_philox(K, C, src, k, L.H, L.st->x[0] - p_atm_k, L.st->x[1],
+      smin = run_lane_philox(K, C, src, k, j_end, L.st->x[0] - p_atm_k, L.st->x[1],
                              L.st->x[2] - p_atm_k, L.dt, L.y_min, thr, &steps);
     }
     const bool ok = smin >= 0.0;

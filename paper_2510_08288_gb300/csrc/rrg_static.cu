@@ -32,7 +32,8 @@ constexpr size_t kOffMin = kOffSs + align256(kStaticMaxCand * sizeof(int32_t));
 constexpr size_t kOffCount = kOffMin + align256(kStaticMaxCand * sizeof(unsigned long long));
 constexpr size_t kOffStats = kOffCount + align256(sizeof(uint32_t));
 constexpr size_t kOffList = kOffStats + align256(sizeof(DevStats));
-constexpr size_t kScratchBytes = kOffList + align256(kStaticMaxLanes * sizeof(uint32_t));
+constexpr size_t kOffJlast = kOffList + align256(kStaticMaxLanes * sizeof(uint32_t));
+constexpr size_t kScratchBytes = kOffJlast + align256(kStaticMaxLanes * sizeof(uint32_t));
 static_assert(kScratchBytes <= RRG_STATIC_SCRATCH_BYTES, "scratch layout exceeds its stated size");
 
 // The scratch itself: held by every device that loads the library.
@@ -162,6 +163,7 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
   L.recheck_count = reinterpret_cast<uint32_t*>(base + kOffCount);
   L.stats = reinterpret_cast<DevStats*>(base + kOffStats);
   L.recheck_list = reinterpret_cast<uint32_t*>(base + kOffList);
+  L.recheck_jlast = reinterpret_cast<uint32_t*>(base + kOffJlast);
   L.P = nullptr;
   L.recheck_blocks = 2 * 152;
 

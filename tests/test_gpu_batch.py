@@ -160,3 +160,22 @@ def test_batch_stats_count_steps(R, orc, params):
     # no early exit: every candidate that passes the steady-state check runs N H steps
     assert st["lane_steps"] - st["lane_steps_fp64"] <= int(np.sum(4 * b["N"] * b["H"]))
     assert st["rollout_launches"] == 1 and st["timed_rollouts"] == 1 and st["rollout_ms"] > 0
+
+
+def test_batch_recheck_runs_only_to_the_last_uncertain_step(R, orc, params):
+    """As the single-problem test: disturbance-free instances whose hold
+    candidate sits 1e-7 above y_min at j = 0 only; the grid's kappa = 0 is
+    admissible, every lane of it is rechecked, and no binary64 step runs."""
+    S, N, H = 3, 200, 300
+    x = np.array([orc.equilibrium(params, 100.0) * np.array([1.0, 1.0, 0.999])] * S)
+    y_min = orc.output(params, x[0], 100.0) - 1e-7
+    cfg = _cfg(R, 4, R.SEARCH_GRID, y_min=y_min, ss_check=0, dist_amp=(0.0, 0.0, 0.0),
+               recheck_eps_rel=1e-6, early_exit=R.EXIT_LANE)
+    with R.BatchGovernor(params, cfg, [N] * S, [H] * S) as g:
+        v, k, f = g.step(x, np.full(S, 150.0), np.full(S, 100.0), 0, 0)
+        st = g.stats()
+    for s in range(S):
+        ko, fo = orc.alg3(params, orc.cfg(H=H, N=N, y_min=y_min, ss_check=0), x[s], 100.0, 150.0, 4,
+                          np.zeros((3, H, N)))
+        assert (k[s], f[s]) == (ko, fo) == (0.0, 0)
+    assert st["rechecked"] == S * N and st["lane_steps_fp64"] == 0

@@ -400,3 +400,28 @@ def test_pipelined_spec_bisect_equals_bisect(R, orc, params, probe, prec):
         assert kap == k_o and fl == f_o, (v_prev, r, kap, k_o)
     if probe == 1:
         assert repairs > 0
+
+
+def test_recheck_runs_only_to_the_last_uncertain_step(R, orc, params):
+    """A lane whose binary32 slack is inside the band only at j = 0 (here y_min
+    sits 1e-7 below the candidate's initial output, disturbance-free, and the
+    OER rises by more than 0.01 at once and stays there) is rechecked in binary64 over step 0 alone: every
+    lane is rechecked, no binary64 step runs, and the decisions equal the
+    oracle's."""
+    N, H = 300, 500
+    x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.0, 0.999])
+    y_min = orc.output(params, x_t, 100.0) - 1e-7
+    kappas = np.array([0.0, 0.001])
+    cfg = _cfg(R, N, H, precision=R.FP32_RECHECK, early_exit=R.EXIT_LANE, max_candidates=2,
+               y_min=y_min, ss_check=0, dist_amp=(0.0, 0.0, 0.0), recheck_eps_rel=1e-6)
+    with R.Governor(params, cfg) as g:
+        g.sample_scenarios(0, 0)
+        adm, ms, P = g.eval_candidates(x_t, 100.0, 150.0, kappas, want_P=True)
+        st = g.stats()
+    d = np.zeros((3, H, N))
+    a_o, ms_o, P_o, _ = orc.eval_candidates(params, orc.cfg(H=H, N=N, y_min=y_min, ss_check=0, early_exit=0),
+                                            x_t, 100.0, 150.0, kappas, d, want_P=True)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+    assert list(adm) == [1, 0]
+    assert st["rechecked"] == N and st["lane_steps_fp64"] == 0
