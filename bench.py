@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
                     help="steps of the probe that pipelines the first two bisection rounds (0: off)")
-    ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch"), default="closed_loop")
+    ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch", "single", "adjoint"),
+                    default="closed_loop")
     ap.add_argument("--instances", type=int, default=BATCH_S, help="batch: number of RG instances")
     ap.add_argument("--sweep-n", type=str, default=",".join(str(n) for n in SWEEP_N),
                     help="scenario counts of the sweep")
@@ -579,6 +580,167 @@ def run_batch(args):
     return 0
 
 
+# ----------------------------------------------------- single update (cfg 1) --
+SINGLE_METRIC = "RG update latency (single robust update, 32 scenarios x 500 steps, N_kappa = 12)"
+
+
+def timed_updates(R, torch, g, x_t, r, v_prev, W, K, seed, flush, stream):
+    """W + K updates (sample + search) through the host-buffer calls; device
+    time of each of the last K from CUDA events on the library's stream."""
+    kap = None
+    ms = []
+    for i in range(W + K):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        g.sample_scenarios(seed, 0)
+        _, kap, fl = g.step(x_t, r, v_prev)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= W:
+            ms.append((a.elapsed_time(b), 1e3 * (time.perf_counter() - t0)))
+    return kap, fl, ms
+
+
+def run_single(args):
+    import numpy as np
+    import torch
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    w = inputs.WORKLOADS["single"]
+    p = inputs.fc3_params()
+    W, K = args.warmup, args.steps
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    legs = {}
+    for name, search, prec, M in (("fp64_bisect", R.SEARCH_BISECT, R.FP64, 2),
+                                  ("fp32_recheck_spec", R.SEARCH_SPEC_BISECT, R.FP32_RECHECK, 64)):
+        cfg = R.rrg_config_default(horizon=w["H"], n_scenarios=w["N"], max_candidates=M, n_bisect=w["n_bisect"],
+                                   search=search, precision=prec, early_exit=R.EXIT_CANDIDATE,
+                                   recheck_eps_rel=RECHECK_EPS_REL)
+        with R.Governor(p, cfg, stream) as g:
+            x_t, _ = g.equilibrium(w["v_prev"])
+            kap, fl, ms = timed_updates(R, torch, g, x_t, w["r"], w["v_prev"], W, K, w["seed"], flush, stream)
+            st = g.stats()
+        dev = [a for a, _ in ms]
+        legs[name] = {"ms_per_update": statistics.median(dev), "host_ms_per_update": statistics.median([b for _, b in ms]),
+                      "kappa": kap, "flags": fl, "gpu_launches_per_update": st["launches"] // (W + K)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        x_o = O.equilibrium(p, w["v_prev"])
+        d = O.sample_disturbances(w["seed"], 0, w["N"], w["H"], inputs.DIST_AMP)
+        c = O.cfg(H=w["H"], N=w["N"])
+        cores = os.cpu_count() or 1
+        reps, t_all = 0, 0.0
+        while t_all < min(args.cpu_seconds, 5.0):
+            t0 = time.perf_counter()
+            k_o, f_o = O.bisect_joint(p, c, x_o, w["v_prev"], w["r"], w["n_bisect"], d, nthreads=1)
+            t_all += time.perf_counter() - t0
+            reps += 1
+        t1 = time.perf_counter()
+        O.bisect_joint(p, c, x_o, w["v_prev"], w["r"], w["n_bisect"], d, nthreads=cores)
+        t_thr = time.perf_counter() - t1
+        cpu = {"value": reps / t_all, "unit": "RG updates/s", "cores": 1, "kind": "oracle",
+               "sample": "the same update, FP64 joint bisection, %d repetitions on 1 core" % reps,
+               "ms_per_update_1core": 1e3 * t_all / reps, "ms_per_update_%dcores" % cores: 1e3 * t_thr,
+               "kappa": k_o, "kappa_equal_to_gpu": bool(k_o == legs["fp64_bisect"]["kappa"] ==
+                                                        legs["fp32_recheck_spec"]["kappa"])}
+    main = legs["fp64_bisect"]
+    out = {"metric": SINGLE_METRIC, "value": 1e3 / main["ms_per_update"], "unit": "RG updates/s", "n_gpus": 1,
+           "steps": K, "warmup": W, "ms_per_step": main["ms_per_update"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "single robust RG update on FC3: x_t at the 100 A equilibrium, r_t = 250 A, "
+                                  "32 scenarios (seed 0), horizon 500 RK4 steps (dt=0.01 s), N_kappa = 12",
+                      "timing": "median device time of sample + search (CUDA events), host time beside it",
+                      "l2": "256 MB written between timed steps"},
+           "legs": legs, "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------- adjoint (cfg 4) --
+ADJ_METRIC = "adjoint gradient latency (4,096 scenarios x 1,000 steps) and Newton kappa search vs 20-step bisection"
+
+
+def run_adjoint(args):
+    import numpy as np
+    import torch
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import inputs
+    from paper_2510_08288_gb300 import rrg as R
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    w = inputs.WORKLOADS["adjoint"]
+    p = inputs.fc3_params()
+    W, K = args.warmup, args.steps
+    N, H, C = w["N"], w["H"], w["checkpoint"]
+    v_prev, r = 100.0, 250.0
+    stream = torch.cuda.Stream()
+    out_legs = {}
+    cfg = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=16, precision=R.FP32_RECHECK,
+                               recheck_eps_rel=RECHECK_EPS_REL)
+    with R.Governor(p, cfg, stream) as g:
+        x_t, _ = g.equilibrium(v_prev)
+        g.sample_scenarios(3, 0)
+        for name, prec in (("gradient_fp64", R.FP64), ("gradient_fp32", R.FP32)):
+            ts = []
+            for i in range(W + K):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gv, grad, ks, js = g.slack_gradient(x_t, v_prev, r, 0.1, C, prec)
+                if i >= W:
+                    ts.append(1e3 * (time.perf_counter() - t0))
+            out_legs[name] = {"ms": statistics.median(ts), "g": gv, "argmin": [ks, js],
+                              "dg_dkappa": float(grad[0])}
+        tol = 2.0 ** -19
+        for name, prec in (("newton_fp32_recheck_eval", R.FP32),):
+            ts, res = [], None
+            for i in range(W + K):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = g.newton_search(x_t, r, v_prev, tol=tol, max_iter=40, checkpoint=C, precision=prec)
+                if i >= W:
+                    ts.append(1e3 * (time.perf_counter() - t0))
+            out_legs[name] = {"ms": statistics.median(ts), "kappa": res[0], "flags": res[1], "gradients": res[2]}
+    # the judge: plain bisection with 20 iterations on the same scenarios
+    for name, prec, search, M in (("bisect20_fp64", R.FP64, R.SEARCH_BISECT, 2),
+                                  ("bisect20_fp32_recheck_spec", R.FP32_RECHECK, R.SEARCH_SPEC_BISECT, 64)):
+        cfgb = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=M, n_bisect=20, search=search,
+                                    precision=prec, recheck_eps_rel=RECHECK_EPS_REL)
+        with R.Governor(p, cfgb, stream) as g:
+            g.sample_scenarios(3, 0)
+            ts, kap = [], None
+            for i in range(W + K):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, kap, fl = g.step(x_t, r, v_prev)
+                if i >= W:
+                    ts.append(1e3 * (time.perf_counter() - t0))
+            out_legs[name] = {"ms": statistics.median(ts), "kappa": kap, "flags": fl}
+    kb = out_legs["bisect20_fp64"]["kappa"]
+    out_legs["newton_fp32_recheck_eval"]["within_one_bracket_of_bisect20"] = bool(
+        abs(out_legs["newton_fp32_recheck_eval"]["kappa"] - kb) <= 2 * tol)
+    main = out_legs["gradient_fp32"]
+    out = {"metric": ADJ_METRIC, "value": 1e3 / main["ms"], "unit": "gradients/s", "n_gpus": 1, "steps": K,
+           "warmup": W, "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "discrete adjoint of min slack on FC3: 4,096 scenarios (seed 3) x 1,000 RK4 "
+                                  "steps, checkpoint every 50 steps, x_t at the 100 A equilibrium, r_t = 250 A, "
+                                  "kappa = 0.1; Newton search to 2^-19 vs 20-iteration bisection",
+                      "timing": "median host time per synchronous call"},
+           "legs": out_legs}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ sweep --
 SWEEP_METRIC = "trajectory-steps/s vs scenario count (large sweep, FP32 + FP64 recheck)"
 
@@ -730,6 +892,10 @@ def main():
         return run_sweep(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "single":
+        return run_single(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_gpu(args)
 
 

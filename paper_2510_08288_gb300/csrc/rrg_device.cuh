@@ -126,30 +126,52 @@ struct RhsC {    // constants of the candidate setpoint v (and the scenario's mo
   T y_scale;     // x_O2 k_sm / W_o2
 };
 
+// x^e - 1 for the compressor term, x = 1 + q_sm / p_atm formed by the caller.
+template <typename T>
+__device__ __forceinline__ T pow_m1(T x, T e);
+template <>
+__device__ __forceinline__ double pow_m1<double>(double x, double e) { return pow(x, e) - 1.0; }
+template <>
+__device__ __forceinline__ float pow_m1<float>(float x, float e) { return __powf(x, e) - 1.0f; }
+
+// x_pw = 1 + q_sm / p_atm is passed in: the caller forms it from the
+// previous stage's d_sm directly (x_pw + (h / p_atm) d_sm), one dependent
+// operation shorter than through the stage state.  e3 / w is formed apart
+// from the compressor power term, so the longest dependent chain of an
+// evaluation is 1 + u -> lg2 -> x e -> ex2 -> - 1 -> f -> d_w.
 template <typename T>
 __device__ __forceinline__ void fc3_rhs_fast(const RhsU<T>& U, const RhsC<T>& C, T q_ca, T w,
-                                             T q_sm, T& d_ca, T& d_w, T& d_sm) {
+                                             T q_sm, T x_pw, T& d_ca, T& d_w, T& d_sm) {
   const T s = q_sm - q_ca;
   const T W_cp = U.a_w * w - U.a_p * q_sm;
   d_ca = U.a1 * s - U.a2 * q_ca - C.a3;
   d_sm = U.RT_Vsm * W_cp - U.b3 * s;
-  const T pr = pow_e_m1<T>(U.e, q_sm * U.inv_p_atm);
-  const T f = U.e1 + U.e3 * div_fast<T>(pr, w);
+  const T pr = pow_m1<T>(x_pw, U.e);
+  const T t = div_fast<T>(U.e3, w);
+  const T f = U.e1 + t * pr;
   d_w = (C.e0 - U.e2 * w) - W_cp * f;
 }
 
+// One RK4 step of size dt followed by the disturbance (e_ca, e_w, e_sm) of
+// Eq. 4, in place.  The update is summed as ((q + e) + h/6 (k1 + 2 (k2 +
+// k3))) + h/6 k4, so only one operation follows the last stage.
 template <typename T>
 __device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C, T dt,
-                                              T& q_ca, T& w, T& q_sm) {
+                                              T& q_ca, T& w, T& q_sm, T e_ca, T e_w, T e_sm) {
   const T h2 = T(0.5) * dt, h6 = dt / T(6);
+  const T g2 = h2 * U.inv_p_atm, g1 = dt * U.inv_p_atm;
+  const T x1 = q_sm * U.inv_p_atm + T(1);
   T a1, b1, c1, a2, b2, c2, a3, b3, c3, a4, b4, c4;
-  fc3_rhs_fast<T>(U, C, q_ca, w, q_sm, a1, b1, c1);
-  fc3_rhs_fast<T>(U, C, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, a2, b2, c2);
-  fc3_rhs_fast<T>(U, C, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, a3, b3, c3);
-  fc3_rhs_fast<T>(U, C, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, a4, b4, c4);
-  q_ca += h6 * ((a1 + a4) + T(2) * (a2 + a3));
-  w += h6 * ((b1 + b4) + T(2) * (b2 + b3));
-  q_sm += h6 * ((c1 + c4) + T(2) * (c2 + c3));
+  fc3_rhs_fast<T>(U, C, q_ca, w, q_sm, x1, a1, b1, c1);
+  fc3_rhs_fast<T>(U, C, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, x1 + g2 * c1, a2, b2, c2);
+  fc3_rhs_fast<T>(U, C, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, x1 + g2 * c2, a3, b3, c3);
+  const T p_ca = (q_ca + e_ca) + h6 * (a1 + T(2) * (a2 + a3));
+  const T p_w = (w + e_w) + h6 * (b1 + T(2) * (b2 + b3));
+  const T p_sm = (q_sm + e_sm) + h6 * (c1 + T(2) * (c2 + c3));
+  fc3_rhs_fast<T>(U, C, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, x1 + g1 * c3, a4, b4, c4);
+  q_ca = p_ca + h6 * a4;
+  w = p_w + h6 * b4;
+  q_sm = p_sm + h6 * c4;
 }
 
 // ---------------------------------------------------------------------------

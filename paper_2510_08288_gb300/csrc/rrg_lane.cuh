@@ -200,10 +200,7 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
           r2[u] = __ldg(pf + 2 * HN);
         }
         pf += N;
-        rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm);
-        q_ca += e0;
-        w += e1;
-        q_sm += e2;
+        rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm, e0, e1, e2);
         ++j;
         const T s = C.y_scale * (q_sm - q_ca) - y_min;
         bmin = fmin(bmin, s);
@@ -225,10 +222,7 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
     while (!stop && j < j_end) {
       const T e0 = __ldg(dp), e1 = __ldg(dp + HN), e2 = __ldg(dp + 2 * HN);
       dp += N;
-      rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm);
-      q_ca += e0;
-      w += e1;
-      q_sm += e2;
+      rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm, e0, e1, e2);
       ++j;
       const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
       smin = fmin(smin, s);
@@ -295,10 +289,8 @@ __device__ __forceinline__ double run_lane_philox(const RhsU<double>& K, const R
     while (j < H) {
       const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
                                     0ull, src.seed, 0ull);
-      rk4_step_fast<double>(K, C, dt, q_ca, w, q_sm);
-      q_ca += uniform_sym(r.w[0], src.amp[0]);
-      w += uniform_sym(r.w[1], src.amp[1]);
-      q_sm += uniform_sym(r.w[2], src.amp[2]);
+      rk4_step_fast<double>(K, C, dt, q_ca, w, q_sm, uniform_sym(r.w[0], src.amp[0]),
+                            uniform_sym(r.w[1], src.amp[1]), uniform_sym(r.w[2], src.amp[2]));
       ++j;
       const double s = checked_slack<double>(C, q_ca, w, q_sm, y_min);
       smin = fmin(smin, s);
