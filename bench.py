@@ -58,12 +58,15 @@ L2_FLUSH_BYTES = 256 << 20
 SWEEP_N = (1024, 2048, 4096, 8192, 16384, 32768, 65536)
 SWEEP_H, SWEEP_M, SWEEP_ROUNDS = 5000, 16, 3
 SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
-# DRAM bytes per rollout launch on this workload (ncu, profiles/
-# rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the kernel
-# sources are the ones profiled
-TRAFFIC_PER_LAUNCH = 25.73e6 / 4
-TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "b79ddbecf5448196b9243cfbb88ab40ccdc7bc13",
-                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "d45d11c95e959aca39fe4cb352a5a835de5a70cf"}
+# DRAM bytes per rollout launch on this workload (ncu, one update's four
+# launches: probe, continuation + round 2, two no-op repair rounds; see
+# profiles/rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the
+# kernel sources are the ones profiled
+TRAFFIC_PER_LAUNCH = (1617664 + 24646144 + 42496 + 42752) / 4
+TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "4fc619da47237c45cdab79654cb851d6da93f86f",
+                   "paper_2510_08288_gb300/csrc/rrg_lane.cuh": "77b956b64a67abeb3b3de7c38fd5f61f4c2220b6",
+                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "bfaf5a435b60a0eb8f6de7c7d9617ed57800b46c",
+                   "paper_2510_08288_gb300/csrc/rrg_internal.h": "bbc7629f085d6f826bf56f6bd175be49719d285e"}
 
 
 def measured_traffic():

@@ -244,7 +244,7 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
     if (cand_stop && smin < thr) *dead = 1;
   }
   bool lane_ok = true, uncertain = false;
-  double contrib = static_cast<double>(inf_v<float>());
+  float contrib = inf_v<float>();
   if (active) {
     if (smin >= eps) {
       contrib = smin;
@@ -263,11 +263,11 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
     }
   }
   const bool all_ok = __all_sync(0xffffffffu, lane_ok);
-  const double wmin = warp_min(contrib);
+  const float wmin = warp_min<float>(contrib);
   const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
   if ((threadIdx.x & 31) == 0) {
     if (!all_ok) B.cand_ok[slot] = 0;
-    if (wmin < static_cast<double>(inf_v<float>())) atomicMin(B.cand_min + slot, dkey(wmin));
+    if (wmin < inf_v<float>()) atomicMin(B.cand_min + slot, dkey(static_cast<double>(wmin)));
     if (wsteps) atomicAdd(&B.stats->lane_steps, static_cast<unsigned long long>(wsteps));
   }
 }

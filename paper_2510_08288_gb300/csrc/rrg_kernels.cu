@@ -289,7 +289,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
     }
   }
   bool lane_ok = true, uncertain = false;
-  double contrib = static_cast<double>(inf_v<T>());
+  T contrib = inf_v<T>();
   if (final_lane) {
     if (classify) {
       if (smin >= eps) {
@@ -313,11 +313,11 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
   if (L.P != nullptr && final_lane) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
 
   const bool all_ok = __all_sync(0xffffffffu, lane_ok);
-  const double wmin = warp_min(contrib);
+  const T wmin = warp_min<T>(contrib);
   const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
   if ((threadIdx.x & 31) == 0) {
     if (!all_ok) L.cand_ok[i] = 0;
-    if (wmin < static_cast<double>(inf_v<T>())) atomicMin(L.cand_min + i, dkey(wmin));
+    if (wmin < inf_v<T>()) atomicMin(L.cand_min + i, dkey(static_cast<double>(wmin)));
     if (wsteps) {
       atomicAdd(&L.stats->lane_steps, static_cast<unsigned long long>(wsteps));
       if (sizeof(T) == 8) atomicAdd(&L.stats->lane_steps_fp64, static_cast<unsigned long long>(wsteps));
