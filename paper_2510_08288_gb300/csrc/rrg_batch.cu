@@ -480,6 +480,7 @@ struct rrg_batch_ctx {
   size_t lanes = 0;            // sum of M N_s
   // device memory
   double* params_dev = nullptr;
+  PowSeries* pws = nullptr;
   BInst* inst_dev = nullptr;
   int32_t* order_dev = nullptr;
   BState* st = nullptr;
@@ -548,7 +549,7 @@ struct BDeviceGuard {
 };
 
 void bfree_all(rrg_batch_ctx* h) {
-  void* ptrs[] = {h->params_dev, h->inst_dev, h->order_dev, h->st, h->d32, h->cand_kappa,
+  void* ptrs[] = {h->params_dev, h->pws, h->inst_dev, h->order_dev, h->st, h->d32, h->cand_kappa,
                   h->cand_v, h->cand_c64, h->cand_c32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->tile_base, h->queue, h->recheck_list, h->recheck_jlast,
                   h->recheck_count,
@@ -706,6 +707,7 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
     }
   };
   alloc(&h->params_dev, RRG_NPARAM);
+  alloc(&h->pws, 1);
   alloc(&h->inst_dev, S);
   alloc(&h->order_dev, S);
   alloc(&h->st, S);
@@ -737,6 +739,9 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   });
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
+  PowSeries ps;
+  make_pow_series((h->params[P_GAMMA] - 1.0) / h->params[P_GAMMA], &ps);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pws, &ps, sizeof ps, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->inst_dev, inst.data(), S * sizeof(BInst), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
@@ -776,6 +781,7 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   for (int i = 0; i < 3; ++i) B.c.amp[i] = cfg->dist_amp[i];
   B.params = h->params_dev;
   fold_constants(h->params, &B.k64, &B.k32);
+  B.k64.pws = h->pws;
   fold_rhs(B.k64, &B.u64, &B.u32);
   B.inst = h->inst_dev;
   B.order = h->order_dev;

@@ -32,6 +32,7 @@ struct rrg_ctx {
   float* d32 = nullptr;
   double* d64b = nullptr;       // second scenario pair, allocated by the first closed loop
   float* d32b = nullptr;
+  PowSeries* pws = nullptr;     // binary64 x^e - 1 series of the model's exponent
   double* pmul = nullptr;       // parameter multipliers of each pair (parametric uncertainty)
   double* pmulb = nullptr;
   cudaStream_t side = nullptr;  // samples update t+1 while update t runs
@@ -171,7 +172,7 @@ void free_all(rrg_ctx* h) {
                   h->cand_min, h->recheck_list, h->recheck_jlast, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state,
                   h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
-                  h->pmul, h->pmulb};
+                  h->pmul, h->pmulb, h->pws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->io_h) cudaFreeHost(h->io_h);
@@ -201,6 +202,7 @@ void fill_launch(rrg_ctx* h) {
   L.scfg = h->scfg;
   L.params = h->params_dev;
   fold_constants(h->params, &L.k64, &L.k32);
+  L.k64.pws = h->pws;
   fold_rhs(L.k64, &L.u64, &L.u32);
   L.d64 = h->d64;
   L.d32 = h->d32;
@@ -392,6 +394,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
     if (e != cudaSuccess) { cudaGetLastError(); }                       \
   }
   ALLOC(params_dev, RRG_NPARAM);
+  ALLOC(pws, 1);
   ALLOC(d64, HN3);
   ALLOC(d32, HN3);
   ALLOC(st, 1);
@@ -427,6 +430,9 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, HN3 * sizeof(float), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
+  PowSeries ps;
+  make_pow_series((h->params[P_GAMMA] - 1.0) / h->params[P_GAMMA], &ps);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->pws, &ps, sizeof ps, cudaMemcpyHostToDevice, h->stream);
   fill_launch(h);
   // the zero scenarios are explicit values (marks pair 0's binary64 array valid)
   if (e == cudaSuccess) e = launch_round_scenarios(h->L);

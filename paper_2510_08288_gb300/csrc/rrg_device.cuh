@@ -10,6 +10,42 @@
 namespace rrg {
 
 // ---------------------------------------------------------------------------
+// Binomial series of x^e - 1 about c = 3/2, for binary64 (GB300's binary64
+// pow has a dependent latency of about 5,800 cycles, this about 500): with
+// t = x / c - 1, |t| <= 1/3 for x in [1, 2], and
+//   x^e - 1 = (c^e - 1) + c^e sum_{n >= 1} binom(e, n) t^n,
+// truncated after t^32 (the rest is below 3^-33 c^e / 33 < 1e-17), evaluated by
+// Estrin's scheme.  Built on the host for one exponent (make_pow_series);
+// another exponent or an x outside [1, 2] takes pow.
+struct PowSeries {
+  double e;      // the exponent the coefficients are for
+  double inv_c;  // 1 / c
+  double a[33];  // a[0] = c^e - 1, a[n] = c^e binom(e, n)
+};
+
+__device__ __forceinline__ double pow_m1_series(const PowSeries* __restrict__ S, double x,
+                                                double e) {
+  if (S != nullptr && S->e == e) {
+    const double t = fma(x, S->inv_c, -1.0);
+    if (fabs(t) <= 1.0 / 3.0) {
+      const double* a = S->a;
+      const double t2 = t * t, t4 = t2 * t2, t8 = t4 * t4, t16 = t8 * t8, t32 = t16 * t16;
+      double p[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) p[i] = fma(a[2 * i + 1], t, a[2 * i]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) p[i] = fma(p[2 * i + 1], t2, p[2 * i]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) p[i] = fma(p[2 * i + 1], t4, p[2 * i]);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) p[i] = fma(p[2 * i + 1], t8, p[2 * i]);
+      return fma(a[32], t32, fma(p[1], t16, p[0]));
+    }
+  }
+  return pow(x, e) - 1.0;
+}
+
+// ---------------------------------------------------------------------------
 // FC3 constants.  The state is kept in gauge coordinates
 //   q = [p_ca - p_atm, w_cp, p_sm - p_atm]
 // so that the pressure differences that set every flow (and the output) are
@@ -29,6 +65,7 @@ struct Fc3K {
   T RT_Vca;      // R_a T_st / V_ca
   T RT_Vsm;      // R_a T_st / V_sm
   T inv_J;       // 1 / J_cp
+  const PowSeries* pws;  // binary64 x^e - 1 (device memory; nullptr: pow)
 };
 
 // Per-candidate constants (functions of the governed setpoint v = I only).
@@ -45,15 +82,15 @@ struct CandK {
 // warp running one trajectory is issue-bound, and the polynomial costs more
 // instructions than the two MUFU operations it would replace.)
 template <typename T>
-__device__ __forceinline__ T pow_e_m1(T e, T u);
+__device__ __forceinline__ T pow_e_m1(T e, T u, const PowSeries* S);
 
 template <>
-__device__ __forceinline__ double pow_e_m1<double>(double e, double u) {
-  return pow(1.0 + u, e) - 1.0;
+__device__ __forceinline__ double pow_e_m1<double>(double e, double u, const PowSeries* S) {
+  return pow_m1_series(S, 1.0 + u, e);
 }
 
 template <>
-__device__ __forceinline__ float pow_e_m1<float>(float e, float u) {
+__device__ __forceinline__ float pow_e_m1<float>(float e, float u, const PowSeries*) {
   return __powf(1.0f + u, e) - 1.0f;
 }
 
@@ -71,7 +108,7 @@ __device__ __forceinline__ void fc3_rhs(const Fc3K<T>& K, const CandK<T>& C,
   const T W_cp = K.a_w * w - K.a_p * q_sm;
   const T W_sm = K.k_sm * (q_sm - q_ca);
   const T W_ca = K.k_ca * q_ca;
-  const T pr_e = pow_e_m1<T>(K.e, q_sm * K.inv_p_atm);
+  const T pr_e = pow_e_m1<T>(K.e, q_sm * K.inv_p_atm, K.pws);
   const T tau_cp = div_fast<T>(K.C_cp * pr_e * W_cp, w);
   const T tau_cm = K.C_m * ((C.V0 - K.K_p * W_cp) - K.k_v * w);
   d_ca = K.RT_Vca * (W_sm - W_ca - C.W_o2);
@@ -117,6 +154,7 @@ struct RhsU {    // constants of the model (per scenario under parametric uncert
   T RT_Vsm, b3;  // RT_Vsm, RT_Vsm k_sm
   T inv_p_atm, e;
   T e1, e2, e3;  // C_m K_p / J, C_m k_v / J, C_cp / J
+  const PowSeries* pws;  // binary64 x^e - 1 (device memory; nullptr: pow)
 };
 
 template <typename T>
@@ -128,11 +166,15 @@ struct RhsC {    // constants of the candidate setpoint v (and the scenario's mo
 
 // x^e - 1 for the compressor term, x = 1 + q_sm / p_atm formed by the caller.
 template <typename T>
-__device__ __forceinline__ T pow_m1(T x, T e);
+__device__ __forceinline__ T pow_m1(T x, T e, const PowSeries* S);
 template <>
-__device__ __forceinline__ double pow_m1<double>(double x, double e) { return pow(x, e) - 1.0; }
+__device__ __forceinline__ double pow_m1<double>(double x, double e, const PowSeries* S) {
+  return pow_m1_series(S, x, e);
+}
 template <>
-__device__ __forceinline__ float pow_m1<float>(float x, float e) { return __powf(x, e) - 1.0f; }
+__device__ __forceinline__ float pow_m1<float>(float x, float e, const PowSeries*) {
+  return __powf(x, e) - 1.0f;
+}
 
 // x_pw = 1 + q_sm / p_atm is passed in: the caller forms it from the
 // previous stage's d_sm directly (x_pw + (h / p_atm) d_sm), one dependent
@@ -146,7 +188,7 @@ __device__ __forceinline__ void fc3_rhs_fast(const RhsU<T>& U, const RhsC<T>& C,
   const T W_cp = U.a_w * w - U.a_p * q_sm;
   d_ca = U.a1 * s - U.a2 * q_ca - C.a3;
   d_sm = U.RT_Vsm * W_cp - U.b3 * s;
-  const T pr = pow_m1<T>(x_pw, U.e);
+  const T pr = pow_m1<T>(x_pw, U.e, U.pws);
   const T t = div_fast<T>(U.e3, w);
   const T f = U.e1 + t * pr;
   d_w = (C.e0 - U.e2 * w) - W_cp * f;

@@ -2,6 +2,7 @@
 // host side of the C ABI (rrg_capi.cu).  Not part of the public interface.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -178,6 +179,7 @@ __host__ __device__ inline void fold_constants(const double* P, Fc3K<double>* k6
   K.RT_Vca = P[P_R_A] * P[P_T_ST] / P[P_V_CA];
   K.RT_Vsm = P[P_R_A] * P[P_T_ST] / P[P_V_SM];
   K.inv_J = 1.0 / P[P_J_CP];
+  K.pws = nullptr;
   *k64 = K;
   Fc3K<float> F{};
   F.inv_p_atm = static_cast<float>(K.inv_p_atm);
@@ -193,6 +195,7 @@ __host__ __device__ inline void fold_constants(const double* P, Fc3K<double>* k6
   F.RT_Vca = static_cast<float>(K.RT_Vca);
   F.RT_Vsm = static_cast<float>(K.RT_Vsm);
   F.inv_J = static_cast<float>(K.inv_J);
+  F.pws = nullptr;
   *k32 = F;
 }
 
@@ -232,6 +235,7 @@ __host__ __device__ inline void fold_rhs(const Fc3K<double>& K, RhsU<double>* u6
   U.e1 = K.C_m * K.K_p * K.inv_J;
   U.e2 = K.C_m * K.k_v * K.inv_J;
   U.e3 = K.C_cp * K.inv_J;
+  U.pws = K.pws;
   *u64 = U;
   RhsU<float> F;
   F.a1 = static_cast<float>(U.a1);
@@ -245,6 +249,7 @@ __host__ __device__ inline void fold_rhs(const Fc3K<double>& K, RhsU<double>* u6
   F.e1 = static_cast<float>(U.e1);
   F.e2 = static_cast<float>(U.e2);
   F.e3 = static_cast<float>(U.e3);
+  F.pws = nullptr;
   *u32 = F;
 }
 
@@ -258,6 +263,20 @@ __host__ __device__ inline void fold_rhs_cand(const Fc3K<double>& K, const CandK
   c32->a3 = static_cast<float>(R.a3);
   c32->e0 = static_cast<float>(R.e0);
   c32->y_scale = static_cast<float>(R.y_scale);
+}
+
+// Coefficients of the binary64 x^e - 1 series (host).
+inline void make_pow_series(double e, PowSeries* S) {
+  const double c = 1.5, lc = std::log(c);
+  const double ce = std::exp(e * lc);
+  S->e = e;
+  S->inv_c = 1.0 / c;
+  S->a[0] = std::expm1(e * lc);
+  double b = 1.0;  // binom(e, n)
+  for (int n = 1; n <= 32; ++n) {
+    b = b * (e - static_cast<double>(n - 1)) / static_cast<double>(n);
+    S->a[n] = ce * b;
+  }
 }
 
 // ---- kernel launchers (rrg_kernels.cu) --------------------------------

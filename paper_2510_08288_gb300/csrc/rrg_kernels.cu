@@ -250,7 +250,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
     if constexpr (PU)
       p_atm = scenario_model<T>(L.params,
                                 (L.st->buf ? L.pmulb : L.pmul) + static_cast<size_t>(k) * RRG_NPARAM,
-                                L.cand_v[i], K, C);
+                                L.cand_v[i], L.k64.pws, K, C);
     T q_ca = static_cast<T>(L.st->x[0] - p_atm), w = static_cast<T>(L.st->x[1]),
       q_sm = static_cast<T>(L.st->x[2] - p_atm);
     T smin0 = inf_v<T>();
@@ -396,7 +396,7 @@ recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
     const double* pm = buf ? L.pmulb : L.pmul;
     if (pm != nullptr)
       p_atm_k = scenario_model<double>(L.params, pm + static_cast<size_t>(k) * RRG_NPARAM,
-                                       L.cand_v[i], K, C);
+                                       L.cand_v[i], L.k64.pws, K, C);
     if (src.d64_valid) {
       int end = 0;
       double q_ca = L.st->x[0] - p_atm_k, w = L.st->x[1], q_sm = L.st->x[2] - p_atm_k;

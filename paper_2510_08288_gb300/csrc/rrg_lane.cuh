@@ -248,13 +248,14 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
 template <typename T>
 __device__ __forceinline__ double scenario_model(const double* __restrict__ P,
                                                  const double* __restrict__ m_k, double v,
-                                                 RhsU<T>& U, RhsC<T>& C) {
+                                                 const PowSeries* pws, RhsU<T>& U, RhsC<T>& C) {
   double Pk[RRG_NPARAM];
 #pragma unroll
   for (int p = 0; p < RRG_NPARAM; ++p) Pk[p] = __dmul_rn(P[p], m_k[p]);
   Fc3K<double> k64;
   Fc3K<float> k32;
   fold_constants(Pk, &k64, &k32);
+  k64.pws = pws;  // used only if the scenario's exponent is the table's
   const CandK<double> c64 = cand_consts(Pk, v);
   RhsU<double> u64;
   RhsU<float> u32;

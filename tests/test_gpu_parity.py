@@ -425,3 +425,25 @@ def test_recheck_runs_only_to_the_last_uncertain_step(R, orc, params):
     np.testing.assert_array_equal(P, P_o)
     assert list(adm) == [1, 0]
     assert st["rechecked"] == N and st["lane_steps_fp64"] == 0
+
+
+@pytest.mark.parametrize("p_sm_rel", [0.97, 1.02, 1.9, 2.05])
+def test_fp64_rollouts_across_the_power_series_domain(R, orc, params, p_sm_rel):
+    """Binary64 rollouts from supply-manifold pressures inside and outside
+    [1, 2] p_atm (the range of the binary64 x^e series; outside it pow is
+    used) match the oracle's slacks to 1e-9 with identical decisions."""
+    N, H = 40, 120
+    names = inputs.FC3_PARAM_NAMES
+    p_atm = params[names.index("p_atm")]
+    x_eq = orc.equilibrium(params, 120.0)
+    x_t = np.array([x_eq[0], x_eq[1], p_sm_rel * p_atm])
+    if x_t[2] <= x_t[0]:
+        x_t[0] = 0.99 * x_t[2]
+    kappas = np.array([0.0, 0.05, 0.2, 1.0])
+    (adm, ms, P, _), (a_o, ms_o, P_o) = _eval_both(R, orc, params, N, H, kappas, R.FP64, 0, v_prev=120.0,
+                                                   r=200.0, x_t=x_t, ss_check=0)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+    fin = np.isfinite(ms_o)
+    np.testing.assert_array_equal(np.isfinite(ms), fin)
+    np.testing.assert_allclose(ms[fin], ms_o[fin], rtol=1e-9, atol=1e-12)
