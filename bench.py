@@ -103,13 +103,14 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS):
+def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND):
     return {
         "workload": "closed-loop robust RG on FC3: N_sim=%d scenarios, horizon %d RK4 steps "
                     "(dt=0.01 s), staircase r (8 levels over 50..300 A, seed 1, 125 updates/level), "
                     "timed updates [%d, %d) of the 1000-update run" % (N, H, W, W + K),
-        "search": "speculative bisection (Alg. 1 result), N_kappa=12, 64 candidates/round, "
-                  "first two rounds pipelined after a %d-step probe" % probe,
+        "search": "speculative bisection (Alg. 1 result), N_kappa=12, %d candidates/round, "
+                  "first two rounds pipelined after a %d-step probe (0: not pipelined); shape chosen by "
+                  "rrg_autotune on update 0" % (m, probe),
         "kappa_tol": 2.0 ** -11,
         "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
         "l2": "256 MB written between timed steps",
@@ -222,13 +223,14 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- GPU side --
-def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev):
+def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning):
     """The timed updates again through the host-buffer entry points
     (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle; every
     call copies its inputs from and its results to host memory."""
     import numpy as np
     import torch
     g2 = R.Governor(p, cfg, stream)
+    g2.set_tuning(*tuning)
     x, v = x0.copy(), V0
     for t in range(W):
         g2.sample_scenarios(seed, t)
@@ -285,6 +287,10 @@ def run_gpu(args):
                                recheck_eps_rel=RECHECK_EPS_REL, probe_steps=args.probe_steps)
     g = R.Governor(p, cfg, stream)
     x0, _ = g.equilibrium(V0)
+    # the speculative bisection's shape (tree width, probe length) by the
+    # library's autotuner on the first update; every shape gives Alg. 1's kappa
+    g.sample_scenarios(seed, 0)
+    tune_m, tune_probe, tune_ms = g.autotune(x0, r_seq[0], V0, repeats=2)
     dev = torch.device("cuda", local)
     d_r = torch.tensor(r_seq, dtype=torch.float64, device=dev)
     d_v = torch.zeros(T, dtype=torch.float64, device=dev)
@@ -323,6 +329,7 @@ def run_gpu(args):
     # the same K updates again through the cached one-update CUDA graph (the
     # library's closed-loop replay mode), on a fresh handle from the same start
     gg = R.Governor(p, cfg, stream)
+    gg.set_tuning(tune_m, tune_probe)
     gd_v, gd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
     gd_f, gd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
     R.rrg_closed_loop_dev(gg.h, x0, V0, d_r, W, seed, 0, amp, True, gd_v, gd_k, gd_f, gd_x)
@@ -356,7 +363,7 @@ def run_gpu(args):
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
         e2e = None
         if not args.no_e2e:
-            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev)
+            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, (tune_m, tune_probe))
 
         # plain FP64 bisection on the same GPU, same updates
         nf = min(args.fp64_steps, K)
@@ -398,7 +405,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(W, K, NS, HZ, args.probe_steps),
+            "config": workload_config(W, K, NS, HZ, tune_probe, tune_m),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -288,6 +288,24 @@ int rrg_closed_loop_dev(rrg_handle h, const double *x0, double v0, const double 
 int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, uint64_t t,
                    const double *plant_amp, double *x_next);
 
+/* Shape of RRG_SEARCH_SPEC_BISECT: m tree nodes per round (1 .. max_candidates)
+ * and the probe length that pipelines its first two rounds (0, or any value
+ * when the handle was created with probe_steps > 0).  The result is Alg. 1's
+ * for every shape; only the time per update changes.  rrg_set_tuning waits
+ * for the handle's stream; RRG_EINVAL for other searches or values. */
+int rrg_set_tuning(rrg_handle h, int m, int probe_steps);
+int rrg_get_tuning(rrg_handle h, int32_t *m, int32_t *probe_steps);
+
+/* Autotuner of RRG_SEARCH_SPEC_BISECT: on the current scenarios and the host
+ * inputs x_t[3], r_t, v_prev, times 1 + repeats updates (CUDA events on the
+ * handle's stream) for each tree width m in {4, 8, ..., max_candidates} and
+ * probe length in {0, 32, 128, 512} (below the horizon; 0 only unless the
+ * handle has probe storage), keeps the fastest and returns it in *m_out,
+ * *probe_out and its mean device time per update in *ms_out (each may be
+ * NULL).  Synchronous; the cached closed-loop graph is discarded. */
+int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_prev, int repeats,
+                 int32_t *m_out, int32_t *probe_out, double *ms_out);
+
 /* Gradient of the robust objective g(kappa) = min over scenarios k and steps
  * j = 0..H of s_j^k = h(x_j^k, v) - y_min on the current scenarios, with
  * v = v_prev + kappa (r_t - v_prev) (Eq. 2) and x_{j+1} = RK4(x_j, v) + d_j^k

@@ -221,7 +221,7 @@ void fill_launch(rrg_ctx* h) {
   L.stats = h->stats;
   L.P = nullptr;
   L.recheck_blocks = 2 * 152;
-  L.probe_steps = c.probe_steps;
+  L.probe_steps = h->scfg.probe_steps;
   L.lane_state = h->lane_state;
   L.pmul = h->pmul;
   L.pmulb = h->pmulb;
@@ -914,6 +914,99 @@ int rrg_newton_search(rrg_handle h, const double* x_t, double r_t, double v_prev
   if (kappa) *kappa = any ? lo : 0.0;
   if (flags) *flags = fl;
   if (iterations) *iterations = it;
+  return RRG_OK;
+}
+
+// Speculative-bisection shape: tree width and probe length.  Neither changes
+// the result (always Alg. 1's); both change the time per update.
+int set_tuning(rrg_ctx* h, int m, int probe) {
+  h->scfg.m_cap = m;
+  h->scfg.probe_steps = probe;
+  fill_launch(h);
+  if (h->cl_exec) {  // the cached closed-loop graph holds the old schedule
+    cudaGraphExecDestroy(h->cl_exec);
+    h->cl_exec = nullptr;
+  }
+  return RRG_OK;
+}
+
+int rrg_set_tuning(rrg_handle h, int m, int probe_steps) {
+  if (!h) return RRG_EINVAL;
+  if (h->cfg.search != RRG_SEARCH_SPEC_BISECT)
+    return set_err(h, RRG_EINVAL, "tuning applies to RRG_SEARCH_SPEC_BISECT");
+  if (m < 1 || m > h->cfg.max_candidates)
+    return set_err(h, RRG_EINVAL, "m must be in [1, max_candidates]");
+  if (probe_steps < 0 || (probe_steps > 0 && !h->lane_state))
+    return set_err(h, RRG_EINVAL, "probe_steps must be >= 0, and 0 unless the handle was created with probe_steps > 0");
+  DeviceGuard g(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  return set_tuning(h, m, probe_steps);
+}
+
+int rrg_get_tuning(rrg_handle h, int32_t* m, int32_t* probe_steps) {
+  if (!h) return RRG_EINVAL;
+  if (m) *m = h->scfg.m_cap;
+  if (probe_steps) *probe_steps = h->scfg.probe_steps;
+  return RRG_OK;
+}
+
+int rrg_autotune(rrg_handle h, const double* x_t, double r_t, double v_prev, int repeats,
+                 int32_t* m_out, int32_t* probe_out, double* ms_out) {
+  if (!h) return RRG_EINVAL;
+  if (h->cfg.search != RRG_SEARCH_SPEC_BISECT)
+    return set_err(h, RRG_EINVAL, "the autotuner tunes RRG_SEARCH_SPEC_BISECT");
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0) || repeats < 1)
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite, v_prev, r_t > 0, repeats >= 1");
+  DeviceGuard g(h->device);
+  const int cap = h->cfg.max_candidates, H = h->cfg.horizon;
+  std::vector<int> ms;
+  for (int m = 4; m < cap; m *= 2) ms.push_back(m);
+  ms.push_back(cap);
+  std::vector<int> probes = {0};
+  if (h->lane_state)
+    for (int p : {32, 128, 512})
+      if (p < H) probes.push_back(p);
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  h->io_h[IO_R] = r_t;
+  h->io_h[IO_V] = v_prev;
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, 5 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  cudaEvent_t a = take_event(h), b = take_event(h);
+  if (!a || !b) return set_err(h, RRG_ECUDA, "event creation failed");
+  const bool prof = h->profiling;
+  h->profiling = false;
+  double best = 0.0;
+  int best_m = h->scfg.m_cap, best_p = h->scfg.probe_steps, rc = RRG_OK;
+  for (int m : ms) {
+    for (int p : probes) {
+      set_tuning(h, m, p);
+      float total = 0.0f;
+      for (int rep = 0; rep <= repeats && rc == RRG_OK; ++rep) {
+        cudaEventRecord(a, h->stream);
+        rc = enqueue_search(h, h->io_dev + IO_X, h->io_dev + IO_R, nullptr, h->io_dev + IO_V,
+                            h->io_dev + IO_OUT, h->io_dev + IO_OUT + 1, h->flag_dev);
+        cudaEventRecord(b, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = RRG_ECUDA;
+        float t = 0.0f;
+        if (rc == RRG_OK && rep > 0 && cudaEventElapsedTime(&t, a, b) == cudaSuccess) total += t;
+      }
+      if (rc != RRG_OK) break;
+      const double mean = total / repeats;
+      if ((m == ms.front() && p == probes.front()) || mean < best) {
+        best = mean;
+        best_m = m;
+        best_p = p;
+      }
+    }
+    if (rc != RRG_OK) break;
+  }
+  h->ev_free.push_back(a);
+  h->ev_free.push_back(b);
+  h->profiling = prof;
+  set_tuning(h, best_m, best_p);
+  if (rc != RRG_OK) return set_err(h, RRG_ECUDA, "autotune: a timed update failed");
+  if (m_out) *m_out = best_m;
+  if (probe_out) *probe_out = best_p;
+  if (ms_out) *ms_out = best;
   return RRG_OK;
 }
 

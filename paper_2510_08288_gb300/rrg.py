@@ -83,6 +83,9 @@ def _load():
                                                ctypes.c_int, _p, _p, _p, _p]),
         "rrg_plant_step": (ctypes.c_int, [_p, _p, _d, _u64, _u64, _p, _p]),
         "rrg_set_profiling": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_set_tuning": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int]),
+        "rrg_get_tuning": (ctypes.c_int, [_p, _p, _p]),
+        "rrg_autotune": (ctypes.c_int, [_p, _p, _d, _d, ctypes.c_int, _p, _p, _p]),
         "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
         "rrg_reset_stats": (ctypes.c_int, [_p]),
         "rrg_slack_gradient": (ctypes.c_int, [_p, _p, _d, _d, _d, ctypes.c_int, ctypes.c_int, _p, _p,
@@ -286,6 +289,26 @@ def rrg_newton_search(h, x_t, r_t, v_prev, tol=2.0 ** -19, max_iter=40, checkpoi
     return k.value, fl.value, it.value
 
 
+def rrg_set_tuning(h, m, probe_steps):
+    _check(lib.rrg_set_tuning(h, int(m), int(probe_steps)), h)
+
+
+def rrg_get_tuning(h):
+    """(tree nodes per round, probe steps) of the speculative bisection."""
+    m, p = _i32(0), _i32(0)
+    _check(lib.rrg_get_tuning(h, ctypes.byref(m), ctypes.byref(p)), h)
+    return m.value, p.value
+
+
+def rrg_autotune(h, x_t, r_t, v_prev, repeats=2):
+    """(m, probe_steps, mean ms per update) chosen by the autotuner."""
+    x = _f64(x_t)
+    m, p, ms = _i32(0), _i32(0), _d(0.0)
+    _check(lib.rrg_autotune(h, _ptr(x), float(r_t), float(v_prev), int(repeats), ctypes.byref(m),
+                            ctypes.byref(p), ctypes.byref(ms)), h)
+    return m.value, p.value, ms.value
+
+
 def rrg_set_profiling(h, on):
     _check(lib.rrg_set_profiling(h, int(bool(on))), h)
 
@@ -383,6 +406,15 @@ class Governor:
 
     def set_profiling(self, on):
         rrg_set_profiling(self.h, on)
+
+    def autotune(self, x_t, r_t, v_prev, repeats=2):
+        return rrg_autotune(self.h, x_t, r_t, v_prev, repeats)
+
+    def set_tuning(self, m, probe_steps):
+        rrg_set_tuning(self.h, m, probe_steps)
+
+    def get_tuning(self):
+        return rrg_get_tuning(self.h)
 
 
 # ---------------------------------------------------------------- batched --

@@ -447,3 +447,33 @@ def test_fp64_rollouts_across_the_power_series_domain(R, orc, params, p_sm_rel):
     fin = np.isfinite(ms_o)
     np.testing.assert_array_equal(np.isfinite(ms), fin)
     np.testing.assert_allclose(ms[fin], ms_o[fin], rtol=1e-9, atol=1e-12)
+
+
+def test_autotune_and_tuning_keep_alg1_result(R, orc, params):
+    """The autotuner and every tree width / probe length give Alg. 1's kappa."""
+    N, H = 256, 400
+    x_t = orc.equilibrium(params, 100.0)
+    cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=R.FP32_RECHECK, max_candidates=64,
+               probe_steps=128, recheck_eps_rel=SLACK32_TOL / 1.9)
+    d = orc.sample_disturbances(3, 1, N, H, inputs.DIST_AMP)
+    k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, 100.0, 250.0, 12, d)
+    with R.Governor(params, cfg) as g:
+        g.sample_scenarios(3, 1)
+        before = g.step(x_t, 250.0, 100.0)
+        m, p, ms = g.autotune(x_t, 250.0, 100.0, repeats=1)
+        assert 4 <= m <= 64 and p in (0, 32, 128) and ms > 0
+        assert g.get_tuning() == (m, p)
+        assert g.step(x_t, 250.0, 100.0) == before
+        for mm, pp in ((1, 0), (3, 0), (7, 32), (64, 1), (64, 399)):
+            g.set_tuning(mm, pp)
+            assert g.step(x_t, 250.0, 100.0) == before, (mm, pp)
+        for bad in ((0, 0), (65, 0), (8, -1)):
+            with pytest.raises(R.RrgError):
+                g.set_tuning(*bad)
+    assert before[1:] == (k_o, f_o)
+    with R.Governor(params, _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, probe_steps=0)) as g:
+        with pytest.raises(R.RrgError):
+            g.set_tuning(8, 32)
+    with R.Governor(params, _cfg(R, N, H, search=R.SEARCH_GRID)) as g:
+        with pytest.raises(R.RrgError):
+            g.autotune(x_t, 250.0, 100.0)
