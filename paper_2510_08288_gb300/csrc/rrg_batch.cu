@@ -47,12 +47,15 @@ struct BInst {
 };
 
 struct BState {
-  double x[3];
+  double x[3];            // x_t of the current update
   double v_prev, r;
+  double lx[3], lv;       // closed-loop state (plant state, last v), kept apart
+                          // from single updates' inputs
   double lo, hi, kappa_opt;
   double v_out;
   int32_t m, round, any, done, invalid, flags;
-  unsigned long long seed, update;
+  int32_t cur, pad;                      // scenario pair of the current update
+  unsigned long long seed_p[2], update_p[2];  // what each pair holds
 };
 
 struct BCfg {
@@ -73,6 +76,7 @@ struct BLaunch {
   const int32_t* order;  // instances, longest horizon (then most scenarios) first
   BState* st;
   float* d32;
+  float* d32b;         // second scenario pair (closed loops), or nullptr
   double* cand_kappa;
   double* cand_v;
   RhsC<double>* cand_c64;
@@ -100,12 +104,13 @@ __global__ void batch_sample_kernel(const BLaunch B, uint64_t seed, uint64_t bas
   const BInst I = B.inst[s];
   const uint64_t upd = base + (B.t_dev ? *B.t_dev : 0ull);
   const uint64_t key = seed + static_cast<uint64_t>(s);
+  const int pair = (B.d32b != nullptr && (upd & 1ull)) ? 1 : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    B.st[s].seed = key;
-    B.st[s].update = upd;
+    B.st[s].seed_p[pair] = key;
+    B.st[s].update_p[pair] = upd;
   }
   const size_t HN = static_cast<size_t>(I.H) * I.N;
-  float* d = B.d32 + I.off;
+  float* d = (pair ? B.d32b : B.d32) + I.off;
   const float s0 = static_cast<float>(B.c.amp[0] * 0x1.0p-23),
               s1 = static_cast<float>(B.c.amp[1] * 0x1.0p-23),
               s2 = static_cast<float>(B.c.amp[2] * 0x1.0p-23);
@@ -148,21 +153,26 @@ __device__ void build_tiles(const BLaunch& B, int tile) {
 }
 
 // Round 1: inputs (device arrays; NULL x / v_prev: the closed loop's state),
-// Alg. 3's grid, the tile list.  r is read at r[t * S + s] (t = the loop
-// counter, 0 without one).
+// the scenario pair of update base + t, Alg. 3's grid, the tile list.  r is
+// read at r[t * S + s] (t = the loop counter, 0 without one).
 __global__ void __launch_bounds__(kDecideThreads)
 batch_begin_kernel(const BLaunch B, const double* __restrict__ d_x, const double* __restrict__ d_r,
-                   const double* __restrict__ d_vp, int tile) {
+                   const double* __restrict__ d_vp, uint64_t base, int tile) {
   const int s = threadIdx.x;
   const unsigned long long t = B.t_dev ? *B.t_dev : 0ull;
   if (s < B.c.S) {
     BState& st = B.st[s];
+    st.cur = (B.d32b != nullptr && ((base + t) & 1ull)) ? 1 : 0;
     if (d_x) {
       st.x[0] = d_x[3 * s];
       st.x[1] = d_x[3 * s + 1];
       st.x[2] = d_x[3 * s + 2];
+    } else {
+      st.x[0] = st.lx[0];
+      st.x[1] = st.lx[1];
+      st.x[2] = st.lx[2];
     }
-    if (d_vp) st.v_prev = d_vp[s];
+    st.v_prev = d_vp ? d_vp[s] : st.lv;
     st.r = d_r[t * static_cast<unsigned long long>(B.c.S) + s];
     const bool ok = isfinite(st.x[0]) && isfinite(st.x[1]) && isfinite(st.x[2]) &&
                     isfinite(st.v_prev) && isfinite(st.r) && st.v_prev > 0.0 && st.r > 0.0;
@@ -237,7 +247,8 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
     float q_ca = static_cast<float>(st.x[0] - p_atm), w = static_cast<float>(st.x[1]),
           q_sm = static_cast<float>(st.x[2] - p_atm);
     int end = LANE_REACHED_END;
-    smin = run_lane<float, PF>(B.u32, B.cand_c32[slot], B.d32 + I.off, k, I.N, I.H, 0, I.H, q_ca,
+    const float* d = (st.cur ? B.d32b : B.d32) + I.off;
+    smin = run_lane<float, PF>(B.u32, B.cand_c32[slot], d, k, I.N, I.H, 0, I.H, q_ca,
                                w, q_sm, inf_v<float>(), static_cast<float>(B.c.dt),
                                static_cast<float>(B.c.y_min), thr, cand_stop ? dead : nullptr,
                                &steps, &end, eps, &jlast);
@@ -322,8 +333,8 @@ __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
     ScenSrc src;
     src.d64_valid = 0;
     src.pad = 0;
-    src.seed = st.seed;
-    src.update = st.update;
+    src.seed = st.seed_p[st.cur];
+    src.update = st.update_p[st.cur];
     src.amp[0] = B.c.amp[0];
     src.amp[1] = B.c.amp[1];
     src.amp[2] = B.c.amp[2];
@@ -418,15 +429,15 @@ batch_plant_kernel(const BLaunch B, uint64_t seed, uint64_t base, const double* 
     const CandK<double> C = cand_consts(B.params, v);
     rk4_step<double>(B.k64, C, B.c.dt, q_ca, w, q_sm);
     const U64x4 r = philox4x64_10(0ull, 0ull, base + t, 1ull, seed + static_cast<uint64_t>(s), 0ull);
-    st.x[0] = (q_ca + p_atm) + uniform_sym(r.w[0], amp[0]);
-    st.x[1] = w + uniform_sym(r.w[1], amp[1]);
-    st.x[2] = (q_sm + p_atm) + uniform_sym(r.w[2], amp[2]);
-    st.v_prev = v;
+    st.lx[0] = (q_ca + p_atm) + uniform_sym(r.w[0], amp[0]);
+    st.lx[1] = w + uniform_sym(r.w[1], amp[1]);
+    st.lx[2] = (q_sm + p_atm) + uniform_sym(r.w[2], amp[2]);
+    st.lv = v;
     if (x_out) {
       double* xo = x_out + ((t + 1) * static_cast<unsigned long long>(B.c.S) + s) * 3;
-      xo[0] = st.x[0];
-      xo[1] = st.x[1];
-      xo[2] = st.x[2];
+      xo[0] = st.lx[0];
+      xo[1] = st.lx[1];
+      xo[2] = st.lx[2];
     }
   }
   __syncthreads();
@@ -439,14 +450,14 @@ __global__ void batch_loop_init_kernel(const BLaunch B, const double* __restrict
   if (s == 0) *B.t_dev = 0ull;
   if (s >= B.c.S) return;
   BState& st = B.st[s];
-  st.x[0] = x0[3 * s];
-  st.x[1] = x0[3 * s + 1];
-  st.x[2] = x0[3 * s + 2];
-  st.v_prev = v0[s];
+  st.lx[0] = x0[3 * s];
+  st.lx[1] = x0[3 * s + 1];
+  st.lx[2] = x0[3 * s + 2];
+  st.lv = v0[s];
   if (x_out) {
-    x_out[3 * s] = st.x[0];
-    x_out[3 * s + 1] = st.x[1];
-    x_out[3 * s + 2] = st.x[2];
+    x_out[3 * s] = st.lx[0];
+    x_out[3 * s + 1] = st.lx[1];
+    x_out[3 * s + 2] = st.lx[2];
   }
 }
 
@@ -485,6 +496,12 @@ struct rrg_batch_ctx {
   int32_t* order_dev = nullptr;
   BState* st = nullptr;
   float* d32 = nullptr;
+  float* d32b = nullptr;       // second scenario pair, allocated by the first closed loop
+  size_t d32_elems = 0;
+  cudaStream_t side = nullptr; // draws update t + 1 while update t searches
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool cl_next_ready = false;
+  uint64_t cl_seed = 0, cl_t0 = 0;
   double* cand_kappa = nullptr;
   double* cand_v = nullptr;
   RhsC<double>* cand_c64 = nullptr;
@@ -549,7 +566,8 @@ struct BDeviceGuard {
 };
 
 void bfree_all(rrg_batch_ctx* h) {
-  void* ptrs[] = {h->params_dev, h->pws, h->inst_dev, h->order_dev, h->st, h->d32, h->cand_kappa,
+  void* ptrs[] = {h->params_dev, h->pws, h->inst_dev, h->order_dev, h->st, h->d32, h->d32b,
+                  h->cand_kappa,
                   h->cand_v, h->cand_c64, h->cand_c32, h->cand_ok, h->cand_dead, h->cand_ss,
                   h->cand_min, h->tile_base, h->queue, h->recheck_list, h->recheck_jlast,
                   h->recheck_count,
@@ -560,6 +578,9 @@ void bfree_all(rrg_batch_ctx* h) {
   for (auto& e : h->ev_free) cudaEventDestroy(e);
   for (auto& pr : h->ev_roll) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (h->cl_exec) cudaGraphExecDestroy(h->cl_exec);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -609,21 +630,28 @@ int enqueue_rollout(rrg_batch_ctx* h) {
 }
 
 // One update of every instance: sample, then the rounds of the search.
-int enqueue_update(rrg_batch_ctx* h, const double* d_x, const double* d_r, const double* d_vp,
-                   uint64_t seed, uint64_t base, double* v_out, double* k_out, int32_t* f_out) {
+int enqueue_sample(rrg_batch_ctx* h, uint64_t seed, uint64_t base, cudaStream_t stream) {
+  int blocks = 1;
+  for (const BInst& I : h->inst) {
+    const size_t hn = static_cast<size_t>(I.H) * I.N;
+    blocks = std::max(blocks, static_cast<int>(std::min<size_t>((hn + 255) / 256, 64)));
+  }
+  batch_sample_kernel<<<dim3(blocks, h->B.c.S), 256, 0, stream>>>(h->B, seed, base);
+  BCK(cudaGetLastError());
+  h->launches++;
+  return RRG_OK;
+}
+
+// The search of one update of every instance on scenarios already drawn for
+// update base + t.
+int enqueue_search_all(rrg_batch_ctx* h, const double* d_x, const double* d_r, const double* d_vp,
+                       uint64_t base, double* v_out, double* k_out, int32_t* f_out) {
   const BLaunch& B = h->B;
   const int S = B.c.S;
   const int tile = kVariants[h->variant].tile;
-  int maxhn_blocks = 1;
-  for (const BInst& I : h->inst) {
-    const size_t hn = static_cast<size_t>(I.H) * I.N;
-    maxhn_blocks = std::max(maxhn_blocks, static_cast<int>(std::min<size_t>((hn + 255) / 256, 64)));
-  }
-  batch_sample_kernel<<<dim3(maxhn_blocks, S), 256, 0, h->stream>>>(B, seed, base);
+  batch_begin_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, d_x, d_r, d_vp, base, tile);
   BCK(cudaGetLastError());
-  batch_begin_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, d_x, d_r, d_vp, tile);
-  BCK(cudaGetLastError());
-  h->launches += 2;
+  h->launches++;
   const int rounds = B.c.search == RRG_SEARCH_GRID ? 1 : B.c.n_rounds;
   const int prep_blocks = (S * B.c.M + 127) / 128;
   for (int r = 0; r < rounds; ++r) {
@@ -640,6 +668,14 @@ int enqueue_update(rrg_batch_ctx* h, const double* d_x, const double* d_r, const
     h->rounds++;
   }
   return RRG_OK;
+}
+
+// Sample, then search (one update of every instance, single stream).
+int enqueue_update(rrg_batch_ctx* h, const double* d_x, const double* d_r, const double* d_vp,
+                   uint64_t seed, uint64_t base, double* v_out, double* k_out, int32_t* f_out) {
+  int rc = enqueue_sample(h, seed, base, h->stream);
+  if (rc != RRG_OK) return rc;
+  return enqueue_search_all(h, d_x, d_r, d_vp, base, v_out, k_out, f_out);
 }
 
 }  // namespace
@@ -712,6 +748,7 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   alloc(&h->order_dev, S);
   alloc(&h->st, S);
   alloc(&h->d32, static_cast<size_t>(elems));
+  h->d32_elems = static_cast<size_t>(elems);
   alloc(&h->cand_kappa, SM);
   alloc(&h->cand_v, SM);
   alloc(&h->cand_c64, SM);
@@ -787,6 +824,7 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   B.order = h->order_dev;
   B.st = h->st;
   B.d32 = h->d32;
+  B.d32b = nullptr;
   B.cand_kappa = h->cand_kappa;
   B.cand_v = h->cand_v;
   B.cand_c64 = h->cand_c64;
@@ -830,6 +868,7 @@ int rrg_batch_step_dev(rrg_batch_handle h, const double* d_x, const double* d_r,
   if (!d_x || !d_r || !d_v_prev) return bset_err(h, RRG_EINVAL, "d_x, d_r and d_v_prev must be non-NULL");
   BDeviceGuard g(h->device);
   h->B.t_dev = nullptr;
+  h->cl_next_ready = false;  // this draw may overwrite a closed loop's next update
   return enqueue_update(h, d_x, d_r, d_v_prev, seed, update_index, d_v_t, d_kappa, d_flags);
 }
 
@@ -844,6 +883,19 @@ int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double* d_x0, const doub
     if (!std::isfinite(plant_amp[i]) || plant_amp[i] < 0.0)
       return bset_err(h, RRG_EINVAL, "plant_amp must be finite and >= 0");
   BDeviceGuard g(h->device);
+  // the second scenario pair and the side stream, on first use
+  if (!h->B.d32b) {
+    if (!h->d32b) BCK(cudaMalloc(reinterpret_cast<void**>(&h->d32b), h->d32_elems * sizeof(float) + 16));
+    if (!h->side) BCK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    if (!h->ev_fork) BCK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    if (!h->ev_join) BCK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    h->B.d32b = h->d32b;
+    h->cl_next_ready = false;
+    if (h->cl_exec) {
+      cudaGraphExecDestroy(h->cl_exec);
+      h->cl_exec = nullptr;
+    }
+  }
   h->B.t_dev = h->t_dev;
   std::memcpy(h->io_h, plant_amp, 3 * sizeof(double));
   BCK(cudaMemcpyAsync(h->amp_dev, h->io_h, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -851,10 +903,29 @@ int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double* d_x0, const doub
     batch_loop_init_kernel<<<(h->B.c.S + 127) / 128, 128, 0, h->stream>>>(h->B, d_x0, d_v0, d_x_out);
     BCK(cudaGetLastError());
     h->launches++;
+    h->cl_next_ready = false;
   }
-  auto one = [&]() -> int {
-    int rc = enqueue_update(h, nullptr, d_r_seq, nullptr, seed, t0, d_v_out, d_kappa_out, d_flags_out);
+  if (T == 0) return RRG_OK;
+  // the first update's scenarios, unless the previous call of this run drew them
+  if (!(h->cl_next_ready && h->cl_seed == seed && h->cl_t0 == t0)) {
+    int rc = enqueue_sample(h, seed, t0, h->stream);
     if (rc != RRG_OK) return rc;
+  }
+  h->cl_seed = seed;
+  h->cl_t0 = t0;
+  h->cl_next_ready = true;
+  // one update: draw update t + 1 on the side stream (into the other pair)
+  // while update t searches; join before the plant advances the counter the
+  // sampler reads
+  auto one = [&]() -> int {
+    BCK(cudaEventRecord(h->ev_fork, h->stream));
+    BCK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    int rc = enqueue_sample(h, seed, t0 + 1, h->side);
+    if (rc != RRG_OK) return rc;
+    BCK(cudaEventRecord(h->ev_join, h->side));
+    rc = enqueue_search_all(h, nullptr, d_r_seq, nullptr, t0, d_v_out, d_kappa_out, d_flags_out);
+    if (rc != RRG_OK) return rc;
+    BCK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     batch_plant_kernel<<<1, kDecideThreads, 0, h->stream>>>(h->B, seed, t0, h->amp_dev, d_x_out);
     BCK(cudaGetLastError());
     h->launches++;
@@ -934,6 +1005,7 @@ int rrg_batch_autotune(rrg_batch_handle h, const double* d_x, const double* d_r,
     return bset_err(h, RRG_EINVAL, "d_x, d_r, d_v_prev non-NULL and repeats >= 1");
   BDeviceGuard g(h->device);
   h->B.t_dev = nullptr;
+  h->cl_next_ready = false;
   const bool prof = h->profiling;
   const double ms0 = h->rollout_ms;
   const uint64_t n0 = h->timed_rollouts;

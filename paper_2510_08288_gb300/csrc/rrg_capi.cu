@@ -475,6 +475,7 @@ int rrg_destroy(rrg_handle h) {
 int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index) {
   if (!h) return RRG_EINVAL;
   DeviceGuard g(h->device);
+  h->cl_next_ready = false;  // pair 0 may hold a closed loop's next update
   CK(launch_sample(h->L, seed, update_index, nullptr, h->cfg.dist_amp));
   h->launches++;
   return RRG_OK;
@@ -484,6 +485,7 @@ int rrg_set_scenarios(rrg_handle h, const double* d) {
   if (!h) return RRG_EINVAL;
   if (!d) return set_err(h, RRG_EINVAL, "d is NULL");
   DeviceGuard g(h->device);
+  h->cl_next_ready = false;
   const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
   CK(cudaMemcpyAsync(h->d64, d, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(launch_round_scenarios(h->L));
@@ -516,6 +518,7 @@ int rrg_set_param_multipliers(rrg_handle h, const double* m) {
     if (!is_fin(m[q]) || !(m[q] > 0.0))
       return set_err(h, RRG_EINVAL, "m[%zu] must be finite and > 0", q);
   DeviceGuard g(h->device);
+  h->cl_next_ready = false;
   CK(cudaMemcpyAsync(h->pmul, m, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return RRG_OK;
@@ -699,9 +702,11 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
     int rc = enqueue_search(h, h->loop->x, d_r_seq, &h->loop->t, &h->loop->v_prev, nullptr,
                             nullptr, nullptr, static_cast<long long>(t0));
     if (rc != RRG_OK) return rc;
+    // the side-stream sampler reads the update counter, which loop_end
+    // advances: join before it
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     CK(launch_loop_end(L, h->loop, seed, t0, amp, d_v_out, d_kappa_out, d_flags_out, d_x_out));
     h->launches++;
-    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     return RRG_OK;
   };
   h->cl_seed = seed;

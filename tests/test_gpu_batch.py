@@ -144,6 +144,9 @@ def test_batch_closed_loop_continues(R, orc, params):
         torch.cuda.synchronize()
         R.rrg_batch_closed_loop_dev(g.h, dev(x0.reshape(-1)), dev(b["v_prev"]), dr, 2, seed, 0, amp, True,
                                     ov, ok, of, ox)
+        # an unrelated update in between (its draw may overwrite the pair
+        # holding the loop's next update)
+        g.step(x0, b["r"], b["v_prev"], 77, 3)
         R.rrg_batch_closed_loop_dev(g.h, None, None, dr, 2, seed, 0, amp, True, ov, ok, of, ox)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(ok.cpu().numpy().reshape(T, S), one[1])

@@ -343,7 +343,8 @@ def test_full_size_update_matches_oracle(R, orc, params):
 
 def test_closed_loop_continuation_equals_one_run(R, orc, params):
     """rrg_closed_loop_dev with x0 = NULL continues the previous run: 2 + 1 + 1
-    updates give exactly the same trajectory as one call of 4 updates."""
+    updates, and 2 + 2 with other draws in between, give exactly the same
+    trajectory as one call of 4 updates."""
     import torch
     N, H, T = 16, 100, 4
     r_seq = inputs.staircase(T, 2, 2, seed=4)
@@ -352,7 +353,7 @@ def test_closed_loop_continuation_equals_one_run(R, orc, params):
     cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=R.FP32_RECHECK, max_candidates=16,
                recheck_eps_rel=SLACK32_TOL / 1.9)
     outs = []
-    for pieces in ((4,), (2, 1, 1)):
+    for pieces in ((4,), (2, 1, 1), (2, "draw", 2)):
         with R.Governor(params, cfg) as g:
             dev = torch.device("cuda")
             d_r = torch.tensor(r_seq, dtype=torch.float64, device=dev)
@@ -362,13 +363,20 @@ def test_closed_loop_continuation_equals_one_run(R, orc, params):
             d_x = torch.zeros(3 * (T + 1), dtype=torch.float64, device=dev)
             first = True
             for n in pieces:
+                if n == "draw":
+                    # an unrelated draw between the calls (it may overwrite
+                    # the pair holding the loop's next update)
+                    g.sample_scenarios(99, 0)
+                    g.sample_scenarios(99, 1)
+                    continue
                 R.rrg_closed_loop_dev(g.h, x0 if first else None, 90.0, d_r, n, 7, 3, amp, not first,
                                       d_v, d_k, d_f, d_x)
                 first = False
             torch.cuda.synchronize()
             outs.append((d_v.cpu().numpy(), d_k.cpu().numpy(), d_x.cpu().numpy()))
-    for a, b in zip(*outs):
-        np.testing.assert_array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
     vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 90.0, r_seq, 7, 3, amp, amp, search=0)
     np.testing.assert_array_equal(outs[0][1], ko)
 
