@@ -207,12 +207,13 @@ __global__ void batch_prepare_kernel(const BLaunch B) {
   if (B.c.ss_check) {
     const double thr = __dadd_rn(B.c.y_min, __dmul_rn(B.c.eps_ss, __dsub_rn(B.c.y_c, B.c.y_min)));
     float q32[3], y32 = 0.0f;
-    const int rc32 = equilibrium_dev<float>(B.k32, B.params, v, q32, &y32);
+    const bool v_ok = v > 0.0 && v <= DBL_MAX;
+    const int rc32 = v_ok ? equilibrium_from<float>(B.k32, B.params, C, q32, &y32) : -1;
     if (rc32 == 0 && fabs(static_cast<double>(y32) - thr) > 1e-4 * (1.0 + fabs(thr))) {
       ok = static_cast<double>(y32) >= thr;
     } else {
       double q[3], y_ss = 0.0;
-      ok = (equilibrium_dev<double>(B.k64, B.params, v, q, &y_ss) == 0) && (y_ss >= thr);
+      ok = v_ok && equilibrium_from<double>(B.k64, B.params, C, q, &y_ss) == 0 && y_ss >= thr;
     }
   }
   B.cand_ok[slot] = ok;

@@ -623,12 +623,13 @@ __device__ void prepare_slot(const Launch& L, int i) {
     // binary32 solve first; it decides unless y_ss lands within 1e-4 of the
     // threshold (its error is ~1e-6), in which case binary64 decides
     float q32[3], y32 = 0.0f;
-    const int rc32 = equilibrium_dev<float>(L.k32, L.params, v, q32, &y32);
+    const bool v_ok = v > 0.0 && v <= DBL_MAX;
+    const int rc32 = v_ok ? equilibrium_from<float>(L.k32, L.params, C, q32, &y32) : -1;
     if (rc32 == 0 && fabs(static_cast<double>(y32) - thr_ss) > 1e-4 * (1.0 + fabs(thr_ss))) {
       ok = static_cast<double>(y32) >= thr_ss;
     } else {
       double q[3], y_ss = 0.0;
-      ok = (equilibrium_dev<double>(K, L.params, v, q, &y_ss) == 0) && (y_ss >= thr_ss);
+      ok = v_ok && equilibrium_from<double>(K, L.params, C, q, &y_ss) == 0 && y_ss >= thr_ss;
     }
   }
   L.cand_ok[i] = ok;

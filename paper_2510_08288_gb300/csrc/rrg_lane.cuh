@@ -49,16 +49,16 @@ template <> __device__ __forceinline__ float eq_tol<float>() { return 1e-6f; }
 
 // Returns 0 and the gauge state q, output *y_ss at the equilibrium, or < 0.
 template <typename T>
-__device__ __forceinline__ int equilibrium_dev(const Fc3K<T>& K, const double* __restrict__ P, double I, T q[3],
-                               T* y_ss) {
-  if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
-  const CandK<double> Cd = cand_consts(P, I);
+__device__ __forceinline__ int equilibrium_from(const Fc3K<T>& K, const double* __restrict__ P,
+                                                const CandK<double>& Cd, T q[3], T* y_ss) {
   CandK<T> C;
   C.W_o2 = static_cast<T>(Cd.W_o2);
   C.V0 = static_cast<T>(Cd.V0);
   C.y_scale = static_cast<T>(Cd.y_scale);
-  const T ikca = static_cast<T>(1.0 / P[P_K_CA]), iksm = static_cast<T>(1.0 / P[P_K_SM]);
-  const T a_p = static_cast<T>(P[P_A_P]), iaw = static_cast<T>(1.0 / P[P_A_W]);
+  // reciprocals in the solve's own precision (binary32 divisions in the
+  // binary32 screen, none of GB300's slow binary64 ones)
+  const T ikca = T(1) / K.k_ca, iksm = T(1) / K.k_sm;
+  const T a_p = K.a_p, iaw = T(1) / K.a_w;
   const T big = static_cast<T>(1e30);
   T lo = C.W_o2;
   if (!(eq_torque<T>(K, C, ikca, iksm, a_p, iaw, lo, q) > T(0))) return -2;
@@ -91,6 +91,14 @@ __device__ __forceinline__ int equilibrium_dev(const Fc3K<T>& K, const double* _
   eq_torque<T>(K, C, ikca, iksm, a_p, iaw, W, q);
   *y_ss = fc3_output<T>(C, q[0], q[2]);
   return 0;
+}
+
+// The same from the setpoint I alone.
+template <typename T>
+__device__ __forceinline__ int equilibrium_dev(const Fc3K<T>& K, const double* __restrict__ P,
+                                               double I, T q[3], T* y_ss) {
+  if (!(I > 0.0) || !(I <= DBL_MAX)) return -1;
+  return equilibrium_from<T>(K, P, cand_consts(P, I), q, y_ss);
 }
 
 // ---------------------------------------------------------------------------
