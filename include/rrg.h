@@ -411,8 +411,10 @@ int rrg_eval_candidates_static(const double *model_params, int n_params, const r
  * (otherwise RRG_ENOTIMPL).  Each instance's result equals rrg_step's for
  * the same inputs and scenarios. */
 #define RRG_BATCH_MAX_INSTANCES 1024
-#define RRG_BATCH_VARIANTS 6   /* rollout variants: lanes per tile {64, 128,
-                                  256} x disturbance prefetch depth {8, 16} */
+#define RRG_BATCH_VARIANTS 8   /* rollout variants: lanes per tile {64, 128,
+                                  256} x disturbance prefetch depth {8, 16},
+                                  then warp tiles (32 lanes, each warp takes its
+                                  own) x {8, 16} */
 typedef struct rrg_batch_ctx *rrg_batch_handle;
 
 /* cfg as for rrg_create (n_scenarios and horizon are ignored); n_scenarios

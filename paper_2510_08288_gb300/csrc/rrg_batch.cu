@@ -319,6 +319,41 @@ __global__ void __launch_bounds__(TILE) batch_rollout_kernel(const BLaunch B) {
   }
 }
 
+// Persistent rollout with warp-sized tiles: each warp takes its own 32-lane
+// tile from the queue, so a warp whose lanes finish early never waits at a
+// CTA barrier for the others.
+__device__ __forceinline__ void tile_of(const BLaunch& B, uint32_t t, int tile, int* s, int* i,
+                                        int* b) {
+  int lo = 0, hi = B.c.S;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (static_cast<uint32_t>(B.tile_base[mid]) <= t) lo = mid; else hi = mid;
+  }
+  *s = B.order[lo];
+  const int nb = (B.inst[*s].N + tile - 1) / tile;
+  const int local = static_cast<int>(t) - B.tile_base[lo];
+  *i = local / nb;
+  *b = local - *i * nb;
+}
+
+template <int PF>
+__global__ void __launch_bounds__(128) batch_rollout_warp_kernel(const BLaunch B) {
+  const uint32_t total = B.queue[1];
+  const int lane = static_cast<int>(threadIdx.x & 31);
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(B.queue, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) return;
+    int s = 0, i = 0, b = 0;
+    if (lane == 0) tile_of(B, t, 32, &s, &i, &b);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    batch_tile<PF>(B, s, i, b * 32 + lane);
+  }
+}
+
 // Binary64 re-run (disturbances regenerated from the Philox counters) over
 // steps 0..jlast of each listed lane.
 __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
@@ -468,11 +503,14 @@ struct Variant {
   int tile, pf;
   void (*kernel)(const BLaunch);
 };
+// tile = 32: warp tiles (CTAs of 4 warps, no CTA barrier)
 const Variant kVariants[RRG_BATCH_VARIANTS] = {
     {64, 8, batch_rollout_kernel<64, 8>},   {64, 16, batch_rollout_kernel<64, 16>},
     {128, 8, batch_rollout_kernel<128, 8>}, {128, 16, batch_rollout_kernel<128, 16>},
     {256, 8, batch_rollout_kernel<256, 8>}, {256, 16, batch_rollout_kernel<256, 16>},
+    {32, 8, batch_rollout_warp_kernel<8>},  {32, 16, batch_rollout_warp_kernel<16>},
 };
+constexpr int block_threads(int tile) { return tile == 32 ? 128 : tile; }
 
 }  // namespace
 }  // namespace rrg
@@ -619,7 +657,7 @@ int enqueue_rollout(rrg_batch_ctx* h) {
     b = btake_event(h);
     if (a && b) BCK(cudaEventRecord(a, h->stream));
   }
-  v.kernel<<<h->grid[h->variant], v.tile, 0, h->stream>>>(h->B);
+  v.kernel<<<h->grid[h->variant], block_threads(v.tile), 0, h->stream>>>(h->B);
   BCK(cudaGetLastError());
   if (timed && a && b) {
     BCK(cudaEventRecord(b, h->stream));
@@ -793,7 +831,8 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   for (int v = 0; v < RRG_BATCH_VARIANTS && e == cudaSuccess; ++v) {
     int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kVariants[v].kernel, kVariants[v].tile, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kVariants[v].kernel,
+                                                      block_threads(kVariants[v].tile), 0);
     h->grid[v] = std::max(1, per) * nsm;
   }
   if (e != cudaSuccess) {

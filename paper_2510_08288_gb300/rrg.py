@@ -418,7 +418,7 @@ class Governor:
 
 
 # ---------------------------------------------------------------- batched --
-BATCH_VARIANTS = 6
+BATCH_VARIANTS = 8
 
 
 def rrg_batch_last_error(h=None) -> str:
