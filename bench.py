@@ -345,6 +345,30 @@ def run_gpu(args):
     graph_s = sum(a.elapsed_time(b) for a, b in gevs) / 1e3
     graph_same = bool(torch.equal(gd_k, d_k))
     gg.close()
+    # and once more with the disturbances drawn inside the trajectory loop
+    # (no stored scenario array, no sampler pass)
+    cfg_gen = R.rrg_config_default(horizon=HZ, n_scenarios=NS, max_candidates=M_CAND,
+                                   n_bisect=N_BISECT, search=R.SEARCH_SPEC_BISECT,
+                                   precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
+                                   recheck_eps_rel=RECHECK_EPS_REL, probe_steps=args.probe_steps,
+                                   scenarios_in_register=1)
+    gr = R.Governor(p, cfg_gen, stream)
+    gr.set_tuning(tune_m, tune_probe)
+    rd_v, rd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
+    rd_f, rd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
+    R.rrg_closed_loop_dev(gr.h, x0, V0, d_r, W, seed, 0, amp, True, rd_v, rd_k, rd_f, rd_x)
+    revs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(float(i))
+            revs[i][0].record(stream)
+            R.rrg_closed_loop_dev(gr.h, None, 0.0, d_r, 1, seed, 0, amp, True, rd_v, rd_k, rd_f, rd_x)
+            revs[i][1].record(stream)
+    torch.cuda.synchronize()
+    reg_s = sum(a.elapsed_time(b) for a, b in revs) / 1e3
+    reg_same = bool(torch.equal(rd_k, d_k))
+    gr.close()
 
     kap_dev = d_k.cpu().numpy()
     flags_dev = d_f.cpu().numpy()
@@ -419,6 +443,9 @@ def run_gpu(args):
             "e2e": e2e,
             "graph_replay": {"value": world * K / graph_s, "unit": UNIT, "ms_per_step": 1e3 * graph_s / K,
                              "kappa_equal_to_direct_launches": graph_same},
+            "scenarios_in_register": {"value": world * K / reg_s, "unit": UNIT, "ms_per_step": 1e3 * reg_s / K,
+                                      "mode": "graph replay, disturbances drawn in the trajectory loop",
+                                      "kappa_equal_to_direct_launches": reg_same},
             "gpu_launches": st["launches"],
             "clocks": clk,
             "fp64_bisect_gpu": fp64,
@@ -864,6 +891,33 @@ def run_sweep(args):
             _, k64, _ = g64.step(x_t, r, v_prev)
             fp64 = {"ms_per_update": 1e3 * (time.perf_counter() - t0), "kappa_equal": bool(k64 == kap[0])}
             g64.close()
+        # the same updates with the disturbances drawn inside the trajectory
+        # loop (no stored array, no sampler pass), at the largest N only
+        gen_leg = None
+        if N == ns[-1]:
+            cfg_g = R.rrg_config_default(horizon=SWEEP_H, n_scenarios=N, max_candidates=SWEEP_M,
+                                         n_rounds=SWEEP_ROUNDS, search=R.SEARCH_KSECTION,
+                                         precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
+                                         recheck_eps_rel=RECHECK_EPS_REL, param_unc_rel=rho,
+                                         param_unc_mask=inputs.FC3_UNCERTAIN_MASK, scenarios_in_register=1)
+            gg = R.Governor(p, cfg_g, stream)
+            kg, gms = [], []
+            for t in range(W + K):
+                flush.fill_(float(t))
+                torch.cuda.synchronize()
+                a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    a_ev.record(stream)
+                    gg.sample_scenarios(SEED, t)
+                    R.rrg_step_dev(gg.h, d_x, d_r, d_vp, d_out[2 * t:2 * t + 1], d_out[2 * t + 1:2 * t + 2],
+                                   d_fl[t:t + 1])
+                    b_ev.record(stream)
+                torch.cuda.synchronize()
+                if t >= W:
+                    gms.append(a_ev.elapsed_time(b_ev))
+                    kg.append(float(d_out[2 * t + 1].item()))
+            gg.close()
+            gen_leg = {"ms_per_update": statistics.mean(gms), "kappa_equal_to_stored": kg == [float(x) for x in kap]}
         rows.append({"n_scenarios": N, "updates_per_s": K / secs, "ms_per_update": 1e3 * secs / K,
                      "trajectory_steps_per_s": st["lane_steps"] / secs,
                      "nominal_trajectory_steps_per_update": SWEEP_ROUNDS * SWEEP_M * N * SWEEP_H,
@@ -871,7 +925,8 @@ def run_sweep(args):
                      "rollout_tflops": achieved, "rollout_frac": achieved / FP32_PEAK_TFLOPS,
                      "rollout_avg_launch_ms": avg_roll_ms, "rechecked": st["rechecked"],
                      "gpu_launches": st["launches"], "kappa": [float(x) for x in kap],
-                     "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64})
+                     "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64,
+                     "scenarios_in_register": gen_leg})
         g.close()
         del d_x, d_r, d_vp, d_out, d_fl
         torch.cuda.empty_cache()

@@ -132,6 +132,14 @@ typedef struct {
                                 simulated plant keep the nominal theta.       */
     uint32_t param_unc_mask; /* bit p: parameter p is uncertain (bits below
                                 RRG_NPARAM only)                             */
+    int32_t scenarios_in_register; /* 1: the rollouts draw each step's
+                                disturbances from its Philox counters inside
+                                the trajectory loop instead of reading the
+                                stored array (rrg_sample_scenarios then writes
+                                no array); same values, same results.  0
+                                (default): stored array.  Single-problem
+                                handles only; rrg_set_scenarios is then
+                                RRG_EINVAL.                                   */
 } rrg_config;
 
 /* FC3 parameters perturbed by default: k_ca, eta_cp, J_cp, eta_cm, R_cm,
@@ -173,8 +181,8 @@ void rrg_config_default(rrg_config *cfg);
  *                 destroys) a private non-blocking stream of its own.
  *   out           host; receives the handle.
  * Allocates all device memory the handle needs (about 36 H N bytes of
- * scenarios plus O(max_candidates * N) bytes of per-candidate and recheck
- * buffers).  RRG_ENOMEM / RRG_ECUDA on failure (nothing leaks). */
+ * scenarios, 24 H N with scenarios_in_register, plus O(max_candidates * N)
+ * bytes of per-candidate and recheck buffers).  RRG_ENOMEM / RRG_ECUDA on failure (nothing leaks). */
 int rrg_create(const double *model_params, int n_params, const rrg_config *cfg,
                void *cuda_stream, rrg_handle *out);
 

@@ -738,8 +738,9 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
     return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_SEARCH_GRID or RRG_SEARCH_KSECTION");
   if (cfg->precision != RRG_FP32_RECHECK)
     return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_FP32_RECHECK");
-  if (cfg->param_unc_rel != 0.0)
-    return bset_err(h, RRG_ENOTIMPL, "batched instances have no parametric uncertainty");
+  if (cfg->param_unc_rel != 0.0 || cfg->scenarios_in_register != 0)
+    return bset_err(h, RRG_ENOTIMPL, "batched instances have no parametric uncertainty and store "
+                    "their scenarios (param_unc_rel and scenarios_in_register must be 0)");
   if (n_instances < 1 || n_instances > kMaxInst)
     return bset_err(h, RRG_EINVAL, "n_instances must be in [1, %d]", kMaxInst);
   if (!n_scenarios || !horizons) return bset_err(h, RRG_EINVAL, "n_scenarios and horizons must be non-NULL");

@@ -153,6 +153,8 @@ int validate_cfg(const rrg_config* c) {
   if (c->probe_steps < 0) return set_err(nullptr, RRG_EINVAL, "probe_steps must be >= 0");
   if (!is_fin(c->param_unc_rel) || c->param_unc_rel < 0.0 || c->param_unc_rel >= 1.0)
     return set_err(nullptr, RRG_EINVAL, "param_unc_rel must be in [0, 1)");
+  if (c->scenarios_in_register != 0 && c->scenarios_in_register != 1)
+    return set_err(nullptr, RRG_EINVAL, "scenarios_in_register must be 0 or 1");
   if (c->param_unc_mask >> RRG_NPARAM)
     return set_err(nullptr, RRG_EINVAL, "param_unc_mask has bits at or above RRG_NPARAM");
   const unsigned long long lanes =
@@ -199,6 +201,7 @@ void fill_launch(rrg_ctx* h) {
   L.dt = c.dt;
   L.y_min = c.y_min;
   L.eps_abs = c.precision == RRG_FP32_RECHECK ? c.recheck_eps_rel * std::fabs(c.y_min) : 0.0;
+  L.scen_gen = c.scenarios_in_register;
   L.scfg = h->scfg;
   L.params = h->params_dev;
   fold_constants(h->params, &L.k64, &L.k32);
@@ -396,7 +399,10 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   ALLOC(params_dev, RRG_NPARAM);
   ALLOC(pws, 1);
   ALLOC(d64, HN3);
-  ALLOC(d32, HN3);
+  // in-register scenarios need no binary32 array (the binary64 one stays for
+  // rrg_get_scenarios and the adjoint)
+  const size_t n32 = c.scenarios_in_register ? 1 : HN3;
+  ALLOC(d32, n32);
   ALLOC(st, 1);
   // two slot ranges: a pipelined round and the round after it run together
   ALLOC(cand_kappa, 2 * M);
@@ -427,7 +433,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(SearchState), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d64, 0, HN3 * sizeof(double), h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, HN3 * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, n32 * sizeof(float), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->params_dev, h->params, sizeof h->params, cudaMemcpyHostToDevice, h->stream);
   PowSeries ps;
@@ -484,6 +490,8 @@ int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index) {
 int rrg_set_scenarios(rrg_handle h, const double* d) {
   if (!h) return RRG_EINVAL;
   if (!d) return set_err(h, RRG_EINVAL, "d is NULL");
+  if (h->cfg.scenarios_in_register)
+    return set_err(h, RRG_EINVAL, "the handle draws its scenarios in-register (scenarios_in_register = 1)");
   DeviceGuard g(h->device);
   h->cl_next_ready = false;
   const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
@@ -661,7 +669,8 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
   if (!h->L.d64b) {
     const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
     if (!h->d64b) CK(cudaMalloc(reinterpret_cast<void**>(&h->d64b), n * sizeof(double)));
-    if (!h->d32b) CK(cudaMalloc(reinterpret_cast<void**>(&h->d32b), n * sizeof(float)));
+    const size_t n32 = h->cfg.scenarios_in_register ? 1 : n;
+    if (!h->d32b) CK(cudaMalloc(reinterpret_cast<void**>(&h->d32b), n32 * sizeof(float)));
     if (h->pmul && !h->pmulb) {
       const size_t np = static_cast<size_t>(h->cfg.n_scenarios) * RRG_NPARAM;
       CK(cudaMalloc(reinterpret_cast<void**>(&h->pmulb), np * sizeof(double)));

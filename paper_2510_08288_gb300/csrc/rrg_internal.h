@@ -122,6 +122,7 @@ struct SearchCfg {
 struct Launch {
   cudaStream_t stream;
   int N, H, precision, early_exit, m_cap;
+  int scen_gen;                 // disturbances drawn inside the trajectory loop
   double dt, y_min, eps_abs;
   SearchCfg scfg;
   const double* params;         // [RRG_NPARAM] (device)

@@ -76,7 +76,7 @@ __device__ __forceinline__ void sample_param_group(double* __restrict__ pm, uint
 __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
                               double* __restrict__ d64b, float* __restrict__ d32b, int N, int H,
                               uint64_t seed, uint64_t base, const unsigned long long* t_dev,
-                              double a0, double a1, double a2, int write64, SearchState* st,
+                              double a0, double a1, double a2, int write64, int gen, SearchState* st,
                               double* __restrict__ pm, double* __restrict__ pmb, double rho,
                               uint32_t mask) {
   const uint64_t upd = base + (t_dev ? *t_dev : 0ull);
@@ -88,7 +88,7 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ScenSrc src;
-    src.d64_valid = write64;
+    src.d64_valid = gen ? 0 : write64;
     src.pad = 0;
     src.seed = seed;
     src.update = upd;
@@ -101,7 +101,8 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   const float s0 = static_cast<float>(a0 * 0x1.0p-23), s1 = static_cast<float>(a1 * 0x1.0p-23),
               s2 = static_cast<float>(a2 * 0x1.0p-23);
-  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
+  for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; !gen && q < HN;
+       q += stride) {
     const uint64_t j = q / static_cast<uint64_t>(N), k = q - j * static_cast<uint64_t>(N);
     const U64x4 w = philox4x64_10(j, k, upd, 0ull, seed, 0ull);
     if (write64) {
@@ -137,7 +138,7 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
   const int write64 = L.precision == RRG_FP64 ? 1 : 0;
   sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, stream ? stream : L.stream>>>(
       L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
-      amp[0], amp[1], amp[2], write64, L.st, L.pmul, dual ? L.pmulb : nullptr, L.punc_rho,
+      amp[0], amp[1], amp[2], write64, L.scen_gen, L.st, L.pmul, dual ? L.pmulb : nullptr, L.punc_rho,
       L.punc_mask);
   return cudaGetLastError();
 }
@@ -185,7 +186,7 @@ __global__ void round_scenarios_kernel(const double* __restrict__ d64, float* __
 }
 
 cudaError_t launch_round_scenarios(const Launch& L) {
-  const size_t n = 3 * static_cast<size_t>(L.H) * L.N;
+  const size_t n = L.scen_gen ? 0 : 3 * static_cast<size_t>(L.H) * L.N;
   round_scenarios_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.d32, n, L.st);
   return cudaGetLastError();
 }
@@ -197,7 +198,7 @@ cudaError_t launch_round_scenarios(const Launch& L) {
 // SEG_PROBE lane that survives its probe steps saves its state and reports
 // nothing yet; the SEG_CONTINUE lane of the next launch finishes it.  PU:
 // parametric uncertainty, each lane folds its scenario's own model constants.
-template <typename T, bool PU>
+template <typename T, bool PU, bool GEN>
 __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
                                              const T* __restrict__ d_pair0,
                                              const T* __restrict__ d_pair1,
@@ -271,9 +272,14 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
     if (final_lane) {
       const int j_end = mode == SEG_PROBE ? L.probe_steps : L.H;
       int end = LANE_REACHED_END;
-      smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, smin0,
-                         static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
-                         cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
+      if constexpr (GEN)
+        smin = run_lane_gen<T>(K, C, L.st->src[L.st->buf], k, j0, j_end, q_ca, w, q_sm, smin0,
+                               static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+                               cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
+      else
+        smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, smin0,
+                           static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+                           cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
       if (cand_stop && smin < thr) *dead = 1;
       if (mode == SEG_PROBE) {
         LaneState<T> o;
@@ -325,12 +331,14 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
   }
 }
 
-template <typename T>
+// GEN: the disturbances are drawn inside the trajectory loop (in-register
+// scenarios) instead of read from the stored array.
+template <typename T, bool GEN>
 __global__ void __launch_bounds__(kRollThreads)
 rollout_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0,
                const T* __restrict__ d_pair1, const RhsC<T>* __restrict__ cand, int early_exit,
                int classify) {
-  rollout_body<T, false>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
+  rollout_body<T, false, GEN>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
 }
 
 // Parametric uncertainty: the per-lane constants need about 30 more
@@ -341,33 +349,38 @@ rollout_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0,
 #ifndef RRG_PU_MIN_BLOCKS
 #define RRG_PU_MIN_BLOCKS 4
 #endif
-template <typename T>
+template <typename T, bool GEN>
 __global__ void __launch_bounds__(kRollThreads, sizeof(T) == 4 ? RRG_PU_MIN_BLOCKS : 1)
 rollout_pu_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0,
                   const T* __restrict__ d_pair1, const RhsC<T>* __restrict__ cand, int early_exit,
                   int classify) {
-  rollout_body<T, true>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
+  rollout_body<T, true, GEN>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
 }
 
 cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
                            bool recheck_classify) {
   dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
   const int cls = recheck_classify ? 1 : 0;
+#define RRG_ROLLOUT(KERNEL, T, GEN, KK, D0, D1, CAND, CLS) \
+  KERNEL<T, GEN><<<grid, kRollThreads, 0, L.stream>>>(L, KK, D0, D1, CAND, early_exit, CLS)
   if (use_fp64) {
-    if (L.pmul)
-      rollout_pu_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.u64, L.d64, L.d64b,
-                                                                     L.cand_c64, early_exit, 0);
-    else
-      rollout_kernel<double><<<grid, kRollThreads, 0, L.stream>>>(L, L.u64, L.d64, L.d64b,
-                                                                  L.cand_c64, early_exit, 0);
+    if (L.pmul) {
+      if (L.scen_gen) RRG_ROLLOUT(rollout_pu_kernel, double, true, L.u64, L.d64, L.d64b, L.cand_c64, 0);
+      else RRG_ROLLOUT(rollout_pu_kernel, double, false, L.u64, L.d64, L.d64b, L.cand_c64, 0);
+    } else {
+      if (L.scen_gen) RRG_ROLLOUT(rollout_kernel, double, true, L.u64, L.d64, L.d64b, L.cand_c64, 0);
+      else RRG_ROLLOUT(rollout_kernel, double, false, L.u64, L.d64, L.d64b, L.cand_c64, 0);
+    }
   } else {
-    if (L.pmul)
-      rollout_pu_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b,
-                                                                    L.cand_c32, early_exit, cls);
-    else
-      rollout_kernel<float><<<grid, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b,
-                                                                 L.cand_c32, early_exit, cls);
+    if (L.pmul) {
+      if (L.scen_gen) RRG_ROLLOUT(rollout_pu_kernel, float, true, L.u32, L.d32, L.d32b, L.cand_c32, cls);
+      else RRG_ROLLOUT(rollout_pu_kernel, float, false, L.u32, L.d32, L.d32b, L.cand_c32, cls);
+    } else {
+      if (L.scen_gen) RRG_ROLLOUT(rollout_kernel, float, true, L.u32, L.d32, L.d32b, L.cand_c32, cls);
+      else RRG_ROLLOUT(rollout_kernel, float, false, L.u32, L.d32, L.d32b, L.cand_c32, cls);
+    }
   }
+#undef RRG_ROLLOUT
   return cudaGetLastError();
 }
 

@@ -250,6 +250,88 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
   return smin;
 }
 
+// Disturbance component of Philox word w with half-range a: the binary32
+// copy (top 24 bits, a 2^-23 folded in) or the binary64 value, exactly as the
+// sampler stores them.
+template <typename T> __device__ __forceinline__ T draw(uint64_t w, double a);
+template <> __device__ __forceinline__ float draw<float>(uint64_t w, double a) {
+  return uniform_sym32(w, static_cast<float>(a * 0x1.0p-23));
+}
+template <> __device__ __forceinline__ double draw<double>(uint64_t w, double a) {
+  return uniform_sym(w, a);
+}
+
+// run_lane with the disturbances drawn from their Philox counters (j, k,
+// update, 0) inside the loop instead of read from the stored array: the
+// same values, so the same trajectory and decisions.  Same contract as
+// run_lane.
+template <typename T, int PF = PrefetchDepth<T>::value>
+__device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, const ScenSrc& src,
+                                          int k, int j0, int j_end, T& q_ca, T& w, T& q_sm,
+                                          T smin_in, T dt, T y_min, T thr,
+                                          const volatile int32_t* dead, unsigned* steps, int* end,
+                                          T band, int* jlast) {
+  T smin = smin_in;
+  int j = j0;
+  int jl = *jlast;
+  int how = LANE_REACHED_END;
+  bool go = j < j_end;
+  if (j0 == 0) {
+    const T s0 = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    smin = fmin(smin, s0);
+    if (s0 < band) jl = 0;
+    if (s0 < thr) {
+      how = LANE_VIOLATED;
+      go = false;
+    }
+  }
+  bool stop = !go;
+  while (!stop && j + PF <= j_end) {
+    const int dead_now = dead != nullptr ? *dead : 0;
+    T nf = T(0), bmin = inf_v<T>();
+#pragma unroll 4
+    for (int u = 0; u < PF; ++u) {
+      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
+                                    0ull, src.seed, 0ull);
+      rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm, draw<T>(r.w[0], src.amp[0]),
+                       draw<T>(r.w[1], src.amp[1]), draw<T>(r.w[2], src.amp[2]));
+      ++j;
+      const T s = C.y_scale * (q_sm - q_ca) - y_min;
+      bmin = fmin(bmin, s);
+      nf = fma_rn(s, T(0), nf);
+    }
+    nf = fma_rn(q_ca, T(0), fma_rn(w, T(0), fma_rn(q_sm, T(0), nf)));
+    if (nf != nf) bmin = -inf_v<T>();
+    smin = fmin(smin, bmin);
+    if (bmin < band) jl = j;
+    if (smin < thr) {
+      how = LANE_VIOLATED;
+      stop = true;
+    } else if (dead_now != 0 && j < j_end) {
+      how = LANE_STOPPED;
+      stop = true;
+    }
+  }
+  while (!stop && j < j_end) {
+    const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update, 0ull,
+                                  src.seed, 0ull);
+    rk4_step_fast<T>(K, C, dt, q_ca, w, q_sm, draw<T>(r.w[0], src.amp[0]),
+                     draw<T>(r.w[1], src.amp[1]), draw<T>(r.w[2], src.amp[2]));
+    ++j;
+    const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    smin = fmin(smin, s);
+    if (s < band) jl = j;
+    if (s < thr) {
+      how = LANE_VIOLATED;
+      stop = true;
+    }
+  }
+  *steps = static_cast<unsigned>(j - j0);
+  *end = how;
+  *jlast = jl;
+  return smin;
+}
+
 // Scenario k's model under parametric uncertainty: the parameters theta_p
 // m_p^k folded like the nominal ones, and the candidate constants at v.
 // Returns the scenario's p_atm (the origin of its gauge coordinates).

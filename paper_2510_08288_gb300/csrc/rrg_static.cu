@@ -105,9 +105,9 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
     if (!std::isfinite(model_params[i])) return fail(RRG_EINVAL, "model_params[%d] not finite", i);
   int rc = check_config(cfg);
   if (rc != RRG_OK) return rc;
-  if (cfg->param_unc_rel != 0.0)
+  if (cfg->param_unc_rel != 0.0 || cfg->scenarios_in_register != 0)
     return fail(RRG_ENOTIMPL, "the allocation-free evaluation has no parametric uncertainty "
-                "(param_unc_rel must be 0)");
+                "and reads the caller's scenarios (param_unc_rel and scenarios_in_register must be 0)");
   if (m < 1 || m > cfg->max_candidates || m > kStaticMaxCand)
     return fail(RRG_EINVAL, "m = %d: the allocation-free evaluation takes 1..%d candidates "
                 "(and at most max_candidates)", m, kStaticMaxCand);

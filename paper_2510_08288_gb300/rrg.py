@@ -38,7 +38,7 @@ class RrgConfig(ctypes.Structure):
         ("n_bisect", _i32), ("n_rounds", _i32), ("search", _i32), ("precision", _i32),
         ("early_exit", _i32), ("ss_check", _i32), ("y_min", _d), ("eps_ss", _d), ("y_c", _d),
         ("recheck_eps_rel", _d), ("dist_amp", _d * 3), ("probe_steps", _i32),
-        ("param_unc_rel", _d), ("param_unc_mask", ctypes.c_uint32),
+        ("param_unc_rel", _d), ("param_unc_mask", ctypes.c_uint32), ("scenarios_in_register", _i32),
     ]
 
 

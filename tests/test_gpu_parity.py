@@ -485,3 +485,44 @@ def test_autotune_and_tuning_keep_alg1_result(R, orc, params):
     with R.Governor(params, _cfg(R, N, H, search=R.SEARCH_GRID)) as g:
         with pytest.raises(R.RrgError):
             g.autotune(x_t, 250.0, 100.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_recheck"])
+def test_in_register_scenarios_equal_stored_ones(R, orc, params, prec):
+    """Drawing each step's disturbances from its Philox counters inside the
+    trajectory loop gives exactly the stored-array results (same values), also
+    under parametric uncertainty and through the pipelined search."""
+    N, H = 300, 333
+    p = {"fp64": R.FP64, "fp32": R.FP32, "fp32_recheck": R.FP32_RECHECK}[prec]
+    x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.02, 1.0])
+    kappas = np.linspace(0.0, 0.3, 13)
+    for unc in (0.0, 0.1):
+        outs = []
+        for gen in (0, 1):
+            cfg = _cfg(R, N, H, precision=p, early_exit=R.EXIT_NONE, max_candidates=16,
+                       scenarios_in_register=gen, param_unc_rel=unc, recheck_eps_rel=SLACK32_TOL / 1.9)
+            with R.Governor(params, cfg) as g:
+                g.sample_scenarios(4, 9)
+                adm, ms, P = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+                step = g.step(x_t, 250.0, 100.0)
+                if gen:
+                    with pytest.raises(R.RrgError):
+                        g.set_scenarios(np.zeros((3, H, N)))
+            outs.append((adm, ms, P, np.array(step)))
+        for a, b in zip(*outs):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_in_register_scenarios_closed_loop(R, orc, params):
+    N, H, T = 32, 200, 5
+    r_seq = inputs.staircase(T, 3, 2, seed=8)
+    x0 = orc.equilibrium(params, 100.0)
+    amp = inputs.DIST_AMP
+    runs = []
+    for gen in (0, 1):
+        cfg = _cfg(R, N, H, precision=R.FP32_RECHECK, max_candidates=16, scenarios_in_register=gen,
+                   recheck_eps_rel=SLACK32_TOL / 1.9)
+        with R.Governor(params, cfg) as g:
+            runs.append(g.closed_loop(x0, 100.0, r_seq, 3, 1, amp, use_graph=True))
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
