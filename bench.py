@@ -382,6 +382,9 @@ def run_gpu(args):
     roll_launches = max(1, st["timed_rollouts"])
     achieved = (fp32_steps / roll_launches) * FLOPS_PER_STEP / (avg_roll_ms * 1e-3) / 1e12
 
+    # the FP32 FMA, FP64 FMA and MUFU throughput measured on this GPU, next to
+    # the derived peak the roofline fraction is reported against
+    peaks = R.rrg_alu_peaks()
     out = None
     if rank == 0:
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
@@ -438,7 +441,10 @@ def run_gpu(args):
                          "kernel": "rollout_kernel<float>",
                          "avg_launch_ms": avg_roll_ms, "launches": st["timed_rollouts"],
                          "flops_per_traj_step": FLOPS_PER_STEP,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                         "measured_units": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
+                                            "mufu_ex2_tops": peaks[2],
+                                            "frac_of_measured_fp32": achieved / peaks[0]}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "graph_replay": {"value": world * K / graph_s, "unit": UNIT, "ms_per_step": 1e3 * graph_s / K,

@@ -405,6 +405,12 @@ int rrg_eval_candidates_static(const double *model_params, int n_params, const r
                                const double *d_kappas, int m, uint8_t *d_admissible,
                                double *d_min_slack);
 
+/* Measured throughput of the arithmetic units the rollouts use, on the current
+ * device (about 10 ms): binary32 FMA and binary64 FMA in TFLOP/s (an FMA
+ * counted as 2 flops) and MUFU exp2 in Top/s; each output may be NULL.
+ * Synchronous on the legacy default stream.  RRG_ECUDA / RRG_ENOMEM. */
+int rrg_alu_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_tops);
+
 /* ------------------------------------------------------------------------ */
 /* Batched instances: S independent robust RG problems (instance s with its
  * own N_s scenarios and horizon H_s) that share the model, dt, the search and

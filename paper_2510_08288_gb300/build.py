@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "librrg.so")
-SOURCES = ("rrg_kernels.cu", "rrg_capi.cu", "rrg_static.cu", "rrg_adjoint.cu", "rrg_batch.cu")
+SOURCES = ("rrg_kernels.cu", "rrg_capi.cu", "rrg_static.cu", "rrg_adjoint.cu", "rrg_batch.cu",
+           "rrg_peaks.cu")
 HEADERS = ("rrg_device.cuh", "rrg_internal.h", "rrg_lane.cuh")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: the binary32 rollouts never meet subnormal values, and flushing

@@ -94,6 +94,7 @@ def _load():
                                              _p, _p, _p]),
         "rrg_eval_candidates_static": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, _p, _p, _p, _d,
                                                       _d, _p, ctypes.c_int, _p, _p]),
+        "rrg_alu_peaks": (ctypes.c_int, [_p, _p, _p]),
         "rrg_batch_create": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), ctypes.c_int, _p, _p, _p, P(_p)]),
         "rrg_batch_destroy": (ctypes.c_int, [_p]),
         "rrg_batch_last_error": (ctypes.c_char_p, [_p]),
@@ -415,6 +416,13 @@ class Governor:
 
     def get_tuning(self):
         return rrg_get_tuning(self.h)
+
+
+def rrg_alu_peaks():
+    """Measured (binary32 FMA TFLOP/s, binary64 FMA TFLOP/s, MUFU exp2 Top/s)."""
+    a, b, c = _d(0.0), _d(0.0), _d(0.0)
+    _check(lib.rrg_alu_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), None)
+    return a.value, b.value, c.value
 
 
 # ---------------------------------------------------------------- batched --

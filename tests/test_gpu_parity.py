@@ -526,3 +526,13 @@ def test_in_register_scenarios_closed_loop(R, orc, params):
             runs.append(g.closed_loop(x0, 100.0, r_seq, 3, 1, amp, use_graph=True))
     for a, b in zip(*runs):
         np.testing.assert_array_equal(a, b)
+
+
+def test_alu_peaks_are_plausible(R):
+    """The unit throughput measured on this GPU: binary32 FMA near the
+    derived 80.5 TFLOP/s, binary64 FMA far below it, MUFU exp2 in between."""
+    f32, f64, mufu = R.rrg_alu_peaks()
+    print("measured: fp32 FMA %.1f TFLOP/s, fp64 FMA %.2f TFLOP/s, MUFU ex2 %.2f Top/s" % (f32, f64, mufu))
+    assert 20.0 < f32 < 100.0
+    assert 0.05 < f64 < f32 / 8
+    assert 0.5 < mufu < f32
