@@ -39,6 +39,13 @@
 
 #include <stdint.h>
 
+/* Entry points are exported; everything else in the library is hidden. */
+#if defined(__GNUC__)
+#define RRG_API __attribute__((visibility("default")))
+#else
+#define RRG_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -163,6 +170,9 @@ typedef struct {
     uint64_t timed_rollouts;    /* rollout launches covered by rollout_ms     */
     uint64_t repairs;           /* pipelined rounds redone after a provisional
                                    outcome turned out wrong                   */
+    uint64_t graph_conditional; /* 1: the cached closed-loop graph holds the
+                                   rounds after a pipelined pair in a
+                                   conditional node (run only when needed)    */
 } rrg_stats;
 
 /* Fills *cfg with the defaults of the paper's fuel-cell experiment: dt 0.01,
@@ -171,7 +181,7 @@ typedef struct {
  * 1e-6, amplitudes (50, 10, 50), probe_steps 128, no parametric
  * uncertainty (param_unc_rel 0, param_unc_mask RRG_PARAM_UNC_MASK_FC3).
  * Never fails. */
-void rrg_config_default(rrg_config *cfg);
+RRG_API void rrg_config_default(rrg_config *cfg);
 
 /* Creates a governor on the current CUDA device.
  *   model_params  host, n_params doubles in the FC3 layout above; copied.
@@ -183,14 +193,14 @@ void rrg_config_default(rrg_config *cfg);
  * Allocates all device memory the handle needs (about 36 H N bytes of
  * scenarios, 24 H N with scenarios_in_register, plus O(max_candidates * N)
  * bytes of per-candidate and recheck buffers).  RRG_ENOMEM / RRG_ECUDA on failure (nothing leaks). */
-int rrg_create(const double *model_params, int n_params, const rrg_config *cfg,
+RRG_API int rrg_create(const double *model_params, int n_params, const rrg_config *cfg,
                void *cuda_stream, rrg_handle *out);
 
 /* Releases every resource of h (after synchronising its stream).  NULL is
  * accepted.  Returns RRG_ECUDA if the stream reported an error. */
-int rrg_destroy(rrg_handle h);
+RRG_API int rrg_destroy(rrg_handle h);
 
-const char *rrg_last_error(rrg_handle h);
+RRG_API const char *rrg_last_error(rrg_handle h);
 
 /* Draws the N scenario sequences of one RG update on the device (Sec. II-C:
  * scenarios are redrawn at every RG time step; Alg. 3 step 2):
@@ -202,27 +212,27 @@ const char *rrg_last_error(rrg_handle h);
  * the binary64 value); the binary64 values are regenerated from the same
  * counters wherever they are needed (recheck, rrg_get_scenarios).
  * Asynchronous on the handle's stream. */
-int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index);
+RRG_API int rrg_sample_scenarios(rrg_handle h, uint64_t seed, uint64_t update_index);
 
 /* Copies the per-scenario parameter multipliers of the current scenarios,
  * m[k * RRG_NPARAM + p], to host m (N * RRG_NPARAM doubles; all 1 when
  * param_unc_rel = 0 or before the first draw).  Synchronous. */
-int rrg_get_param_multipliers(rrg_handle h, double *m);
+RRG_API int rrg_get_param_multipliers(rrg_handle h, double *m);
 
 /* Loads explicit multipliers m[k * RRG_NPARAM + p] (host, N * RRG_NPARAM
  * doubles, each finite and > 0; parameters outside param_unc_mask are used
  * as given too).  RRG_EINVAL unless the handle was created with
  * param_unc_rel > 0.  The next rrg_sample_scenarios overwrites them.
  * Synchronous. */
-int rrg_set_param_multipliers(rrg_handle h, const double *m);
+RRG_API int rrg_set_param_multipliers(rrg_handle h, const double *m);
 
 /* Loads explicit scenarios instead: d host, 3*H*N doubles (layout above).
  * The binary32 copy is the round-to-nearest of each value.  Synchronous. */
-int rrg_set_scenarios(rrg_handle h, const double *d);
+RRG_API int rrg_set_scenarios(rrg_handle h, const double *d);
 
 /* Copies the current scenarios (binary64, layout above, 3*H*N doubles) to the
  * host buffer d.  Synchronous. */
-int rrg_get_scenarios(rrg_handle h, double *d);
+RRG_API int rrg_get_scenarios(rrg_handle h, double *d);
 
 /* Evaluates m candidate kappas on the current scenarios (Alg. 3 parallel
  * steps 1-3 for given kappas, Eq. 5's P).  Host buffers:
@@ -238,7 +248,7 @@ int rrg_get_scenarios(rrg_handle h, double *d);
  *                         admissible for scenario k; when P is requested the
  *                         candidate-level early exit is not used
  * Synchronous. */
-int rrg_eval_candidates(rrg_handle h, const double *x_t, double v_prev, double r_t,
+RRG_API int rrg_eval_candidates(rrg_handle h, const double *x_t, double v_prev, double r_t,
                         const double *kappas, int m, uint8_t *admissible,
                         double *min_slack, uint8_t *P);
 
@@ -248,20 +258,20 @@ int rrg_eval_candidates(rrg_handle h, const double *x_t, double v_prev, double r
  * multiply-add), *kappa, *flags (bit 0: no evaluated candidate was admissible,
  * so kappa = 0 and v_t = v_prev; bit 1: inputs were rejected on the device).
  * Synchronous. */
-int rrg_step(rrg_handle h, const double *x_t, double r_t, double v_prev,
+RRG_API int rrg_step(rrg_handle h, const double *x_t, double r_t, double v_prev,
              double *v_t, double *kappa, int32_t *flags);
 
 /* Same as rrg_step with device pointers: d_x_t[3], *d_r_t, *d_v_prev in;
  * *d_v_t, *d_kappa, *d_flags out.  Asynchronous; nothing is copied to or from
  * the host, so it can be enqueued back to back or captured in a CUDA graph. */
-int rrg_step_dev(rrg_handle h, const double *d_x_t, const double *d_r_t,
+RRG_API int rrg_step_dev(rrg_handle h, const double *d_x_t, const double *d_r_t,
                  const double *d_v_prev, double *d_v_t, double *d_kappa,
                  int32_t *d_flags);
 
 /* Equilibrium of FC3 at constant setpoint v (Sec. II-A's equilibrium
  * manifold) and its output y_ss(v), in binary64 on the device.  Host out.
  * RRG_EINVAL if v is not positive and finite or no equilibrium is found. */
-int rrg_equilibrium(rrg_handle h, double v, double *x_eq, double *y_ss);
+RRG_API int rrg_equilibrium(rrg_handle h, double v, double *x_eq, double *y_ss);
 
 /* Closed loop of Fig. 1 with a simulated plant, T updates, all on the device:
  * for t = 0..T-1: sample scenarios (seed, t0 + t); RG update with r_seq[t];
@@ -274,7 +284,7 @@ int rrg_equilibrium(rrg_handle h, double v, double *x_eq, double *y_ss);
  *   use_graph: 1 replays one captured CUDA graph per update, 0 launches the
  *             kernels of each update directly.
  * Synchronous. */
-int rrg_closed_loop(rrg_handle h, const double *x0, double v0, const double *r_seq,
+RRG_API int rrg_closed_loop(rrg_handle h, const double *x0, double v0, const double *r_seq,
                     int T, uint64_t seed, uint64_t t0, const double *plant_amp,
                     int use_graph, double *v_out, double *kappa_out,
                     int32_t *flags_out, double *x_out);
@@ -286,14 +296,14 @@ int rrg_closed_loop(rrg_handle h, const double *x0, double v0, const double *r_s
  * it: state, v_{t-1} and the update counter t carry over, r_seq and the
  * outputs are indexed by that running t (so they must cover every update of
  * the run), and the scenarios of update t use update index t0 + t. */
-int rrg_closed_loop_dev(rrg_handle h, const double *x0, double v0, const double *d_r_seq,
+RRG_API int rrg_closed_loop_dev(rrg_handle h, const double *x0, double v0, const double *d_r_seq,
                         int T, uint64_t seed, uint64_t t0, const double *plant_amp,
                         int use_graph, double *d_v_out, double *d_kappa_out,
                         int32_t *d_flags_out, double *d_x_out);
 
 /* One plant step of the closed loop above with host buffers: x_next =
  * RK4(x_t, v_t) + d_plant(seed, t).  Synchronous. */
-int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, uint64_t t,
+RRG_API int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, uint64_t t,
                    const double *plant_amp, double *x_next);
 
 /* Shape of RRG_SEARCH_SPEC_BISECT: m tree nodes per round (1 .. max_candidates)
@@ -301,8 +311,8 @@ int rrg_plant_step(rrg_handle h, const double *x_t, double v_t, uint64_t seed, u
  * when the handle was created with probe_steps > 0).  The result is Alg. 1's
  * for every shape; only the time per update changes.  rrg_set_tuning waits
  * for the handle's stream; RRG_EINVAL for other searches or values. */
-int rrg_set_tuning(rrg_handle h, int m, int probe_steps);
-int rrg_get_tuning(rrg_handle h, int32_t *m, int32_t *probe_steps);
+RRG_API int rrg_set_tuning(rrg_handle h, int m, int probe_steps);
+RRG_API int rrg_get_tuning(rrg_handle h, int32_t *m, int32_t *probe_steps);
 
 /* Autotuner of RRG_SEARCH_SPEC_BISECT: on the current scenarios and the host
  * inputs x_t[3], r_t, v_prev, times 1 + repeats updates (CUDA events on the
@@ -311,7 +321,7 @@ int rrg_get_tuning(rrg_handle h, int32_t *m, int32_t *probe_steps);
  * handle has probe storage), keeps the fastest and returns it in *m_out,
  * *probe_out and its mean device time per update in *ms_out (each may be
  * NULL).  Synchronous; the cached closed-loop graph is discarded. */
-int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_prev, int repeats,
+RRG_API int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_prev, int repeats,
                  int32_t *m_out, int32_t *probe_out, double *ms_out);
 
 /* Gradient of the robust objective g(kappa) = min over scenarios k and steps
@@ -329,7 +339,7 @@ int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_prev, int
  * parameter layout), *k_star, *j_star.  Under parametric uncertainty
  * scenario k runs with theta_p m_p^k and dg/dtheta is with respect to the
  * nominal theta.  Synchronous. */
-int rrg_slack_gradient(rrg_handle h, const double *x_t, double v_prev, double r_t, double kappa,
+RRG_API int rrg_slack_gradient(rrg_handle h, const double *x_t, double v_prev, double r_t, double kappa,
                        int checkpoint, int precision, double *g, double *grad, int64_t *k_star,
                        int64_t *j_star);
 
@@ -344,18 +354,18 @@ int rrg_slack_gradient(rrg_handle h, const double *x_t, double v_prev, double r_
  * lo not admissible, hi admissible, or the bracket still wider than tol),
  * *iterations (gradient evaluations).  Needs max_candidates >= 2.
  * Synchronous. */
-int rrg_newton_search(rrg_handle h, const double *x_t, double r_t, double v_prev, double tol,
+RRG_API int rrg_newton_search(rrg_handle h, const double *x_t, double r_t, double v_prev, double tol,
                       int max_iter, int checkpoint, int precision, double *kappa, int32_t *flags,
                       int32_t *iterations);
 
 /* Profiling: while on, every rollout and recheck launch is bracketed by CUDA
  * events on the handle's stream and their durations are summed into
  * rrg_stats.rollout_ms / recheck_ms. */
-int rrg_set_profiling(rrg_handle h, int on);
+RRG_API int rrg_set_profiling(rrg_handle h, int on);
 
 /* Reads the counters (synchronises the handle's stream).  Host out. */
-int rrg_get_stats(rrg_handle h, rrg_stats *out);
-int rrg_reset_stats(rrg_handle h);
+RRG_API int rrg_get_stats(rrg_handle h, rrg_stats *out);
+RRG_API int rrg_reset_stats(rrg_handle h);
 
 /* ---- allocation-free candidate evaluation ---------------------------
  * The paper has no counterpart of this entry point.  It is for callers that
@@ -399,7 +409,7 @@ int rrg_reset_stats(rrg_handle h);
 #define RRG_STATIC_MAX_CANDIDATES 64
 #define RRG_STATIC_MAX_LANES 131072
 #define RRG_STATIC_SCRATCH_BYTES (2u << 20)
-int rrg_eval_candidates_static(const double *model_params, int n_params, const rrg_config *cfg,
+RRG_API int rrg_eval_candidates_static(const double *model_params, int n_params, const rrg_config *cfg,
                                void *cuda_stream, const double *d_scen64, const float *d_scen32,
                                const double *d_x_t, double v_prev, double r_t,
                                const double *d_kappas, int m, uint8_t *d_admissible,
@@ -409,7 +419,7 @@ int rrg_eval_candidates_static(const double *model_params, int n_params, const r
  * device (about 10 ms): binary32 FMA and binary64 FMA in TFLOP/s (an FMA
  * counted as 2 flops) and MUFU exp2 in Top/s; each output may be NULL.
  * Synchronous on the legacy default stream.  RRG_ECUDA / RRG_ENOMEM. */
-int rrg_alu_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_tops);
+RRG_API int rrg_alu_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_tops);
 
 /* ------------------------------------------------------------------------ */
 /* Batched instances: S independent robust RG problems (instance s with its
@@ -435,18 +445,18 @@ typedef struct rrg_batch_ctx *rrg_batch_handle;
  * and horizons: host arrays of n_instances values >= 1; sum over instances of
  * max_candidates * N_s must be below 2^31.  Allocates 12 sum(H_s N_s) bytes of
  * scenarios plus O(sum M N_s) bytes of recheck list. */
-int rrg_batch_create(const double *model_params, int n_params, const rrg_config *cfg,
+RRG_API int rrg_batch_create(const double *model_params, int n_params, const rrg_config *cfg,
                      int n_instances, const int32_t *n_scenarios, const int32_t *horizons,
                      void *cuda_stream, rrg_batch_handle *out);
-int rrg_batch_destroy(rrg_batch_handle h);
-const char *rrg_batch_last_error(rrg_batch_handle h);
+RRG_API int rrg_batch_destroy(rrg_batch_handle h);
+RRG_API const char *rrg_batch_last_error(rrg_batch_handle h);
 
 /* One update of every instance from device inputs: d_x[3 S] (instance s at
  * 3 s), d_r[S], d_v_prev[S]; draws the scenarios of update_index, searches,
  * and writes d_v_t[S], d_kappa[S], d_flags[S] (each may be NULL; flags as
  * rrg_step).  An instance with non-finite or non-positive inputs holds
  * (kappa 0, flag bit 1).  Asynchronous on the handle's stream. */
-int rrg_batch_step_dev(rrg_batch_handle h, const double *d_x, const double *d_r,
+RRG_API int rrg_batch_step_dev(rrg_batch_handle h, const double *d_x, const double *d_r,
                        const double *d_v_prev, uint64_t seed, uint64_t update_index,
                        double *d_v_t, double *d_kappa, int32_t *d_flags);
 
@@ -457,7 +467,7 @@ int rrg_batch_step_dev(rrg_batch_handle h, const double *d_x, const double *d_r,
  * [((t + 1) S + s) 3], the start at t = 0), each may be NULL.  use_graph: one
  * update is captured once and replayed (the graph is kept while pointers,
  * seed, t0 and the rollout variant stay the same).  Asynchronous. */
-int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double *d_x0, const double *d_v0,
+RRG_API int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double *d_x0, const double *d_v0,
                               const double *d_r_seq, int T, uint64_t seed, uint64_t t0,
                               const double *plant_amp, int use_graph, double *d_v_out,
                               double *d_kappa_out, int32_t *d_flags_out, double *d_x_out);
@@ -467,14 +477,14 @@ int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double *d_x0, const doub
  * returns it in *variant_out; ms_out (optional, RRG_BATCH_VARIANTS doubles)
  * receives each variant's mean rollout time per update.  Results do not
  * depend on the variant.  Synchronous. */
-int rrg_batch_autotune(rrg_batch_handle h, const double *d_x, const double *d_r,
+RRG_API int rrg_batch_autotune(rrg_batch_handle h, const double *d_x, const double *d_r,
                        const double *d_v_prev, uint64_t seed, uint64_t update_index, int repeats,
                        int *variant_out, double *ms_out);
-int rrg_batch_set_variant(rrg_batch_handle h, int variant);
-int rrg_batch_get_variant(rrg_batch_handle h, int *variant, int *tile_lanes, int *prefetch);
-int rrg_batch_set_profiling(rrg_batch_handle h, int on);
-int rrg_batch_get_stats(rrg_batch_handle h, rrg_stats *out);
-int rrg_batch_reset_stats(rrg_batch_handle h);
+RRG_API int rrg_batch_set_variant(rrg_batch_handle h, int variant);
+RRG_API int rrg_batch_get_variant(rrg_batch_handle h, int *variant, int *tile_lanes, int *prefetch);
+RRG_API int rrg_batch_set_profiling(rrg_batch_handle h, int on);
+RRG_API int rrg_batch_get_stats(rrg_batch_handle h, rrg_stats *out);
+RRG_API int rrg_batch_reset_stats(rrg_batch_handle h);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: the binary32 rollouts never meet subnormal values, and flushing
 # lets lg2/ex2/rcp issue as single MUFU operations on the critical path
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-              "--expt-relaxed-constexpr"]
+              "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

@@ -1105,6 +1105,7 @@ int rrg_batch_get_stats(rrg_batch_handle h, rrg_stats* out) {
   out->recheck_ms = 0.0;
   out->timed_rollouts = h->timed_rollouts;
   out->repairs = 0;
+  out->graph_conditional = 0;
   return RRG_OK;
 }
 

@@ -53,6 +53,7 @@ struct rrg_ctx {
   const void* cl_key[6] = {};
   uint64_t cl_key_seed = 0, cl_key_t0 = 0;
   uint64_t cl_per = 0, cl_rl_per = 0, cl_rd_per = 0;
+  bool cl_conditional = false;  // the cached graph uses a conditional node
   SearchState* st = nullptr;
   double* cand_kappa = nullptr;
   double* cand_v = nullptr;
@@ -275,9 +276,32 @@ int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit, b
 // The search of one RG update on already-sampled scenarios.  Each search
 // kernel decides on the device and names the slots the following prepare
 // launch sets up; the host only enqueues the fixed sequence.
+// The standard rounds that follow a pipelined pair (they finish the search,
+// after a wrong provisional outcome or when more levels remain; no-ops
+// otherwise).
+int enqueue_extra_rounds(rrg_ctx* h, double* d_vt, double* d_kappa, int32_t* d_flags) {
+  const Launch& L = h->L;
+  const SearchCfg& c = h->scfg;
+  const int extra = search_extra_rounds(c), wx = search_extra_width(c);
+  for (int r = 0; r < extra; ++r) {
+    CK(launch_prepare(L, wx));
+    h->launches++;
+    int rc = enqueue_round_work(h, L, wx, h->cfg.early_exit);
+    if (rc != RRG_OK) return rc;
+    CK(launch_search_next(L, d_vt, d_kappa, d_flags));
+    h->launches++;
+    h->rounds++;
+  }
+  return RRG_OK;
+}
+
+// with_extra = false: a pipelined search stops after the validating search
+// kernel (the caller enqueues enqueue_extra_rounds, e.g. in a conditional
+// graph node).
 int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
                    const unsigned long long* t_dev, const double* d_vp, double* d_vt,
-                   double* d_kappa, int32_t* d_flags, long long buf_base = -1) {
+                   double* d_kappa, int32_t* d_flags, long long buf_base = -1,
+                   bool with_extra = true) {
   const Launch& L = h->L;
   const SearchCfg& c = h->scfg;
   const int R = search_round_count(c);
@@ -303,17 +327,7 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
     h->rounds++;
     // after a wrong provisional outcome the search resumes from the level
     // where it went wrong; these rounds do nothing when it went right
-    const int extra = search_extra_rounds(c), wx = search_extra_width(c);
-    for (int r = 0; r < extra; ++r) {
-      CK(launch_prepare(L, wx));
-      h->launches++;
-      rc = enqueue_round_work(h, L, wx, h->cfg.early_exit);
-      if (rc != RRG_OK) return rc;
-      CK(launch_search_next(L, d_vt, d_kappa, d_flags));
-      h->launches++;
-      h->rounds++;
-    }
-    return RRG_OK;
+    return with_extra ? enqueue_extra_rounds(h, d_vt, d_kappa, d_flags) : RRG_OK;
   }
   for (int r = r0; r < R; ++r) {
     const int width = search_round_width(c, r);
@@ -331,6 +345,99 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
 }
 
 bool x_ok(const double* x) { return x && is_fin(x[0]) && is_fin(x[1]) && is_fin(x[2]); }
+
+// One closed-loop update as a graph with a conditional node around the rounds
+// that follow the pipelined pair; nullptr if any graph call fails (the stream
+// is left outside any capture).
+cudaGraph_t capture_conditional_update(rrg_ctx* h, uint64_t seed, uint64_t t0, const double* amp,
+                                       const double* d_r_seq, double* d_v_out, double* d_kappa_out,
+                                       int32_t* d_flags_out, double* d_x_out) {
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) return nullptr;
+  bool ok = true;
+  auto end_capture = [&]() {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(h->stream, &g);
+    }
+    cudaGetLastError();
+  };
+  cudaGraphConditionalHandle hc = 0;
+  ok = cudaGraphConditionalHandleCreate(&hc, G, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+  std::vector<cudaGraphNode_t> sinks;
+  // part 1: draw of update t + 1 (side stream), the search up to the kernel
+  // that validates the pipelined pair, the join
+  if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, G, nullptr, nullptr, 0, mode) == cudaSuccess;
+  if (ok) {
+    const Launch& L = h->L;
+    h->capturing = true;
+    h->L.cond = hc;
+    ok = cudaEventRecord(h->ev_fork, h->stream) == cudaSuccess &&
+         cudaStreamWaitEvent(h->side, h->ev_fork, 0) == cudaSuccess &&
+         launch_sample(L, seed, t0 + 1, &h->loop->t, h->cfg.dist_amp, true, h->side) == cudaSuccess &&
+         cudaEventRecord(h->ev_join, h->side) == cudaSuccess;
+    if (ok)
+      ok = enqueue_search(h, h->loop->x, d_r_seq, &h->loop->t, &h->loop->v_prev, nullptr, nullptr,
+                          nullptr, static_cast<long long>(t0), false) == RRG_OK;
+    h->L.cond = 0ull;
+    if (ok) ok = cudaStreamWaitEvent(h->stream, h->ev_join, 0) == cudaSuccess;
+    if (ok) {
+      cudaStreamCaptureStatus st;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      ok = cudaStreamGetCaptureInfo(h->stream, &st, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+           nd > 0;
+      if (ok) sinks.assign(deps, deps + nd);
+    }
+    cudaGraph_t g1 = nullptr;
+    ok = (cudaStreamEndCapture(h->stream, &g1) == cudaSuccess) && ok;
+  }
+  // part 2: the conditional node and its body (the remaining rounds)
+  cudaGraphNode_t cn = nullptr;
+  if (ok) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&cn, G, sinks.data(), nullptr, sinks.size(), &cp) == cudaSuccess;
+    cudaGraph_t body = ok ? cp.conditional.phGraph_out[0] : nullptr;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, mode) == cudaSuccess;
+    if (ok) {
+      ok = enqueue_extra_rounds(h, nullptr, nullptr, nullptr) == RRG_OK;
+      ok = (cudaStreamEndCapture(h->stream, &body) == cudaSuccess) && ok;
+    }
+  }
+  // part 3: plant step and loop bookkeeping, after the conditional node
+  if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, G, &cn, nullptr, 1, mode) == cudaSuccess;
+  if (ok) {
+    ok = launch_loop_end(h->L, h->loop, seed, t0, amp, d_v_out, d_kappa_out, d_flags_out, d_x_out) ==
+         cudaSuccess;
+    cudaGraph_t g3 = nullptr;
+    ok = (cudaStreamEndCapture(h->stream, &g3) == cudaSuccess) && ok;
+  }
+  h->capturing = false;
+  if (!ok) {
+    end_capture();
+    cudaGraphDestroy(G);
+    return nullptr;
+  }
+  return G;
+}
+
+// Host counters of one plain update, without enqueueing anything (the graph
+// replays of a conditional capture are counted as plain updates).
+void enqueue_count_only(rrg_ctx* h) {
+  const uint64_t extra = static_cast<uint64_t>(search_extra_rounds(h->scfg));
+  const uint64_t rec = h->cfg.precision == RRG_FP32_RECHECK ? 1 : 0;
+  // sample; begin, prepare; probe rollout; mid, prepare; rollout (+ recheck);
+  // next; per extra round prepare, rollout (+ recheck), next; loop end
+  h->launches += 1 + 2 + 1 + 2 + (1 + rec) + 1 + extra * (3 + rec) + 1;
+  h->rollout_launches += 2 + extra;
+  h->rounds += 1 + extra;
+}
 
 }  // namespace
 
@@ -741,13 +848,34 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
     }
     const uint64_t launches0 = h->launches, rl0 = h->rollout_launches, rounds0 = h->rounds;
     cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    h->capturing = true;
-    int rc = enqueue_update();
-    h->capturing = false;
-    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
-    if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-    if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    // A pipelined search rarely needs the rounds after its pipelined pair:
+    // they go into a conditional node that runs only when the validating
+    // search kernel reports the search unfinished.  Falls back to the plain
+    // capture (rounds always enqueued, no-ops when done) if the graph API
+    // refuses any step.
+    if (search_pipelined(h->scfg, h->cfg.horizon)) {
+      graph = capture_conditional_update(h, seed, t0, amp, d_r_seq, d_v_out, d_kappa_out,
+                                         d_flags_out, d_x_out);
+      h->launches = launches0;
+      h->rollout_launches = rl0;
+      h->rounds = rounds0;
+    }
+    int rc = RRG_OK;
+    cudaError_t ce = cudaSuccess;
+    h->cl_conditional = graph != nullptr;
+    if (!graph) {
+      CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      h->capturing = true;
+      rc = enqueue_update();
+      h->capturing = false;
+      ce = cudaStreamEndCapture(h->stream, &graph);
+      if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+      if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    } else {
+      // count one update as the plain capture would (the conditional rounds
+      // included)
+      enqueue_count_only(h);
+    }
     ce = cudaGraphInstantiate(&h->cl_exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
@@ -1063,6 +1191,7 @@ int rrg_get_stats(rrg_handle h, rrg_stats* out) {
   out->recheck_ms = h->recheck_ms;
   out->timed_rollouts = h->timed_rollouts;
   out->repairs = ds.repairs;
+  out->graph_conditional = h->cl_exec != nullptr && h->cl_conditional ? 1 : 0;
   return RRG_OK;
 }
 

@@ -123,6 +123,10 @@ struct Launch {
   cudaStream_t stream;
   int N, H, precision, early_exit, m_cap;
   int scen_gen;                 // disturbances drawn inside the trajectory loop
+  // conditional-node handle of a captured closed-loop update (0: none); the
+  // search kernel that validates the pipelined rounds sets it to "the search
+  // is not finished", which runs the remaining rounds
+  unsigned long long cond;
   double dt, y_min, eps_abs;
   SearchCfg scfg;
   const double* params;         // [RRG_NPARAM] (device)

@@ -792,6 +792,7 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
     set_segments(s, SEG_FULL, m, 0, SEG_FULL, 0, 0);
     s->prep_base = 0;
     s->prep_m = m;
+    if (L.cond != 0ull) cudaGraphSetConditional(L.cond, s->done ? 0u : 1u);
   }
   __syncthreads();
   build_tree_block(L);

@@ -49,6 +49,7 @@ class RrgStats(ctypes.Structure):
         ("launches", _u64), ("rollout_launches", _u64), ("lane_steps", _u64),
         ("lane_steps_fp64", _u64), ("rechecked", _u64), ("rounds", _u64),
         ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64), ("repairs", _u64),
+        ("graph_conditional", _u64),
     ]
 
 

@@ -536,3 +536,27 @@ def test_alu_peaks_are_plausible(R):
     assert 20.0 < f32 < 100.0
     assert 0.05 < f64 < f32 / 8
     assert 0.5 < mufu < f32
+
+
+@pytest.mark.parametrize("m,probe", [(4, 1), (64, 1), (64, 32)])
+def test_closed_loop_graph_runs_remaining_rounds_when_needed(R, orc, params, m, probe):
+    """In the replayed graph the rounds after the pipelined pair sit in a
+    conditional node that runs only when the search is unfinished (a wrong
+    provisional outcome, or more levels than the pair covers, as with 4
+    candidates per round): the kappas equal direct launches and the oracle."""
+    N, H, T = 24, 150, 6
+    r_seq = inputs.staircase(T, 3, 2, seed=12)
+    x0 = orc.equilibrium(params, 100.0) * np.array([1.0, 1.04, 1.02])
+    amp = inputs.DIST_AMP
+    cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=R.FP32_RECHECK, max_candidates=m,
+               probe_steps=probe, recheck_eps_rel=SLACK32_TOL / 1.9)
+    runs = []
+    for use_graph in (False, True):
+        with R.Governor(params, cfg) as g:
+            runs.append(g.closed_loop(x0, 100.0, r_seq, 2, 0, amp, use_graph=use_graph))
+            assert g.stats()["graph_conditional"] == (1 if use_graph else 0)
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
+    vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 100.0, r_seq, 2, 0, amp, amp, search=0)
+    np.testing.assert_array_equal(runs[1][1], ko)
+    np.testing.assert_array_equal(runs[1][2], fo)
