@@ -59,14 +59,15 @@ SWEEP_N = (1024, 2048, 4096, 8192, 16384, 32768, 65536)
 SWEEP_H, SWEEP_M, SWEEP_ROUNDS = 5000, 16, 3
 SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # DRAM bytes per rollout launch on this workload (ncu, one update's four
-# launches: probe, continuation + round 2, two no-op repair rounds; see
+# launches with the tuned shape 64 nodes / 32-step probe: probe, continuation
+# + round 2, two no-op rounds; see
 # profiles/rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the
 # kernel sources are the ones profiled
-TRAFFIC_PER_LAUNCH = (1617664 + 24646144 + 42496 + 42752) / 4
-TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "4fc619da47237c45cdab79654cb851d6da93f86f",
-                   "paper_2510_08288_gb300/csrc/rrg_lane.cuh": "77b956b64a67abeb3b3de7c38fd5f61f4c2220b6",
-                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "bfaf5a435b60a0eb8f6de7c7d9617ed57800b46c",
-                   "paper_2510_08288_gb300/csrc/rrg_internal.h": "bbc7629f085d6f826bf56f6bd175be49719d285e"}
+TRAFFIC_PER_LAUNCH = (438528 + 24622080 + 42752 + 42240) / 4
+TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "82628d1a7ddb1cbafe12103933c61cf025a7859b",
+                   "paper_2510_08288_gb300/csrc/rrg_lane.cuh": "315bfe6ec7bf6aebeb06fd37f76e0663c1f81883",
+                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "e931684eb6efbaa49158a781f8c212529bec96b5",
+                   "paper_2510_08288_gb300/csrc/rrg_internal.h": "7391646724a2d88938a2912be79a995da2629de4"}
 
 
 def measured_traffic():
@@ -93,6 +94,8 @@ def parse():
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
                     help="steps of the probe that pipelines the first two bisection rounds (0: off)")
+    ap.add_argument("--shape", type=str, default=None,
+                    help="closed loop: 'm,probe' sets the speculative bisection's shape instead of autotuning it")
     ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch", "single", "adjoint"),
                     default="closed_loop")
     ap.add_argument("--instances", type=int, default=BATCH_S, help="batch: number of RG instances")
@@ -103,14 +106,14 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND):
+def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, given=False):
     return {
         "workload": "closed-loop robust RG on FC3: N_sim=%d scenarios, horizon %d RK4 steps "
                     "(dt=0.01 s), staircase r (8 levels over 50..300 A, seed 1, 125 updates/level), "
                     "timed updates [%d, %d) of the 1000-update run" % (N, H, W, W + K),
         "search": "speculative bisection (Alg. 1 result), N_kappa=12, %d candidates/round, "
-                  "first two rounds pipelined after a %d-step probe (0: not pipelined); shape chosen by "
-                  "rrg_autotune on update 0" % (m, probe),
+                  "first two rounds pipelined after a %d-step probe (0: not pipelined); shape %s"
+                  % (m, probe, "given" if given else "chosen by rrg_autotune on update 0"),
         "kappa_tol": 2.0 ** -11,
         "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
         "l2": "256 MB written between timed steps",
@@ -289,8 +292,12 @@ def run_gpu(args):
     x0, _ = g.equilibrium(V0)
     # the speculative bisection's shape (tree width, probe length) by the
     # library's autotuner on the first update; every shape gives Alg. 1's kappa
-    g.sample_scenarios(seed, 0)
-    tune_m, tune_probe, tune_ms = g.autotune(x0, r_seq[0], V0, repeats=2)
+    if args.shape:
+        tune_m, tune_probe = (int(v) for v in args.shape.split(","))
+        g.set_tuning(tune_m, tune_probe)
+    else:
+        g.sample_scenarios(seed, 0)
+        tune_m, tune_probe, tune_ms = g.autotune(x0, r_seq[0], V0, repeats=2)
     dev = torch.device("cuda", local)
     d_r = torch.tensor(r_seq, dtype=torch.float64, device=dev)
     d_v = torch.zeros(T, dtype=torch.float64, device=dev)
@@ -432,7 +439,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(W, K, NS, HZ, tune_probe, tune_m),
+            "config": workload_config(W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
