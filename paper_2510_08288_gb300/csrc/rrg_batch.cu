@@ -460,14 +460,14 @@ batch_plant_kernel(const BLaunch B, uint64_t seed, uint64_t base, const double* 
   if (s < B.c.S) {
     BState& st = B.st[s];
     const double v = st.v_out;
-    const double p_atm = B.params[P_P_ATM];
-    double q_ca = st.x[0] - p_atm, w = st.x[1], q_sm = st.x[2] - p_atm;
-    const CandK<double> C = cand_consts(B.params, v);
-    rk4_step<double>(B.k64, C, B.c.dt, q_ca, w, q_sm);
     const U64x4 r = philox4x64_10(0ull, 0ull, base + t, 1ull, seed + static_cast<uint64_t>(s), 0ull);
-    st.lx[0] = (q_ca + p_atm) + uniform_sym(r.w[0], amp[0]);
-    st.lx[1] = w + uniform_sym(r.w[1], amp[1]);
-    st.lx[2] = (q_sm + p_atm) + uniform_sym(r.w[2], amp[2]);
+    const double x[3] = {st.x[0], st.x[1], st.x[2]};
+    double xn[3];
+    plant_step_fast(B.k64, B.u64, B.params, B.c.dt, v, x, uniform_sym(r.w[0], amp[0]),
+                    uniform_sym(r.w[1], amp[1]), uniform_sym(r.w[2], amp[2]), xn);
+    st.lx[0] = xn[0];
+    st.lx[1] = xn[1];
+    st.lx[2] = xn[2];
     st.lv = v;
     if (x_out) {
       double* xo = x_out + ((t + 1) * static_cast<unsigned long long>(B.c.S) + s) * 3;

@@ -20,6 +20,7 @@ thread_local std::string g_create_error;
 
 struct rrg_ctx {
   int device = 0;
+  int sms = 152;                // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   rrg_config cfg{};
@@ -224,7 +225,8 @@ void fill_launch(rrg_ctx* h) {
   L.recheck_count = h->recheck_count;
   L.stats = h->stats;
   L.P = nullptr;
-  L.recheck_blocks = 2 * 152;
+  L.sms = h->sms;
+  L.recheck_blocks = 2 * h->sms;
   L.probe_steps = h->scfg.probe_steps;
   L.lane_state = h->lane_state;
   L.pmul = h->pmul;
@@ -274,8 +276,9 @@ int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit, b
 }
 
 // The search of one RG update on already-sampled scenarios.  Each search
-// kernel decides on the device and names the slots the following prepare
-// launch sets up; the host only enqueues the fixed sequence.
+// kernel decides on the device, sets up the next round's candidates (kappas,
+// constants, steady-state check) and the slots the following rollout runs;
+// the host only enqueues the fixed sequence.
 // The standard rounds that follow a pipelined pair (they finish the search,
 // after a wrong provisional outcome or when more levels remain; no-ops
 // otherwise).
@@ -284,8 +287,6 @@ int enqueue_extra_rounds(rrg_ctx* h, double* d_vt, double* d_kappa, int32_t* d_f
   const SearchCfg& c = h->scfg;
   const int extra = search_extra_rounds(c), wx = search_extra_width(c);
   for (int r = 0; r < extra; ++r) {
-    CK(launch_prepare(L, wx));
-    h->launches++;
     int rc = enqueue_round_work(h, L, wx, h->cfg.early_exit);
     if (rc != RRG_OK) return rc;
     CK(launch_search_next(L, d_vt, d_kappa, d_flags));
@@ -305,9 +306,9 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
   const Launch& L = h->L;
   const SearchCfg& c = h->scfg;
   const int R = search_round_count(c);
+  // every search kernel also prepares the candidates of the round it sets up
   CK(launch_search_begin(L, d_x, d_r, t_dev, d_vp, buf_base));
-  CK(launch_prepare(L, search_round_width(c, 0)));
-  h->launches += 2;
+  h->launches++;
   int r0 = 0;
   const bool pipe = search_pipelined(c, h->cfg.horizon);
   if (pipe) {
@@ -317,8 +318,7 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
     int rc = enqueue_round_work(h, L, w0, h->cfg.early_exit, false);
     if (rc != RRG_OK) return rc;
     CK(launch_search_mid(L));
-    CK(launch_prepare(L, w1));
-    h->launches += 2;
+    h->launches++;
     // rows: the <= 11 path nodes of round 1 that continue, then round 2
     rc = enqueue_round_work(h, L, (w0 < 11 ? w0 : 11) + w1, h->cfg.early_exit);
     if (rc != RRG_OK) return rc;
@@ -335,16 +335,22 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
     if (rc != RRG_OK) return rc;
     CK(launch_search_next(L, d_vt, d_kappa, d_flags));
     h->launches++;
-    if (r + 1 < R) {
-      CK(launch_prepare(L, search_round_width(c, r + 1)));
-      h->launches++;
-    }
     h->rounds++;
   }
   return RRG_OK;
 }
 
 bool x_ok(const double* x) { return x && is_fin(x[0]) && is_fin(x[1]) && is_fin(x[2]); }
+
+// Launches, rollout launches and rounds of the rounds after a pipelined
+// pair: per round rollout (+ recheck), next.
+void extra_round_counts(const rrg_ctx* h, uint32_t* launches, uint32_t* rollouts, uint32_t* rounds) {
+  const uint32_t extra = static_cast<uint32_t>(search_extra_rounds(h->scfg));
+  const uint32_t rec = h->cfg.precision == RRG_FP32_RECHECK ? 1u : 0u;
+  *launches = extra * (2u + rec);
+  *rollouts = extra;
+  *rounds = extra;
+}
 
 // One closed-loop update as a graph with a conditional node around the rounds
 // that follow the pipelined pair; nullptr if any graph call fails (the stream
@@ -374,6 +380,7 @@ cudaGraph_t capture_conditional_update(rrg_ctx* h, uint64_t seed, uint64_t t0, c
     const Launch& L = h->L;
     h->capturing = true;
     h->L.cond = hc;
+    extra_round_counts(h, &h->L.cond_launches, &h->L.cond_rollouts, &h->L.cond_rounds);
     ok = cudaEventRecord(h->ev_fork, h->stream) == cudaSuccess &&
          cudaStreamWaitEvent(h->side, h->ev_fork, 0) == cudaSuccess &&
          launch_sample(L, seed, t0 + 1, &h->loop->t, h->cfg.dist_amp, true, h->side) == cudaSuccess &&
@@ -427,16 +434,15 @@ cudaGraph_t capture_conditional_update(rrg_ctx* h, uint64_t seed, uint64_t t0, c
   return G;
 }
 
-// Host counters of one plain update, without enqueueing anything (the graph
-// replays of a conditional capture are counted as plain updates).
+// Host counters of the unconditional part of one captured update (sample;
+// begin; probe rollout; mid; rollout (+ recheck); next; loop end), without
+// enqueueing anything.  Runs of the conditional body are counted on the
+// device by the kernel that opens it.
 void enqueue_count_only(rrg_ctx* h) {
-  const uint64_t extra = static_cast<uint64_t>(search_extra_rounds(h->scfg));
   const uint64_t rec = h->cfg.precision == RRG_FP32_RECHECK ? 1 : 0;
-  // sample; begin, prepare; probe rollout; mid, prepare; rollout (+ recheck);
-  // next; per extra round prepare, rollout (+ recheck), next; loop end
-  h->launches += 1 + 2 + 1 + 2 + (1 + rec) + 1 + extra * (3 + rec) + 1;
-  h->rollout_launches += 2 + extra;
-  h->rounds += 1 + extra;
+  h->launches += 1 + 1 + 1 + 1 + (1 + rec) + 1 + 1;
+  h->rollout_launches += 2;
+  h->rounds += 1;
 }
 
 }  // namespace
@@ -487,6 +493,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   h->cfg = *cfg;
   std::memcpy(h->params, model_params, sizeof h->params);
   cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) {
     if (cuda_stream) {
       h->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -645,7 +652,7 @@ int rrg_get_scenarios(rrg_handle h, double* d) {
   DeviceGuard g(h->device);
   const size_t n = 3 * static_cast<size_t>(h->cfg.horizon) * h->cfg.n_scenarios;
   CK(launch_materialize64(h->L));
-  h->launches++;
+  h->launches += 2;
   CK(cudaMemcpyAsync(d, h->d64, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return RRG_OK;
@@ -872,8 +879,6 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
       if (rc != RRG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
       if (ce != cudaSuccess) return set_err(h, RRG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
     } else {
-      // count one update as the plain capture would (the conditional rounds
-      // included)
       enqueue_count_only(h);
     }
     ce = cudaGraphInstantiate(&h->cl_exec, graph, 0);
@@ -977,7 +982,7 @@ int rrg_slack_gradient(rrg_handle h, const double* x_t, double v_prev, double r_
   CK(launch_adjoint(h->L, precision == RRG_FP64, h->io_dev + IO_X, v_prev, r_t, kappa, checkpoint,
                     h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
                     reinterpret_cast<long long*>(h->adj_out + 1), h->adj_out + 3));
-  h->launches += 4;
+  h->launches += 5;
   double out[3 + 4 + RRG_NPARAM];
   CK(cudaMemcpyAsync(out, h->adj_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1181,12 +1186,12 @@ int rrg_get_stats(rrg_handle h, rrg_stats* out) {
     h->ev_free.push_back(pr.second);
   }
   h->ev_rec.clear();
-  out->launches = h->launches;
-  out->rollout_launches = h->rollout_launches;
+  out->launches = h->launches + ds.cond_launches;
+  out->rollout_launches = h->rollout_launches + ds.cond_rollouts;
   out->lane_steps = ds.lane_steps;
   out->lane_steps_fp64 = ds.lane_steps_fp64;
   out->rechecked = ds.rechecked;
-  out->rounds = h->rounds;
+  out->rounds = h->rounds + ds.cond_rounds;
   out->rollout_ms = h->rollout_ms;
   out->recheck_ms = h->recheck_ms;
   out->timed_rollouts = h->timed_rollouts;

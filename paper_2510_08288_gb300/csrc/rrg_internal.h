@@ -98,6 +98,9 @@ struct DevStats {
   unsigned long long lane_steps_fp64;
   unsigned long long rechecked;
   unsigned long long repairs;   // probed rounds whose provisional outcome was wrong
+  // kernels, rollout launches and search rounds run by the conditional body
+  // of a captured closed-loop update (counted by the kernel that opens it)
+  unsigned long long cond_launches, cond_rollouts, cond_rounds;
 };
 
 // Closed-loop device state.
@@ -127,6 +130,7 @@ struct Launch {
   // search kernel that validates the pipelined rounds sets it to "the search
   // is not finished", which runs the remaining rounds
   unsigned long long cond;
+  uint32_t cond_launches, cond_rollouts, cond_rounds;  // what one run of that body launches
   double dt, y_min, eps_abs;
   SearchCfg scfg;
   const double* params;         // [RRG_NPARAM] (device)
@@ -153,6 +157,7 @@ struct Launch {
   DevStats* stats;
   uint8_t* P;                   // optional
   int recheck_blocks;
+  int sms;                      // streaming multiprocessors of the device
   int probe_steps;              // steps of a SEG_PROBE segment
   void* lane_state;             // LaneState<T>[m_cap * N] for probed rounds
   // parametric uncertainty: per-scenario parameter multipliers m[k * NPARAM

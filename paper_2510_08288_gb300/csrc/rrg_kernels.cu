@@ -136,7 +136,12 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
                           cudaStream_t stream) {
   const size_t n = static_cast<size_t>(L.H) * L.N;
   const int write64 = L.precision == RRG_FP64 ? 1 : 0;
-  sample_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, stream ? stream : L.stream>>>(
+  // Full width also for the next closed-loop update's draw on the side
+  // stream: it then finishes while the search's short kernels run.  (One
+  // block per SM stretched it over the long rollout and slowed the update by
+  // 7 %; stream priorities changed nothing, measured on GB300.)
+  const int sms = L.sms > 0 ? L.sms : 152;
+  sample_kernel<<<grid_for(n, 256, sms * 16), 256, 0, stream ? stream : L.stream>>>(
       L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
       amp[0], amp[1], amp[2], write64, L.scen_gen, L.st, L.pmul, dual ? L.pmulb : nullptr, L.punc_rho,
       L.punc_mask);
@@ -171,9 +176,14 @@ __global__ void materialize64_kernel(double* __restrict__ d64, int N, int H,
   }
 }
 
+// Marks pair 0's binary64 array valid once every block of the fill is done
+// (a separate launch: a block of the fill itself could not know that).
+__global__ void mark64_kernel(SearchState* st) { st->src[0].d64_valid = 1; }
+
 cudaError_t launch_materialize64(const Launch& L) {
   const size_t n = static_cast<size_t>(L.H) * L.N;
   materialize64_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.N, L.H, L.st);
+  mark64_kernel<<<1, 1, 0, L.stream>>>(L.st);
   return cudaGetLastError();
 }
 
@@ -660,6 +670,17 @@ __global__ void __launch_bounds__(32) prepare_kernel(const Launch L) {
   if (static_cast<int>(blockIdx.x) < s->prep_m) prepare_slot(L, s->prep_base + blockIdx.x);
 }
 
+// The same inside a search kernel, one thread per slot of the round it just
+// set up (after build_tree_block has written the round's kappas): the
+// closed loop's critical path then has no separate prepare launch.
+__device__ void prepare_block(const Launch& L) {
+  __syncthreads();
+  const SearchState* s = L.st;
+  if (threadIdx.x == 0) *L.recheck_count = 0u;
+  const int base = s->prep_base, m = s->prep_m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) prepare_slot(L, base + i);
+}
+
 cudaError_t launch_prepare(const Launch& L, int width) {
   prepare_kernel<<<width > 0 ? width : 1, 32, 0, L.stream>>>(L);
   return cudaGetLastError();
@@ -711,6 +732,7 @@ search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double
   }
   __syncthreads();
   build_tree_block(L);
+  prepare_block(L);
 }
 
 // Between the probe of round 1 and the launch that finishes it: walk round
@@ -749,6 +771,7 @@ search_mid_kernel(const Launch L) {
   }
   __syncthreads();
   build_tree_block(L);
+  prepare_block(L);
 }
 
 __global__ void __launch_bounds__(kSearchThreads)
@@ -792,10 +815,18 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
     set_segments(s, SEG_FULL, m, 0, SEG_FULL, 0, 0);
     s->prep_base = 0;
     s->prep_m = m;
-    if (L.cond != 0ull) cudaGraphSetConditional(L.cond, s->done ? 0u : 1u);
+    if (L.cond != 0ull) {
+      cudaGraphSetConditional(L.cond, s->done ? 0u : 1u);
+      if (!s->done) {
+        L.stats->cond_launches += L.cond_launches;
+        L.stats->cond_rollouts += L.cond_rollouts;
+        L.stats->cond_rounds += L.cond_rounds;
+      }
+    }
   }
   __syncthreads();
   build_tree_block(L);
+  prepare_block(L);
 }
 
 cudaError_t launch_search_begin(const Launch& L, const double* d_x, const double* d_r,
@@ -862,15 +893,9 @@ cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d
 // Simulated plant of the closed loop (Fig. 1) and the loop bookkeeping.
 __device__ void plant_step(const Launch& L, const double* x, double v, uint64_t seed, uint64_t upd,
                            const double* amp, double* x_next) {
-  const Fc3K<double>& K = L.k64;
-  const CandK<double> C = cand_consts(L.params, v);
-  const double p_atm = L.params[P_P_ATM];
-  double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm;
-  rk4_step<double>(K, C, L.dt, q_ca, w, q_sm);
   const U64x4 r = philox4x64_10(0ull, 0ull, upd, 1ull, seed, 0ull);
-  x_next[0] = (q_ca + p_atm) + uniform_sym(r.w[0], amp[0]);
-  x_next[1] = w + uniform_sym(r.w[1], amp[1]);
-  x_next[2] = (q_sm + p_atm) + uniform_sym(r.w[2], amp[2]);
+  plant_step_fast(L.k64, L.u64, L.params, L.dt, v, x, uniform_sym(r.w[0], amp[0]),
+                  uniform_sym(r.w[1], amp[1]), uniform_sym(r.w[2], amp[2]), x_next);
 }
 
 __global__ void plant_kernel(const Launch L, const double* d_x, const double* d_v, uint64_t seed,

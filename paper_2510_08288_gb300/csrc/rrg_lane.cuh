@@ -414,4 +414,25 @@ __device__ __forceinline__ int interior_points(double* cand_kappa, int M, double
   return M;
 }
 
+// ---------------------------------------------------------------------------
+// One step of the simulated plant at setpoint v (Fig. 1): x_{t+1} =
+// RK4(x_t, v) + (e_ca, e_w, e_sm), the plant's own draw added after the step
+// as in Eq. 4.  Binary64, with the rollouts' multiplied-out right-hand side
+// and x^e - 1 series: the plant step sits on the closed loop's critical path,
+// and a binary64 pow() costs thousands of cycles on GB300.
+__device__ __forceinline__ void plant_step_fast(const Fc3K<double>& K, const RhsU<double>& U,
+                                                const double* __restrict__ P, double dt, double v,
+                                                const double x[3], double e_ca, double e_w,
+                                                double e_sm, double x_next[3]) {
+  RhsC<double> c64;
+  RhsC<float> c32;
+  fold_rhs_cand(K, cand_consts(P, v), &c64, &c32);
+  const double p_atm = P[P_P_ATM];
+  double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm;
+  rk4_step_fast<double>(U, c64, dt, q_ca, w, q_sm, e_ca, e_w, e_sm);
+  x_next[0] = q_ca + p_atm;
+  x_next[1] = w;
+  x_next[2] = q_sm + p_atm;
+}
+
 }  // namespace rrg

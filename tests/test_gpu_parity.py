@@ -550,13 +550,29 @@ def test_closed_loop_graph_runs_remaining_rounds_when_needed(R, orc, params, m, 
     amp = inputs.DIST_AMP
     cfg = _cfg(R, N, H, search=R.SEARCH_SPEC_BISECT, precision=R.FP32_RECHECK, max_candidates=m,
                probe_steps=probe, recheck_eps_rel=SLACK32_TOL / 1.9)
-    runs = []
+    runs, stats = [], []
     for use_graph in (False, True):
         with R.Governor(params, cfg) as g:
             runs.append(g.closed_loop(x0, 100.0, r_seq, 2, 0, amp, use_graph=use_graph))
-            assert g.stats()["graph_conditional"] == (1 if use_graph else 0)
+            stats.append(g.stats())
+            assert stats[-1]["graph_conditional"] == (1 if use_graph else 0)
     for a, b in zip(*runs):
         np.testing.assert_array_equal(a, b)
+    # launch counts: direct launches enqueue every round of every update (the
+    # pair, then `extra` rounds that are no-ops once the search is done); the
+    # replays count the conditional body's rounds only on the updates where
+    # it ran (rollout + recheck + search kernel per round)
+    direct, graph = stats
+    extra = direct["rounds"] // T - 1
+    assert extra >= 1 and direct["rounds"] == T * (1 + extra)
+    assert (graph["rounds"] - T) % extra == 0
+    body_runs = (graph["rounds"] - T) // extra
+    assert 0 <= body_runs <= T
+    skipped = T - body_runs
+    assert graph["rollout_launches"] == direct["rollout_launches"] - skipped * extra
+    assert graph["launches"] == direct["launches"] - skipped * extra * 3
+    if m == 4:      # the pair covers 5 of the 12 levels: unfinished unless kappa = 1 passes
+        assert body_runs >= 1
     vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 100.0, r_seq, 2, 0, amp, amp, search=0)
     np.testing.assert_array_equal(runs[1][1], ko)
     np.testing.assert_array_equal(runs[1][2], fo)
