@@ -8,11 +8,15 @@ level.  One benchmark step is one closed-loop update: redraw the scenarios,
 run the robust RG search (speculative bisection, N_kappa = 12, binary32
 rollouts with a binary64 recheck of near-zero slacks), move the simulated
 plant one step.  W warm-up updates run first; the K timed updates are the
-next K of the same run.
+next K of the same run, each a replay of the library's one-update CUDA graph
+(rrg_closed_loop_dev with the graph on; the rounds after the pipelined pair
+sit in a conditional node).
 
 Printed (rank 0): one JSON line.  value = RG updates/s over all ranks, device
 time (CUDA events on the library's stream, inputs resident in HBM, L2 flushed
-between timed steps).  e2e = the same through the host-buffer C-ABI calls
+between timed steps).  direct_launches = the same K updates with every kernel
+launched directly; its CUDA events around each rollout launch give the
+roofline's kernel duration.  e2e = the same through the host-buffer C-ABI calls
 (rrg_sample_scenarios + rrg_step + rrg_plant_step, host copies included).
 roofline = the binary32 rollout kernel's achieved FP32 rate vs the FP32 FMA
 peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz.  cpu_baseline = the
@@ -117,36 +121,69 @@ def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, give
         "kappa_tol": 2.0 ** -11,
         "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
         "l2": "256 MB written between timed steps",
+        "launch": "one CUDA graph replay per update (rrg_closed_loop_dev, graph on)",
     }
 
 
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
+    """nvidia-smi's SM clock and throttle reasons every PERIOD_MS, read by a
+    thread that stamps each line with the host clock.  begin()/end() bracket
+    a timed region (host times taken after a device synchronize, so the
+    region's kernels ran between them); stop() keeps the samples inside the
+    regions widened by one period on each side, so that a region shorter than
+    the period still gets the samples that bracket it."""
+    PERIOD_MS = 100
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index=None):
-        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        import threading
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", str(self.PERIOD_MS)]
         if gpu_index is not None:
             cmd += ["-i", str(gpu_index)]
+        self.lines, self.windows, self._t0 = [], [], None
+        self._first = threading.Event()
         try:
             self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+        self._first.wait(5.0)               # nvidia-smi is up before any region starts
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append((time.monotonic(), line))
+            self._first.set()
+
+    def begin(self):
+        self._t0 = time.monotonic()
+
+    def end(self):
+        if self._t0 is not None:
+            self.windows.append((self._t0, time.monotonic()))
+            self._t0 = None
 
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
         try:
-            out, _ = self.p.communicate(timeout=5)
+            self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-            out, _ = self.p.communicate()
+            self.p.wait()
+        self.th.join(timeout=5)
+        pad = self.PERIOD_MS / 1e3
+        keep = [line for t, line in self.lines
+                if not self.windows or any(a - pad <= t <= b + pad for a, b in self.windows)]
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in out.strip().splitlines():
+        for line in keep:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -160,7 +197,9 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "timed_ms": round(1e3 * sum(b - a for a, b in self.windows), 1),
+                "period_ms": self.PERIOD_MS}
 
 
 # -------------------------------------------------------------- CPU side --
@@ -307,51 +346,58 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
-    # warm-up updates (also initialises the loop state on the device)
-    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, W, seed, 0, amp, False, d_v, d_k, d_f, d_x)
+    # warm-up updates (also initialise the loop state on the device and
+    # capture the one-update CUDA graph the timed updates replay)
+    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, W, seed, 0, amp, True, d_v, d_k, d_f, d_x)
     torch.cuda.synchronize()
     g.reset_stats()
-    g.set_profiling(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = ClockSampler()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.begin()
     with torch.cuda.stream(stream):
         for i in range(K):
             flush.fill_(float(i))                       # L2 flush, outside the timed window
             evs[i][0].record(stream)
-            R.rrg_closed_loop_dev(g.h, None, 0.0, d_r, 1, seed, 0, amp, False, d_v, d_k, d_f, d_x)
+            R.rrg_closed_loop_dev(g.h, None, 0.0, d_r, 1, seed, 0, amp, True, d_v, d_k, d_f, d_x)
             evs[i][1].record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = sum(step_ms) / 1e3
     st = g.stats()
-    g.set_profiling(False)
     if dist:
         t = torch.tensor([total_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
-    # the same K updates again through the cached one-update CUDA graph (the
-    # library's closed-loop replay mode), on a fresh handle from the same start
-    gg = R.Governor(p, cfg, stream)
-    gg.set_tuning(tune_m, tune_probe)
-    gd_v, gd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
-    gd_f, gd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
-    R.rrg_closed_loop_dev(gg.h, x0, V0, d_r, W, seed, 0, amp, True, gd_v, gd_k, gd_f, gd_x)
-    gevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    # graph replays cannot time single kernels: the same K updates again by
+    # direct launches, on a fresh handle from the same start, with CUDA
+    # events around every rollout launch (the roofline's kernel duration)
+    gd = R.Governor(p, cfg, stream)
+    gd.set_tuning(tune_m, tune_probe)
+    dd_v, dd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
+    dd_f, dd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
+    R.rrg_closed_loop_dev(gd.h, x0, V0, d_r, W, seed, 0, amp, False, dd_v, dd_k, dd_f, dd_x)
+    torch.cuda.synchronize()
+    gd.reset_stats()
+    gd.set_profiling(True)
+    devs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for i in range(K):
             flush.fill_(float(i))
-            gevs[i][0].record(stream)
-            R.rrg_closed_loop_dev(gg.h, None, 0.0, d_r, 1, seed, 0, amp, True, gd_v, gd_k, gd_f, gd_x)
-            gevs[i][1].record(stream)
+            devs[i][0].record(stream)
+            R.rrg_closed_loop_dev(gd.h, None, 0.0, d_r, 1, seed, 0, amp, False, dd_v, dd_k, dd_f, dd_x)
+            devs[i][1].record(stream)
     torch.cuda.synchronize()
-    graph_s = sum(a.elapsed_time(b) for a, b in gevs) / 1e3
-    graph_same = bool(torch.equal(gd_k, d_k))
-    gg.close()
+    direct_s = sum(a.elapsed_time(b) for a, b in devs) / 1e3
+    std = gd.stats()
+    gd.set_profiling(False)
+    direct_same = bool(torch.equal(dd_k, d_k))
+    gd.close()
     # and once more with the disturbances drawn inside the trajectory loop
     # (no stored scenario array, no sampler pass)
     cfg_gen = R.rrg_config_default(horizon=HZ, n_scenarios=NS, max_candidates=M_CAND,
@@ -382,11 +428,12 @@ def run_gpu(args):
     x_dev = d_x.cpu().numpy().reshape(T + 1, 3)
     value = world * K / total_s
 
-    # executed and nominal trajectory-steps of the timed updates
+    # executed trajectory-steps of the timed updates; the rollout kernel's
+    # duration and work per launch from the direct-launch run
     exec_steps = st["lane_steps"]
-    fp32_steps = st["lane_steps"] - st["lane_steps_fp64"]
-    avg_roll_ms = st["rollout_ms"] / max(1, st["timed_rollouts"])
-    roll_launches = max(1, st["timed_rollouts"])
+    fp32_steps = std["lane_steps"] - std["lane_steps_fp64"]
+    avg_roll_ms = std["rollout_ms"] / max(1, std["timed_rollouts"])
+    roll_launches = max(1, std["timed_rollouts"])
     achieved = (fp32_steps / roll_launches) * FLOPS_PER_STEP / (avg_roll_ms * 1e-3) / 1e12
 
     # the FP32 FMA, FP64 FMA and MUFU throughput measured on this GPU, next to
@@ -446,7 +493,9 @@ def run_gpu(args):
                          "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": measured_traffic() if (NS, HZ) == (N_SCEN, HORIZON) else None,
                          "kernel": "rollout_kernel<float>",
-                         "avg_launch_ms": avg_roll_ms, "launches": st["timed_rollouts"],
+                         "avg_launch_ms": avg_roll_ms, "launches": std["timed_rollouts"],
+                         "timing": "CUDA events around each rollout launch of the same K updates run by "
+                                   "direct launches (graph replays cannot time single kernels)",
                          "flops_per_traj_step": FLOPS_PER_STEP,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
                          "measured_units": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
@@ -454,11 +503,11 @@ def run_gpu(args):
                                             "frac_of_measured_fp32": achieved / peaks[0]}},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "graph_replay": {"value": world * K / graph_s, "unit": UNIT, "ms_per_step": 1e3 * graph_s / K,
-                             "kappa_equal_to_direct_launches": graph_same},
+            "direct_launches": {"value": world * K / direct_s, "unit": UNIT, "ms_per_step": 1e3 * direct_s / K,
+                                "gpu_launches": std["launches"], "kappa_equal_to_graph_replay": direct_same},
             "scenarios_in_register": {"value": world * K / reg_s, "unit": UNIT, "ms_per_step": 1e3 * reg_s / K,
                                       "mode": "graph replay, disturbances drawn in the trajectory loop",
-                                      "kappa_equal_to_direct_launches": reg_same},
+                                      "kappa_equal_to_stored_scenarios": reg_same},
             "gpu_launches": st["launches"],
             "clocks": clk,
             "fp64_bisect_gpu": fp64,
@@ -563,6 +612,7 @@ def run_batch(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = ClockSampler()
     torch.cuda.synchronize()
+    clocks.begin()
     with torch.cuda.stream(stream):
         for i in range(K):
             flush.fill_(float(i))
@@ -570,6 +620,7 @@ def run_batch(args):
             R.rrg_batch_closed_loop_dev(g.h, None, None, dr, 1, SEED, 0, amp, True, dv, dk, df, dxo)
             evs[i][1].record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     clk = clocks.stop()
     secs = sum(a.elapsed_time(c) for a, c in evs) / 1e3
     st = g.stats()
@@ -669,6 +720,9 @@ def run_single(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     legs = {}
+    clocks = ClockSampler()
+    torch.cuda.synchronize()
+    clocks.begin()
     for name, search, prec, M in (("fp64_bisect", R.SEARCH_BISECT, R.FP64, 2),
                                   ("fp32_recheck_spec", R.SEARCH_SPEC_BISECT, R.FP32_RECHECK, 64)):
         cfg = R.rrg_config_default(horizon=w["H"], n_scenarios=w["N"], max_candidates=M, n_bisect=w["n_bisect"],
@@ -681,6 +735,9 @@ def run_single(args):
         dev = [a for a, _ in ms]
         legs[name] = {"ms_per_update": statistics.median(dev), "host_ms_per_update": statistics.median([b for _, b in ms]),
                       "kappa": kap, "flags": fl, "gpu_launches_per_update": st["launches"] // (W + K)}
+    torch.cuda.synchronize()
+    clocks.end()
+    clk = clocks.stop()
     cpu = None
     if not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -710,7 +767,7 @@ def run_single(args):
                                   "32 scenarios (seed 0), horizon 500 RK4 steps (dt=0.01 s), N_kappa = 12",
                       "timing": "median device time of sample + search (CUDA events), host time beside it",
                       "l2": "256 MB written between timed steps"},
-           "legs": legs, "cpu_baseline": cpu}
+           "legs": legs, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -735,6 +792,9 @@ def run_adjoint(args):
     v_prev, r = 100.0, 250.0
     stream = torch.cuda.Stream()
     out_legs = {}
+    clocks = ClockSampler()
+    torch.cuda.synchronize()
+    clocks.begin()
     cfg = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=16, precision=R.FP32_RECHECK,
                                recheck_eps_rel=RECHECK_EPS_REL)
     with R.Governor(p, cfg, stream) as g:
@@ -775,6 +835,9 @@ def run_adjoint(args):
                 if i >= W:
                     ts.append(1e3 * (time.perf_counter() - t0))
             out_legs[name] = {"ms": statistics.median(ts), "kappa": kap, "flags": fl}
+    torch.cuda.synchronize()
+    clocks.end()
+    clk = clocks.stop()
     kb = out_legs["bisect20_fp64"]["kappa"]
     out_legs["newton_fp32_recheck_eval"]["within_one_bracket_of_bisect20"] = bool(
         abs(out_legs["newton_fp32_recheck_eval"]["kappa"] - kb) <= 2 * tol)
@@ -786,7 +849,7 @@ def run_adjoint(args):
                                   "steps, checkpoint every 50 steps, x_t at the 100 A equilibrium, r_t = 250 A, "
                                   "kappa = 0.1; Newton search to 2^-19 vs 20-iteration bisection",
                       "timing": "median host time per synchronous call"},
-           "legs": out_legs}
+           "legs": out_legs, "clocks": clk}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -872,6 +935,7 @@ def run_sweep(args):
         g.reset_stats()
         g.set_profiling(True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        clocks.begin()
         with torch.cuda.stream(stream):
             for i in range(K):
                 t = W + i
@@ -882,6 +946,7 @@ def run_sweep(args):
                                d_fl[t:t + 1])
                 evs[i][1].record(stream)
         torch.cuda.synchronize()
+        clocks.end()
         secs = sum(a.elapsed_time(b) for a, b in evs) / 1e3
         st = g.stats()
         g.set_profiling(False)
