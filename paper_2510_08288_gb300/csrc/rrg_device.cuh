@@ -194,14 +194,30 @@ __device__ __forceinline__ void fc3_rhs_fast(const RhsU<T>& U, const RhsC<T>& C,
   d_w = (C.e0 - U.e2 * w) - W_cp * f;
 }
 
+// Step-size constants of rk4_step_fast, formed once per trajectory (the
+// division dt / 6 is not left to the compiler to hoist out of the loop).
+template <typename T>
+struct StepC {
+  T dt, h2, h6, g2, g1;  // dt, dt / 2, dt / 6, dt / (2 p_atm), dt / p_atm
+};
+template <typename T>
+__device__ __forceinline__ StepC<T> step_consts(const RhsU<T>& U, T dt) {
+  StepC<T> S;
+  S.dt = dt;
+  S.h2 = T(0.5) * dt;
+  S.h6 = dt / T(6);
+  S.g2 = S.h2 * U.inv_p_atm;
+  S.g1 = dt * U.inv_p_atm;
+  return S;
+}
+
 // One RK4 step of size dt followed by the disturbance (e_ca, e_w, e_sm) of
 // Eq. 4, in place.  The update is summed as ((q + e) + h/6 (k1 + 2 (k2 +
 // k3))) + h/6 k4, so only one operation follows the last stage.
 template <typename T>
-__device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C, T dt,
+__device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C, const StepC<T>& S,
                                               T& q_ca, T& w, T& q_sm, T e_ca, T e_w, T e_sm) {
-  const T h2 = T(0.5) * dt, h6 = dt / T(6);
-  const T g2 = h2 * U.inv_p_atm, g1 = dt * U.inv_p_atm;
+  const T dt = S.dt, h2 = S.h2, h6 = S.h6, g2 = S.g2, g1 = S.g1;
   const T x1 = q_sm * U.inv_p_atm + T(1);
   T a1, b1, c1, a2, b2, c2, a3, b3, c3, a4, b4, c4;
   fc3_rhs_fast<T>(U, C, q_ca, w, q_sm, x1, a1, b1, c1);
@@ -214,6 +230,12 @@ __device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C
   q_ca = p_ca + h6 * a4;
   w = p_w + h6 * b4;
   q_sm = p_sm + h6 * c4;
+}
+
+template <typename T>
+__device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C, T dt, T& q_ca,
+                                              T& w, T& q_sm, T e_ca, T e_w, T e_sm) {
+  rk4_step_fast<T>(U, C, step_consts<T>(U, dt), q_ca, w, q_sm, e_ca, e_w, e_sm);
 }
 
 // ---------------------------------------------------------------------------

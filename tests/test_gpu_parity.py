@@ -513,6 +513,39 @@ def test_in_register_scenarios_equal_stored_ones(R, orc, params, prec):
             np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("unc", [0.0, 0.1])
+def test_register_and_shared_rings_agree(R, orc, params, unc):
+    """Binary32 lanes read the stored scenarios through a shared-memory ring
+    when a launch leaves most warp slots empty (at most 16 warps per SM) and
+    through a register ring when it fills the SMs.  12 candidates x 8,192
+    scenarios in one launch (3,072 warps: register ring) and each candidate
+    alone (256 warps: shared ring) give the same min slack and the same P bit
+    for bit, with and without parametric uncertainty; sampled lanes match the
+    oracle's per-trajectory decisions."""
+    N, H = 8192, 200
+    x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.03, 1.0])
+    kappas = np.linspace(0.0, 1.0, 12)
+    cfg = _cfg(R, N, H, precision=R.FP32, early_exit=R.EXIT_NONE, max_candidates=16, param_unc_rel=unc)
+    with R.Governor(params, cfg) as g:
+        g.sample_scenarios(5, 2)
+        adm, ms, P = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        for i, k in enumerate(kappas):
+            a1, m1, P1 = g.eval_candidates(x_t, 100.0, 250.0, [k], want_P=True)
+            assert a1[0] == adm[i] and m1[0] == ms[i]
+            np.testing.assert_array_equal(P1[0], P[i])
+        d = g.get_scenarios()
+        mult = g.get_param_multipliers() if unc else None
+    assert 0 < int(P.sum()) < P.size
+    c = orc.cfg(H=H, N=N, early_exit=0)
+    rng = np.random.default_rng(7)
+    with orc.param_multipliers(mult):
+        for k in rng.choice(N, size=12, replace=False):
+            for i in (0, 5, 11):
+                s, _ = orc.rollout(params, c, x_t, orc.governed(100.0, 250.0, kappas[i]), d, k)
+                if abs(s) > SLACK32_TOL:
+                    assert P[i, k] == (1 if s >= 0 else 0)
+
+
 def test_in_register_scenarios_closed_loop(R, orc, params):
     N, H, T = 32, 200, 5
     r_seq = inputs.staircase(T, 3, 2, seed=8)
