@@ -67,11 +67,11 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # + round 2, two no-op rounds; see
 # profiles/rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the
 # kernel sources are the ones profiled
-TRAFFIC_PER_LAUNCH = (438528 + 24622080 + 42752 + 42240) / 4
-TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "82628d1a7ddb1cbafe12103933c61cf025a7859b",
-                   "paper_2510_08288_gb300/csrc/rrg_lane.cuh": "315bfe6ec7bf6aebeb06fd37f76e0663c1f81883",
-                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "e931684eb6efbaa49158a781f8c212529bec96b5",
-                   "paper_2510_08288_gb300/csrc/rrg_internal.h": "7391646724a2d88938a2912be79a995da2629de4"}
+TRAFFIC_PER_LAUNCH = (431360 + 24614400 + 36864 + 34816) / 4
+TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "31d4b60dca992bd359f07e6790910fcfc222f36b",
+                   "paper_2510_08288_gb300/csrc/rrg_lane.cuh": "aaee7ca3f8c52f4b799df2034fc33845bffe6b99",
+                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "cc5eb334f99d59c13bbc8c27c2b9caded008436c",
+                   "paper_2510_08288_gb300/csrc/rrg_internal.h": "4e03f564284843e9c7ad89f3cb325a5a8170c08c"}
 
 
 def measured_traffic():

@@ -384,15 +384,17 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
   dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
   const int cls = recheck_classify ? 1 : 0;
   // Binary32 lanes on the stored array: the shared-memory ring when the
-  // launch leaves most warp slots empty (at most 16 warps per SM: each warp
-  // then runs its trajectory alone on its scheduler, bound by the step's
-  // latency), the register ring when it fills the SMs (bound by issue, where
-  // the ring's extra instructions cost more than they save).  Measured on
-  // GB300: the ring ran the 1,024-scenario closed loop 10 % faster, the
-  // register ring the 65,536-scenario sweep 6-10 % faster.
+  // launch leaves most warp slots empty (each warp then runs its trajectory
+  // alone on its scheduler, bound by the step's latency), the register ring
+  // when it fills the SMs (bound by issue, where the ring's extra
+  // instructions cost more than they save).  Thresholds measured on GB300:
+  // nominal model, ring up to 16 warps per SM (the 1,024-scenario closed loop
+  // ran 10 % faster, 8,192 x 16 candidates 3 % slower); parametric model
+  // (more registers, fewer resident warps), up to 64 (16,384 x 16 candidates
+  // 2-6 % faster, 65,536 x 16 6 % slower).
   const int sms = L.sms > 0 ? L.sms : 152;
   const long long warps = static_cast<long long>(grid.x) * grid.y * (kRollThreads / 32);
-  const bool ring = warps <= 16LL * sms;
+  const bool ring = warps <= (L.pmul ? 64LL : 16LL) * sms;
 #define RRG_ROLLOUT(KERNEL, T, SRC, KK, D0, D1, CAND, CLS) \
   KERNEL<T, SRC><<<grid, kRollThreads, 0, L.stream>>>(L, KK, D0, D1, CAND, early_exit, CLS)
   if (use_fp64) {

@@ -513,16 +513,16 @@ def test_in_register_scenarios_equal_stored_ones(R, orc, params, prec):
             np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("unc", [0.0, 0.1])
-def test_register_and_shared_rings_agree(R, orc, params, unc):
+@pytest.mark.parametrize("unc,N", [(0.0, 8192), (0.1, 32768)])
+def test_register_and_shared_rings_agree(R, orc, params, unc, N):
     """Binary32 lanes read the stored scenarios through a shared-memory ring
-    when a launch leaves most warp slots empty (at most 16 warps per SM) and
-    through a register ring when it fills the SMs.  12 candidates x 8,192
-    scenarios in one launch (3,072 warps: register ring) and each candidate
-    alone (256 warps: shared ring) give the same min slack and the same P bit
-    for bit, with and without parametric uncertainty; sampled lanes match the
+    when a launch leaves most warp slots empty (at most 16 warps per SM, 64
+    with parametric uncertainty) and through a register ring when it fills
+    the SMs.  12 candidates in one launch (3,072 / 12,288 warps: register
+    ring) and each candidate alone (256 / 1,024 warps: shared ring) give the
+    same min slack and the same P bit for bit; sampled lanes match the
     oracle's per-trajectory decisions."""
-    N, H = 8192, 200
+    H = 200
     x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.03, 1.0])
     kappas = np.linspace(0.0, 1.0, 12)
     cfg = _cfg(R, N, H, precision=R.FP32, early_exit=R.EXIT_NONE, max_candidates=16, param_unc_rel=unc)
