@@ -127,8 +127,9 @@ def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, give
 
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
-    """nvidia-smi's SM clock and throttle reasons every PERIOD_MS, read by a
-    thread that stamps each line with the host clock.  begin()/end() bracket
+    """nvidia-smi's SM clock, throttle reasons, power draw (and, where the
+    driver answers them, memory clock and enforced power limit) every
+    PERIOD_MS, read by a thread that stamps each line with the host clock.  begin()/end() bracket
     a timed region (host times taken after a device synchronize, so the
     region's kernels ran between them); stop() keeps the samples inside the
     regions widened by one period on each side, so that a region shorter than
@@ -137,28 +138,47 @@ class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    EXTRA = ",clocks.mem,enforced.power.limit"
 
     def __init__(self, gpu_index=None):
+        self.lines, self.windows, self._t0 = [], [], None
+        self.p = None
+        # the extra fields first; the required ones alone if that query is refused
+        for fields in (self.FIELDS + self.EXTRA, self.FIELDS):
+            if self._start(fields, gpu_index):
+                return
+
+    def _start(self, fields, gpu_index):
         import threading
-        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+        cmd = ["nvidia-smi", "--query-gpu=" + fields, "--format=csv,noheader,nounits",
                "-lms", str(self.PERIOD_MS)]
         if gpu_index is not None:
             cmd += ["-i", str(gpu_index)]
-        self.lines, self.windows, self._t0 = [], [], None
         self._first = threading.Event()
         try:
             self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
-            return
+            return True                     # no nvidia-smi at all: nothing to retry
         self.th = threading.Thread(target=self._read, daemon=True)
         self.th.start()
         self._first.wait(5.0)               # nvidia-smi is up before any region starts
+        if any(len(x.split(",")) >= 9 for _, x in self.lines):
+            return True
+        try:
+            self.p.wait(timeout=1.0)
+        except subprocess.TimeoutExpired:
+            return True                     # still running: keep it
+        self.th.join(timeout=5)             # refused (an unknown field): try the next query
+        self.lines, self.p = [], None
+        return False
 
     def _read(self):
         for line in self.p.stdout:
             self.lines.append((time.monotonic(), line))
-            self._first.set()
+            if len(line.split(",")) >= 9:
+                self._first.set()
+        self._first.set()                   # the query ended (refused, or stop())
 
     def begin(self):
         self._t0 = time.monotonic()
@@ -181,8 +201,14 @@ class ClockSampler:
         pad = self.PERIOD_MS / 1e3
         keep = [line for t, line in self.lines
                 if not self.windows or any(a - pad <= t <= b + pad for a, b in self.windows)]
-        sm, smax, reasons = [], [], set()
+        sm, smax, mem, plim, power, reasons = [], [], [], [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+        def num(v, into):
+            try:
+                into.append(float(v))
+            except ValueError:
+                pass
         for line in keep:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
@@ -192,14 +218,21 @@ class ClockSampler:
                 smax.append(float(f[2]))
             except ValueError:
                 continue
+            num(f[3], power)
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+            if len(f) >= 11:
+                num(f[9], mem)
+                num(f[10], plim)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm),
                 "timed_ms": round(1e3 * sum(b - a for a, b in self.windows), 1),
-                "period_ms": self.PERIOD_MS}
+                "period_ms": self.PERIOD_MS,
+                "mem_mhz": statistics.median(mem) if mem else None,
+                "power_w": statistics.median(power) if power else None,
+                "power_limit_w": statistics.median(plim) if plim else None}
 
 
 # -------------------------------------------------------------- CPU side --
