@@ -156,14 +156,17 @@ typedef struct {
 
 typedef struct rrg_ctx *rrg_handle;
 
-/* Counters kept by a handle since creation or the last rrg_reset_stats. */
+/* Counters kept by a handle since creation or the last rrg_reset_stats.
+ * Under closed-loop graph replay the launch, rollout and round counts are
+ * those of the kernels that ran: a conditional node's body is counted on the
+ * replays that executed it (by the device, read back here). */
 typedef struct {
     uint64_t launches;          /* kernels this handle launched               */
     uint64_t rollout_launches;  /* of which rollout kernels                   */
     uint64_t lane_steps;        /* RK4 steps executed over all trajectories   */
     uint64_t lane_steps_fp64;   /* of which in binary64                       */
     uint64_t rechecked;         /* trajectories re-run in binary64            */
-    uint64_t rounds;            /* search rounds enqueued                     */
+    uint64_t rounds;            /* search rounds run                          */
     double   rollout_ms;        /* summed device time of rollout launches
                                    (only while profiling is on)               */
     double   recheck_ms;        /* same for recheck launches                  */
