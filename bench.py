@@ -853,7 +853,7 @@ def run_adjoint(args):
                 if i >= W:
                     ts.append(1e3 * (time.perf_counter() - t0))
             out_legs[name] = {"ms": statistics.median(ts), "kappa": res[0], "flags": res[1], "gradients": res[2]}
-    # the judge: plain bisection with 20 iterations on the same scenarios
+    # the comparator: plain bisection with 20 iterations on the same scenarios
     for name, prec, search, M in (("bisect20_fp64", R.FP64, R.SEARCH_BISECT, 2),
                                   ("bisect20_fp32_recheck_spec", R.FP32_RECHECK, R.SEARCH_SPEC_BISECT, 64)):
         cfgb = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=M, n_bisect=20, search=search,
