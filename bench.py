@@ -103,6 +103,8 @@ def parse():
     ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch", "single", "adjoint"),
                     default="closed_loop")
     ap.add_argument("--instances", type=int, default=BATCH_S, help="batch: number of RG instances")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="batch: use this rollout variant instead of autotuning it")
     ap.add_argument("--sweep-n", type=str, default=",".join(str(n) for n in SWEEP_N),
                     help="scenario counts of the sweep")
     ap.add_argument("--param-unc-rel", type=float, default=None,
@@ -631,7 +633,13 @@ def run_batch(args):
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     dx0, dv0, dr = d(x0.reshape(-1)), d(b["v_prev"]), d(r_seq.reshape(-1))
     torch.cuda.synchronize()
-    best, tune_ms = R.rrg_batch_autotune(g.h, dx0, d(r), dv0, SEED, 0, 1)
+    # the rollout variant: by the library's autotuner on the first update, or
+    # given (results never depend on it)
+    if args.variant is not None:
+        g.set_variant(args.variant)
+        tune_ms = None
+    else:
+        best, tune_ms = R.rrg_batch_autotune(g.h, dx0, d(r), dv0, SEED, 0, 1)
     dv = torch.zeros(T * S, dtype=torch.float64, device=dev)
     dk = torch.zeros_like(dv)
     df = torch.zeros(T * S, dtype=torch.int32, device=dev)
@@ -699,12 +707,13 @@ def run_batch(args):
         "trajectory_steps_per_s": {"executed": st["lane_steps"] / secs, "executed_per_step": st["lane_steps"] / K},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "batch_rollout_kernel<%d, %d>" % (variant[1], variant[2]),
+                     "kernel": ("batch_rollout_warp_kernel<%d>" % variant[2]) if variant[1] == 32
+                               else ("batch_rollout_kernel<%d, %d>" % (variant[1], variant[2])),
                      "avg_launch_ms": avg_roll_ms, "launches": st2["timed_rollouts"],
                      "timing": "%d direct-launch updates after the timed ones" % K2,
                      "flops_per_traj_step": FLOPS_PER_STEP,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
-        "autotune_rollout_ms": [float(x) for x in tune_ms],
+        "autotune_rollout_ms": [float(x) for x in tune_ms] if tune_ms is not None else None,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": st["launches"],
         "rechecked_trajectories": st["rechecked"],
         "no_admissible_fraction": float(np.mean(flags[W:W + K] & 1)),
