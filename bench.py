@@ -474,6 +474,13 @@ def run_gpu(args):
     # the FP32 FMA, FP64 FMA and MUFU throughput measured on this GPU, next to
     # the derived peak the roofline fraction is reported against
     peaks = R.rrg_alu_peaks()
+    # the latency bound of the launches whose surviving lanes run alone on a
+    # scheduler: one warp's cycles per trajectory step against the rollout
+    # time per update spread over the horizon those lanes integrate
+    chain_cycles = g.step_latency(V0, HZ)
+    roll_ms_per_update = std["rollout_ms"] / max(1, K)
+    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    step_cycles = roll_ms_per_update * 1e-3 * sm_hz / HZ
     out = None
     if rank == 0:
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
@@ -535,7 +542,12 @@ def run_gpu(args):
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
                          "measured_units": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
                                             "mufu_ex2_tops": peaks[2],
-                                            "frac_of_measured_fp32": achieved / peaks[0]}},
+                                            "frac_of_measured_fp32": achieved / peaks[0]},
+                         "latency": {"cycles_per_step": step_cycles, "chain_cycles_per_step": chain_cycles,
+                                     "frac": chain_cycles / step_cycles,
+                                     "basis": "rollout time per update (direct launches) over the %d-step "
+                                              "horizon its surviving lanes integrate, at the sampled SM clock; "
+                                              "chain: rrg_step_latency, one warp, same right-hand side" % HZ}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "direct_launches": {"value": world * K / direct_s, "unit": UNIT, "ms_per_step": 1e3 * direct_s / K,

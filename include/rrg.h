@@ -424,6 +424,15 @@ RRG_API int rrg_eval_candidates_static(const double *model_params, int n_params,
  * Synchronous on the legacy default stream.  RRG_ECUDA / RRG_ENOMEM. */
 RRG_API int rrg_alu_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_tops);
 
+/* Latency of one binary32 trajectory step on the current device: one warp
+ * integrates `steps` RK4 steps of the rollout (the handle's model, setpoint v,
+ * from the equilibrium of v, no disturbance, the slack test of every step)
+ * and the SM clock times it; *cycles_per_step receives the least of three
+ * runs.  The bound of a launch whose lanes each run alone on a warp
+ * scheduler (the closed loop's long rollouts).  Synchronous on the handle's
+ * stream.  RRG_EINVAL: v not finite or <= 0, steps < 1, no equilibrium. */
+RRG_API int rrg_step_latency(rrg_handle h, double v, int steps, double *cycles_per_step);
+
 /* ------------------------------------------------------------------------ */
 /* Batched instances: S independent robust RG problems (instance s with its
  * own N_s scenarios and horizon H_s) that share the model, dt, the search and

@@ -750,6 +750,26 @@ int rrg_equilibrium(rrg_handle h, double v, double* x_eq, double* y_ss) {
   return RRG_OK;
 }
 
+int rrg_step_latency(rrg_handle h, double v, int steps, double* cycles_per_step) {
+  if (!h) return RRG_EINVAL;
+  if (!is_fin(v) || !(v > 0.0) || steps < 1 || !cycles_per_step)
+    return set_err(h, RRG_EINVAL, "v must be finite and > 0, steps >= 1, cycles_per_step non-NULL");
+  DeviceGuard g(h->device);
+  double best = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {  // the first run also warms the instruction caches
+    CK(launch_step_latency(h->L, v, steps, h->io_dev + IO_OUT, h->flag_dev + 1));
+    h->launches++;
+    CK(cudaMemcpyAsync(h->io_h + IO_OUT, h->io_dev + IO_OUT, 2 * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->flag_h + 1, h->flag_dev + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->flag_h[1] != 0) return set_err(h, RRG_EINVAL, "no equilibrium found for v = %g", v);
+    if (rep == 0 || h->io_h[IO_OUT] < best) best = h->io_h[IO_OUT];
+  }
+  *cycles_per_step = best;
+  return RRG_OK;
+}
+
 int rrg_plant_step(rrg_handle h, const double* x_t, double v_t, uint64_t seed, uint64_t t,
                    const double* plant_amp, double* x_next) {
   if (!h) return RRG_EINVAL;

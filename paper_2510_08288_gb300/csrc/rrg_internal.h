@@ -318,6 +318,7 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
                            bool recheck_classify);
 cudaError_t launch_recheck(const Launch& L, int early_exit);
 cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_t* d_status);
+cudaError_t launch_step_latency(const Launch& L, double v, int steps, double* d_out2, int32_t* d_status);
 cudaError_t launch_plant(const Launch& L, const double* d_x, const double* d_v, uint64_t seed,
                          uint64_t base, const unsigned long long* t_dev, const double* amp_dev,
                          double* d_x_next);

@@ -46,6 +46,50 @@ cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_
   return cudaGetLastError();
 }
 
+// One warp integrating `steps` binary32 RK4 steps of the rollout (the same
+// right-hand side, constants, slack and finiteness accumulation as the
+// trajectory loop, no disturbance) from the equilibrium of v, timed with the
+// SM clock: the latency of the trajectory loop's dependent chain, the bound of
+// a launch whose lanes each run alone on a scheduler.  out[0] = cycles per
+// step, out[1] keeps the lanes' results alive; *status = the equilibrium's.
+__global__ void __launch_bounds__(32)
+step_latency_kernel(const Launch L, const RhsU<float> U, double v, int steps, double* out,
+                    int32_t* status) {
+  const CandK<double> Cd = cand_consts(L.params, v);
+  RhsC<double> c64;
+  RhsC<float> c32;
+  fold_rhs_cand(L.k64, Cd, &c64, &c32);
+  float q[3] = {0.0f, 0.0f, 0.0f}, y = 0.0f;
+  const int rc = equilibrium_from<float>(L.k32, L.params, Cd, q, &y);
+  float q_ca = q[0] + 1e-3f * static_cast<float>(threadIdx.x), w = q[1], q_sm = q[2];
+  const StepC<float> S = step_consts<float>(U, static_cast<float>(L.dt));
+  const float y_min = static_cast<float>(L.y_min);
+  float smin = inf_v<float>(), nf = 0.0f;
+  __syncwarp();
+  const long long t0 = clock64();
+#pragma unroll 8
+  for (int j = 0; j < steps; ++j) {
+    rk4_step_fast<float>(U, c32, S, q_ca, w, q_sm, 0.0f, 0.0f, 0.0f);
+    const float s = c32.y_scale * (q_sm - q_ca) - y_min;
+    smin = fminf(smin, s);
+    nf = fma_rn(s, 0.0f, nf);
+  }
+  const long long t1 = clock64();
+  float r = smin + nf + q_ca + w + q_sm;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  if (threadIdx.x == 0) {
+    out[0] = static_cast<double>(t1 - t0) / steps;
+    out[1] = r;
+    *status = rc;
+  }
+}
+
+cudaError_t launch_step_latency(const Launch& L, double v, int steps, double* d_out2, int32_t* d_status) {
+  step_latency_kernel<<<1, 32, 0, L.stream>>>(L, L.u32, v, steps, d_out2, d_status);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Scenario sampling: one thread per (j, k), coalesced over k.
 //

@@ -96,6 +96,7 @@ def _load():
         "rrg_eval_candidates_static": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, _p, _p, _p, _d,
                                                       _d, _p, ctypes.c_int, _p, _p]),
         "rrg_alu_peaks": (ctypes.c_int, [_p, _p, _p]),
+        "rrg_step_latency": (ctypes.c_int, [_p, ctypes.c_double, ctypes.c_int, _p]),
         "rrg_batch_create": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), ctypes.c_int, _p, _p, _p, P(_p)]),
         "rrg_batch_destroy": (ctypes.c_int, [_p]),
         "rrg_batch_last_error": (ctypes.c_char_p, [_p]),
@@ -236,6 +237,13 @@ def rrg_equilibrium(h, v):
     y = _d(0.0)
     _check(lib.rrg_equilibrium(h, float(v), _ptr(x), ctypes.byref(y)), h)
     return x, y.value
+
+
+def rrg_step_latency(h, v, steps=2000):
+    """Cycles per binary32 trajectory step for one warp on the current GPU."""
+    c = _d(0.0)
+    _check(lib.rrg_step_latency(h, float(v), int(steps), ctypes.byref(c)), h)
+    return c.value
 
 
 def rrg_closed_loop(h, x0, v0, r_seq, seed, t0, plant_amp, use_graph=True):
@@ -387,6 +395,9 @@ class Governor:
 
     def equilibrium(self, v):
         return rrg_equilibrium(self.h, v)
+
+    def step_latency(self, v, steps=2000):
+        return rrg_step_latency(self.h, v, steps)
 
     def closed_loop(self, x0, v0, r_seq, seed, t0, plant_amp, use_graph=True):
         return rrg_closed_loop(self.h, x0, v0, r_seq, seed, t0, plant_amp, use_graph)

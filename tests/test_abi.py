@@ -144,3 +144,10 @@ def test_batch_create_validation_without_gpu():
         with pytest.raises(R.RrgError) as e:
             R.rrg_batch_create(p, cfg, ns, hz)
         assert e.value.code == code, (ns, hz, str(e.value))
+
+
+def test_step_latency_rejects_a_null_handle():
+    """The latency probe validates its arguments before touching a device."""
+    from paper_2510_08288_gb300 import rrg as R
+    c = ctypes.c_double(0.0)
+    assert R.lib.rrg_step_latency(None, 100.0, 10, ctypes.byref(c)) == R.RRG_EINVAL

@@ -561,6 +561,25 @@ def test_in_register_scenarios_closed_loop(R, orc, params):
         np.testing.assert_array_equal(a, b)
 
 
+def test_step_latency(R, orc, params):
+    """One warp's cycles per binary32 trajectory step: positive, stable over
+    horizons, argument errors reported, and the handle's results unchanged."""
+    cfg = _cfg(R, 64, 300, precision=R.FP32_RECHECK, recheck_eps_rel=SLACK32_TOL / 1.9)
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, cfg) as g:
+        g.sample_scenarios(3, 1)
+        before = g.step(x_t, 250.0, 100.0)
+        c2000 = g.step_latency(100.0, 2000)
+        c500 = g.step_latency(180.0, 500)
+        assert 50.0 < c2000 < 5000.0 and 50.0 < c500 < 5000.0
+        assert abs(c500 - c2000) < 0.3 * c2000
+        with pytest.raises(R.RrgError):
+            g.step_latency(-1.0)
+        with pytest.raises(R.RrgError):
+            g.step_latency(100.0, 0)
+        assert g.step(x_t, 250.0, 100.0) == before
+
+
 def test_alu_peaks_are_plausible(R):
     """The unit throughput measured on this GPU: binary32 FMA near the
     derived 80.5 TFLOP/s, binary64 FMA far below it, MUFU exp2 in between."""
