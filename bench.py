@@ -66,21 +66,41 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # launches with the tuned shape 64 nodes / 32-step probe: probe, continuation
 # + round 2, two no-op rounds; see
 # profiles/rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the
-# kernel sources are the ones profiled
+# rollout's sources are the ones profiled: the trajectory loops and model
+# (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
+# rrg_kernels.cu, and the Launch struct (sha1 of each region)
 TRAFFIC_PER_LAUNCH = (431360 + 24614400 + 36864 + 34816) / 4
-TRAFFIC_SOURCES = {"paper_2510_08288_gb300/csrc/rrg_kernels.cu": "31d4b60dca992bd359f07e6790910fcfc222f36b",
-                   "paper_2510_08288_gb300/csrc/rrg_lane.cuh": "aaee7ca3f8c52f4b799df2034fc33845bffe6b99",
-                   "paper_2510_08288_gb300/csrc/rrg_device.cuh": "cc5eb334f99d59c13bbc8c27c2b9caded008436c",
-                   "paper_2510_08288_gb300/csrc/rrg_internal.h": "4e03f564284843e9c7ad89f3cb325a5a8170c08c"}
+TRAFFIC_SOURCES = (
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "aaee7ca3f8c52f4b799df2034fc33845bffe6b99"),
+    ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "cc5eb334f99d59c13bbc8c27c2b9caded008436c"),
+    ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
+     "// Binary64 re-run of the trajectories", "208aa315d110bd29a90ab25d98f9e15fc17a6ba4"),
+    ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
+     "babf78733fa6871fdc4b8fb328a1cce64fc61742"),
+)
+
+
+def source_region(rel, begin, end):
+    """The text of a source file, or of its region from `begin` up to the
+    first `end` after it."""
+    with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+        text = f.read()
+    if begin is None:
+        return text
+    i = text.index(begin)
+    return text[i:text.index(end, i) + len(end)]
 
 
 def measured_traffic():
-    """The profiled DRAM bytes per launch, or None if the kernel changed."""
+    """The profiled DRAM bytes per launch, or None if the rollout changed."""
     import hashlib
-    for rel, sha in TRAFFIC_SOURCES.items():
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            if hashlib.sha1(f.read()).hexdigest() != sha:
-                return None
+    for rel, begin, end, sha in TRAFFIC_SOURCES:
+        try:
+            region = source_region(rel, begin, end)
+        except (OSError, ValueError):
+            return None
+        if hashlib.sha1(region.encode("utf-8")).hexdigest() != sha:
+            return None
     return TRAFFIC_PER_LAUNCH
 
 
