@@ -264,7 +264,9 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
 // a single warp and the scenario array in DRAM: 332 cycles per step for the
 // register ring at depth 16, 262 for this ring; in the 1,024-scenario closed
 // loop the average rollout launch took 70.5 us with D = 32, B = 16, U = 8
-// against 78.4 us with the register ring.  Results equal run_lane's bit for
+// against 78.4 us with the register ring; on another box 69.1 us with
+// B = 32 against 70.2 us with B = 16 (U = 16 with B = 16: 78.3, a body too
+// large for the instruction cache).  Results equal run_lane's bit for
 // bit (same arithmetic in the same order); a lane may run one block longer
 // after its candidate died, which changes no decision.
 //
@@ -277,7 +279,7 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
 #define RRG_RING_UNROLL 8
 #endif
 #ifndef RRG_RING_BLOCK
-#define RRG_RING_BLOCK 16
+#define RRG_RING_BLOCK 32
 #endif
 static_assert((RRG_RING_DEPTH & (RRG_RING_DEPTH - 1)) == 0, "ring depth: a power of two");
 static_assert(RRG_RING_BLOCK % RRG_RING_UNROLL == 0, "block: a multiple of the unroll");
