@@ -69,9 +69,9 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
-TRAFFIC_PER_LAUNCH = (431360 + 24614400 + 36864 + 34816) / 4
+TRAFFIC_PER_LAUNCH = (430592 + 24615936 + 34560 + 35072) / 4
 TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "aaee7ca3f8c52f4b799df2034fc33845bffe6b99"),
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "6e4d02064039bc79576c0f09c48108e3b687aa4f"),
     ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "cc5eb334f99d59c13bbc8c27c2b9caded008436c"),
     ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
      "// Binary64 re-run of the trajectories", "208aa315d110bd29a90ab25d98f9e15fc17a6ba4"),
