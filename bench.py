@@ -546,7 +546,8 @@ def run_gpu(args):
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * total_s / K, "ms_per_step_median": statistics.median(step_ms),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
@@ -695,7 +696,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     clocks.end()
     clk = clocks.stop()
-    secs = sum(a.elapsed_time(c) for a, c in evs) / 1e3
+    step_ms = [a.elapsed_time(c) for a, c in evs]
+    secs = sum(step_ms) / 1e3
     st = g.stats()
     # graph replays cannot time single kernels: K2 more updates with direct
     # launches give the rollout kernel's duration (CUDA events in the library)
@@ -733,7 +735,8 @@ def run_batch(args):
     g.close()
     out = {
         "metric": BATCH_METRIC, "value": S * K / secs, "unit": "RG updates/s (instance updates)", "n_gpus": 1,
-        "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "higher_is_better": True, "scaling": "weak",
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "ms_per_step_median": statistics.median(step_ms),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": batch_config(S, W, K, {"index": variant[0], "tile_lanes": variant[1], "prefetch": variant[2]}),
         "trajectory_steps_per_s": {"executed": st["lane_steps"] / secs, "executed_per_step": st["lane_steps"] / K},
