@@ -807,11 +807,20 @@ def run_single(args):
                                    recheck_eps_rel=RECHECK_EPS_REL)
         with R.Governor(p, cfg, stream) as g:
             x_t, _ = g.equilibrium(w["v_prev"])
+            shape = None
+            if search == R.SEARCH_SPEC_BISECT:
+                # the tree width and probe by the library's autotuner on this
+                # update (every shape gives Alg. 1's kappa)
+                g.sample_scenarios(w["seed"], 0)
+                shape = g.autotune(x_t, w["r"], w["v_prev"], repeats=2)[:2]
+            g.reset_stats()
             kap, fl, ms = timed_updates(R, torch, g, x_t, w["r"], w["v_prev"], W, K, w["seed"], flush, stream)
             st = g.stats()
         dev = [a for a, _ in ms]
         legs[name] = {"ms_per_update": statistics.median(dev), "host_ms_per_update": statistics.median([b for _, b in ms]),
                       "kappa": kap, "flags": fl, "gpu_launches_per_update": st["launches"] // (W + K)}
+        if shape is not None:
+            legs[name]["shape"] = {"candidates_per_round": shape[0], "probe_steps": shape[1]}
     torch.cuda.synchronize()
     clocks.end()
     clk = clocks.stop()
