@@ -98,7 +98,7 @@ extern "C" {
 typedef struct {
     double  dt;              /* RK4 step, s (> 0)                             */
     int32_t horizon;         /* H = j*: outputs checked at j = 0..H (>= 1)    */
-    int32_t n_scenarios;     /* N_sim (1..65535 * 128)                        */
+    int32_t n_scenarios;     /* N_sim (>= 1)                                  */
     int32_t max_candidates;  /* candidates per round, 1..RRG_MAX_CANDIDATES;
                                 the grid size M for GRID and KSECTION         */
     int32_t n_bisect;        /* N_kappa of Alg. 1 (>= 1)                      */

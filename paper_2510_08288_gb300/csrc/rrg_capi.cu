@@ -130,9 +130,6 @@ int validate_cfg(const rrg_config* c) {
   if (!(c->dt > 0.0) || !is_fin(c->dt)) return set_err(nullptr, RRG_EINVAL, "dt must be > 0");
   if (c->horizon < 1) return set_err(nullptr, RRG_EINVAL, "horizon must be >= 1");
   if (c->n_scenarios < 1) return set_err(nullptr, RRG_EINVAL, "n_scenarios must be >= 1");
-  // the rollout grid's second dimension counts tiles of 128 scenarios
-  if (c->n_scenarios > 65535 * 128)
-    return set_err(nullptr, RRG_EINVAL, "n_scenarios must be <= %d", 65535 * 128);
   if (c->max_candidates < 1 || c->max_candidates > RRG_MAX_CANDIDATES)
     return set_err(nullptr, RRG_EINVAL, "max_candidates must be in [1, %d]", RRG_MAX_CANDIDATES);
   if (c->n_bisect < 1 || c->n_bisect > 60)

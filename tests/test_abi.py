@@ -83,9 +83,6 @@ def test_config_defaults_and_create_validation_without_gpu():
     with pytest.raises(R.RrgError) as e:
         R.rrg_create(inputs.fc3_params(), bad)
     assert e.value.code == R.RRG_EINVAL and "horizon" in str(e.value)
-    with pytest.raises(R.RrgError) as e:
-        R.rrg_create(inputs.fc3_params(), R.rrg_config_default(n_scenarios=65535 * 128 + 1))
-    assert e.value.code == R.RRG_EINVAL and "n_scenarios" in str(e.value)
     with pytest.raises(R.RrgError):
         R.rrg_create(inputs.fc3_params()[:5], c)
     with pytest.raises(R.RrgError):
