@@ -91,6 +91,15 @@ def source_region(rel, begin, end):
     return text[i:text.index(end, i) + len(end)]
 
 
+# The sweep's rollout launches (parametric model, register ring): DRAM bytes
+# per launch of one update's three k-section rounds at 32,768 scenarios (ncu,
+# one pass; profiles/rollout_pu_kernel_f32_sweep_N65536_H5000.md), and the
+# same per-launch figure scaled to 65,536 scenarios by the units processed
+# (the scenario array, which dominates the traffic, doubles).
+SWEEP_TRAFFIC_32K = (3602669056 + 3401216 + 2197011712 + 273152 + 7767449088 + 80128) / 3
+SWEEP_TRAFFIC_64K = 2 * SWEEP_TRAFFIC_32K
+
+
 def measured_traffic():
     """The profiled DRAM bytes per launch, or None if the rollout changed."""
     import hashlib
@@ -1103,7 +1112,11 @@ def run_sweep(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(sweep_config(ns, W, K), param_unc_rel=rho),
         "roofline": {"bound": "alu", "achieved": top["rollout_tflops"], "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": top["rollout_frac"], "traffic": None,
+                     "unit": "TFLOP/s", "frac": top["rollout_frac"],
+                     "traffic": (SWEEP_TRAFFIC_64K if top["n_scenarios"] == 65536 and rho == inputs.PARAM_UNC_REL
+                                 and measured_traffic() is not None else None),
+                     "traffic_basis": "ncu DRAM bytes per rollout launch at 32,768 scenarios (one update's "
+                                      "3 rounds), scaled x2 to 65,536 by the units processed",
                      "kernel": "rollout_kernel<float, parametric>", "n_scenarios": top["n_scenarios"],
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
         "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
