@@ -233,3 +233,38 @@ def test_adjoint_matches_complex_step(R, orc, params, checkpoint):
             assert gv == pytest.approx(go, rel=1e-10, abs=1e-12)
             scale = np.maximum(np.abs(gro), 1e-12 * np.max(np.abs(gro)))
             assert np.all(np.abs(grad - gro) <= 1e-7 * scale + 1e-14)
+
+
+def test_full_size_sweep_update_matches_fp64_and_oracle(R, orc, params):
+    """The large sweep's configuration at its largest size (65,536 scenarios x
+    5,000 steps, k-section with 16 candidates x 3 rounds, +-10 % on the
+    uncertain parameters, FP32 rollouts with the FP64 recheck, in the
+    launch shape the benchmark times): kappa equals the plain FP64 search on
+    the same draws, and sampled trajectories' decisions at the chosen and the
+    next grid point equal the oracle's."""
+    N, H, M = 65536, 5000, 16
+    v_prev, r = 100.0, 150.0
+    seed, upd = 1, 3
+    x_t = orc.equilibrium(params, v_prev)
+    kw = dict(max_candidates=M, n_rounds=3, search=R.SEARCH_KSECTION, recheck_eps_rel=1e-6)
+    with R.Governor(params, _cfg(R, N, H, precision=R.FP32_RECHECK, **kw)) as g:
+        g.sample_scenarios(seed, upd)
+        v32, k32, f32 = g.step(x_t, r, v_prev)
+        probe = np.array([k32, min(1.0, k32 + 1.0 / (M - 1))])
+        adm, ms, P = g.eval_candidates(x_t, v_prev, r, probe, want_P=True)
+    with R.Governor(params, _cfg(R, N, H, precision=R.FP64, **kw)) as g:
+        g.sample_scenarios(seed, upd)
+        v64, k64, f64 = g.step(x_t, r, v_prev)
+    assert (k32, f32) == (k64, f64)
+    assert adm[0] == 1
+    # the oracle on scenarios k < 1,024 (Philox counters do not depend on N)
+    n = 1024
+    d = orc.sample_disturbances(seed, upd, n, H, inputs.DIST_AMP)
+    mult = orc.sample_param_multipliers(seed, upd, n, RHO, MASK)
+    c = orc.cfg(H=H, N=n, early_exit=1)
+    rng = np.random.default_rng(11)
+    with orc.param_multipliers(mult):
+        for k in rng.choice(n, size=12, replace=False):
+            for i, kk in enumerate(probe):
+                s, _ = orc.rollout(params, c, x_t, orc.governed(v_prev, r, kk), d, k)
+                assert P[i, k] == (1 if s >= 0 else 0), (k, i, s)
