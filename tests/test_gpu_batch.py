@@ -182,3 +182,31 @@ def test_batch_recheck_runs_only_to_the_last_uncertain_step(R, orc, params):
                           np.zeros((3, H, N)))
         assert (k[s], f[s]) == (ko, fo) == (0.0, 0)
     assert st["rechecked"] == S * N and st["lane_steps_fp64"] == 0
+
+
+def test_full_size_batch_update_matches_single_problems_and_oracle(R, orc, params):
+    """The batched workload at full size (256 instances, N_s up to 8,192,
+    H_s up to 4,000, k-section with 32 candidates x 3 rounds, seed 2, in the
+    variant the autotuner picks): every instance's kappa equals the
+    single-problem search on the same draw (seed + s), and the oracle's on
+    the cheapest instances."""
+    S, seed, upd, M = 256, 2, 0, 32
+    b, x = _problem(orc, params, S, seed)
+    cfg = _cfg(R, M, R.SEARCH_KSECTION, recheck_eps_rel=1e-6)
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        g.autotune(x, b["r"], b["v_prev"], seed, upd, repeats=1)
+        v, k, f = g.step(x, b["r"], b["v_prev"], seed, upd)
+    for s in range(S):
+        N, H = int(b["N"][s]), int(b["H"][s])
+        c1 = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=M, n_rounds=3,
+                                  search=R.SEARCH_KSECTION, precision=R.FP32_RECHECK,
+                                  early_exit=R.EXIT_CANDIDATE, recheck_eps_rel=1e-6)
+        with R.Governor(params, c1) as g1:
+            g1.sample_scenarios(seed + s, upd)
+            assert g1.step(x[s], b["r"][s], b["v_prev"][s]) == (v[s], k[s], f[s]), s
+    cheapest = sorted(range(S), key=lambda s: int(b["N"][s]) * int(b["H"][s]))[:6]
+    for s in cheapest:
+        N, H = int(b["N"][s]), int(b["H"][s])
+        d = orc.sample_disturbances(seed + s, upd, N, H, inputs.DIST_AMP)
+        ko, fo = _oracle(orc, params, "ksection", x[s], b["v_prev"][s], b["r"][s], d, N, H, M)
+        assert (k[s], f[s]) == (ko, fo), s
