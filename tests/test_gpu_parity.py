@@ -124,10 +124,11 @@ def test_eval_fp64_matches_oracle(R, orc, params, N, H, early):
         np.testing.assert_allclose(ms, ms_o, rtol=SLACK64_RTOL, atol=1e-12)
 
 
-@pytest.mark.parametrize("N,H", [(32, 500), (129, 300)])
+@pytest.mark.parametrize("N,H", [(32, 500), (129, 300), (1, 1), (37, 31), (5, 32), (70, 33), (9, 65)])
 def test_eval_fp32_within_band(R, orc, params, N, H):
     """Plain binary32: slack error inside the band; decisions differ only
-    where the binary64 slack is inside it."""
+    where the binary64 slack is inside it.  Horizons around the shared
+    ring's depth and exit block (32 steps) included."""
     kappas = np.linspace(0.0, 0.2, 21)
     (adm, ms, P, _), (a_o, ms_o, P_o) = _eval_both(R, orc, params, N, H, kappas, R.FP32, 0)
     assert np.max(np.abs(ms - ms_o)) < SLACK32_TOL
@@ -135,7 +136,7 @@ def test_eval_fp32_within_band(R, orc, params, N, H):
     assert np.all(np.abs(ms_o[differ]) < SLACK32_TOL)
 
 
-@pytest.mark.parametrize("N,H", [(32, 500), (129, 300), (1000, 120)])
+@pytest.mark.parametrize("N,H", [(32, 500), (129, 300), (1000, 120), (64, 31), (64, 33)])
 def test_eval_fp32_recheck_is_exact(R, orc, params, N, H):
     """Binary32 bulk + binary64 recheck of the near-zero lanes decides exactly
     like the binary64 oracle (the band is wide enough to cover binary32 error)."""
