@@ -56,6 +56,11 @@ PROBE_STEPS = 128
 # stage points of 6, the RK4 combination of 18, the disturbance add of 3, and
 # output, slack, running min and the finiteness accumulator of 6
 FLOPS_PER_STEP = 141
+# instructions a warp issues per trajectory step in the register-ring loop
+# (ncu, one warp): an issue-bound step reaches at most 141 / (2 x 124) of the
+# derived FP32 peak, which counts every instruction as an FMA
+INSTR_PER_STEP = 124
+ISSUE_CEILING = FLOPS_PER_STEP / (2.0 * INSTR_PER_STEP)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # large sweep: N_sim 1K..64K, 16 candidates, horizon 5,000, parametric uncertainty
@@ -570,6 +575,8 @@ def run_gpu(args):
                                    "direct launches (graph replays cannot time single kernels)",
                          "flops_per_traj_step": FLOPS_PER_STEP,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                         "issue_ceiling": ISSUE_CEILING,
+                         "frac_of_issue_ceiling": achieved / FP32_PEAK_TFLOPS / ISSUE_CEILING,
                          "measured_units": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
                                             "mufu_ex2_tops": peaks[2],
                                             "frac_of_measured_fp32": achieved / peaks[0]},
@@ -756,7 +763,8 @@ def run_batch(args):
                      "avg_launch_ms": avg_roll_ms, "launches": st2["timed_rollouts"],
                      "timing": "%d direct-launch updates after the timed ones" % K2,
                      "flops_per_traj_step": FLOPS_PER_STEP,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                     "issue_ceiling": ISSUE_CEILING, "frac_of_issue_ceiling": achieved / FP32_PEAK_TFLOPS / ISSUE_CEILING},
         "autotune_rollout_ms": [float(x) for x in tune_ms] if tune_ms is not None else None,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": st["launches"],
         "rechecked_trajectories": st["rechecked"],
@@ -1118,7 +1126,8 @@ def run_sweep(args):
                      "traffic_basis": "ncu DRAM bytes per rollout launch at 32,768 scenarios (one update's "
                                       "3 rounds), scaled x2 to 65,536 by the units processed",
                      "kernel": "rollout_kernel<float, parametric>", "n_scenarios": top["n_scenarios"],
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"},
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                     "issue_ceiling": ISSUE_CEILING, "frac_of_issue_ceiling": top["rollout_frac"] / ISSUE_CEILING},
         "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
         "gpu_launches": top["gpu_launches"],
     }
