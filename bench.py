@@ -274,7 +274,8 @@ class ClockSampler:
 # -------------------------------------------------------------- CPU side --
 def cpu_oracle_closed_loop(x0, r_seq, seconds, cores):
     """Times the FP64 oracle's closed loop (plain joint bisection) on a
-    bounded prefix of the run; returns (updates/s, updates, seconds, kappas)."""
+    bounded prefix of the run; returns (updates/s, updates, seconds, kappas,
+    seconds of the first update)."""
     from oracle import oracle as O
     from paper_2510_08288_gb300 import inputs
     p = inputs.fc3_params()
@@ -294,7 +295,20 @@ def cpu_oracle_closed_loop(x0, r_seq, seconds, cores):
     else:
         total = one
     n = 1 + more
-    return n / total, n, total, kaps
+    return n / total, n, total, kaps, one
+
+
+def cpu_oracle_one_core(x0, r_seq):
+    """The first update of the same closed loop on one host thread: the
+    sequential FP64 oracle beside the threaded one; returns (updates/s, kappa)."""
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    p = inputs.fc3_params()
+    c = O.cfg(H=HORIZON, N=N_SCEN)
+    t0 = time.perf_counter()
+    v, kap, fl, xs = O.closed_loop(p, c, x0, V0, r_seq[:1], SEED, 0, inputs.DIST_AMP, inputs.DIST_AMP,
+                                   search=0, n_kappa=N_BISECT, nthreads=1)
+    return 1.0 / (time.perf_counter() - t0), float(kap[0])
 
 
 def run_reference(args):
@@ -549,7 +563,7 @@ def run_gpu(args):
             cores = os.cpu_count() or 1
             from oracle import oracle as O
             x0o = O.equilibrium(p, V0)
-            cval, cn, cs, ckap = cpu_oracle_closed_loop(x0o, inputs.staircase(1000, 8, 125, SEED),
+            cval, cn, cs, ckap, cone = cpu_oracle_closed_loop(x0o, inputs.staircase(1000, 8, 125, SEED),
                                                         args.cpu_seconds, cores)
             cpu = {"value": cval, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "first %d updates of the same closed loop (seed %d), FP64 plain joint "
@@ -557,6 +571,11 @@ def run_gpu(args):
             # rank 0's replica starts from the same state and scenarios: kappas must agree
             nk = min(cn, T)
             cpu["kappa_equal_to_gpu"] = bool(np.all(np.array(ckap[:nk]) == kap_dev[:nk]))
+            v1, k1 = cpu_oracle_one_core(x0o, inputs.staircase(1000, 8, 125, SEED))
+            cpu["one_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                               "threaded_same_update": 1.0 / cone,
+                               "sample": "first update of the same closed loop, one host thread",
+                               "kappa_equal_to_threaded": k1 == ckap[0]}
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -637,23 +656,38 @@ def batch_inputs(R, p, S):
 
 def batch_cpu(p, b, x0, r, seconds, cores):
     """The FP64 oracle's k-section on a bounded sample: whole instances (the
-    shortest first) for one update each, until about `seconds` are spent."""
+    shortest first) for one update each, until about `seconds` are spent; then
+    the sequential oracle on one thread over the first of those instances, for
+    about a quarter of that time."""
     from oracle import oracle as O
     from paper_2510_08288_gb300 import inputs
     order = sorted(range(len(b["N"])), key=lambda s: int(b["N"][s]) * int(b["H"][s]))
-    done, t_total = 0, 0.0
-    for s in order:
+
+    def one(s, threads):
         N, H = int(b["N"][s]), int(b["H"][s])
         d = O.sample_disturbances(SEED + s, 0, N, H, inputs.DIST_AMP)
         t0 = time.perf_counter()
-        O.ksection(p, O.cfg(H=H, N=N), x0[s], b["v_prev"][s], r[s], BATCH_M, BATCH_ROUNDS, d, nthreads=cores)
-        t_total += time.perf_counter() - t0
-        done += 1
-        if t_total > seconds:
+        O.ksection(p, O.cfg(H=H, N=N), x0[s], b["v_prev"][s], r[s], BATCH_M, BATCH_ROUNDS, d, nthreads=threads)
+        return time.perf_counter() - t0
+
+    per = []
+    for s in order:
+        per.append(one(s, cores))
+        if sum(per) > seconds:
             break
-    return {"value": done / t_total, "unit": "RG updates/s (instance updates)", "cores": cores, "kind": "oracle",
+    t1 = []
+    for s in order[:len(per)]:
+        t1.append(one(s, 1))
+        if sum(t1) > seconds / 4:
+            break
+    n1 = len(t1)
+    return {"value": len(per) / sum(per), "unit": "RG updates/s (instance updates)", "cores": cores,
+            "kind": "oracle",
             "sample": "%d of %d instances (smallest N*H first: biased towards cheap ones), one update each, "
-                      "FP64 k-section, %.1f s" % (done, len(b["N"]), t_total)}
+                      "FP64 k-section, %.1f s" % (len(per), len(b["N"]), sum(per)),
+            "one_core": {"value": n1 / sum(t1), "unit": "RG updates/s (instance updates)", "cores": 1,
+                         "threaded_same_instances": n1 / sum(per[:n1]),
+                         "sample": "the first %d of those instances on one host thread, %.1f s" % (n1, sum(t1))}}
 
 
 def run_batch(args):
@@ -993,9 +1027,20 @@ def sweep_cpu(p, seconds, cores):
             _, _, _, steps = O.eval_candidates(p, c, x_t, v_prev, r, kappas, d, nthreads=cores)
         dt = time.perf_counter() - t0
         if dt > seconds / 4 or n >= 4096:
-            return {"value": steps / dt, "unit": "trajectory-steps/s", "cores": cores, "kind": "oracle",
-                    "sample": "%d scenarios x %d candidates x horizon %d, FP64, %.1f s" % (n, SWEEP_M, SWEEP_H, dt)}
+            break
         n *= 2
+    # the sequential oracle on one thread, over the first n / cores scenarios
+    n1 = max(16, n // max(cores, 1))
+    with O.param_multipliers(m[:n1]):
+        t1 = time.perf_counter()
+        _, _, _, steps1 = O.eval_candidates(p, O.cfg(H=SWEEP_H, N=n1), x_t, v_prev, r, kappas, d[:, :, :n1],
+                                            nthreads=1)
+        dt1 = time.perf_counter() - t1
+    return {"value": steps / dt, "unit": "trajectory-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d scenarios x %d candidates x horizon %d, FP64, %.1f s" % (n, SWEEP_M, SWEEP_H, dt),
+            "one_core": {"value": steps1 / dt1, "unit": "trajectory-steps/s", "cores": 1,
+                         "sample": "%d scenarios x %d candidates x horizon %d, FP64, one host thread, %.1f s"
+                                   % (n1, SWEEP_M, SWEEP_H, dt1)}}
 
 
 def run_sweep(args):

@@ -1,0 +1,57 @@
+"""Host-side legs of bench.py (no GPU): the CPU-oracle baselines and the
+reference arm's JSON line.
+
+The reference arm times the FP64 oracle's closed loop (plain joint
+bisection, Alg. 1 on all scenarios) on the host cores and prints one JSON
+line with the contract's keys; the CPU baselines of the batched and sweep
+workloads report the threaded oracle and the sequential one beside it.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 1 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_sweep_cpu_baseline_reports_threaded_and_one_core():
+    from paper_2510_08288_gb300 import inputs
+    c = bench.sweep_cpu(inputs.fc3_params(), 0.01, 2)
+    assert c["kind"] == "oracle" and c["cores"] == 2 and c["value"] > 0
+    assert c["one_core"]["cores"] == 1 and c["one_core"]["value"] > 0
+    assert c["unit"] == c["one_core"]["unit"] == "trajectory-steps/s"
+
+
+def test_batch_cpu_baseline_reports_threaded_and_one_core():
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    p = inputs.fc3_params()
+    b = inputs.batched_instances(bench.BATCH_S, bench.BATCH_SEED)
+    x0 = np.array([O.equilibrium(p, v) for v in b["v_prev"]]) * b["xfac"]
+    c = bench.batch_cpu(p, b, x0, b["r"], 0.01, 2)
+    assert c["kind"] == "oracle" and c["cores"] == 2 and c["value"] > 0
+    one = c["one_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["threaded_same_instances"] > 0
