@@ -575,7 +575,7 @@ def run_gpu(args):
             cpu["one_core"] = {"value": v1, "unit": UNIT, "cores": 1,
                                "threaded_same_update": 1.0 / cone,
                                "sample": "first update of the same closed loop, one host thread",
-                               "kappa_equal_to_threaded": k1 == ckap[0]}
+                               "kappa_equal_to_threaded": bool(k1 == float(ckap[0]))}
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,

@@ -43,6 +43,7 @@ def test_sweep_cpu_baseline_reports_threaded_and_one_core():
     assert c["kind"] == "oracle" and c["cores"] == 2 and c["value"] > 0
     assert c["one_core"]["cores"] == 1 and c["one_core"]["value"] > 0
     assert c["unit"] == c["one_core"]["unit"] == "trajectory-steps/s"
+    json.dumps(c)
 
 
 def test_batch_cpu_baseline_reports_threaded_and_one_core():
@@ -55,3 +56,16 @@ def test_batch_cpu_baseline_reports_threaded_and_one_core():
     assert c["kind"] == "oracle" and c["cores"] == 2 and c["value"] > 0
     one = c["one_core"]
     assert one["cores"] == 1 and one["value"] > 0 and one["threaded_same_instances"] > 0
+    json.dumps(c)
+
+
+def test_closed_loop_cpu_legs_agree_and_serialise():
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    x0 = O.equilibrium(inputs.fc3_params(), bench.V0)
+    r = inputs.staircase(1000, 8, 125, bench.SEED)
+    val, n, secs, kaps, first = bench.cpu_oracle_closed_loop(x0, r, 0.01, 2)
+    assert n == 1 and val > 0 and first > 0
+    v1, k1 = bench.cpu_oracle_one_core(x0, r)
+    assert v1 > 0 and k1 == float(kaps[0])  # thread count does not change the oracle's result
+    json.dumps({"value": val, "one_core": v1, "kappa": k1})
