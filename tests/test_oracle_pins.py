@@ -400,3 +400,67 @@ def test_param_multipliers_scale_scenario_parameters(orc, params):
     # multipliers of one make no difference
     with orc.param_multipliers(np.ones_like(m)):
         assert [orc.rollout(params, c, x, 180.0, d, k)[0] for k in range(N)] == nominal
+
+
+# ------------------------------------------------- adjoint's objective ----
+def _slack_by_steps(orc, p, x_t, I, d, k, jstar, dt=0.01, y_min=1.9):
+    """s_jstar^k by the real-valued primitives one step at a time: jstar RK4
+    steps of scenario k, each followed by its disturbance, then h - y_min."""
+    x = np.array(x_t, dtype=float)
+    for j in range(jstar):
+        x = orc.rk4_step(p, x, I, dt) + d[:, j, k]
+    return orc.output(p, x, I) - y_min
+
+
+def test_min_slack_argmin_is_the_brute_force_minimum(orc, params):
+    """The adjoint's objective g = min_k min_j s_j^k over the full horizon
+    (j = 0 included) and its first argmin in (k, then j) order, against every
+    slack computed step by step from the real primitives."""
+    H, N = 40, 4
+    x = orc.equilibrium(params, 100.0) * np.array([1.03, 0.98, 1.01])
+    d = orc.sample_disturbances(11, 0, N, H, inputs.DIST_AMP)
+    for kappa in (0.0, 0.05, 0.3):
+        I = orc.governed(100.0, 250.0, kappa)
+        S = np.array([[_slack_by_steps(orc, params, x, I, d, k, j) for j in range(H + 1)] for k in range(N)])
+        g, k, j = orc.min_slack_argmin(params, orc.cfg(H=H, N=N), x, I, d)
+        assert g == pytest.approx(S.min(), rel=1e-13, abs=1e-13)
+        assert (k, j) == tuple(int(i) for i in np.unravel_index(np.argmin(S), S.shape))
+
+
+@pytest.mark.parametrize("with_multipliers", [False, True])
+@pytest.mark.parametrize("k,jstar", [(0, 0), (1, 17), (2, 40)])
+def test_slack_gradient_matches_central_differences(orc, params, k, jstar, with_multipliers):
+    """The complex-step gradient of s_jstar^k (kappa, x_t, theta; Squire and
+    Trapp 1998, a separate complex-valued copy of the model) against central
+    differences of the real-valued primitives with relative steps 1e-6; its
+    real part equals the real-valued slack.  With parameter multipliers the
+    derivative is taken with respect to the nominal theta."""
+    H, N, v_prev, r, kappa = 40, 3, 100.0, 250.0, 0.1
+    x = orc.equilibrium(params, v_prev) * np.array([1.02, 0.99, 1.01])
+    d = orc.sample_disturbances(7, 0, N, H, inputs.DIST_AMP)
+    m = orc.sample_param_multipliers(3, 0, N, 0.1, (1 << orc.nparam()) - 1) if with_multipliers else None
+    c = orc.cfg(H=H, N=N)
+
+    def s_real(p, x_t, kap):
+        pk = p * m[k] if m is not None else p
+        return _slack_by_steps(orc, pk, x_t, orc.governed(v_prev, r, kap), d, k, jstar)
+
+    with orc.param_multipliers(m):
+        s, grad = orc.slack_grad(params, c, x, v_prev, r, kappa, d, k, jstar)
+    assert s == pytest.approx(s_real(params, x, kappa), rel=1e-13, abs=1e-14)
+    fd = [(s_real(params, x, kappa + 1e-6) - s_real(params, x, kappa - 1e-6)) / 2e-6]
+    for i in range(3):
+        h = 1e-6 * abs(x[i])
+        e = np.zeros(3)
+        e[i] = h
+        fd.append((s_real(params, x + e, kappa) - s_real(params, x - e, kappa)) / (2 * h))
+    for i in range(orc.nparam()):
+        h = 1e-6 * abs(params[i]) if params[i] != 0 else 1e-6
+        e = np.zeros(orc.nparam())
+        e[i] = h
+        fd.append((s_real(params + e, x, kappa) - s_real(params - e, x, kappa)) / (2 * h))
+    fd = np.array(fd)
+    scale = np.abs(grad) + np.abs(fd)
+    assert np.all(np.abs(grad - fd) <= 1e-5 * scale + 1e-12), np.max(np.abs(grad - fd) / np.maximum(scale, 1e-300))
+    if jstar > 0:
+        assert np.count_nonzero(grad) == grad.size  # every parameter reaches a state after one step
