@@ -10,11 +10,13 @@
 //   forward  adjoint_forward_kernel: one thread per scenario, full horizon,
 //            the state saved every `checkpoint` steps, per-lane min and argmin;
 //   argmin   adjoint_argmin_kernel: the first (k, then j) attaining the min;
-//   reverse  adjoint_reverse_kernel: one thread; each checkpoint segment is
-//            recomputed forward into local memory, then swept backwards with
-//            the vector-Jacobian products of the FC3 right-hand side; the
-//            adjoints of the folded constants are mapped to the 27 model
-//            parameters, to x_t and (through the setpoint) to kappa.
+//   reverse  adjoint_reverse_kernel: the checkpoint segments before j* are
+//            recomputed in parallel (one thread each), storing every step's
+//            state and RK4 stage points; one thread then sweeps them
+//            backwards with the vector-Jacobian products of the FC3
+//            right-hand side; the adjoints of the folded constants are
+//            mapped to the 27 model parameters, to x_t and (through the
+//            setpoint) to kappa.
 #include <cfloat>
 #include <cmath>
 
@@ -97,36 +99,45 @@ __device__ void fc3_rhs_vjp(const Fc3K<T>& K, const CandK<T>& C, T q_ca, T w, T 
   qb_sm += qsm_b;
 }
 
-// Adjoint of one RK4 step q+ = q + dt/6 (k1 + 2 k2 + 2 k3 + k4) (+ d): given
-// the adjoint (l0, l1, l2) of q+, overwrites it with the adjoint of q.
+// The RK4 stage points of one step from x: y2 = x + dt/2 k1, y3 = x + dt/2 k2,
+// y4 = x + dt k3 (k_i the right-hand side at the previous stage point);
+// y[0..2] = y2, y[3..5] = y3, y[6..8] = y4.  They do not depend on the adjoint.
 template <typename T>
-__device__ void rk4_step_vjp(const Fc3K<T>& K, const CandK<T>& C, T dt, T q_ca, T w, T q_sm,
-                             T& l0, T& l1, T& l2, ConstAdj<T>& g) {
+__device__ __forceinline__ void rk4_stage_points(const Fc3K<T>& K, const CandK<T>& C, T dt, T q_ca, T w,
+                                                 T q_sm, T* y) {
+  const T h2 = T(0.5) * dt;
+  T a, b, c;
+  fc3_rhs<T>(K, C, q_ca, w, q_sm, a, b, c);
+  y[0] = q_ca + h2 * a; y[1] = w + h2 * b; y[2] = q_sm + h2 * c;
+  fc3_rhs<T>(K, C, y[0], y[1], y[2], a, b, c);
+  y[3] = q_ca + h2 * a; y[4] = w + h2 * b; y[5] = q_sm + h2 * c;
+  fc3_rhs<T>(K, C, y[3], y[4], y[5], a, b, c);
+  y[6] = q_ca + dt * a; y[7] = w + dt * b; y[8] = q_sm + dt * c;
+}
+
+// Adjoint of one RK4 step q+ = q + dt/6 (k1 + 2 k2 + 2 k3 + k4) (+ d) at state
+// q with stage points y (rk4_stage_points): given the adjoint (l0, l1, l2) of
+// q+, overwrites it with the adjoint of q; the constants' adjoints accumulate
+// into g.
+template <typename T>
+__device__ void rk4_step_vjp_at(const Fc3K<T>& K, const CandK<T>& C, T dt, T q_ca, T w, T q_sm,
+                                const T* y, T& l0, T& l1, T& l2, ConstAdj<T>& g) {
   const T h2 = T(0.5) * dt, h6 = dt / T(6);
-  // forward stages
-  T a1, b1, c1, a2, b2, c2, a3, b3, c3;
-  fc3_rhs<T>(K, C, q_ca, w, q_sm, a1, b1, c1);
-  const T y2_0 = q_ca + h2 * a1, y2_1 = w + h2 * b1, y2_2 = q_sm + h2 * c1;
-  fc3_rhs<T>(K, C, y2_0, y2_1, y2_2, a2, b2, c2);
-  const T y3_0 = q_ca + h2 * a2, y3_1 = w + h2 * b2, y3_2 = q_sm + h2 * c2;
-  fc3_rhs<T>(K, C, y3_0, y3_1, y3_2, a3, b3, c3);
-  const T y4_0 = q_ca + dt * a3, y4_1 = w + dt * b3, y4_2 = q_sm + dt * c3;
-  // reverse
   T q0 = l0, q1 = l1, q2 = l2;                  // identity part
   T k1_0 = h6 * l0, k1_1 = h6 * l1, k1_2 = h6 * l2;
   T k2_0 = T(2) * h6 * l0, k2_1 = T(2) * h6 * l1, k2_2 = T(2) * h6 * l2;
   T k3_0 = T(2) * h6 * l0, k3_1 = T(2) * h6 * l1, k3_2 = T(2) * h6 * l2;
   const T k4_0 = h6 * l0, k4_1 = h6 * l1, k4_2 = h6 * l2;
   T y0 = 0, y1 = 0, y2 = 0;
-  fc3_rhs_vjp<T>(K, C, y4_0, y4_1, y4_2, k4_0, k4_1, k4_2, y0, y1, y2, g);
+  fc3_rhs_vjp<T>(K, C, y[6], y[7], y[8], k4_0, k4_1, k4_2, y0, y1, y2, g);
   q0 += y0; q1 += y1; q2 += y2;
   k3_0 += dt * y0; k3_1 += dt * y1; k3_2 += dt * y2;
   y0 = y1 = y2 = 0;
-  fc3_rhs_vjp<T>(K, C, y3_0, y3_1, y3_2, k3_0, k3_1, k3_2, y0, y1, y2, g);
+  fc3_rhs_vjp<T>(K, C, y[3], y[4], y[5], k3_0, k3_1, k3_2, y0, y1, y2, g);
   q0 += y0; q1 += y1; q2 += y2;
   k2_0 += h2 * y0; k2_1 += h2 * y1; k2_2 += h2 * y2;
   y0 = y1 = y2 = 0;
-  fc3_rhs_vjp<T>(K, C, y2_0, y2_1, y2_2, k2_0, k2_1, k2_2, y0, y1, y2, g);
+  fc3_rhs_vjp<T>(K, C, y[0], y[1], y[2], k2_0, k2_1, k2_2, y0, y1, y2, g);
   q0 += y0; q1 += y1; q2 += y2;
   k1_0 += h2 * y0; k1_1 += h2 * y1; k1_2 += h2 * y2;
   y0 = y1 = y2 = 0;
@@ -190,16 +201,23 @@ adjoint_forward_kernel(const Launch L, const double* __restrict__ d, const doubl
   const size_t HN = static_cast<size_t>(H) * N;
   T smin = fc3_output<T>(C, q_ca, q_sm) - y_min;
   int arg = 0;
+  // the disturbances are read two steps ahead of their use (steps past the
+  // horizon re-read the last one), so that their latency hides behind the
+  // two RK4 steps in between
+  auto at = [&](int j) { return static_cast<size_t>(j < H ? j : H - 1) * N + k; };
+  double c0 = d[at(0)], c1 = d[HN + at(0)], c2 = d[2 * HN + at(0)];
+  double n0 = d[at(1)], n1 = d[HN + at(1)], n2 = d[2 * HN + at(1)];
   for (int j = 0; j < H; ++j) {
+    const size_t of = at(j + 2);
+    const double f0 = d[of], f1 = d[HN + of], f2 = d[2 * HN + of];
     if (j % checkpoint == 0) {
       double* c = ckpt + (static_cast<size_t>(k) * nseg + j / checkpoint) * 3;
       c[0] = q_ca; c[1] = w; c[2] = q_sm;
     }
-    const size_t o = static_cast<size_t>(j) * N + k;
-    const T e0 = static_cast<T>(d[o]), e1 = static_cast<T>(d[HN + o]),
-            e2 = static_cast<T>(d[2 * HN + o]);
     rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-    q_ca += e0; w += e1; q_sm += e2;
+    q_ca += static_cast<T>(c0); w += static_cast<T>(c1); q_sm += static_cast<T>(c2);
+    c0 = n0; c1 = n1; c2 = n2;
+    n0 = f0; n1 = f1; n2 = f2;
     const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
     if (s < smin) { smin = s; arg = j + 1; }
   }
@@ -239,18 +257,34 @@ __global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
   }
 }
 
-// Reverse sweep of trajectory k* from j* to 0 (one thread), then the chain
-// rule from the folded constants to the model parameters and kappa.
-// seg: scratch of checkpoint * 3 values for the recomputed segment.
+// Values stored per step of the recomputed trajectory: x_j and the three
+// stage points of step j.
+constexpr int kSegVals = 12;
+constexpr int kRevThreads = 128;
+
+// Reverse sweep of trajectory k* from j* to 0, then the chain rule from the
+// folded constants to the model parameters and kappa.  One block:
+//   phase 1, all threads: the checkpoint segments before j* are recomputed
+//     in parallel, one segment per thread, storing for each step j its state
+//     and stage points in seg[j * kSegVals ...], and x_{j*} after the last one;
+//   phase 2, thread 0: the adjoint recursion from j* down to 0 over the
+//     stored steps (the only serial part), each step's values loaded one step
+//     ahead.
+// seg: scratch of (j* + 1) * kSegVals values (at most (H + 1) * kSegVals).
 // out[0] = dg/dkappa, out[1..3] = dg/dx_t, out[4..4+NPARAM) = dg/dtheta.
 template <typename T>
-__global__ void adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
-                                       double v_prev, double r, double kappa, int checkpoint,
-                                       const double* __restrict__ ckpt, const long long* kj,
-                                       T* __restrict__ seg, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(kRevThreads)
+adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
+                       double v_prev, double r, double kappa, int checkpoint,
+                       const double* __restrict__ ckpt, const long long* kj,
+                       T* __restrict__ seg, double* __restrict__ out) {
+  if (blockIdx.x != 0) return;
   const double v = governed(v_prev, r, kappa);
   const int N = L.N, H = L.H;
+  if (kj[0] < 0 || kj[0] >= N || kj[1] < 0 || kj[1] > H) {  // no argmin: same for every thread
+    if (threadIdx.x < 4 + RRG_NPARAM) out[threadIdx.x] = NAN;
+    return;
+  }
   const int k = static_cast<int>(kj[0]), jstar = static_cast<int>(kj[1]);
   double P[RRG_NPARAM];
   scenario_params(L, k, P);
@@ -259,44 +293,55 @@ __global__ void adjoint_reverse_kernel(const Launch L, const double* __restrict_
   const T dt = static_cast<T>(L.dt);
   const int nseg = H / checkpoint + 1;
   const size_t HN = static_cast<size_t>(H) * N;
-  ConstAdj<T> g{};
-  // the state at j*: recompute from its checkpoint
-  T q_ca, w, q_sm;
-  {
-    int c = jstar / checkpoint;
-    const int last = (H - 1) / checkpoint;  // last stored checkpoint
-    if (c > last) c = last;
-    const double* cp = ckpt + (static_cast<size_t>(k) * nseg + c) * 3;
-    q_ca = static_cast<T>(cp[0]); w = static_cast<T>(cp[1]); q_sm = static_cast<T>(cp[2]);
-    for (int j = c * checkpoint; j < jstar; ++j) {
-      const size_t o = static_cast<size_t>(j) * N + k;
-      rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-      q_ca += static_cast<T>(d[o]);
-      w += static_cast<T>(d[HN + o]);
-      q_sm += static_cast<T>(d[2 * HN + o]);
-    }
-  }
-  // output at j*: s = y_scale (q_sm - q_ca) - y_min
-  g.y_scale += q_sm - q_ca;
-  T l0 = -C.y_scale, l1 = T(0), l2 = C.y_scale;
-  // backwards over the segments that end at or before j*
-  for (int c = (jstar - 1) / checkpoint; jstar > 0 && c >= 0; --c) {
+  const double* ck = ckpt + static_cast<size_t>(k) * nseg * 3;
+  // phase 1: segment c covers steps c * checkpoint .. min((c + 1) * checkpoint, j*) - 1
+  const int nc = jstar > 0 ? (jstar - 1) / checkpoint + 1 : 0;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     const int j0 = c * checkpoint;
-    const int j1 = (j0 + checkpoint < jstar) ? j0 + checkpoint : jstar;  // steps j0..j1-1
-    const double* cp = ckpt + (static_cast<size_t>(k) * nseg + c) * 3;
-    T a = static_cast<T>(cp[0]), b = static_cast<T>(cp[1]), e = static_cast<T>(cp[2]);
+    const int j1 = (j0 + checkpoint < jstar) ? j0 + checkpoint : jstar;
+    T a = static_cast<T>(ck[c * 3]), b = static_cast<T>(ck[c * 3 + 1]), e = static_cast<T>(ck[c * 3 + 2]);
     for (int j = j0; j < j1; ++j) {
-      T* sj = seg + static_cast<size_t>(j - j0) * 3;
+      T* sj = seg + static_cast<size_t>(j) * kSegVals;
       sj[0] = a; sj[1] = b; sj[2] = e;
+      rk4_stage_points<T>(K, C, dt, a, b, e, sj + 3);
       const size_t o = static_cast<size_t>(j) * N + k;
       rk4_step<T>(K, C, dt, a, b, e);
       a += static_cast<T>(d[o]);
       b += static_cast<T>(d[HN + o]);
       e += static_cast<T>(d[2 * HN + o]);
     }
-    for (int j = j1 - 1; j >= j0; --j) {
-      const T* sj = seg + static_cast<size_t>(j - j0) * 3;
-      rk4_step_vjp<T>(K, C, dt, sj[0], sj[1], sj[2], l0, l1, l2, g);
+    if (j1 == jstar) {
+      T* sj = seg + static_cast<size_t>(jstar) * kSegVals;
+      sj[0] = a; sj[1] = b; sj[2] = e;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  ConstAdj<T> g{};
+  // output at j*: s = y_scale (q_sm - q_ca) - y_min (x_0 is checkpoint 0)
+  T q_ca, q_sm;
+  if (jstar == 0) {
+    q_ca = static_cast<T>(ck[0]);
+    q_sm = static_cast<T>(ck[2]);
+  } else {
+    q_ca = seg[static_cast<size_t>(jstar) * kSegVals];
+    q_sm = seg[static_cast<size_t>(jstar) * kSegVals + 2];
+  }
+  g.y_scale += q_sm - q_ca;
+  T l0 = -C.y_scale, l1 = T(0), l2 = C.y_scale;
+  // phase 2: backwards over the stored steps
+  if (jstar > 0) {
+    T cur[kSegVals];
+#pragma unroll
+    for (int u = 0; u < kSegVals; ++u) cur[u] = seg[static_cast<size_t>(jstar - 1) * kSegVals + u];
+    for (int j = jstar - 1; j >= 0; --j) {
+      T nxt[kSegVals];
+      const int jn = j > 0 ? j - 1 : 0;
+#pragma unroll
+      for (int u = 0; u < kSegVals; ++u) nxt[u] = seg[static_cast<size_t>(jn) * kSegVals + u];
+      rk4_step_vjp_at<T>(K, C, dt, cur[0], cur[1], cur[2], cur + 3, l0, l1, l2, g);
+#pragma unroll
+      for (int u = 0; u < kSegVals; ++u) cur[u] = nxt[u];
     }
   }
   // chain rule to the parameter vector (binary64)
@@ -364,18 +409,23 @@ __global__ void adjoint_reverse_kernel(const Launch L, const double* __restrict_
 
 // Host side: enqueue forward, argmin and reverse on the handle's stream.
 // ckpt: N * (H / checkpoint + 1) * 3 doubles; lane_min/lane_arg: N each;
-// seg: checkpoint * 3 doubles; d_kj: 2; d_out: 1 + 3 + RRG_NPARAM.
+// seg: (H + 1) * 12 doubles; d_kj: 2; d_out: 1 + 3 + RRG_NPARAM.
 cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
                            double kappa, int checkpoint, double* ckpt, double* lane_min,
                            int* lane_arg, double* seg, double* d_g, long long* d_kj,
                            double* d_out) {
-  const int blocks = (L.N + 127) / 128;
+  // one warp per block until the blocks of 128 threads would fill every SM:
+  // each scenario is one dependent chain, so spreading them over SMs costs
+  // nothing and puts more SMs' binary64 units to work
+  const int sms = L.sms > 0 ? L.sms : 152;
+  const int threads = (L.N >= 128 * sms) ? 128 : 32;
+  const int blocks = (L.N + threads - 1) / threads;
   if (fp64) {
-    adjoint_forward_kernel<double><<<blocks, 128, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
-                                                                 checkpoint, ckpt, lane_min, lane_arg);
+    adjoint_forward_kernel<double><<<blocks, threads, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
+                                                                     checkpoint, ckpt, lane_min, lane_arg);
   } else {
-    adjoint_forward_kernel<float><<<blocks, 128, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
-                                                                checkpoint, ckpt, lane_min, lane_arg);
+    adjoint_forward_kernel<float><<<blocks, threads, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
+                                                                    checkpoint, ckpt, lane_min, lane_arg);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -383,12 +433,12 @@ cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (fp64) {
-    adjoint_reverse_kernel<double><<<1, 32, 0, L.stream>>>(L, L.d64, v_prev, r, kappa, checkpoint,
-                                                           ckpt, d_kj, seg, d_out);
+    adjoint_reverse_kernel<double><<<1, kRevThreads, 0, L.stream>>>(L, L.d64, v_prev, r, kappa,
+                                                                     checkpoint, ckpt, d_kj, seg, d_out);
   } else {
-    adjoint_reverse_kernel<float><<<1, 32, 0, L.stream>>>(L, L.d64, v_prev, r, kappa, checkpoint,
-                                                          ckpt, d_kj, reinterpret_cast<float*>(seg),
-                                                          d_out);
+    adjoint_reverse_kernel<float><<<1, kRevThreads, 0, L.stream>>>(L, L.d64, v_prev, r, kappa, checkpoint,
+                                                                    ckpt, d_kj, reinterpret_cast<float*>(seg),
+                                                                    d_out);
   }
   return cudaGetLastError();
 }

@@ -46,7 +46,7 @@ struct rrg_ctx {
   double* adj_lane_min = nullptr;
   int* adj_lane_arg = nullptr;
   double* adj_seg = nullptr;
-  int adj_seg_cap = 0;
+  size_t adj_seg_cap = 0;
   double* adj_out = nullptr;   // [0] g, [1..2] k*, j* (as long long), [3..] gradient
   // the captured one-update graph of the last closed loop, reused while the
   // run's pointers and indices stay the same
@@ -989,12 +989,14 @@ int rrg_slack_gradient(rrg_handle h, const double* x_t, double v_prev, double r_
     CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_lane_arg), N * sizeof(int)));
     CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_out), (3 + 4 + RRG_NPARAM) * sizeof(double)));
   }
-  if (checkpoint > h->adj_seg_cap) {
+  // every step's state and stage points of the reverse sweep: (H + 1) * 12 values
+  const size_t seg_need = (H + 1) * 12;
+  if (seg_need > h->adj_seg_cap) {
     if (h->adj_seg) cudaFree(h->adj_seg);
     h->adj_seg = nullptr;
     h->adj_seg_cap = 0;
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_seg), static_cast<size_t>(checkpoint) * 3 * sizeof(double)));
-    h->adj_seg_cap = checkpoint;
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_seg), seg_need * sizeof(double)));
+    h->adj_seg_cap = seg_need;
   }
   std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
   CK(cudaMemcpyAsync(h->io_dev, h->io_h, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));

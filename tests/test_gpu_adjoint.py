@@ -50,6 +50,26 @@ def test_adjoint_fp64_matches_complex_step(R, orc, params, checkpoint):
             assert np.all(np.abs(grad - gro) <= 1e-7 * scale + 1e-14)
 
 
+@pytest.mark.parametrize("checkpoint", [1, 7, 50, 800])
+def test_adjoint_late_argmin_matches_complex_step(R, orc, params, checkpoint):
+    """kappa = 0 (hold) from the 100 A equilibrium: the minimum slack comes
+    late in the horizon (step 489 of 800), so the reverse sweep spans many
+    checkpoint segments (489 at checkpoint 1, a partial last one at 7 and
+    50, one at 800), all recomputed in parallel before the adjoint sweep."""
+    N, H = 32, 800
+    x_t = orc.equilibrium(params, 100.0)
+    with _gov(R, params, N, H) as g:
+        g.sample_scenarios(9, 0)
+        d = g.get_scenarios()
+        gv, grad, ks, js = g.slack_gradient(x_t, 100.0, 250.0, 0.0, checkpoint, R.FP64)
+    c = orc.cfg(H=H, N=N, early_exit=0)
+    go, ko, jo = orc.min_slack_argmin(params, c, x_t, orc.governed(100.0, 250.0, 0.0), d)
+    assert (ks, js) == (ko, jo) and jo > 400
+    assert gv == pytest.approx(go, rel=1e-10, abs=1e-12)
+    _, gro = orc.slack_grad(params, c, x_t, 100.0, 250.0, 0.0, d, ko, jo)
+    np.testing.assert_allclose(grad, gro, rtol=1e-7, atol=1e-14 * np.max(np.abs(gro)))
+
+
 def test_adjoint_fp32_close_to_fp64(R, orc, params):
     N, H = 64, 400
     x_t = orc.equilibrium(params, 120.0)
