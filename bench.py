@@ -947,6 +947,17 @@ def run_adjoint(args):
                     ts.append(1e3 * (time.perf_counter() - t0))
             out_legs[name] = {"ms": statistics.median(ts), "g": gv, "argmin": [ks, js],
                               "dg_dkappa": float(grad[0])}
+        # the forward pass's device time per launch (CUDA events on the
+        # handle's stream around it), over K more binary32 gradients
+        g.reset_stats()
+        g.set_profiling(True)
+        for i in range(K):
+            g.slack_gradient(x_t, v_prev, r, 0.1, C, R.FP32)
+        stp = g.stats()
+        g.set_profiling(False)
+        fwd_ms = stp["rollout_ms"] / max(1, stp["timed_rollouts"])
+        launches_per_gradient = stp["launches"] / max(1, K)
+        chain_cycles = g.step_latency(v_prev + 0.1 * (r - v_prev), H)
         tol = 2.0 ** -19
         for name, prec in (("newton_fp32_recheck_eval", R.FP32),):
             ts, res = [], None
@@ -979,16 +990,65 @@ def run_adjoint(args):
     out_legs["newton_fp32_recheck_eval"]["within_one_bracket_of_bisect20"] = bool(
         abs(out_legs["newton_fp32_recheck_eval"]["kappa"] - kb) <= 2 * tol)
     main = out_legs["gradient_fp32"]
-    out = {"metric": ADJ_METRIC, "value": 1e3 / main["ms"], "unit": "gradients/s", "n_gpus": 1, "steps": K,
+    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    achieved = N * H * FLOPS_PER_STEP / (fwd_ms * 1e-3) / 1e12
+    step_cycles = fwd_ms * 1e-3 * sm_hz / H
+    cpu = None if args.no_cpu_baseline else adjoint_cpu(p, x_t, v_prev, r, N, H, args.cpu_seconds,
+                                                        out_legs["gradient_fp64"]["argmin"])
+    value = 1e3 / main["ms"]
+    out = {"metric": ADJ_METRIC, "value": value, "unit": "gradients/s", "n_gpus": 1, "steps": K,
            "warmup": W, "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "discrete adjoint of min slack on FC3: 4,096 scenarios (seed 3) x 1,000 RK4 "
                                   "steps, checkpoint every 50 steps, x_t at the 100 A equilibrium, r_t = 250 A, "
                                   "kappa = 0.1; Newton search to 2^-19 vs 20-iteration bisection",
-                      "timing": "median host time per synchronous call"},
+                      "timing": "median host time per synchronous call (x_t in from and the gradient out to "
+                                "host memory: value and e2e are the same measurement)",
+                      "l2": "scenarios (98 MB binary64) re-read by every call; no flush"},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                        "kernel": "adjoint_forward_kernel<float>", "avg_launch_ms": fwd_ms,
+                        "launches": stp["timed_rollouts"],
+                        "timing": "CUDA events around the forward pass of %d more binary32 gradients" % K,
+                        "flops_per_traj_step": FLOPS_PER_STEP, "traj_steps_per_launch": N * H,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                        "issue_ceiling": ISSUE_CEILING,
+                        "frac_of_issue_ceiling": achieved / FP32_PEAK_TFLOPS / ISSUE_CEILING,
+                        "latency": {"cycles_per_step": step_cycles, "chain_cycles_per_step": chain_cycles,
+                                    "frac": chain_cycles / step_cycles,
+                                    "basis": "forward pass time over its %d dependent steps at the sampled SM "
+                                             "clock (4,096 scenarios: 128 warps, one per SM); chain: "
+                                             "rrg_step_latency, one warp, the rollout kernel's step" % H}},
+           "cpu_baseline": cpu,
+           "e2e": {"value": value, "unit": "gradients/s", "h2d_bytes_per_step": 3 * 8,
+                   "d2h_bytes_per_step": (3 + 4 + 27) * 8},
+           "gpu_launches": int(round(launches_per_gradient * K)),
            "legs": out_legs, "clocks": clk}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def adjoint_cpu(p, x_t, v_prev, r, N, H, seconds, gpu_argmin):
+    """The FP64 oracle's gradient of the same workload, whole: min slack and
+    its argmin over every scenario and step, then the complex-step gradient
+    at the argmin; repeated while the time stays under `seconds`."""
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    c = O.cfg(H=H, N=N, early_exit=0)
+    d = O.sample_disturbances(3, 0, N, H, inputs.DIST_AMP)
+    I = O.governed(v_prev, r, 0.1)
+    n, t, kj = 0, 0.0, None
+    while n == 0 or t + t / n < seconds:
+        t0 = time.perf_counter()
+        g, k, j = O.min_slack_argmin(p, c, x_t, I, d)
+        O.slack_grad(p, c, x_t, v_prev, r, 0.1, d, k, j)
+        t += time.perf_counter() - t0
+        n += 1
+        kj = [k, j]
+    return {"value": n / t, "unit": "gradients/s", "cores": 1, "kind": "oracle",
+            "sample": "%d whole gradient(s) of the same workload (4,096 x 1,000 forward, complex-step "
+                      "gradient at the argmin), FP64, one host thread, %.1f s" % (n, t),
+            "argmin_equal_to_gpu_fp64": kj == list(gpu_argmin)}
 
 
 # ------------------------------------------------------------------ sweep --

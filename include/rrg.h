@@ -363,7 +363,8 @@ RRG_API int rrg_newton_search(rrg_handle h, const double *x_t, double r_t, doubl
 
 /* Profiling: while on, every rollout and recheck launch is bracketed by CUDA
  * events on the handle's stream and their durations are summed into
- * rrg_stats.rollout_ms / recheck_ms. */
+ * rrg_stats.rollout_ms / recheck_ms.  The forward pass of rrg_slack_gradient
+ * (every scenario over the full horizon) counts as a rollout launch. */
 RRG_API int rrg_set_profiling(rrg_handle h, int on);
 
 /* Reads the counters (synchronises the handle's stream).  Host out. */

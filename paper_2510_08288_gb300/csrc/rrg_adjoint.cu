@@ -175,6 +175,9 @@ __device__ CandK<T> cand_of(const double* P, double I) {
   return C;
 }
 
+// Register slots of the forward pass's disturbance prefetch ring.
+constexpr int kFwdRing = 8;
+
 // Forward: one thread per scenario, full horizon; state saved at j = 0, C,
 // 2C, ... (j < H) into ckpt[(k * nseg + c) * 3 + i]; per-lane min slack and
 // the first step attaining it.  The binary64 scenarios are read and rounded
@@ -201,25 +204,35 @@ adjoint_forward_kernel(const Launch L, const double* __restrict__ d, const doubl
   const size_t HN = static_cast<size_t>(H) * N;
   T smin = fc3_output<T>(C, q_ca, q_sm) - y_min;
   int arg = 0;
-  // the disturbances are read two steps ahead of their use (steps past the
-  // horizon re-read the last one), so that their latency hides behind the
-  // two RK4 steps in between
+  // the disturbances pass through a ring of kFwdRing register slots: step j
+  // takes slot j % kFwdRing and refills it with step j + kFwdRing's values
+  // (steps past the horizon re-read the last one), so each load has
+  // kFwdRing steps to arrive; the unrolled loop keeps the slots in registers
   auto at = [&](int j) { return static_cast<size_t>(j < H ? j : H - 1) * N + k; };
-  double c0 = d[at(0)], c1 = d[HN + at(0)], c2 = d[2 * HN + at(0)];
-  double n0 = d[at(1)], n1 = d[HN + at(1)], n2 = d[2 * HN + at(1)];
-  for (int j = 0; j < H; ++j) {
-    const size_t of = at(j + 2);
-    const double f0 = d[of], f1 = d[HN + of], f2 = d[2 * HN + of];
-    if (j % checkpoint == 0) {
-      double* c = ckpt + (static_cast<size_t>(k) * nseg + j / checkpoint) * 3;
-      c[0] = q_ca; c[1] = w; c[2] = q_sm;
+  double ring[kFwdRing][3];
+#pragma unroll
+  for (int u = 0; u < kFwdRing; ++u) {
+    const size_t o = at(u);
+    ring[u][0] = d[o]; ring[u][1] = d[HN + o]; ring[u][2] = d[2 * HN + o];
+  }
+  for (int j0 = 0; j0 < H; j0 += kFwdRing) {
+#pragma unroll
+    for (int u = 0; u < kFwdRing; ++u) {
+      const int j = j0 + u;
+      if (j >= H) break;
+      const T e0 = static_cast<T>(ring[u][0]), e1 = static_cast<T>(ring[u][1]),
+              e2 = static_cast<T>(ring[u][2]);
+      const size_t o = at(j + kFwdRing);
+      ring[u][0] = d[o]; ring[u][1] = d[HN + o]; ring[u][2] = d[2 * HN + o];
+      if (j % checkpoint == 0) {
+        double* c = ckpt + (static_cast<size_t>(k) * nseg + j / checkpoint) * 3;
+        c[0] = q_ca; c[1] = w; c[2] = q_sm;
+      }
+      rk4_step<T>(K, C, dt, q_ca, w, q_sm);
+      q_ca += e0; w += e1; q_sm += e2;
+      const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
+      if (s < smin) { smin = s; arg = j + 1; }
     }
-    rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-    q_ca += static_cast<T>(c0); w += static_cast<T>(c1); q_sm += static_cast<T>(c2);
-    c0 = n0; c1 = n1; c2 = n2;
-    n0 = f0; n1 = f1; n2 = f2;
-    const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
-    if (s < smin) { smin = s; arg = j + 1; }
   }
   lane_min[k] = static_cast<double>(smin);
   lane_arg[k] = arg;
@@ -409,17 +422,22 @@ adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
 
 // Host side: enqueue forward, argmin and reverse on the handle's stream.
 // ckpt: N * (H / checkpoint + 1) * 3 doubles; lane_min/lane_arg: N each;
-// seg: (H + 1) * 12 doubles; d_kj: 2; d_out: 1 + 3 + RRG_NPARAM.
+// seg: (H + 1) * 12 doubles; d_kj: 2; d_out: 1 + 3 + RRG_NPARAM.  fwd_begin /
+// fwd_end (either may be null): events recorded around the forward kernel.
 cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
                            double kappa, int checkpoint, double* ckpt, double* lane_min,
                            int* lane_arg, double* seg, double* d_g, long long* d_kj,
-                           double* d_out) {
+                           double* d_out, cudaEvent_t fwd_begin, cudaEvent_t fwd_end) {
   // one warp per block until the blocks of 128 threads would fill every SM:
   // each scenario is one dependent chain, so spreading them over SMs costs
   // nothing and puts more SMs' binary64 units to work
   const int sms = L.sms > 0 ? L.sms : 152;
   const int threads = (L.N >= 128 * sms) ? 128 : 32;
   const int blocks = (L.N + threads - 1) / threads;
+  if (fwd_begin) {
+    const cudaError_t er = cudaEventRecord(fwd_begin, L.stream);
+    if (er != cudaSuccess) return er;
+  }
   if (fp64) {
     adjoint_forward_kernel<double><<<blocks, threads, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
                                                                      checkpoint, ckpt, lane_min, lane_arg);
@@ -429,6 +447,10 @@ cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (fwd_end) {
+    e = cudaEventRecord(fwd_end, L.stream);
+    if (e != cudaSuccess) return e;
+  }
   adjoint_argmin_kernel<<<1, 256, 0, L.stream>>>(lane_min, lane_arg, L.N, d_g, d_kj, d_kj + 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

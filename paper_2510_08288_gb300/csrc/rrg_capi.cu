@@ -1001,10 +1001,20 @@ int rrg_slack_gradient(rrg_handle h, const double* x_t, double v_prev, double r_
   std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
   CK(cudaMemcpyAsync(h->io_dev, h->io_h, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(launch_materialize64(h->L));
+  // the forward pass rolls out every scenario: timed as a rollout launch
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (h->profiling && !h->capturing) { ea = take_event(h); eb = take_event(h); }
+  if (!(ea && eb)) {
+    if (ea) h->ev_free.push_back(ea);
+    if (eb) h->ev_free.push_back(eb);
+    ea = eb = nullptr;
+  }
   CK(launch_adjoint(h->L, precision == RRG_FP64, h->io_dev + IO_X, v_prev, r_t, kappa, checkpoint,
                     h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
-                    reinterpret_cast<long long*>(h->adj_out + 1), h->adj_out + 3));
+                    reinterpret_cast<long long*>(h->adj_out + 1), h->adj_out + 3, ea, eb));
+  if (ea) h->ev_roll.emplace_back(ea, eb);
   h->launches += 5;
+  h->rollout_launches += 1;
   double out[3 + 4 + RRG_NPARAM];
   CK(cudaMemcpyAsync(out, h->adj_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

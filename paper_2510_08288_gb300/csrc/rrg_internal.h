@@ -332,7 +332,7 @@ cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, d
 cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
                            double kappa, int checkpoint, double* ckpt, double* lane_min,
                            int* lane_arg, double* seg, double* d_g, long long* d_kj,
-                           double* d_out);
+                           double* d_out, cudaEvent_t fwd_begin, cudaEvent_t fwd_end);
 
 // Configuration check shared with the handle-less entry point (rrg_capi.cu);
 // on failure the message is readable with rrg_last_error(NULL).

@@ -69,3 +69,15 @@ def test_closed_loop_cpu_legs_agree_and_serialise():
     v1, k1 = bench.cpu_oracle_one_core(x0, r)
     assert v1 > 0 and k1 == float(kaps[0])  # thread count does not change the oracle's result
     json.dumps({"value": val, "one_core": v1, "kappa": k1})
+
+
+def test_adjoint_cpu_baseline_runs_whole_gradients():
+    from oracle import oracle as O
+    from paper_2510_08288_gb300 import inputs
+    p = inputs.fc3_params()
+    w = inputs.WORKLOADS["adjoint"]
+    x_t = O.equilibrium(p, 100.0)
+    c = bench.adjoint_cpu(p, x_t, 100.0, 250.0, w["N"], w["H"], 0.01, [-1, -1])
+    assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0
+    assert c["argmin_equal_to_gpu_fp64"] is False  # no scenario has index -1
+    json.dumps(c)

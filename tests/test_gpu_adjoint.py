@@ -70,6 +70,22 @@ def test_adjoint_late_argmin_matches_complex_step(R, orc, params, checkpoint):
     np.testing.assert_allclose(grad, gro, rtol=1e-7, atol=1e-14 * np.max(np.abs(gro)))
 
 
+def test_adjoint_forward_pass_is_timed_as_a_rollout(R, orc, params):
+    """With profiling on, a gradient's forward pass (all scenarios, full
+    horizon) is one timed rollout launch of the five the call makes."""
+    N, H = 256, 300
+    x_t = orc.equilibrium(params, 100.0)
+    with _gov(R, params, N, H) as g:
+        g.sample_scenarios(2, 0)
+        g.reset_stats()
+        g.set_profiling(True)
+        for prec in (R.FP32, R.FP64):
+            g.slack_gradient(x_t, 100.0, 250.0, 0.1, 50, prec)
+        st = g.stats()
+    assert st["launches"] == 10 and st["rollout_launches"] == 2
+    assert st["timed_rollouts"] == 2 and st["rollout_ms"] > 0
+
+
 def test_adjoint_fp32_close_to_fp64(R, orc, params):
     N, H = 64, 400
     x_t = orc.equilibrium(params, 120.0)
