@@ -105,17 +105,35 @@ SWEEP_TRAFFIC_32K = (3602669056 + 3401216 + 2197011712 + 273152 + 7767449088 + 8
 SWEEP_TRAFFIC_64K = 2 * SWEEP_TRAFFIC_32K
 
 
-def measured_traffic():
-    """The profiled DRAM bytes per launch, or None if the rollout changed."""
+# DRAM bytes of one adjoint_forward_kernel<float> launch on the adjoint
+# workload (4,096 x 1,000, checkpoint 50; ncu --set full,
+# profiles/adjoint_forward_kernel_f32_adjoint_4096x1000.md), valid while the
+# forward kernel, its launch, the model and the Launch struct are the ones
+# profiled
+ADJ_TRAFFIC_PER_LAUNCH = 98381824 + 3629824
+ADJ_TRAFFIC_SOURCES = (
+    ("paper_2510_08288_gb300/csrc/rrg_adjoint.cu",
+     "// Register slots of the forward pass's disturbance prefetch ring.",
+     "__global__ void adjoint_argmin_kernel", "79ed5e5d73ab060e06240b79c605ebcf937f0a6a"),
+    ("paper_2510_08288_gb300/csrc/rrg_adjoint.cu", "cudaError_t launch_adjoint(", "adjoint_argmin_kernel<<<",
+     "05ab892987d1e13fb56434169be7ff5b6f618c3b"),
+    ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "cc5eb334f99d59c13bbc8c27c2b9caded008436c"),
+    ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
+     "babf78733fa6871fdc4b8fb328a1cce64fc61742"),
+)
+
+
+def measured_traffic(sources=TRAFFIC_SOURCES, per_launch=TRAFFIC_PER_LAUNCH):
+    """The profiled DRAM bytes per launch, or None if the kernel changed."""
     import hashlib
-    for rel, begin, end, sha in TRAFFIC_SOURCES:
+    for rel, begin, end, sha in sources:
         try:
             region = source_region(rel, begin, end)
         except (OSError, ValueError):
             return None
         if hashlib.sha1(region.encode("utf-8")).hexdigest() != sha:
             return None
-    return TRAFFIC_PER_LAUNCH
+    return per_launch
 
 
 def parse():
@@ -1006,7 +1024,9 @@ def run_adjoint(args):
                                 "host memory: value and e2e are the same measurement)",
                       "l2": "scenarios (98 MB binary64) re-read by every call; no flush"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                        "frac": achieved / FP32_PEAK_TFLOPS,
+                        "traffic": measured_traffic(ADJ_TRAFFIC_SOURCES, ADJ_TRAFFIC_PER_LAUNCH),
+                        "algorithmic_bytes_per_launch": N * H * 3 * 8,
                         "kernel": "adjoint_forward_kernel<float>", "avg_launch_ms": fwd_ms,
                         "launches": stp["timed_rollouts"],
                         "timing": "CUDA events around the forward pass of %d more binary32 gradients" % K,

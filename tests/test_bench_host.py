@@ -81,3 +81,13 @@ def test_adjoint_cpu_baseline_runs_whole_gradients():
     assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0
     assert c["argmin_equal_to_gpu_fp64"] is False  # no scenario has index -1
     json.dumps(c)
+
+
+def test_traffic_guard_drops_figures_of_changed_sources():
+    """A profiled DRAM figure is reported only while the hashed source regions
+    are the ones profiled."""
+    assert bench.measured_traffic((("bench.py", None, None, "0" * 40),), 123) is None
+    assert bench.measured_traffic((("bench.py", "no such marker", "x", "0" * 40),), 123) is None
+    import hashlib
+    sha = hashlib.sha1(bench.source_region("bench.py", None, None).encode("utf-8")).hexdigest()
+    assert bench.measured_traffic((("bench.py", None, None, sha),), 123) == 123
