@@ -151,3 +151,22 @@ def test_step_latency_rejects_a_null_handle():
     from paper_2510_08288_gb300 import rrg as R
     c = ctypes.c_double(0.0)
     assert R.lib.rrg_step_latency(None, 100.0, 10, ctypes.byref(c)) == R.RRG_EINVAL
+
+
+def test_handle_entry_points_reject_a_null_handle():
+    """Every handle entry point returns RRG_EINVAL for a null handle before it
+    touches a device (the adjoint, the Newton search, profiling, statistics)."""
+    from paper_2510_08288_gb300 import rrg as R
+    x = (ctypes.c_double * 3)(1.0, 2.0, 3.0)
+    g = ctypes.c_double(0.0)
+    grad = (ctypes.c_double * 31)()
+    k, j = ctypes.c_int64(0), ctypes.c_int64(0)
+    assert R.lib.rrg_slack_gradient(None, x, 100.0, 250.0, 0.1, 50, R.FP32, ctypes.byref(g), grad,
+                                    ctypes.byref(k), ctypes.byref(j)) == R.RRG_EINVAL
+    kap = ctypes.c_double(0.0)
+    fl, it = ctypes.c_int32(0), ctypes.c_int32(0)
+    assert R.lib.rrg_newton_search(None, x, 250.0, 100.0, 1e-6, 10, 50, R.FP32, ctypes.byref(kap),
+                                   ctypes.byref(fl), ctypes.byref(it)) == R.RRG_EINVAL
+    assert R.lib.rrg_set_profiling(None, 1) == R.RRG_EINVAL
+    st = R.RrgStats()
+    assert R.lib.rrg_get_stats(None, ctypes.byref(st)) == R.RRG_EINVAL
