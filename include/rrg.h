@@ -335,8 +335,13 @@ RRG_API int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_p
  * (first k, then first j, attaining the min; a subgradient where the argmin
  * is not unique) by the discrete adjoint of the RK4 recursion: the forward
  * pass saves every trajectory's state every `checkpoint` steps, the reverse
- * pass recomputes one checkpoint segment at a time.  Host in: x_t[3]
- * (finite), v_prev, r_t (> 0), kappa in [0, 1], checkpoint >= 1, precision
+ * pass recomputes trajectory k*'s segments before j* in parallel and then
+ * sweeps them backwards; the handle keeps N * (H / checkpoint + 1) * 3 and
+ * (H + 1) * 12 doubles of device scratch for them, allocated on first use.
+ * Errors: RRG_EINVAL for a null handle or an argument outside its range,
+ * RRG_ECUDA (message in rrg_last_error) from the allocation or the
+ * launches.  Host in: x_t[3]
+ * (finite), v_prev, r_t (> 0), kappa in [0, 1], checkpoint in [1, 65536], precision
  * RRG_FP64 or RRG_FP32 (arithmetic of both passes).  Host out (each may be
  * NULL): *g, grad[31] = (dg/dkappa, dg/dx_t[3], dg/dtheta[27] in the FC3
  * parameter layout), *k_star, *j_star.  Under parametric uncertainty
