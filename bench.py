@@ -19,7 +19,8 @@ launched directly; its CUDA events around each rollout launch give the
 roofline's kernel duration.  e2e = the same through the host-buffer C-ABI calls
 (rrg_sample_scenarios + rrg_step + rrg_plant_step, host copies included).
 roofline = the binary32 rollout kernel's achieved FP32 rate vs the FP32 FMA
-peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz.  cpu_baseline = the
+peak derived from the device's SM count x 128 lanes x 2 flop x the SM clock
+sampled during the timed region.  cpu_baseline = the
 FP64 CPU oracle (plain joint bisection) on a bounded prefix of the same run.
 
 --impl reference times that oracle alone (the CPU arm) on the same workload.
@@ -61,16 +62,36 @@ FLOPS_PER_STEP = 141
 # derived FP32 peak, which counts every instruction as an FMA
 INSTR_PER_STEP = 124
 ISSUE_CEILING = FLOPS_PER_STEP / (2.0 * INSTR_PER_STEP)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak(clk):
+    """FP32 FMA peak in TFLOP/s from unit counts and clocks: the device's SM
+    count (queried) x 128 FP32 lanes x 2 flop per FMA x the median SM clock
+    sampled during the timed region (the maximum SM clock nvidia-smi reports
+    when no sample fell inside it); returns (peak, source)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz, how = clk.get("sm_mhz"), "median sampled SM clock"
+    if not mhz:
+        mhz, how = clk.get("sm_max_mhz"), "maximum SM clock (no sample in the timed region)"
+    if not mhz:
+        return None, "no SM clock available from nvidia-smi"
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return peak, "derived: %d SMs x %d FP32 lanes x 2 flop/FMA x %.0f MHz (%s)" % (
+        sms, FP32_LANES_PER_SM, mhz, how)
+
+
+def frac_of(a, b):
+    return (a / b) if (a is not None and b) else None
 L2_FLUSH_BYTES = 256 << 20
 # large sweep: N_sim 1K..64K, 16 candidates, horizon 5,000, parametric uncertainty
 SWEEP_N = (1024, 2048, 4096, 8192, 16384, 32768, 65536)
 SWEEP_H, SWEEP_M, SWEEP_ROUNDS = 5000, 16, 3
 SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
-# DRAM bytes per rollout launch on this workload (ncu, one update's four
-# launches with the tuned shape 64 nodes / 32-step probe: probe, continuation
-# + round 2, two no-op rounds; see
-# profiles/rollout_kernel_f32_closed_loop_N1024_H2000.md), valid while the
+# DRAM bytes per rollout launch on this workload (ncu, one pass over one
+# update's four launches with the tuned shape 64 nodes / 32-step probe:
+# probe, continuation + round 2, two no-op rounds), valid while the
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
@@ -98,7 +119,7 @@ def source_region(rel, begin, end):
 
 # The sweep's rollout launches (parametric model, register ring): DRAM bytes
 # per launch of one update's three k-section rounds at 32,768 scenarios (ncu,
-# one pass; profiles/rollout_pu_kernel_f32_sweep_N65536_H5000.md), and the
+# one pass over the three launches of one update), and the
 # same per-launch figure scaled to 65,536 scenarios by the units processed
 # (the scenario array, which dominates the traffic, doubles).
 SWEEP_TRAFFIC_32K = (3602669056 + 3401216 + 2197011712 + 273152 + 7767449088 + 80128) / 3
@@ -106,8 +127,8 @@ SWEEP_TRAFFIC_64K = 2 * SWEEP_TRAFFIC_32K
 
 
 # DRAM bytes of one adjoint_forward_kernel<float> launch on the adjoint
-# workload (4,096 x 1,000, checkpoint 50; ncu --set full,
-# profiles/adjoint_forward_kernel_f32_adjoint_4096x1000.md), valid while the
+# workload (4,096 x 1,000, checkpoint 50; ncu --set full on one launch of
+# the bench's adjoint workload), valid while the
 # forward kernel, its launch, the model and the Launch struct are the ones
 # profiled
 ADJ_TRAFFIC_PER_LAUNCH = 98381824 + 3629824
@@ -545,8 +566,9 @@ def run_gpu(args):
     # time per update spread over the horizon those lanes integrate
     chain_cycles = g.step_latency(V0, HZ)
     roll_ms_per_update = std["rollout_ms"] / max(1, K)
-    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
-    step_cycles = roll_ms_per_update * 1e-3 * sm_hz / HZ
+    peak, peak_src = fp32_peak(clk)
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
+    step_cycles = roll_ms_per_update * 1e-3 * sm_mhz * 1e6 / HZ if sm_mhz else None
     out = None
     if rank == 0:
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
@@ -603,22 +625,22 @@ def run_gpu(args):
             "config": workload_config(W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": frac_of(achieved, peak),
                          "traffic": measured_traffic() if (NS, HZ) == (N_SCEN, HORIZON) else None,
                          "kernel": "rollout_kernel<float>",
                          "avg_launch_ms": avg_roll_ms, "launches": std["timed_rollouts"],
                          "timing": "CUDA events around each rollout launch of the same K updates run by "
                                    "direct launches (graph replays cannot time single kernels)",
                          "flops_per_traj_step": FLOPS_PER_STEP,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                         "peak_source": peak_src,
                          "issue_ceiling": ISSUE_CEILING,
-                         "frac_of_issue_ceiling": achieved / FP32_PEAK_TFLOPS / ISSUE_CEILING,
+                         "frac_of_issue_ceiling": frac_of(frac_of(achieved, peak), ISSUE_CEILING),
                          "measured_units": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
                                             "mufu_ex2_tops": peaks[2],
                                             "frac_of_measured_fp32": achieved / peaks[0]},
                          "latency": {"cycles_per_step": step_cycles, "chain_cycles_per_step": chain_cycles,
-                                     "frac": chain_cycles / step_cycles,
+                                     "frac": frac_of(chain_cycles, step_cycles),
                                      "basis": "rollout time per update (direct launches) over the %d-step "
                                               "horizon its surviving lanes integrate, at the sampled SM clock; "
                                               "chain: rrg_step_latency, one warp, same right-hand side" % HZ}},
@@ -801,6 +823,7 @@ def run_batch(args):
     if not args.no_cpu_baseline:
         cpu = batch_cpu(p, b, x0, r, args.cpu_seconds, os.cpu_count() or 1)
     g.close()
+    peak, peak_src = fp32_peak(clk)
     out = {
         "metric": BATCH_METRIC, "value": S * K / secs, "unit": "RG updates/s (instance updates)", "n_gpus": 1,
         "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "ms_per_step_median": statistics.median(step_ms),
@@ -808,15 +831,16 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": batch_config(S, W, K, {"index": variant[0], "tile_lanes": variant[1], "prefetch": variant[2]}),
         "trajectory_steps_per_s": {"executed": st["lane_steps"] / secs, "executed_per_step": st["lane_steps"] / K},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": frac_of(achieved, peak), "traffic": None,
                      "kernel": ("batch_rollout_warp_kernel<%d>" % variant[2]) if variant[1] == 32
                                else ("batch_rollout_kernel<%d, %d>" % (variant[1], variant[2])),
                      "avg_launch_ms": avg_roll_ms, "launches": st2["timed_rollouts"],
                      "timing": "%d direct-launch updates after the timed ones" % K2,
                      "flops_per_traj_step": FLOPS_PER_STEP,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
-                     "issue_ceiling": ISSUE_CEILING, "frac_of_issue_ceiling": achieved / FP32_PEAK_TFLOPS / ISSUE_CEILING},
+                     "peak_source": peak_src,
+                     "issue_ceiling": ISSUE_CEILING,
+                     "frac_of_issue_ceiling": frac_of(frac_of(achieved, peak), ISSUE_CEILING)},
         "autotune_rollout_ms": [float(x) for x in tune_ms] if tune_ms is not None else None,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": st["launches"],
         "rechecked_trajectories": st["rechecked"],
@@ -1008,9 +1032,10 @@ def run_adjoint(args):
     out_legs["newton_fp32_recheck_eval"]["within_one_bracket_of_bisect20"] = bool(
         abs(out_legs["newton_fp32_recheck_eval"]["kappa"] - kb) <= 2 * tol)
     main = out_legs["gradient_fp32"]
-    sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    peak, peak_src = fp32_peak(clk)
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
     achieved = N * H * FLOPS_PER_STEP / (fwd_ms * 1e-3) / 1e12
-    step_cycles = fwd_ms * 1e-3 * sm_hz / H
+    step_cycles = fwd_ms * 1e-3 * sm_mhz * 1e6 / H if sm_mhz else None
     cpu = None if args.no_cpu_baseline else adjoint_cpu(p, x_t, v_prev, r, N, H, args.cpu_seconds,
                                                         out_legs["gradient_fp64"]["argmin"])
     value = 1e3 / main["ms"]
@@ -1023,19 +1048,19 @@ def run_adjoint(args):
                       "timing": "median host time per synchronous call (x_t in from and the gradient out to "
                                 "host memory: value and e2e are the same measurement)",
                       "l2": "scenarios (98 MB binary64) re-read by every call; no flush"},
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP32_PEAK_TFLOPS,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": frac_of(achieved, peak),
                         "traffic": measured_traffic(ADJ_TRAFFIC_SOURCES, ADJ_TRAFFIC_PER_LAUNCH),
                         "algorithmic_bytes_per_launch": N * H * 3 * 8,
                         "kernel": "adjoint_forward_kernel<float>", "avg_launch_ms": fwd_ms,
                         "launches": stp["timed_rollouts"],
                         "timing": "CUDA events around the forward pass of %d more binary32 gradients" % K,
                         "flops_per_traj_step": FLOPS_PER_STEP, "traj_steps_per_launch": N * H,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
+                        "peak_source": peak_src,
                         "issue_ceiling": ISSUE_CEILING,
-                        "frac_of_issue_ceiling": achieved / FP32_PEAK_TFLOPS / ISSUE_CEILING,
+                        "frac_of_issue_ceiling": frac_of(frac_of(achieved, peak), ISSUE_CEILING),
                         "latency": {"cycles_per_step": step_cycles, "chain_cycles_per_step": chain_cycles,
-                                    "frac": chain_cycles / step_cycles,
+                                    "frac": frac_of(chain_cycles, step_cycles),
                                     "basis": "forward pass time over its %d dependent steps at the sampled SM "
                                              "clock (4,096 scenarios: 128 warps, one per SM); chain: "
                                              "rrg_step_latency, one warp, the rollout kernel's step" % H}},
@@ -1228,7 +1253,7 @@ def run_sweep(args):
                      "trajectory_steps_per_s": st["lane_steps"] / secs,
                      "nominal_trajectory_steps_per_update": SWEEP_ROUNDS * SWEEP_M * N * SWEEP_H,
                      "executed_trajectory_steps_per_update": st["lane_steps"] / K,
-                     "rollout_tflops": achieved, "rollout_frac": achieved / FP32_PEAK_TFLOPS,
+                     "rollout_tflops": achieved,
                      "rollout_avg_launch_ms": avg_roll_ms, "rechecked": st["rechecked"],
                      "gpu_launches": st["launches"], "kappa": [float(x) for x in kap],
                      "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64,
@@ -1237,6 +1262,9 @@ def run_sweep(args):
         del d_x, d_r, d_vp, d_out, d_fl
         torch.cuda.empty_cache()
     clk = clocks.stop()
+    peak, peak_src = fp32_peak(clk)
+    for row in rows:
+        row["rollout_frac"] = frac_of(row["rollout_tflops"], peak)
     top = rows[-1]
     cpu = None if args.no_cpu_baseline else sweep_cpu(p, args.cpu_seconds, os.cpu_count() or 1)
     out = {
@@ -1244,15 +1272,16 @@ def run_sweep(args):
         "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": top["ms_per_update"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(sweep_config(ns, W, K), param_unc_rel=rho),
-        "roofline": {"bound": "alu", "achieved": top["rollout_tflops"], "peak": FP32_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": top["rollout_tflops"], "peak": peak,
                      "unit": "TFLOP/s", "frac": top["rollout_frac"],
                      "traffic": (SWEEP_TRAFFIC_64K if top["n_scenarios"] == 65536 and rho == inputs.PARAM_UNC_REL
                                  and measured_traffic() is not None else None),
                      "traffic_basis": "ncu DRAM bytes per rollout launch at 32,768 scenarios (one update's "
                                       "3 rounds), scaled x2 to 65,536 by the units processed",
                      "kernel": "rollout_kernel<float, parametric>", "n_scenarios": top["n_scenarios"],
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz",
-                     "issue_ceiling": ISSUE_CEILING, "frac_of_issue_ceiling": top["rollout_frac"] / ISSUE_CEILING},
+                     "peak_source": peak_src,
+                     "issue_ceiling": ISSUE_CEILING,
+                     "frac_of_issue_ceiling": frac_of(top["rollout_frac"], ISSUE_CEILING)},
         "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
         "gpu_launches": top["gpu_launches"],
     }

@@ -407,8 +407,13 @@ RRG_API int rrg_reset_stats(rrg_handle h);
  * routine.  It only enqueues work (asynchronous).
  *
  * The first call on each device looks up the scratch's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.  Every call uses the same scratch, which
+ * (cudaGetSymbolAddress) with that device current, and looks it up again
+ * whenever the device's current context has changed since (after a
+ * cudaDeviceReset, for example, the module and its array are loaded anew);
+ * make the first call on a device, and the first after such a change, before
+ * any stream capture begins.  The binary64 rollouts evaluate x^e - 1 by the
+ * same series as a handle's, so results equal rrg_eval_candidates's on the
+ * same scenarios bit for bit.  Every call uses the same scratch, which
  * keeps the last call's contents; each call re-initialises everything it
  * reads, but calls that may overlap on the GPU (on different streams, or from
  * host threads without ordering between them) race on the scratch and their

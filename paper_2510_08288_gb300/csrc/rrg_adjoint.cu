@@ -431,7 +431,8 @@ cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double
   // one warp per block until the blocks of 128 threads would fill every SM:
   // each scenario is one dependent chain, so spreading them over SMs costs
   // nothing and puts more SMs' binary64 units to work
-  const int sms = L.sms > 0 ? L.sms : 152;
+  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
+  const int sms = L.sms;
   const int threads = (L.N >= 128 * sms) ? 128 : 32;
   const int blocks = (L.N + threads - 1) / threads;
   if (fwd_begin) {

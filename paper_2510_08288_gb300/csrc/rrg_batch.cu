@@ -526,6 +526,7 @@ struct rrg_batch_ctx {
   BLaunch B{};
   std::vector<BInst> inst;
   int variant = 3;             // 128 lanes per tile, prefetch 16
+  int sms = 0;                 // streaming multiprocessors of the device (queried)
   int grid[RRG_BATCH_VARIANTS]{};
   size_t lanes = 0;            // sum of M N_s
   // device memory
@@ -698,7 +699,7 @@ int enqueue_search_all(rrg_batch_ctx* h, const double* d_x, const double* d_r, c
     BCK(cudaGetLastError());
     int rc = enqueue_rollout(h);
     if (rc != RRG_OK) return rc;
-    batch_recheck_kernel<<<2 * 152, 64, 0, h->stream>>>(B);
+    batch_recheck_kernel<<<2 * h->sms, 64, 0, h->stream>>>(B);
     BCK(cudaGetLastError());
     const int final = r == rounds - 1;
     batch_decide_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, final, tile, v_out, k_out, f_out);
@@ -828,8 +829,9 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   if (e == cudaSuccess) e = cudaMemsetAsync(h->t_dev, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d32, 0, static_cast<size_t>(elems) * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  int nsm = 152;
+  int nsm = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  h->sms = nsm;
   for (int v = 0; v < RRG_BATCH_VARIANTS && e == cudaSuccess; ++v) {
     int per = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kVariants[v].kernel,

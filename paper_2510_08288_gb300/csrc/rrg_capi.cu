@@ -20,7 +20,7 @@ thread_local std::string g_create_error;
 
 struct rrg_ctx {
   int device = 0;
-  int sms = 152;                // streaming multiprocessors of the device
+  int sms = 0;                  // streaming multiprocessors of the device (queried)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   rrg_config cfg{};

@@ -157,7 +157,8 @@ struct Launch {
   DevStats* stats;
   uint8_t* P;                   // optional
   int recheck_blocks;
-  int sms;                      // streaming multiprocessors of the device
+  int sms;                      // streaming multiprocessors of the device (> 0; launches
+                                //   refuse a descriptor without it)
   int probe_steps;              // steps of a SEG_PROBE segment
   void* lane_state;             // LaneState<T>[m_cap * N] for probed rounds
   // parametric uncertainty: per-scenario parameter multipliers m[k * NPARAM

@@ -184,8 +184,8 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
   // stream: it then finishes while the search's short kernels run.  (One
   // block per SM stretched it over the long rollout and slowed the update by
   // 7 %; stream priorities changed nothing, measured on GB300.)
-  const int sms = L.sms > 0 ? L.sms : 152;
-  sample_kernel<<<grid_for(n, 256, sms * 16), 256, 0, stream ? stream : L.stream>>>(
+  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
+  sample_kernel<<<grid_for(n, 256, L.sms * 16), 256, 0, stream ? stream : L.stream>>>(
       L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
       amp[0], amp[1], amp[2], write64, L.scen_gen, L.st, L.pmul, dual ? L.pmulb : nullptr, L.punc_rho,
       L.punc_mask);
@@ -199,7 +199,8 @@ __global__ void fill_kernel(double* __restrict__ a, size_t n, double v) {
 }
 
 cudaError_t launch_fill(const Launch& L, double* a, size_t n, double v) {
-  fill_kernel<<<grid_for(n, 256, 152 * 4), 256, 0, L.stream>>>(a, n, v);
+  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
+  fill_kernel<<<grid_for(n, 256, L.sms * 4), 256, 0, L.stream>>>(a, n, v);
   return cudaGetLastError();
 }
 
@@ -226,7 +227,8 @@ __global__ void mark64_kernel(SearchState* st) { st->src[0].d64_valid = 1; }
 
 cudaError_t launch_materialize64(const Launch& L) {
   const size_t n = static_cast<size_t>(L.H) * L.N;
-  materialize64_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.N, L.H, L.st);
+  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
+  materialize64_kernel<<<grid_for(n, 256, L.sms * 16), 256, 0, L.stream>>>(L.d64, L.N, L.H, L.st);
   mark64_kernel<<<1, 1, 0, L.stream>>>(L.st);
   return cudaGetLastError();
 }
@@ -241,7 +243,8 @@ __global__ void round_scenarios_kernel(const double* __restrict__ d64, float* __
 
 cudaError_t launch_round_scenarios(const Launch& L) {
   const size_t n = L.scen_gen ? 0 : 3 * static_cast<size_t>(L.H) * L.N;
-  round_scenarios_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, L.stream>>>(L.d64, L.d32, n, L.st);
+  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
+  round_scenarios_kernel<<<grid_for(n, 256, L.sms * 16), 256, 0, L.stream>>>(L.d64, L.d32, n, L.st);
   return cudaGetLastError();
 }
 
@@ -436,7 +439,8 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
   // ran 10 % faster, 8,192 x 16 candidates 3 % slower); parametric model
   // (more registers, fewer resident warps), up to 64 (16,384 x 16 candidates
   // 2-6 % faster, 65,536 x 16 6 % slower).
-  const int sms = L.sms > 0 ? L.sms : 152;
+  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
+  const int sms = L.sms;
   const long long warps = static_cast<long long>(grid.x) * grid.y * (kRollThreads / 32);
   const bool ring = warps <= (L.pmul ? 64LL : 16LL) * sms;
 #define RRG_ROLLOUT(KERNEL, T, SRC, KK, D0, D1, CAND, CLS) \

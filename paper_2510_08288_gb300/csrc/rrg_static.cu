@@ -9,6 +9,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>  // driver types only (CUcontext); the calls go through cudaGetDriverEntryPoint
+
 #include "rrg_internal.h"
 
 namespace rrg {
@@ -21,7 +23,8 @@ constexpr size_t kStaticMaxLanes = RRG_STATIC_MAX_LANES;
 constexpr size_t align256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
 constexpr size_t kOffState = 0;
 constexpr size_t kOffParams = kOffState + align256(sizeof(SearchState));
-constexpr size_t kOffKappa = kOffParams + align256(RRG_NPARAM * sizeof(double));
+constexpr size_t kOffPws = kOffParams + align256(RRG_NPARAM * sizeof(double));
+constexpr size_t kOffKappa = kOffPws + align256(sizeof(PowSeries));
 constexpr size_t kOffV = kOffKappa + align256(kStaticMaxCand * sizeof(double));
 constexpr size_t kOffK64 = kOffV + align256(kStaticMaxCand * sizeof(double));
 constexpr size_t kOffK32 = kOffK64 + align256(kStaticMaxCand * sizeof(RhsC<double>));
@@ -39,14 +42,18 @@ static_assert(kScratchBytes <= RRG_STATIC_SCRATCH_BYTES, "scratch layout exceeds
 // The scratch itself: held by every device that loads the library.
 __device__ __align__(256) unsigned char g_rrg_static_scratch[RRG_STATIC_SCRATCH_BYTES];
 
-struct ParamBlock { double v[RRG_NPARAM]; };
+struct ParamBlock {
+  double v[RRG_NPARAM];
+  PowSeries pws;   // binary64 x^e - 1 series of the model's exponent (as rrg_create builds it)
+};
 
-// Writes the parameter vector (passed by value) into the scratch and clears
-// the scratch's step counters.
-__global__ void static_params_kernel(ParamBlock pb, double* params, DevStats* stats,
-                                     SearchState* st) {
+// Writes the parameter vector and the x^e - 1 series (passed by value) into
+// the scratch and clears the scratch's step counters.
+__global__ void static_params_kernel(ParamBlock pb, double* params, PowSeries* pws,
+                                     DevStats* stats, SearchState* st) {
   const int i = threadIdx.x;
   if (i < RRG_NPARAM) params[i] = pb.v[i];
+  if (i == 0) *pws = pb.pws;
   if (i == 0) {
     st->src[0].d64_valid = 1;  // the caller's binary64 array holds the values
     st->src[1].d64_valid = 1;
@@ -56,10 +63,24 @@ __global__ void static_params_kernel(ParamBlock pb, double* params, DevStats* st
   }
 }
 
-// Device address of the scratch on each device, looked up once per device.
+// Device address of the scratch, looked up once per device and context: a
+// device reset or a recreated primary context loads the module again, and
+// the array may then sit at another address, so each cached address is kept
+// with the id of the context it was looked up in (cuCtxGetId, reached through
+// cudaGetDriverEntryPointByVersion so that the library needs no link to the
+// driver library).  The SM count is cached beside it.
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  unsigned char* ptr;
+  int sms;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -71,20 +92,55 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-int scratch_for_current_device(unsigned char** out) {
+// Id of the calling thread's current context (0 if none is current yet).
+int current_context_id(unsigned long long* id) {
+  if (g_ctx_get_current == nullptr || g_ctx_get_id == nullptr) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    const cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    const cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+        q2 != cudaDriverEntryPointSuccess || f1 == nullptr || f2 == nullptr)
+      return fail(RRG_ECUDA, "the driver's cuCtxGetCurrent / cuCtxGetId are not available");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return fail(RRG_ECUDA, "cuCtxGetCurrent failed");
+  *id = 0;
+  if (ctx != nullptr && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return fail(RRG_ECUDA, "cuCtxGetId failed");
+  return RRG_OK;
+}
+
+int scratch_for_current_device(unsigned char** out, int* sms) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(RRG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(RRG_EINVAL, "device ordinal %d not supported", dev);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
+  unsigned long long ctx = 0;
+  int rc = current_context_id(&ctx);
+  if (rc != RRG_OK) return rc;
+  ScratchEntry& c = g_scratch[dev];
+  if (c.ptr == nullptr || ctx == 0 || c.ctx_id != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_rrg_static_scratch);
     if (e != cudaSuccess || p == nullptr)
       return fail(RRG_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n < 1)
+      return fail(RRG_ECUDA, "cudaDeviceGetAttribute(SM count): %s", cudaGetErrorString(e));
+    // the look-up made the primary context current if none was
+    rc = current_context_id(&ctx);
+    if (rc != RRG_OK) return rc;
+    c.ctx_id = ctx;
+    c.ptr = static_cast<unsigned char*>(p);
+    c.sms = n;
   }
-  *out = g_scratch_ptr[dev];
+  *out = c.ptr;
+  *sms = c.sms;
   return RRG_OK;
 }
 
@@ -125,7 +181,8 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
                 cfg->precision == RRG_FP64 ? "binary64" : (cfg->precision == RRG_FP32 ? "binary32" : "binary64 and binary32"));
 
   unsigned char* base = nullptr;
-  rc = scratch_for_current_device(&base);
+  int sms = 0;
+  rc = scratch_for_current_device(&base, &sms);
   if (rc != RRG_OK) return rc;
 
   Launch L{};
@@ -147,6 +204,9 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
   L.scfg.eps_ss = cfg->eps_ss;
   L.scfg.y_c = cfg->y_c;
   fold_constants(model_params, &L.k64, &L.k32);
+  // the binary64 rollouts and the recheck evaluate x^e - 1 by the same series
+  // as a handle's, so both give the same bits
+  L.k64.pws = reinterpret_cast<const PowSeries*>(base + kOffPws);
   fold_rhs(L.k64, &L.u64, &L.u32);
   L.params = reinterpret_cast<double*>(base + kOffParams);
   L.d64 = const_cast<double*>(d_scen64);
@@ -165,11 +225,14 @@ extern "C" int rrg_eval_candidates_static(const double* model_params, int n_para
   L.recheck_list = reinterpret_cast<uint32_t*>(base + kOffList);
   L.recheck_jlast = reinterpret_cast<uint32_t*>(base + kOffJlast);
   L.P = nullptr;
-  L.recheck_blocks = 2 * 152;
+  L.sms = sms;
+  L.recheck_blocks = 2 * sms;
 
   ParamBlock pb;
   std::memcpy(pb.v, model_params, sizeof pb.v);
-  static_params_kernel<<<1, 32, 0, L.stream>>>(pb, const_cast<double*>(L.params), L.stats, L.st);
+  make_pow_series((model_params[P_GAMMA] - 1.0) / model_params[P_GAMMA], &pb.pws);
+  static_params_kernel<<<1, 32, 0, L.stream>>>(pb, const_cast<double*>(L.params),
+                                               const_cast<PowSeries*>(L.k64.pws), L.stats, L.st);
   cudaError_t e = cudaGetLastError();
   // the prepare kernel rewrites every per-candidate flag, key and the recheck
   // count, so nothing left in the scratch by an earlier call is read
