@@ -50,6 +50,12 @@ UNIT = "RG updates/s"
 N_SCEN, HORIZON, N_BISECT, M_CAND = 1024, 2000, 12, 64
 SEED, V0 = 1, 100.0
 RECHECK_EPS_REL = 1e-6
+RUN_UPDATES = 1000
+# The timed window of the closed loop opens at update 115, ten updates before
+# the staircase's first level change (update 125): the timed updates include
+# the large kappas and the binary64 rechecks of a reference step.  The
+# updates before it run untimed (the last W of them are the warm-up).
+WINDOW_START = 115
 PROBE_STEPS = 128
 # algorithmic binary32 flops of one trajectory step, counted from the source
 # of the rollout's right-hand side with its constants multiplied out: 4
@@ -163,7 +169,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
-    ap.add_argument("--fp64-steps", type=int, default=3, help="updates of the plain FP64 bisection comparator")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="updates of the plain FP64 bisection comparator (default: all timed updates)")
+    ap.add_argument("--window-start", type=int, default=WINDOW_START,
+                    help="closed loop: first timed update (the updates before it run untimed)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -185,11 +194,19 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, given=False):
+def window_start(W, K, start=WINDOW_START):
+    """First timed update of the closed loop: `start`, moved so that the W
+    warm-up updates fit before it and the K timed ones inside the run."""
+    return max(W, min(start, RUN_UPDATES - K))
+
+
+def workload_config(S0, W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, given=False):
     return {
         "workload": "closed-loop robust RG on FC3: N_sim=%d scenarios, horizon %d RK4 steps "
                     "(dt=0.01 s), staircase r (8 levels over 50..300 A, seed 1, 125 updates/level), "
-                    "timed updates [%d, %d) of the 1000-update run" % (N, H, W, W + K),
+                    "timed updates [%d, %d) of the 1000-update run (updates [%d, %d) warm up, the ones "
+                    "before them position the loop; the level change at update 125 falls in the window "
+                    "when it is long enough)" % (N, H, S0, S0 + K, S0 - W, S0),
         "search": "speculative bisection (Alg. 1 result), N_kappa=12, %d candidates/round, "
                   "first two rounds pipelined after a %d-step probe (0: not pipelined); shape %s"
                   % (m, probe, "given" if given else "chosen by rrg_autotune on update 0"),
@@ -358,16 +375,18 @@ def run_reference(args):
     from paper_2510_08288_gb300 import inputs
     p = inputs.fc3_params()
     W, K = args.warmup, args.steps
-    r_seq = inputs.staircase(W + K, 8, 125, SEED)
+    S0 = window_start(W, K, args.window_start)
+    r_seq = inputs.staircase(S0 + K, 8, 125, SEED)
     x0 = O.equilibrium(p, V0)
     cores = os.cpu_count() or 1
     c = O.cfg(H=HORIZON, N=N_SCEN)
     amp = inputs.DIST_AMP
-    v, kap, fl, xs = O.closed_loop(p, c, x0, V0, r_seq[:W], SEED, 0, amp, amp, search=0, n_kappa=N_BISECT,
-                                   nthreads=cores) if W else (None, None, None, [x0])
-    xw, vw = (xs[-1], v[-1]) if W else (x0, V0)
+    # untimed: the updates before the window (the last W of them the warm-up)
+    v, kap, fl, xs = O.closed_loop(p, c, x0, V0, r_seq[:S0], SEED, 0, amp, amp, search=0, n_kappa=N_BISECT,
+                                   nthreads=cores) if S0 else (None, None, None, [x0])
+    xw, vw = (xs[-1], v[-1]) if S0 else (x0, V0)
     t0 = time.perf_counter()
-    O.closed_loop(p, c, xw, vw, r_seq[W:W + K], SEED, W, amp, amp, search=0, n_kappa=N_BISECT,
+    O.closed_loop(p, c, xw, vw, r_seq[S0:S0 + K], SEED, S0, amp, amp, search=0, n_kappa=N_BISECT,
                   nthreads=cores)
     dt = time.perf_counter() - t0
     val = K / dt
@@ -375,11 +394,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(W, K), search="plain joint bisection (Alg. 1 on all scenarios)",
+        "config": dict(workload_config(S0, W, K), search="plain joint bisection (Alg. 1 on all scenarios)",
                        precision="binary64", l2="n/a (CPU)"),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "updates [%d, %d) of the closed loop, FP64 CPU oracle, %d threads"
-                                   % (W, W + K, cores)},
+                                   % (S0, S0 + K, cores)},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -388,9 +407,10 @@ def run_reference(args):
 
 # -------------------------------------------------------------- GPU side --
 def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning):
-    """The timed updates again through the host-buffer entry points
-    (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle; every
-    call copies its inputs from and its results to host memory."""
+    """The timed updates [W, T) again through the host-buffer entry points
+    (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle, after
+    the updates before them untimed; every call copies its inputs from and its
+    results to host memory."""
     import numpy as np
     import torch
     g2 = R.Governor(p, cfg, stream)
@@ -419,6 +439,88 @@ def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tunin
             "kappa_equal_to_device_run": bool(np.all(np.array(kap_e2e) == kap_dev[W:T]))}
 
 
+def fp64_comparator(R, torch, p, stream, flush, H, N, seed, amp, d_r, S0, n, x_start, v_start, kap32, dev):
+    """Plain FP64 bisection (Alg. 1, 12 rounds) on the same closed loop over
+    updates [S0, S0 + n), through rrg_closed_loop_dev from the given state,
+    with CUDA events around every update on the launching stream."""
+    import numpy as np
+    if n <= 0:
+        return None
+    cfg64 = R.rrg_config_default(horizon=H, n_scenarios=N, max_candidates=M_CAND, n_bisect=N_BISECT,
+                                 search=R.SEARCH_BISECT, precision=R.FP64, early_exit=R.EXIT_CANDIDATE)
+    g3 = R.Governor(p, cfg64, stream)
+    o_v = torch.zeros(n, dtype=torch.float64, device=dev)
+    o_k = torch.zeros(n, dtype=torch.float64, device=dev)
+    o_f = torch.zeros(n, dtype=torch.int32, device=dev)
+    o_x = torch.zeros(3 * (n + 1), dtype=torch.float64, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(n):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            if i == 0:
+                R.rrg_closed_loop_dev(g3.h, np.asarray(x_start, dtype=np.float64), float(v_start), d_r[S0:], 1,
+                                      seed, S0, amp, False, o_v, o_k, o_f, o_x)
+            else:
+                R.rrg_closed_loop_dev(g3.h, None, 0.0, d_r[S0:], 1, seed, S0, amp, False, o_v, o_k, o_f, o_x)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    g3.close()
+    k64 = o_k.cpu().numpy()
+    diff = np.abs(k64 - np.asarray(kap32[:n]))
+    return {"value": n / (sum(ms) / 1e3), "unit": UNIT, "ms_per_update": sum(ms) / n, "updates": n,
+            "window": [S0, S0 + n],
+            "timing": "CUDA events around each update (rrg_closed_loop_dev, direct launches), L2 flushed "
+                      "between updates, same closed loop and updates as the timed binary32 window",
+            "kappa_equal_to_fp32_recheck": bool(np.all(diff == 0.0)),
+            "kappa_max_abs_diff": float(diff.max())}
+
+
+def fp32_error_probe(R, p, stream, H, N, seed, probes, m_grid=16, m_near=16, param_unc=0.0, n_cap=None):
+    """The binary32 rollouts' slack error against binary64 on sampled updates
+    (rrg_slack_error: every trajectory in both precisions over the full
+    horizon, no early exit): per update (t, x_t, v_prev, r_t, kappa_t), the
+    candidates are m_grid points on [0, 1] and m_near dyadic points spaced
+    2^-11 around the update's kappa.  n_cap: only the first n_cap scenarios
+    (the Philox draws are nested in N, so they are the run's own)."""
+    import numpy as np
+    from paper_2510_08288_gb300 import inputs
+    n = N if n_cap is None else min(N, n_cap)
+    band = RECHECK_EPS_REL * inputs.Y_MIN
+    kw = {}
+    if param_unc > 0:
+        kw = dict(param_unc_rel=param_unc, param_unc_mask=inputs.FC3_UNCERTAIN_MASK)
+    cfg = R.rrg_config_default(horizon=H, n_scenarios=n, max_candidates=m_grid + m_near,
+                               precision=R.FP32_RECHECK, recheck_eps_rel=RECHECK_EPS_REL, **kw)
+    g = R.Governor(p, cfg, stream)
+    emax, rmax, bad, lanes, meds, ts = 0.0, 0.0, 0, 0, [], []
+    for (t, x, vp, r, kap) in probes:
+        near = np.clip(kap + (np.arange(m_near) - (m_near // 2 - 1)) * 2.0 ** -11, 0.0, 1.0)
+        kappas = np.unique(np.concatenate([np.linspace(0.0, 1.0, m_grid), near]))
+        g.sample_scenarios(seed, t)
+        out = g.slack_error(np.asarray(x, dtype=np.float64), float(vp), float(r), kappas, band)
+        emax = max(emax, float(out["err"].max()))
+        rmax = max(rmax, float(out["ratio"].max()))
+        bad += int(out["unsafe"].sum())
+        lanes += out["err"].size
+        meds.append(float(np.median(out["err"])))
+        ts.append(int(t))
+    g.close()
+    return {"band": band, "updates": ts, "trajectories": lanes, "steps_per_trajectory": H + 1,
+            "scenarios": n if n == N else "%d of %d" % (n, N),
+            "kappas": "%d grid points on [0, 1] and %d dyadic points spaced 2^-11 around the update's kappa"
+                      % (m_grid, m_near),
+            "max_abs_slack_error": emax,
+            "median_trajectory_max_error": float(np.median(meds)),
+            "max_error_over_band_or_slack": rmax,
+            "unsafe_steps": bad,
+            "basis": "rrg_slack_error: binary32 and binary64 slacks of every trajectory at every step "
+                     "j = 0..H, no early exit; unsafe = steps the band rule would decide wrongly; "
+                     "max_error_over_band_or_slack = max |s32 - s64| / max(band, |s64|) (below 1: exact)"}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -439,7 +541,8 @@ def run_gpu(args):
 
     p = inputs.fc3_params()
     W, K = args.warmup, args.steps
-    T = W + K
+    S0 = window_start(W, K, args.window_start)   # first timed update
+    T = S0 + K
     seed = SEED + 1000 * rank          # replicas run independent closed loops
     r_seq = inputs.staircase(T, 8, 125, SEED)
     amp = np.array(inputs.DIST_AMP)
@@ -468,9 +571,10 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
-    # warm-up updates (also initialise the loop state on the device and
-    # capture the one-update CUDA graph the timed updates replay)
-    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, W, seed, 0, amp, True, d_v, d_k, d_f, d_x)
+    # the updates before the window, the last W of them the warm-up (they
+    # also initialise the loop state on the device and capture the one-update
+    # CUDA graph the timed updates replay)
+    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, S0, seed, 0, amp, True, d_v, d_k, d_f, d_x)
     torch.cuda.synchronize()
     g.reset_stats()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -502,7 +606,7 @@ def run_gpu(args):
     gd.set_tuning(tune_m, tune_probe)
     dd_v, dd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
     dd_f, dd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
-    R.rrg_closed_loop_dev(gd.h, x0, V0, d_r, W, seed, 0, amp, False, dd_v, dd_k, dd_f, dd_x)
+    R.rrg_closed_loop_dev(gd.h, x0, V0, d_r, S0, seed, 0, amp, False, dd_v, dd_k, dd_f, dd_x)
     torch.cuda.synchronize()
     gd.reset_stats()
     gd.set_profiling(True)
@@ -531,7 +635,7 @@ def run_gpu(args):
     gr.set_tuning(tune_m, tune_probe)
     rd_v, rd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
     rd_f, rd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
-    R.rrg_closed_loop_dev(gr.h, x0, V0, d_r, W, seed, 0, amp, True, rd_v, rd_k, rd_f, rd_x)
+    R.rrg_closed_loop_dev(gr.h, x0, V0, d_r, S0, seed, 0, amp, True, rd_v, rd_k, rd_f, rd_x)
     revs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -574,29 +678,24 @@ def run_gpu(args):
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
         e2e = None
         if not args.no_e2e:
-            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, (tune_m, tune_probe))
+            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, S0, T, flush, kap_dev, (tune_m, tune_probe))
 
-        # plain FP64 bisection on the same GPU, same updates
-        nf = min(args.fp64_steps, K)
-        fp64 = None
-        if nf > 0:
-            cfg64 = R.rrg_config_default(horizon=HZ, n_scenarios=NS, max_candidates=M_CAND,
-                                         n_bisect=N_BISECT, search=R.SEARCH_BISECT, precision=R.FP64,
-                                         early_exit=R.EXIT_CANDIDATE)
-            g3 = R.Governor(p, cfg64, stream)
-            ms64, kap64 = [], []
-            v_dev = d_v.cpu().numpy()
-            for t in range(W, W + nf):
-                g3.sample_scenarios(seed, t)
-                flush.fill_(0.0)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                _, kk, _ = g3.step(x_dev[t], r_seq[t], v_dev[t - 1] if t else V0)
-                ms64.append(1e3 * (time.perf_counter() - t0))
-                kap64.append(kk)
-            g3.close()
-            fp64 = {"value": 1e3 / statistics.mean(ms64), "unit": UNIT, "ms_per_update": statistics.mean(ms64),
-                    "updates": nf, "kappa_equal_to_fp32_recheck": bool(np.all(np.array(kap64) == kap_dev[W:W + nf]))}
+        # plain FP64 bisection on the same GPU over the same timed updates,
+        # timed the same way (CUDA events around each update, L2 flushed in
+        # between): the same closed loop through rrg_closed_loop_dev, started
+        # from the binary32 run's state at the window (its kappas, and so its
+        # states, must then agree update by update)
+        v_dev = d_v.cpu().numpy()
+        nf = K if args.fp64_steps is None else min(args.fp64_steps, K)
+        fp64 = fp64_comparator(R, torch, p, stream, flush, HZ, NS, seed, amp, d_r, S0, nf,
+                               x_dev[S0], v_dev[S0 - 1] if S0 else V0, kap_dev[S0:S0 + nf], dev)
+        # binary32 slack error against binary64 on sampled timed updates
+        probe_ts = sorted({S0, min(max(125, S0), T - 1), S0 + K // 2, T - 1})
+        fp32_err = fp32_error_probe(R, p, stream, HZ, NS, seed,
+                                    [(t, x_dev[t], v_dev[t - 1] if t else V0, r_seq[t], kap_dev[t])
+                                     for t in probe_ts])
+        if fp64 is not None:
+            fp32_err["kappa_max_abs_diff_fp64"] = fp64["kappa_max_abs_diff"]
 
         cpu = None
         if not args.no_cpu_baseline and (NS, HZ) == (N_SCEN, HORIZON):
@@ -622,7 +721,7 @@ def run_gpu(args):
             "ms_per_step": 1e3 * total_s / K, "ms_per_step_median": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
+            "config": workload_config(S0, W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -654,10 +753,12 @@ def run_gpu(args):
             "gpu_launches": st["launches"],
             "clocks": clk,
             "fp64_bisect_gpu": fp64,
+            "fp32_error": fp32_err,
             "rechecked_trajectories": st["rechecked"],
             "pipeline_repairs": st["repairs"],
-            "no_admissible_updates": int(np.sum(flags_dev[W:T] & 1)),
-            "kappa_mean": float(np.mean(kap_dev[W:T])),
+            "no_admissible_updates": int(np.sum(flags_dev[S0:T] & 1)),
+            "kappa_mean": float(np.mean(kap_dev[S0:T])),
+            "kappa_max": float(np.max(kap_dev[S0:T])),
         }
     g.close()
     if dist:

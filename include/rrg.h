@@ -255,6 +255,38 @@ RRG_API int rrg_eval_candidates(rrg_handle h, const double *x_t, double v_prev, 
                         const double *kappas, int m, uint8_t *admissible,
                         double *min_slack, uint8_t *P);
 
+/* Error of the binary32 rollouts against binary64, per trajectory and per
+ * step: the quantity behind the FP32 + FP64-recheck rule (the paper reports
+ * no visible effect of single precision in Sec. III-C and leaves its accuracy
+ * open in Sec. V).  For each of the m candidate kappas (host, each in [0, 1])
+ * and each scenario k of the current scenarios, the trajectory from x_t is
+ * integrated over the full horizon, without early exit, twice: exactly as the
+ * binary32 rollouts integrate it (stored binary32 disturbances, the same
+ * constants and right-hand side) and exactly as the binary64 rollouts and the
+ * recheck do (binary64 disturbances, regenerated from their Philox counters
+ * unless rrg_set_scenarios stored them).  Host outputs, each m * N values at
+ * [i * N + k]:
+ *   err[]     max over j = 0..H of |s32_j - s64_j| (+inf where exactly one
+ *             side is non-finite at some step, 0 at steps where both are)
+ *   j_err[]   (optional) the first step attaining it
+ *   smin32[]  (optional) min over j of s32_j (as binary64); equals the
+ *             binary32 rollout's min slack of that trajectory bit for bit
+ *   smin64[]  (optional) min over j of s64_j
+ *   unsafe[]  (optional) number of steps at which the recheck rule with the
+ *             absolute band `band` decides wrongly: s32_j >= band but
+ *             s64_j < 0, or s32_j < -band but s64_j >= 0.  The handle's
+ *             band is recheck_eps_rel * |y_min|.
+ *   ratio[]   (optional) max over j of |s32_j - s64_j| / max(band, |s64_j|):
+ *             below 1, no step of the trajectory can be decided wrongly by
+ *             the band rule (1 / ratio is the margin)
+ * The handle must use RRG_FP32 or RRG_FP32_RECHECK (RRG_EINVAL otherwise);
+ * 1 <= m <= max_candidates; band finite and >= 0.  Allocates 40 m N bytes of
+ * device scratch on first use (grown on demand).  Synchronous.  RRG_EINVAL,
+ * RRG_ECUDA. */
+RRG_API int rrg_slack_error(rrg_handle h, const double *x_t, double v_prev, double r_t,
+                    const double *kappas, int m, double band, double *err, int32_t *j_err,
+                    double *smin32, double *smin64, int32_t *unsafe, double *ratio);
+
 /* One robust RG update with the configured search on the current scenarios.
  * Host in: x_t[3], r_t, v_prev.  Host out: *v_t (Eq. 2 applied to the chosen
  * kappa, evaluated as v_prev + kappa * (r_t - v_prev) without fused

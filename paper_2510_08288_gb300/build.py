@@ -19,12 +19,15 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "librrg.so")
 SOURCES = ("rrg_kernels.cu", "rrg_capi.cu", "rrg_static.cu", "rrg_adjoint.cu", "rrg_batch.cu",
-           "rrg_peaks.cu")
+           "rrg_peaks.cu", "rrg_error.cu")
 HEADERS = ("rrg_device.cuh", "rrg_internal.h", "rrg_lane.cuh")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: the binary32 rollouts never meet subnormal values, and flushing
 # lets lg2/ex2/rcp issue as single MUFU operations on the critical path
+# -ffp-contract=off for the host compiler: host code folds constants the
+# device folds too (fold_rhs) and must not fuse them differently
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+              "-Xcompiler", "-ffp-contract=off",
               "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
 

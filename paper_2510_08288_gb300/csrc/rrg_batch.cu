@@ -201,21 +201,9 @@ __global__ void batch_prepare_kernel(const BLaunch B) {
   const size_t slot = static_cast<size_t>(s) * M + i;
   const double v = governed(st.v_prev, st.r, B.cand_kappa[slot]);
   B.cand_v[slot] = v;
-  const CandK<double> C = cand_consts(B.params, v);
-  fold_rhs_cand(B.k64, C, B.cand_c64 + slot, B.cand_c32 + slot);
-  int ok = 1;
-  if (B.c.ss_check) {
-    const double thr = __dadd_rn(B.c.y_min, __dmul_rn(B.c.eps_ss, __dsub_rn(B.c.y_c, B.c.y_min)));
-    float q32[3], y32 = 0.0f;
-    const bool v_ok = v > 0.0 && v <= DBL_MAX;
-    const int rc32 = v_ok ? equilibrium_from<float>(B.k32, B.params, C, q32, &y32) : -1;
-    if (rc32 == 0 && fabs(static_cast<double>(y32) - thr) > 1e-4 * (1.0 + fabs(thr))) {
-      ok = static_cast<double>(y32) >= thr;
-    } else {
-      double q[3], y_ss = 0.0;
-      ok = v_ok && equilibrium_from<double>(B.k64, B.params, C, q, &y_ss) == 0 && y_ss >= thr;
-    }
-  }
+  const double thr = __dadd_rn(B.c.y_min, __dmul_rn(B.c.eps_ss, __dsub_rn(B.c.y_c, B.c.y_min)));
+  const int ok = candidate_setup(B.k64, B.k32, B.params, v, B.c.ss_check, thr, B.c.y_min,
+                                 B.cand_c64 + slot, B.cand_c32 + slot);
   B.cand_ok[slot] = ok;
   B.cand_ss[slot] = ok;
   B.cand_dead[slot] = ok ? 0 : 1;
@@ -245,13 +233,14 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
   if (active) {
     const BState& st = B.st[s];
     const double p_atm = B.params[P_P_ATM];
-    float q_ca = static_cast<float>(st.x[0] - p_atm), w = static_cast<float>(st.x[1]),
-          q_sm = static_cast<float>(st.x[2] - p_atm);
+    const RhsC<float> C = B.cand_c32[slot];
+    float q_ca, w, q_sm, w_abs;  // the deviation from the candidate's reference point
+    start_state<float>(C, st.x, p_atm, q_ca, w, q_sm, w_abs);
     int end = LANE_REACHED_END;
     const float* d = (st.cur ? B.d32b : B.d32) + I.off;
-    smin = run_lane<float, PF>(B.u32, B.cand_c32[slot], d, k, I.N, I.H, 0, I.H, q_ca,
-                               w, q_sm, inf_v<float>(), static_cast<float>(B.c.dt),
-                               static_cast<float>(B.c.y_min), thr, cand_stop ? dead : nullptr,
+    smin = run_lane<float, PF>(B.u32, C, d, k, I.N, I.H, 0, I.H, q_ca,
+                               w, q_sm, w_abs, inf_v<float>(), static_cast<float>(B.c.dt),
+                               thr, cand_stop ? dead : nullptr,
                                &steps, &end, eps, &jlast);
     if (cand_stop && smin < thr) *dead = 1;
   }
@@ -375,10 +364,12 @@ __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
     src.amp[1] = B.c.amp[1];
     src.amp[2] = B.c.amp[2];
     unsigned steps = 0;
-    const double smin = run_lane_philox(B.u64, B.cand_c64[slot], src, k,
+    const RhsC<double> C = B.cand_c64[slot];
+    double q_ca, w, q_sm, w_abs;
+    start_state<double>(C, st.x, p_atm, q_ca, w, q_sm, w_abs);
+    const double smin = run_lane_philox(B.u64, C, src, k,
                                         min(static_cast<int>(B.recheck_jlast[e]), B.inst[s].H),
-                                        st.x[0] - p_atm, st.x[1], st.x[2] - p_atm, B.c.dt,
-                                        B.c.y_min,
+                                        q_ca, w, q_sm, w_abs, B.c.dt,
                                         B.c.early_exit != RRG_EXIT_NONE ? 0.0 : -inf_v<double>(),
                                         &steps);
     if (!(smin >= 0.0)) B.cand_ok[slot] = 0;

@@ -48,6 +48,9 @@ struct rrg_ctx {
   double* adj_seg = nullptr;
   size_t adj_seg_cap = 0;
   double* adj_out = nullptr;   // [0] g, [1..2] k*, j* (as long long), [3..] gradient
+  // binary32-vs-binary64 slack error per lane (allocated on first use)
+  void* err_buf = nullptr;
+  size_t err_cap = 0;
   // the captured one-update graph of the last closed loop, reused while the
   // run's pointers and indices stay the same
   cudaGraphExec_t cl_exec = nullptr;
@@ -176,7 +179,7 @@ void free_all(rrg_ctx* h) {
                   h->cand_min, h->recheck_list, h->recheck_jlast, h->recheck_count, h->stats, h->P_dev, h->io_dev,
                   h->flag_dev, h->kap_dev, h->adm_dev, h->loop, h->cl_dev, h->lane_state,
                   h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
-                  h->pmul, h->pmulb, h->pws};
+                  h->pmul, h->pmulb, h->pws, h->err_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->io_h) cudaFreeHost(h->io_h);
@@ -700,6 +703,58 @@ int rrg_eval_candidates(rrg_handle h, const double* x_t, double v_prev, double r
   CK(cudaStreamSynchronize(h->stream));
   std::memcpy(admissible, adm_h, m);
   if (min_slack) std::memcpy(min_slack, kap_h + M, m * sizeof(double));
+  return RRG_OK;
+}
+
+int rrg_slack_error(rrg_handle h, const double* x_t, double v_prev, double r_t,
+                    const double* kappas, int m, double band, double* err, int32_t* j_err,
+                    double* smin32, double* smin64, int32_t* unsafe, double* ratio) {
+  if (!h) return RRG_EINVAL;
+  if (h->cfg.precision == RRG_FP64)
+    return set_err(h, RRG_EINVAL, "the handle draws no binary32 scenarios (precision RRG_FP64)");
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite and v_prev, r_t > 0");
+  if (!kappas || !err || m < 1 || m > h->cfg.max_candidates)
+    return set_err(h, RRG_EINVAL, "need 1 <= m <= max_candidates and non-NULL kappas/err");
+  if (!(band >= 0.0) || !(band <= 1e30))
+    return set_err(h, RRG_EINVAL, "band must be finite and >= 0");
+  for (int i = 0; i < m; ++i)
+    if (!(kappas[i] >= 0.0 && kappas[i] <= 1.0))
+      return set_err(h, RRG_EINVAL, "kappas[%d] outside [0, 1]", i);
+  DeviceGuard g(h->device);
+  const size_t lanes = static_cast<size_t>(m) * h->cfg.n_scenarios;
+  const size_t need = lanes * (4 * sizeof(double) + 2 * sizeof(int32_t));
+  if (need > h->err_cap) {
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->err_buf) cudaFree(h->err_buf);
+    h->err_buf = nullptr;
+    h->err_cap = 0;
+    CK(cudaMalloc(&h->err_buf, need));
+    h->err_cap = need;
+  }
+  double* d_err = static_cast<double*>(h->err_buf);
+  double* d_s32 = d_err + lanes;
+  double* d_s64 = d_s32 + lanes;
+  double* d_ratio = d_s64 + lanes;
+  int32_t* d_j = reinterpret_cast<int32_t*>(d_ratio + lanes);
+  int32_t* d_bad = d_j + lanes;
+  double* kap_h = h->io_h + IO_LEN;
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  std::memcpy(kap_h, kappas, m * sizeof(double));
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, IO_LEN * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->kap_dev, kap_h, m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const Launch& L = h->L;
+  CK(launch_eval_prepare(L, h->io_dev + IO_X, v_prev, r_t, h->kap_dev, m));
+  CK(launch_prepare(L, m));
+  CK(launch_slack_error(L, m, static_cast<float>(band), d_err, d_j, d_s32, d_s64, d_bad, d_ratio));
+  h->launches += 3;
+  CK(cudaMemcpyAsync(err, d_err, lanes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (smin32) CK(cudaMemcpyAsync(smin32, d_s32, lanes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (smin64) CK(cudaMemcpyAsync(smin64, d_s64, lanes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (j_err) CK(cudaMemcpyAsync(j_err, d_j, lanes * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (unsafe) CK(cudaMemcpyAsync(unsafe, d_bad, lanes * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (ratio) CK(cudaMemcpyAsync(ratio, d_ratio, lanes * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return RRG_OK;
 }
 

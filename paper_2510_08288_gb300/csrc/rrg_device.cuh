@@ -139,29 +139,45 @@ __device__ __forceinline__ void rk4_step(const Fc3K<T>& K, const CandK<T>& C, T 
 
 // ---------------------------------------------------------------------------
 // The same right-hand side with its constants multiplied out, for the
-// rollouts (the equilibrium solve, the simulated plant and the adjoint keep
-// the form above).  With s = q_sm - q_ca and W_cp = a_w w - a_p q_sm:
-//   d_ca = RT_Vca (k_sm s - k_ca q_ca - W_o2)          = a1 s - a2 q_ca - a3
-//   d_sm = RT_Vsm (W_cp - k_sm s)                        = RT_Vsm W_cp - b3 s
+// rollouts (the equilibrium solve and the adjoint keep the form above), in
+// deviation coordinates z = q - q_r about a reference point q_r of the
+// candidate (its binary32 equilibrium; 0 gives the gauge form):
+//   d_ca = RT_Vca (k_sm (p_sm - p_ca) - k_ca p_ca - W_o2)
+//        = a1 z_sm - (a1 + a2) z_ca + c_ca
+//   d_sm = RT_Vsm (W_cp - k_sm (p_sm - p_ca))
+//        = RT_Vsm a_w z_w - (RT_Vsm a_p + b3) z_sm + b3 z_ca + c_sm
 //   d_w  = (C_m (V0 - K_p W_cp - k_v w) - C_cp pr W_cp / w) / J
-//        = (e0 - e2 w) - W_cp (e1 + e3 pr / w)
-// which is 17 instructions per evaluation in binary32 (3 of them MUFU)
-// against about 24 for the form above.
+//        = (e0 - e2 z_w) - W_cp (e1 + e3 pr / w),
+//   W_cp = a_w z_w - a_p z_sm + W_r,  w = w_r + z_w
+// where c_ca, c_sm (the derivatives at q_r), W_r and e0 are folded in
+// binary64 and rounded once.  Near the reference every binary32 term is of
+// the size of the deviation, not of the ~1e4 Pa gauge pressures, so the
+// state's rounding and the cancellations between the flow terms shrink with
+// it (and the terms can be multiplied out without losing digits).  16
+// instructions per evaluation in binary32 (3 of them MUFU), as many as the
+// gauge form, plus five per step that carry the absolute speed w (see
+// rk4_step_fast).
 template <typename T>
-struct RhsU {    // constants of the model (per scenario under parametric uncertainty)
-  T a1, a2;      // RT_Vca k_sm, RT_Vca k_ca
-  T a_w, a_p;    // compressor map
-  T RT_Vsm, b3;  // RT_Vsm, RT_Vsm k_sm
+struct RhsU {      // constants of the model (per scenario under parametric uncertainty)
+  T a1, a12;       // RT_Vca k_sm, RT_Vca (k_sm + k_ca)
+  T a_w, a_p;      // compressor map
+  T b3;            // RT_Vsm k_sm
+  T g_w, g_sm;     // RT_Vsm a_w, RT_Vsm a_p + b3
   T inv_p_atm, e;
-  T e1, e2, e3;  // C_m K_p / J, C_m k_v / J, C_cp / J
+  T e1, e2, e3;    // C_m K_p / J, C_m k_v / J, C_cp / J
   const PowSeries* pws;  // binary64 x^e - 1 (device memory; nullptr: pow)
 };
 
 template <typename T>
 struct RhsC {    // constants of the candidate setpoint v (and the scenario's model)
-  T a3;          // RT_Vca W_o2
-  T e0;          // C_m V0 / J
+  T c_ca;        // d_ca at q_r: a1 s_r - a2 ca_r - RT_Vca W_o2
+  T c_sm;        // d_sm at q_r: RT_Vsm W_r - b3 s_r
+  T W_r;         // compressor flow at q_r: a_w w_r - a_p sm_r
+  T e0;          // C_m V0 / J - e2 w_r
+  T x_r;         // 1 + sm_r / p_atm
   T y_scale;     // x_O2 k_sm / W_o2
+  T s_off;       // slack at q_r: y_scale s_r - y_min
+  T r_ca, r_w, r_sm;  // q_r (binary32 values, so both precisions share it)
 };
 
 // x^e - 1 for the compressor term, x = 1 + q_sm / p_atm formed by the caller.
@@ -176,22 +192,38 @@ __device__ __forceinline__ float pow_m1<float>(float x, float e, const PowSeries
   return __powf(x, e) - 1.0f;
 }
 
-// x_pw = 1 + q_sm / p_atm is passed in: the caller forms it from the
-// previous stage's d_sm directly (x_pw + (h / p_atm) d_sm), one dependent
-// operation shorter than through the stage state.  e3 / w is formed apart
-// from the compressor power term, so the longest dependent chain of an
-// evaluation is 1 + u -> lg2 -> x e -> ex2 -> - 1 -> f -> d_w.
+// The compressor torque factor f = e1 + e3 pr / w.  binary32: e3 pr is
+// formed on the power term's path and the approximate reciprocal of w feeds
+// the final multiply-add directly (w arrives last, from the previous stage's
+// d_w); binary64: IEEE division.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+template <typename T> __device__ __forceinline__ T torque_factor(const RhsU<T>& U, T pr, T w);
+template <>
+__device__ __forceinline__ float torque_factor<float>(const RhsU<float>& U, float pr, float w) {
+  return fmaf(U.e3 * pr, rcp_approx(w), U.e1);
+}
+template <>
+__device__ __forceinline__ double torque_factor<double>(const RhsU<double>& U, double pr, double w) {
+  return U.e1 + (U.e3 / w) * pr;
+}
+
+// x_pw = x_r + z_sm / p_atm and the absolute speed w = w_r + z_w are passed
+// in: the caller forms both from the previous stage's derivatives directly
+// (x_pw + (h / p_atm) d_sm, w + h d_w), one dependent operation shorter than
+// through the stage state.  The terms with z_w, the component that arrives
+// last, are added last.
 template <typename T>
-__device__ __forceinline__ void fc3_rhs_fast(const RhsU<T>& U, const RhsC<T>& C, T q_ca, T w,
-                                             T q_sm, T x_pw, T& d_ca, T& d_w, T& d_sm) {
-  const T s = q_sm - q_ca;
-  const T W_cp = U.a_w * w - U.a_p * q_sm;
-  d_ca = U.a1 * s - U.a2 * q_ca - C.a3;
-  d_sm = U.RT_Vsm * W_cp - U.b3 * s;
-  const T pr = pow_m1<T>(x_pw, U.e, U.pws);
-  const T t = div_fast<T>(U.e3, w);
-  const T f = U.e1 + t * pr;
-  d_w = (C.e0 - U.e2 * w) - W_cp * f;
+__device__ __forceinline__ void fc3_rhs_fast(const RhsU<T>& U, const RhsC<T>& C, T z_ca, T z_w,
+                                             T z_sm, T w, T x_pw, T& d_ca, T& d_w, T& d_sm) {
+  d_ca = U.a1 * z_sm + (C.c_ca - U.a12 * z_ca);
+  d_sm = U.g_w * z_w + ((C.c_sm + U.b3 * z_ca) - U.g_sm * z_sm);
+  const T W_cp = U.a_w * z_w + (C.W_r - U.a_p * z_sm);
+  const T f = torque_factor<T>(U, pow_m1<T>(x_pw, U.e, U.pws), w);
+  d_w = (C.e0 - U.e2 * z_w) - W_cp * f;
 }
 
 // Step-size constants of rk4_step_fast, formed once per trajectory (the
@@ -212,30 +244,43 @@ __device__ __forceinline__ StepC<T> step_consts(const RhsU<T>& U, T dt) {
 }
 
 // One RK4 step of size dt followed by the disturbance (e_ca, e_w, e_sm) of
-// Eq. 4, in place.  The update is summed as ((q + e) + h/6 (k1 + 2 (k2 +
-// k3))) + h/6 k4, so only one operation follows the last stage.
+// Eq. 4, in place, on the deviation z = (q_ca, w, q_sm) - q_r.  w_abs is the
+// absolute compressor speed w_r + w that the torque term divides by: it is
+// re-derived from the deviation every step ((p_w + w_r) + h/6 k4 next to
+// p_w + h/6 k4), so it never drifts from it by more than a rounding, and the
+// stage points form it from the previous stage's d_w in one operation.  (A
+// first-order update of one reciprocal per step would not do: in the largest
+// FC3 transients w moves by up to 20 % within half a step.)  The update is
+// summed as ((z + e) + h/6 (k1 + 2 (k2 + k3))) + h/6 k4, so only one
+// operation follows the last stage.
 template <typename T>
 __device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C, const StepC<T>& S,
-                                              T& q_ca, T& w, T& q_sm, T e_ca, T e_w, T e_sm) {
+                                              T& q_ca, T& w, T& q_sm, T& w_abs, T e_ca, T e_w,
+                                              T e_sm) {
   const T dt = S.dt, h2 = S.h2, h6 = S.h6, g2 = S.g2, g1 = S.g1;
-  const T x1 = q_sm * U.inv_p_atm + T(1);
+  const T x1 = q_sm * U.inv_p_atm + C.x_r;
   T a1, b1, c1, a2, b2, c2, a3, b3, c3, a4, b4, c4;
-  fc3_rhs_fast<T>(U, C, q_ca, w, q_sm, x1, a1, b1, c1);
-  fc3_rhs_fast<T>(U, C, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, x1 + g2 * c1, a2, b2, c2);
-  fc3_rhs_fast<T>(U, C, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, x1 + g2 * c2, a3, b3, c3);
+  fc3_rhs_fast<T>(U, C, q_ca, w, q_sm, w_abs, x1, a1, b1, c1);
+  fc3_rhs_fast<T>(U, C, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, w_abs + h2 * b1, x1 + g2 * c1,
+                  a2, b2, c2);
+  fc3_rhs_fast<T>(U, C, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, w_abs + h2 * b2, x1 + g2 * c2,
+                  a3, b3, c3);
   const T p_ca = (q_ca + e_ca) + h6 * (a1 + T(2) * (a2 + a3));
   const T p_w = (w + e_w) + h6 * (b1 + T(2) * (b2 + b3));
   const T p_sm = (q_sm + e_sm) + h6 * (c1 + T(2) * (c2 + c3));
-  fc3_rhs_fast<T>(U, C, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, x1 + g1 * c3, a4, b4, c4);
+  const T p_wa = p_w + C.r_w;
+  fc3_rhs_fast<T>(U, C, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, w_abs + dt * b3, x1 + g1 * c3,
+                  a4, b4, c4);
   q_ca = p_ca + h6 * a4;
   w = p_w + h6 * b4;
   q_sm = p_sm + h6 * c4;
+  w_abs = p_wa + h6 * b4;
 }
 
 template <typename T>
 __device__ __forceinline__ void rk4_step_fast(const RhsU<T>& U, const RhsC<T>& C, T dt, T& q_ca,
-                                              T& w, T& q_sm, T e_ca, T e_w, T e_sm) {
-  rk4_step_fast<T>(U, C, step_consts<T>(U, dt), q_ca, w, q_sm, e_ca, e_w, e_sm);
+                                              T& w, T& q_sm, T& w_abs, T e_ca, T e_w, T e_sm) {
+  rk4_step_fast<T>(U, C, step_consts<T>(U, dt), q_ca, w, q_sm, w_abs, e_ca, e_w, e_sm);
 }
 
 // ---------------------------------------------------------------------------

@@ -41,7 +41,8 @@ struct Seg {
 // 1: finished in the probe and already reduced).
 template <typename T>
 struct LaneState {
-  T q[3];
+  T q[3];         // deviation from the candidate's reference point
+  T w_abs;        // the absolute speed carried with it
   T smin;
   int32_t status;
   int32_t jlast;  // last step with slack below the recheck band so far (-1: none)
@@ -231,30 +232,50 @@ __device__ __forceinline__ CandK<float> cand_round(const CandK<double>& C) {
   return F;
 }
 
-// The multiplied-out constants of the rollout right-hand side (products of
-// the folded binary64 constants, each rounded once to binary32).
+// Binary64 product and sum rounded on their own on host and device alike
+// (the device compiler would otherwise fuse a product into a following add).
+__host__ __device__ inline double mul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ inline double add_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+
+// The multiplied-out constants of the rollout right-hand side (products and
+// sums of the folded binary64 constants, each rounded on its own, then
+// rounded once to binary32), the same bits on the host and the device.
 __host__ __device__ inline void fold_rhs(const Fc3K<double>& K, RhsU<double>* u64, RhsU<float>* u32) {
   RhsU<double> U;
-  U.a1 = K.RT_Vca * K.k_sm;
-  U.a2 = K.RT_Vca * K.k_ca;
+  U.a1 = mul_rn(K.RT_Vca, K.k_sm);
+  U.a12 = add_rn(U.a1, mul_rn(K.RT_Vca, K.k_ca));
   U.a_w = K.a_w;
   U.a_p = K.a_p;
-  U.RT_Vsm = K.RT_Vsm;
-  U.b3 = K.RT_Vsm * K.k_sm;
+  U.b3 = mul_rn(K.RT_Vsm, K.k_sm);
+  U.g_w = mul_rn(K.RT_Vsm, K.a_w);
+  U.g_sm = add_rn(mul_rn(K.RT_Vsm, K.a_p), U.b3);
   U.inv_p_atm = K.inv_p_atm;
   U.e = K.e;
-  U.e1 = K.C_m * K.K_p * K.inv_J;
-  U.e2 = K.C_m * K.k_v * K.inv_J;
-  U.e3 = K.C_cp * K.inv_J;
+  U.e1 = mul_rn(mul_rn(K.C_m, K.K_p), K.inv_J);
+  U.e2 = mul_rn(mul_rn(K.C_m, K.k_v), K.inv_J);
+  U.e3 = mul_rn(K.C_cp, K.inv_J);
   U.pws = K.pws;
   *u64 = U;
   RhsU<float> F;
   F.a1 = static_cast<float>(U.a1);
-  F.a2 = static_cast<float>(U.a2);
+  F.a12 = static_cast<float>(U.a12);
   F.a_w = static_cast<float>(U.a_w);
   F.a_p = static_cast<float>(U.a_p);
-  F.RT_Vsm = static_cast<float>(U.RT_Vsm);
   F.b3 = static_cast<float>(U.b3);
+  F.g_w = static_cast<float>(U.g_w);
+  F.g_sm = static_cast<float>(U.g_sm);
   F.inv_p_atm = static_cast<float>(U.inv_p_atm);
   F.e = static_cast<float>(U.e);
   F.e1 = static_cast<float>(U.e1);
@@ -264,16 +285,40 @@ __host__ __device__ inline void fold_rhs(const Fc3K<double>& K, RhsU<double>* u6
   *u32 = F;
 }
 
-__host__ __device__ inline void fold_rhs_cand(const Fc3K<double>& K, const CandK<double>& C,
+// Candidate constants of the rollouts about the reference point q_r (gauge
+// coordinates; binary32 values, or 0 for the gauge form), with the output
+// bound y_min folded into the slack offset.  Every operation is rounded on
+// its own in binary64 (no fused multiply-add), so each call site computes the
+// same bits; the products a1, a2, b3, e2 are those of fold_rhs.
+__device__ __forceinline__ void fold_rhs_cand(const Fc3K<double>& K, const CandK<double>& C,
+                                              const double q_r[3], double y_min,
                                               RhsC<double>* c64, RhsC<float>* c32) {
+  const double a1 = __dmul_rn(K.RT_Vca, K.k_sm), a2 = __dmul_rn(K.RT_Vca, K.k_ca);
+  const double b3 = __dmul_rn(K.RT_Vsm, K.k_sm);
+  const double e2 = __dmul_rn(__dmul_rn(K.C_m, K.k_v), K.inv_J);
+  const double s_r = __dsub_rn(q_r[2], q_r[0]);
   RhsC<double> R;
-  R.a3 = K.RT_Vca * C.W_o2;
-  R.e0 = K.C_m * C.V0 * K.inv_J;
+  R.W_r = __dsub_rn(__dmul_rn(K.a_w, q_r[1]), __dmul_rn(K.a_p, q_r[2]));
+  R.c_ca = __dsub_rn(__dsub_rn(__dmul_rn(a1, s_r), __dmul_rn(a2, q_r[0])), __dmul_rn(K.RT_Vca, C.W_o2));
+  R.c_sm = __dsub_rn(__dmul_rn(K.RT_Vsm, R.W_r), __dmul_rn(b3, s_r));
+  R.e0 = __dsub_rn(__dmul_rn(__dmul_rn(K.C_m, C.V0), K.inv_J), __dmul_rn(e2, q_r[1]));
+  R.x_r = __dadd_rn(1.0, __dmul_rn(q_r[2], K.inv_p_atm));
   R.y_scale = C.y_scale;
+  R.s_off = __dsub_rn(__dmul_rn(C.y_scale, s_r), y_min);
+  R.r_ca = q_r[0];
+  R.r_w = q_r[1];
+  R.r_sm = q_r[2];
   *c64 = R;
-  c32->a3 = static_cast<float>(R.a3);
+  c32->c_ca = static_cast<float>(R.c_ca);
+  c32->c_sm = static_cast<float>(R.c_sm);
+  c32->W_r = static_cast<float>(R.W_r);
   c32->e0 = static_cast<float>(R.e0);
+  c32->x_r = static_cast<float>(R.x_r);
   c32->y_scale = static_cast<float>(R.y_scale);
+  c32->s_off = static_cast<float>(R.s_off);
+  c32->r_ca = static_cast<float>(R.r_ca);
+  c32->r_w = static_cast<float>(R.r_w);
+  c32->r_sm = static_cast<float>(R.r_sm);
 }
 
 // Coefficients of the binary64 x^e - 1 series (host).
@@ -334,6 +379,15 @@ cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double
                            double kappa, int checkpoint, double* ckpt, double* lane_min,
                            int* lane_arg, double* seg, double* d_g, long long* d_kj,
                            double* d_out, cudaEvent_t fwd_begin, cudaEvent_t fwd_end);
+
+// Binary32-vs-binary64 slack error of every trajectory of the m candidates
+// the last eval_prepare + prepare set up (rrg_error.cu): per lane o = i N + k
+// the largest |s32_j - s64_j| over j = 0..H and its step, both min slacks and
+// the number of steps the band rule [-band, band) would decide wrongly and
+// the largest ratio of a step's error to max(band, |s64_j|).  j_err, smin32,
+// smin64, unsafe, ratio may be null.
+cudaError_t launch_slack_error(const Launch& L, int m, float band, double* err, int32_t* j_err,
+                               double* smin32, double* smin64, int32_t* unsafe, double* ratio);
 
 // Configuration check shared with the handle-less entry point (rrg_capi.cu);
 // on failure the message is readable with rrg_last_error(NULL).

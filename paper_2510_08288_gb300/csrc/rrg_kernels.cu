@@ -58,24 +58,25 @@ step_latency_kernel(const Launch L, const RhsU<float> U, double v, int steps, do
   const CandK<double> Cd = cand_consts(L.params, v);
   RhsC<double> c64;
   RhsC<float> c32;
-  fold_rhs_cand(L.k64, Cd, &c64, &c32);
   float q[3] = {0.0f, 0.0f, 0.0f}, y = 0.0f;
   const int rc = equilibrium_from<float>(L.k32, L.params, Cd, q, &y);
-  float q_ca = q[0] + 1e-3f * static_cast<float>(threadIdx.x), w = q[1], q_sm = q[2];
+  const double q_r[3] = {q[0], q[1], q[2]};
+  fold_rhs_cand(L.k64, Cd, q_r, L.y_min, &c64, &c32);
+  // deviation coordinates about the equilibrium, lanes slightly apart
+  float q_ca = 1e-3f * static_cast<float>(threadIdx.x), w = 0.0f, q_sm = 0.0f, w_abs = c32.r_w;
   const StepC<float> S = step_consts<float>(U, static_cast<float>(L.dt));
-  const float y_min = static_cast<float>(L.y_min);
   float smin = inf_v<float>(), nf = 0.0f;
   __syncwarp();
   const long long t0 = clock64();
 #pragma unroll 8
   for (int j = 0; j < steps; ++j) {
-    rk4_step_fast<float>(U, c32, S, q_ca, w, q_sm, 0.0f, 0.0f, 0.0f);
-    const float s = c32.y_scale * (q_sm - q_ca) - y_min;
+    rk4_step_fast<float>(U, c32, S, q_ca, w, q_sm, w_abs, 0.0f, 0.0f, 0.0f);
+    const float s = c32.y_scale * (q_sm - q_ca) + c32.s_off;
     smin = fminf(smin, s);
     nf = fma_rn(s, 0.0f, nf);
   }
   const long long t1 = clock64();
-  float r = smin + nf + q_ca + w + q_sm;
+  float r = smin + nf + q_ca + w + q_sm + w_abs;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   if (threadIdx.x == 0) {
@@ -315,9 +316,9 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
     if constexpr (PU)
       p_atm = scenario_model<T>(L.params,
                                 (L.st->buf ? L.pmulb : L.pmul) + static_cast<size_t>(k) * RRG_NPARAM,
-                                L.cand_v[i], L.k64.pws, K, C);
-    T q_ca = static_cast<T>(L.st->x[0] - p_atm), w = static_cast<T>(L.st->x[1]),
-      q_sm = static_cast<T>(L.st->x[2] - p_atm);
+                                L.cand_v[i], L.k64.pws, L.y_min, K, C);
+    T q_ca, w, q_sm, w_abs;  // the deviation from the candidate's reference point
+    start_state<T>(C, L.st->x, p_atm, q_ca, w, q_sm, w_abs);
     T smin0 = inf_v<T>();
     int j0 = 0;
     if (mode == SEG_CONTINUE) {
@@ -328,6 +329,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
         q_ca = st.q[0];
         w = st.q[1];
         q_sm = st.q[2];
+        w_abs = st.w_abs;
         smin0 = st.smin;
         jlast = st.jlast;
         j0 = L.probe_steps;
@@ -337,18 +339,18 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
       const int j_end = mode == SEG_PROBE ? L.probe_steps : L.H;
       int end = LANE_REACHED_END;
       if constexpr (SRC == SRC_GEN)
-        smin = run_lane_gen<T>(K, C, L.st->src[L.st->buf], k, j0, j_end, q_ca, w, q_sm, smin0,
-                               static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+        smin = run_lane_gen<T>(K, C, L.st->src[L.st->buf], k, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
+                               static_cast<T>(L.dt), thr,
                                cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
       else if constexpr (SRC == SRC_RING) {
         static_assert(sizeof(T) == 4, "the shared-memory ring is binary32");
         __shared__ float ring[RRG_RING_DEPTH * 3 * kRollThreads];
-        smin = run_lane_ring(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, smin0,
-                             static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+        smin = run_lane_ring(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
+                             static_cast<T>(L.dt), thr,
                              cand_stop ? dead : nullptr, &steps, &end, band, &jlast, ring);
       } else
-        smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, smin0,
-                           static_cast<T>(L.dt), static_cast<T>(L.y_min), thr,
+        smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
+                           static_cast<T>(L.dt), thr,
                            cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
       if (cand_stop && smin < thr) *dead = 1;
       if (mode == SEG_PROBE) {
@@ -356,6 +358,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
         o.q[0] = q_ca;
         o.q[1] = w;
         o.q[2] = q_sm;
+        o.w_abs = w_abs;
         o.smin = smin;
         o.status = end == LANE_REACHED_END ? 0 : 1;
         o.jlast = jlast;
@@ -493,17 +496,17 @@ recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
     const double* pm = buf ? L.pmulb : L.pmul;
     if (pm != nullptr)
       p_atm_k = scenario_model<double>(L.params, pm + static_cast<size_t>(k) * RRG_NPARAM,
-                                       L.cand_v[i], L.k64.pws, K, C);
+                                       L.cand_v[i], L.k64.pws, L.y_min, K, C);
+    double q_ca, w, q_sm, w_abs;
+    start_state<double>(C, L.st->x, p_atm_k, q_ca, w, q_sm, w_abs);
     if (src.d64_valid) {
       int end = 0;
-      double q_ca = L.st->x[0] - p_atm_k, w = L.st->x[1], q_sm = L.st->x[2] - p_atm_k;
       int jl = -1;
       smin = run_lane<double>(K, C, buf ? L.d64b : L.d64, k, N, L.H, 0, j_end, q_ca, w, q_sm,
-                              inf_v<double>(), L.dt, L.y_min, thr, nullptr, &steps, &end,
+                              w_abs, inf_v<double>(), L.dt, thr, nullptr, &steps, &end,
                               -inf_v<double>(), &jl);
     } else {
-      smin = run_lane_philox(K, C, src, k, j_end, L.st->x[0] - p_atm_k, L.st->x[1],
-                             L.st->x[2] - p_atm_k, L.dt, L.y_min, thr, &steps);
+      smin = run_lane_philox(K, C, src, k, j_end, q_ca, w, q_sm, w_abs, L.dt, thr, &steps);
     }
     const bool ok = smin >= 0.0;
     if (!ok) L.cand_ok[i] = 0;
@@ -708,27 +711,12 @@ __device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa
 // Eq. 3 and fresh flags.
 __device__ void prepare_slot(const Launch& L, int i) {
   const SearchState* s = L.st;
-  const Fc3K<double>& K = L.k64;
   const double thr_ss =
       __dadd_rn(L.scfg.y_min, __dmul_rn(L.scfg.eps_ss, __dsub_rn(L.scfg.y_c, L.scfg.y_min)));
   const double v = governed(s->v_prev, s->r, L.cand_kappa[i]);
   L.cand_v[i] = v;
-  const CandK<double> C = cand_consts(L.params, v);
-  fold_rhs_cand(K, C, L.cand_c64 + i, L.cand_c32 + i);
-  int ok = 1;
-  if (L.scfg.ss_check) {
-    // binary32 solve first; it decides unless y_ss lands within 1e-4 of the
-    // threshold (its error is ~1e-6), in which case binary64 decides
-    float q32[3], y32 = 0.0f;
-    const bool v_ok = v > 0.0 && v <= DBL_MAX;
-    const int rc32 = v_ok ? equilibrium_from<float>(L.k32, L.params, C, q32, &y32) : -1;
-    if (rc32 == 0 && fabs(static_cast<double>(y32) - thr_ss) > 1e-4 * (1.0 + fabs(thr_ss))) {
-      ok = static_cast<double>(y32) >= thr_ss;
-    } else {
-      double q[3], y_ss = 0.0;
-      ok = v_ok && equilibrium_from<double>(K, L.params, C, q, &y_ss) == 0 && y_ss >= thr_ss;
-    }
-  }
+  const int ok = candidate_setup(L.k64, L.k32, L.params, v, L.scfg.ss_check, thr_ss, L.y_min,
+                                 L.cand_c64 + i, L.cand_c32 + i);
   L.cand_ok[i] = ok;
   L.cand_ss[i] = ok;
   L.cand_dead[i] = ok ? 0 : 1;

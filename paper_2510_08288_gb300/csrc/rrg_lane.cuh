@@ -101,6 +101,48 @@ __device__ __forceinline__ int equilibrium_dev(const Fc3K<T>& K, const double* _
   return equilibrium_from<T>(K, P, cand_consts(P, I), q, y_ss);
 }
 
+// Candidate set-up shared by the single-problem and batched searches: the
+// binary32 equilibrium of setpoint v (Sec. II-A) is the reference point of
+// the rollouts' deviation coordinates (0 when it cannot be found), the
+// candidate's rollout constants are folded about it, and, when ss_check is
+// set, the steady-state check of Eq. 3 (y_ss(v) >= thr_ss) is decided by it
+// unless y_ss lands within 1e-4 of the threshold (its error is ~1e-6), in
+// which case a binary64 solve decides.  Returns the check's outcome (1 when
+// off).
+__device__ __forceinline__ int candidate_setup(const Fc3K<double>& k64, const Fc3K<float>& k32,
+                                               const double* __restrict__ P, double v, int ss_check,
+                                               double thr_ss, double y_min, RhsC<double>* c64,
+                                               RhsC<float>* c32) {
+  const CandK<double> C = cand_consts(P, v);
+  float q32[3] = {0.0f, 0.0f, 0.0f}, y32 = 0.0f;
+  const bool v_ok = v > 0.0 && v <= DBL_MAX;
+  const int rc32 = v_ok ? equilibrium_from<float>(k32, P, C, q32, &y32) : -1;
+  double q_r[3] = {0.0, 0.0, 0.0};
+  if (rc32 == 0 && fabsf(q32[0]) <= FLT_MAX && fabsf(q32[1]) <= FLT_MAX && fabsf(q32[2]) <= FLT_MAX) {
+    q_r[0] = q32[0];
+    q_r[1] = q32[1];
+    q_r[2] = q32[2];
+  }
+  fold_rhs_cand(k64, C, q_r, y_min, c64, c32);
+  if (!ss_check) return 1;
+  if (rc32 == 0 && fabs(static_cast<double>(y32) - thr_ss) > 1e-4 * (1.0 + fabs(thr_ss)))
+    return static_cast<double>(y32) >= thr_ss;
+  double q[3], y_ss = 0.0;
+  return v_ok && equilibrium_from<double>(k64, P, C, q, &y_ss) == 0 && y_ss >= thr_ss;
+}
+
+// Start of a trajectory: the deviation z = q - q_r of the absolute state x
+// (pressures measured from p_atm), formed in binary64 and rounded once, and
+// the absolute speed w_r + z_w that rk4_step_fast carries next to it.
+template <typename T>
+__device__ __forceinline__ void start_state(const RhsC<T>& C, const double* x, double p_atm, T& z_ca,
+                                            T& z_w, T& z_sm, T& w_abs) {
+  z_ca = static_cast<T>((x[0] - p_atm) - static_cast<double>(C.r_ca));
+  z_w = static_cast<T>(x[1] - static_cast<double>(C.r_w));
+  z_sm = static_cast<T>((x[2] - p_atm) - static_cast<double>(C.r_sm));
+  w_abs = C.r_w + z_w;
+}
+
 // ---------------------------------------------------------------------------
 // One trajectory: x_0 = x_t, x_{j+1} = RK4(x_j, v) + d_j, slack s_j =
 // h(x_j, v) - y_min at j = 0..H; a non-finite state or output counts as
@@ -125,9 +167,10 @@ __device__ __forceinline__ int equilibrium_dev(const Fc3K<T>& K, const double* _
 template <typename T> struct PrefetchDepth { static constexpr int value = RRG_PREFETCH; };
 template <> struct PrefetchDepth<double> { static constexpr int value = RRG_PREFETCH64; };
 
+// The slack y_j - y_min of the deviation state (y_min is folded into s_off).
 template <typename T>
-__device__ __forceinline__ T checked_slack(const RhsC<T>& C, T q_ca, T w, T q_sm, T y_min) {
-  const T s = C.y_scale * (q_sm - q_ca) - y_min;
+__device__ __forceinline__ T checked_slack(const RhsC<T>& C, T q_ca, T w, T q_sm) {
+  const T s = C.y_scale * (q_sm - q_ca) + C.s_off;
   const bool fin = fabs(q_ca) <= max_finite<T>() && fabs(w) <= max_finite<T>() &&
                    fabs(q_sm) <= max_finite<T>() && fabs(s) <= max_finite<T>();
   return fin ? s : -inf_v<T>();
@@ -154,7 +197,7 @@ enum LaneEnd : int { LANE_REACHED_END = 0, LANE_VIOLATED = 1, LANE_STOPPED = 2 }
 template <typename T, int PF = PrefetchDepth<T>::value>
 __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
                                       const T* __restrict__ d, int k, int N, int H, int j0,
-                                      int j_end, T& q_ca, T& w, T& q_sm, T smin_in, T dt, T y_min,
+                                      int j_end, T& q_ca, T& w, T& q_sm, T& w_abs, T smin_in, T dt,
                                       T thr, const volatile int32_t* dead, unsigned* steps,
                                       int* end, T band, int* jlast) {
   T smin = smin_in;
@@ -163,7 +206,7 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
   int how = LANE_REACHED_END;
   bool go = j < j_end;
   if (j0 == 0) {
-    const T s0 = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    const T s0 = checked_slack<T>(C, q_ca, w, q_sm);
     smin = fmin(smin, s0);
     if (s0 < band) jl = 0;
     if (s0 < thr) {
@@ -212,9 +255,9 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
           r2[u] = __ldg(pf + 2 * HN);
         }
         pf += N;
-        rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, e0, e1, e2);
+        rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, w_abs, e0, e1, e2);
         ++j;
-        const T s = C.y_scale * (q_sm - q_ca) - y_min;
+        const T s = C.y_scale * (q_sm - q_ca) + C.s_off;
         bmin = fmin(bmin, s);
         nf = fma_rn(s, T(0), nf);
       }
@@ -234,9 +277,9 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
     while (!stop && j < j_end) {
       const T e0 = __ldg(dp), e1 = __ldg(dp + HN), e2 = __ldg(dp + 2 * HN);
       dp += N;
-      rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, e0, e1, e2);
+      rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, w_abs, e0, e1, e2);
       ++j;
-      const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+      const T s = checked_slack<T>(C, q_ca, w, q_sm);
       smin = fmin(smin, s);
       if (s < band) jl = j;
       if (s < thr) {
@@ -296,7 +339,7 @@ template <int D = RRG_RING_DEPTH, int B = RRG_RING_BLOCK, int U = RRG_RING_UNROL
 __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<float>& C,
                                                const float* __restrict__ d, int k, int N, int H,
                                                int j0, int j_end, float& q_ca, float& w,
-                                               float& q_sm, float smin_in, float dt, float y_min,
+                                               float& q_sm, float& w_abs, float smin_in, float dt,
                                                float thr, const volatile int32_t* dead,
                                                unsigned* steps, int* end, float band, int* jlast,
                                                float* ring) {
@@ -306,7 +349,7 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
   int how = LANE_REACHED_END;
   bool go = j < j_end;
   if (j0 == 0) {
-    const float s0 = checked_slack<float>(C, q_ca, w, q_sm, y_min);
+    const float s0 = checked_slack<float>(C, q_ca, w, q_sm);
     smin = fmin(smin, s0);
     if (s0 < band) jl = 0;
     if (s0 < thr) {
@@ -345,7 +388,7 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
         cp_async_wait<D - 1>();
         float* e = my + (3 * slot) * bd;
         const float e0 = e[0], e1 = e[bd], e2 = e[2 * bd];
-        rk4_step_fast<float>(K, C, S, q_ca, w, q_sm, e0, e1, e2);
+        rk4_step_fast<float>(K, C, S, q_ca, w, q_sm, w_abs, e0, e1, e2);
         // the slot is free once its values are in registers: step j + D
         if (j + D < j_end) {
           cp_async4(e, pf);
@@ -356,7 +399,7 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
         pf += N;
         slot = (slot + 1) & (D - 1);
         ++j;
-        const float s = C.y_scale * (q_sm - q_ca) - y_min;
+        const float s = C.y_scale * (q_sm - q_ca) + C.s_off;
         bmin = fmin(bmin, s);
         nf = fma_rn(s, 0.0f, nf);
       }
@@ -377,7 +420,7 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
       cp_async_wait<D - 1>();
       float* e = my + (3 * slot) * bd;
       const float e0 = e[0], e1 = e[bd], e2 = e[2 * bd];
-      rk4_step_fast<float>(K, C, S, q_ca, w, q_sm, e0, e1, e2);
+      rk4_step_fast<float>(K, C, S, q_ca, w, q_sm, w_abs, e0, e1, e2);
       if (j + D < j_end) {
         cp_async4(e, pf);
         cp_async4(e + bd, pf + HN);
@@ -387,7 +430,7 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
       pf += N;
       slot = (slot + 1) & (D - 1);
       ++j;
-      const float s = checked_slack<float>(C, q_ca, w, q_sm, y_min);
+      const float s = checked_slack<float>(C, q_ca, w, q_sm);
       smin = fmin(smin, s);
       if (s < band) jl = j;
       if (s < thr) {
@@ -421,7 +464,7 @@ template <> __device__ __forceinline__ double draw<double>(uint64_t w, double a)
 template <typename T, int PF = PrefetchDepth<T>::value>
 __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, const ScenSrc& src,
                                           int k, int j0, int j_end, T& q_ca, T& w, T& q_sm,
-                                          T smin_in, T dt, T y_min, T thr,
+                                          T& w_abs, T smin_in, T dt, T thr,
                                           const volatile int32_t* dead, unsigned* steps, int* end,
                                           T band, int* jlast) {
   T smin = smin_in;
@@ -430,7 +473,7 @@ __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, co
   int how = LANE_REACHED_END;
   bool go = j < j_end;
   if (j0 == 0) {
-    const T s0 = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    const T s0 = checked_slack<T>(C, q_ca, w, q_sm);
     smin = fmin(smin, s0);
     if (s0 < band) jl = 0;
     if (s0 < thr) {
@@ -447,10 +490,10 @@ __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, co
     for (int u = 0; u < PF; ++u) {
       const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
                                     0ull, src.seed, 0ull);
-      rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, draw<T>(r.w[0], src.amp[0]),
+      rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, w_abs, draw<T>(r.w[0], src.amp[0]),
                        draw<T>(r.w[1], src.amp[1]), draw<T>(r.w[2], src.amp[2]));
       ++j;
-      const T s = C.y_scale * (q_sm - q_ca) - y_min;
+      const T s = C.y_scale * (q_sm - q_ca) + C.s_off;
       bmin = fmin(bmin, s);
       nf = fma_rn(s, T(0), nf);
     }
@@ -469,10 +512,10 @@ __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, co
   while (!stop && j < j_end) {
     const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update, 0ull,
                                   src.seed, 0ull);
-    rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, draw<T>(r.w[0], src.amp[0]),
+    rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, w_abs, draw<T>(r.w[0], src.amp[0]),
                      draw<T>(r.w[1], src.amp[1]), draw<T>(r.w[2], src.amp[2]));
     ++j;
-    const T s = checked_slack<T>(C, q_ca, w, q_sm, y_min);
+    const T s = checked_slack<T>(C, q_ca, w, q_sm);
     smin = fmin(smin, s);
     if (s < band) jl = j;
     if (s < thr) {
@@ -487,12 +530,17 @@ __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, co
 }
 
 // Scenario k's model under parametric uncertainty: the parameters theta_p
-// m_p^k folded like the nominal ones, and the candidate constants at v.
-// Returns the scenario's p_atm (the origin of its gauge coordinates).
+// m_p^k folded like the nominal ones, and the candidate constants at v about
+// the reference point of the nominal candidate constants C comes in with
+// (replaced on return).  Returns the scenario's p_atm (the origin of its
+// gauge coordinates).
 template <typename T>
 __device__ __forceinline__ double scenario_model(const double* __restrict__ P,
                                                  const double* __restrict__ m_k, double v,
-                                                 const PowSeries* pws, RhsU<T>& U, RhsC<T>& C) {
+                                                 const PowSeries* pws, double y_min, RhsU<T>& U,
+                                                 RhsC<T>& C) {
+  const double q_r[3] = {static_cast<double>(C.r_ca), static_cast<double>(C.r_w),
+                         static_cast<double>(C.r_sm)};
   double Pk[RRG_NPARAM];
 #pragma unroll
   for (int p = 0; p < RRG_NPARAM; ++p) Pk[p] = __dmul_rn(P[p], m_k[p]);
@@ -506,7 +554,7 @@ __device__ __forceinline__ double scenario_model(const double* __restrict__ P,
   RhsC<double> r64;
   RhsC<float> r32;
   fold_rhs(k64, &u64, &u32);
-  fold_rhs_cand(k64, c64, &r64, &r32);
+  fold_rhs_cand(k64, c64, q_r, y_min, &r64, &r32);
   if constexpr (sizeof(T) == 8) {
     U = u64;
     C = r64;
@@ -532,19 +580,19 @@ __device__ __forceinline__ T warp_min(T v) {
 // steps 1..H with early exit at s < thr.
 __device__ __forceinline__ double run_lane_philox(const RhsU<double>& K, const RhsC<double>& C,
                                   const ScenSrc& src, int k, int H, double q_ca, double w,
-                                  double q_sm, double dt, double y_min, double thr,
+                                  double q_sm, double w_abs, double dt, double thr,
                                   unsigned* steps) {
-  double smin = checked_slack<double>(C, q_ca, w, q_sm, y_min);
+  double smin = checked_slack<double>(C, q_ca, w, q_sm);
   int j = 0;
   const StepC<double> S = step_consts<double>(K, dt);
   if (!(smin < thr)) {
     while (j < H) {
       const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
                                     0ull, src.seed, 0ull);
-      rk4_step_fast<double>(K, C, S, q_ca, w, q_sm, uniform_sym(r.w[0], src.amp[0]),
+      rk4_step_fast<double>(K, C, S, q_ca, w, q_sm, w_abs, uniform_sym(r.w[0], src.amp[0]),
                             uniform_sym(r.w[1], src.amp[1]), uniform_sym(r.w[2], src.amp[2]));
       ++j;
-      const double s = checked_slack<double>(C, q_ca, w, q_sm, y_min);
+      const double s = checked_slack<double>(C, q_ca, w, q_sm);
       smin = fmin(smin, s);
       if (s < thr) break;
     }
@@ -581,10 +629,11 @@ __device__ __forceinline__ void plant_step_fast(const Fc3K<double>& K, const Rhs
                                                 double e_sm, double x_next[3]) {
   RhsC<double> c64;
   RhsC<float> c32;
-  fold_rhs_cand(K, cand_consts(P, v), &c64, &c32);
+  const double q0[3] = {0.0, 0.0, 0.0};
+  fold_rhs_cand(K, cand_consts(P, v), q0, 0.0, &c64, &c32);
   const double p_atm = P[P_P_ATM];
-  double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm;
-  rk4_step_fast<double>(U, c64, dt, q_ca, w, q_sm, e_ca, e_w, e_sm);
+  double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm, w_abs = x[1];
+  rk4_step_fast<double>(U, c64, dt, q_ca, w, q_sm, w_abs, e_ca, e_w, e_sm);
   x_next[0] = q_ca + p_atm;
   x_next[1] = w;
   x_next[2] = q_sm + p_atm;

@@ -75,6 +75,7 @@ def _load():
         "rrg_get_param_multipliers": (ctypes.c_int, [_p, _p]),
         "rrg_set_param_multipliers": (ctypes.c_int, [_p, _p]),
         "rrg_eval_candidates": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, _p, _p, _p]),
+        "rrg_slack_error": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, _d, _p, _p, _p, _p, _p, _p]),
         "rrg_step": (ctypes.c_int, [_p, _p, _d, _d, _p, _p, _p]),
         "rrg_step_dev": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _p]),
         "rrg_equilibrium": (ctypes.c_int, [_p, _d, _p, _p]),
@@ -217,6 +218,21 @@ def rrg_eval_candidates(h, x_t, v_prev, r_t, kappas, want_P=False, n_scenarios=N
                                  _ptr(P) if P is not None else None)
     _check(rc, h)
     return adm, ms, P
+
+
+def rrg_slack_error(h, x_t, v_prev, r_t, kappas, band, n_scenarios):
+    """Per-trajectory binary32-vs-binary64 slack error (all arrays [m, N]):
+    returns dict err, j_err, smin32, smin64, unsafe, ratio."""
+    x, k = _f64(x_t), _f64(kappas)
+    m = k.shape[0]
+    out = dict(err=np.zeros((m, n_scenarios)), j_err=np.zeros((m, n_scenarios), dtype=np.int32),
+               smin32=np.zeros((m, n_scenarios)), smin64=np.zeros((m, n_scenarios)),
+               unsafe=np.zeros((m, n_scenarios), dtype=np.int32), ratio=np.zeros((m, n_scenarios)))
+    rc = lib.rrg_slack_error(h, _ptr(x), float(v_prev), float(r_t), _ptr(k), m, float(band),
+                             _ptr(out["err"]), _ptr(out["j_err"]), _ptr(out["smin32"]),
+                             _ptr(out["smin64"]), _ptr(out["unsafe"]), _ptr(out["ratio"]))
+    _check(rc, h)
+    return out
 
 
 def rrg_step(h, x_t, r_t, v_prev):
@@ -389,6 +405,11 @@ class Governor:
 
     def eval_candidates(self, x_t, v_prev, r_t, kappas, want_P=False):
         return rrg_eval_candidates(self.h, x_t, v_prev, r_t, kappas, want_P, self.cfg.n_scenarios)
+
+    def slack_error(self, x_t, v_prev, r_t, kappas, band=None):
+        if band is None:
+            band = self.cfg.recheck_eps_rel * abs(self.cfg.y_min)
+        return rrg_slack_error(self.h, x_t, v_prev, r_t, kappas, band, self.cfg.n_scenarios)
 
     def step(self, x_t, r_t, v_prev):
         return rrg_step(self.h, x_t, r_t, v_prev)

@@ -91,3 +91,14 @@ def test_traffic_guard_drops_figures_of_changed_sources():
     import hashlib
     sha = hashlib.sha1(bench.source_region("bench.py", None, None).encode("utf-8")).hexdigest()
     assert bench.measured_traffic((("bench.py", None, None, sha),), 123) == 123
+
+
+def test_closed_loop_window_crosses_the_first_level_change():
+    """The timed window opens at update 115 (the staircase's first level change
+    is at 125) unless the W warm-up updates or the K timed ones do not fit."""
+    assert bench.window_start(5, 20) == 115
+    assert bench.window_start(3, 100) == 115
+    assert bench.window_start(200, 20) == 200          # the warm-up comes first
+    assert bench.window_start(5, 990) == 10             # the window stays inside the run
+    c = bench.workload_config(115, 5, 20)
+    assert "timed updates [115, 135)" in c["workload"] and "[110, 115) warm up" in c["workload"]
