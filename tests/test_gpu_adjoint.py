@@ -37,7 +37,7 @@ def test_adjoint_fp64_matches_complex_step(R, orc, params, checkpoint):
     x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.02, 1.01])
     with _gov(R, params, N, H) as g:
         g.sample_scenarios(4, 2)
-        d = g.get_scenarios()
+        d = orc.sample_disturbances(4, 2, N, H, inputs.DIST_AMP)
         for kappa in (0.05, 0.1, 0.3):
             gv, grad, ks, js = g.slack_gradient(x_t, 100.0, 250.0, kappa, checkpoint, R.FP64)
             c = orc.cfg(H=H, N=N, early_exit=0)
@@ -60,7 +60,7 @@ def test_adjoint_late_argmin_matches_complex_step(R, orc, params, checkpoint):
     x_t = orc.equilibrium(params, 100.0)
     with _gov(R, params, N, H) as g:
         g.sample_scenarios(9, 0)
-        d = g.get_scenarios()
+        d = orc.sample_disturbances(9, 0, N, H, inputs.DIST_AMP)
         gv, grad, ks, js = g.slack_gradient(x_t, 100.0, 250.0, 0.0, checkpoint, R.FP64)
     c = orc.cfg(H=H, N=N, early_exit=0)
     go, ko, jo = orc.min_slack_argmin(params, c, x_t, orc.governed(100.0, 250.0, 0.0), d)
@@ -124,7 +124,7 @@ def test_adjoint_full_size_workload(R, orc, params):
     x_t = orc.equilibrium(params, 100.0)
     with _gov(R, params, N, H) as g:
         g.sample_scenarios(3, 0)
-        d = g.get_scenarios()
+        d = orc.sample_disturbances(3, 0, N, H, inputs.DIST_AMP)
         gv, grad, ks, js = g.slack_gradient(x_t, 100.0, 250.0, 0.1, C, R.FP64)
     c = orc.cfg(H=H, N=N, early_exit=0)
     go, ko, jo = orc.min_slack_argmin(params, c, x_t, orc.governed(100.0, 250.0, 0.1), d)
@@ -164,7 +164,7 @@ def test_newton_search_agrees_with_bisection(R, orc, params, case):
     with _gov(R, params, N, H, precision=R.FP32_RECHECK, recheck_eps_rel=1e-4) as g:
         g.sample_scenarios(8, 1)
         k_n, fl, it = g.newton_search(x_t, r, v_prev, tol=tol, max_iter=40)
-        d = g.get_scenarios()
+    d = orc.sample_disturbances(8, 1, N, H, inputs.DIST_AMP)
     k_b, f_b = orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, v_prev, r, 20, d)
     assert fl == f_b
     assert abs(k_n - k_b) <= tol + 2.0 ** -19

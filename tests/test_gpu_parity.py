@@ -22,7 +22,8 @@ from paper_2510_08288_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 SLACK64_RTOL = 1e-9
-SLACK32_TOL = 2e-4        # absolute OER units; measured max error is reported by test_fp32_error_band
+SLACK32_TOL = 2e-4        # absolute OER units: the plain binary32 tests' loose band
+BENCH_BAND = 1e-6 * inputs.Y_MIN   # the recheck band the benchmark runs with
 
 
 @pytest.fixture(scope="module")
@@ -137,15 +138,18 @@ def test_eval_fp32_within_band(R, orc, params, N, H):
 
 
 @pytest.mark.parametrize("N,H", [(32, 500), (129, 300), (1000, 120), (64, 31), (64, 33)])
-def test_eval_fp32_recheck_is_exact(R, orc, params, N, H):
+@pytest.mark.parametrize("eps_rel", [SLACK32_TOL / 1.9, 1e-6])
+def test_eval_fp32_recheck_is_exact(R, orc, params, N, H, eps_rel):
     """Binary32 bulk + binary64 recheck of the near-zero lanes decides exactly
-    like the binary64 oracle (the band is wide enough to cover binary32 error)."""
+    like the binary64 oracle, with a wide band (many lanes rechecked) and with
+    the benchmark's 1e-6 relative band."""
     kappas = np.linspace(0.09, 0.115, 26)
     (adm, ms, P, st), (a_o, ms_o, P_o) = _eval_both(
-        R, orc, params, N, H, kappas, R.FP32_RECHECK, 1, recheck_eps_rel=SLACK32_TOL / 1.9)
+        R, orc, params, N, H, kappas, R.FP32_RECHECK, 1, recheck_eps_rel=eps_rel)
     np.testing.assert_array_equal(adm, a_o)
     np.testing.assert_array_equal(P, P_o)
-    assert st["rechecked"] >= 1
+    if eps_rel > 1e-5:
+        assert st["rechecked"] >= 1
 
 
 def test_steady_state_failure_rows(R, orc, params):
@@ -166,9 +170,10 @@ def test_steady_state_failure_rows(R, orc, params):
 
 
 def test_fp32_error_band(R, orc, params):
-    """Measures max |s32 - s64| over full-horizon trajectories (no early exit)
-    of the 1,024 x 2,000 closed-loop workload at kappas near the boundary and
-    asserts it is inside the band the recheck tests use."""
+    """max |s32 - s64| of each candidate's min slack over full-horizon
+    trajectories (no early exit) of the 1,024 x 2,000 closed-loop workload at
+    kappas near the boundary, inside the benchmark's recheck band 1.9e-6 (the
+    per-step, per-trajectory statement is in test_gpu_fp32_error.py)."""
     N, H = 1024, 2000
     kappas = np.array([0.0, 0.1, 0.102, 0.104, 0.2])
     x_t = orc.equilibrium(params, 100.0)
@@ -179,7 +184,7 @@ def test_fp32_error_band(R, orc, params):
             errs.append(g.eval_candidates(x_t, 100.0, 250.0, kappas)[1])
     err = np.max(np.abs(errs[0] - errs[1]))
     print("max |s32 - s64| (min over scenarios) = %.3e" % err)
-    assert err < SLACK32_TOL
+    assert err < BENCH_BAND
 
 
 # ------------------------------------------------------------- searches ----
@@ -534,8 +539,8 @@ def test_register_and_shared_rings_agree(R, orc, params, unc, N):
             a1, m1, P1 = g.eval_candidates(x_t, 100.0, 250.0, [k], want_P=True)
             assert a1[0] == adm[i] and m1[0] == ms[i]
             np.testing.assert_array_equal(P1[0], P[i])
-        d = g.get_scenarios()
-        mult = g.get_param_multipliers() if unc else None
+    d = orc.sample_disturbances(5, 2, N, H, inputs.DIST_AMP)
+    mult = orc.sample_param_multipliers(5, 2, N, unc, inputs.FC3_UNCERTAIN_MASK) if unc else None
     assert 0 < int(P.sum()) < P.size
     c = orc.cfg(H=H, N=N, early_exit=0)
     rng = np.random.default_rng(7)

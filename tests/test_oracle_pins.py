@@ -464,3 +464,49 @@ def test_slack_gradient_matches_central_differences(orc, params, k, jstar, with_
     assert np.all(np.abs(grad - fd) <= 1e-5 * scale + 1e-12), np.max(np.abs(grad - fd) / np.maximum(scale, 1e-300))
     if jstar > 0:
         assert np.count_nonzero(grad) == grad.size  # every parameter reaches a state after one step
+
+
+# ----------------------------------------------------------- closed loop ----
+def _numpy_block(ctr, key):
+    """Philox4x64-10 block at counter ctr from numpy.random.Philox (which adds
+    one to the 256-bit counter, with carries, before each block)."""
+    c = [int(w) for w in ctr]
+    v = (c[0] | (c[1] << 64) | (c[2] << 128) | (c[3] << 192)) - 1
+    words = [(v >> (64 * i)) & (2**64 - 1) for i in range(4)]
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(words, dtype=np.uint64))
+    return bg.random_raw(4)
+
+
+def _sym(w, a):
+    """a (2u - 1), u = (w >> 11) 2^-53 (the uniform mapping of the draws)."""
+    return a * (2.0 * ((int(w) >> 11) * 2.0 ** -53) - 1.0)
+
+
+def test_closed_loop_is_sample_search_govern_plant(orc, params):
+    """Fig. 1's loop, two updates written out from its pieces: update t draws
+    its scenarios from Philox counters (j, k, t0 + t, 0), runs Alg. 1 on the
+    joint predicate from (x_t, v_{t-1}, r_t), applies Eq. 2, and the plant
+    takes one RK4 step at v_t plus its own draw from counter (0, 0, t0 + t, 1).
+    The draws are recomputed from numpy's Philox, so a wrong update index,
+    stream, setpoint or order in the oracle's loop fails this test."""
+    N, H, seed, t0 = 8, 120, 77, 5
+    amp, pamp = np.array(inputs.DIST_AMP), np.array([30.0, 5.0, 20.0])
+    c = orc.cfg(H=H, N=N)
+    x0 = orc.equilibrium(params, 100.0) * np.array([1.0, 1.01, 0.995])
+    r_seq = np.array([230.0, 120.0])
+    v, kap, fl, xs = orc.closed_loop(params, c, x0, 100.0, r_seq, seed, t0, amp, pamp, search=0, n_kappa=12)
+    x, vp = x0.copy(), 100.0
+    for t in range(2):
+        d = orc.sample_disturbances(seed, t0 + t, N, H, amp)
+        for (j, k) in ((1, 0), (7, 5), (H - 1, N - 1)):
+            w = _numpy_block([j, k, t0 + t, 0], [seed, 0])
+            for i in range(3):
+                assert d[i, j, k] == _sym(w[i], amp[i])
+        k_t, f_t = orc.bisect_joint(params, c, x, vp, r_seq[t], 12, d)
+        v_t = vp + k_t * (r_seq[t] - vp)
+        wp = _numpy_block([0, 0, t0 + t, 1], [seed, 0])
+        x = orc.rk4_step(params, x, v_t, 0.01) + np.array([_sym(wp[i], pamp[i]) for i in range(3)])
+        assert (kap[t], fl[t], v[t]) == (k_t, f_t, v_t)
+        np.testing.assert_array_equal(xs[t + 1], x)
+        vp = v_t
+    assert 0.0 < kap[0] < 1.0      # the first update governs (kappa neither 0 nor 1)
