@@ -478,6 +478,21 @@ def fp64_comparator(R, torch, p, stream, flush, H, N, seed, amp, d_r, S0, n, x_s
             "kappa_max_abs_diff": float(diff.max())}
 
 
+def merge_fp32_errors(parts, where):
+    """One fp32_error object from several probes (the worst of each figure)."""
+    if not parts:
+        return None
+    out = dict(parts[0])
+    out["updates"] = where
+    out["scenarios"] = [q["scenarios"] for q in parts]
+    out["trajectories"] = sum(q["trajectories"] for q in parts)
+    out["steps_per_trajectory"] = [q["steps_per_trajectory"] for q in parts]
+    for key in ("max_abs_slack_error", "median_trajectory_max_error", "max_error_over_band_or_slack"):
+        out[key] = max(q[key] for q in parts)
+    out["unsafe_steps"] = sum(q["unsafe_steps"] for q in parts)
+    return out
+
+
 def fp32_error_probe(R, p, stream, H, N, seed, probes, m_grid=16, m_near=16, param_unc=0.0, n_cap=None):
     """The binary32 rollouts' slack error against binary64 on sampled updates
     (rrg_slack_error: every trajectory in both precisions over the full
@@ -923,6 +938,20 @@ def run_batch(args):
     cpu = None
     if not args.no_cpu_baseline:
         cpu = batch_cpu(p, b, x0, r, args.cpu_seconds, os.cpu_count() or 1)
+    # binary32 slack error against binary64 at the first timed update, on the
+    # two longest-horizon instances (each with its own scenarios, seed + s)
+    xs_all = dxo.cpu().numpy().reshape(T + 1, S, 3)
+    vs_all = dv.cpu().numpy().reshape(T, S)
+    parts = []
+    for s_i in np.argsort(-b["H"])[:2]:
+        s_i = int(s_i)
+        parts.append(fp32_error_probe(R, p, stream, int(b["H"][s_i]), int(b["N"][s_i]), SEED + s_i,
+                                      [(W, xs_all[W, s_i], vs_all[W - 1, s_i] if W else b["v_prev"][s_i],
+                                        r_seq[W][s_i], kap[W, s_i])],
+                                      m_grid=BATCH_M, m_near=16))
+    fp32_err = merge_fp32_errors(parts, "update %d of the two longest-horizon instances (%s)"
+                                 % (W, ", ".join("H=%d, N=%d" % (b["H"][i], b["N"][i])
+                                                 for i in np.argsort(-b["H"])[:2])))
     g.close()
     peak, peak_src = fp32_peak(clk)
     out = {
@@ -947,6 +976,7 @@ def run_batch(args):
         "rechecked_trajectories": st["rechecked"],
         "no_admissible_fraction": float(np.mean(flags[W:W + K] & 1)),
         "kappa_mean": float(np.mean(kap[W:W + K])),
+        "fp32_error": fp32_err,
     }
     print(json.dumps(out), flush=True)
     return 0
@@ -1040,6 +1070,11 @@ def run_single(args):
                "kappa": k_o, "kappa_equal_to_gpu": bool(k_o == legs["fp64_bisect"]["kappa"] ==
                                                         legs["fp32_recheck_spec"]["kappa"])}
     main = legs["fp64_bisect"]
+    # binary32 slack error against binary64 on this update, at the kappa the
+    # binary32 + recheck search chose
+    k32 = float(legs["fp32_recheck_spec"]["kappa"])
+    fp32_err = fp32_error_probe(R, p, stream, w["H"], w["N"], w["seed"], [(0, x_t, w["v_prev"], w["r"], k32)])
+    fp32_err["kappa_max_abs_diff_fp64"] = abs(k32 - float(legs["fp64_bisect"]["kappa"]))
     out = {"metric": SINGLE_METRIC, "value": 1e3 / main["ms_per_update"], "unit": "RG updates/s", "n_gpus": 1,
            "steps": K, "warmup": W, "ms_per_step": main["ms_per_update"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1047,7 +1082,7 @@ def run_single(args):
                                   "32 scenarios (seed 0), horizon 500 RK4 steps (dt=0.01 s), N_kappa = 12",
                       "timing": "median device time of sample + search (CUDA events), host time beside it",
                       "l2": "256 MB written between timed steps"},
-           "legs": legs, "cpu_baseline": cpu, "clocks": clk}
+           "legs": legs, "cpu_baseline": cpu, "clocks": clk, "fp32_error": fp32_err}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -1367,6 +1402,13 @@ def run_sweep(args):
     for row in rows:
         row["rollout_frac"] = frac_of(row["rollout_tflops"], peak)
     top = rows[-1]
+    # binary32 slack error against binary64 at the first timed update of the
+    # largest N, on its first 8,192 scenarios (nested draws: the run's own)
+    fp32_err = fp32_error_probe(R, p, stream, SWEEP_H, top["n_scenarios"], SEED,
+                                [(W, x_t, v_prev, r, top["kappa"][0])], m_grid=SWEEP_M, m_near=16,
+                                param_unc=rho, n_cap=8192)
+    fp32_err["kappa_equal_fp64_same_search"] = {str(row["n_scenarios"]): row["fp64_same_search"]["kappa_equal"]
+                                                for row in rows if row["fp64_same_search"]}
     cpu = None if args.no_cpu_baseline else sweep_cpu(p, args.cpu_seconds, os.cpu_count() or 1)
     out = {
         "metric": SWEEP_METRIC, "value": top["trajectory_steps_per_s"], "unit": "trajectory-steps/s",
@@ -1385,6 +1427,7 @@ def run_sweep(args):
                      "frac_of_issue_ceiling": frac_of(top["rollout_frac"], ISSUE_CEILING)},
         "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
         "gpu_launches": top["gpu_launches"],
+        "fp32_error": fp32_err,
     }
     print(json.dumps(out), flush=True)
     return 0

@@ -147,6 +147,19 @@ typedef struct {
                                 (default): stored array.  Single-problem
                                 handles only; rrg_set_scenarios is then
                                 RRG_EINVAL.                                   */
+    int64_t scenario_base;   /* global index of the handle's scenario 0, in
+                                [0, 2^62]: scenario k of the handle draws its
+                                disturbances (and parameter multipliers) from
+                                the Philox counters of global scenario
+                                scenario_base + k.  Handles with bases 0, n_1,
+                                n_1 + n_2, ... then hold consecutive shards of
+                                one scenario set (Sec. II-C's N_sim scenarios
+                                are independent), and the AND of their
+                                admissibility flags (the min of their min
+                                slacks) is the unsharded handle's; see
+                                rrg_bisect_plan.  Default 0.  Single-problem
+                                handles only (the batched handles and the
+                                allocation-free call ignore or reject it).    */
 } rrg_config;
 
 /* FC3 parameters perturbed by default: k_ca, eta_cp, J_cp, eta_cm, R_cm,
@@ -407,6 +420,50 @@ RRG_API int rrg_set_profiling(rrg_handle h, int on);
 /* Reads the counters (synchronises the handle's stream).  Host out. */
 RRG_API int rrg_get_stats(rrg_handle h, rrg_stats *out);
 RRG_API int rrg_reset_stats(rrg_handle h);
+
+/* ---- Alg. 1 rounds for evaluations the caller runs --------------------
+ * The searches of rrg_step run on the device without a host round trip.  A
+ * caller that evaluates candidates itself -- typically one handle per shard
+ * of the scenarios (rrg_config.scenario_base), one per GPU or several on one,
+ * combined per round by an AND of their admissible flags -- splits each round
+ * of the speculative bisection into plan -> evaluate -> combine -> decide:
+ *   rrg_bisect_init(&s, n_bisect);
+ *   while (!s.done) {
+ *     rrg_bisect_plan(&s, m_max, kappas, &m);          (m >= 1 while !done)
+ *     for each shard: rrg_eval_candidates(shard, x_t, v_prev, r_t, kappas, m,
+ *                                         adm_shard, NULL, NULL);
+ *     adm[i] = AND over shards of adm_shard[i];         (the exchange)
+ *     rrg_bisect_decide(&s, adm, m);
+ *   }
+ *   kappa = s.kappa_opt; flags bit 0 = !s.any; v_t = v_prev + kappa (r_t - v_prev)
+ * The result is Alg. 1's (Sec. II-B, the joint predicate over all scenarios
+ * of all shards): each round evaluates every node of the next levels of
+ * Alg. 1's bisection tree that fit in m_max (2^d - 1 nodes, or 2^(d-1) from
+ * a kappa = 1 root, whose admissible outcome ends the search), and decide
+ * walks Alg. 1's path through their outcomes -- the same tree and walk as
+ * RRG_SEARCH_SPEC_BISECT without pipelining.  Host only: no device work, no
+ * handle.  Nodes are listed breadth-first: node 0 is the state's kappa; node
+ * n's children follow "not admissible" (upper bracket end <- its kappa)
+ * before "admissible" (lower end <- its kappa); children's kappas are the
+ * bracket midpoints (lo + hi) / 2.  Errors (RRG_EINVAL): null pointers,
+ * n_bisect outside [1, 62], m_max < 1, decide on a finished state or with an
+ * m that is not the size of the planned round. */
+typedef struct {
+    double  lo, hi;        /* Alg. 1's bracket                              */
+    double  kappa;         /* the kappa Alg. 1 tests next                   */
+    double  kappa_opt;     /* largest admissible kappa found (0: none yet)  */
+    int32_t iter;          /* iterations of Alg. 1 done (of n_bisect)       */
+    int32_t n_bisect;      /* N_kappa                                       */
+    int32_t any;           /* 1: some tested kappa was admissible           */
+    int32_t done;          /* 1: kappa_opt is Alg. 1's result               */
+} rrg_bisect_state;
+
+RRG_API int rrg_bisect_init(rrg_bisect_state *s, int n_bisect);
+/* kappas: host, room for m_max doubles; *m receives the round's node count
+ * (0 once the search is done). */
+RRG_API int rrg_bisect_plan(const rrg_bisect_state *s, int m_max, double *kappas, int32_t *m);
+/* admissible: host, the m combined outcomes of the planned kappas. */
+RRG_API int rrg_bisect_decide(rrg_bisect_state *s, const uint8_t *admissible, int m);
 
 /* ---- allocation-free candidate evaluation ---------------------------
  * The paper has no counterpart of this entry point.  It is for callers that

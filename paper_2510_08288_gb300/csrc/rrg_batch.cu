@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
     src.pad = 0;
     src.seed = st.seed_p[st.cur];
     src.update = st.update_p[st.cur];
+    src.base = 0;
     src.amp[0] = B.c.amp[0];
     src.amp[1] = B.c.amp[1];
     src.amp[2] = B.c.amp[2];
@@ -730,9 +731,9 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
     return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_SEARCH_GRID or RRG_SEARCH_KSECTION");
   if (cfg->precision != RRG_FP32_RECHECK)
     return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_FP32_RECHECK");
-  if (cfg->param_unc_rel != 0.0 || cfg->scenarios_in_register != 0)
+  if (cfg->param_unc_rel != 0.0 || cfg->scenarios_in_register != 0 || cfg->scenario_base != 0)
     return bset_err(h, RRG_ENOTIMPL, "batched instances have no parametric uncertainty and store "
-                    "their scenarios (param_unc_rel and scenarios_in_register must be 0)");
+                    "their scenarios (param_unc_rel, scenarios_in_register and scenario_base must be 0)");
   if (n_instances < 1 || n_instances > kMaxInst)
     return bset_err(h, RRG_EINVAL, "n_instances must be in [1, %d]", kMaxInst);
   if (!n_scenarios || !horizons) return bset_err(h, RRG_EINVAL, "n_scenarios and horizons must be non-NULL");

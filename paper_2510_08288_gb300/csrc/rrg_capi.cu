@@ -160,6 +160,8 @@ int validate_cfg(const rrg_config* c) {
     return set_err(nullptr, RRG_EINVAL, "param_unc_rel must be in [0, 1)");
   if (c->scenarios_in_register != 0 && c->scenarios_in_register != 1)
     return set_err(nullptr, RRG_EINVAL, "scenarios_in_register must be 0 or 1");
+  if (c->scenario_base < 0 || c->scenario_base > (int64_t(1) << 62))
+    return set_err(nullptr, RRG_EINVAL, "scenario_base must be in [0, 2^62]");
   if (c->param_unc_mask >> RRG_NPARAM)
     return set_err(nullptr, RRG_EINVAL, "param_unc_mask has bits at or above RRG_NPARAM");
   const unsigned long long lanes =
@@ -207,6 +209,7 @@ void fill_launch(rrg_ctx* h) {
   L.y_min = c.y_min;
   L.eps_abs = c.precision == RRG_FP32_RECHECK ? c.recheck_eps_rel * std::fabs(c.y_min) : 0.0;
   L.scen_gen = c.scenarios_in_register;
+  L.kbase = static_cast<unsigned long long>(c.scenario_base);
   L.scfg = h->scfg;
   L.params = h->params_dev;
   fold_constants(h->params, &L.k64, &L.k32);
@@ -475,6 +478,8 @@ void rrg_config_default(rrg_config* c) {
   c->probe_steps = 128;
   c->param_unc_rel = 0.0;
   c->param_unc_mask = RRG_PARAM_UNC_MASK_FC3;
+  c->scenarios_in_register = 0;
+  c->scenario_base = 0;
 }
 
 const char* rrg_last_error(rrg_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -1298,6 +1303,113 @@ int rrg_reset_stats(rrg_handle h) {
   h->launches = h->rollout_launches = h->rounds = 0;
   h->rollout_ms = h->recheck_ms = 0.0;
   h->timed_rollouts = 0;
+  return RRG_OK;
+}
+
+// ---- Alg. 1 rounds for caller-run evaluations ---------------------------
+// The speculative bisection's tree on the host: the nodes of the next levels
+// of Alg. 1's bisection tree from the current state, in breadth-first order
+// (heap numbering: node 2n follows "not admissible" at node n, 2n + 1
+// "admissible"; an admissible kappa = 1 ends the search, so it has no
+// admissible child), and the walk of Alg. 1's path through their outcomes.
+namespace {
+
+struct TreeNode {
+  uint32_t heap;
+  double lo, hi, kappa;
+};
+
+int tree_size(bool root_is_one, int d) { return root_is_one ? (1 << (d - 1)) : ((1 << d) - 1); }
+
+// Levels of the next round: the most that fit in m_max nodes and in the
+// iterations Alg. 1 has left (0 when the search is finished).
+int tree_depth(const rrg_bisect_state* s, int m_max) {
+  if (s->done || s->iter >= s->n_bisect || m_max < 1) return 0;
+  const bool one = s->kappa == 1.0;
+  int d = 1;
+  while (d < 20 && d + 1 <= s->n_bisect - s->iter && tree_size(one, d + 1) <= m_max) ++d;
+  return d;
+}
+
+int build_nodes(const rrg_bisect_state* s, int d, TreeNode* out) {
+  int n = 0;
+  out[n++] = TreeNode{1u, s->lo, s->hi, s->kappa};
+  for (int q = 0; q < n; ++q) {
+    const TreeNode a = out[q];
+    int depth = 0;
+    for (uint32_t h = a.heap; h > 1u; h >>= 1) ++depth;
+    if (depth + 1 >= d) continue;
+    out[n++] = TreeNode{2u * a.heap, a.lo, a.kappa, (a.lo + a.kappa) / 2.0};
+    if (a.kappa != 1.0) out[n++] = TreeNode{2u * a.heap + 1u, a.kappa, a.hi, (a.kappa + a.hi) / 2.0};
+  }
+  return n;
+}
+
+}  // namespace
+
+int rrg_bisect_init(rrg_bisect_state* s, int n_bisect) {
+  if (!s || n_bisect < 1 || n_bisect > 62) return RRG_EINVAL;
+  s->lo = 0.0;
+  s->hi = 1.0;
+  s->kappa = 1.0;
+  s->kappa_opt = 0.0;
+  s->iter = 0;
+  s->n_bisect = n_bisect;
+  s->any = 0;
+  s->done = 0;
+  return RRG_OK;
+}
+
+int rrg_bisect_plan(const rrg_bisect_state* s, int m_max, double* kappas, int32_t* m) {
+  if (!s || !m || m_max < 1 || (m_max > 0 && !kappas)) return RRG_EINVAL;
+  if (s->n_bisect < 1 || s->n_bisect > 62) return RRG_EINVAL;
+  const int d = tree_depth(s, m_max > RRG_MAX_CANDIDATES ? RRG_MAX_CANDIDATES : m_max);
+  if (d == 0) {
+    *m = 0;
+    return RRG_OK;
+  }
+  std::vector<TreeNode> nodes(static_cast<size_t>(tree_size(s->kappa == 1.0, d)));
+  const int n = build_nodes(s, d, nodes.data());
+  for (int i = 0; i < n; ++i) kappas[i] = nodes[i].kappa;
+  *m = n;
+  return RRG_OK;
+}
+
+int rrg_bisect_decide(rrg_bisect_state* s, const uint8_t* admissible, int m) {
+  if (!s || !admissible || m < 1 || s->done) return RRG_EINVAL;
+  const bool one = s->kappa == 1.0;
+  int d = 0;
+  for (int k = 1; k <= 20; ++k)
+    if (tree_size(one, k) == m) d = k;
+  if (d == 0 || d > s->n_bisect - s->iter) return RRG_EINVAL;
+  std::vector<TreeNode> nodes(static_cast<size_t>(m));
+  build_nodes(s, d, nodes.data());
+  uint32_t heap = 1u;
+  for (;;) {
+    int pos = -1;
+    for (int i = 0; i < m; ++i)
+      if (nodes[i].heap == heap) pos = i;
+    if (pos < 0) break;  // past the round's levels
+    const bool ok = admissible[pos] != 0;
+    s->iter += 1;
+    if (ok) {
+      s->kappa_opt = s->kappa;
+      s->any = 1;
+      if (s->kappa == 1.0) {
+        s->done = 1;
+        break;
+      }
+      s->lo = s->kappa;
+    } else {
+      s->hi = s->kappa;
+    }
+    s->kappa = (s->lo + s->hi) / 2.0;
+    if (s->iter >= s->n_bisect) {
+      s->done = 1;
+      break;
+    }
+    heap = 2u * heap + (ok ? 1u : 0u);
+  }
   return RRG_OK;
 }
 

@@ -98,7 +98,7 @@ slack_error_kernel(const Launch L, float band, double* __restrict__ err, int32_t
     float e0, e1, e2;
     double f0, f1, f2;
     if (gen || !have64) {
-      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
+      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), src.base + static_cast<uint64_t>(k), src.update,
                                     0ull, src.seed, 0ull);
       f0 = uniform_sym(r.w[0], src.amp[0]);
       f1 = uniform_sym(r.w[1], src.amp[1]);

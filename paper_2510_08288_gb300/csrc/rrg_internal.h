@@ -55,6 +55,7 @@ struct ScenSrc {
   int32_t d64_valid;     // 1: the binary64 array holds the values
   int32_t pad;
   unsigned long long seed, update;
+  unsigned long long base;  // global index of scenario 0 (the Philox counter's k)
   double amp[3];
 };
 
@@ -127,6 +128,7 @@ struct Launch {
   cudaStream_t stream;
   int N, H, precision, early_exit, m_cap;
   int scen_gen;                 // disturbances drawn inside the trajectory loop
+  unsigned long long kbase;     // global index of the handle's scenario 0 (scenario sharding)
   // conditional-node handle of a captured closed-loop update (0: none); the
   // search kernel that validates the pipelined rounds sets it to "the search
   // is not finished", which runs the remaining rounds

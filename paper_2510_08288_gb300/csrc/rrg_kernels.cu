@@ -106,10 +106,10 @@ cudaError_t launch_step_latency(const Launch& L, double v, int steps, double* d_
 // the Philox block at counter (p / 4, k, update, 2).
 constexpr int kParamGroups = (RRG_NPARAM + 3) / 4;
 
-__device__ __forceinline__ void sample_param_group(double* __restrict__ pm, uint64_t k, int g,
-                                                   uint64_t upd, uint64_t seed, double rho,
+__device__ __forceinline__ void sample_param_group(double* __restrict__ pm, uint64_t k, uint64_t kbase,
+                                                   int g, uint64_t upd, uint64_t seed, double rho,
                                                    uint32_t mask) {
-  const U64x4 w = philox4x64_10(static_cast<uint64_t>(g), k, upd, 2ull, seed, 0ull);
+  const U64x4 w = philox4x64_10(static_cast<uint64_t>(g), kbase + k, upd, 2ull, seed, 0ull);
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int p = 4 * g + b;
@@ -123,7 +123,7 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
                               uint64_t seed, uint64_t base, const unsigned long long* t_dev,
                               double a0, double a1, double a2, int write64, int gen, SearchState* st,
                               double* __restrict__ pm, double* __restrict__ pmb, double rho,
-                              uint32_t mask) {
+                              uint32_t mask, uint64_t kbase) {
   const uint64_t upd = base + (t_dev ? *t_dev : 0ull);
   const int pair = (d64b != nullptr && (upd & 1ull)) ? 1 : 0;
   if (pair) {
@@ -137,6 +137,7 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
     src.pad = 0;
     src.seed = seed;
     src.update = upd;
+    src.base = kbase;
     src.amp[0] = a0;
     src.amp[1] = a1;
     src.amp[2] = a2;
@@ -149,7 +150,7 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
   for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; !gen && q < HN;
        q += stride) {
     const uint64_t j = q / static_cast<uint64_t>(N), k = q - j * static_cast<uint64_t>(N);
-    const U64x4 w = philox4x64_10(j, k, upd, 0ull, seed, 0ull);
+    const U64x4 w = philox4x64_10(j, kbase + k, upd, 0ull, seed, 0ull);
     if (write64) {
       d64[q] = uniform_sym(w.w[0], a0);
       d64[HN + q] = uniform_sym(w.w[1], a1);
@@ -164,7 +165,7 @@ __global__ void sample_kernel(double* __restrict__ d64, float* __restrict__ d32,
     const size_t G = static_cast<size_t>(N) * kParamGroups;
     for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < G; q += stride) {
       const uint64_t k = q / kParamGroups;
-      sample_param_group(pm, k, static_cast<int>(q - k * kParamGroups), upd, seed, rho, mask);
+      sample_param_group(pm, k, kbase, static_cast<int>(q - k * kParamGroups), upd, seed, rho, mask);
     }
   }
 }
@@ -189,7 +190,7 @@ cudaError_t launch_sample(const Launch& L, uint64_t seed, uint64_t base,
   sample_kernel<<<grid_for(n, 256, L.sms * 16), 256, 0, stream ? stream : L.stream>>>(
       L.d64, L.d32, dual ? L.d64b : nullptr, dual ? L.d32b : nullptr, L.N, L.H, seed, base, t_dev,
       amp[0], amp[1], amp[2], write64, L.scen_gen, L.st, L.pmul, dual ? L.pmulb : nullptr, L.punc_rho,
-      L.punc_mask);
+      L.punc_mask, L.kbase);
   return cudaGetLastError();
 }
 
@@ -215,7 +216,7 @@ __global__ void materialize64_kernel(double* __restrict__ d64, int N, int H,
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < HN; q += stride) {
     const uint64_t j = q / static_cast<uint64_t>(N), k = q - j * static_cast<uint64_t>(N);
-    const U64x4 w = philox4x64_10(j, k, src.update, 0ull, src.seed, 0ull);
+    const U64x4 w = philox4x64_10(j, src.base + k, src.update, 0ull, src.seed, 0ull);
     d64[q] = uniform_sym(w.w[0], src.amp[0]);
     d64[HN + q] = uniform_sym(w.w[1], src.amp[1]);
     d64[2 * HN + q] = uniform_sym(w.w[2], src.amp[2]);

@@ -488,7 +488,7 @@ __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, co
     T nf = T(0), bmin = inf_v<T>();
 #pragma unroll 4
     for (int u = 0; u < PF; ++u) {
-      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
+      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), src.base + static_cast<uint64_t>(k), src.update,
                                     0ull, src.seed, 0ull);
       rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, w_abs, draw<T>(r.w[0], src.amp[0]),
                        draw<T>(r.w[1], src.amp[1]), draw<T>(r.w[2], src.amp[2]));
@@ -510,7 +510,7 @@ __device__ __forceinline__ T run_lane_gen(const RhsU<T>& K, const RhsC<T>& C, co
     }
   }
   while (!stop && j < j_end) {
-    const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update, 0ull,
+    const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), src.base + static_cast<uint64_t>(k), src.update, 0ull,
                                   src.seed, 0ull);
     rk4_step_fast<T>(K, C, S, q_ca, w, q_sm, w_abs, draw<T>(r.w[0], src.amp[0]),
                      draw<T>(r.w[1], src.amp[1]), draw<T>(r.w[2], src.amp[2]));
@@ -587,7 +587,7 @@ __device__ __forceinline__ double run_lane_philox(const RhsU<double>& K, const R
   const StepC<double> S = step_consts<double>(K, dt);
   if (!(smin < thr)) {
     while (j < H) {
-      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), static_cast<uint64_t>(k), src.update,
+      const U64x4 r = philox4x64_10(static_cast<uint64_t>(j), src.base + static_cast<uint64_t>(k), src.update,
                                     0ull, src.seed, 0ull);
       rk4_step_fast<double>(K, C, S, q_ca, w, q_sm, w_abs, uniform_sym(r.w[0], src.amp[0]),
                             uniform_sym(r.w[1], src.amp[1]), uniform_sym(r.w[2], src.amp[2]));

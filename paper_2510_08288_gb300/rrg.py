@@ -39,6 +39,16 @@ class RrgConfig(ctypes.Structure):
         ("early_exit", _i32), ("ss_check", _i32), ("y_min", _d), ("eps_ss", _d), ("y_c", _d),
         ("recheck_eps_rel", _d), ("dist_amp", _d * 3), ("probe_steps", _i32),
         ("param_unc_rel", _d), ("param_unc_mask", ctypes.c_uint32), ("scenarios_in_register", _i32),
+        ("scenario_base", ctypes.c_int64),
+    ]
+
+
+class RrgBisectState(ctypes.Structure):
+    """Mirror of rrg_bisect_state."""
+
+    _fields_ = [
+        ("lo", _d), ("hi", _d), ("kappa", _d), ("kappa_opt", _d), ("iter", _i32), ("n_bisect", _i32),
+        ("any", _i32), ("done", _i32),
     ]
 
 
@@ -75,6 +85,9 @@ def _load():
         "rrg_get_param_multipliers": (ctypes.c_int, [_p, _p]),
         "rrg_set_param_multipliers": (ctypes.c_int, [_p, _p]),
         "rrg_eval_candidates": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, _p, _p, _p]),
+        "rrg_bisect_init": (ctypes.c_int, [P(RrgBisectState), ctypes.c_int]),
+        "rrg_bisect_plan": (ctypes.c_int, [P(RrgBisectState), ctypes.c_int, _p, P(_i32)]),
+        "rrg_bisect_decide": (ctypes.c_int, [P(RrgBisectState), _p, ctypes.c_int]),
         "rrg_slack_error": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, _d, _p, _p, _p, _p, _p, _p]),
         "rrg_step": (ctypes.c_int, [_p, _p, _d, _d, _p, _p, _p]),
         "rrg_step_dev": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _p]),
@@ -233,6 +246,25 @@ def rrg_slack_error(h, x_t, v_prev, r_t, kappas, band, n_scenarios):
                              _ptr(out["smin64"]), _ptr(out["unsafe"]), _ptr(out["ratio"]))
     _check(rc, h)
     return out
+
+
+def rrg_bisect_init(n_bisect) -> RrgBisectState:
+    s = RrgBisectState()
+    _check(lib.rrg_bisect_init(ctypes.byref(s), int(n_bisect)))
+    return s
+
+
+def rrg_bisect_plan(s: RrgBisectState, m_max):
+    """The next round's kappas (empty once the search is done)."""
+    k = np.zeros(max(1, int(m_max)))
+    m = _i32(0)
+    _check(lib.rrg_bisect_plan(ctypes.byref(s), int(m_max), _ptr(k), ctypes.byref(m)))
+    return k[:m.value].copy()
+
+
+def rrg_bisect_decide(s: RrgBisectState, admissible):
+    a = np.ascontiguousarray(np.asarray(admissible, dtype=np.uint8))
+    _check(lib.rrg_bisect_decide(ctypes.byref(s), _ptr(a), int(a.shape[0])))
 
 
 def rrg_step(h, x_t, r_t, v_prev):

@@ -5,8 +5,10 @@ admissibility is an AND over scenarios and its min slack a MIN over them
 (Eq. 5 reduced per row).  Splitting the N_sim scenarios into contiguous shards
 across ranks therefore needs one exchange per search round: an all-reduce MIN
 of the m per-candidate flags (AND on {0, 1}) and of the m min slacks.  The
-shards use the global scenario indices, so the result does not depend on the
-number of ranks.
+shards use the global scenario indices (a handle's rrg_config.scenario_base),
+so the result does not depend on the number of ranks.  sharded_search runs
+the speculative bisection by rounds around that exchange, with the library's
+rrg_bisect_plan / rrg_bisect_decide deciding each round.
 
 Replicas (independent RG instances, one per rank) need no data exchange at
 all; only the benchmark's timing uses a MAX all-reduce.
@@ -50,3 +52,24 @@ def allreduce_max(value: float, group=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def sharded_search(evaluate, n_bisect: int, m_max: int, combine=None):
+    """Alg. 1 (joint predicate over every shard's scenarios) by rounds of the
+    speculative bisection: rrg_bisect_plan lists the round's kappas,
+    evaluate(kappas) -> (admissible[m], min_slack[m]) evaluates them on this
+    caller's shard(s), combine (default: allreduce_candidates, AND / MIN over
+    the ranks of the default group) makes them global, and rrg_bisect_decide
+    walks Alg. 1's path.  Returns (kappa, flags, rounds); flags bit 0: no
+    kappa was admissible (kappa = 0, hold)."""
+    from paper_2510_08288_gb300 import rrg as R
+    combine = combine or allreduce_candidates
+    s = R.rrg_bisect_init(n_bisect)
+    rounds = 0
+    while not s.done:
+        kap = R.rrg_bisect_plan(s, m_max)
+        a, ms = evaluate(kap)
+        a, _ = combine(a, ms)
+        R.rrg_bisect_decide(s, a)
+        rounds += 1
+    return s.kappa_opt, (0 if s.any else 1), rounds

@@ -2,7 +2,10 @@
 
 Each rank evaluates its contiguous shard of the scenarios with the FP64
 oracle and the ranks combine with shard.allreduce_candidates; the combined
-flags and slacks must equal the unsharded evaluation.  The replica path's
+flags and slacks must equal the unsharded evaluation, and the speculative
+bisection run by rounds around that exchange (shard.sharded_search, decided
+by the library's rrg_bisect_plan / rrg_bisect_decide) must give the
+oracle's joint bisection over all scenarios.  The replica path's
 bookkeeping (distinct seeds, MAX of the timed region) is checked the same way.
 """
 import os
@@ -41,7 +44,13 @@ def _worker(rank, world, port, q):
         a, s, _, _ = O.eval_candidates(p, c, x_t, 100.0, 250.0, kap, dl)
         a_all, s_all = shard.allreduce_candidates(a, s)
         t_max = shard.allreduce_max(float(rank) + 0.5)
-        q.put((rank, a_all.tolist(), s_all.tolist(), t_max, shard.replica_seed(1, rank), (k0, k1)))
+        # the search by rounds: each round's kappas on this rank's shard, the
+        # flags combined over the ranks
+        cs = O.cfg(H=H, N=k1 - k0)
+        ev = lambda kk: O.eval_candidates(p, cs, x_t, 100.0, 250.0, kk, dl)[:2]
+        ks, fs, rounds = shard.sharded_search(ev, 12, 8)
+        q.put((rank, a_all.tolist(), s_all.tolist(), t_max, shard.replica_seed(1, rank), (k0, k1),
+               (ks, fs, rounds)))
     finally:
         dist.destroy_process_group()
 
@@ -65,10 +74,12 @@ def test_sharded_evaluation_equals_unsharded():
     d = O.sample_disturbances(5, 2, N, H, inputs.DIST_AMP)
     a, s, _, _ = O.eval_candidates(p, O.cfg(H=H, N=N, early_exit=0), O.equilibrium(p, 100.0), 100.0, 250.0,
                                    np.linspace(0.0, 0.3, 13), d)
-    for rank, a_all, s_all, t_max, seed, rng in res:
+    k_o, f_o = O.bisect_joint(p, O.cfg(H=H, N=N), O.equilibrium(p, 100.0), 100.0, 250.0, 12, d)
+    for rank, a_all, s_all, t_max, seed, rng, search in res:
         np.testing.assert_array_equal(np.array(a_all, dtype=np.uint8), a)
         np.testing.assert_array_equal(np.array(s_all), s)
         assert t_max == 1.5
+        assert search[:2] == (k_o, f_o) and search[2] < 12
     assert res[0][4] != res[1][4]
     assert res[0][5] == (0, 19) and res[1][5] == (19, 37)
 
