@@ -391,22 +391,57 @@ RRG_API int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_p
  * NULL): *g, grad[31] = (dg/dkappa, dg/dx_t[3], dg/dtheta[27] in the FC3
  * parameter layout), *k_star, *j_star.  Under parametric uncertainty
  * scenario k runs with theta_p m_p^k and dg/dtheta is with respect to the
- * nominal theta.  Synchronous. */
+ * nominal theta.  rrg_slack_gradients with m = 1.  Synchronous. */
 RRG_API int rrg_slack_gradient(rrg_handle h, const double *x_t, double v_prev, double r_t, double kappa,
                        int checkpoint, int precision, double *g, double *grad, int64_t *k_star,
                        int64_t *j_star);
 
-/* Safeguarded Newton search for the largest admissible kappa on the current
- * scenarios, driven by rrg_slack_gradient: kappa = 1 is tried first (as in
- * Alg. 1), then Newton steps on g(kappa) = 0 inside a bracket [lo, hi] with
- * lo admissible and hi not (steady-state check and g >= 0), bisection when a
- * step leaves the bracket, until hi - lo <= tol or max_iter gradients.  The
- * final bracket is then judged by rrg_eval_candidates (the handle's own
- * admissibility test).  Host out: *kappa = lo (0 if nothing admissible),
- * *flags (bit 0: nothing admissible found; bit 2: the bracket check failed:
- * lo not admissible, hi admissible, or the bracket still wider than tol),
- * *iterations (gradient evaluations).  Needs max_candidates >= 2.
- * Synchronous. */
+/* The same for m kappas at once (host kappas[m], 1 <= m <= max_candidates,
+ * each in [0, 1]): one forward pass over the m x N trajectories, one argmin
+ * and one reverse sweep per kappa, all in one launch each.  With 4,096
+ * scenarios the forward pass of one kappa occupies one warp per SM, so a few
+ * kappas cost about as much as one.  The forward pass integrates with the
+ * rollouts' arithmetic (deviation coordinates about each candidate's
+ * equilibrium; the binary32 gradient reads the stored binary32 disturbances
+ * when the handle draws them); the reverse sweep recomputes the segments
+ * before j* from the saved states in the gauge form of the model.  Host out,
+ * each may be NULL: g[m], grad[m * 31] (kappa i's 31 values at 31 i),
+ * k_star[m], j_star[m], ss_ok[m] (1: the steady-state check of Eq. 3 passed
+ * at kappa i; always 1 with ss_check off).  Device scratch as above, times m
+ * (allocated on first use, grown on demand).  Synchronous.  RRG_EINVAL,
+ * RRG_ECUDA. */
+RRG_API int rrg_slack_gradients(rrg_handle h, const double *x_t, double v_prev, double r_t,
+                        const double *kappas, int m, int checkpoint, int precision, double *g,
+                        double *grad, int64_t *k_star, int64_t *j_star, uint8_t *ss_ok);
+
+/* Adjoint-driven search for the largest admissible kappa on the current
+ * scenarios; only the handle's own evaluation (rrg_eval_candidates) decides,
+ * the gradients steer:
+ *   A. one forward pass (no reverse sweep) at kappa = j / G, j = 0..G (G = 8,
+ *      or the largest power of two with G + 1 <= max_candidates): g and the
+ *      steady-state outcome at each point.  kappa = 1 (Alg. 1's first test)
+ *      is evaluated by the handle unless its g is below -1e-4 or its
+ *      steady-state check failed (then it is inadmissible in binary64 too);
+ *      admissible: done.  Alg. 1's path below kappa = 1 through the grid's
+ *      outcomes (steady-state check and g >= 0, in the gradient's precision)
+ *      gives a bracket of width 1 / G;
+ *   B. the reverse sweep of the bracket's upper (violating) end on the
+ *      saved states, and a Newton step from there as the first estimate (the
+ *      secant through both ends' values when it leaves the bracket);
+ *   C. Newton steps on g(kappa) = 0, one gradient each, kept inside the
+ *      bracket the outcomes narrow, until the step, or the next iterate's
+ *      error predicted from the curvature of the last two slopes, is below
+ *      tol / 4, or max_iter gradients have been computed;
+ *   D. the handle evaluates [k - tol/2, k + tol/2] around the last iterate;
+ *      if it does not judge the lower end admissible and the upper one not,
+ *      exact rounds of max_candidates points equispaced inside the judged
+ *      bracket (Alg. 3's rule) shrink it to at most tol.
+ * Host out: *kappa = the judged bracket's admissible end (0 if none), *flags
+ * (bit 0: no evaluated kappa was admissible), *iterations (gradient
+ * evaluations, each kappa of a multi-kappa call counted).  Under a monotone
+ * predicate the result is within tol + 2^(1 - N) of Alg. 1's with N
+ * iterations.  Needs max_candidates >= 3.  Synchronous.  RRG_EINVAL,
+ * RRG_ECUDA. */
 RRG_API int rrg_newton_search(rrg_handle h, const double *x_t, double r_t, double v_prev, double tol,
                       int max_iter, int checkpoint, int precision, double *kappa, int32_t *flags,
                       int32_t *iterations);

@@ -7,9 +7,11 @@
 // (k*, j*) (a subgradient where the argmin is not unique) is obtained by the
 // reverse (adjoint) sweep of the RK4 recursion of trajectory k* from j* back
 // to 0:
-//   forward  adjoint_forward_kernel: one thread per scenario, full horizon,
-//            the state saved every `checkpoint` steps, per-lane min and argmin;
-//   argmin   adjoint_argmin_kernel: the first (k, then j) attaining the min;
+//   forward  adjoint_forward_kernel: one thread per (kappa, scenario), full
+//            horizon, with the rollouts' binary32/binary64 step, the state
+//            saved every `checkpoint` steps, per-lane min and argmin;
+//   argmin   adjoint_argmin_kernel: per kappa, the first (k, then j)
+//            attaining the min;
 //   reverse  adjoint_reverse_kernel: the checkpoint segments before j* are
 //            recomputed in parallel (one thread each), storing every step's
 //            state and RK4 stage points; one thread then sweeps them
@@ -22,6 +24,7 @@
 
 #include "rrg_device.cuh"
 #include "rrg_internal.h"
+#include "rrg_lane.cuh"
 
 namespace rrg {
 
@@ -34,6 +37,27 @@ struct ConstAdj {
   T W_o2, V0, y_scale;
 };
 
+// The elementary functions of the reverse sweep.  binary32: MUFU forms
+// (__powf, __logf, approximate reciprocal), relative errors of a few 1e-7,
+// far inside what a binary32 gradient carries anyway; binary64: x^e through
+// the handle's series (pow_m1_series falls back to pow outside [1, 2] or for
+// another exponent), log and IEEE division.
+template <typename T> struct VjpMath;
+template <>
+struct VjpMath<float> {
+  static __device__ __forceinline__ float pw(float x, float e, const PowSeries*) { return __powf(x, e); }
+  static __device__ __forceinline__ float ln(float x) { return __logf(x); }
+  static __device__ __forceinline__ float inv(float x) { return __fdividef(1.0f, x); }
+};
+template <>
+struct VjpMath<double> {
+  static __device__ __forceinline__ double pw(double x, double e, const PowSeries* S) {
+    return pow_m1_series(S, x, e) + 1.0;
+  }
+  static __device__ __forceinline__ double ln(double x) { return log(x); }
+  static __device__ __forceinline__ double inv(double x) { return 1.0 / x; }
+};
+
 // Vector-Jacobian product of fc3_rhs at q with output adjoint (b_ca, b_w,
 // b_sm): adds J^T b to (qb_ca, qb_w, qb_sm) and the constants' adjoints to g.
 template <typename T>
@@ -44,9 +68,9 @@ __device__ void fc3_rhs_vjp(const Fc3K<T>& K, const CandK<T>& C, T q_ca, T w, T 
   const T W_sm = K.k_sm * (q_sm - q_ca);
   const T W_ca = K.k_ca * q_ca;
   const T Pi = T(1) + q_sm * K.inv_p_atm;
-  const T Pe = pow(Pi, K.e);
+  const T Pe = VjpMath<T>::pw(Pi, K.e, K.pws);
   const T pr = Pe - T(1);
-  const T inv_w = T(1) / w;
+  const T inv_w = VjpMath<T>::inv(w);
   const T tau_cp = K.C_cp * pr * W_cp * inv_w;
   const T v_cm = C.V0 - K.K_p * W_cp;
   const T tau_cm = K.C_m * (v_cm - K.k_v * w);
@@ -77,8 +101,8 @@ __device__ void fc3_rhs_vjp(const Fc3K<T>& K, const CandK<T>& C, T q_ca, T w, T 
   Wcp_b += tcp_b * K.C_cp * pr * inv_w;
   w_b += -tcp_b * tau_cp * inv_w;
   // pr = Pi^e - 1
-  g.e += pr_b * Pe * log(Pi);
-  const T Pi_b = pr_b * K.e * Pe / Pi;
+  g.e += pr_b * Pe * VjpMath<T>::ln(Pi);
+  const T Pi_b = pr_b * K.e * Pe * VjpMath<T>::inv(Pi);
   // Pi = 1 + q_sm inv_p_atm
   T qsm_b = Pi_b * K.inv_p_atm;
   g.inv_p_atm += Pi_b * q_sm;
@@ -176,77 +200,106 @@ __device__ CandK<T> cand_of(const double* P, double I) {
 }
 
 // Register slots of the forward pass's disturbance prefetch ring.
+
 constexpr int kFwdRing = 8;
 
-// Forward: one thread per scenario, full horizon; state saved at j = 0, C,
-// 2C, ... (j < H) into ckpt[(k * nseg + c) * 3 + i]; per-lane min slack and
-// the first step attaining it.  The binary64 scenarios are read and rounded
-// to T.
-template <typename T>
+// The launch's rollout constants in precision T.
+template <typename T> __device__ __forceinline__ RhsU<T> launch_u(const Launch& L);
+template <> __device__ __forceinline__ RhsU<float> launch_u<float>(const Launch& L) { return L.u32; }
+template <> __device__ __forceinline__ RhsU<double> launch_u<double>(const Launch& L) { return L.u64; }
+template <typename T> __device__ __forceinline__ RhsC<T> launch_c(const Launch& L, int i);
+template <> __device__ __forceinline__ RhsC<float> launch_c<float>(const Launch& L, int i) { return L.cand_c32[i]; }
+template <> __device__ __forceinline__ RhsC<double> launch_c<double>(const Launch& L, int i) { return L.cand_c64[i]; }
+
+// Forward: one thread per (candidate slot i = blockIdx.y, scenario k), full
+// horizon, with the rollouts' arithmetic (deviation coordinates about the
+// candidate's reference point, the multiplied-out right-hand side, the
+// slot's constants from the candidate set-up; under parametric uncertainty
+// the scenario's own model): the state x_j is saved in gauge coordinates at
+// j = 0, C, 2C, ... (j < H) into ckpt[((i N + k) nseg + c) 3 + .], and the
+// lane's min slack and the first step attaining it go to lane_min / lane_arg
+// [i N + k].  DT: the disturbance array's type (the stored binary32 copy for
+// binary32 gradients when the handle draws one, else the binary64 values
+// rounded to T).  The disturbances pass through a ring of kFwdRing register
+// slots: step j takes slot j % kFwdRing and refills it with step j +
+// kFwdRing's values (steps past the horizon re-read the last one), so each
+// load has kFwdRing steps to arrive.
+template <typename T, typename DT>
 __global__ void __launch_bounds__(128)
-adjoint_forward_kernel(const Launch L, const double* __restrict__ d, const double* __restrict__ x_t,
-                       double v_prev, double r, double kappa, int checkpoint,
+adjoint_forward_kernel(const Launch L, const DT* __restrict__ d, int checkpoint,
                        double* __restrict__ ckpt, double* __restrict__ lane_min,
                        int* __restrict__ lane_arg) {
+  const int i = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = L.N, H = L.H;
   if (k >= N) return;
-  const double v = governed(v_prev, r, kappa);
-  double Pk[RRG_NPARAM];
-  scenario_params(L, k, Pk);
-  const Fc3K<T> K = konst<T>(Pk);
-  const CandK<T> C = cand_of<T>(Pk, v);
-  const double p_atm = Pk[P_P_ATM];
-  T q_ca = static_cast<T>(x_t[0] - p_atm), w = static_cast<T>(x_t[1]),
-    q_sm = static_cast<T>(x_t[2] - p_atm);
-  const T dt = static_cast<T>(L.dt), y_min = static_cast<T>(L.y_min);
+  RhsU<T> K = launch_u<T>(L);
+  RhsC<T> C = launch_c<T>(L, i);
+  double p_atm = L.params[P_P_ATM];
+  if (L.pmul != nullptr)
+    p_atm = scenario_model<T>(L.params, L.pmul + static_cast<size_t>(k) * RRG_NPARAM, L.cand_v[i],
+                              L.k64.pws, L.y_min, K, C);
+  T z_ca, z_w, z_sm, w_abs;
+  start_state<T>(C, L.st->x, p_atm, z_ca, z_w, z_sm, w_abs);
+  const double r_ca = static_cast<double>(C.r_ca), r_w = static_cast<double>(C.r_w),
+               r_sm = static_cast<double>(C.r_sm);
+  const StepC<T> S = step_consts<T>(K, static_cast<T>(L.dt));
   const int nseg = H / checkpoint + 1;
   const size_t HN = static_cast<size_t>(H) * N;
-  T smin = fc3_output<T>(C, q_ca, q_sm) - y_min;
+  double* ck = ckpt + (static_cast<size_t>(i) * N + k) * nseg * 3;
+  T smin = C.y_scale * (z_sm - z_ca) + C.s_off;
   int arg = 0;
-  // the disturbances pass through a ring of kFwdRing register slots: step j
-  // takes slot j % kFwdRing and refills it with step j + kFwdRing's values
-  // (steps past the horizon re-read the last one), so each load has
-  // kFwdRing steps to arrive; the unrolled loop keeps the slots in registers
   auto at = [&](int j) { return static_cast<size_t>(j < H ? j : H - 1) * N + k; };
-  double ring[kFwdRing][3];
+  T ring[kFwdRing][3];
 #pragma unroll
   for (int u = 0; u < kFwdRing; ++u) {
     const size_t o = at(u);
-    ring[u][0] = d[o]; ring[u][1] = d[HN + o]; ring[u][2] = d[2 * HN + o];
+    ring[u][0] = static_cast<T>(d[o]);
+    ring[u][1] = static_cast<T>(d[HN + o]);
+    ring[u][2] = static_cast<T>(d[2 * HN + o]);
   }
+  int next_ck = 0;  // the next step whose state is saved
   for (int j0 = 0; j0 < H; j0 += kFwdRing) {
 #pragma unroll
     for (int u = 0; u < kFwdRing; ++u) {
       const int j = j0 + u;
       if (j >= H) break;
-      const T e0 = static_cast<T>(ring[u][0]), e1 = static_cast<T>(ring[u][1]),
-              e2 = static_cast<T>(ring[u][2]);
+      const T e0 = ring[u][0], e1 = ring[u][1], e2 = ring[u][2];
       const size_t o = at(j + kFwdRing);
-      ring[u][0] = d[o]; ring[u][1] = d[HN + o]; ring[u][2] = d[2 * HN + o];
-      if (j % checkpoint == 0) {
-        double* c = ckpt + (static_cast<size_t>(k) * nseg + j / checkpoint) * 3;
-        c[0] = q_ca; c[1] = w; c[2] = q_sm;
+      ring[u][0] = static_cast<T>(d[o]);
+      ring[u][1] = static_cast<T>(d[HN + o]);
+      ring[u][2] = static_cast<T>(d[2 * HN + o]);
+      if (j == next_ck) {
+        double* c = ck + (j / checkpoint) * 3;
+        c[0] = static_cast<double>(z_ca) + r_ca;
+        c[1] = static_cast<double>(z_w) + r_w;
+        c[2] = static_cast<double>(z_sm) + r_sm;
+        next_ck += checkpoint;
       }
-      rk4_step<T>(K, C, dt, q_ca, w, q_sm);
-      q_ca += e0; w += e1; q_sm += e2;
-      const T s = fc3_output<T>(C, q_ca, q_sm) - y_min;
+      rk4_step_fast<T>(K, C, S, z_ca, z_w, z_sm, w_abs, e0, e1, e2);
+      const T s = C.y_scale * (z_sm - z_ca) + C.s_off;
       if (s < smin) { smin = s; arg = j + 1; }
     }
   }
-  lane_min[k] = static_cast<double>(smin);
-  lane_arg[k] = arg;
+  lane_min[static_cast<size_t>(i) * N + k] = static_cast<double>(smin);
+  lane_arg[static_cast<size_t>(i) * N + k] = arg;
 }
 
+// Slot i = blockIdx.x: the first (k, then j) attaining the min of the
+// slot's lanes; out[i * kOutStride + 0] = g, [1], [2] = k*, j* (as long long).
+constexpr int kOutStride = kAdjOutStride;
+
 __global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
-                                      const int* __restrict__ lane_arg, int N, double* out_g,
-                                      long long* out_k, long long* out_j) {
+                                      const int* __restrict__ lane_arg, int N, double* out) {
   __shared__ double sv[256];
   __shared__ int sk[256];
+  const int i = blockIdx.x;
+  const double* lm = lane_min + static_cast<size_t>(i) * N;
+  const int* la = lane_arg + static_cast<size_t>(i) * N;
   double best = INFINITY;
   int bk = 0x7fffffff;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const double s = lane_min[k];
+    const double s = lm[k];
     if (s < best || (s == best && k < bk)) { best = s; bk = k; }
   }
   sv[threadIdx.x] = best;
@@ -264,9 +317,10 @@ __global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *out_g = sv[0];
-    *out_k = sk[0];
-    *out_j = (sk[0] >= 0 && sk[0] < N) ? lane_arg[sk[0]] : 0;
+    double* o = out + static_cast<size_t>(i) * kOutStride;
+    long long kj[2] = {sk[0], (sk[0] >= 0 && sk[0] < N) ? la[sk[0]] : 0};
+    o[0] = sv[0];
+    memcpy(o + 1, kj, sizeof kj);
   }
 }
 
@@ -285,15 +339,20 @@ constexpr int kRevThreads = 128;
 //     ahead.
 // seg: scratch of (j* + 1) * kSegVals values (at most (H + 1) * kSegVals).
 // out[0] = dg/dkappa, out[1..3] = dg/dx_t, out[4..4+NPARAM) = dg/dtheta.
-template <typename T>
+template <typename T, typename DT>
 __global__ void __launch_bounds__(kRevThreads)
-adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
-                       double v_prev, double r, double kappa, int checkpoint,
-                       const double* __restrict__ ckpt, const long long* kj,
-                       T* __restrict__ seg, double* __restrict__ out) {
-  if (blockIdx.x != 0) return;
-  const double v = governed(v_prev, r, kappa);
+adjoint_reverse_kernel(const Launch L, const DT* __restrict__ d, double v_prev, double r,
+                       int checkpoint, const double* __restrict__ ckpt, T* __restrict__ seg_all,
+                       double* __restrict__ out_all, int slot0) {
+  const int i = slot0 + static_cast<int>(blockIdx.x);  // candidate slot
   const int N = L.N, H = L.H;
+  double* o = out_all + static_cast<size_t>(i) * kOutStride;
+  long long kj[2];
+  memcpy(kj, o + 1, sizeof kj);
+  double* out = o + 3;
+  T* seg = seg_all + static_cast<size_t>(i) * (H + 1) * kSegVals;
+  const double kappa = L.cand_kappa[i];
+  const double v = governed(v_prev, r, kappa);
   if (kj[0] < 0 || kj[0] >= N || kj[1] < 0 || kj[1] > H) {  // no argmin: same for every thread
     if (threadIdx.x < 4 + RRG_NPARAM) out[threadIdx.x] = NAN;
     return;
@@ -301,12 +360,13 @@ adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
   const int k = static_cast<int>(kj[0]), jstar = static_cast<int>(kj[1]);
   double P[RRG_NPARAM];
   scenario_params(L, k, P);
-  const Fc3K<T> K = konst<T>(P);
+  Fc3K<T> K = konst<T>(P);
+  if (sizeof(T) == 8) K.pws = L.k64.pws;  // the series of the model's exponent (checked per call)
   const CandK<T> C = cand_of<T>(P, v);
   const T dt = static_cast<T>(L.dt);
   const int nseg = H / checkpoint + 1;
   const size_t HN = static_cast<size_t>(H) * N;
-  const double* ck = ckpt + static_cast<size_t>(k) * nseg * 3;
+  const double* ck = ckpt + (static_cast<size_t>(i) * N + k) * nseg * 3;
   // phase 1: segment c covers steps c * checkpoint .. min((c + 1) * checkpoint, j*) - 1
   const int nc = jstar > 0 ? (jstar - 1) / checkpoint + 1 : 0;
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
@@ -420,49 +480,67 @@ adjoint_reverse_kernel(const Launch L, const double* __restrict__ d,
 
 }  // namespace
 
-// Host side: enqueue forward, argmin and reverse on the handle's stream.
-// ckpt: N * (H / checkpoint + 1) * 3 doubles; lane_min/lane_arg: N each;
-// seg: (H + 1) * 12 doubles; d_kj: 2; d_out: 1 + 3 + RRG_NPARAM.  fwd_begin /
-// fwd_end (either may be null): events recorded around the forward kernel.
-cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
-                           double kappa, int checkpoint, double* ckpt, double* lane_min,
-                           int* lane_arg, double* seg, double* d_g, long long* d_kj,
-                           double* d_out, cudaEvent_t fwd_begin, cudaEvent_t fwd_end) {
-  // one warp per block until the blocks of 128 threads would fill every SM:
+// Host side.  launch_adjoint_forward enqueues the forward pass and the
+// argmin for the m candidate slots the last candidate set-up prepared
+// (kappas in cand_kappa); launch_adjoint_reverse the reverse sweeps of slots
+// slot0 .. slot0 + count - 1 on the states the forward pass saved.
+// ckpt: m N (H / checkpoint + 1) 3 doubles; lane_min / lane_arg: m N each;
+// seg: m (H + 1) 12 values of T; d_out: m kOutStride doubles (per slot: g,
+// k*, j*, then dg/dkappa, dg/dx_t, dg/dtheta).  fwd_begin / fwd_end (either
+// may be null): events around the forward kernel.  The binary32 gradient
+// reads the stored binary32 disturbances when the handle draws them (the
+// values its binary32 rollouts use), otherwise the binary64 array (filled by
+// the caller) rounded to binary32.
+namespace {
+bool reads32(const Launch& L, bool fp64) { return !fp64 && L.precision != RRG_FP64 && !L.scen_gen; }
+}  // namespace
+
+cudaError_t launch_adjoint_forward(const Launch& L, bool fp64, int m, int checkpoint, double* ckpt,
+                                   double* lane_min, int* lane_arg, double* d_out,
+                                   cudaEvent_t fwd_begin, cudaEvent_t fwd_end) {
+  // one warp per block until blocks of 128 threads would fill every SM:
   // each scenario is one dependent chain, so spreading them over SMs costs
-  // nothing and puts more SMs' binary64 units to work
-  if (L.sms <= 0) return cudaErrorInvalidConfiguration;
-  const int sms = L.sms;
-  const int threads = (L.N >= 128 * sms) ? 128 : 32;
-  const int blocks = (L.N + threads - 1) / threads;
+  // nothing
+  if (L.sms <= 0 || m < 1) return cudaErrorInvalidConfiguration;
+  const long long lanes = static_cast<long long>(L.N) * m;
+  const int threads = (lanes >= 128LL * L.sms) ? 128 : 32;
+  const dim3 grid((L.N + threads - 1) / threads, m);
   if (fwd_begin) {
     const cudaError_t er = cudaEventRecord(fwd_begin, L.stream);
     if (er != cudaSuccess) return er;
   }
-  if (fp64) {
-    adjoint_forward_kernel<double><<<blocks, threads, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
-                                                                     checkpoint, ckpt, lane_min, lane_arg);
-  } else {
-    adjoint_forward_kernel<float><<<blocks, threads, 0, L.stream>>>(L, L.d64, d_x, v_prev, r, kappa,
-                                                                    checkpoint, ckpt, lane_min, lane_arg);
-  }
+  if (fp64)
+    adjoint_forward_kernel<double, double><<<grid, threads, 0, L.stream>>>(L, L.d64, checkpoint, ckpt,
+                                                                           lane_min, lane_arg);
+  else if (reads32(L, fp64))
+    adjoint_forward_kernel<float, float><<<grid, threads, 0, L.stream>>>(L, L.d32, checkpoint, ckpt,
+                                                                         lane_min, lane_arg);
+  else
+    adjoint_forward_kernel<float, double><<<grid, threads, 0, L.stream>>>(L, L.d64, checkpoint, ckpt,
+                                                                          lane_min, lane_arg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (fwd_end) {
     e = cudaEventRecord(fwd_end, L.stream);
     if (e != cudaSuccess) return e;
   }
-  adjoint_argmin_kernel<<<1, 256, 0, L.stream>>>(lane_min, lane_arg, L.N, d_g, d_kj, d_kj + 1);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (fp64) {
-    adjoint_reverse_kernel<double><<<1, kRevThreads, 0, L.stream>>>(L, L.d64, v_prev, r, kappa,
-                                                                     checkpoint, ckpt, d_kj, seg, d_out);
-  } else {
-    adjoint_reverse_kernel<float><<<1, kRevThreads, 0, L.stream>>>(L, L.d64, v_prev, r, kappa, checkpoint,
-                                                                    ckpt, d_kj, reinterpret_cast<float*>(seg),
-                                                                    d_out);
-  }
+  adjoint_argmin_kernel<<<m, 256, 0, L.stream>>>(lane_min, lane_arg, L.N, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_reverse(const Launch& L, bool fp64, int slot0, int count, double v_prev,
+                                   double r, int checkpoint, const double* ckpt, void* seg,
+                                   double* d_out) {
+  if (count < 1 || slot0 < 0) return cudaErrorInvalidConfiguration;
+  if (fp64)
+    adjoint_reverse_kernel<double, double><<<count, kRevThreads, 0, L.stream>>>(
+        L, L.d64, v_prev, r, checkpoint, ckpt, static_cast<double*>(seg), d_out, slot0);
+  else if (reads32(L, fp64))
+    adjoint_reverse_kernel<float, float><<<count, kRevThreads, 0, L.stream>>>(
+        L, L.d32, v_prev, r, checkpoint, ckpt, static_cast<float*>(seg), d_out, slot0);
+  else
+    adjoint_reverse_kernel<float, double><<<count, kRevThreads, 0, L.stream>>>(
+        L, L.d64, v_prev, r, checkpoint, ckpt, static_cast<float*>(seg), d_out, slot0);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ struct rrg_ctx {
   size_t adj_ckpt_cap = 0;
   double* adj_lane_min = nullptr;
   int* adj_lane_arg = nullptr;
+  size_t adj_lane_cap = 0;      // lanes (m N) the lane arrays and adj_out hold
   double* adj_seg = nullptr;
   size_t adj_seg_cap = 0;
   double* adj_out = nullptr;   // [0] g, [1..2] k*, j* (as long long), [3..] gradient
@@ -449,6 +450,109 @@ void enqueue_count_only(rrg_ctx* h) {
   h->launches += 1 + 1 + 1 + 1 + (1 + rec) + 1 + 1;
   h->rollout_launches += 2;
   h->rounds += 1;
+}
+
+}  // namespace
+
+namespace {
+
+// Grows a device buffer to n elements (contents not kept).
+template <typename T>
+cudaError_t grow(T** p, size_t* cap, size_t n) {
+  if (n <= *cap) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+}  // namespace
+
+namespace {
+
+// Scratch of the adjoint for m kappas (grown on demand; a buffer queued work
+// may still use is freed only after the stream drained).
+int adj_buffers(rrg_ctx* h, size_t M, int checkpoint) {
+  const size_t N = h->cfg.n_scenarios, H = h->cfg.horizon;
+  const size_t ckpt_need = M * N * (H / checkpoint + 1) * 3;
+  const size_t seg_need = M * (H + 1) * 12;  // every step's state and stage points, per kappa
+  if (ckpt_need > h->adj_ckpt_cap || seg_need > h->adj_seg_cap || M * N > h->adj_lane_cap)
+    CK(cudaStreamSynchronize(h->stream));
+  CK(grow(&h->adj_ckpt, &h->adj_ckpt_cap, ckpt_need));
+  CK(grow(&h->adj_seg, &h->adj_seg_cap, seg_need));
+  if (M * N > h->adj_lane_cap) {
+    size_t c1 = 0, c2 = 0, c3 = 0;
+    if (h->adj_lane_min) { cudaFree(h->adj_lane_min); h->adj_lane_min = nullptr; }
+    if (h->adj_lane_arg) { cudaFree(h->adj_lane_arg); h->adj_lane_arg = nullptr; }
+    if (h->adj_out) { cudaFree(h->adj_out); h->adj_out = nullptr; }
+    h->adj_lane_cap = 0;
+    CK(grow(&h->adj_lane_min, &c1, M * N));
+    CK(grow(&h->adj_lane_arg, &c2, M * N));
+    CK(grow(&h->adj_out, &c3, static_cast<size_t>(h->cfg.max_candidates) * kAdjOutStride));
+    h->adj_lane_cap = M * N;
+  }
+  return RRG_OK;
+}
+
+// Enqueues the candidate set-up of m kappas, the binary64 scenario fill if
+// the gradient reads it, the forward pass and the argmin (no sync).
+int adj_enqueue_forward(rrg_ctx* h, const double* x_t, double v_prev, double r_t, const double* kappas,
+                        int m, int checkpoint, int precision) {
+  int rc = adj_buffers(h, static_cast<size_t>(m), checkpoint);
+  if (rc != RRG_OK) return rc;
+  double* kap_h = h->io_h + IO_LEN;
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  std::memcpy(kap_h, kappas, static_cast<size_t>(m) * sizeof(double));
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, IO_LEN * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->kap_dev, kap_h, m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const Launch& L = h->L;
+  // candidate set-up (kappas, setpoints, rollout constants, steady-state check)
+  CK(launch_eval_prepare(L, h->io_dev + IO_X, v_prev, r_t, h->kap_dev, m));
+  CK(launch_prepare(L, m));
+  h->launches += 2;
+  const bool use32 = precision == RRG_FP32 && h->cfg.precision != RRG_FP64 && !h->cfg.scenarios_in_register;
+  if (!use32) {
+    CK(launch_materialize64(L));
+    h->launches += 2;
+  }
+  // the forward pass rolls out every scenario: timed as a rollout launch
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (h->profiling && !h->capturing) { ea = take_event(h); eb = take_event(h); }
+  if (!(ea && eb)) {
+    if (ea) h->ev_free.push_back(ea);
+    if (eb) h->ev_free.push_back(eb);
+    ea = eb = nullptr;
+  }
+  CK(launch_adjoint_forward(L, precision == RRG_FP64, m, checkpoint, h->adj_ckpt, h->adj_lane_min,
+                            h->adj_lane_arg, h->adj_out, ea, eb));
+  if (ea) h->ev_roll.emplace_back(ea, eb);
+  h->launches += 2;
+  h->rollout_launches += 1;
+  return RRG_OK;
+}
+
+int adj_enqueue_reverse(rrg_ctx* h, int slot0, int count, double v_prev, double r_t, int checkpoint,
+                        int precision) {
+  CK(launch_adjoint_reverse(h->L, precision == RRG_FP64, slot0, count, v_prev, r_t, checkpoint,
+                            h->adj_ckpt, h->adj_seg, h->adj_out));
+  h->launches += 1;
+  return RRG_OK;
+}
+
+// Reads slots 0..m-1 of the adjoint's output (and the steady-state flags)
+// after the stream drained.
+int adj_read(rrg_ctx* h, int m, std::vector<double>* out, std::vector<int32_t>* ss) {
+  out->resize(static_cast<size_t>(m) * kAdjOutStride);
+  CK(cudaMemcpyAsync(out->data(), h->adj_out, out->size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  if (ss) {
+    ss->resize(static_cast<size_t>(m));
+    CK(cudaMemcpyAsync(ss->data(), h->cand_ss, m * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return RRG_OK;
 }
 
 }  // namespace
@@ -1023,137 +1127,211 @@ int rrg_closed_loop(rrg_handle h, const double* x0, double v0, const double* r_s
   return RRG_OK;
 }
 
-int rrg_slack_gradient(rrg_handle h, const double* x_t, double v_prev, double r_t, double kappa,
-                       int checkpoint, int precision, double* g, double* grad, int64_t* k_star,
-                       int64_t* j_star) {
+int rrg_slack_gradients(rrg_handle h, const double* x_t, double v_prev, double r_t, const double* kappas,
+                        int m, int checkpoint, int precision, double* g, double* grad, int64_t* k_star,
+                        int64_t* j_star, uint8_t* ss_ok) {
   if (!h) return RRG_EINVAL;
   if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
     return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite and v_prev, r_t > 0");
-  if (!(kappa >= 0.0 && kappa <= 1.0)) return set_err(h, RRG_EINVAL, "kappa outside [0, 1]");
+  if (!kappas || m < 1 || m > h->cfg.max_candidates)
+    return set_err(h, RRG_EINVAL, "need 1 <= m <= max_candidates and non-NULL kappas");
+  for (int i = 0; i < m; ++i)
+    if (!(kappas[i] >= 0.0 && kappas[i] <= 1.0))
+      return set_err(h, RRG_EINVAL, "kappas[%d] outside [0, 1]", i);
   if (checkpoint < 1 || checkpoint > 1 << 16)
     return set_err(h, RRG_EINVAL, "checkpoint must be in [1, 65536]");
   if (precision != RRG_FP64 && precision != RRG_FP32)
     return set_err(h, RRG_EINVAL, "precision must be RRG_FP64 or RRG_FP32");
   DeviceGuard gd(h->device);
-  const size_t N = h->cfg.n_scenarios, H = h->cfg.horizon;
-  const size_t need = N * (H / checkpoint + 1) * 3;
-  if (need > h->adj_ckpt_cap) {
-    if (h->adj_ckpt) cudaFree(h->adj_ckpt);
-    h->adj_ckpt = nullptr;
-    h->adj_ckpt_cap = 0;
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_ckpt), need * sizeof(double)));
-    h->adj_ckpt_cap = need;
+  int rc = adj_enqueue_forward(h, x_t, v_prev, r_t, kappas, m, checkpoint, precision);
+  if (rc != RRG_OK) return rc;
+  rc = adj_enqueue_reverse(h, 0, m, v_prev, r_t, checkpoint, precision);
+  if (rc != RRG_OK) return rc;
+  std::vector<double> out;
+  std::vector<int32_t> ss;
+  rc = adj_read(h, m, &out, ss_ok ? &ss : nullptr);
+  if (rc != RRG_OK) return rc;
+  for (int i = 0; i < m; ++i) {
+    const double* o = out.data() + static_cast<size_t>(i) * kAdjOutStride;
+    long long kj[2];
+    std::memcpy(kj, o + 1, sizeof kj);
+    if (g) g[i] = o[0];
+    if (k_star) k_star[i] = kj[0];
+    if (j_star) j_star[i] = kj[1];
+    if (grad) std::memcpy(grad + static_cast<size_t>(i) * (4 + RRG_NPARAM), o + 3, (4 + RRG_NPARAM) * sizeof(double));
+    if (ss_ok) ss_ok[i] = ss[i] ? 1 : 0;
   }
-  if (!h->adj_lane_min) {
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_lane_min), N * sizeof(double)));
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_lane_arg), N * sizeof(int)));
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_out), (3 + 4 + RRG_NPARAM) * sizeof(double)));
-  }
-  // every step's state and stage points of the reverse sweep: (H + 1) * 12 values
-  const size_t seg_need = (H + 1) * 12;
-  if (seg_need > h->adj_seg_cap) {
-    if (h->adj_seg) cudaFree(h->adj_seg);
-    h->adj_seg = nullptr;
-    h->adj_seg_cap = 0;
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->adj_seg), seg_need * sizeof(double)));
-    h->adj_seg_cap = seg_need;
-  }
-  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
-  CK(cudaMemcpyAsync(h->io_dev, h->io_h, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  CK(launch_materialize64(h->L));
-  // the forward pass rolls out every scenario: timed as a rollout launch
-  cudaEvent_t ea = nullptr, eb = nullptr;
-  if (h->profiling && !h->capturing) { ea = take_event(h); eb = take_event(h); }
-  if (!(ea && eb)) {
-    if (ea) h->ev_free.push_back(ea);
-    if (eb) h->ev_free.push_back(eb);
-    ea = eb = nullptr;
-  }
-  CK(launch_adjoint(h->L, precision == RRG_FP64, h->io_dev + IO_X, v_prev, r_t, kappa, checkpoint,
-                    h->adj_ckpt, h->adj_lane_min, h->adj_lane_arg, h->adj_seg, h->adj_out,
-                    reinterpret_cast<long long*>(h->adj_out + 1), h->adj_out + 3, ea, eb));
-  if (ea) h->ev_roll.emplace_back(ea, eb);
-  h->launches += 5;
-  h->rollout_launches += 1;
-  double out[3 + 4 + RRG_NPARAM];
-  CK(cudaMemcpyAsync(out, h->adj_out, sizeof out, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  long long kj[2];
-  std::memcpy(kj, out + 1, sizeof kj);
-  if (g) *g = out[0];
-  if (k_star) *k_star = kj[0];
-  if (j_star) *j_star = kj[1];
-  if (grad) std::memcpy(grad, out + 3, (4 + RRG_NPARAM) * sizeof(double));
   return RRG_OK;
 }
 
+int rrg_slack_gradient(rrg_handle h, const double* x_t, double v_prev, double r_t, double kappa,
+                       int checkpoint, int precision, double* g, double* grad, int64_t* k_star,
+                       int64_t* j_star) {
+  if (!h) return RRG_EINVAL;
+  if (!(kappa >= 0.0 && kappa <= 1.0)) return set_err(h, RRG_EINVAL, "kappa outside [0, 1]");
+  return rrg_slack_gradients(h, x_t, v_prev, r_t, &kappa, 1, checkpoint, precision, g, grad, k_star,
+                             j_star, nullptr);
+}
+
+
+// Adjoint-driven search (see rrg.h).  Each round is one synchronous call:
+//   A. the forward pass and argmin (no reverse sweep) at kappa = j / G, j =
+//      0..G (G = 8, or the largest power of two with G + 1 <= max_candidates):
+//      g and the steady-state outcome at each point.  kappa = 1 is judged
+//      by the handle's own evaluation unless the binary32 g(1) is below
+//      -1e-4, far outside the binary32 error (below 1e-5 on these
+//      workloads), or its steady-state check failed.  Alg. 1's path below
+//      kappa = 1 through the grid's outcomes gives a bracket of width 1 / G;
+//   B. the reverse sweep of the bracket's upper end on the states the
+//      forward pass saved, and a Newton step from there (the secant through
+//      both ends' values when it leaves the bracket);
+//   C. Newton steps on g(kappa) = 0, one gradient each, inside the bracket
+//      (narrowed by each outcome), until the step, or the next iterate's
+//      error predicted from the curvature of the last two slopes, is below
+//      tol / 4;
+//   D. the handle evaluates [k - tol/2, k + tol/2] around the last iterate;
+//      if it does not judge the lower end admissible and the upper one not,
+//      exact rounds of max_candidates points equispaced inside the judged
+//      bracket (Alg. 3's rule) shrink it to at most tol.
+// Only the handle's evaluations decide; the gradients steer.
 int rrg_newton_search(rrg_handle h, const double* x_t, double r_t, double v_prev, double tol,
                       int max_iter, int checkpoint, int precision, double* kappa, int32_t* flags,
                       int32_t* iterations) {
   if (!h) return RRG_EINVAL;
   if (!(tol > 0.0) || max_iter < 1) return set_err(h, RRG_EINVAL, "tol > 0 and max_iter >= 1 needed");
-  if (h->cfg.max_candidates < 2)
-    return set_err(h, RRG_EINVAL, "the bracket check needs max_candidates >= 2");
-  const double thr_ss = h->cfg.y_min + h->cfg.eps_ss * (h->cfg.y_c - h->cfg.y_min);
-  // admissible(k): steady-state check (device equilibrium) and g >= 0
-  auto ss_ok = [&](double k, bool* ok) -> int {
-    if (!h->cfg.ss_check) { *ok = true; return RRG_OK; }
-    double x[3], y = 0.0;
-    const double v = v_prev + k * (r_t - v_prev);
-    const int rc = rrg_equilibrium(h, v, x, &y);
-    if (rc == RRG_EINVAL) { *ok = false; return RRG_OK; }
-    if (rc != RRG_OK) return rc;
-    *ok = y >= thr_ss;
+  if (h->cfg.max_candidates < 3)
+    return set_err(h, RRG_EINVAL, "the search needs max_candidates >= 3");
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0))
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite and v_prev, r_t > 0");
+  if (checkpoint < 1 || checkpoint > 1 << 16)
+    return set_err(h, RRG_EINVAL, "checkpoint must be in [1, 65536]");
+  if (precision != RRG_FP64 && precision != RRG_FP32)
+    return set_err(h, RRG_EINVAL, "precision must be RRG_FP64 or RRG_FP32");
+  DeviceGuard gd(h->device);
+  const int M = h->cfg.max_candidates;
+  int32_t grads = 0;
+  int rc;
+  auto done = [&](double k, int32_t fl) {
+    if (kappa) *kappa = k;
+    if (flags) *flags = fl;
+    if (iterations) *iterations = grads;
     return RRG_OK;
   };
-  int32_t it = 0;
-  // Alg. 1 starts with kappa = 1, judged by the handle's own evaluation
-  const double one = 1.0;
-  uint8_t adm_one = 0;
-  int rc = rrg_eval_candidates(h, x_t, v_prev, r_t, &one, 1, &adm_one, nullptr, nullptr);
+  // A. values on the grid j / G, j = 0..G
+  int G = 8;
+  while (G + 1 > M) G /= 2;
+  double kg[9];
+  for (int j = 0; j <= G; ++j) kg[j] = static_cast<double>(j) / G;
+  rc = adj_enqueue_forward(h, x_t, v_prev, r_t, kg, G + 1, checkpoint, precision);
   if (rc != RRG_OK) return rc;
-  if (adm_one) {
-    if (kappa) *kappa = 1.0;
-    if (flags) *flags = 0;
-    if (iterations) *iterations = 0;
-    return RRG_OK;
+  std::vector<double> out;
+  std::vector<int32_t> ss;
+  rc = adj_read(h, G + 1, &out, &ss);
+  if (rc != RRG_OK) return rc;
+  grads += G + 1;
+  auto gval = [&](int j) { return out[static_cast<size_t>(j) * kAdjOutStride]; };
+  auto adm_at = [&](int j) { return ss[j] && gval(j) >= 0.0; };
+  if (ss[G] && !(gval(G) < -1e-4)) {
+    // kappa = 1 is not clearly inadmissible: Alg. 1's first test, judged
+    const double one = 1.0;
+    uint8_t adm_one = 0;
+    rc = rrg_eval_candidates(h, x_t, v_prev, r_t, &one, 1, &adm_one, nullptr, nullptr);
+    if (rc != RRG_OK) return rc;
+    if (adm_one) return done(1.0, 0);
+    // the slots were reused by the evaluation: set the grid up again
+    rc = adj_enqueue_forward(h, x_t, v_prev, r_t, kg, G + 1, checkpoint, precision);
+    if (rc != RRG_OK) return rc;
+    rc = adj_read(h, G + 1, &out, &ss);
+    if (rc != RRG_OK) return rc;
   }
-  // like Alg. 1, kappa = 0 is never tested: it is the hold returned when no
-  // tested kappa is admissible
-  double lo = 0.0, hi = 1.0, k = 0.5;
-  bool any = false;
-  while (it < max_iter && hi - lo > tol) {
+  // Alg. 1's walk below kappa = 1 through the grid's levels
+  int jlo = 0, jhi = G;
+  while (jhi - jlo > 1) {
+    const int jm = (jlo + jhi) / 2;
+    if (adm_at(jm)) jlo = jm; else jhi = jm;
+  }
+  double lo = static_cast<double>(jlo) / G, hi = static_cast<double>(jhi) / G;
+  // B. the slope at the bracket's upper end (the violating side, whose
+  // argmin is the constraint's early dip, so its reverse sweep is short;
+  // the admissible end's minimum often comes late in the horizon), and a
+  // Newton step from there; the secant through both ends' values guards it
+  rc = adj_enqueue_reverse(h, jhi, 1, v_prev, r_t, checkpoint, precision);
+  if (rc != RRG_OK) return rc;
+  rc = adj_read(h, G + 1, &out, nullptr);
+  if (rc != RRG_OK) return rc;
+  const double ghi = gval(jhi), dhi = out[static_cast<size_t>(jhi) * kAdjOutStride + 3];
+  double k = 0.5 * (lo + hi);
+  if (ss[jhi] && ghi < 0.0 && dhi < 0.0 && std::isfinite(dhi)) {
+    k = hi - ghi / dhi;
+    if (adm_at(jlo) && !(k > lo)) {
+      // Newton overshoots below lo: the secant root instead
+      const double glo = gval(jlo);
+      k = lo + (hi - lo) * glo / (glo - ghi);
+    }
+  }
+  if (!(k > lo && k < hi)) k = 0.5 * (lo + hi);
+  double curv = 0.0;  // |g''| estimate from the last two slopes (none yet)
+  double k_prev = hi, d_prev = dhi;
+  // C. Newton steps inside the bracket
+  while (grads < max_iter && hi - lo > tol) {
     double g = 0.0, grad[4 + RRG_NPARAM];
-    int64_t ks, js;
-    rc = rrg_slack_gradient(h, x_t, v_prev, r_t, k, checkpoint, precision, &g, grad, &ks, &js);
+    uint8_t s1 = 0;
+    rc = rrg_slack_gradients(h, x_t, v_prev, r_t, &k, 1, checkpoint, precision, &g, grad, nullptr,
+                             nullptr, &s1);
     if (rc != RRG_OK) return rc;
-    ++it;
-    bool ok = false;
-    rc = ss_ok(k, &ok);
-    if (rc != RRG_OK) return rc;
-    const bool adm = ok && g >= 0.0;
-    if (adm) { lo = k; any = true; } else { hi = k; }
-    // Newton step on g(kappa) = 0 (g decreases through the boundary); fall
-    // back to the bracket midpoint when the step leaves the bracket
-    double kn = (grad[0] < 0.0 && ok) ? k - g / grad[0] : 0.5 * (lo + hi);
+    ++grads;
+    if (s1 && g >= 0.0) lo = k; else hi = k;
+    const double slope = grad[0];
+    if (std::isfinite(d_prev) && k != k_prev) curv = std::fabs(slope - d_prev) / std::fabs(k - k_prev);
+    k_prev = k;
+    d_prev = slope;
+    double kn = (s1 && slope < 0.0 && std::isfinite(g)) ? k - g / slope : 0.5 * (lo + hi);
     if (!(kn > lo && kn < hi)) kn = 0.5 * (lo + hi);
-    // a root approached from one side: step just across it to close the bracket
-    if (adm && kn - lo < 0.25 * tol) kn = lo + 0.5 * tol;
-    if (!adm && hi - kn < 0.25 * tol) kn = hi - 0.5 * tol;
-    if (kn <= lo || kn >= hi) kn = 0.5 * (lo + hi);
+    const double step = std::fabs(kn - k);
+    const double predicted = (s1 && slope < 0.0 && curv > 0.0) ? curv * step * step / (2.0 * -slope) : step;
     k = kn;
+    if (step <= 0.25 * tol || predicted <= 0.25 * tol) break;
   }
-  // the bracket as plain bisection judges it: lo admissible, hi not
-  int32_t fl = any ? 0 : 1;
-  const double br[2] = {lo, hi};
-  uint8_t a[2] = {0, 0};
-  rc = rrg_eval_candidates(h, x_t, v_prev, r_t, br, 2, a, nullptr, nullptr);
-  if (rc != RRG_OK) return rc;
-  if ((lo > 0.0 && !a[0]) || a[1] || hi - lo > tol) fl |= 4;
-  if (kappa) *kappa = any ? lo : 0.0;
-  if (flags) *flags = fl;
-  if (iterations) *iterations = it;
-  return RRG_OK;
+  // D. the handle's judgement of [k - tol/2, k + tol/2]
+  double lo_j = 0.0, hi_j = 1.0;  // judged: lo_j admissible (or 0), hi_j not
+  bool any = false;
+  {
+    double a = k - 0.5 * tol, b = k + 0.5 * tol;
+    if (a < 0.0) a = 0.0;
+    if (b > 1.0) b = 1.0;
+    const double br[2] = {a, b};
+    uint8_t ad[2] = {0, 0};
+    rc = rrg_eval_candidates(h, x_t, v_prev, r_t, br, 2, ad, nullptr, nullptr);
+    if (rc != RRG_OK) return rc;
+    if (ad[1]) {            // b admissible: the boundary lies above it
+      lo_j = b;
+      any = true;
+    } else if (ad[0]) {     // the expected outcome: [a, b], at most tol wide
+      lo_j = a;
+      hi_j = b;
+      any = a > 0.0;
+    } else {                // both inadmissible: below a
+      hi_j = a;
+    }
+  }
+  // fallback: exact k-section rounds inside the judged bracket
+  std::vector<double> pts(static_cast<size_t>(M));
+  std::vector<uint8_t> ad(static_cast<size_t>(M));
+  while (hi_j - lo_j > tol && hi_j > 0.0) {
+    for (int i = 0; i < M; ++i) pts[i] = lo_j + (hi_j - lo_j) * (i + 1) / (M + 1);
+    rc = rrg_eval_candidates(h, x_t, v_prev, r_t, pts.data(), M, ad.data(), nullptr, nullptr);
+    if (rc != RRG_OK) return rc;
+    int best = -1;
+    for (int i = 0; i < M; ++i)
+      if (ad[i]) best = i;
+    // Alg. 3's rule within the bracket: the largest admissible point
+    const double nlo = best >= 0 ? pts[best] : lo_j;
+    const double nhi = best + 1 < M ? pts[best + 1] : hi_j;
+    if (best >= 0) any = true;
+    lo_j = nlo;
+    hi_j = nhi;
+  }
+  return done(any ? lo_j : 0.0, any ? 0 : 1);
 }
 
 // Speculative-bisection shape: tree width and probe length.  Neither changes

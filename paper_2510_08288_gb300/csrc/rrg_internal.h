@@ -376,11 +376,15 @@ cudaError_t launch_loop_end(const Launch& L, LoopState* ls, uint64_t seed, uint6
 cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, double v0,
                              double* d_x_out);
 
-// Discrete adjoint of the min-slack objective (rrg_adjoint.cu).
-cudaError_t launch_adjoint(const Launch& L, bool fp64, const double* d_x, double v_prev, double r,
-                           double kappa, int checkpoint, double* ckpt, double* lane_min,
-                           int* lane_arg, double* seg, double* d_g, long long* d_kj,
-                           double* d_out, cudaEvent_t fwd_begin, cudaEvent_t fwd_end);
+// Discrete adjoint of the min-slack objective (rrg_adjoint.cu), for the m
+// candidate slots the last candidate set-up prepared; layouts in the file.
+constexpr int kAdjOutStride = 3 + 4 + RRG_NPARAM;
+cudaError_t launch_adjoint_forward(const Launch& L, bool fp64, int m, int checkpoint, double* ckpt,
+                                   double* lane_min, int* lane_arg, double* d_out,
+                                   cudaEvent_t fwd_begin, cudaEvent_t fwd_end);
+cudaError_t launch_adjoint_reverse(const Launch& L, bool fp64, int slot0, int count, double v_prev,
+                                   double r, int checkpoint, const double* ckpt, void* seg,
+                                   double* d_out);
 
 // Binary32-vs-binary64 slack error of every trajectory of the m candidates
 // the last eval_prepare + prepare set up (rrg_error.cu): per lane o = i N + k

@@ -105,6 +105,8 @@ def _load():
         "rrg_reset_stats": (ctypes.c_int, [_p]),
         "rrg_slack_gradient": (ctypes.c_int, [_p, _p, _d, _d, _d, ctypes.c_int, ctypes.c_int, _p, _p,
                                               P(ctypes.c_int64), P(ctypes.c_int64)]),
+        "rrg_slack_gradients": (ctypes.c_int, [_p, _p, _d, _d, _p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               _p, _p, _p, _p, _p]),
         "rrg_newton_search": (ctypes.c_int, [_p, _p, _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              _p, _p, _p]),
         "rrg_eval_candidates_static": (ctypes.c_int, [_p, ctypes.c_int, P(RrgConfig), _p, _p, _p, _p, _d,
@@ -337,6 +339,19 @@ def rrg_slack_gradient(h, x_t, v_prev, r_t, kappa, checkpoint=50, precision=FP64
     return g.value, grad, ks.value, js.value
 
 
+def rrg_slack_gradients(h, x_t, v_prev, r_t, kappas, checkpoint=50, precision=FP64):
+    """Gradients at m kappas in one call: (g[m], grad[m, 31], k*[m], j*[m],
+    ss_ok[m])."""
+    x, k = _f64(x_t), _f64(kappas)
+    m = k.shape[0]
+    g, grad = np.zeros(m), np.zeros((m, 4 + NPARAM))
+    ks, js = np.zeros(m, dtype=np.int64), np.zeros(m, dtype=np.int64)
+    ss = np.zeros(m, dtype=np.uint8)
+    _check(lib.rrg_slack_gradients(h, _ptr(x), float(v_prev), float(r_t), _ptr(k), m, int(checkpoint),
+                                   int(precision), _ptr(g), _ptr(grad), _ptr(ks), _ptr(js), _ptr(ss)), h)
+    return g, grad, ks, js, ss
+
+
 def rrg_newton_search(h, x_t, r_t, v_prev, tol=2.0 ** -19, max_iter=40, checkpoint=50, precision=FP64):
     """(kappa, flags, iterations) of the adjoint-driven Newton search."""
     x = _f64(x_t)
@@ -460,6 +475,9 @@ class Governor:
 
     def slack_gradient(self, x_t, v_prev, r_t, kappa, checkpoint=50, precision=FP64):
         return rrg_slack_gradient(self.h, x_t, v_prev, r_t, kappa, checkpoint, precision)
+
+    def slack_gradients(self, x_t, v_prev, r_t, kappas, checkpoint=50, precision=FP64):
+        return rrg_slack_gradients(self.h, x_t, v_prev, r_t, kappas, checkpoint, precision)
 
     def newton_search(self, x_t, r_t, v_prev, tol=2.0 ** -19, max_iter=40, checkpoint=50, precision=FP64):
         return rrg_newton_search(self.h, x_t, r_t, v_prev, tol, max_iter, checkpoint, precision)

@@ -72,7 +72,10 @@ def test_adjoint_late_argmin_matches_complex_step(R, orc, params, checkpoint):
 
 def test_adjoint_forward_pass_is_timed_as_a_rollout(R, orc, params):
     """With profiling on, a gradient's forward pass (all scenarios, full
-    horizon) is one timed rollout launch of the five the call makes."""
+    horizon) is one timed rollout launch of the seven the call makes on a
+    binary64 handle (candidate set-up 2, binary64 scenario fill 2, forward,
+    argmin, reverse); a binary32 gradient on a binary32 handle reads the
+    stored binary32 draw and skips the fill."""
     N, H = 256, 300
     x_t = orc.equilibrium(params, 100.0)
     with _gov(R, params, N, H) as g:
@@ -82,8 +85,13 @@ def test_adjoint_forward_pass_is_timed_as_a_rollout(R, orc, params):
         for prec in (R.FP32, R.FP64):
             g.slack_gradient(x_t, 100.0, 250.0, 0.1, 50, prec)
         st = g.stats()
-    assert st["launches"] == 10 and st["rollout_launches"] == 2
+    assert st["launches"] == 14 and st["rollout_launches"] == 2
     assert st["timed_rollouts"] == 2 and st["rollout_ms"] > 0
+    with _gov(R, params, N, H, precision=R.FP32_RECHECK) as g:
+        g.sample_scenarios(2, 0)
+        g.reset_stats()
+        g.slack_gradient(x_t, 100.0, 250.0, 0.1, 50, R.FP32)
+        assert g.stats()["launches"] == 5
 
 
 def test_adjoint_fp32_close_to_fp64(R, orc, params):
@@ -169,3 +177,48 @@ def test_newton_search_agrees_with_bisection(R, orc, params, case):
     assert fl == f_b
     assert abs(k_n - k_b) <= tol + 2.0 ** -19
     assert it <= 20
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_multi_kappa_gradients_equal_single_calls(R, orc, params, precision):
+    """rrg_slack_gradients at m kappas gives each kappa's single-call result
+    bit for bit (each kappa's forward lanes, argmin and reverse sweep are its
+    own), with the steady-state outcome of each."""
+    N, H = 96, 300
+    prec = R.FP64 if precision == "fp64" else R.FP32
+    x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.02, 1.01])
+    kappas = np.array([0.0, 0.05, 0.1, 0.3, 0.9])
+    with _gov(R, params, N, H, precision=R.FP32_RECHECK) as g:
+        g.sample_scenarios(4, 2)
+        gm, grm, km, jm, ss = g.slack_gradients(x_t, 100.0, 250.0, kappas, 7, prec)
+        for i, k in enumerate(kappas):
+            g1, gr1, k1, j1 = g.slack_gradient(x_t, 100.0, 250.0, k, 7, prec)
+            assert (gm[i], km[i], jm[i]) == (g1, k1, j1)
+            np.testing.assert_array_equal(grm[i], gr1)
+    assert np.all(ss == 1)
+    if prec == R.FP64:
+        d = orc.sample_disturbances(4, 2, N, H, inputs.DIST_AMP)
+        c = orc.cfg(H=H, N=N, early_exit=0)
+        for i in (1, 3):
+            go, ko, jo = orc.min_slack_argmin(params, c, x_t, orc.governed(100.0, 250.0, kappas[i]), d)
+            assert (km[i], jm[i]) == (ko, jo) and gm[i] == pytest.approx(go, rel=1e-10, abs=1e-12)
+
+
+def test_newton_search_full_size_workload(R, orc, params):
+    """4,096 scenarios x 1,000 steps, checkpoint 50, binary32 gradients: the
+    search lands within one bracket of the oracle's 20-iteration joint
+    bisection (own draw), with the bracket judged by the binary32 + binary64
+    recheck evaluation at the benchmark's band."""
+    w = inputs.WORKLOADS["adjoint"]
+    N, H, C = w["N"], w["H"], w["checkpoint"]
+    tol = 2.0 ** -19
+    x_t = orc.equilibrium(params, 100.0)
+    with _gov(R, params, N, H, precision=R.FP32_RECHECK, recheck_eps_rel=1e-6, max_candidates=32) as g:
+        g.sample_scenarios(3, 0)
+        k_n, fl, it = g.newton_search(x_t, 250.0, 100.0, tol=tol, max_iter=40, checkpoint=C, precision=R.FP32)
+    d = orc.sample_disturbances(3, 0, N, H, inputs.DIST_AMP)
+    k_b, f_b = orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, 100.0, 250.0, 20, d,
+                                nthreads=min(16, __import__("os").cpu_count() or 1))
+    assert fl == f_b
+    assert abs(k_n - k_b) <= tol + 2.0 ** -19
+    assert it <= 12
