@@ -64,9 +64,11 @@ PROBE_STEPS = 128
 # output, slack, running min and the finiteness accumulator of 6
 FLOPS_PER_STEP = 141
 # instructions a warp issues per trajectory step in the register-ring loop
-# (ncu, one warp): an issue-bound step reaches at most 141 / (2 x 124) of the
+# (ncu: instructions executed by the 65,536-scenario sweep's rollout launches
+# at 32,768 scenarios over their lane-steps / 32, parametric and nominal
+# model alike): an issue-bound step reaches at most 141 / (2 x 114) of the
 # derived FP32 peak, which counts every instruction as an FMA
-INSTR_PER_STEP = 124
+INSTR_PER_STEP = 114
 ISSUE_CEILING = FLOPS_PER_STEP / (2.0 * INSTR_PER_STEP)
 FP32_LANES_PER_SM = 128
 
@@ -101,14 +103,14 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
-TRAFFIC_PER_LAUNCH = (430592 + 24615936 + 34560 + 35072) / 4
+TRAFFIC_PER_LAUNCH = (433408 + 24648960 + 35584 + 35584) / 4
 TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "6e4d02064039bc79576c0f09c48108e3b687aa4f"),
-    ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "cc5eb334f99d59c13bbc8c27c2b9caded008436c"),
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "9de4b83aaf76b41a6535e655f2a8a3ac5a7ff877"),
+    ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "1ef24ed4a16f67f78ee586ee6229fd831974dc8e"),
     ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
-     "// Binary64 re-run of the trajectories", "208aa315d110bd29a90ab25d98f9e15fc17a6ba4"),
+     "// Binary64 re-run of the trajectories", "004171175f2499b048b7d9236c4002cb77b71680"),
     ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
-     "babf78733fa6871fdc4b8fb328a1cce64fc61742"),
+     "e14339bba280983049fb0c6adcc53a1d56f9258a"),
 )
 
 
@@ -125,28 +127,27 @@ def source_region(rel, begin, end):
 
 # The sweep's rollout launches (parametric model, register ring): DRAM bytes
 # per launch of one update's three k-section rounds at 32,768 scenarios (ncu,
-# one pass over the three launches of one update), and the
+# one pass over the three launches of the first timed update), and the
 # same per-launch figure scaled to 65,536 scenarios by the units processed
-# (the scenario array, which dominates the traffic, doubles).
-SWEEP_TRAFFIC_32K = (3602669056 + 3401216 + 2197011712 + 273152 + 7767449088 + 80128) / 3
+# (the scenario array, which dominates the traffic, doubles).  Each round
+# reads the array once per candidate that is still running (tile-major
+# order; the array does not fit in L2), up to 16 times the algorithmic bytes.
+SWEEP_TRAFFIC_32K = (3609574912 + 3337216 + 9606733568 + 94464 + 25251835904 + 451584) / 3
 SWEEP_TRAFFIC_64K = 2 * SWEEP_TRAFFIC_32K
 
 
-# DRAM bytes of one adjoint_forward_kernel<float> launch on the adjoint
-# workload (4,096 x 1,000, checkpoint 50; ncu --set full on one launch of
-# the bench's adjoint workload), valid while the
-# forward kernel, its launch, the model and the Launch struct are the ones
-# profiled
-ADJ_TRAFFIC_PER_LAUNCH = 98381824 + 3629824
+# DRAM bytes of one adjoint_forward_kernel<float, float> launch on the adjoint
+# workload (4,096 x 1,000, checkpoint 50; ncu --set full on one launch of the
+# bench's adjoint workload: the 49 MB binary32 disturbance array read once,
+# checkpoints and lane minima written), valid while the forward kernel, its
+# launch, the step and the Launch struct are the ones profiled
+ADJ_TRAFFIC_PER_LAUNCH = 49206784 + 3840000
 ADJ_TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_adjoint.cu",
-     "// Register slots of the forward pass's disturbance prefetch ring.",
-     "__global__ void adjoint_argmin_kernel", "79ed5e5d73ab060e06240b79c605ebcf937f0a6a"),
-    ("paper_2510_08288_gb300/csrc/rrg_adjoint.cu", "cudaError_t launch_adjoint(", "adjoint_argmin_kernel<<<",
-     "05ab892987d1e13fb56434169be7ff5b6f618c3b"),
-    ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "cc5eb334f99d59c13bbc8c27c2b9caded008436c"),
-    ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
-     "babf78733fa6871fdc4b8fb328a1cce64fc61742"),
+    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', '03f6ed3f12a4a64cac17959873b61107f4a29de8'),
+    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
+    ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
+    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '9de4b83aaf76b41a6535e655f2a8a3ac5a7ff877'),
+    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', 'e14339bba280983049fb0c6adcc53a1d56f9258a'),
 )
 
 
@@ -1183,11 +1184,11 @@ def run_adjoint(args):
                                   "kappa = 0.1; Newton search to 2^-19 vs 20-iteration bisection",
                       "timing": "median host time per synchronous call (x_t in from and the gradient out to "
                                 "host memory: value and e2e are the same measurement)",
-                      "l2": "scenarios (98 MB binary64) re-read by every call; no flush"},
+                      "l2": "scenarios (49 MB binary32) re-read by every call; no flush"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": frac_of(achieved, peak),
                         "traffic": measured_traffic(ADJ_TRAFFIC_SOURCES, ADJ_TRAFFIC_PER_LAUNCH),
-                        "algorithmic_bytes_per_launch": N * H * 3 * 8,
+                        "algorithmic_bytes_per_launch": N * H * 3 * 4,
                         "kernel": "adjoint_forward_kernel<float>", "avg_launch_ms": fwd_ms,
                         "launches": stp["timed_rollouts"],
                         "timing": "CUDA events around the forward pass of %d more binary32 gradients" % K,
