@@ -177,6 +177,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-spec", action="store_true", help="batch: skip the speculative-bisection leg")
     ap.add_argument("--scenarios", type=int, default=N_SCEN, help="smaller cases for profiling only")
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
@@ -954,6 +955,37 @@ def run_batch(args):
                                  % (W, ", ".join("H=%d, N=%d" % (b["H"][i], b["N"][i])
                                                  for i in np.argsort(-b["H"])[:2])))
     g.close()
+    # the speculative-bisection batch (Alg. 1's kappa per instance for every
+    # tree width): the library's autotuner picks the width (the candidate
+    # count) on the first update, then the same K updates are timed
+    spec = None
+    if not args.no_spec:
+        cfg_s = R.rrg_config_default(max_candidates=64, n_bisect=N_BISECT, search=R.SEARCH_SPEC_BISECT,
+                                     precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
+                                     recheck_eps_rel=RECHECK_EPS_REL)
+        gs = R.BatchGovernor(p, cfg_s, b["N"], b["H"], stream)
+        gs.set_variant(variant[0])
+        w_best, ws, wms = R.rrg_batch_autotune_width(gs.h, dx0, d(r), dv0, SEED, 0, 1)
+        sv, sk = torch.zeros_like(dv), torch.zeros_like(dk)
+        sf, sx = torch.zeros_like(df), torch.zeros_like(dxo)
+        R.rrg_batch_closed_loop_dev(gs.h, dx0, dv0, dr, W, SEED, 0, amp, True, sv, sk, sf, sx)
+        sevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for i in range(K):
+                flush.fill_(float(i))
+                sevs[i][0].record(stream)
+                R.rrg_batch_closed_loop_dev(gs.h, None, None, dr, 1, SEED, 0, amp, True, sv, sk, sf, sx)
+                sevs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ssecs = sum(a.elapsed_time(c) for a, c in sevs) / 1e3
+        gs.close()
+        spec = {"value": S * K / ssecs, "unit": "RG updates/s (instance updates)", "ms_per_step": 1e3 * ssecs / K,
+                "search": "speculative bisection, N_kappa = %d (Alg. 1's kappa per instance for every width)"
+                          % N_BISECT,
+                "width_chosen": int(w_best),
+                "autotune": {"widths": [int(x) for x in ws], "ms_per_update": [float(x) for x in wms]},
+                "kappa_mean": float(np.mean(sk.cpu().numpy().reshape(T, S)[W:W + K]))}
     peak, peak_src = fp32_peak(clk)
     out = {
         "metric": BATCH_METRIC, "value": S * K / secs, "unit": "RG updates/s (instance updates)", "n_gpus": 1,
@@ -978,6 +1010,7 @@ def run_batch(args):
         "no_admissible_fraction": float(np.mean(flags[W:W + K] & 1)),
         "kappa_mean": float(np.mean(kap[W:W + K])),
         "fp32_error": fp32_err,
+        "spec_bisect_autotuned_width": spec,
     }
     print(json.dumps(out), flush=True)
     return 0

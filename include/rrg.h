@@ -578,9 +578,10 @@ RRG_API int rrg_step_latency(rrg_handle h, double v, int steps, double *cycles_p
  * its scenarios exactly as rrg_sample_scenarios with seed + s (mod 2^64), and
  * its simulated plant disturbance as rrg_plant_step with seed + s.  Search:
  * RRG_SEARCH_GRID (Alg. 3) or RRG_SEARCH_KSECTION with max_candidates per
- * instance and round; precision RRG_FP32_RECHECK; no parametric uncertainty
- * (otherwise RRG_ENOTIMPL).  Each instance's result equals rrg_step's for
- * the same inputs and scenarios. */
+ * instance and round, or RRG_SEARCH_SPEC_BISECT (Alg. 1's result, trees of a
+ * tunable width, see rrg_batch_set_width; no pipelined probe); precision
+ * RRG_FP32_RECHECK; no parametric uncertainty (otherwise RRG_ENOTIMPL).  Each
+ * instance's result equals rrg_step's for the same inputs and scenarios. */
 #define RRG_BATCH_MAX_INSTANCES 1024
 #define RRG_BATCH_VARIANTS 8   /* rollout variants: lanes per tile {64, 128,
                                   256} x disturbance prefetch depth {8, 16},
@@ -629,6 +630,28 @@ RRG_API int rrg_batch_autotune(rrg_batch_handle h, const double *d_x, const doub
                        int *variant_out, double *ms_out);
 RRG_API int rrg_batch_set_variant(rrg_batch_handle h, int variant);
 RRG_API int rrg_batch_get_variant(rrg_batch_handle h, int *variant, int *tile_lanes, int *prefetch);
+/* Width of RRG_SEARCH_SPEC_BISECT batches: the tree nodes each instance
+ * evaluates per round, 1..max_candidates (default max_candidates).  Every
+ * instance's result is Alg. 1's for every width (the same tree and walk as
+ * rrg_bisect_plan / rrg_bisect_decide); the width sets the number of rounds
+ * (1 + ceil((n_bisect - d0) / d1) for trees of d0 levels from the kappa = 1
+ * root and d1 below it) against the work per round.  RRG_EINVAL for the grid
+ * searches, whose candidate count is their grid size.  set_width waits for
+ * the handle's stream; the cached closed-loop graph is rebuilt on its next
+ * use. */
+#define RRG_BATCH_MAX_WIDTHS 24
+RRG_API int rrg_batch_set_width(rrg_batch_handle h, int width);
+RRG_API int rrg_batch_get_width(rrg_batch_handle h, int *width);
+/* Autotuner of the width: times 1 + repeats whole updates (CUDA events on the
+ * handle's stream around sample and search) on the given inputs for each tree
+ * size 1, 2, 3, 4, 7, 8, 15, 16, ... up to max_candidates (at most
+ * RRG_BATCH_MAX_WIDTHS of them), keeps the fastest and returns it in
+ * *width_out; widths[] / ms_out[] (each may be NULL, room for
+ * RRG_BATCH_MAX_WIDTHS) receive the widths tried and their mean ms per
+ * update, *n_out how many.  Results do not depend on the width.  Synchronous. */
+RRG_API int rrg_batch_autotune_width(rrg_batch_handle h, const double *d_x, const double *d_r,
+                             const double *d_v_prev, uint64_t seed, uint64_t update_index, int repeats,
+                             int *width_out, int32_t *widths, double *ms_out, int *n_out);
 RRG_API int rrg_batch_set_profiling(rrg_batch_handle h, int on);
 RRG_API int rrg_batch_get_stats(rrg_batch_handle h, rrg_stats *out);
 RRG_API int rrg_batch_reset_stats(rrg_batch_handle h);

@@ -52,14 +52,17 @@ struct BState {
   double lx[3], lv;       // closed-loop state (plant state, last v), kept apart
                           // from single updates' inputs
   double lo, hi, kappa_opt;
+  double kappa;           // speculative bisection: the kappa Alg. 1 tests next
   double v_out;
   int32_t m, round, any, done, invalid, flags;
+  int32_t iter, pad2;     // speculative bisection: Alg. 1 iterations done
   int32_t cur, pad;                      // scenario pair of the current update
   unsigned long long seed_p[2], update_p[2];  // what each pair holds
 };
 
 struct BCfg {
   int S, M, n_rounds, search, ss_check, early_exit;
+  int n_bisect, width;  // speculative bisection: N_kappa, tree nodes per round (<= M)
   double dt, y_min, eps_ss, y_c, eps_abs;
   double amp[3];
 };
@@ -152,6 +155,89 @@ __device__ void build_tiles(const BLaunch& B, int tile) {
   }
 }
 
+// Speculative bisection per instance: the nodes of the next levels of
+// Alg. 1's bisection tree from the instance's state that fit in `width`
+// (breadth-first; node 2n follows "not admissible" at node n, 2n + 1
+// "admissible"; an admissible kappa = 1 ends the search, so it has no
+// admissible child), and the walk of Alg. 1's path through their outcomes.
+// The same tree and walk as the single-problem speculative bisection and
+// rrg_bisect_plan / rrg_bisect_decide, so every instance's kappa is Alg. 1's
+// whatever the width.
+__device__ int btree_size(bool one, int d) { return one ? (1 << (d - 1)) : ((1 << d) - 1); }
+
+__device__ int btree_depth(const BState& st, int width, int n_bisect) {
+  if (st.done || st.iter >= n_bisect || width < 1) return 0;
+  const bool one = st.kappa == 1.0;
+  int d = 1;
+  while (d < 11 && d + 1 <= n_bisect - st.iter && btree_size(one, d + 1) <= width) ++d;
+  return d;
+}
+
+// kappa of heap node `heap`: Alg. 1's bracket updates along the path the
+// node's bits spell out below the root (the instance's state).
+__device__ double btree_kappa(const BState& st, uint32_t heap) {
+  double lo = st.lo, hi = st.hi, k = st.kappa;
+  for (int b = 30 - __clz(heap); b >= 0; --b) {
+    if ((heap >> b) & 1u) lo = k; else hi = k;
+    k = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+  }
+  return k;
+}
+
+// Writes the round's kappas into kap[0..m), breadth-first, and returns m
+// (<= width <= M).  Below a kappa = 1 root only node 2's subtree exists:
+// level l >= 1 holds heap nodes 2^l .. 2^l + 2^(l-1) - 1.
+__device__ int btree_plan(const BState& st, int width, int n_bisect, double* kap) {
+  const int d = btree_depth(st, width, n_bisect);
+  if (d == 0) return 0;
+  const bool one = st.kappa == 1.0;
+  int n = 0;
+  kap[n++] = st.kappa;
+  for (int l = 1; l < d; ++l) {
+    const uint32_t first = 1u << l, count = one ? (1u << (l - 1)) : (1u << l);
+    for (uint32_t q = 0; q < count; ++q) kap[n++] = btree_kappa(st, first + q);
+  }
+  return n;
+}
+
+// Alg. 1's walk through the outcomes ok[0..m) of the planned round.
+__device__ void btree_walk(BState& st, const int32_t* ok, int m, int n_bisect) {
+  // breadth-first position of each heap node of the round (nodes exist
+  // level by level; an admissible kappa = 1 root has no node 3)
+  const bool one = st.kappa == 1.0;
+  uint32_t heap = 1u;
+  int pos = 0;
+  for (;;) {
+    const bool adm = ok[pos] != 0;
+    st.iter += 1;
+    if (adm) {
+      st.kappa_opt = st.kappa;
+      st.any = 1;
+      if (st.kappa == 1.0) { st.done = 1; return; }
+      st.lo = st.kappa;
+    } else {
+      st.hi = st.kappa;
+    }
+    st.kappa = __dmul_rn(__dadd_rn(st.lo, st.hi), 0.5);
+    if (st.iter >= n_bisect) { st.done = 1; return; }
+    heap = 2u * heap + (adm ? 1u : 0u);
+    // position of `heap` in the breadth-first order of the round's tree
+    const int depth = 31 - __clz(heap);
+    int p;
+    if (!one) {
+      p = static_cast<int>(heap) - 1;
+    } else {
+      // below a kappa = 1 root only node 2's subtree exists: level l >= 1
+      // starts at 2^(l-1) and holds 2^(l-1) nodes (heap 2^l .. 2^l + 2^(l-1) - 1)
+      const uint32_t first = 1u << depth;
+      if (heap - first >= (1u << (depth - 1))) return;  // node 3's subtree: not in the round
+      p = (1 << (depth - 1)) + static_cast<int>(heap - first);
+    }
+    if (p >= m) return;  // past the round's levels
+    pos = p;
+  }
+}
+
 // Round 1: inputs (device arrays; NULL x / v_prev: the closed loop's state),
 // the scenario pair of update base + t, Alg. 3's grid, the tile list.  r is
 // read at r[t * S + s] (t = the loop counter, 0 without one).
@@ -184,7 +270,13 @@ batch_begin_kernel(const BLaunch B, const double* __restrict__ d_x, const double
     st.round = 0;
     st.flags = 0;
     st.done = ok ? 0 : 1;
-    st.m = ok ? grid_points(B.cand_kappa + static_cast<size_t>(s) * B.c.M, B.c.M) : 0;
+    st.kappa = 1.0;
+    st.iter = 0;
+    double* kap = B.cand_kappa + static_cast<size_t>(s) * B.c.M;
+    if (B.c.search == RRG_SEARCH_SPEC_BISECT)
+      st.m = ok ? btree_plan(st, B.c.width, B.c.n_bisect, kap) : 0;
+    else
+      st.m = ok ? grid_points(kap, B.c.M) : 0;
   }
   __syncthreads();
   build_tiles(B, tile);
@@ -399,7 +491,11 @@ batch_decide_kernel(const BLaunch B, int final, int tile, double* __restrict__ v
       for (int i = 0; i < m; ++i)
         if (ok[i]) best = i;
       int next = 0;
-      if (B.c.search == RRG_SEARCH_GRID) {
+      if (B.c.search == RRG_SEARCH_SPEC_BISECT) {
+        btree_walk(st, ok, m, B.c.n_bisect);
+        if (!st.done) next = btree_plan(st, B.c.width, B.c.n_bisect, kap);
+        if (next == 0) st.done = 1;
+      } else if (B.c.search == RRG_SEARCH_GRID) {
         if (best >= 0) { st.kappa_opt = kap[best]; st.any = 1; }
         st.done = 1;
       } else if (st.round == 0 && (best < 0 || best == m - 1)) {
@@ -555,7 +651,7 @@ struct rrg_batch_ctx {
   cudaGraphExec_t cl_exec = nullptr;
   const void* cl_key[5] = {};
   uint64_t cl_key_seed = 0, cl_key_t0 = 0;
-  int cl_key_variant = -1;
+  int cl_key_variant = -1, cl_key_width = -1;
   uint64_t cl_per = 0, cl_rl_per = 0;
   // counters and profiling
   uint64_t launches = 0, rollout_launches = 0, rounds = 0;
@@ -641,6 +737,21 @@ void bcollect(rrg_batch_ctx* h) {
   h->ev_roll.clear();
 }
 
+// Rounds of one update's search: 1 for Alg. 3, n_rounds for the k-section;
+// for the speculative bisection enough trees of the current width to finish
+// Alg. 1's n_bisect iterations from kappa = 1 (instances that finish sooner
+// skip the rest: their rounds have no tiles).
+int batch_rounds(const rrg_batch_ctx* h) {
+  const BCfg& c = h->B.c;
+  if (c.search == RRG_SEARCH_GRID) return 1;
+  if (c.search != RRG_SEARCH_SPEC_BISECT) return c.n_rounds;
+  int d0 = 1, d1 = 1;
+  while (d0 + 1 <= c.n_bisect && (1 << d0) <= c.width) ++d0;            // 2^(d-1) nodes from the root
+  while (d1 + 1 <= c.n_bisect && (1 << (d1 + 1)) - 1 <= c.width) ++d1;  // 2^d - 1 nodes below it
+  const int rest = c.n_bisect - d0;
+  return 1 + (rest > 0 ? (rest + d1 - 1) / d1 : 0);
+}
+
 int enqueue_rollout(rrg_batch_ctx* h) {
   const Variant& v = kVariants[h->variant];
   const bool timed = h->profiling && !h->capturing;
@@ -684,7 +795,7 @@ int enqueue_search_all(rrg_batch_ctx* h, const double* d_x, const double* d_r, c
   batch_begin_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, d_x, d_r, d_vp, base, tile);
   BCK(cudaGetLastError());
   h->launches++;
-  const int rounds = B.c.search == RRG_SEARCH_GRID ? 1 : B.c.n_rounds;
+  const int rounds = batch_rounds(h);
   const int prep_blocks = (S * B.c.M + 127) / 128;
   for (int r = 0; r < rounds; ++r) {
     batch_prepare_kernel<<<prep_blocks, 128, 0, h->stream>>>(B);
@@ -727,8 +838,12 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
     if (!std::isfinite(model_params[i])) return bset_err(h, RRG_EINVAL, "model_params[%d] not finite", i);
   int rc = check_config(cfg);
   if (rc != RRG_OK) return bset_err(h, rc, "%s", rrg_last_error(nullptr));
-  if (cfg->search != RRG_SEARCH_GRID && cfg->search != RRG_SEARCH_KSECTION)
-    return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_SEARCH_GRID or RRG_SEARCH_KSECTION");
+  if (cfg->search != RRG_SEARCH_GRID && cfg->search != RRG_SEARCH_KSECTION &&
+      cfg->search != RRG_SEARCH_SPEC_BISECT)
+    return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_SEARCH_GRID, RRG_SEARCH_KSECTION or "
+                    "RRG_SEARCH_SPEC_BISECT");
+  if (cfg->search == RRG_SEARCH_SPEC_BISECT && cfg->n_bisect > 62)
+    return bset_err(h, RRG_EINVAL, "n_bisect must be <= 62");
   if (cfg->precision != RRG_FP32_RECHECK)
     return bset_err(h, RRG_ENOTIMPL, "batched instances run RRG_FP32_RECHECK");
   if (cfg->param_unc_rel != 0.0 || cfg->scenarios_in_register != 0 || cfg->scenario_base != 0)
@@ -843,6 +958,8 @@ int rrg_batch_create(const double* model_params, int n_params, const rrg_config*
   B.c.M = M;
   B.c.n_rounds = cfg->n_rounds;
   B.c.search = cfg->search;
+  B.c.n_bisect = cfg->n_bisect;
+  B.c.width = M;
   B.c.ss_check = cfg->ss_check;
   B.c.early_exit = cfg->early_exit;
   B.c.dt = cfg->dt;
@@ -975,7 +1092,8 @@ int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double* d_x0, const doub
   }
   const void* key[5] = {d_r_seq, d_v_out, d_kappa_out, d_flags_out, d_x_out};
   const bool hit = h->cl_exec && std::memcmp(key, h->cl_key, sizeof key) == 0 &&
-                   h->cl_key_seed == seed && h->cl_key_t0 == t0 && h->cl_key_variant == h->variant;
+                   h->cl_key_seed == seed && h->cl_key_t0 == t0 && h->cl_key_variant == h->variant &&
+                   h->cl_key_width == h->B.c.width;
   if (!hit) {
     if (h->cl_exec) {
       cudaGraphExecDestroy(h->cl_exec);
@@ -1005,13 +1123,14 @@ int rrg_batch_closed_loop_dev(rrg_batch_handle h, const double* d_x0, const doub
     h->cl_key_seed = seed;
     h->cl_key_t0 = t0;
     h->cl_key_variant = h->variant;
+    h->cl_key_width = h->B.c.width;
   }
   for (int t = 0; t < T; ++t) {
     const cudaError_t ce = cudaGraphLaunch(h->cl_exec, h->stream);
     if (ce != cudaSuccess) return bset_err(h, RRG_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
     h->launches += h->cl_per;
     h->rollout_launches += h->cl_rl_per;
-    h->rounds += h->cfg.search == RRG_SEARCH_GRID ? 1 : h->cfg.n_rounds;
+    h->rounds += batch_rounds(h);
   }
   return RRG_OK;
 }
@@ -1029,6 +1148,85 @@ int rrg_batch_get_variant(rrg_batch_handle h, int* variant, int* tile_lanes, int
   if (variant) *variant = h->variant;
   if (tile_lanes) *tile_lanes = kVariants[h->variant].tile;
   if (prefetch) *prefetch = kVariants[h->variant].pf;
+  return RRG_OK;
+}
+
+int rrg_batch_set_width(rrg_batch_handle h, int width) {
+  if (!h) return RRG_EINVAL;
+  if (h->cfg.search != RRG_SEARCH_SPEC_BISECT)
+    return bset_err(h, RRG_EINVAL, "the width is a parameter of RRG_SEARCH_SPEC_BISECT only (for the grid "
+                    "searches it is the grid size, fixed at creation)");
+  if (width < 1 || width > h->B.c.M) return bset_err(h, RRG_EINVAL, "width must be in [1, max_candidates]");
+  BDeviceGuard g(h->device);
+  BCK(cudaStreamSynchronize(h->stream));
+  h->B.c.width = width;
+  return RRG_OK;
+}
+
+int rrg_batch_get_width(rrg_batch_handle h, int* width) {
+  if (!h || !width) return RRG_EINVAL;
+  *width = h->B.c.width;
+  return RRG_OK;
+}
+
+int rrg_batch_autotune_width(rrg_batch_handle h, const double* d_x, const double* d_r,
+                             const double* d_v_prev, uint64_t seed, uint64_t update_index, int repeats,
+                             int* width_out, int32_t* widths, double* ms_out, int* n_out) {
+  if (!h) return RRG_EINVAL;
+  if (h->cfg.search != RRG_SEARCH_SPEC_BISECT)
+    return bset_err(h, RRG_EINVAL, "the width is tuned for RRG_SEARCH_SPEC_BISECT only");
+  if (!d_x || !d_r || !d_v_prev || repeats < 1)
+    return bset_err(h, RRG_EINVAL, "d_x, d_r, d_v_prev non-NULL and repeats >= 1");
+  BDeviceGuard g(h->device);
+  h->B.t_dev = nullptr;
+  h->cl_next_ready = false;
+  BCK(cudaStreamSynchronize(h->stream));
+  bcollect(h);
+  // the tree sizes: 2^d - 1 and 2^(d-1) (from a kappa = 1 root) nodes
+  std::vector<int> cand;
+  for (int w = 1; w <= h->B.c.M; w *= 2) {
+    cand.push_back(w);
+    if (2 * w - 1 > w && 2 * w - 1 <= h->B.c.M) cand.push_back(2 * w - 1);
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  if (cand.size() > static_cast<size_t>(RRG_BATCH_MAX_WIDTHS)) cand.resize(RRG_BATCH_MAX_WIDTHS);
+  cudaEvent_t a = nullptr, b = nullptr;
+  BCK(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return bset_err(h, RRG_ECUDA, "event"); }
+  const int keep = h->B.c.width;
+  double best = 0.0;
+  int best_w = keep, rc = RRG_OK;
+  for (size_t q = 0; q < cand.size() && rc == RRG_OK; ++q) {
+    h->B.c.width = cand[q];
+    double total = 0.0;
+    for (int rep = 0; rep <= repeats && rc == RRG_OK; ++rep) {
+      if (cudaEventRecord(a, h->stream) != cudaSuccess) { rc = bset_err(h, RRG_ECUDA, "event record"); break; }
+      rc = enqueue_update(h, d_x, d_r, d_v_prev, seed, update_index, nullptr, nullptr, nullptr);
+      if (rc != RRG_OK) break;
+      if (cudaEventRecord(b, h->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+        rc = bset_err(h, RRG_ECUDA, "event wait");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0) total += ms;  // the first run warms up
+    }
+    const double mean = total / repeats;
+    if (widths) widths[q] = cand[q];
+    if (ms_out) ms_out[q] = mean;
+    if (q == 0 || mean < best) {
+      best = mean;
+      best_w = cand[q];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  bcollect(h);
+  h->B.c.width = rc == RRG_OK ? best_w : keep;
+  if (rc != RRG_OK) return rc;
+  if (width_out) *width_out = best_w;
+  if (n_out) *n_out = static_cast<int>(cand.size());
   return RRG_OK;
 }
 

@@ -120,6 +120,10 @@ def _load():
         "rrg_batch_closed_loop_dev": (ctypes.c_int, [_p, _p, _p, _p, ctypes.c_int, _u64, _u64, _p, ctypes.c_int,
                                                      _p, _p, _p, _p]),
         "rrg_batch_autotune": (ctypes.c_int, [_p, _p, _p, _p, _u64, _u64, ctypes.c_int, P(ctypes.c_int), _p]),
+        "rrg_batch_set_width": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_batch_get_width": (ctypes.c_int, [_p, P(ctypes.c_int)]),
+        "rrg_batch_autotune_width": (ctypes.c_int, [_p, _p, _p, _p, _u64, _u64, ctypes.c_int, P(ctypes.c_int), _p,
+                                                    _p, P(ctypes.c_int)]),
         "rrg_batch_set_variant": (ctypes.c_int, [_p, ctypes.c_int]),
         "rrg_batch_get_variant": (ctypes.c_int, [_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "rrg_batch_set_profiling": (ctypes.c_int, [_p, ctypes.c_int]),
@@ -510,6 +514,7 @@ def rrg_alu_peaks():
 
 # ---------------------------------------------------------------- batched --
 BATCH_VARIANTS = 8
+BATCH_MAX_WIDTHS = 24
 
 
 def rrg_batch_last_error(h=None) -> str:
@@ -560,6 +565,27 @@ def rrg_batch_autotune(h, d_x, d_r, d_v_prev, seed, update_index, repeats=2):
     _bcheck(lib.rrg_batch_autotune(h, _tensor_ptr(d_x), _tensor_ptr(d_r), _tensor_ptr(d_v_prev), int(seed),
                                    int(update_index), int(repeats), ctypes.byref(v), _ptr(ms)), h)
     return v.value, ms
+
+
+def rrg_batch_set_width(h, width):
+    _bcheck(lib.rrg_batch_set_width(h, int(width)), h)
+
+
+def rrg_batch_get_width(h):
+    w = ctypes.c_int(0)
+    _bcheck(lib.rrg_batch_get_width(h, ctypes.byref(w)), h)
+    return w.value
+
+
+def rrg_batch_autotune_width(h, d_x, d_r, d_v_prev, seed, update_index, repeats=2):
+    """(chosen width, widths tried, mean ms per update of each)."""
+    w, n = ctypes.c_int(0), ctypes.c_int(0)
+    ws = np.zeros(BATCH_MAX_WIDTHS, dtype=np.int32)
+    ms = np.zeros(BATCH_MAX_WIDTHS)
+    _bcheck(lib.rrg_batch_autotune_width(h, _tensor_ptr(d_x), _tensor_ptr(d_r), _tensor_ptr(d_v_prev), int(seed),
+                                         int(update_index), int(repeats), ctypes.byref(w), _ptr(ws), _ptr(ms),
+                                         ctypes.byref(n)), h)
+    return w.value, ws[:n.value].copy(), ms[:n.value].copy()
 
 
 def rrg_batch_set_variant(h, variant):
@@ -665,6 +691,17 @@ class BatchGovernor:
 
     def set_variant(self, v):
         rrg_batch_set_variant(self.h, v)
+
+    def set_width(self, w):
+        rrg_batch_set_width(self.h, w)
+
+    def get_width(self):
+        return rrg_batch_get_width(self.h)
+
+    def autotune_width(self, x, r, v_prev, seed, update_index, repeats=2):
+        dx, dr, dv = self._dev(np.asarray(x).reshape(-1)), self._dev(r), self._dev(v_prev)
+        self._sync()
+        return rrg_batch_autotune_width(self.h, dx, dr, dv, seed, update_index, repeats)
 
     def get_variant(self):
         return rrg_batch_get_variant(self.h)

@@ -210,3 +210,51 @@ def test_full_size_batch_update_matches_single_problems_and_oracle(R, orc, param
         d = orc.sample_disturbances(seed + s, upd, N, H, inputs.DIST_AMP)
         ko, fo = _oracle(orc, params, "ksection", x[s], b["v_prev"][s], b["r"][s], d, N, H, M)
         assert (k[s], f[s]) == (ko, fo), s
+
+
+# ----------------------------------------------- speculative bisection ----
+@pytest.mark.parametrize("width", [1, 2, 3, 8, 31, 64])
+def test_batch_spec_bisect_is_alg1_for_every_width(R, orc, params, width):
+    """RRG_SEARCH_SPEC_BISECT batches: every instance's kappa and flags equal
+    the oracle's joint bisection (Alg. 1, N_kappa = 12) on the instance's own
+    draw, whatever the tree width, with the binary32 + recheck rollouts at
+    the benchmark's band."""
+    S, seed, upd = 9, 7, 3
+    b, x = _problem(orc, params, S, 5, N_lo=1, N_hi=300, H_lo=1, H_hi=250)
+    cfg = _cfg(R, 64, R.SEARCH_SPEC_BISECT, n_bisect=12, recheck_eps_rel=1e-6)
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        g.set_width(width)
+        assert g.get_width() == width
+        v, k, f = g.step(x, b["r"], b["v_prev"], seed, upd)
+        st = g.stats()
+    for s in range(S):
+        N, H = int(b["N"][s]), int(b["H"][s])
+        d = orc.sample_disturbances(seed + s, upd, N, H, inputs.DIST_AMP)
+        k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x[s], b["v_prev"][s], b["r"][s], 12, d)
+        assert (k[s], f[s]) == (k_o, f_o), s
+        assert v[s] == b["v_prev"][s] + k_o * (b["r"][s] - b["v_prev"][s])
+    # rounds: enough trees of this width for 12 iterations from kappa = 1
+    d0 = max(dd for dd in range(1, 13) if 2 ** (dd - 1) <= width)
+    d1 = max(dd for dd in range(1, 13) if 2 ** dd - 1 <= width)
+    assert st["rounds"] == 1 + -(-(12 - min(d0, 12)) // d1)
+
+
+def test_batch_width_autotune_keeps_every_result(R, orc, params):
+    """The width autotuner times whole updates for each tree size and keeps
+    the fastest; every instance's kappa is the same at every width."""
+    S = 6
+    b, x = _problem(orc, params, S, 9, N_lo=64, N_hi=512, H_lo=100, H_hi=400)
+    cfg = _cfg(R, 32, R.SEARCH_SPEC_BISECT, n_bisect=12, recheck_eps_rel=1e-6)
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        _, k_ref, f_ref = g.step(x, b["r"], b["v_prev"], 4, 0)
+        w, ws, ms = g.autotune_width(x, b["r"], b["v_prev"], 4, 0, repeats=1)
+        assert w in ws and np.all(ms > 0) and list(ws) == sorted(ws) and ws[0] == 1 and ws[-1] == 32
+        assert g.get_width() == w
+        for width in (1, 7, 32):
+            g.set_width(width)
+            _, k, f = g.step(x, b["r"], b["v_prev"], 4, 0)
+            np.testing.assert_array_equal(k, k_ref)
+            np.testing.assert_array_equal(f, f_ref)
+    with R.BatchGovernor(params, _cfg(R, 8, R.SEARCH_KSECTION), b["N"], b["H"]) as g:
+        with pytest.raises(R.RrgError):
+            g.set_width(4)
