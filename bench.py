@@ -103,14 +103,14 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
-TRAFFIC_PER_LAUNCH = (433408 + 24648960 + 35584 + 35584) / 4
+TRAFFIC_PER_LAUNCH = (433408 + 24614656 + 35328 + 35328) / 4
 TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "9de4b83aaf76b41a6535e655f2a8a3ac5a7ff877"),
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "a253b18870262175390aa12d856e6f9d7944a5ad"),
     ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "1ef24ed4a16f67f78ee586ee6229fd831974dc8e"),
     ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
-     "// Binary64 re-run of the trajectories", "004171175f2499b048b7d9236c4002cb77b71680"),
+     "// Binary64 re-run of the trajectories", "f36d3f510e79581f7b795bd2c97642472e368c63"),
     ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
-     "e14339bba280983049fb0c6adcc53a1d56f9258a"),
+     "620fdebcc8f93db38dd95e832d5fa2703a5d7ba7"),
 )
 
 
@@ -125,29 +125,28 @@ def source_region(rel, begin, end):
     return text[i:text.index(end, i) + len(end)]
 
 
-# The sweep's rollout launches (parametric model, register ring): DRAM bytes
-# per launch of one update's three k-section rounds at 32,768 scenarios (ncu,
-# one pass over the three launches of the first timed update), and the
-# same per-launch figure scaled to 65,536 scenarios by the units processed
-# (the scenario array, which dominates the traffic, doubles).  Each round
-# reads the array once per candidate that is still running (tile-major
-# order; the array does not fit in L2), up to 16 times the algorithmic bytes.
-SWEEP_TRAFFIC_32K = (3609574912 + 3337216 + 9606733568 + 94464 + 25251835904 + 451584) / 3
-SWEEP_TRAFFIC_64K = 2 * SWEEP_TRAFFIC_32K
+# The sweep's rollout launches at 65,536 scenarios (parametric model, two
+# candidates per thread): DRAM bytes per launch of one update's three
+# k-section rounds (ncu, one pass over the three launches of the first timed
+# update).  Each round reads the array once per candidate pair that is still
+# running (tile-major order; the 3.9 GB array does not fit in L2), up to 8
+# times the algorithmic bytes.
+SWEEP_TRAFFIC_64K = (3964652800 + 3377408 + 11857334784 + 501248 + 27630950400 + 606720) / 3
 
 
 # DRAM bytes of one adjoint_forward_kernel<float, float> launch on the adjoint
-# workload (4,096 x 1,000, checkpoint 50; ncu --set full on one launch of the
-# bench's adjoint workload: the 49 MB binary32 disturbance array read once,
-# checkpoints and lane minima written), valid while the forward kernel, its
-# launch, the step and the Launch struct are the ones profiled
-ADJ_TRAFFIC_PER_LAUNCH = 49206784 + 3840000
+# workload (4,096 x 1,000, checkpoint 50; ncu, one pass over one launch of the
+# bench's adjoint workload: the 49 MB binary32 disturbance array read once;
+# the 3.8 MB of checkpoints and lane minima stay in L2 during the launch),
+# valid while the forward kernel, its launch, the step and the Launch struct
+# are the ones profiled
+ADJ_TRAFFIC_PER_LAUNCH = 49208064 + 2304
 ADJ_TRAFFIC_SOURCES = (
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', '03f6ed3f12a4a64cac17959873b61107f4a29de8'),
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
     ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
-    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '9de4b83aaf76b41a6535e655f2a8a3ac5a7ff877'),
-    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', 'e14339bba280983049fb0c6adcc53a1d56f9258a'),
+    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, 'a253b18870262175390aa12d856e6f9d7944a5ad'),
+    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', '620fdebcc8f93db38dd95e832d5fa2703a5d7ba7'),
 )
 
 
@@ -178,6 +177,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-spec", action="store_true", help="batch: skip the speculative-bisection leg")
+    ap.add_argument("--pairing", choices=("never", "filled", "always", "autotune"), default="filled",
+                    help="sweep: candidates per thread of the rollouts (rrg_set_pairing); autotune times "
+                         "every mode on the first warm-up update and keeps the fastest")
     ap.add_argument("--scenarios", type=int, default=N_SCEN, help="smaller cases for profiling only")
     ap.add_argument("--horizon", type=int, default=HORIZON, help="smaller cases for profiling only")
     ap.add_argument("--probe-steps", type=int, default=PROBE_STEPS,
@@ -1268,6 +1270,7 @@ def adjoint_cpu(p, x_t, v_prev, r, N, H, seconds, gpu_argmin):
 
 # ------------------------------------------------------------------ sweep --
 SWEEP_METRIC = "trajectory-steps/s vs scenario count (large sweep, FP32 + FP64 recheck)"
+PAIRING_NAMES = ("never", "filled", "always")
 
 
 def sweep_config(ns, W, K):
@@ -1346,6 +1349,13 @@ def run_sweep(args):
                                    param_unc_rel=rho, param_unc_mask=inputs.FC3_UNCERTAIN_MASK)
         g = R.Governor(p, cfg, stream)
         x_t, _ = g.equilibrium(v_prev)
+        pairing_ms = None
+        if args.pairing == "autotune":
+            g.sample_scenarios(SEED, 0)
+            _, ms_modes = g.autotune_pairing(x_t, r, v_prev, repeats=3)
+            pairing_ms = dict(zip(PAIRING_NAMES, ms_modes))
+        else:
+            g.set_pairing(PAIRING_NAMES.index(args.pairing))
         d_x = torch.tensor(x_t, dtype=torch.float64, device=dev)
         d_r = torch.tensor([r], dtype=torch.float64, device=dev)
         d_vp = torch.tensor([v_prev], dtype=torch.float64, device=dev)
@@ -1425,6 +1435,8 @@ def run_sweep(args):
                      "executed_trajectory_steps_per_update": st["lane_steps"] / K,
                      "rollout_tflops": achieved,
                      "rollout_avg_launch_ms": avg_roll_ms, "rechecked": st["rechecked"],
+                     "pairing": PAIRING_NAMES[g.get_pairing()], "pairing_autotune_ms": pairing_ms,
+                     "paired_step_fraction": st["lane_steps_paired"] / max(1, st["lane_steps"]),
                      "gpu_launches": st["launches"], "kappa": [float(x) for x in kap],
                      "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64,
                      "scenarios_in_register": gen_leg})
@@ -1448,14 +1460,19 @@ def run_sweep(args):
         "metric": SWEEP_METRIC, "value": top["trajectory_steps_per_s"], "unit": "trajectory-steps/s",
         "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": top["ms_per_update"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(sweep_config(ns, W, K), param_unc_rel=rho),
+        "config": dict(sweep_config(ns, W, K), param_unc_rel=rho,
+                       pairing="%s (two candidates per thread where the paired grid fills the SMs 6 times "
+                               "over)" % args.pairing if args.pairing == "filled" else args.pairing),
         "roofline": {"bound": "alu", "achieved": top["rollout_tflops"], "peak": peak,
                      "unit": "TFLOP/s", "frac": top["rollout_frac"],
                      "traffic": (SWEEP_TRAFFIC_64K if top["n_scenarios"] == 65536 and rho == inputs.PARAM_UNC_REL
-                                 and measured_traffic() is not None else None),
-                     "traffic_basis": "ncu DRAM bytes per rollout launch at 32,768 scenarios (one update's "
-                                      "3 rounds), scaled x2 to 65,536 by the units processed",
-                     "kernel": "rollout_kernel<float, parametric>", "n_scenarios": top["n_scenarios"],
+                                 and top["paired_step_fraction"] > 0.5 and measured_traffic() is not None
+                                 else None),
+                     "traffic_basis": "ncu DRAM bytes per rollout launch at 65,536 scenarios (one update's "
+                                      "3 rounds, two candidates per thread)",
+                     "kernel": ("rollout_pair_kernel<parametric> (two candidates per thread)"
+                                if top["paired_step_fraction"] > 0.5 else "rollout_kernel<float, parametric>"),
+                     "n_scenarios": top["n_scenarios"],
                      "peak_source": peak_src,
                      "issue_ceiling": ISSUE_CEILING,
                      "frac_of_issue_ceiling": frac_of(top["rollout_frac"], ISSUE_CEILING)},

@@ -189,6 +189,8 @@ typedef struct {
     uint64_t graph_conditional; /* 1: the cached closed-loop graph holds the
                                    rounds after a pipelined pair in a
                                    conditional node (run only when needed)    */
+    uint64_t lane_steps_paired; /* of lane_steps, those run two trajectories
+                                   per thread (rrg_set_pairing)               */
 } rrg_stats;
 
 /* Fills *cfg with the defaults of the paper's fuel-cell experiment: dt 0.01,
@@ -371,6 +373,35 @@ RRG_API int rrg_get_tuning(rrg_handle h, int32_t *m, int32_t *probe_steps);
  * NULL).  Synchronous; the cached closed-loop graph is discarded. */
 RRG_API int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_prev, int repeats,
                  int32_t *m_out, int32_t *probe_out, double *ms_out);
+
+/* Trajectories per thread of the binary32 rollouts that read the stored
+ * scenario array (RRG_FP32, RRG_FP32_RECHECK; scenarios_in_register = 0):
+ * RRG_PAIR_NEVER, one trajectory per thread; RRG_PAIR_FILLED, two candidates
+ * of one scenario per thread (one load of each disturbance, two independent
+ * step chains) in rollout launches large enough that the paired grid fills
+ * the SMs at least six times over, one elsewhere;
+ * RRG_PAIR_ALWAYS, two in every launch whose rows are full-horizon segments
+ * (the probe and continuation launches of a pipelined search never pair).
+ * The same arithmetic in every mode: every admissible flag, every search
+ * result and the min slack of every admissible candidate are identical; only
+ * the time changes.  Both calls wait for the handle's stream; setting the mode
+ * discards the cached closed-loop graph.  RRG_EINVAL for a null handle or
+ * pointer or a mode outside 0..2.  New handles start at RRG_PAIR_FILLED. */
+#define RRG_PAIR_NEVER 0
+#define RRG_PAIR_FILLED 1
+#define RRG_PAIR_ALWAYS 2
+RRG_API int rrg_set_pairing(rrg_handle h, int mode);
+RRG_API int rrg_get_pairing(rrg_handle h, int32_t *mode);
+
+/* Times 1 + repeats updates of the handle's search (rrg_autotune's
+ * protocol: current scenarios, host inputs x_t[3], r_t, v_prev, CUDA events
+ * on the handle's stream) in each pairing mode, keeps the fastest and returns
+ * it in *mode_out and the mean device time per update of each mode in
+ * ms_out[3] (each may be NULL).  Synchronous; the cached closed-loop graph is
+ * discarded.  RRG_EINVAL for invalid inputs, RRG_ECUDA if an update fails
+ * (the mode is then left unchanged). */
+RRG_API int rrg_autotune_pairing(rrg_handle h, const double *x_t, double r_t, double v_prev, int repeats,
+                         int32_t *mode_out, double *ms_out);
 
 /* Gradient of the robust objective g(kappa) = min over scenarios k and steps
  * j = 0..H of s_j^k = h(x_j^k, v) - y_min on the current scenarios, with

@@ -26,6 +26,7 @@ struct rrg_ctx {
   rrg_config cfg{};
   double params[RRG_NPARAM]{};
   SearchCfg scfg{};
+  int pair = RRG_PAIR_FILLED;   // trajectories per thread of the binary32 rollouts (rrg_set_pairing)
   Launch L{};
   // device memory
   double* params_dev = nullptr;
@@ -201,6 +202,7 @@ void fill_launch(rrg_ctx* h) {
   Launch& L = h->L;
   const rrg_config& c = h->cfg;
   L.stream = h->stream;
+  L.pair = h->pair;
   L.N = c.n_scenarios;
   L.H = c.horizon;
   L.precision = c.precision;
@@ -255,13 +257,16 @@ cudaEvent_t take_event(rrg_ctx* h) {
 
 // Rollout of the current round (+ recheck in FP32_RECHECK mode unless the
 // launch is a probe, whose lanes are not decided yet).
-int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit, bool recheck = true) {
+// allow_pair = false for the two launches of a pipelined pair (probe and
+// continuation segments), whose rows cannot share a thread.
+int enqueue_round_work(rrg_ctx* h, const Launch& L, int width, int early_exit, bool recheck = true,
+                       bool allow_pair = true) {
   const bool timed = h->profiling && !h->capturing;
   cudaEvent_t a = nullptr, b = nullptr;
   if (timed) { a = take_event(h); b = take_event(h); }
   if (a && b) CK(cudaEventRecord(a, h->stream));
   const bool fp64 = h->cfg.precision == RRG_FP64;
-  CK(launch_rollout(L, width, fp64, early_exit, h->cfg.precision == RRG_FP32_RECHECK));
+  CK(launch_rollout(L, width, fp64, early_exit, h->cfg.precision == RRG_FP32_RECHECK, allow_pair));
   if (a && b) {
     CK(cudaEventRecord(b, h->stream));
     h->ev_roll.emplace_back(a, b);
@@ -322,12 +327,12 @@ int enqueue_search(rrg_ctx* h, const double* d_x, const double* d_r,
     // probe of round 1, then round 1's remainder together with round 2; the
     // rounds after it only do work when the validation found a wrong guess
     const int w0 = search_round_width(c, 0), w1 = search_round_width(c, 1);
-    int rc = enqueue_round_work(h, L, w0, h->cfg.early_exit, false);
+    int rc = enqueue_round_work(h, L, w0, h->cfg.early_exit, false, false);
     if (rc != RRG_OK) return rc;
     CK(launch_search_mid(L));
     h->launches++;
     // rows: the <= 11 path nodes of round 1 that continue, then round 2
-    rc = enqueue_round_work(h, L, (w0 < 11 ? w0 : 11) + w1, h->cfg.early_exit);
+    rc = enqueue_round_work(h, L, (w0 < 11 ? w0 : 11) + w1, h->cfg.early_exit, true, false);
     if (rc != RRG_OK) return rc;
     CK(launch_search_next(L, d_vt, d_kappa, d_flags));
     h->launches++;
@@ -688,6 +693,9 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   s.eps_ss = c.eps_ss;
   s.y_c = c.y_c;
   fill_launch(h);
+  // occupancy of the paired kernel, queried once here (never inside a capture)
+  (void)pair_blocks_per_sm(false);
+  (void)pair_blocks_per_sm(true);
   *out = h;
   return RRG_OK;
 }
@@ -1427,6 +1435,79 @@ int rrg_autotune(rrg_handle h, const double* x_t, double r_t, double v_prev, int
   return RRG_OK;
 }
 
+int rrg_set_pairing(rrg_handle h, int mode) {
+  if (!h) return RRG_EINVAL;
+  if (mode < RRG_PAIR_NEVER || mode > RRG_PAIR_ALWAYS)
+    return set_err(h, RRG_EINVAL, "pairing mode must be RRG_PAIR_NEVER, RRG_PAIR_FILLED or RRG_PAIR_ALWAYS");
+  DeviceGuard g(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  h->pair = mode;
+  fill_launch(h);
+  if (h->cl_exec) {  // the cached closed-loop graph holds the old kernels
+    cudaGraphExecDestroy(h->cl_exec);
+    h->cl_exec = nullptr;
+  }
+  return RRG_OK;
+}
+
+int rrg_get_pairing(rrg_handle h, int32_t* mode) {
+  if (!h || !mode) return RRG_EINVAL;
+  *mode = h->pair;
+  return RRG_OK;
+}
+
+int rrg_autotune_pairing(rrg_handle h, const double* x_t, double r_t, double v_prev, int repeats,
+                         int32_t* mode_out, double* ms_out) {
+  if (!h) return RRG_EINVAL;
+  if (!x_ok(x_t) || !is_fin(v_prev) || !is_fin(r_t) || !(v_prev > 0.0) || !(r_t > 0.0) || repeats < 1)
+    return set_err(h, RRG_EINVAL, "x_t, v_prev, r_t must be finite, v_prev, r_t > 0, repeats >= 1");
+  DeviceGuard g(h->device);
+  std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  h->io_h[IO_R] = r_t;
+  h->io_h[IO_V] = v_prev;
+  CK(cudaMemcpyAsync(h->io_dev, h->io_h, 5 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  cudaEvent_t a = take_event(h), b = take_event(h);
+  if (!a || !b) return set_err(h, RRG_ECUDA, "event creation failed");
+  const bool prof = h->profiling;
+  h->profiling = false;
+  const int old = h->pair;
+  int best_mode = old, rc = RRG_OK;
+  double best = 0.0;
+  for (int mode = RRG_PAIR_NEVER; mode <= RRG_PAIR_ALWAYS && rc == RRG_OK; ++mode) {
+    h->pair = mode;
+    fill_launch(h);
+    float total = 0.0f;
+    for (int rep = 0; rep <= repeats && rc == RRG_OK; ++rep) {
+      cudaEventRecord(a, h->stream);
+      rc = enqueue_search(h, h->io_dev + IO_X, h->io_dev + IO_R, nullptr, h->io_dev + IO_V,
+                          h->io_dev + IO_OUT, h->io_dev + IO_OUT + 1, h->flag_dev);
+      cudaEventRecord(b, h->stream);
+      if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = RRG_ECUDA;
+      float t = 0.0f;
+      if (rc == RRG_OK && rep > 0 && cudaEventElapsedTime(&t, a, b) == cudaSuccess) total += t;
+    }
+    if (rc != RRG_OK) break;
+    const double mean = total / repeats;
+    if (ms_out) ms_out[mode] = mean;
+    if (mode == RRG_PAIR_NEVER || mean < best) {
+      best = mean;
+      best_mode = mode;
+    }
+  }
+  h->ev_free.push_back(a);
+  h->ev_free.push_back(b);
+  h->profiling = prof;
+  h->pair = rc == RRG_OK ? best_mode : old;
+  fill_launch(h);
+  if (h->cl_exec) {
+    cudaGraphExecDestroy(h->cl_exec);
+    h->cl_exec = nullptr;
+  }
+  if (rc != RRG_OK) return set_err(h, RRG_ECUDA, "autotune: a timed update failed");
+  if (mode_out) *mode_out = best_mode;
+  return RRG_OK;
+}
+
 int rrg_set_profiling(rrg_handle h, int on) {
   if (!h) return RRG_EINVAL;
   h->profiling = on != 0;
@@ -1467,6 +1548,7 @@ int rrg_get_stats(rrg_handle h, rrg_stats* out) {
   out->timed_rollouts = h->timed_rollouts;
   out->repairs = ds.repairs;
   out->graph_conditional = h->cl_exec != nullptr && h->cl_conditional ? 1 : 0;
+  out->lane_steps_paired = ds.lane_steps_paired;
   return RRG_OK;
 }
 

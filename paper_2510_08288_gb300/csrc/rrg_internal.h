@@ -103,6 +103,7 @@ struct DevStats {
   // kernels, rollout launches and search rounds run by the conditional body
   // of a captured closed-loop update (counted by the kernel that opens it)
   unsigned long long cond_launches, cond_rollouts, cond_rounds;
+  unsigned long long lane_steps_paired;  // of lane_steps, run two trajectories per thread
 };
 
 // Closed-loop device state.
@@ -129,6 +130,8 @@ struct Launch {
   int N, H, precision, early_exit, m_cap;
   int scen_gen;                 // disturbances drawn inside the trajectory loop
   unsigned long long kbase;     // global index of the handle's scenario 0 (scenario sharding)
+  int pair;                     // RRG_PAIR_*: two candidates per thread in binary32 rollouts
+                                //   of full-horizon rows (never, launches that fill the SMs, always)
   // conditional-node handle of a captured closed-loop update (0: none); the
   // search kernel that validates the pipelined rounds sets it to "the search
   // is not finished", which runs the remaining rounds
@@ -362,8 +365,13 @@ cudaError_t launch_prepare(const Launch& L, int width);
 cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
                                 const double* d_kappas, int m);
 cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d_min_slack);
+// Resident blocks per SM of the two-candidates-per-thread rollout kernel
+// (queried from the runtime on the first call, then cached).
+int pair_blocks_per_sm(bool pu);
+// allow_pair: the round's rows are all full-horizon segments (no pipelined
+// probe), so two candidates may share a thread (Launch::pair).
 cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
-                           bool recheck_classify);
+                           bool recheck_classify, bool allow_pair = false);
 cudaError_t launch_recheck(const Launch& L, int early_exit);
 cudaError_t launch_equilibrium(const Launch& L, double v, double* d_out4, int32_t* d_status);
 cudaError_t launch_step_latency(const Launch& L, double v, int steps, double* d_out2, int32_t* d_status);

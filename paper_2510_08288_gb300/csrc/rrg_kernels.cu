@@ -264,6 +264,52 @@ enum RollSrc : int {
   SRC_GEN = 2    // drawn from Philox inside the trajectory loop (run_lane_gen)
 };
 
+// The lane's outcome for candidate slot i (called by every thread of the
+// warp): classified against the recheck band in the binary32 + recheck mode
+// (an undecided lane is listed for the binary64 recheck unless its candidate
+// has already failed), its P entry, then the warp's AND of the flags, min
+// slack and step count folded into the candidate's by one atomic each.
+template <typename T>
+__device__ __forceinline__ void reduce_lane(const Launch& L, int i, int k, int N, bool final_lane, T smin,
+                                            unsigned steps, int jlast, int classify, T eps,
+                                            volatile int32_t* dead) {
+  bool lane_ok = true, uncertain = false;
+  T contrib = inf_v<T>();
+  if (final_lane) {
+    if (classify) {
+      if (smin >= eps) {
+        contrib = smin;
+      } else if (smin < -eps) {
+        lane_ok = false;
+        contrib = smin;
+      } else {
+        uncertain = true;
+      }
+    } else {
+      lane_ok = smin >= T(0);
+      contrib = smin;
+    }
+  }
+  if (uncertain && *dead == 0) {
+    const uint32_t slot = atomicAdd(L.recheck_count, 1u);
+    L.recheck_list[slot] = static_cast<uint32_t>(i) * static_cast<uint32_t>(N) + static_cast<uint32_t>(k);
+    L.recheck_jlast[slot] = static_cast<uint32_t>(jlast);
+  }
+  if (L.P != nullptr && final_lane) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
+
+  const bool all_ok = __all_sync(0xffffffffu, lane_ok);
+  const T wmin = warp_min<T>(contrib);
+  const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
+  if ((threadIdx.x & 31) == 0) {
+    if (!all_ok) L.cand_ok[i] = 0;
+    if (wmin < inf_v<T>()) atomicMin(L.cand_min + i, dkey(static_cast<double>(wmin)));
+    if (wsteps) {
+      atomicAdd(&L.stats->lane_steps, static_cast<unsigned long long>(wsteps));
+      if (sizeof(T) == 8) atomicAdd(&L.stats->lane_steps_fp64, static_cast<unsigned long long>(wsteps));
+    }
+  }
+}
+
 template <typename T, bool PU, int SRC>
 __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
                                              const T* __restrict__ d_pair0,
@@ -368,41 +414,7 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
       }
     }
   }
-  bool lane_ok = true, uncertain = false;
-  T contrib = inf_v<T>();
-  if (final_lane) {
-    if (classify) {
-      if (smin >= eps) {
-        contrib = smin;
-      } else if (smin < -eps) {
-        lane_ok = false;
-        contrib = smin;
-      } else {
-        uncertain = true;
-      }
-    } else {
-      lane_ok = smin >= T(0);
-      contrib = smin;
-    }
-  }
-  if (uncertain && *dead == 0) {
-    const uint32_t slot = atomicAdd(L.recheck_count, 1u);
-    L.recheck_list[slot] = static_cast<uint32_t>(i) * static_cast<uint32_t>(N) + static_cast<uint32_t>(k);
-    L.recheck_jlast[slot] = static_cast<uint32_t>(jlast);
-  }
-  if (L.P != nullptr && final_lane) L.P[static_cast<size_t>(i) * N + k] = lane_ok ? 1 : 0;
-
-  const bool all_ok = __all_sync(0xffffffffu, lane_ok);
-  const T wmin = warp_min<T>(contrib);
-  const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
-  if ((threadIdx.x & 31) == 0) {
-    if (!all_ok) L.cand_ok[i] = 0;
-    if (wmin < inf_v<T>()) atomicMin(L.cand_min + i, dkey(static_cast<double>(wmin)));
-    if (wsteps) {
-      atomicAdd(&L.stats->lane_steps, static_cast<unsigned long long>(wsteps));
-      if (sizeof(T) == 8) atomicAdd(&L.stats->lane_steps_fp64, static_cast<unsigned long long>(wsteps));
-    }
-  }
+  reduce_lane<T>(L, i, k, N, final_lane, smin, steps, jlast, classify, eps, dead);
 }
 
 // SRC: where the lanes take their disturbances from (RollSrc).
@@ -430,8 +442,121 @@ rollout_pu_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0
   rollout_body<T, true, SRC>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
 }
 
+// Two candidates per thread (binary32, register ring): block row y runs the
+// launch's rows 2y and 2y + 1 (the slots of the round's full-horizon
+// segments; rounds with a pipelined probe are never paired) for the same
+// scenarios, through run_lane_pair; a row whose candidate failed the
+// steady-state check, or has already been stopped, leaves its partner to run
+// alone.  Each candidate's lanes are reduced exactly as in rollout_body.
+#ifndef RRG_PAIR_PU_MIN_BLOCKS
+#define RRG_PAIR_PU_MIN_BLOCKS 2
+#endif
+#ifndef RRG_PAIR_MIN_BLOCKS
+#define RRG_PAIR_MIN_BLOCKS 1
+#endif
+// Prefetch depth (and exit block) of a paired thread: each step issues two
+// trajectories' instructions, so half the single lane's depth covers the same
+// load latency with half the unrolled code.
+#ifndef RRG_PAIR_PF
+#define RRG_PAIR_PF 8
+#endif
+template <bool PU>
+__global__ void __launch_bounds__(kRollThreads, PU ? RRG_PAIR_PU_MIN_BLOCKS : RRG_PAIR_MIN_BLOCKS)
+rollout_pair_kernel(const Launch L, const RhsU<float> K0, const float* __restrict__ d_pair0,
+                    const float* __restrict__ d_pair1, const RhsC<float>* __restrict__ cand, int early_exit,
+                    int classify) {
+  const float* __restrict__ d = L.st->buf ? d_pair1 : d_pair0;
+  const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
+  const int rows = s0.count + s1.count;
+  const int ya = 2 * static_cast<int>(blockIdx.y), yb = ya + 1;
+  if (ya >= rows) return;
+  const int ia = ya < s0.count ? s0.base + ya : s1.base + (ya - s0.count);
+  const int ib = yb >= rows ? -1 : (yb < s0.count ? s0.base + yb : s1.base + (yb - s0.count));
+  const int N = L.N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = k < N;
+  const bool ssa = L.cand_ss[ia] != 0, ssb = ib >= 0 && L.cand_ss[ib] != 0;
+  if (!ssa && L.P != nullptr && active) L.P[static_cast<size_t>(ia) * N + k] = 0;
+  if (ib >= 0 && !ssb && L.P != nullptr && active) L.P[static_cast<size_t>(ib) * N + k] = 0;
+  const bool cand_stop = early_exit == RRG_EXIT_CANDIDATE;
+  volatile int32_t* deada = L.cand_dead + ia;
+  volatile int32_t* deadb = L.cand_dead + (ib >= 0 ? ib : ia);
+  // which candidates this warp runs (uniform: the flags are read by lane 0)
+  bool runa = ssa, runb = ssb;
+  if (cand_stop) {
+    const int da = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 && runa ? *deada : 0, 0);
+    const int db = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 && runb ? *deadb : 0, 0);
+    runa = runa && !da;
+    runb = runb && !db;
+  }
+  if (!runa && !runb) return;
+  const float eps = static_cast<float>(L.eps_abs);
+  const float thr = early_exit != RRG_EXIT_NONE ? (classify ? -eps : 0.0f) : -inf_v<float>();
+  const float band = classify ? eps : -inf_v<float>();
+  float sm[2] = {inf_v<float>(), inf_v<float>()};
+  unsigned st[2] = {0u, 0u};
+  int jl[2] = {-1, -1}, en[2] = {LANE_REACHED_END, LANE_REACHED_END};
+  unsigned paired = 0;  // trajectory steps this lane ran two per thread
+  if (active) {
+    RhsU<float> K = K0;
+    RhsC<float> CA = cand[ia], CB = cand[ib >= 0 ? ib : ia];
+    double p_atm = L.params[P_P_ATM];
+    if constexpr (PU) {
+      const double* mk = (L.st->buf ? L.pmulb : L.pmul) + static_cast<size_t>(k) * RRG_NPARAM;
+      if (runa) p_atm = scenario_model<float>(L.params, mk, L.cand_v[ia], L.k64.pws, L.y_min, K, CA);
+      if (runb) p_atm = scenario_model<float>(L.params, mk, L.cand_v[ib], L.k64.pws, L.y_min, K, CB);
+    }
+    float za[4], zb[4];
+    start_state<float>(CA, L.st->x, p_atm, za[0], za[1], za[2], za[3]);
+    start_state<float>(CB, L.st->x, p_atm, zb[0], zb[1], zb[2], zb[3]);
+    const float dt = static_cast<float>(L.dt);
+    if (runa && runb) {
+      paired = 2u * static_cast<unsigned>(run_lane_pair<float, RRG_PAIR_PF>(
+                            K, CA, CB, d, k, N, L.H, L.H, za, zb, dt, thr, band, cand_stop ? deada : nullptr,
+                            cand_stop ? deadb : nullptr, sm, st, en, jl));
+    } else if (runa) {
+      sm[0] = run_lane<float, RRG_PAIR_PF>(K, CA, d, k, N, L.H, 0, L.H, za[0], za[1], za[2], za[3],
+                                           inf_v<float>(), dt, thr, cand_stop ? deada : nullptr, &st[0],
+                                           &en[0], band, &jl[0]);
+    } else {
+      sm[1] = run_lane<float, RRG_PAIR_PF>(K, CB, d, k, N, L.H, 0, L.H, zb[0], zb[1], zb[2], zb[3],
+                                           inf_v<float>(), dt, thr, cand_stop ? deadb : nullptr, &st[1],
+                                           &en[1], band, &jl[1]);
+    }
+    if (cand_stop && runa && sm[0] < thr) *deada = 1;
+    if (cand_stop && runb && sm[1] < thr) *deadb = 1;
+  }
+  if (runa) reduce_lane<float>(L, ia, k, N, active, sm[0], st[0], jl[0], classify, eps, deada);
+  if (runb) reduce_lane<float>(L, ib, k, N, active, sm[1], st[1], jl[1], classify, eps, deadb);
+  if (runa && runb) {
+    const unsigned wp = __reduce_add_sync(0xffffffffu, paired);
+    if ((threadIdx.x & 31) == 0 && wp) atomicAdd(&L.stats->lane_steps_paired, static_cast<unsigned long long>(wp));
+  }
+}
+
+// Resident blocks per SM of the paired kernel (its register count decides).
+int pair_blocks_per_sm(bool pu) {
+  static const int n[2] = {
+      [] { int b = 0; return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_pair_kernel<false>,
+                                                                           kRollThreads, 0) == cudaSuccess && b > 0 ? b : 1; }(),
+      [] { int b = 0; return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_pair_kernel<true>,
+                                                                           kRollThreads, 0) == cudaSuccess && b > 0 ? b : 1; }()};
+  return n[pu ? 1 : 0];
+}
+
+// RRG_PAIR_FILLED pairs a launch whose paired grid fills the SMs at least
+// this many times over: a paired block does twice a single block's work, so
+// a short grid ends in a long, half-empty last wave.  Measured on GB300
+// (k-section updates, 16 candidates x 5,000 steps): 65,536 scenarios (9
+// paired waves) 7.5 % faster with uncertain parameters, 3.6 % nominal;
+// 32,768 (4.5 waves) 1 % faster and 3 % slower; 8,192 (1.1 waves) 22 %
+// slower.
+#ifndef RRG_PAIR_MIN_WAVES
+#define RRG_PAIR_MIN_WAVES 6
+#endif
+
 cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
-                           bool recheck_classify) {
+                           bool recheck_classify, bool allow_pair) {
   dim3 grid((L.N + kRollThreads - 1) / kRollThreads, m_launch);
   const int cls = recheck_classify ? 1 : 0;
   // Binary32 lanes on the stored array: the shared-memory ring when the
@@ -447,6 +572,10 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
   const int sms = L.sms;
   const long long warps = static_cast<long long>(grid.x) * grid.y * (kRollThreads / 32);
   const bool ring = warps <= (L.pmul ? 64LL : 16LL) * sms;
+  const long long pair_blocks = static_cast<long long>(grid.x) * ((m_launch + 1) / 2);
+  const bool filled = !ring && L.pair == RRG_PAIR_FILLED &&
+                      pair_blocks >= static_cast<long long>(RRG_PAIR_MIN_WAVES) *
+                                         pair_blocks_per_sm(L.pmul != nullptr) * sms;
 #define RRG_ROLLOUT(KERNEL, T, SRC, KK, D0, D1, CAND, CLS) \
   KERNEL<T, SRC><<<grid, kRollThreads, 0, L.stream>>>(L, KK, D0, D1, CAND, early_exit, CLS)
   if (use_fp64) {
@@ -457,6 +586,16 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
       if (L.scen_gen) RRG_ROLLOUT(rollout_kernel, double, SRC_GEN, L.u64, L.d64, L.d64b, L.cand_c64, 0);
       else RRG_ROLLOUT(rollout_kernel, double, SRC_REGS, L.u64, L.d64, L.d64b, L.cand_c64, 0);
     }
+  } else if (allow_pair && !L.scen_gen && m_launch > 1 && (L.pair == RRG_PAIR_ALWAYS || filled)) {
+    // two candidates per thread (issue-bound launches: one load of each
+    // disturbance and one loop's bookkeeping serve both)
+    const dim3 g2(grid.x, (m_launch + 1) / 2);
+    if (L.pmul)
+      rollout_pair_kernel<true><<<g2, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b, L.cand_c32,
+                                                                   early_exit, cls);
+    else
+      rollout_pair_kernel<false><<<g2, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b, L.cand_c32,
+                                                                    early_exit, cls);
   } else {
     if (L.pmul) {
       if (L.scen_gen) RRG_ROLLOUT(rollout_pu_kernel, float, SRC_GEN, L.u32, L.d32, L.d32b, L.cand_c32, cls);

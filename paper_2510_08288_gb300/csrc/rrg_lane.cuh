@@ -295,6 +295,130 @@ __device__ __forceinline__ T run_lane(const RhsU<T>& K, const RhsC<T>& C,
 }
 
 // ---------------------------------------------------------------------------
+// Two trajectories of one scenario k -- candidates A and B, the same
+// disturbances -- in one thread: each step's three disturbance loads, the
+// ring's addressing and the loop's bookkeeping serve both, and the two step
+// chains are independent work for the scheduler.  Same arithmetic as
+// run_lane for each trajectory: the decisions, and the min slack of a
+// trajectory that does not violate, equal run_lane's bit for bit (a
+// violating one may be integrated a little longer, so its min slack, an upper
+// bound either way, can come out lower).
+//
+// From step 0 (its slack checked first: a violation there runs nothing in
+// pair) over whole blocks of PF steps while
+// neither candidate has been stopped: a trajectory that violates keeps being
+// integrated with its partner (its min slack only falls, so no decision
+// changes) and, when dead_X is given, marks its candidate dead at once, so
+// the stop reaches every lane together at a block end (read at the block's
+// start, as in run_lane) instead of splitting the warp.  Without dead flags
+// (no candidate-level exit) a lane leaves the pair when either trajectory
+// has violated.  The survivor then finishes alone in run_lane from the
+// step reached; the last, partial block too.  z_X[4] = (q_ca, w, q_sm,
+// w_abs) in and out; smin, steps, end, jlast per trajectory as run_lane's.
+// Returns the steps both trajectories ran together.
+template <typename T, int PF = PrefetchDepth<T>::value>
+__device__ __forceinline__ int run_lane_pair(const RhsU<T>& K, const RhsC<T>& CA, const RhsC<T>& CB,
+                                              const T* __restrict__ d, int k, int N, int H, int j_end,
+                                              T* za, T* zb, T dt, T thr, T band,
+                                              volatile int32_t* deadA, volatile int32_t* deadB,
+                                              T* smin, unsigned* steps, int* end, int* jlast) {
+  smin[0] = checked_slack<T>(CA, za[0], za[1], za[2]);
+  smin[1] = checked_slack<T>(CB, zb[0], zb[1], zb[2]);
+  jlast[0] = smin[0] < band ? 0 : -1;
+  jlast[1] = smin[1] < band ? 0 : -1;
+  int how[2] = {smin[0] < thr ? LANE_VIOLATED : LANE_REACHED_END,
+                smin[1] < thr ? LANE_VIOLATED : LANE_REACHED_END};
+  if (how[0] == LANE_VIOLATED && deadA != nullptr) *deadA = 1;
+  if (how[1] == LANE_VIOLATED && deadB != nullptr) *deadB = 1;
+  const bool cand_stop = deadA != nullptr;
+  int j = 0;
+  const StepC<T> S = step_consts<T>(K, dt);
+  bool pair = how[0] == LANE_REACHED_END && how[1] == LANE_REACHED_END;
+  bool stopA = false, stopB = false;  // candidate stopped (dead flag) while not violated
+  if (pair && j + PF <= j_end) {
+    const size_t HN = static_cast<size_t>(H) * N;
+    T r0[PF], r1[PF], r2[PF];
+    const T* pf = d + k;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      r0[u] = __ldg(pf);
+      r1[u] = __ldg(pf + HN);
+      r2[u] = __ldg(pf + 2 * HN);
+      pf += N;
+    }
+    while (pair && j + PF <= j_end) {
+      const int dA = cand_stop ? *deadA : 0, dB = cand_stop ? *deadB : 0;
+      T nfa = T(0), nfb = T(0), ba = inf_v<T>(), bb = inf_v<T>();
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const T e0 = r0[u], e1 = r1[u], e2 = r2[u];
+        if (j + PF < j_end) {
+          r0[u] = __ldg(pf);
+          r1[u] = __ldg(pf + HN);
+          r2[u] = __ldg(pf + 2 * HN);
+        }
+        pf += N;
+        rk4_step_fast<T>(K, CA, S, za[0], za[1], za[2], za[3], e0, e1, e2);
+        rk4_step_fast<T>(K, CB, S, zb[0], zb[1], zb[2], zb[3], e0, e1, e2);
+        ++j;
+        const T sa = CA.y_scale * (za[2] - za[0]) + CA.s_off;
+        const T sb = CB.y_scale * (zb[2] - zb[0]) + CB.s_off;
+        ba = fmin(ba, sa);
+        bb = fmin(bb, sb);
+        nfa = fma_rn(sa, T(0), nfa);
+        nfb = fma_rn(sb, T(0), nfb);
+      }
+      nfa = fma_rn(za[0], T(0), fma_rn(za[1], T(0), fma_rn(za[2], T(0), nfa)));
+      nfb = fma_rn(zb[0], T(0), fma_rn(zb[1], T(0), fma_rn(zb[2], T(0), nfb)));
+      if (nfa != nfa) ba = -inf_v<T>();
+      if (nfb != nfb) bb = -inf_v<T>();
+      smin[0] = fmin(smin[0], ba);
+      smin[1] = fmin(smin[1], bb);
+      if (ba < band) jlast[0] = j;
+      if (bb < band) jlast[1] = j;
+      if (how[0] == LANE_REACHED_END && smin[0] < thr) {
+        how[0] = LANE_VIOLATED;
+        if (cand_stop) *deadA = 1;
+      }
+      if (how[1] == LANE_REACHED_END && smin[1] < thr) {
+        how[1] = LANE_VIOLATED;
+        if (cand_stop) *deadB = 1;
+      }
+      if (cand_stop) {
+        // a candidate's stop comes to every lane at once: from the flag
+        stopA = dA != 0 && j < j_end;
+        stopB = dB != 0 && j < j_end;
+        pair = !stopA && !stopB;
+        if (how[0] == LANE_VIOLATED && how[1] == LANE_VIOLATED) pair = false;
+      } else {
+        pair = how[0] == LANE_REACHED_END && how[1] == LANE_REACHED_END;
+      }
+    }
+  }
+  unsigned extra[2] = {0u, 0u};
+  // each trajectory still running finishes alone
+  if (how[0] == LANE_REACHED_END && stopA) how[0] = LANE_STOPPED;
+  if (how[1] == LANE_REACHED_END && stopB) how[1] = LANE_STOPPED;
+  if (how[0] == LANE_REACHED_END && j < j_end) {
+    int e = LANE_REACHED_END;
+    smin[0] = run_lane<T, PF>(K, CA, d, k, N, H, j, j_end, za[0], za[1], za[2], za[3], smin[0], dt, thr,
+                              deadA, &extra[0], &e, band, &jlast[0]);
+    how[0] = e;
+  }
+  if (how[1] == LANE_REACHED_END && j < j_end) {
+    int e = LANE_REACHED_END;
+    smin[1] = run_lane<T, PF>(K, CB, d, k, N, H, j, j_end, zb[0], zb[1], zb[2], zb[3], smin[1], dt, thr,
+                              deadB, &extra[1], &e, band, &jlast[1]);
+    how[1] = e;
+  }
+  steps[0] = static_cast<unsigned>(j) + extra[0];
+  steps[1] = static_cast<unsigned>(j) + extra[1];
+  end[0] = how[0];
+  end[1] = how[1];
+  return j;
+}
+
+// ---------------------------------------------------------------------------
 // The same trajectory loop with the disturbances staged through a ring of D
 // steps in shared memory, filled by cp.async (LDGSTS) D steps ahead.  The
 // exit and finiteness tests come every B steps as in run_lane (the candidate's

@@ -22,6 +22,7 @@ RRG_OK, RRG_EINVAL, RRG_ENOMEM, RRG_ECUDA, RRG_ETIMEOUT, RRG_ENOTIMPL = range(6)
 SEARCH_BISECT, SEARCH_GRID, SEARCH_KSECTION, SEARCH_SPEC_BISECT = range(4)
 FP64, FP32, FP32_RECHECK = range(3)
 EXIT_NONE, EXIT_LANE, EXIT_CANDIDATE = range(3)
+PAIR_NEVER, PAIR_FILLED, PAIR_ALWAYS = range(3)
 NPARAM = 27
 MAX_CANDIDATES = 1024
 FLAG_NONE_ADMISSIBLE = 1
@@ -59,7 +60,7 @@ class RrgStats(ctypes.Structure):
         ("launches", _u64), ("rollout_launches", _u64), ("lane_steps", _u64),
         ("lane_steps_fp64", _u64), ("rechecked", _u64), ("rounds", _u64),
         ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64), ("repairs", _u64),
-        ("graph_conditional", _u64),
+        ("graph_conditional", _u64), ("lane_steps_paired", _u64),
     ]
 
 
@@ -101,6 +102,9 @@ def _load():
         "rrg_set_tuning": (ctypes.c_int, [_p, ctypes.c_int, ctypes.c_int]),
         "rrg_get_tuning": (ctypes.c_int, [_p, _p, _p]),
         "rrg_autotune": (ctypes.c_int, [_p, _p, _d, _d, ctypes.c_int, _p, _p, _p]),
+        "rrg_set_pairing": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_get_pairing": (ctypes.c_int, [_p, _p]),
+        "rrg_autotune_pairing": (ctypes.c_int, [_p, _p, _d, _d, ctypes.c_int, _p, _p]),
         "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
         "rrg_reset_stats": (ctypes.c_int, [_p]),
         "rrg_slack_gradient": (ctypes.c_int, [_p, _p, _d, _d, _d, ctypes.c_int, ctypes.c_int, _p, _p,
@@ -386,6 +390,27 @@ def rrg_autotune(h, x_t, r_t, v_prev, repeats=2):
     return m.value, p.value, ms.value
 
 
+def rrg_set_pairing(h, mode):
+    _check(lib.rrg_set_pairing(h, int(mode)), h)
+
+
+def rrg_get_pairing(h):
+    """PAIR_NEVER, PAIR_FILLED or PAIR_ALWAYS."""
+    m = _i32(0)
+    _check(lib.rrg_get_pairing(h, ctypes.byref(m)), h)
+    return m.value
+
+
+def rrg_autotune_pairing(h, x_t, r_t, v_prev, repeats=2):
+    """(chosen pairing mode, mean ms per update of each mode)."""
+    x = _f64(x_t)
+    m = _i32(0)
+    ms = (ctypes.c_double * 3)()
+    _check(lib.rrg_autotune_pairing(h, _ptr(x), float(r_t), float(v_prev), int(repeats), ctypes.byref(m),
+                                    ms), h)
+    return m.value, list(ms)
+
+
 def rrg_set_profiling(h, on):
     _check(lib.rrg_set_profiling(h, int(bool(on))), h)
 
@@ -503,6 +528,15 @@ class Governor:
 
     def get_tuning(self):
         return rrg_get_tuning(self.h)
+
+    def set_pairing(self, mode):
+        rrg_set_pairing(self.h, mode)
+
+    def get_pairing(self):
+        return rrg_get_pairing(self.h)
+
+    def autotune_pairing(self, x_t, r_t, v_prev, repeats=2):
+        return rrg_autotune_pairing(self.h, x_t, r_t, v_prev, repeats)
 
 
 def rrg_alu_peaks():
