@@ -186,6 +186,8 @@ def parse():
                     help="steps of the probe that pipelines the first two bisection rounds (0: off)")
     ap.add_argument("--shape", type=str, default=None,
                     help="closed loop: 'm,probe' sets the speculative bisection's shape instead of autotuning it")
+    ap.add_argument("--no-tma", action="store_true",
+                    help="closed loop, sweep: binary32 rings by per-lane asynchronous copies instead of the TMA")
     ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch", "single", "adjoint"),
                     default="closed_loop")
     ap.add_argument("--instances", type=int, default=BATCH_S, help="batch: number of RG instances")
@@ -204,6 +206,21 @@ def window_start(W, K, start=WINDOW_START):
     return max(W, min(start, RUN_UPDATES - K))
 
 
+def shape_seconds(g, shape, states, seed, reps=3):
+    """Host time of `reps` synchronous updates at each state (update index,
+    x_t, r_t, v_prev) with the speculative bisection's shape (m, probe)."""
+    g.set_tuning(*shape)
+    total = 0.0
+    for t, x, r, v in states:
+        g.sample_scenarios(seed, t)
+        g.step(x, r, v)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            g.step(x, r, v)
+        total += time.perf_counter() - t0
+    return total
+
+
 def workload_config(S0, W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, given=False):
     return {
         "workload": "closed-loop robust RG on FC3: N_sim=%d scenarios, horizon %d RK4 steps "
@@ -213,7 +230,9 @@ def workload_config(S0, W, K, N=N_SCEN, H=HORIZON, probe=PROBE_STEPS, m=M_CAND, 
                     "when it is long enough)" % (N, H, S0, S0 + K, S0 - W, S0),
         "search": "speculative bisection (Alg. 1 result), N_kappa=12, %d candidates/round, "
                   "first two rounds pipelined after a %d-step probe (0: not pipelined); shape %s"
-                  % (m, probe, "given" if given else "chosen by rrg_autotune on update 0"),
+                  % (m, probe, "given" if given else
+                     "chosen by rrg_autotune on update 0 and on update %d (the first warm-up update); "
+                     "when the two differ, the one with the smaller time over both" % (S0 - W)),
         "kappa_tol": 2.0 ** -11,
         "precision": "binary32 rollouts, binary64 recheck of |slack| < 1e-6*1.9",
         "l2": "256 MB written between timed steps",
@@ -410,7 +429,7 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- GPU side --
-def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning):
+def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning, tma=True):
     """The timed updates [W, T) again through the host-buffer entry points
     (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle, after
     the updates before them untimed; every call copies its inputs from and its
@@ -419,6 +438,8 @@ def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tunin
     import torch
     g2 = R.Governor(p, cfg, stream)
     g2.set_tuning(*tuning)
+    if not tma:
+        g2.set_tma(R.TMA_NEVER)
     x, v = x0.copy(), V0
     for t in range(W):
         g2.sample_scenarios(seed, t)
@@ -572,15 +593,19 @@ def run_gpu(args):
                                precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
                                recheck_eps_rel=RECHECK_EPS_REL, probe_steps=args.probe_steps)
     g = R.Governor(p, cfg, stream)
+    if args.no_tma:
+        g.set_tma(R.TMA_NEVER)
     x0, _ = g.equilibrium(V0)
     # the speculative bisection's shape (tree width, probe length) by the
-    # library's autotuner on the first update; every shape gives Alg. 1's kappa
+    # library's autotuner; every shape gives Alg. 1's kappa
+    shapes = []
     if args.shape:
         tune_m, tune_probe = (int(v) for v in args.shape.split(","))
         g.set_tuning(tune_m, tune_probe)
     else:
         g.sample_scenarios(seed, 0)
-        tune_m, tune_probe, tune_ms = g.autotune(x0, r_seq[0], V0, repeats=2)
+        tune_m, tune_probe, _ = g.autotune(x0, r_seq[0], V0, repeats=2)
+        shapes.append((tune_m, tune_probe))
     dev = torch.device("cuda", local)
     d_r = torch.tensor(r_seq, dtype=torch.float64, device=dev)
     d_v = torch.zeros(T, dtype=torch.float64, device=dev)
@@ -592,8 +617,24 @@ def run_gpu(args):
 
     # the updates before the window, the last W of them the warm-up (they
     # also initialise the loop state on the device and capture the one-update
-    # CUDA graph the timed updates replay)
-    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, S0, seed, 0, amp, True, d_v, d_k, d_f, d_x)
+    # CUDA graph the timed updates replay); the shape is tuned a second time
+    # on the first warm-up update, an operating point of the run itself
+    tw = S0 - W
+    R.rrg_closed_loop_dev(g.h, x0, V0, d_r, tw, seed, 0, amp, True, d_v, d_k, d_f, d_x)
+    torch.cuda.synchronize()
+    if not args.shape and tw > 0:
+        xw = d_x[3 * tw:3 * tw + 3].cpu().numpy()
+        vw = float(d_v[tw - 1].item())
+        g.sample_scenarios(seed, tw)
+        m2, p2, _ = g.autotune(xw, r_seq[tw], vw, repeats=2)
+        shapes.append((m2, p2))
+        if shapes[1] != shapes[0]:
+            states = [(0, x0, r_seq[0], V0), (tw, xw, r_seq[tw], vw)]
+            tune_m, tune_probe = min(shapes, key=lambda sh: shape_seconds(g, sh, states, seed))
+        else:
+            tune_m, tune_probe = m2, p2
+        g.set_tuning(tune_m, tune_probe)
+    R.rrg_closed_loop_dev(g.h, None, 0.0, d_r, W, seed, 0, amp, True, d_v, d_k, d_f, d_x)
     torch.cuda.synchronize()
     g.reset_stats()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -623,6 +664,8 @@ def run_gpu(args):
     # events around every rollout launch (the roofline's kernel duration)
     gd = R.Governor(p, cfg, stream)
     gd.set_tuning(tune_m, tune_probe)
+    if args.no_tma:
+        gd.set_tma(R.TMA_NEVER)
     dd_v, dd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
     dd_f, dd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
     R.rrg_closed_loop_dev(gd.h, x0, V0, d_r, S0, seed, 0, amp, False, dd_v, dd_k, dd_f, dd_x)
@@ -697,7 +740,8 @@ def run_gpu(args):
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
         e2e = None
         if not args.no_e2e:
-            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, S0, T, flush, kap_dev, (tune_m, tune_probe))
+            e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, S0, T, flush, kap_dev, (tune_m, tune_probe),
+                          not args.no_tma)
 
         # plain FP64 bisection on the same GPU over the same timed updates,
         # timed the same way (CUDA events around each update, L2 flushed in
@@ -740,7 +784,8 @@ def run_gpu(args):
             "ms_per_step": 1e3 * total_s / K, "ms_per_step_median": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(S0, W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
+            "config": dict(workload_config(S0, W, K, NS, HZ, tune_probe, tune_m, bool(args.shape)),
+                           rollout_ring=TMA_NAMES[g.get_tma()]),
             "trajectory_steps_per_s": {"executed": world * exec_steps / total_s,
                                        "executed_per_update": exec_steps / K},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -1271,6 +1316,8 @@ def adjoint_cpu(p, x_t, v_prev, r, N, H, seconds, gpu_argmin):
 # ------------------------------------------------------------------ sweep --
 SWEEP_METRIC = "trajectory-steps/s vs scenario count (large sweep, FP32 + FP64 recheck)"
 PAIRING_NAMES = ("never", "filled", "always")
+TMA_NAMES = ("per-lane cp.async", "TMA for ring launches of >= 24 warps per SM, per-lane cp.async below",
+             "TMA for every ring launch")
 
 
 def sweep_config(ns, W, K):
@@ -1356,6 +1403,8 @@ def run_sweep(args):
             pairing_ms = dict(zip(PAIRING_NAMES, ms_modes))
         else:
             g.set_pairing(PAIRING_NAMES.index(args.pairing))
+        if args.no_tma:
+            g.set_tma(R.TMA_NEVER)
         d_x = torch.tensor(x_t, dtype=torch.float64, device=dev)
         d_r = torch.tensor([r], dtype=torch.float64, device=dev)
         d_vp = torch.tensor([v_prev], dtype=torch.float64, device=dev)
@@ -1436,6 +1485,7 @@ def run_sweep(args):
                      "rollout_tflops": achieved,
                      "rollout_avg_launch_ms": avg_roll_ms, "rechecked": st["rechecked"],
                      "pairing": PAIRING_NAMES[g.get_pairing()], "pairing_autotune_ms": pairing_ms,
+                     "rollout_ring": TMA_NAMES[g.get_tma()],
                      "paired_step_fraction": st["lane_steps_paired"] / max(1, st["lane_steps"]),
                      "gpu_launches": st["launches"], "kappa": [float(x) for x in kap],
                      "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64,

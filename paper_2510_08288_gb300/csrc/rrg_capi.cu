@@ -27,6 +27,11 @@ struct rrg_ctx {
   double params[RRG_NPARAM]{};
   SearchCfg scfg{};
   int pair = RRG_PAIR_FILLED;   // trajectories per thread of the binary32 rollouts (rrg_set_pairing)
+  // tensor maps of the binary32 scenario arrays (pair 0, pair 1) for the TMA
+  // ring; tma_ok once both describe the arrays in use
+  CUtensorMap tmap[2];
+  bool tma_ok = false;
+  int tma_mode = RRG_TMA_AUTO;  // rrg_set_tma
   Launch L{};
   // device memory
   double* params_dev = nullptr;
@@ -203,6 +208,8 @@ void fill_launch(rrg_ctx* h) {
   const rrg_config& c = h->cfg;
   L.stream = h->stream;
   L.pair = h->pair;
+  L.tmap = h->tma_ok && h->tma_mode != RRG_TMA_NEVER ? h->tmap : nullptr;
+  L.tma = h->tma_mode;
   L.N = c.n_scenarios;
   L.H = c.horizon;
   L.precision = c.precision;
@@ -692,10 +699,16 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
   s.y_min = c.y_min;
   s.eps_ss = c.eps_ss;
   s.y_c = c.y_c;
-  fill_launch(h);
-  // occupancy of the paired kernel, queried once here (never inside a capture)
+  // occupancy of the paired kernel and the TMA kernels' shared-memory limit,
+  // set once here (never inside a capture)
   (void)pair_blocks_per_sm(false);
   (void)pair_blocks_per_sm(true);
+  if (!c.scenarios_in_register && tma_ring_prepare() &&
+      encode_scenario_map(&h->tmap[0], h->d32, c.n_scenarios, c.horizon)) {
+    h->tmap[1] = h->tmap[0];
+    h->tma_ok = true;
+  }
+  fill_launch(h);
   *out = h;
   return RRG_OK;
 }
@@ -985,6 +998,10 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
     if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    if (h->tma_ok && !encode_scenario_map(&h->tmap[1], h->d32b, h->cfg.n_scenarios, h->cfg.horizon)) {
+      h->tma_ok = false;  // the rings fall back to per-lane asynchronous copies
+      h->L.tmap = nullptr;
+    }
     h->L.d64b = h->d64b;
     h->L.d32b = h->d32b;
     h->L.pmulb = h->pmulb;
@@ -1450,6 +1467,30 @@ int rrg_set_pairing(rrg_handle h, int mode) {
   return RRG_OK;
 }
 
+int rrg_set_tma(rrg_handle h, int mode) {
+  if (!h) return RRG_EINVAL;
+  if (mode < RRG_TMA_NEVER || mode > RRG_TMA_ALWAYS)
+    return set_err(h, RRG_EINVAL, "TMA mode must be RRG_TMA_NEVER, RRG_TMA_AUTO or RRG_TMA_ALWAYS");
+  if (mode != RRG_TMA_NEVER && !h->tma_ok)
+    return set_err(h, RRG_EINVAL, "no TMA ring for this handle (n_scenarios %% 4 != 0, in-register "
+                                  "scenarios, or the driver refused the tensor map)");
+  DeviceGuard g(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  h->tma_mode = mode;
+  fill_launch(h);
+  if (h->cl_exec) {  // the cached closed-loop graph holds the old kernels
+    cudaGraphExecDestroy(h->cl_exec);
+    h->cl_exec = nullptr;
+  }
+  return RRG_OK;
+}
+
+int rrg_get_tma(rrg_handle h, int32_t* mode) {
+  if (!h || !mode) return RRG_EINVAL;
+  *mode = h->tma_ok ? h->tma_mode : RRG_TMA_NEVER;
+  return RRG_OK;
+}
+
 int rrg_get_pairing(rrg_handle h, int32_t* mode) {
   if (!h || !mode) return RRG_EINVAL;
   *mode = h->pair;
@@ -1549,6 +1590,7 @@ int rrg_get_stats(rrg_handle h, rrg_stats* out) {
   out->repairs = ds.repairs;
   out->graph_conditional = h->cl_exec != nullptr && h->cl_conditional ? 1 : 0;
   out->lane_steps_paired = ds.lane_steps_paired;
+  out->wait_timeouts = ds.wait_timeouts;
   return RRG_OK;
 }
 

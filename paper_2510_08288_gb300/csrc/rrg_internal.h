@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rrg.h"
@@ -104,6 +105,7 @@ struct DevStats {
   // of a captured closed-loop update (counted by the kernel that opens it)
   unsigned long long cond_launches, cond_rollouts, cond_rounds;
   unsigned long long lane_steps_paired;  // of lane_steps, run two trajectories per thread
+  unsigned long long wait_timeouts;      // bounded waits that gave up (TMA ring copies)
 };
 
 // Closed-loop device state.
@@ -173,6 +175,11 @@ struct Launch {
   double* pmulb;
   double punc_rho;
   uint32_t punc_mask;
+  // host: the tensor maps of the two binary32 scenario arrays (the second
+  // repeats the first until a second pair exists), or nullptr: the binary32
+  // rings then use per-lane asynchronous copies
+  const CUtensorMap* tmap;
+  int tma;                      // RRG_TMA_*: which ring launches take the TMA
 };
 
 // Folds the FC3 parameter vector into the constants the kernels use
@@ -365,6 +372,13 @@ cudaError_t launch_prepare(const Launch& L, int width);
 cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
                                 const double* d_kappas, int m);
 cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d_min_slack);
+// Tensor map of a binary32 scenario array [3][H][N] for the TMA ring (boxes
+// of 32 scenarios x one chunk of steps x 3 components); false when N is not a
+// multiple of 4 (row strides must be multiples of 16 bytes) or the driver
+// refuses.  tma_ring_prepare() sets the TMA kernels' shared-memory limit once;
+// false if the runtime refuses.
+bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H);
+bool tma_ring_prepare();
 // Resident blocks per SM of the two-candidates-per-thread rollout kernel
 // (queried from the runtime on the first call, then cached).
 int pair_blocks_per_sm(bool pu);

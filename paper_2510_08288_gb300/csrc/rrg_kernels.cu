@@ -19,6 +19,7 @@
 // captured in a CUDA graph.
 #include <cfloat>
 #include <cmath>
+#include <cudaTypedefs.h>
 
 #include "rrg_device.cuh"
 #include "rrg_internal.h"
@@ -26,7 +27,10 @@
 
 namespace rrg {
 
-constexpr int kRollThreads = 128;
+#ifndef RRG_ROLL_THREADS
+#define RRG_ROLL_THREADS 128
+#endif
+constexpr int kRollThreads = RRG_ROLL_THREADS;
 constexpr int kSearchThreads = 256;
 
 __global__ void equilibrium_kernel(const double* __restrict__ P, const Fc3K<double> k64,
@@ -261,8 +265,15 @@ cudaError_t launch_round_scenarios(const Launch& L) {
 enum RollSrc : int {
   SRC_REGS = 0,  // the stored array through a register prefetch ring (run_lane)
   SRC_RING = 1,  // the stored array through a shared-memory ring (run_lane_ring, binary32)
-  SRC_GEN = 2    // drawn from Philox inside the trajectory loop (run_lane_gen)
+  SRC_GEN = 2,   // drawn from Philox inside the trajectory loop (run_lane_gen)
+  SRC_TMA = 3    // the stored array through a per-warp TMA ring (run_lane_tma, binary32)
 };
+
+// Dynamic shared memory of the TMA-ring rollouts: per warp two stages of
+// kTmaStageBytes, then per warp two mbarriers.
+extern __shared__ __align__(1024) unsigned char rrg_dyn_smem[];
+constexpr size_t kTmaSmemBytes =
+    static_cast<size_t>(kRollThreads / 32) * (2 * kTmaStageBytes + 2 * sizeof(uint64_t));
 
 // The lane's outcome for candidate slot i (called by every thread of the
 // warp): classified against the recheck band in the binary32 + recheck mode
@@ -315,7 +326,8 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
                                              const T* __restrict__ d_pair0,
                                              const T* __restrict__ d_pair1,
                                              const RhsC<T>* __restrict__ cand, int early_exit,
-                                             int classify) {
+                                             int classify, const void* tm0 = nullptr,
+                                             const void* tm1 = nullptr) {
   const T* __restrict__ d = L.st->buf ? d_pair1 : d_pair0;
   const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
   const int y = blockIdx.y;
@@ -355,19 +367,20 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
   int jlast = -1;
   const T band = classify ? eps : -inf_v<T>();
   bool final_lane = active;  // this launch decides the lane
+  // segment bounds (the same for every lane of the launch row)
+  const int j_end = mode == SEG_PROBE ? L.probe_steps : L.H;
+  const int j0 = mode == SEG_CONTINUE ? L.probe_steps : 0;
+  LaneState<T>* ls = nullptr;
+  T q_ca = T(0), w = T(0), q_sm = T(0), w_abs = T(0);  // the deviation from the candidate's reference point
+  T smin0 = inf_v<T>();
   if (active) {
-    LaneState<T>* ls = mode == SEG_FULL ? nullptr
-                                        : static_cast<LaneState<T>*>(L.lane_state) +
-                                              static_cast<size_t>(i) * N + k;
+    if (mode != SEG_FULL) ls = static_cast<LaneState<T>*>(L.lane_state) + static_cast<size_t>(i) * N + k;
     double p_atm = L.params[P_P_ATM];
     if constexpr (PU)
       p_atm = scenario_model<T>(L.params,
                                 (L.st->buf ? L.pmulb : L.pmul) + static_cast<size_t>(k) * RRG_NPARAM,
                                 L.cand_v[i], L.k64.pws, L.y_min, K, C);
-    T q_ca, w, q_sm, w_abs;  // the deviation from the candidate's reference point
     start_state<T>(C, L.st->x, p_atm, q_ca, w, q_sm, w_abs);
-    T smin0 = inf_v<T>();
-    int j0 = 0;
     if (mode == SEG_CONTINUE) {
       const LaneState<T> st = *ls;
       if (st.status != 0) {
@@ -379,39 +392,52 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
         w_abs = st.w_abs;
         smin0 = st.smin;
         jlast = st.jlast;
-        j0 = L.probe_steps;
       }
     }
-    if (final_lane) {
-      const int j_end = mode == SEG_PROBE ? L.probe_steps : L.H;
-      int end = LANE_REACHED_END;
-      if constexpr (SRC == SRC_GEN)
-        smin = run_lane_gen<T>(K, C, L.st->src[L.st->buf], k, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
-                               static_cast<T>(L.dt), thr,
-                               cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
-      else if constexpr (SRC == SRC_RING) {
-        static_assert(sizeof(T) == 4, "the shared-memory ring is binary32");
-        __shared__ float ring[RRG_RING_DEPTH * 3 * kRollThreads];
-        smin = run_lane_ring(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
+  }
+  int end = LANE_REACHED_END;
+  if constexpr (SRC == SRC_TMA) {
+    // every lane of the warp takes part (the chunk copies serve the warp)
+    static_assert(sizeof(T) == 4, "the TMA ring is binary32");
+    const int wid = threadIdx.x >> 5;
+    float* stages = reinterpret_cast<float*>(rrg_dyn_smem) + static_cast<size_t>(wid) * 2 * kTmaStageFloats;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(rrg_dyn_smem + (kRollThreads / 32) * 2 * kTmaStageBytes) +
+                     2 * wid;
+    const bool lane_runs = active && final_lane;
+    const T s_out = run_lane_tma(K, C, L.st->buf ? tm1 : tm0, k & ~31, lane_runs, j0, j_end, q_ca, w, q_sm,
+                                 w_abs, smin0, static_cast<T>(L.dt), thr, cand_stop ? dead : nullptr,
+                                 cand_stop ? dead : nullptr, &steps, &end, band, &jlast, stages, bars,
+                                 &L.stats->wait_timeouts);
+    if (lane_runs) smin = s_out;
+  } else if (active && final_lane) {
+    if constexpr (SRC == SRC_GEN)
+      smin = run_lane_gen<T>(K, C, L.st->src[L.st->buf], k, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
                              static_cast<T>(L.dt), thr,
-                             cand_stop ? dead : nullptr, &steps, &end, band, &jlast, ring);
-      } else
-        smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
+                             cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
+    else if constexpr (SRC == SRC_RING) {
+      static_assert(sizeof(T) == 4, "the shared-memory ring is binary32");
+      __shared__ float ring[RRG_RING_DEPTH * 3 * kRollThreads];
+      smin = run_lane_ring(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
                            static_cast<T>(L.dt), thr,
-                           cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
-      if (cand_stop && smin < thr) *dead = 1;
-      if (mode == SEG_PROBE) {
-        LaneState<T> o;
-        o.q[0] = q_ca;
-        o.q[1] = w;
-        o.q[2] = q_sm;
-        o.w_abs = w_abs;
-        o.smin = smin;
-        o.status = end == LANE_REACHED_END ? 0 : 1;
-        o.jlast = jlast;
-        *ls = o;
-        if (end == LANE_REACHED_END) final_lane = false;
-      }
+                           cand_stop ? dead : nullptr, &steps, &end, band, &jlast, ring);
+    } else
+      smin = run_lane<T>(K, C, d, k, N, L.H, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
+                         static_cast<T>(L.dt), thr,
+                         cand_stop ? dead : nullptr, &steps, &end, band, &jlast);
+  }
+  if (active && final_lane) {
+    if (cand_stop && smin < thr) *dead = 1;
+    if (mode == SEG_PROBE) {
+      LaneState<T> o;
+      o.q[0] = q_ca;
+      o.q[1] = w;
+      o.q[2] = q_sm;
+      o.w_abs = w_abs;
+      o.smin = smin;
+      o.status = end == LANE_REACHED_END ? 0 : 1;
+      o.jlast = jlast;
+      *ls = o;
+      if (end == LANE_REACHED_END) final_lane = false;
     }
   }
   reduce_lane<T>(L, i, k, N, final_lane, smin, steps, jlast, classify, eps, dead);
@@ -440,6 +466,18 @@ rollout_pu_kernel(const Launch L, const RhsU<T> K, const T* __restrict__ d_pair0
                   const T* __restrict__ d_pair1, const RhsC<T>* __restrict__ cand, int early_exit,
                   int classify) {
   rollout_body<T, true, SRC>(L, K, d_pair0, d_pair1, cand, early_exit, classify);
+}
+
+// Binary32 lanes through the per-warp TMA ring (launches that leave warp
+// slots empty, as SRC_RING): the tensor maps of the two scenario pairs are
+// kernel parameters, so a captured graph keeps them.
+template <bool PU>
+__global__ void __launch_bounds__(kRollThreads, PU ? RRG_PU_MIN_BLOCKS : 1)
+rollout_tma_kernel(const Launch L, const RhsU<float> K, const float* __restrict__ d_pair0,
+                   const float* __restrict__ d_pair1, const RhsC<float>* __restrict__ cand, int early_exit,
+                   int classify, const __grid_constant__ CUtensorMap tm0,
+                   const __grid_constant__ CUtensorMap tm1) {
+  rollout_body<float, PU, SRC_TMA>(L, K, d_pair0, d_pair1, cand, early_exit, classify, &tm0, &tm1);
 }
 
 // Two candidates per thread (binary32, register ring): block row y runs the
@@ -534,6 +572,37 @@ rollout_pair_kernel(const Launch L, const RhsU<float> K0, const float* __restric
   }
 }
 
+bool tma_ring_prepare() {
+  static const bool ok =
+      cudaFuncSetAttribute(rollout_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess &&
+      cudaFuncSetAttribute(rollout_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess;
+  return ok;
+}
+
+bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  if (encode == nullptr || d32 == nullptr || N <= 0 || H <= 0 || N % 4 != 0) return false;
+  // dims innermost first: scenario k, step j, component c
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(H), 3};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * sizeof(float),
+                                 static_cast<cuuint64_t>(H) * N * sizeof(float)};
+  const cuuint32_t box[3] = {32, static_cast<cuuint32_t>(kTmaChunk), 3};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d32), dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Resident blocks per SM of the paired kernel (its register count decides).
 int pair_blocks_per_sm(bool pu) {
   static const int n[2] = {
@@ -553,6 +622,20 @@ int pair_blocks_per_sm(bool pu) {
 // slower.
 #ifndef RRG_PAIR_MIN_WAVES
 #define RRG_PAIR_MIN_WAVES 6
+#endif
+
+// RRG_TMA_AUTO takes the TMA ring for ring launches of at least this many
+// warps per SM.  The TMA saves the per-step copy instructions, which pays
+// where many warps compete for issue; a warp running alone pays the chunk's
+// wait, warp votes and fence on its dependency chain instead.  Measured on
+// GB300 (k-section sweep, 16 candidates x 5,000 steps, per update): 16,384
+// scenarios with uncertain parameters (54 warps per SM) 6.28 against
+// 6.75 ms, 8,192 (27) 4.46 against 4.53 ms, 4,096 (13.5) 2.78 against 2.70
+// ms, 1,024 (3.4) 1.85 against 1.64 ms; the 1,024-scenario closed loop (8.8
+// warps per SM at launch, mostly single survivors) 2,743 against 2,927
+// updates/s.
+#ifndef RRG_TMA_MIN_WARPS_PER_SM
+#define RRG_TMA_MIN_WARPS_PER_SM 24
 #endif
 
 cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int early_exit,
@@ -596,6 +679,16 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
     else
       rollout_pair_kernel<false><<<g2, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b, L.cand_c32,
                                                                     early_exit, cls);
+  } else if (ring && !L.scen_gen && L.tmap != nullptr &&
+             (L.tma == RRG_TMA_ALWAYS ||
+              (L.tma == RRG_TMA_AUTO && warps >= static_cast<long long>(RRG_TMA_MIN_WARPS_PER_SM) * sms))) {
+    // the ring through the TMA: one tensor copy per warp and chunk of steps
+    if (L.pmul)
+      rollout_tma_kernel<true><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
+          L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
+    else
+      rollout_tma_kernel<false><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
+          L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
   } else {
     if (L.pmul) {
       if (L.scen_gen) RRG_ROLLOUT(rollout_pu_kernel, float, SRC_GEN, L.u32, L.d32, L.d32b, L.cand_c32, cls);

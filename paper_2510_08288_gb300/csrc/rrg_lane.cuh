@@ -570,6 +570,223 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
   return smin;
 }
 
+// ---------------------------------------------------------------------------
+// The trajectory loop fed by the Tensor Memory Accelerator.  Each warp owns a
+// two-stage ring of T-step chunks in shared memory; a chunk is one
+// cp.async.bulk.tensor copy of the box (32 scenarios from the warp's first,
+// T steps, 3 components) of the binary32 array [3][H][N], issued by lane 0
+// and counted on the stage's mbarrier, so a step reads its three values with
+// shared loads at fixed offsets instead of issuing three per-lane
+// asynchronous copies, their commit and wait and the address arithmetic.
+// Scenarios and steps of a box beyond the array are filled with zeros by the
+// copy (the ragged last warp, the last chunk).
+//
+// The warp walks the chunks together: the copies serve every lane, so a lane
+// that has stopped keeps its place, does no arithmetic, and the chunk loop
+// ends once no lane runs.  Per trajectory the arithmetic is run_lane's in the
+// same order, so the min slack and the decisions equal it bit for bit; the
+// exit and finiteness tests come at each whole chunk's end (the last, partial
+// chunk steps one at a time with run_lane's per-step test); the candidate's
+// dead flag is read at a chunk's start and used at its end, and a lane that
+// violates marks `mark` at once.  on = false: the lane only keeps the warp
+// company (inactive scenario, or finished in an earlier segment).
+//
+// Waits are bounded.  A stage whose copy has not landed after kTmaWaitLimit
+// polls ends the loop for the whole warp: the call counts one timeout in
+// *timeouts and every lane still running reports a violation (min slack
+// -inf, so no candidate is accepted on data that did not arrive).  Before
+// returning, the warp waits (bounded again) for every copy it issued, so
+// nothing lands in shared memory after the block has left.
+//
+// stages: the warp's 2 * 3 * T * 32 floats (128-byte aligned); bars: its two
+// mbarriers.  Called by all 32 lanes of the warp.
+#ifndef RRG_TMA_CHUNK
+#define RRG_TMA_CHUNK 16
+#endif
+constexpr int kTmaChunk = RRG_TMA_CHUNK;
+constexpr int kTmaStageFloats = 3 * kTmaChunk * 32;
+constexpr unsigned kTmaStageBytes = kTmaStageFloats * 4u;
+constexpr int kTmaWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+// Makes the initialised barriers visible to the asynchronous proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's (and, after a warp barrier, the warp's) generic-proxy
+// shared-memory accesses before the asynchronous proxy's next writes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Polls until the phase of the given parity has completed, at most
+// kTmaWaitLimit times; false if it has not.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kTmaWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Chunk copy: box (x = k0, y = j, z = 0) of the tensor map into `dst`,
+// completion counted on `bar` (lane 0 only).
+__device__ __forceinline__ void tma_chunk(const void* tmap, uint32_t dst, uint32_t bar, int k0, int j) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTmaStageBytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(k0), "r"(j), "r"(0), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ float run_lane_tma(const RhsU<float>& K, const RhsC<float>& C, const void* tmap,
+                                              int k0, bool on, int j0, int j_end, float& q_ca, float& w,
+                                              float& q_sm, float& w_abs, float smin_in, float dt, float thr,
+                                              const volatile int32_t* dead, volatile int32_t* mark,
+                                              unsigned* steps, int* end, float band, int* jlast,
+                                              float* stages, uint64_t* bars,
+                                              unsigned long long* timeouts) {
+  constexpr int T = kTmaChunk;
+  const int lane = threadIdx.x & 31;
+  float smin = smin_in;
+  int j = j0;
+  int jl = *jlast;
+  int how = LANE_REACHED_END;
+  bool run = on && j0 < j_end;
+  if (on && j0 == 0) {
+    const float s0 = checked_slack<float>(C, q_ca, w, q_sm);
+    smin = fmin(smin, s0);
+    if (s0 < band) jl = 0;
+    if (s0 < thr) {
+      how = LANE_VIOLATED;
+      run = false;
+      if (mark != nullptr) *mark = 1;
+    }
+  }
+  const StepC<float> S = step_consts<float>(K, dt);
+  const int nchunks = j_end > j0 ? (j_end - j0 + T - 1) / T : 0;
+  if (nchunks > 0 && __any_sync(0xffffffffu, run)) {
+    const uint32_t st0 = smem_u32(stages), bar0 = smem_u32(bars);
+    if (lane == 0) {
+      mbar_init(bar0, 1u);
+      mbar_init(bar0 + 8u, 1u);
+      fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) {
+      tma_chunk(tmap, st0, bar0, k0, j0);
+      if (nchunks > 1) tma_chunk(tmap, st0 + kTmaStageBytes, bar0 + 8u, k0, j0 + T);
+    }
+    int issued = nchunks > 1 ? 2 : 1;  // chunks whose copy was issued
+    int waited = 0;                     // chunks whose copy has landed
+    bool timed_out = false;
+    for (int c = 0; c < nchunks; ++c) {
+      const int sg = c & 1;
+      const uint32_t bar = bar0 + 8u * static_cast<uint32_t>(sg);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, static_cast<uint32_t>((c >> 1) & 1)));
+      if (!ok) {
+        timed_out = true;
+        break;
+      }
+      waited = c + 1;
+      const float* e = stages + sg * kTmaStageFloats + lane;
+      const int nst = j_end - (j0 + c * T) < T ? j_end - (j0 + c * T) : T;
+      const int dead_now = (run && dead != nullptr) ? *dead : 0;
+      if (run) {
+        if (nst == T) {
+          float nf = 0.0f, bmin = inf_v<float>();
+#pragma unroll
+          for (int u = 0; u < T; ++u) {
+            const float e0 = e[u * 32], e1 = e[(T + u) * 32], e2 = e[(2 * T + u) * 32];
+            rk4_step_fast<float>(K, C, S, q_ca, w, q_sm, w_abs, e0, e1, e2);
+            const float sl = C.y_scale * (q_sm - q_ca) + C.s_off;
+            bmin = fmin(bmin, sl);
+            nf = fma_rn(sl, 0.0f, nf);
+          }
+          j += T;
+          nf = fma_rn(q_ca, 0.0f, fma_rn(w, 0.0f, fma_rn(q_sm, 0.0f, nf)));
+          if (nf != nf) bmin = -inf_v<float>();
+          smin = fmin(smin, bmin);
+          if (bmin < band) jl = j;
+          if (smin < thr) {
+            how = LANE_VIOLATED;
+            run = false;
+            if (mark != nullptr) *mark = 1;
+          } else if (dead_now != 0 && j < j_end) {
+            how = LANE_STOPPED;
+            run = false;
+          }
+        } else {
+          for (int u = 0; u < nst && run; ++u) {
+            const float e0 = e[u * 32], e1 = e[(T + u) * 32], e2 = e[(2 * T + u) * 32];
+            rk4_step_fast<float>(K, C, S, q_ca, w, q_sm, w_abs, e0, e1, e2);
+            ++j;
+            const float sl = checked_slack<float>(C, q_ca, w, q_sm);
+            smin = fmin(smin, sl);
+            if (sl < band) jl = j;
+            if (sl < thr) {
+              how = LANE_VIOLATED;
+              run = false;
+              if (mark != nullptr) *mark = 1;
+            }
+          }
+        }
+      }
+      if (!__any_sync(0xffffffffu, run)) break;
+      // every lane is done reading this stage: refill it with chunk c + 2
+      __syncwarp();
+      if (c + 2 < nchunks) {
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          tma_chunk(tmap, st0 + static_cast<uint32_t>(sg) * kTmaStageBytes, bar, k0, j0 + (c + 2) * T);
+        }
+        issued = c + 3;
+      }
+    }
+    // nothing may land after the warp leaves: wait for the copies issued and
+    // not yet waited for
+    bool drained = true;
+    for (int c = waited; c < issued; ++c)
+      drained = mbar_wait_bounded(bar0 + 8u * static_cast<uint32_t>(c & 1),
+                                  static_cast<uint32_t>((c >> 1) & 1)) && drained;
+    drained = __all_sync(0xffffffffu, drained);
+    if (timed_out || !drained) {
+      if (lane == 0) atomicAdd(timeouts, 1ull);
+      if (run) {
+        smin = -inf_v<float>();
+        how = LANE_VIOLATED;
+        run = false;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && drained) {
+      mbar_inval(bar0);
+      mbar_inval(bar0 + 8u);
+    }
+  }
+  *steps = static_cast<unsigned>(j - j0);
+  *end = how;
+  *jlast = jl;
+  return smin;
+}
+
 // Disturbance component of Philox word w with half-range a: the binary32
 // copy (top 24 bits, a 2^-23 folded in) or the binary64 value, exactly as the
 // sampler stores them.

@@ -23,6 +23,7 @@ SEARCH_BISECT, SEARCH_GRID, SEARCH_KSECTION, SEARCH_SPEC_BISECT = range(4)
 FP64, FP32, FP32_RECHECK = range(3)
 EXIT_NONE, EXIT_LANE, EXIT_CANDIDATE = range(3)
 PAIR_NEVER, PAIR_FILLED, PAIR_ALWAYS = range(3)
+TMA_NEVER, TMA_AUTO, TMA_ALWAYS = range(3)
 NPARAM = 27
 MAX_CANDIDATES = 1024
 FLAG_NONE_ADMISSIBLE = 1
@@ -60,7 +61,7 @@ class RrgStats(ctypes.Structure):
         ("launches", _u64), ("rollout_launches", _u64), ("lane_steps", _u64),
         ("lane_steps_fp64", _u64), ("rechecked", _u64), ("rounds", _u64),
         ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64), ("repairs", _u64),
-        ("graph_conditional", _u64), ("lane_steps_paired", _u64),
+        ("graph_conditional", _u64), ("lane_steps_paired", _u64), ("wait_timeouts", _u64),
     ]
 
 
@@ -103,6 +104,8 @@ def _load():
         "rrg_get_tuning": (ctypes.c_int, [_p, _p, _p]),
         "rrg_autotune": (ctypes.c_int, [_p, _p, _d, _d, ctypes.c_int, _p, _p, _p]),
         "rrg_set_pairing": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_set_tma": (ctypes.c_int, [_p, ctypes.c_int]),
+        "rrg_get_tma": (ctypes.c_int, [_p, _p]),
         "rrg_get_pairing": (ctypes.c_int, [_p, _p]),
         "rrg_autotune_pairing": (ctypes.c_int, [_p, _p, _d, _d, ctypes.c_int, _p, _p]),
         "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
@@ -394,6 +397,17 @@ def rrg_set_pairing(h, mode):
     _check(lib.rrg_set_pairing(h, int(mode)), h)
 
 
+def rrg_set_tma(h, mode):
+    _check(lib.rrg_set_tma(h, int(mode)), h)
+
+
+def rrg_get_tma(h):
+    """TMA_NEVER, TMA_AUTO or TMA_ALWAYS (TMA_NEVER where the TMA ring is unavailable)."""
+    m = _i32(0)
+    _check(lib.rrg_get_tma(h, ctypes.byref(m)), h)
+    return m.value
+
+
 def rrg_get_pairing(h):
     """PAIR_NEVER, PAIR_FILLED or PAIR_ALWAYS."""
     m = _i32(0)
@@ -531,6 +545,12 @@ class Governor:
 
     def set_pairing(self, mode):
         rrg_set_pairing(self.h, mode)
+
+    def set_tma(self, mode):
+        rrg_set_tma(self.h, mode)
+
+    def get_tma(self):
+        return rrg_get_tma(self.h)
 
     def get_pairing(self):
         return rrg_get_pairing(self.h)

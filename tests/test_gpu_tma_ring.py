@@ -1,0 +1,161 @@
+"""The binary32 ring through the Tensor Memory Accelerator (rrg_set_tma).
+
+RRG_TMA_ALWAYS forces the TMA for every ring launch and RRG_TMA_NEVER the
+per-lane copies, so each test runs both paths on the same launches.
+
+Launches that leave most warp slots empty bring the stored disturbances into
+a shared-memory ring.  With the TMA, one tensor copy per warp fills a
+32-scenario x 16-step x 3-component box (zeros past the array); without it,
+each lane issues its own 4-byte copies.  The arithmetic is the same, so the
+two give identical flags, P entries and min slacks (every min slack without
+an early exit, the admissible candidates' with one), and the oracle's
+decisions.  Scenario counts that are not a multiple of the 32-lane box leave
+a ragged last warp; horizons that are not a multiple of 16 end in a partial
+chunk; probes that are not a multiple of 16 start the continuation mid-chunk.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2510_08288_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+NTH = max(1, min(16, os.cpu_count() or 1))
+MASK = inputs.FC3_UNCERTAIN_MASK
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_08288_gb300 import build as B
+    B.build()
+    from paper_2510_08288_gb300 import rrg
+    return rrg
+
+
+def _cfg(R, N, H, **kw):
+    c = dict(horizon=H, n_scenarios=N, max_candidates=16, n_bisect=12, search=R.SEARCH_SPEC_BISECT,
+             precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE, recheck_eps_rel=1e-6,
+             param_unc_mask=MASK, probe_steps=0)
+    c.update(kw)
+    return R.rrg_config_default(**c)
+
+
+def _same(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    np.testing.assert_array_equal(np.isnan(a), np.isnan(b))
+    np.testing.assert_array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+
+
+@pytest.mark.parametrize("N,H", [(1000, 203), (4096, 2000), (36, 65), (300, 16), (1028, 33)])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_recheck"])
+@pytest.mark.parametrize("unc", [0.0, 0.1])
+@pytest.mark.parametrize("early", [0, 1, 2])
+def test_tma_ring_equals_async_ring(R, orc, params, N, H, prec, unc, early):
+    p = R.FP32 if prec == "fp32" else R.FP32_RECHECK
+    kappas = np.linspace(0.0, 1.0, 13)
+    x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.03, 1.0])
+    res = {}
+    with R.Governor(params, _cfg(R, N, H, precision=p, early_exit=early, param_unc_rel=unc)) as g:
+        assert g.get_tma() == R.TMA_AUTO
+        g.sample_scenarios(5, 2)
+        for mode in (R.TMA_ALWAYS, R.TMA_NEVER):
+            g.set_tma(mode)
+            assert g.get_tma() == mode
+            g.reset_stats()
+            res[mode] = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+            assert g.stats()["wait_timeouts"] == 0
+    (a1, m1, P1), (a0, m0, P0) = res[R.TMA_ALWAYS], res[R.TMA_NEVER]
+    np.testing.assert_array_equal(a1, a0)
+    np.testing.assert_array_equal(P1, P0)
+    if early == 0:
+        _same(m1, m0)
+    else:
+        _same(m1[a0 == 1], m0[a0 == 1])
+
+
+@pytest.mark.parametrize("unc", [0.0, 0.1])
+def test_tma_ring_decides_like_the_oracle(R, orc, params, unc):
+    """At the benchmark's band, candidates around the boundary (many near-zero
+    lanes, rechecked in binary64): the oracle's P and flags; the oracle draws
+    its own disturbances and multipliers."""
+    N, H, seed, upd = 1000, 203, 3, 4
+    kappas = np.linspace(0.0, 0.06, 25) if unc else np.linspace(0.09, 0.115, 26)
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, _cfg(R, N, H, max_candidates=32, early_exit=R.EXIT_LANE, param_unc_rel=unc)) as g:
+        g.set_tma(R.TMA_ALWAYS)
+        g.sample_scenarios(seed, upd)
+        adm, _, P = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        assert g.stats()["wait_timeouts"] == 0
+    d = orc.sample_disturbances(seed, upd, N, H, inputs.DIST_AMP)
+    mult = orc.sample_param_multipliers(seed, upd, N, unc, MASK) if unc else None
+    with orc.param_multipliers(mult):
+        a_o, _, P_o, _ = orc.eval_candidates(params, orc.cfg(H=H, N=N, early_exit=0), x_t, 100.0, 250.0,
+                                             kappas, d, want_P=True, nthreads=NTH)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+    assert 0 < int(a_o.sum()) < len(kappas)
+
+
+@pytest.mark.parametrize("probe", [1, 20, 128])
+def test_tma_ring_in_pipelined_searches(R, orc, params, probe):
+    """Probe and continuation launches (the continuation starts at the probe's
+    step, mid-chunk unless the probe is a multiple of 16): the same result
+    with and without the TMA, and the oracle's joint bisection."""
+    N, H, seed, upd = 1024, 500, 3, 7
+    cases = [(100.0, 250.0, orc.equilibrium(params, 100.0)),
+             (180.0, 90.0, orc.equilibrium(params, 180.0) * np.array([1.02, 0.99, 1.01]))]
+    out = {}
+    with R.Governor(params, _cfg(R, N, H, max_candidates=64, probe_steps=probe)) as g:
+        g.sample_scenarios(seed, upd)
+        for mode in (R.TMA_ALWAYS, R.TMA_NEVER, R.TMA_AUTO):
+            g.set_tma(mode)
+            g.reset_stats()
+            out[mode] = [g.step(x_t, r, v_prev) for v_prev, r, x_t in cases]
+            assert g.stats()["wait_timeouts"] == 0
+    assert out[R.TMA_ALWAYS] == out[R.TMA_NEVER] == out[R.TMA_AUTO]
+    d = orc.sample_disturbances(seed, upd, N, H, inputs.DIST_AMP)
+    for (v_prev, r, x_t), (_, k, f) in zip(cases, out[R.TMA_ALWAYS]):
+        assert (k, f) == orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, v_prev, r, 12, d, nthreads=NTH)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_tma_ring_closed_loop(R, orc, params, use_graph):
+    """The closed loop alternates two scenario pairs (two tensor maps, the
+    second made when the loop first runs): the same trajectory with and
+    without the TMA, across a level change."""
+    N, H = 1024, 300
+    x0 = orc.equilibrium(params, 100.0)
+    r_seq = np.array([250.0] * 3 + [120.0] * 3)
+    runs = []
+    with R.Governor(params, _cfg(R, N, H, max_candidates=64, probe_steps=32)) as g:
+        for mode in (R.TMA_ALWAYS, R.TMA_NEVER, R.TMA_AUTO):
+            g.set_tma(mode)
+            g.reset_stats()
+            runs.append(g.closed_loop(x0, 100.0, r_seq, 9, 0, inputs.DIST_AMP, use_graph=use_graph))
+            assert g.stats()["wait_timeouts"] == 0
+    for r in runs[1:]:
+        for a, b in zip(r, runs[0]):
+            np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_tma_availability(R, params):
+    """No TMA ring where the tensor map cannot describe the array: a row
+    stride that is not a multiple of 16 bytes, or no stored binary32 array."""
+    with R.Governor(params, _cfg(R, 37, 20)) as g:
+        assert g.get_tma() == R.TMA_NEVER
+        for mode in (R.TMA_AUTO, R.TMA_ALWAYS):
+            with pytest.raises(R.RrgError):
+                g.set_tma(mode)
+        g.set_tma(R.TMA_NEVER)
+    with R.Governor(params, _cfg(R, 64, 20, precision=R.FP32, early_exit=R.EXIT_LANE,
+                                 scenarios_in_register=1)) as g:
+        assert g.get_tma() == R.TMA_NEVER
+    with R.Governor(params, _cfg(R, 64, 20)) as g:
+        assert g.get_tma() == R.TMA_AUTO
+        for bad in (-1, 3):
+            with pytest.raises(R.RrgError):
+                g.set_tma(bad)
