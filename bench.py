@@ -103,14 +103,14 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
-TRAFFIC_PER_LAUNCH = (433408 + 24614656 + 35328 + 35328) / 4
+TRAFFIC_PER_LAUNCH = (433920 + 24614656 + 35840 + 35840) / 4
 TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "a253b18870262175390aa12d856e6f9d7944a5ad"),
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "6e67ada78c68a3ad6b7b31ebb37a6e221e16a418"),
     ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "1ef24ed4a16f67f78ee586ee6229fd831974dc8e"),
     ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
-     "// Binary64 re-run of the trajectories", "f36d3f510e79581f7b795bd2c97642472e368c63"),
+     "// Binary64 re-run of the trajectories", "b60bd7819245eced7bf4956a634788d859836197"),
     ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
-     "620fdebcc8f93db38dd95e832d5fa2703a5d7ba7"),
+     "96d6b91d2c134d4c92bdc946aaa754140e564bd9"),
 )
 
 
@@ -131,7 +131,7 @@ def source_region(rel, begin, end):
 # update).  Each round reads the array once per candidate pair that is still
 # running (tile-major order; the 3.9 GB array does not fit in L2), up to 8
 # times the algorithmic bytes.
-SWEEP_TRAFFIC_64K = (3964652800 + 3377408 + 11857334784 + 501248 + 27630950400 + 606720) / 3
+SWEEP_TRAFFIC_64K = (3968265984 + 3202560 + 11859865344 + 545024 + 27633282048 + 934144) / 3
 
 
 # DRAM bytes of one adjoint_forward_kernel<float, float> launch on the adjoint
@@ -140,13 +140,13 @@ SWEEP_TRAFFIC_64K = (3964652800 + 3377408 + 11857334784 + 501248 + 27630950400 +
 # the 3.8 MB of checkpoints and lane minima stay in L2 during the launch),
 # valid while the forward kernel, its launch, the step and the Launch struct
 # are the ones profiled
-ADJ_TRAFFIC_PER_LAUNCH = 49208064 + 2304
+ADJ_TRAFFIC_PER_LAUNCH = 49214208 + 7680
 ADJ_TRAFFIC_SOURCES = (
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', '03f6ed3f12a4a64cac17959873b61107f4a29de8'),
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
     ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
-    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, 'a253b18870262175390aa12d856e6f9d7944a5ad'),
-    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', '620fdebcc8f93db38dd95e832d5fa2703a5d7ba7'),
+    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '6e67ada78c68a3ad6b7b31ebb37a6e221e16a418'),
+    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', '96d6b91d2c134d4c92bdc946aaa754140e564bd9'),
 )
 
 
@@ -186,8 +186,9 @@ def parse():
                     help="steps of the probe that pipelines the first two bisection rounds (0: off)")
     ap.add_argument("--shape", type=str, default=None,
                     help="closed loop: 'm,probe' sets the speculative bisection's shape instead of autotuning it")
-    ap.add_argument("--no-tma", action="store_true",
-                    help="closed loop, sweep: binary32 rings by per-lane asynchronous copies instead of the TMA")
+    ap.add_argument("--tma", choices=("never", "auto", "always"), default="auto",
+                    help="closed loop, sweep: which binary32 ring launches take their disturbances through the "
+                         "TMA (rrg_set_tma; auto: the library's default rule)")
     ap.add_argument("--workload", choices=("closed_loop", "sweep", "batch", "single", "adjoint"),
                     default="closed_loop")
     ap.add_argument("--instances", type=int, default=BATCH_S, help="batch: number of RG instances")
@@ -204,6 +205,12 @@ def window_start(W, K, start=WINDOW_START):
     """First timed update of the closed loop: `start`, moved so that the W
     warm-up updates fit before it and the K timed ones inside the run."""
     return max(W, min(start, RUN_UPDATES - K))
+
+
+def apply_tma(R, g, mode):
+    """rrg_set_tma where the handle has a TMA ring (otherwise it stays off)."""
+    if mode == R.TMA_NEVER or g.get_tma() != R.TMA_NEVER:
+        g.set_tma(mode)
 
 
 def shape_seconds(g, shape, states, seed, reps=3):
@@ -429,7 +436,7 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- GPU side --
-def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning, tma=True):
+def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning, tma=1):
     """The timed updates [W, T) again through the host-buffer entry points
     (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle, after
     the updates before them untimed; every call copies its inputs from and its
@@ -438,8 +445,7 @@ def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tunin
     import torch
     g2 = R.Governor(p, cfg, stream)
     g2.set_tuning(*tuning)
-    if not tma:
-        g2.set_tma(R.TMA_NEVER)
+    apply_tma(R, g2, tma)
     x, v = x0.copy(), V0
     for t in range(W):
         g2.sample_scenarios(seed, t)
@@ -593,8 +599,7 @@ def run_gpu(args):
                                precision=R.FP32_RECHECK, early_exit=R.EXIT_CANDIDATE,
                                recheck_eps_rel=RECHECK_EPS_REL, probe_steps=args.probe_steps)
     g = R.Governor(p, cfg, stream)
-    if args.no_tma:
-        g.set_tma(R.TMA_NEVER)
+    apply_tma(R, g, TMA_MODES.index(args.tma))
     x0, _ = g.equilibrium(V0)
     # the speculative bisection's shape (tree width, probe length) by the
     # library's autotuner; every shape gives Alg. 1's kappa
@@ -664,8 +669,7 @@ def run_gpu(args):
     # events around every rollout launch (the roofline's kernel duration)
     gd = R.Governor(p, cfg, stream)
     gd.set_tuning(tune_m, tune_probe)
-    if args.no_tma:
-        gd.set_tma(R.TMA_NEVER)
+    apply_tma(R, gd, TMA_MODES.index(args.tma))
     dd_v, dd_k = torch.zeros_like(d_v), torch.zeros_like(d_k)
     dd_f, dd_x = torch.zeros_like(d_f), torch.zeros_like(d_x)
     R.rrg_closed_loop_dev(gd.h, x0, V0, d_r, S0, seed, 0, amp, False, dd_v, dd_k, dd_f, dd_x)
@@ -741,7 +745,7 @@ def run_gpu(args):
         e2e = None
         if not args.no_e2e:
             e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, S0, T, flush, kap_dev, (tune_m, tune_probe),
-                          not args.no_tma)
+                          TMA_MODES.index(args.tma))
 
         # plain FP64 bisection on the same GPU over the same timed updates,
         # timed the same way (CUDA events around each update, L2 flushed in
@@ -1316,6 +1320,7 @@ def adjoint_cpu(p, x_t, v_prev, r, N, H, seconds, gpu_argmin):
 # ------------------------------------------------------------------ sweep --
 SWEEP_METRIC = "trajectory-steps/s vs scenario count (large sweep, FP32 + FP64 recheck)"
 PAIRING_NAMES = ("never", "filled", "always")
+TMA_MODES = ("never", "auto", "always")
 TMA_NAMES = ("per-lane cp.async", "TMA for ring launches of >= 24 warps per SM, per-lane cp.async below",
              "TMA for every ring launch")
 
@@ -1403,8 +1408,7 @@ def run_sweep(args):
             pairing_ms = dict(zip(PAIRING_NAMES, ms_modes))
         else:
             g.set_pairing(PAIRING_NAMES.index(args.pairing))
-        if args.no_tma:
-            g.set_tma(R.TMA_NEVER)
+        apply_tma(R, g, TMA_MODES.index(args.tma))
         d_x = torch.tensor(x_t, dtype=torch.float64, device=dev)
         d_r = torch.tensor([r], dtype=torch.float64, device=dev)
         d_vp = torch.tensor([v_prev], dtype=torch.float64, device=dev)
