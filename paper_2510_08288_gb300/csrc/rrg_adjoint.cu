@@ -249,6 +249,58 @@ adjoint_forward_kernel(const Launch L, const DT* __restrict__ d, int checkpoint,
   double* ck = ckpt + (static_cast<size_t>(i) * N + k) * nseg * 3;
   T smin = C.y_scale * (z_sm - z_ca) + C.s_off;
   int arg = 0;
+  int next_ck = 0;  // the next step whose state is saved
+  if constexpr (sizeof(T) == 4 && sizeof(DT) == 4) {
+    // binary32 from the stored binary32 array: the rollouts' shared-memory
+    // ring, one asynchronous copy per lane, component and step, RRG_RING_DEPTH
+    // steps ahead (a warp running its chain alone issues its steps in order,
+    // and the register ring's loads and index arithmetic sit between them)
+    constexpr int D = RRG_RING_DEPTH;
+    __shared__ float sring[D * 3 * 128];
+    const int bd = blockDim.x;
+    float* my = sring + threadIdx.x;
+    const DT* pf = d + k;  // the next step to fetch
+#pragma unroll 1
+    for (int u = 0; u < D; ++u) {
+      if (u < H) {
+        cp_async4(my + (3 * u) * bd, pf);
+        cp_async4(my + (3 * u + 1) * bd, pf + HN);
+        cp_async4(my + (3 * u + 2) * bd, pf + 2 * HN);
+      }
+      cp_async_commit();
+      pf += N;
+    }
+    int slot = 0;
+#pragma unroll 4
+    for (int j = 0; j < H; ++j) {
+      cp_async_wait<D - 1>();
+      float* e = my + (3 * slot) * bd;
+      const float e0 = e[0], e1 = e[bd], e2 = e[2 * bd];
+      if (j == next_ck) {
+        double* c = ck + (j / checkpoint) * 3;
+        c[0] = static_cast<double>(z_ca) + r_ca;
+        c[1] = static_cast<double>(z_w) + r_w;
+        c[2] = static_cast<double>(z_sm) + r_sm;
+        next_ck += checkpoint;
+      }
+      rk4_step_fast<T>(K, C, S, z_ca, z_w, z_sm, w_abs, e0, e1, e2);
+      // the slot is free once its values are in registers: step j + D
+      if (j + D < H) {
+        cp_async4(e, pf);
+        cp_async4(e + bd, pf + HN);
+        cp_async4(e + 2 * bd, pf + 2 * HN);
+      }
+      cp_async_commit();
+      pf += N;
+      slot = (slot + 1) & (D - 1);
+      const T s = C.y_scale * (z_sm - z_ca) + C.s_off;
+      if (s < smin) { smin = s; arg = j + 1; }
+    }
+    cp_async_wait<0>();  // nothing in flight into the ring when the lane ends
+    lane_min[static_cast<size_t>(i) * N + k] = static_cast<double>(smin);
+    lane_arg[static_cast<size_t>(i) * N + k] = arg;
+    return;
+  }
   auto at = [&](int j) { return static_cast<size_t>(j < H ? j : H - 1) * N + k; };
   T ring[kFwdRing][3];
 #pragma unroll
@@ -258,7 +310,6 @@ adjoint_forward_kernel(const Launch L, const DT* __restrict__ d, int checkpoint,
     ring[u][1] = static_cast<T>(d[HN + o]);
     ring[u][2] = static_cast<T>(d[2 * HN + o]);
   }
-  int next_ck = 0;  // the next step whose state is saved
   for (int j0 = 0; j0 < H; j0 += kFwdRing) {
 #pragma unroll
     for (int u = 0; u < kFwdRing; ++u) {
