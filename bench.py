@@ -140,9 +140,9 @@ SWEEP_TRAFFIC_64K = (3968265984 + 3202560 + 11859865344 + 545024 + 27633282048 +
 # the 3.8 MB of checkpoints and lane minima stay in L2 during the launch),
 # valid while the forward kernel, its launch, the step and the Launch struct
 # are the ones profiled
-ADJ_TRAFFIC_PER_LAUNCH = 49214208 + 7680
+ADJ_TRAFFIC_PER_LAUNCH = 49196800 + 4864
 ADJ_TRAFFIC_SOURCES = (
-    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', '03f6ed3f12a4a64cac17959873b61107f4a29de8'),
+    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', 'b726a6442e28e5a458abb23e2651863f42659404'),
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
     ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
     ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '6e67ada78c68a3ad6b7b31ebb37a6e221e16a418'),
