@@ -842,6 +842,18 @@ BATCH_S, BATCH_M, BATCH_ROUNDS, BATCH_SEED = 256, 32, 3, 2
 BATCH_METRIC = "RG updates/s (instance updates, batched) & trajectory-steps/s; FP32 + FP64 recheck"
 
 
+BATCH_PAIR_VARIANT = 8   # warp tiles of two candidates per thread
+
+
+def batch_kernel_name(variant):
+    """The rollout kernel of a batch variant (index, lanes per tile, prefetch)."""
+    if variant[0] == BATCH_PAIR_VARIANT:
+        return "batch_rollout_warp_pair_kernel<%d> (two candidates per thread)" % variant[2]
+    if variant[1] == 32:
+        return "batch_rollout_warp_kernel<%d>" % variant[2]
+    return "batch_rollout_kernel<%d, %d>" % (variant[1], variant[2])
+
+
 def batch_config(S, W, K, variant):
     return {"workload": "batched instances on FC3: %d independent RG problems advanced together per step "
                         "(closed loop with plants), scenario counts log-uniform on [64, 8192], horizons "
@@ -1047,8 +1059,7 @@ def run_batch(args):
         "trajectory_steps_per_s": {"executed": st["lane_steps"] / secs, "executed_per_step": st["lane_steps"] / K},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": frac_of(achieved, peak), "traffic": None,
-                     "kernel": ("batch_rollout_warp_kernel<%d>" % variant[2]) if variant[1] == 32
-                               else ("batch_rollout_kernel<%d, %d>" % (variant[1], variant[2])),
+                     "kernel": batch_kernel_name(variant),
                      "avg_launch_ms": avg_roll_ms, "launches": st2["timed_rollouts"],
                      "timing": "%d direct-launch updates after the timed ones" % K2,
                      "flops_per_traj_step": FLOPS_PER_STEP,

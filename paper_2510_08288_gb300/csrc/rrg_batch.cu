@@ -127,16 +127,17 @@ __global__ void batch_sample_kernel(const BLaunch B, uint64_t seed, uint64_t bas
   }
 }
 
-// Tile list of the next round: instance order[o] contributes m x ceil(N / tile)
-// tiles; block-wide inclusive scan (blockDim = kDecideThreads >= S).
-__device__ void build_tiles(const BLaunch& B, int tile) {
+// Tile list of the next round: instance order[o] contributes ceil(m / rows) x
+// ceil(N / tile) tiles (rows = 2: two candidate slots per tile); block-wide
+// inclusive scan (blockDim = kDecideThreads >= S).
+__device__ void build_tiles(const BLaunch& B, int tile, int rows) {
   __shared__ int sc[kDecideThreads];
   const int o = threadIdx.x;
   int cnt = 0;
   if (o < B.c.S) {
     const int s = B.order[o];
     const BState& st = B.st[s];
-    cnt = (st.done ? 0 : st.m) * ((B.inst[s].N + tile - 1) / tile);
+    cnt = (st.done ? 0 : (st.m + rows - 1) / rows) * ((B.inst[s].N + tile - 1) / tile);
   }
   sc[o] = cnt;
   __syncthreads();
@@ -243,7 +244,7 @@ __device__ void btree_walk(BState& st, const int32_t* ok, int m, int n_bisect) {
 // read at r[t * S + s] (t = the loop counter, 0 without one).
 __global__ void __launch_bounds__(kDecideThreads)
 batch_begin_kernel(const BLaunch B, const double* __restrict__ d_x, const double* __restrict__ d_r,
-                   const double* __restrict__ d_vp, uint64_t base, int tile) {
+                   const double* __restrict__ d_vp, uint64_t base, int tile, int rows) {
   const int s = threadIdx.x;
   const unsigned long long t = B.t_dev ? *B.t_dev : 0ull;
   if (s < B.c.S) {
@@ -279,7 +280,7 @@ batch_begin_kernel(const BLaunch B, const double* __restrict__ d_x, const double
       st.m = ok ? grid_points(kap, B.c.M) : 0;
   }
   __syncthreads();
-  build_tiles(B, tile);
+  build_tiles(B, tile, rows);
 }
 
 // v_i, candidate constants and the steady-state check of one (instance, slot).
@@ -300,6 +301,42 @@ __global__ void batch_prepare_kernel(const BLaunch B) {
   B.cand_ss[slot] = ok;
   B.cand_dead[slot] = ok ? 0 : 1;
   B.cand_min[slot] = dkey(inf_v<double>());
+}
+
+// A lane's outcome for candidate slot `slot` (called by every thread of the
+// warp): classified against the recheck band (an undecided lane is listed for
+// the binary64 recheck unless the candidate has already failed), then the
+// warp's AND of the flags, min slack and step count folded into the slot's.
+__device__ __forceinline__ void batch_reduce(const BLaunch& B, size_t slot, int k, bool active, float smin,
+                                             unsigned steps, int jlast, float eps,
+                                             volatile int32_t* dead) {
+  bool lane_ok = true, uncertain = false;
+  float contrib = inf_v<float>();
+  if (active) {
+    if (smin >= eps) {
+      contrib = smin;
+    } else if (smin < -eps) {
+      lane_ok = false;
+      contrib = smin;
+    } else {
+      uncertain = true;
+    }
+  }
+  if (uncertain && *dead == 0) {
+    const uint32_t e = atomicAdd(B.recheck_count, 1u);
+    if (e < B.recheck_cap) {
+      B.recheck_list[e] = make_uint2(static_cast<uint32_t>(slot), static_cast<uint32_t>(k));
+      B.recheck_jlast[e] = static_cast<uint32_t>(jlast);
+    }
+  }
+  const bool all_ok = __all_sync(0xffffffffu, lane_ok);
+  const float wmin = warp_min<float>(contrib);
+  const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
+  if ((threadIdx.x & 31) == 0) {
+    if (!all_ok) B.cand_ok[slot] = 0;
+    if (wmin < inf_v<float>()) atomicMin(B.cand_min + slot, dkey(static_cast<double>(wmin)));
+    if (wsteps) atomicAdd(&B.stats->lane_steps, static_cast<unsigned long long>(wsteps));
+  }
 }
 
 // One tile: lanes k of candidate slot (s, i), binary32 rollouts classified
@@ -336,33 +373,7 @@ __device__ __forceinline__ void batch_tile(const BLaunch& B, int s, int i, int k
                                &steps, &end, eps, &jlast);
     if (cand_stop && smin < thr) *dead = 1;
   }
-  bool lane_ok = true, uncertain = false;
-  float contrib = inf_v<float>();
-  if (active) {
-    if (smin >= eps) {
-      contrib = smin;
-    } else if (smin < -eps) {
-      lane_ok = false;
-      contrib = smin;
-    } else {
-      uncertain = true;
-    }
-  }
-  if (uncertain && *dead == 0) {
-    const uint32_t e = atomicAdd(B.recheck_count, 1u);
-    if (e < B.recheck_cap) {
-      B.recheck_list[e] = make_uint2(static_cast<uint32_t>(slot), static_cast<uint32_t>(k));
-      B.recheck_jlast[e] = static_cast<uint32_t>(jlast);
-    }
-  }
-  const bool all_ok = __all_sync(0xffffffffu, lane_ok);
-  const float wmin = warp_min<float>(contrib);
-  const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
-  if ((threadIdx.x & 31) == 0) {
-    if (!all_ok) B.cand_ok[slot] = 0;
-    if (wmin < inf_v<float>()) atomicMin(B.cand_min + slot, dkey(static_cast<double>(wmin)));
-    if (wsteps) atomicAdd(&B.stats->lane_steps, static_cast<unsigned long long>(wsteps));
-  }
+  batch_reduce(B, slot, k, active, smin, steps, jlast, eps, dead);
 }
 
 // Persistent rollout: each CTA takes tiles from the queue until none is left.
@@ -435,6 +446,85 @@ __global__ void __launch_bounds__(128) batch_rollout_warp_kernel(const BLaunch B
   }
 }
 
+// A warp tile of two candidate slots, 2p and 2p + 1 (the second absent when
+// the round has an odd count), of instance s: each lane runs both
+// trajectories of its scenario through run_lane_pair (one load of each
+// disturbance, two independent step chains), or the one still running
+// through run_lane, and reduces each slot as batch_tile does.  The prefetch
+// depth is half the single lane's: each step issues two trajectories'
+// instructions.  Called by all 32 lanes; returns are warp-uniform.
+template <int PF>
+__device__ __forceinline__ void batch_tile_pair(const BLaunch& B, int s, int p, int k) {
+  const BInst I = B.inst[s];
+  const int m = B.st[s].m;
+  const size_t slotA = static_cast<size_t>(s) * B.c.M + 2 * p;
+  const bool hasB = 2 * p + 1 < m;
+  const size_t slotB = hasB ? slotA + 1 : slotA;
+  volatile int32_t* deadA = B.cand_dead + slotA;
+  volatile int32_t* deadB = B.cand_dead + slotB;
+  const bool cand_stop = B.c.early_exit == RRG_EXIT_CANDIDATE;
+  bool runA = B.cand_ss[slotA] != 0, runB = hasB && B.cand_ss[slotB] != 0;
+  if (cand_stop) {
+    const int da = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 && runA ? *deadA : 0, 0);
+    const int db = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 && runB ? *deadB : 0, 0);
+    runA = runA && !da;
+    runB = runB && !db;
+  }
+  if (!runA && !runB) return;
+  const bool active = k < I.N;
+  const float eps = static_cast<float>(B.c.eps_abs);
+  const float thr = B.c.early_exit != RRG_EXIT_NONE ? -eps : -inf_v<float>();
+  float sm[2] = {inf_v<float>(), inf_v<float>()};
+  unsigned st[2] = {0u, 0u};
+  int jl[2] = {-1, -1}, en[2] = {LANE_REACHED_END, LANE_REACHED_END};
+  if (active) {
+    const BState& bs = B.st[s];
+    const double p_atm = B.params[P_P_ATM];
+    const RhsC<float> CA = B.cand_c32[slotA], CB = B.cand_c32[slotB];
+    float za[4], zb[4];
+    start_state<float>(CA, bs.x, p_atm, za[0], za[1], za[2], za[3]);
+    start_state<float>(CB, bs.x, p_atm, zb[0], zb[1], zb[2], zb[3]);
+    const float* d = (bs.cur ? B.d32b : B.d32) + I.off;
+    const float dt = static_cast<float>(B.c.dt);
+    if (runA && runB) {
+      run_lane_pair<float, PF>(B.u32, CA, CB, d, k, I.N, I.H, I.H, za, zb, dt, thr, eps,
+                               cand_stop ? deadA : nullptr, cand_stop ? deadB : nullptr, sm, st, en, jl);
+    } else if (runA) {
+      sm[0] = run_lane<float, PF>(B.u32, CA, d, k, I.N, I.H, 0, I.H, za[0], za[1], za[2], za[3],
+                                  inf_v<float>(), dt, thr, cand_stop ? deadA : nullptr, &st[0], &en[0], eps,
+                                  &jl[0]);
+    } else {
+      sm[1] = run_lane<float, PF>(B.u32, CB, d, k, I.N, I.H, 0, I.H, zb[0], zb[1], zb[2], zb[3],
+                                  inf_v<float>(), dt, thr, cand_stop ? deadB : nullptr, &st[1], &en[1], eps,
+                                  &jl[1]);
+    }
+    if (cand_stop && runA && sm[0] < thr) *deadA = 1;
+    if (cand_stop && runB && sm[1] < thr) *deadB = 1;
+  }
+  if (runA) batch_reduce(B, slotA, k, active, sm[0], st[0], jl[0], eps, deadA);
+  if (runB) batch_reduce(B, slotB, k, active, sm[1], st[1], jl[1], eps, deadB);
+}
+
+// Warp tiles of candidate pairs (the tile list counts ceil(m / 2) pairs per
+// instance and scenario block).
+template <int PF>
+__global__ void __launch_bounds__(128) batch_rollout_warp_pair_kernel(const BLaunch B) {
+  const uint32_t total = B.queue[1];
+  const int lane = static_cast<int>(threadIdx.x & 31);
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(B.queue, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) return;
+    int s = 0, p = 0, b = 0;
+    if (lane == 0) tile_of(B, t, 32, &s, &p, &b);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    p = __shfl_sync(0xffffffffu, p, 0);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    batch_tile_pair<PF>(B, s, p, b * 32 + lane);
+  }
+}
+
 // Binary64 re-run (disturbances regenerated from the Philox counters) over
 // steps 0..jlast of each listed lane.
 __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
@@ -477,7 +567,7 @@ __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
 // single-problem search), the next round's candidates and tiles; `final`
 // also writes every instance's result at index t * S + s.
 __global__ void __launch_bounds__(kDecideThreads)
-batch_decide_kernel(const BLaunch B, int final, int tile, double* __restrict__ v_out,
+batch_decide_kernel(const BLaunch B, int final, int tile, int rows, double* __restrict__ v_out,
                     double* __restrict__ k_out, int32_t* __restrict__ f_out) {
   const int s = threadIdx.x;
   const int M = B.c.M;
@@ -535,7 +625,7 @@ batch_decide_kernel(const BLaunch B, int final, int tile, double* __restrict__ v
     }
   }
   __syncthreads();
-  build_tiles(B, tile);
+  build_tiles(B, tile, rows);
 }
 
 // Simulated plants: x_{t+1} = RK4(x_t, v_t) + d_plant(seed + s, update),
@@ -586,17 +676,19 @@ __global__ void batch_loop_init_kernel(const BLaunch B, const double* __restrict
 }
 
 // Rollout variants the autotuner chooses from: threads (= scenario lanes)
-// per tile, and the disturbance prefetch depth.
+// per tile, the disturbance prefetch depth, and candidate slots per tile.
 struct Variant {
-  int tile, pf;
+  int tile, pf, rows;
   void (*kernel)(const BLaunch);
 };
-// tile = 32: warp tiles (CTAs of 4 warps, no CTA barrier)
+// tile = 32: warp tiles (CTAs of 4 warps, no CTA barrier); rows = 2: two
+// candidates per thread
 const Variant kVariants[RRG_BATCH_VARIANTS] = {
-    {64, 8, batch_rollout_kernel<64, 8>},   {64, 16, batch_rollout_kernel<64, 16>},
-    {128, 8, batch_rollout_kernel<128, 8>}, {128, 16, batch_rollout_kernel<128, 16>},
-    {256, 8, batch_rollout_kernel<256, 8>}, {256, 16, batch_rollout_kernel<256, 16>},
-    {32, 8, batch_rollout_warp_kernel<8>},  {32, 16, batch_rollout_warp_kernel<16>},
+    {64, 8, 1, batch_rollout_kernel<64, 8>},   {64, 16, 1, batch_rollout_kernel<64, 16>},
+    {128, 8, 1, batch_rollout_kernel<128, 8>}, {128, 16, 1, batch_rollout_kernel<128, 16>},
+    {256, 8, 1, batch_rollout_kernel<256, 8>}, {256, 16, 1, batch_rollout_kernel<256, 16>},
+    {32, 8, 1, batch_rollout_warp_kernel<8>},  {32, 16, 1, batch_rollout_warp_kernel<16>},
+    {32, 8, 2, batch_rollout_warp_pair_kernel<8>},
 };
 constexpr int block_threads(int tile) { return tile == 32 ? 128 : tile; }
 
@@ -791,8 +883,8 @@ int enqueue_search_all(rrg_batch_ctx* h, const double* d_x, const double* d_r, c
                        uint64_t base, double* v_out, double* k_out, int32_t* f_out) {
   const BLaunch& B = h->B;
   const int S = B.c.S;
-  const int tile = kVariants[h->variant].tile;
-  batch_begin_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, d_x, d_r, d_vp, base, tile);
+  const int tile = kVariants[h->variant].tile, rows = kVariants[h->variant].rows;
+  batch_begin_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, d_x, d_r, d_vp, base, tile, rows);
   BCK(cudaGetLastError());
   h->launches++;
   const int rounds = batch_rounds(h);
@@ -805,7 +897,7 @@ int enqueue_search_all(rrg_batch_ctx* h, const double* d_x, const double* d_r, c
     batch_recheck_kernel<<<2 * h->sms, 64, 0, h->stream>>>(B);
     BCK(cudaGetLastError());
     const int final = r == rounds - 1;
-    batch_decide_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, final, tile, v_out, k_out, f_out);
+    batch_decide_kernel<<<1, kDecideThreads, 0, h->stream>>>(B, final, tile, rows, v_out, k_out, f_out);
     BCK(cudaGetLastError());
     h->launches += 3;
     h->rounds++;

@@ -567,7 +567,7 @@ def rrg_alu_peaks():
 
 
 # ---------------------------------------------------------------- batched --
-BATCH_VARIANTS = 8
+BATCH_VARIANTS = 9
 BATCH_MAX_WIDTHS = 24
 
 

@@ -258,3 +258,40 @@ def test_batch_width_autotune_keeps_every_result(R, orc, params):
     with R.BatchGovernor(params, _cfg(R, 8, R.SEARCH_KSECTION), b["N"], b["H"]) as g:
         with pytest.raises(R.RrgError):
             g.set_width(4)
+
+
+PAIR_VARIANT = 8   # warp tiles of two candidates per thread
+
+
+@pytest.mark.parametrize("width", [1, 3, 7])
+@pytest.mark.parametrize("kind", ["spec", "ksection"])
+def test_batch_pair_tiles_match_single_tiles_and_oracle(R, orc, params, width, kind):
+    """The paired warp-tile variant (candidate slots 2p and 2p + 1 in one
+    thread; an odd round leaves the last pair with one) gives every
+    instance's kappa and flags of the single warp tiles and of the oracle,
+    for the speculative bisection at odd tree widths and for the k-section
+    (odd grid 7)."""
+    S, seed, upd = 9, 7, 3
+    b, x = _problem(orc, params, S, 5, N_lo=1, N_hi=300, H_lo=1, H_hi=250)
+    if kind == "spec":
+        cfg = _cfg(R, 64, R.SEARCH_SPEC_BISECT, n_bisect=12, recheck_eps_rel=1e-6)
+    else:
+        cfg = _cfg(R, 7, R.SEARCH_KSECTION, recheck_eps_rel=1e-6)
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        if kind == "spec":
+            g.set_width(width)
+        out = {}
+        for var in (7, PAIR_VARIANT):
+            g.set_variant(var)
+            out[var] = g.step(x, b["r"], b["v_prev"], seed, upd)
+    for a, c in zip(out[7], out[PAIR_VARIANT]):
+        np.testing.assert_array_equal(a, c)
+    v, k, f = out[PAIR_VARIANT]
+    for s in range(S):
+        N, H = int(b["N"][s]), int(b["H"][s])
+        d = orc.sample_disturbances(seed + s, upd, N, H, inputs.DIST_AMP)
+        if kind == "spec":
+            k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x[s], b["v_prev"][s], b["r"][s], 12, d)
+        else:
+            k_o, f_o = _oracle(orc, params, "ksection", x[s], b["v_prev"][s], b["r"][s], d, N, H, 7)
+        assert (k[s], f[s]) == (k_o, f_o), s
