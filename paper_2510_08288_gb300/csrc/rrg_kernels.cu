@@ -838,6 +838,10 @@ __device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* slo
                           const int32_t* cand_ok, uint32_t* bits, int* len,
                           int32_t* visited = nullptr, const uint32_t* expect = nullptr,
                           bool* diverged = nullptr) {
+  // the walk's state in registers, written back once: each level's decision
+  // would otherwise wait on the previous level's stores to global memory
+  double kap = s->kappa, lo = s->lo, hi = s->hi, kopt = s->kappa_opt;
+  int iter = s->iter, any = s->any, done = s->done;
   int n = 1;
   uint32_t b = 0;
   int l = 0;
@@ -846,8 +850,8 @@ __device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* slo
     const int slot = slot_map[n];
     if (slot < 0) break;  // cannot happen: the path only visits valid nodes
     if (visited) visited[lev] = slot;
-    const double k = s->kappa;
-    s->iter += 1;
+    const double k = kap;
+    iter += 1;
     ++l;
     const bool ok = cand_ok[slot] != 0;
     if (expect && ok != (((*expect >> lev) & 1u) != 0)) {
@@ -856,20 +860,42 @@ __device__ void walk_tree(SearchState* s, const SearchCfg& c, const int32_t* slo
     }
     if (ok) {
       b |= 1u << lev;
-      s->kappa_opt = k;
-      s->any = 1;
-      if (k == 1.0) { s->done = 1; break; }
-      s->lo = k;
+      kopt = k;
+      any = 1;
+      if (k == 1.0) { done = 1; break; }
+      lo = k;
       n = 2 * n + 1;
     } else {
-      s->hi = k;
+      hi = k;
       n = 2 * n;
     }
-    s->kappa = __dmul_rn(__dadd_rn(s->lo, s->hi), 0.5);
-    if (s->iter >= c.n_bisect) { s->done = 1; break; }
+    kap = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    if (iter >= c.n_bisect) { done = 1; break; }
   }
+  s->kappa = kap; s->lo = lo; s->hi = hi; s->kappa_opt = kopt;
+  s->iter = iter; s->any = any; s->done = done;
   *bits = b;
   *len = l;
+}
+
+// The walks' inputs, staged in shared memory by the whole block before the
+// deciding thread walks: the slot of each heap node of the round's tree (and
+// of the pipelined second tree) and the slots' outcomes, so the walk's levels
+// do not chain dependent global loads.
+struct WalkStage {
+  int32_t map0[kMaxTreeNodes];
+  int32_t map1[kMaxTreeNodes];
+  int32_t ok[2 * RRG_MAX_CANDIDATES];
+};
+__device__ void stage_walk(const Launch& L, WalkStage& w, bool second) {
+  const SearchState* s = L.st;
+  const int n0 = 1 << s->depth;
+  for (int n = threadIdx.x; n < n0; n += blockDim.x) w.map0[n] = s->slot_of_node[n];
+  if (second) {
+    const int n1 = 1 << s->depth1;
+    for (int n = threadIdx.x; n < n1; n += blockDim.x) w.map1[n] = s->slot_of_node1[n];
+  }
+  for (int i = threadIdx.x; i < 2 * L.scfg.m_cap; i += blockDim.x) w.ok[i] = L.cand_ok[i];
 }
 
 __device__ void set_segments(SearchState* s, int mode0, int count0, int base0, int mode1,
@@ -900,12 +926,12 @@ __device__ int first_round(SearchState* s, const SearchCfg& c, double* cand_kapp
 
 // Decides from the evaluated round and prepares the next; returns next m.
 __device__ int next_round(SearchState* s, const SearchCfg& c, double* cand_kappa,
-                          const int32_t* cand_ok) {
+                          const int32_t* cand_ok, const int32_t* slot_map) {
   const int m = s->m;
   if (c.search == RRG_SEARCH_BISECT || c.search == RRG_SEARCH_SPEC_BISECT) {
     uint32_t bits;
     int len;
-    walk_tree(s, c, s->slot_of_node, s->depth, cand_ok, &bits, &len);
+    walk_tree(s, c, slot_map, s->depth, cand_ok, &bits, &len);
     s->round += 1;
     if (s->done) return 0;
     s->depth = choose_depth(s, c);
@@ -1038,7 +1064,9 @@ search_begin_kernel(const Launch L, const double* __restrict__ d_x, const double
 __global__ void __launch_bounds__(kSearchThreads)
 search_mid_kernel(const Launch L) {
   SearchState* s = L.st;
+  __shared__ WalkStage W;
   if (threadIdx.x == 0) g_tree_req.pending = 0;
+  stage_walk(L, W, false);
   __syncthreads();
   if (threadIdx.x == 0) {
     int m1 = 0;
@@ -1048,7 +1076,7 @@ search_mid_kernel(const Launch L) {
       restore_walk_start(s);
       uint32_t bits;
       int len;
-      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len, s->cont_slot);
+      walk_tree(s, L.scfg, W.map0, s->depth, W.ok, &bits, &len, s->cont_slot);
       s->prov_bits = bits;
       s->prov_len = len;
       s->prov_done = s->done;
@@ -1072,7 +1100,9 @@ search_mid_kernel(const Launch L) {
 __global__ void __launch_bounds__(kSearchThreads)
 search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
   SearchState* s = L.st;
+  __shared__ WalkStage W;
   if (threadIdx.x == 0) g_tree_req.pending = 0;
+  stage_walk(L, W, s->probe != 0);
   __syncthreads();
   if (threadIdx.x == 0) {
     int m = 0;
@@ -1086,11 +1116,10 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
       int len;
       bool diverged = false;
       const uint32_t expect = s->prov_bits;
-      walk_tree(s, L.scfg, s->slot_of_node, s->depth, L.cand_ok, &bits, &len, nullptr, &expect,
-                &diverged);
+      walk_tree(s, L.scfg, W.map0, s->depth, W.ok, &bits, &len, nullptr, &expect, &diverged);
       s->round += 1;
       if (!diverged && !s->done) {
-        walk_tree(s, L.scfg, s->slot_of_node1, s->depth1, L.cand_ok, &bits, &len);
+        walk_tree(s, L.scfg, W.map1, s->depth1, W.ok, &bits, &len);
         s->round += 1;
       } else if (diverged) {
         L.stats->repairs += 1ull;
@@ -1100,7 +1129,7 @@ search_next_kernel(const Launch L, double* v_t, double* kappa, int32_t* flags) {
         m = build_tree(s, 0, 0, s->depth);
       }
     } else if (!s->done) {
-      m = next_round(s, L.scfg, L.cand_kappa, L.cand_ok);
+      m = next_round(s, L.scfg, L.cand_kappa, W.ok, W.map0);
     }
     if (s->done) {
       m = 0;
