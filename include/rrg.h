@@ -421,6 +421,16 @@ RRG_API int rrg_get_pairing(rrg_handle h, int32_t *mode);
 RRG_API int rrg_set_tma(rrg_handle h, int mode);
 RRG_API int rrg_get_tma(rrg_handle h, int32_t *mode);
 
+/* Test support for the device-side failure handling (0, the default, in
+ * normal use).  RRG_INJECT_TMA_NO_COPY: the TMA ring issues no copies, so each
+ * warp's first chunk wait runs out (after at most 0.1 s): the warp counts one
+ * timeout in rrg_stats.wait_timeouts, its running lanes report a violation
+ * (no candidate is admissible on data that did not arrive), the kernel
+ * returns and the handle stays usable.  Waits for the stream and discards the
+ * cached closed-loop graph; RRG_EINVAL for unknown flags. */
+#define RRG_INJECT_TMA_NO_COPY 1
+RRG_API int rrg_set_injection(rrg_handle h, int flags);
+
 /* Times 1 + repeats updates of the handle's search (rrg_autotune's
  * protocol: current scenarios, host inputs x_t[3], r_t, v_prev, CUDA events
  * on the handle's stream) in each pairing mode, keeps the fastest and returns

@@ -32,6 +32,7 @@ struct rrg_ctx {
   CUtensorMap tmap[2];
   bool tma_ok = false;
   int tma_mode = RRG_TMA_AUTO;  // rrg_set_tma
+  int inject = 0;               // rrg_set_injection
   Launch L{};
   // device memory
   double* params_dev = nullptr;
@@ -210,6 +211,7 @@ void fill_launch(rrg_ctx* h) {
   L.pair = h->pair;
   L.tmap = h->tma_ok && h->tma_mode != RRG_TMA_NEVER ? h->tmap : nullptr;
   L.tma = h->tma_mode;
+  L.inject = h->inject;
   L.N = c.n_scenarios;
   L.H = c.horizon;
   L.precision = c.precision;
@@ -1479,6 +1481,20 @@ int rrg_set_tma(rrg_handle h, int mode) {
   h->tma_mode = mode;
   fill_launch(h);
   if (h->cl_exec) {  // the cached closed-loop graph holds the old kernels
+    cudaGraphExecDestroy(h->cl_exec);
+    h->cl_exec = nullptr;
+  }
+  return RRG_OK;
+}
+
+int rrg_set_injection(rrg_handle h, int flags) {
+  if (!h) return RRG_EINVAL;
+  if (flags & ~RRG_INJECT_TMA_NO_COPY) return set_err(h, RRG_EINVAL, "unknown injection flags 0x%x", flags);
+  DeviceGuard g(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  h->inject = flags;
+  fill_launch(h);
+  if (h->cl_exec) {
     cudaGraphExecDestroy(h->cl_exec);
     h->cl_exec = nullptr;
   }

@@ -180,6 +180,7 @@ struct Launch {
   // rings then use per-lane asynchronous copies
   const CUtensorMap* tmap;
   int tma;                      // RRG_TMA_*: which ring launches take the TMA
+  int inject;                   // RRG_INJECT_* test switches (0 in normal use)
 };
 
 // Folds the FC3 parameter vector into the constants the kernels use

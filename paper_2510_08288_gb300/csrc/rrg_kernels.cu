@@ -404,7 +404,8 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
     uint64_t* bars = reinterpret_cast<uint64_t*>(rrg_dyn_smem + (kRollThreads / 32) * 2 * kTmaStageBytes) +
                      2 * wid;
     const bool lane_runs = active && final_lane;
-    const T s_out = run_lane_tma(K, C, L.st->buf ? tm1 : tm0, k & ~31, lane_runs, j0, j_end, q_ca, w, q_sm,
+    const void* tm = (L.inject & RRG_INJECT_TMA_NO_COPY) ? nullptr : (L.st->buf ? tm1 : tm0);
+    const T s_out = run_lane_tma(K, C, tm, k & ~31, lane_runs, j0, j_end, q_ca, w, q_sm,
                                  w_abs, smin0, static_cast<T>(L.dt), thr, cand_stop ? dead : nullptr,
                                  cand_stop ? dead : nullptr, &steps, &end, band, &jlast, stages, bars,
                                  &L.stats->wait_timeouts);

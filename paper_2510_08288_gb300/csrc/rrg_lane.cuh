@@ -592,7 +592,7 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
 // company (inactive scenario, or finished in an earlier segment).
 //
 // Waits are bounded.  A stage whose copy has not landed after kTmaWaitLimit
-// polls ends the loop for the whole warp: the call counts one timeout in
+// polls or kTmaWaitNs of the global timer ends the loop for the whole warp: the call counts one timeout in
 // *timeouts and every lane still running reports a violation (min slack
 // -inf, so no candidate is accepted on data that did not arrive).  Before
 // returning, the warp waits (bounded again) for every copy it issued, so
@@ -606,7 +606,8 @@ __device__ __forceinline__ float run_lane_ring(const RhsU<float>& K, const RhsC<
 constexpr int kTmaChunk = RRG_TMA_CHUNK;
 constexpr int kTmaStageFloats = 3 * kTmaChunk * 32;
 constexpr unsigned kTmaStageBytes = kTmaStageFloats * 4u;
-constexpr int kTmaWaitLimit = 1 << 22;
+constexpr int kTmaWaitLimit = 1 << 22;          // polls
+constexpr unsigned long long kTmaWaitNs = 100000000ull;  // and at most 0.1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -637,16 +638,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Polls until the phase of the given parity has completed, at most
-// kTmaWaitLimit times; false if it has not.
+// kTmaWaitLimit times and kTmaWaitNs of the global timer; false if it has
+// not.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kTmaWaitLimit; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int it = 1; it < kTmaWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 0 && global_ns() - t0 > kTmaWaitNs) return false;
+  }
   return false;
 }
 // Chunk copy: box (x = k0, y = j, z = 0) of the tensor map into `dst`,
-// completion counted on `bar` (lane 0 only).
+// completion counted on `bar` (lane 0 only).  tmap == nullptr (the test
+// switch RRG_INJECT_TMA_NO_COPY): nothing is issued, so the stage's wait runs
+// out.
 __device__ __forceinline__ void tma_chunk(const void* tmap, uint32_t dst, uint32_t bar, int k0, int j) {
+  if (tmap == nullptr) return;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTmaStageBytes)
                : "memory");
   asm volatile(

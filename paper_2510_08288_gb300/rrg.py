@@ -24,6 +24,7 @@ FP64, FP32, FP32_RECHECK = range(3)
 EXIT_NONE, EXIT_LANE, EXIT_CANDIDATE = range(3)
 PAIR_NEVER, PAIR_FILLED, PAIR_ALWAYS = range(3)
 TMA_NEVER, TMA_AUTO, TMA_ALWAYS = range(3)
+INJECT_TMA_NO_COPY = 1
 NPARAM = 27
 MAX_CANDIDATES = 1024
 FLAG_NONE_ADMISSIBLE = 1
@@ -106,6 +107,7 @@ def _load():
         "rrg_set_pairing": (ctypes.c_int, [_p, ctypes.c_int]),
         "rrg_set_tma": (ctypes.c_int, [_p, ctypes.c_int]),
         "rrg_get_tma": (ctypes.c_int, [_p, _p]),
+        "rrg_set_injection": (ctypes.c_int, [_p, ctypes.c_int]),
         "rrg_get_pairing": (ctypes.c_int, [_p, _p]),
         "rrg_autotune_pairing": (ctypes.c_int, [_p, _p, _d, _d, ctypes.c_int, _p, _p]),
         "rrg_get_stats": (ctypes.c_int, [_p, P(RrgStats)]),
@@ -401,6 +403,10 @@ def rrg_set_tma(h, mode):
     _check(lib.rrg_set_tma(h, int(mode)), h)
 
 
+def rrg_set_injection(h, flags):
+    _check(lib.rrg_set_injection(h, int(flags)), h)
+
+
 def rrg_get_tma(h):
     """TMA_NEVER, TMA_AUTO or TMA_ALWAYS (TMA_NEVER where the TMA ring is unavailable)."""
     m = _i32(0)
@@ -551,6 +557,9 @@ class Governor:
 
     def get_tma(self):
         return rrg_get_tma(self.h)
+
+    def set_injection(self, flags):
+        rrg_set_injection(self.h, flags)
 
     def get_pairing(self):
         return rrg_get_pairing(self.h)

@@ -159,3 +159,35 @@ def test_tma_availability(R, params):
         for bad in (-1, 3):
             with pytest.raises(R.RrgError):
                 g.set_tma(bad)
+
+
+def test_tma_wait_timeout_is_reported_and_the_handle_recovers(R, orc, params):
+    """Bounded waits (RRG_INJECT_TMA_NO_COPY: the ring issues no copies, so
+    nothing ever arrives): every warp's wait runs out within its limit, the
+    launch returns, rrg_stats.wait_timeouts counts the warps, and every lane
+    that was running reports a violation, so no candidate is admissible and P
+    is all zero.  With the switch off the same handle gives its normal
+    results again."""
+    N, H = 1000, 100
+    kappas = np.linspace(0.0, 0.2, 7)
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, _cfg(R, N, H, early_exit=R.EXIT_LANE)) as g:
+        g.set_tma(R.TMA_ALWAYS)
+        g.sample_scenarios(1, 1)
+        a0, m0, P0 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        assert a0.any()
+        g.set_injection(R.INJECT_TMA_NO_COPY)
+        g.reset_stats()
+        a1, _, P1 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        st = g.stats()
+        assert st["wait_timeouts"] > 0
+        assert not a1.any() and not P1.any()
+        g.set_injection(0)
+        g.reset_stats()
+        a2, m2, P2 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        assert g.stats()["wait_timeouts"] == 0
+        with pytest.raises(R.RrgError):
+            g.set_injection(2)
+    np.testing.assert_array_equal(a2, a0)
+    np.testing.assert_array_equal(P2, P0)
+    _same(m2, m0)
