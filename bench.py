@@ -103,14 +103,14 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
-TRAFFIC_PER_LAUNCH = (433920 + 24614656 + 35840 + 35840) / 4
+TRAFFIC_PER_LAUNCH = (433920 + 24625152 + 35840 + 35840) / 4
 TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "6e67ada78c68a3ad6b7b31ebb37a6e221e16a418"),
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "6974a9bcf1f03779f0a0b2b8b315615007072de0"),
     ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "1ef24ed4a16f67f78ee586ee6229fd831974dc8e"),
     ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
-     "// Binary64 re-run of the trajectories", "b60bd7819245eced7bf4956a634788d859836197"),
+     "// Binary64 re-run of the trajectories", "a84c48ddcffea78ff0046eb2a42f5af85977e10a"),
     ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
-     "96d6b91d2c134d4c92bdc946aaa754140e564bd9"),
+     "b6965d96ced6990869710984b1659f342995ad8b"),
 )
 
 
@@ -125,13 +125,15 @@ def source_region(rel, begin, end):
     return text[i:text.index(end, i) + len(end)]
 
 
-# The sweep's rollout launches at 65,536 scenarios (parametric model, two
-# candidates per thread): DRAM bytes per launch of one update's three
-# k-section rounds (ncu, one pass over the three launches of the first timed
-# update).  Each round reads the array once per candidate pair that is still
-# running (tile-major order; the 3.9 GB array does not fit in L2), up to 8
-# times the algorithmic bytes.
-SWEEP_TRAFFIC_64K = (3968265984 + 3202560 + 11859865344 + 545024 + 27633282048 + 934144) / 3
+# The sweep's rollout launches at 65,536 scenarios (parametric model, TMA
+# ring): DRAM bytes per launch of one update's three k-section rounds (ncu,
+# one pass over the three launches of the first timed update).  Each round
+# reads the array once per candidate that is still running (tile-major order;
+# the 3.9 GB array does not fit in L2), up to 16 times the algorithmic bytes.
+SWEEP_TRAFFIC_64K = (7910840064 + 3330816 + 19834391552 + 548352 + 51305616640 + 654592) / 3
+# warp instructions per trajectory-step of the TMA-ring kernel there (22.50 G
+# over 6.56 G lane-steps in the same capture)
+TMA_INSTR_PER_STEP = 110
 
 
 # DRAM bytes of one adjoint_forward_kernel<float, float> launch on the adjoint
@@ -140,13 +142,13 @@ SWEEP_TRAFFIC_64K = (3968265984 + 3202560 + 11859865344 + 545024 + 27633282048 +
 # the 3.8 MB of checkpoints and lane minima stay in L2 during the launch),
 # valid while the forward kernel, its launch, the step and the Launch struct
 # are the ones profiled
-ADJ_TRAFFIC_PER_LAUNCH = 49196800 + 4864
+ADJ_TRAFFIC_PER_LAUNCH = 49196544 + 4864
 ADJ_TRAFFIC_SOURCES = (
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', 'b726a6442e28e5a458abb23e2651863f42659404'),
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
     ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
-    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '6e67ada78c68a3ad6b7b31ebb37a6e221e16a418'),
-    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', '96d6b91d2c134d4c92bdc946aaa754140e564bd9'),
+    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '6974a9bcf1f03779f0a0b2b8b315615007072de0'),
+    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', 'b6965d96ced6990869710984b1659f342995ad8b'),
 )
 
 
@@ -1336,6 +1338,13 @@ TMA_NAMES = ("per-lane cp.async", "TMA for ring launches of >= 24 warps per SM, 
              "TMA for every ring launch")
 
 
+def sweep_ceiling(row):
+    """Issue ceiling of the kernel that ran the row: FLOPS_PER_STEP over two
+    flops per issued FMA slot times its instructions per trajectory-step."""
+    instr = TMA_INSTR_PER_STEP if row["tma_step_fraction"] > 0.5 else INSTR_PER_STEP
+    return FLOPS_PER_STEP / (2.0 * instr)
+
+
 def sweep_config(ns, W, K):
     return {"workload": "large sweep on FC3: one robust RG update per step, N_sim in %s, k-section "
                         "with %d kappa candidates per round, %d rounds, horizon %d RK4 steps (dt=0.01 s), "
@@ -1502,6 +1511,7 @@ def run_sweep(args):
                      "pairing": PAIRING_NAMES[g.get_pairing()], "pairing_autotune_ms": pairing_ms,
                      "rollout_ring": TMA_NAMES[g.get_tma()],
                      "paired_step_fraction": st["lane_steps_paired"] / max(1, st["lane_steps"]),
+                     "tma_step_fraction": st["lane_steps_tma"] / max(1, st["lane_steps"]),
                      "gpu_launches": st["launches"], "kappa": [float(x) for x in kap],
                      "no_admissible_updates": int(np.sum(flags & 1)), "fp64_same_search": fp64,
                      "scenarios_in_register": gen_leg})
@@ -1531,16 +1541,17 @@ def run_sweep(args):
         "roofline": {"bound": "alu", "achieved": top["rollout_tflops"], "peak": peak,
                      "unit": "TFLOP/s", "frac": top["rollout_frac"],
                      "traffic": (SWEEP_TRAFFIC_64K if top["n_scenarios"] == 65536 and rho == inputs.PARAM_UNC_REL
-                                 and top["paired_step_fraction"] > 0.5 and measured_traffic() is not None
+                                 and top["tma_step_fraction"] > 0.5 and measured_traffic() is not None
                                  else None),
                      "traffic_basis": "ncu DRAM bytes per rollout launch at 65,536 scenarios (one update's "
-                                      "3 rounds, two candidates per thread)",
-                     "kernel": ("rollout_pair_kernel<parametric> (two candidates per thread)"
+                                      "3 rounds, TMA ring)",
+                     "kernel": ("rollout_tma_kernel<parametric> (TMA ring)" if top["tma_step_fraction"] > 0.5
+                                else "rollout_pair_kernel<parametric> (two candidates per thread)"
                                 if top["paired_step_fraction"] > 0.5 else "rollout_kernel<float, parametric>"),
                      "n_scenarios": top["n_scenarios"],
                      "peak_source": peak_src,
-                     "issue_ceiling": ISSUE_CEILING,
-                     "frac_of_issue_ceiling": frac_of(top["rollout_frac"], ISSUE_CEILING)},
+                     "issue_ceiling": sweep_ceiling(top),
+                     "frac_of_issue_ceiling": frac_of(top["rollout_frac"], sweep_ceiling(top))},
         "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
         "gpu_launches": top["gpu_launches"],
         "fp32_error": fp32_err,

@@ -196,6 +196,8 @@ typedef struct {
                                    lanes it served report a violation, so a
                                    result is never admissible on missing
                                    data.  0 in every correct run.             */
+    uint64_t lane_steps_tma;    /* of lane_steps, those whose disturbances came
+                                   through the TMA ring (rrg_set_tma)         */
 } rrg_stats;
 
 /* Fills *cfg with the defaults of the paper's fuel-cell experiment: dt 0.01,
@@ -398,23 +400,25 @@ RRG_API int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_p
 RRG_API int rrg_set_pairing(rrg_handle h, int mode);
 RRG_API int rrg_get_pairing(rrg_handle h, int32_t *mode);
 
-/* How the binary32 rollouts of launches that leave most warp slots empty
- * (the shared-memory ring: at most 16 warps per SM, 64 under parametric
- * uncertainty) bring in the stored disturbances: through the Tensor Memory
- * Accelerator (one tensor copy per warp of a 32-scenario x 16-step x
- * 3-component box, completion on an mbarrier) or by one asynchronous 4-byte
- * copy per lane, component and step.  RRG_TMA_NEVER: always the per-lane
- * copies; RRG_TMA_AUTO (the default where available): the TMA for ring
- * launches of at least 24 warps per SM, where warps compete for issue and the
- * saved copy instructions pay, the per-lane copies below, where a warp
- * running alone would pay the chunk's wait and warp votes on its dependency
- * chain; RRG_TMA_ALWAYS: the TMA for every ring launch.  The results are
- * identical; only the time changes.  The TMA needs stored binary32 scenarios
- * with n_scenarios a multiple of 4 (the tensor map's row stride must be a
- * multiple of 16 bytes) and a driver that encodes the map: without it
- * rrg_get_tma reports RRG_TMA_NEVER and setting another mode returns
- * RRG_EINVAL.  Setting waits for the handle's stream and discards the cached
- * closed-loop graph; RRG_EINVAL for a mode outside 0..2. */
+/* How the binary32 rollouts on the stored scenario array bring in their
+ * disturbances.  The TMA ring: one tensor copy per warp of a 32-scenario x
+ * 16-step x 3-component box into shared memory, completion on an mbarrier, so
+ * a step reads its values with three shared loads.  Otherwise: per-lane
+ * 4-byte asynchronous copies into a shared-memory ring (launches of at most
+ * 16 warps per SM, 64 under parametric uncertainty) or register prefetch
+ * (larger launches, optionally two candidates per thread, rrg_set_pairing).
+ * RRG_TMA_NEVER: never the TMA; RRG_TMA_AUTO (the default where available):
+ * the TMA for launches of at least 24 warps per SM, where warps compete for
+ * issue and the saved load instructions pay, ahead of pairing (which it beat
+ * where both apply); below, where a warp running alone would pay the
+ * chunk's wait and warp votes on its dependency chain, the per-lane forms;
+ * RRG_TMA_ALWAYS: the TMA for every such launch.  The results are identical;
+ * only the time changes.  The TMA needs stored binary32 scenarios with
+ * n_scenarios a multiple of 4 (the tensor map's row stride must be a multiple
+ * of 16 bytes) and a driver that encodes the map: without it rrg_get_tma
+ * reports RRG_TMA_NEVER and setting another mode returns RRG_EINVAL.  Setting
+ * waits for the handle's stream and discards the cached closed-loop graph;
+ * RRG_EINVAL for a mode outside 0..2. */
 #define RRG_TMA_NEVER 0
 #define RRG_TMA_AUTO 1
 #define RRG_TMA_ALWAYS 2

@@ -1607,6 +1607,7 @@ int rrg_get_stats(rrg_handle h, rrg_stats* out) {
   out->graph_conditional = h->cl_exec != nullptr && h->cl_conditional ? 1 : 0;
   out->lane_steps_paired = ds.lane_steps_paired;
   out->wait_timeouts = ds.wait_timeouts;
+  out->lane_steps_tma = ds.lane_steps_tma;
   return RRG_OK;
 }
 

@@ -106,6 +106,7 @@ struct DevStats {
   unsigned long long cond_launches, cond_rollouts, cond_rounds;
   unsigned long long lane_steps_paired;  // of lane_steps, run two trajectories per thread
   unsigned long long wait_timeouts;      // bounded waits that gave up (TMA ring copies)
+  unsigned long long lane_steps_tma;     // of lane_steps, fed by the TMA ring
 };
 
 // Closed-loop device state.

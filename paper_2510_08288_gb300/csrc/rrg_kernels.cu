@@ -410,6 +410,9 @@ __device__ __forceinline__ void rollout_body(const Launch& L, const RhsU<T>& K0,
                                  cand_stop ? dead : nullptr, &steps, &end, band, &jlast, stages, bars,
                                  &L.stats->wait_timeouts);
     if (lane_runs) smin = s_out;
+    const unsigned wsteps = __reduce_add_sync(0xffffffffu, steps);
+    if ((threadIdx.x & 31) == 0 && wsteps)
+      atomicAdd(&L.stats->lane_steps_tma, static_cast<unsigned long long>(wsteps));
   } else if (active && final_lane) {
     if constexpr (SRC == SRC_GEN)
       smin = run_lane_gen<T>(K, C, L.st->src[L.st->buf], k, j0, j_end, q_ca, w, q_sm, w_abs, smin0,
@@ -625,16 +628,20 @@ int pair_blocks_per_sm(bool pu) {
 #define RRG_PAIR_MIN_WAVES 6
 #endif
 
-// RRG_TMA_AUTO takes the TMA ring for ring launches of at least this many
-// warps per SM.  The TMA saves the per-step copy instructions, which pays
-// where many warps compete for issue; a warp running alone pays the chunk's
-// wait, warp votes and fence on its dependency chain instead.  Measured on
-// GB300 (k-section sweep, 16 candidates x 5,000 steps, per update): 16,384
-// scenarios with uncertain parameters (54 warps per SM) 6.28 against
-// 6.75 ms, 8,192 (27) 4.46 against 4.53 ms, 4,096 (13.5) 2.78 against 2.70
-// ms, 1,024 (3.4) 1.85 against 1.64 ms; the 1,024-scenario closed loop (8.8
-// warps per SM at launch, mostly single survivors) 2,743 against 2,927
-// updates/s.
+// RRG_TMA_AUTO takes the TMA ring for binary32 launches on the stored array
+// of at least this many warps per SM, ahead of the other rings and of
+// pairing.  The TMA saves the per-step load instructions, which pays where
+// many warps compete for issue; a warp running alone pays the chunk's wait,
+// warp votes and fence on its dependency chain instead.  Measured on GB300
+// (k-section sweep, 16 candidates x 5,000 steps, per update), TMA against the
+// per-lane cp.async ring: 16,384 scenarios with uncertain parameters (54
+// warps per SM) 6.28 against 6.75 ms, 8,192 (27) 4.46 against 4.53 ms, 4,096
+// (13.5) 2.78 against 2.70 ms, 1,024 (3.4) 1.85 against 1.64 ms; the
+// 1,024-scenario closed loop (8.8 warps per SM at launch, mostly single
+// survivors) 2,743 against 2,927 updates/s.  Against the register ring and
+// pairing on launches that fill the SMs: 65,536 parametric 21.8 ms against
+// 23.9 (single) and 24.0 (paired), 32,768 10.9 against 11.8; nominal 65,536
+// 27.5 against 30.4 and 30.2.
 #ifndef RRG_TMA_MIN_WARPS_PER_SM
 #define RRG_TMA_MIN_WARPS_PER_SM 24
 #endif
@@ -670,6 +677,17 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
       if (L.scen_gen) RRG_ROLLOUT(rollout_kernel, double, SRC_GEN, L.u64, L.d64, L.d64b, L.cand_c64, 0);
       else RRG_ROLLOUT(rollout_kernel, double, SRC_REGS, L.u64, L.d64, L.d64b, L.cand_c64, 0);
     }
+  } else if (!L.scen_gen && L.tmap != nullptr &&
+             (L.tma == RRG_TMA_ALWAYS ||
+              (L.tma == RRG_TMA_AUTO && warps >= static_cast<long long>(RRG_TMA_MIN_WARPS_PER_SM) * sms))) {
+    // the TMA ring: one tensor copy per warp and chunk of steps (it takes
+    // precedence over pairing, which it beat where both apply)
+    if (L.pmul)
+      rollout_tma_kernel<true><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
+          L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
+    else
+      rollout_tma_kernel<false><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
+          L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
   } else if (allow_pair && !L.scen_gen && m_launch > 1 && (L.pair == RRG_PAIR_ALWAYS || filled)) {
     // two candidates per thread (issue-bound launches: one load of each
     // disturbance and one loop's bookkeeping serve both)
@@ -680,16 +698,6 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
     else
       rollout_pair_kernel<false><<<g2, kRollThreads, 0, L.stream>>>(L, L.u32, L.d32, L.d32b, L.cand_c32,
                                                                     early_exit, cls);
-  } else if (ring && !L.scen_gen && L.tmap != nullptr &&
-             (L.tma == RRG_TMA_ALWAYS ||
-              (L.tma == RRG_TMA_AUTO && warps >= static_cast<long long>(RRG_TMA_MIN_WARPS_PER_SM) * sms))) {
-    // the ring through the TMA: one tensor copy per warp and chunk of steps
-    if (L.pmul)
-      rollout_tma_kernel<true><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
-          L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
-    else
-      rollout_tma_kernel<false><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
-          L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
   } else {
     if (L.pmul) {
       if (L.scen_gen) RRG_ROLLOUT(rollout_pu_kernel, float, SRC_GEN, L.u32, L.d32, L.d32b, L.cand_c32, cls);

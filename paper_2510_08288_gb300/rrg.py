@@ -63,6 +63,7 @@ class RrgStats(ctypes.Structure):
         ("lane_steps_fp64", _u64), ("rechecked", _u64), ("rounds", _u64),
         ("rollout_ms", _d), ("recheck_ms", _d), ("timed_rollouts", _u64), ("repairs", _u64),
         ("graph_conditional", _u64), ("lane_steps_paired", _u64), ("wait_timeouts", _u64),
+        ("lane_steps_tma", _u64),
     ]
 
 

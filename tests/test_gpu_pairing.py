@@ -1,5 +1,8 @@
 """Two candidates per thread (rrg_set_pairing) against one per thread.
 
+The TMA ring, which takes precedence over pairing on large launches, is off
+in these tests (RRG_TMA_NEVER), so the paired kernel is the one compared.
+
 A paired thread runs candidates A and B of the same scenario off one load of
 each disturbance, with the same per-trajectory arithmetic as a single lane:
 the admissible flags, the P entries, every search result and the min slack
@@ -41,6 +44,12 @@ def _cfg(R, N, H, **kw):
     return R.rrg_config_default(**c)
 
 
+def _gov(R, params, cfg):
+    g = R.Governor(params, cfg)
+    g.set_tma(R.TMA_NEVER)
+    return g
+
+
 def _same_slack(a, b):
     """Bit-identical, NaN (a candidate failing the steady-state check) included."""
     a, b = np.asarray(a), np.asarray(b)
@@ -58,7 +67,7 @@ def test_pairs_equal_single_lanes(R, orc, params, N, H, prec, unc, early):
     kappas = np.linspace(0.0, 1.0, 13)   # 13 rows: the last pair has one
     x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.03, 1.0])
     res = {}
-    with R.Governor(params, _cfg(R, N, H, precision=p, early_exit=early, param_unc_rel=unc)) as g:
+    with _gov(R, params, _cfg(R, N, H, precision=p, early_exit=early, param_unc_rel=unc)) as g:
         assert g.get_pairing() == R.PAIR_FILLED
         g.sample_scenarios(5, 2)
         for mode in (R.PAIR_NEVER, R.PAIR_ALWAYS, R.PAIR_FILLED):
@@ -90,7 +99,7 @@ def test_paired_recheck_decides_like_the_oracle(R, orc, params, unc):
     # the boundary: kappa ~ 0.1 for the nominal model, lower with uncertain parameters
     kappas = np.linspace(0.0, 0.06, 25) if unc else np.linspace(0.09, 0.115, 26)
     x_t = orc.equilibrium(params, 100.0)
-    with R.Governor(params, _cfg(R, N, H, early_exit=R.EXIT_LANE, param_unc_rel=unc)) as g:
+    with _gov(R, params, _cfg(R, N, H, early_exit=R.EXIT_LANE, param_unc_rel=unc)) as g:
         g.set_pairing(R.PAIR_ALWAYS)
         g.sample_scenarios(seed, upd)
         adm, _, P = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
@@ -118,7 +127,7 @@ def test_searches_are_unchanged_by_pairing(R, orc, params, name, kw):
              (180.0, 90.0, orc.equilibrium(params, 180.0) * np.array([1.02, 0.99, 1.01])),
              (60.0, 280.0, orc.equilibrium(params, 60.0))]
     out = {}
-    with R.Governor(params, _cfg(R, N, H, **kw)) as g:
+    with _gov(R, params, _cfg(R, N, H, **kw)) as g:
         g.sample_scenarios(seed, upd)
         for mode in (R.PAIR_NEVER, R.PAIR_FILLED, R.PAIR_ALWAYS):
             g.set_pairing(mode)
@@ -140,7 +149,7 @@ def test_closed_loop_is_unchanged_by_pairing(R, orc, params, use_graph):
     x0 = orc.equilibrium(params, 100.0)
     r_seq = np.array([250.0] * 3 + [120.0] * 3)
     runs = []
-    with R.Governor(params, _cfg(R, N, H, max_candidates=16)) as g:
+    with _gov(R, params, _cfg(R, N, H, max_candidates=16)) as g:
         for mode in (R.PAIR_NEVER, R.PAIR_ALWAYS, R.PAIR_NEVER, R.PAIR_FILLED):
             g.set_pairing(mode)
             runs.append(g.closed_loop(x0, 100.0, r_seq, 9, 0, inputs.DIST_AMP, use_graph=use_graph))
@@ -152,7 +161,7 @@ def test_closed_loop_is_unchanged_by_pairing(R, orc, params, use_graph):
 def test_autotune_pairing_keeps_the_result(R, orc, params):
     N, H = 8192, 300
     x_t = orc.equilibrium(params, 100.0)
-    with R.Governor(params, _cfg(R, N, H, max_candidates=16)) as g:
+    with _gov(R, params, _cfg(R, N, H, max_candidates=16)) as g:
         g.sample_scenarios(1, 1)
         want = g.step(x_t, 250.0, 100.0)
         mode, ms = g.autotune_pairing(x_t, 250.0, 100.0, repeats=2)
@@ -164,7 +173,7 @@ def test_autotune_pairing_keeps_the_result(R, orc, params):
 
 
 def test_pairing_mode_is_validated(R, params):
-    with R.Governor(params, _cfg(R, 64, 10)) as g:
+    with _gov(R, params, _cfg(R, 64, 10)) as g:
         for bad in (-1, 3):
             with pytest.raises(R.RrgError):
                 g.set_pairing(bad)
@@ -176,7 +185,7 @@ def test_paired_steps_are_counted(R, orc, params):
     of lane_steps (the steps a survivor runs alone are not paired)."""
     N, H = 4096, 300
     x_t = orc.equilibrium(params, 100.0)
-    with R.Governor(params, _cfg(R, N, H, max_candidates=16, search=R.SEARCH_KSECTION, n_rounds=3)) as g:
+    with _gov(R, params, _cfg(R, N, H, max_candidates=16, search=R.SEARCH_KSECTION, n_rounds=3)) as g:
         g.sample_scenarios(1, 1)
         for mode in (R.PAIR_NEVER, R.PAIR_ALWAYS):
             g.set_pairing(mode)

@@ -191,3 +191,29 @@ def test_tma_wait_timeout_is_reported_and_the_handle_recovers(R, orc, params):
     np.testing.assert_array_equal(a2, a0)
     np.testing.assert_array_equal(P2, P0)
     _same(m2, m0)
+
+
+def test_tma_auto_takes_large_launches_only(R, orc, params):
+    """RRG_TMA_AUTO: launches of at least 24 warps per SM (8,192 scenarios x
+    16 candidates: 27 per SM) take the TMA ring, ahead of pairing; small ones
+    (1,024 x 16: 3.4 per SM) keep the per-lane copies; results equal."""
+    x_t = orc.equilibrium(params, 100.0)
+    kappas = np.linspace(0.0, 1.0, 16)
+    res = {}
+    for N, want_tma in ((8192, True), (1024, False)):
+        with R.Governor(params, _cfg(R, N, 200, early_exit=R.EXIT_NONE, precision=R.FP32)) as g:
+            g.sample_scenarios(2, 2)
+            for mode in (R.TMA_AUTO, R.TMA_NEVER):
+                g.set_tma(mode)
+                g.reset_stats()
+                res[(N, mode)] = g.eval_candidates(x_t, 100.0, 250.0, kappas)
+                st = g.stats()
+                used = st["lane_steps_tma"] > 0
+                assert used == (want_tma and mode == R.TMA_AUTO), (N, mode)
+                if used:
+                    assert st["lane_steps_tma"] == st["lane_steps"]
+                    assert st["lane_steps_paired"] == 0
+            a0, m0, _ = res[(N, R.TMA_AUTO)]
+            a1, m1, _ = res[(N, R.TMA_NEVER)]
+            np.testing.assert_array_equal(a0, a1)
+            _same(m0, m1)
