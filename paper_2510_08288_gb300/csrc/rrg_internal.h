@@ -377,8 +377,8 @@ cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d
 // Tensor map of a binary32 scenario array [3][H][N] for the TMA ring (boxes
 // of 32 scenarios x one chunk of steps x 3 components); false when N is not a
 // multiple of 4 (row strides must be multiples of 16 bytes) or the driver
-// refuses.  tma_ring_prepare() sets the TMA kernels' shared-memory limit once;
-// false if the runtime refuses.
+// refuses.  tma_ring_prepare() sets the TMA kernels' shared-memory limit on
+// the current device (once per device); false if the runtime refuses.
 bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H);
 bool tma_ring_prepare();
 // Resident blocks per SM of the two-candidates-per-thread rollout kernel

@@ -17,6 +17,7 @@
 //
 // Nothing returns to the host between rounds; the whole update can be
 // captured in a CUDA graph.
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cudaTypedefs.h>
@@ -576,47 +577,6 @@ rollout_pair_kernel(const Launch L, const RhsU<float> K0, const float* __restric
   }
 }
 
-bool tma_ring_prepare() {
-  static const bool ok =
-      cudaFuncSetAttribute(rollout_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess &&
-      cudaFuncSetAttribute(rollout_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess;
-  return ok;
-}
-
-bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H) {
-  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      f = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }();
-  if (encode == nullptr || d32 == nullptr || N <= 0 || H <= 0 || N % 4 != 0) return false;
-  // dims innermost first: scenario k, step j, component c
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(H), 3};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * sizeof(float),
-                                 static_cast<cuuint64_t>(H) * N * sizeof(float)};
-  const cuuint32_t box[3] = {32, static_cast<cuuint32_t>(kTmaChunk), 3};
-  const cuuint32_t elem[3] = {1, 1, 1};
-  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d32), dims, strides, box, elem,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Resident blocks per SM of the paired kernel (its register count decides).
-int pair_blocks_per_sm(bool pu) {
-  static const int n[2] = {
-      [] { int b = 0; return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_pair_kernel<false>,
-                                                                           kRollThreads, 0) == cudaSuccess && b > 0 ? b : 1; }(),
-      [] { int b = 0; return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_pair_kernel<true>,
-                                                                           kRollThreads, 0) == cudaSuccess && b > 0 ? b : 1; }()};
-  return n[pu ? 1 : 0];
-}
-
 // RRG_PAIR_FILLED pairs a launch whose paired grid fills the SMs at least
 // this many times over: a paired block does twice a single block's work, so
 // a short grid ends in a long, half-empty last wave.  Measured on GB300
@@ -758,6 +718,57 @@ recheck_kernel(const Launch L, const RhsU<double> K0, int early_exit) {
     atomicAdd(&L.stats->lane_steps_fp64, static_cast<unsigned long long>(steps));
     atomicAdd(&L.stats->rechecked, 1ull);
   }
+}
+
+// ---- host-side set-up of the rollout kernels ------------------------------
+// The shared-memory limit is a per-device attribute of the kernels: set once
+// for each device a handle is created on.
+bool tma_ring_prepare() {
+  constexpr int kDevices = 64;
+  static std::atomic<int> state[kDevices];  // 0 not yet, 1 set, 2 refused
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return false;
+  const int st = state[dev].load();
+  if (st != 0) return st == 1;
+  const bool ok =
+      cudaFuncSetAttribute(rollout_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess &&
+      cudaFuncSetAttribute(rollout_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess;
+  state[dev].store(ok ? 1 : 2);
+  return ok;
+}
+
+bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  if (encode == nullptr || d32 == nullptr || N <= 0 || H <= 0 || N % 4 != 0) return false;
+  // dims innermost first: scenario k, step j, component c
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(H), 3};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(N) * sizeof(float),
+                                 static_cast<cuuint64_t>(H) * N * sizeof(float)};
+  const cuuint32_t box[3] = {32, static_cast<cuuint32_t>(kTmaChunk), 3};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d32), dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Resident blocks per SM of the paired kernel (its register count decides).
+int pair_blocks_per_sm(bool pu) {
+  static const int n[2] = {
+      [] { int b = 0; return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_pair_kernel<false>,
+                                                                           kRollThreads, 0) == cudaSuccess && b > 0 ? b : 1; }(),
+      [] { int b = 0; return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_pair_kernel<true>,
+                                                                           kRollThreads, 0) == cudaSuccess && b > 0 ? b : 1; }()};
+  return n[pu ? 1 : 0];
 }
 
 cudaError_t launch_recheck(const Launch& L, int early_exit) {
