@@ -385,10 +385,13 @@ RRG_API int rrg_autotune(rrg_handle h, const double *x_t, double r_t, double v_p
  * scenario array (RRG_FP32, RRG_FP32_RECHECK; scenarios_in_register = 0):
  * RRG_PAIR_NEVER, one trajectory per thread; RRG_PAIR_FILLED, two candidates
  * of one scenario per thread (one load of each disturbance, two independent
- * step chains) in rollout launches large enough that the paired grid fills
- * the SMs at least six times over, one elsewhere;
- * RRG_PAIR_ALWAYS, two in every launch whose rows are full-horizon segments
- * (the probe and continuation launches of a pipelined search never pair).
+ * step chains) in register-ring launches large enough that the paired grid
+ * fills the SMs at least six times over, one elsewhere (launches that take
+ * the TMA ring, rrg_set_tma, stay single: the TMA ring measured faster than
+ * either pairing);
+ * RRG_PAIR_ALWAYS, two in every launch whose rows are full-horizon segments,
+ * on whichever ring the launch takes (the probe and continuation launches of
+ * a pipelined search never pair).
  * The same arithmetic in every mode: every admissible flag, every search
  * result and the min slack of every admissible candidate are identical; only
  * the time changes.  Both calls wait for the handle's stream; setting the mode

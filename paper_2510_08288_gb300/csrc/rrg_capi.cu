@@ -33,6 +33,7 @@ struct rrg_ctx {
   bool tma_ok = false;
   int tma_mode = RRG_TMA_AUTO;  // rrg_set_tma
   int inject = 0;               // rrg_set_injection
+  int tma_pair_bps = 0;         // occupancy of the paired TMA kernel (queried at creation)
   Launch L{};
   // device memory
   double* params_dev = nullptr;
@@ -212,6 +213,7 @@ void fill_launch(rrg_ctx* h) {
   L.tmap = h->tma_ok && h->tma_mode != RRG_TMA_NEVER ? h->tmap : nullptr;
   L.tma = h->tma_mode;
   L.inject = h->inject;
+  L.tma_pair_bps = h->tma_pair_bps;
   L.N = c.n_scenarios;
   L.H = c.horizon;
   L.precision = c.precision;
@@ -709,6 +711,7 @@ int rrg_create(const double* model_params, int n_params, const rrg_config* cfg, 
       encode_scenario_map(&h->tmap[0], h->d32, c.n_scenarios, c.horizon)) {
     h->tmap[1] = h->tmap[0];
     h->tma_ok = true;
+    h->tma_pair_bps = tma_pair_blocks_per_sm(c.param_unc_rel > 0.0);
   }
   fill_launch(h);
   *out = h;

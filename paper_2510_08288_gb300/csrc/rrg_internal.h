@@ -182,6 +182,7 @@ struct Launch {
   const CUtensorMap* tmap;
   int tma;                      // RRG_TMA_*: which ring launches take the TMA
   int inject;                   // RRG_INJECT_* test switches (0 in normal use)
+  int tma_pair_bps;             // resident blocks per SM of the paired TMA kernel (0: never paired)
 };
 
 // Folds the FC3 parameter vector into the constants the kernels use
@@ -381,6 +382,9 @@ cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d
 // the current device (once per device); false if the runtime refuses.
 bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H);
 bool tma_ring_prepare();
+// Resident blocks per SM of the two-candidates-per-thread TMA kernel (after
+// tma_ring_prepare on the current device; 0 if the runtime does not answer).
+int tma_pair_blocks_per_sm(bool pu);
 // Resident blocks per SM of the two-candidates-per-thread rollout kernel
 // (queried from the runtime on the first call, then cached).
 int pair_blocks_per_sm(bool pu);

@@ -577,6 +577,82 @@ rollout_pair_kernel(const Launch L, const RhsU<float> K0, const float* __restric
   }
 }
 
+// Two candidates per thread on the TMA ring: block row y runs the launch's
+// rows 2y and 2y + 1 (full-horizon segments only, as rollout_pair_kernel)
+// for the same scenarios through run_lane_tma_pair; every lane of a warp
+// takes part in the ring's copies and waits.  Each candidate's lanes are
+// reduced as in rollout_body.
+template <bool PU>
+__global__ void __launch_bounds__(kRollThreads, PU ? RRG_PAIR_PU_MIN_BLOCKS : RRG_PAIR_MIN_BLOCKS)
+rollout_tma_pair_kernel(const Launch L, const RhsU<float> K0, const RhsC<float>* __restrict__ cand,
+                        int early_exit, int classify, const __grid_constant__ CUtensorMap tm0,
+                        const __grid_constant__ CUtensorMap tm1) {
+  const Seg s0 = L.st->seg[0], s1 = L.st->seg[1];
+  const int rows = s0.count + s1.count;
+  const int ya = 2 * static_cast<int>(blockIdx.y), yb = ya + 1;
+  if (ya >= rows) return;
+  const int ia = ya < s0.count ? s0.base + ya : s1.base + (ya - s0.count);
+  const int ib = yb >= rows ? -1 : (yb < s0.count ? s0.base + yb : s1.base + (yb - s0.count));
+  const int N = L.N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = k < N;
+  const bool ssa = L.cand_ss[ia] != 0, ssb = ib >= 0 && L.cand_ss[ib] != 0;
+  if (!ssa && L.P != nullptr && active) L.P[static_cast<size_t>(ia) * N + k] = 0;
+  if (ib >= 0 && !ssb && L.P != nullptr && active) L.P[static_cast<size_t>(ib) * N + k] = 0;
+  const bool cand_stop = early_exit == RRG_EXIT_CANDIDATE;
+  volatile int32_t* deada = L.cand_dead + ia;
+  volatile int32_t* deadb = L.cand_dead + (ib >= 0 ? ib : ia);
+  bool runa = ssa, runb = ssb;
+  if (cand_stop) {
+    const int da = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 && runa ? *deada : 0, 0);
+    const int db = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 && runb ? *deadb : 0, 0);
+    runa = runa && !da;
+    runb = runb && !db;
+  }
+  if (!runa && !runb) return;
+  const float eps = static_cast<float>(L.eps_abs);
+  const float thr = early_exit != RRG_EXIT_NONE ? (classify ? -eps : 0.0f) : -inf_v<float>();
+  const float band = classify ? eps : -inf_v<float>();
+  TmaTraj a{}, b{};
+  a.smin = b.smin = inf_v<float>();
+  a.jl = b.jl = -1;
+  RhsU<float> K = K0;
+  RhsC<float> CA = cand[ia], CB = cand[ib >= 0 ? ib : ia];
+  if (active) {
+    double p_atm = L.params[P_P_ATM];
+    if constexpr (PU) {
+      const double* mk = (L.st->buf ? L.pmulb : L.pmul) + static_cast<size_t>(k) * RRG_NPARAM;
+      if (runa) p_atm = scenario_model<float>(L.params, mk, L.cand_v[ia], L.k64.pws, L.y_min, K, CA);
+      if (runb) p_atm = scenario_model<float>(L.params, mk, L.cand_v[ib], L.k64.pws, L.y_min, K, CB);
+    }
+    start_state<float>(CA, L.st->x, p_atm, a.q_ca, a.w, a.q_sm, a.w_abs);
+    start_state<float>(CB, L.st->x, p_atm, b.q_ca, b.w, b.q_sm, b.w_abs);
+  }
+  const int wid = threadIdx.x >> 5;
+  float* stages = reinterpret_cast<float*>(rrg_dyn_smem) + static_cast<size_t>(wid) * 2 * kTmaStageFloats;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rrg_dyn_smem + (kRollThreads / 32) * 2 * kTmaStageBytes) + 2 * wid;
+  const void* tm = (L.inject & RRG_INJECT_TMA_NO_COPY) ? nullptr : (L.st->buf ? &tm1 : &tm0);
+  unsigned paired = 0;
+  run_lane_tma_pair(K, CA, CB, tm, k & ~31, active && runa, active && runb, 0, L.H, a, b,
+                    static_cast<float>(L.dt), thr, band, cand_stop ? deada : nullptr,
+                    cand_stop ? deadb : nullptr, cand_stop ? deada : nullptr, cand_stop ? deadb : nullptr, stages,
+                    bars, &L.stats->wait_timeouts, &paired);
+  if (active && cand_stop) {
+    if (runa && a.smin < thr) *deada = 1;
+    if (runb && b.smin < thr) *deadb = 1;
+  }
+  const unsigned sa = active && runa ? static_cast<unsigned>(a.j) : 0u;
+  const unsigned sb = active && runb ? static_cast<unsigned>(b.j) : 0u;
+  if (runa) reduce_lane<float>(L, ia, k, N, active, a.smin, sa, a.jl, classify, eps, deada);
+  if (runb) reduce_lane<float>(L, ib, k, N, active, b.smin, sb, b.jl, classify, eps, deadb);
+  const unsigned wp = __reduce_add_sync(0xffffffffu, paired);
+  const unsigned wt = __reduce_add_sync(0xffffffffu, sa + sb);
+  if ((threadIdx.x & 31) == 0) {
+    if (wp) atomicAdd(&L.stats->lane_steps_paired, static_cast<unsigned long long>(wp));
+    if (wt) atomicAdd(&L.stats->lane_steps_tma, static_cast<unsigned long long>(wt));
+  }
+}
+
 // RRG_PAIR_FILLED pairs a launch whose paired grid fills the SMs at least
 // this many times over: a paired block does twice a single block's work, so
 // a short grid ends in a long, half-empty last wave.  Measured on GB300
@@ -641,13 +717,27 @@ cudaError_t launch_rollout(const Launch& L, int m_launch, bool use_fp64, int ear
              (L.tma == RRG_TMA_ALWAYS ||
               (L.tma == RRG_TMA_AUTO && warps >= static_cast<long long>(RRG_TMA_MIN_WARPS_PER_SM) * sms))) {
     // the TMA ring: one tensor copy per warp and chunk of steps (it takes
-    // precedence over pairing, which it beat where both apply)
-    if (L.pmul)
+    // precedence over the register-ring pairing, which it beat where both
+    // apply).  Two candidates per thread on it only with RRG_PAIR_ALWAYS:
+    // measured on GB300 (65,536 x 16 candidates x 5,000 steps, per update)
+    // 22.7 against 21.9 ms with uncertain parameters (the paired kernel holds
+    // 3 blocks per SM at 150 registers), 27.9 against 27.6 ms nominal.
+    const bool tpair = allow_pair && m_launch > 1 && L.tma_pair_bps > 0 && L.pair == RRG_PAIR_ALWAYS;
+    if (tpair) {
+      const dim3 g2(grid.x, (m_launch + 1) / 2);
+      if (L.pmul)
+        rollout_tma_pair_kernel<true><<<g2, kRollThreads, kTmaSmemBytes, L.stream>>>(
+            L, L.u32, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
+      else
+        rollout_tma_pair_kernel<false><<<g2, kRollThreads, kTmaSmemBytes, L.stream>>>(
+            L, L.u32, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
+    } else if (L.pmul) {
       rollout_tma_kernel<true><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
           L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
-    else
+    } else {
       rollout_tma_kernel<false><<<grid, kRollThreads, kTmaSmemBytes, L.stream>>>(
           L, L.u32, L.d32, L.d32b, L.cand_c32, early_exit, cls, L.tmap[0], L.tmap[1]);
+    }
   } else if (allow_pair && !L.scen_gen && m_launch > 1 && (L.pair == RRG_PAIR_ALWAYS || filled)) {
     // two candidates per thread (issue-bound launches: one load of each
     // disturbance and one loop's bookkeeping serve both)
@@ -730,11 +820,12 @@ bool tma_ring_prepare() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return false;
   const int st = state[dev].load();
   if (st != 0) return st == 1;
-  const bool ok =
-      cudaFuncSetAttribute(rollout_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess &&
-      cudaFuncSetAttribute(rollout_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kTmaSmemBytes)) == cudaSuccess;
+  const int sm = static_cast<int>(kTmaSmemBytes);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const bool ok = cudaFuncSetAttribute(rollout_tma_kernel<false>, a, sm) == cudaSuccess &&
+                  cudaFuncSetAttribute(rollout_tma_kernel<true>, a, sm) == cudaSuccess &&
+                  cudaFuncSetAttribute(rollout_tma_pair_kernel<false>, a, sm) == cudaSuccess &&
+                  cudaFuncSetAttribute(rollout_tma_pair_kernel<true>, a, sm) == cudaSuccess;
   state[dev].store(ok ? 1 : 2);
   return ok;
 }
@@ -759,6 +850,16 @@ bool encode_scenario_map(CUtensorMap* m, const float* d32, int N, int H) {
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d32), dims, strides, box, elem,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tma_pair_blocks_per_sm(bool pu) {
+  int b = 0;
+  const cudaError_t e =
+      pu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_tma_pair_kernel<true>, kRollThreads,
+                                                         kTmaSmemBytes)
+         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rollout_tma_pair_kernel<false>, kRollThreads,
+                                                         kTmaSmemBytes);
+  return e == cudaSuccess && b > 0 ? b : 0;
 }
 
 // Resident blocks per SM of the paired kernel (its register count decides).

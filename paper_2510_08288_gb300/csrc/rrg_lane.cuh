@@ -801,6 +801,212 @@ __device__ __forceinline__ float run_lane_tma(const RhsU<float>& K, const RhsC<f
   return smin;
 }
 
+// ---------------------------------------------------------------------------
+// Two candidates of one scenario per thread on the TMA ring: the warp's chunk
+// copies, waits and shared loads serve both trajectories, whose step chains
+// are independent work for the scheduler (run_lane_pair's idea on
+// run_lane_tma's ring).  Per trajectory the arithmetic, the chunk-end tests
+// and the dead-flag handling are run_lane_tma's, so the decisions and the min
+// slack of a trajectory that does not violate equal it bit for bit.  A chunk
+// in which both trajectories of a lane run takes one body for both; one that
+// has stopped leaves the other to a single-trajectory body.
+struct TmaTraj {
+  float q_ca, w, q_sm, w_abs;  // deviation state and absolute speed
+  float smin;
+  int jl, how, j;
+  bool run;
+};
+
+__device__ __forceinline__ void tma_traj_start(TmaTraj& t, const RhsC<float>& C, bool on, int j0, int j_end,
+                                               float thr, float band, volatile int32_t* mark) {
+  t.j = j0;
+  t.how = LANE_REACHED_END;
+  t.run = on && j0 < j_end;
+  if (on && j0 == 0) {
+    const float s0 = checked_slack<float>(C, t.q_ca, t.w, t.q_sm);
+    t.smin = fmin(t.smin, s0);
+    if (s0 < band) t.jl = 0;
+    if (s0 < thr) {
+      t.how = LANE_VIOLATED;
+      t.run = false;
+      if (mark != nullptr) *mark = 1;
+    }
+  }
+}
+
+// The tests at the end of a whole chunk of T steps (run_lane_tma's).
+__device__ __forceinline__ void tma_traj_chunk_end(TmaTraj& t, float bmin, float nf, int T, int j_end, float thr,
+                                                   float band, int dead_now, volatile int32_t* mark) {
+  t.j += T;
+  nf = fma_rn(t.q_ca, 0.0f, fma_rn(t.w, 0.0f, fma_rn(t.q_sm, 0.0f, nf)));
+  if (nf != nf) bmin = -inf_v<float>();
+  t.smin = fmin(t.smin, bmin);
+  if (bmin < band) t.jl = t.j;
+  if (t.smin < thr) {
+    t.how = LANE_VIOLATED;
+    t.run = false;
+    if (mark != nullptr) *mark = 1;
+  } else if (dead_now != 0 && t.j < j_end) {
+    t.how = LANE_STOPPED;
+    t.run = false;
+  }
+}
+
+// A whole chunk for one trajectory (e: the lane's column of the stage).
+template <int T>
+__device__ __forceinline__ void tma_traj_chunk(TmaTraj& t, const RhsU<float>& K, const RhsC<float>& C,
+                                               const StepC<float>& S, const float* e, float& bmin, float& nf) {
+#pragma unroll 8
+  for (int u = 0; u < T; ++u) {
+    const float e0 = e[u * 32], e1 = e[(T + u) * 32], e2 = e[(2 * T + u) * 32];
+    rk4_step_fast<float>(K, C, S, t.q_ca, t.w, t.q_sm, t.w_abs, e0, e1, e2);
+    const float sl = C.y_scale * (t.q_sm - t.q_ca) + C.s_off;
+    bmin = fmin(bmin, sl);
+    nf = fma_rn(sl, 0.0f, nf);
+  }
+}
+
+// A whole chunk for both trajectories, one load of each value for the two.
+template <int T>
+__device__ __forceinline__ void tma_pair_chunk(TmaTraj& a, TmaTraj& b, const RhsU<float>& K,
+                                               const RhsC<float>& CA, const RhsC<float>& CB,
+                                               const StepC<float>& S, const float* e, float& bma, float& nfa,
+                                               float& bmb, float& nfb) {
+#pragma unroll 8
+  for (int u = 0; u < T; ++u) {
+    const float e0 = e[u * 32], e1 = e[(T + u) * 32], e2 = e[(2 * T + u) * 32];
+    rk4_step_fast<float>(K, CA, S, a.q_ca, a.w, a.q_sm, a.w_abs, e0, e1, e2);
+    rk4_step_fast<float>(K, CB, S, b.q_ca, b.w, b.q_sm, b.w_abs, e0, e1, e2);
+    const float sa = CA.y_scale * (a.q_sm - a.q_ca) + CA.s_off;
+    const float sb = CB.y_scale * (b.q_sm - b.q_ca) + CB.s_off;
+    bma = fmin(bma, sa);
+    bmb = fmin(bmb, sb);
+    nfa = fma_rn(sa, 0.0f, nfa);
+    nfb = fma_rn(sb, 0.0f, nfb);
+  }
+}
+
+// The last, partial chunk: step by step with the per-step test (run_lane's).
+__device__ __forceinline__ void tma_traj_tail(TmaTraj& t, const RhsU<float>& K, const RhsC<float>& C,
+                                              const StepC<float>& S, const float* e, int T, int nst, float thr,
+                                              float band, volatile int32_t* mark) {
+  for (int u = 0; u < nst && t.run; ++u) {
+    const float e0 = e[u * 32], e1 = e[(T + u) * 32], e2 = e[(2 * T + u) * 32];
+    rk4_step_fast<float>(K, C, S, t.q_ca, t.w, t.q_sm, t.w_abs, e0, e1, e2);
+    ++t.j;
+    const float sl = checked_slack<float>(C, t.q_ca, t.w, t.q_sm);
+    t.smin = fmin(t.smin, sl);
+    if (sl < band) t.jl = t.j;
+    if (sl < thr) {
+      t.how = LANE_VIOLATED;
+      t.run = false;
+      if (mark != nullptr) *mark = 1;
+    }
+  }
+}
+
+// The chunk loop of run_lane_tma for two trajectories per lane (a: candidate
+// A, b: candidate B; state, smin and jl in, everything out; steps = j - j0).
+// dead_X / mark_X: the candidates' flags (nullptr without a candidate-level
+// exit).  *paired: steps this lane ran for both trajectories at once.  Called
+// by all 32 lanes of the warp.
+__device__ __forceinline__ void run_lane_tma_pair(const RhsU<float>& K, const RhsC<float>& CA,
+                                                  const RhsC<float>& CB, const void* tmap, int k0, bool onA,
+                                                  bool onB, int j0, int j_end, TmaTraj& a, TmaTraj& b, float dt,
+                                                  float thr, float band, const volatile int32_t* deadA,
+                                                  const volatile int32_t* deadB, volatile int32_t* markA,
+                                                  volatile int32_t* markB, float* stages, uint64_t* bars,
+                                                  unsigned long long* timeouts, unsigned* paired) {
+  constexpr int T = kTmaChunk;
+  const int lane = threadIdx.x & 31;
+  tma_traj_start(a, CA, onA, j0, j_end, thr, band, markA);
+  tma_traj_start(b, CB, onB, j0, j_end, thr, band, markB);
+  *paired = 0u;
+  const StepC<float> S = step_consts<float>(K, dt);
+  const int nchunks = j_end > j0 ? (j_end - j0 + T - 1) / T : 0;
+  if (nchunks > 0 && __any_sync(0xffffffffu, a.run || b.run)) {
+    const uint32_t st0 = smem_u32(stages), bar0 = smem_u32(bars);
+    if (lane == 0) {
+      mbar_init(bar0, 1u);
+      mbar_init(bar0 + 8u, 1u);
+      fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) {
+      tma_chunk(tmap, st0, bar0, k0, j0);
+      if (nchunks > 1) tma_chunk(tmap, st0 + kTmaStageBytes, bar0 + 8u, k0, j0 + T);
+    }
+    int issued = nchunks > 1 ? 2 : 1;
+    int waited = 0;
+    bool timed_out = false;
+    for (int c = 0; c < nchunks; ++c) {
+      const int sg = c & 1;
+      const uint32_t bar = bar0 + 8u * static_cast<uint32_t>(sg);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, static_cast<uint32_t>((c >> 1) & 1)));
+      if (!ok) {
+        timed_out = true;
+        break;
+      }
+      waited = c + 1;
+      const float* e = stages + sg * kTmaStageFloats + lane;
+      const int nst = j_end - (j0 + c * T) < T ? j_end - (j0 + c * T) : T;
+      const int da = (a.run && deadA != nullptr) ? *deadA : 0;
+      const int db = (b.run && deadB != nullptr) ? *deadB : 0;
+      if (nst == T) {
+        float bma = inf_v<float>(), nfa = 0.0f, bmb = inf_v<float>(), nfb = 0.0f;
+        if (a.run && b.run) {
+          tma_pair_chunk<T>(a, b, K, CA, CB, S, e, bma, nfa, bmb, nfb);
+          *paired += 2u * T;
+          tma_traj_chunk_end(a, bma, nfa, T, j_end, thr, band, da, markA);
+          tma_traj_chunk_end(b, bmb, nfb, T, j_end, thr, band, db, markB);
+        } else if (a.run) {
+          tma_traj_chunk<T>(a, K, CA, S, e, bma, nfa);
+          tma_traj_chunk_end(a, bma, nfa, T, j_end, thr, band, da, markA);
+        } else if (b.run) {
+          tma_traj_chunk<T>(b, K, CB, S, e, bmb, nfb);
+          tma_traj_chunk_end(b, bmb, nfb, T, j_end, thr, band, db, markB);
+        }
+      } else {
+        tma_traj_tail(a, K, CA, S, e, T, nst, thr, band, markA);
+        tma_traj_tail(b, K, CB, S, e, T, nst, thr, band, markB);
+      }
+      if (!__any_sync(0xffffffffu, a.run || b.run)) break;
+      // every lane is done reading this stage: refill it with chunk c + 2
+      __syncwarp();
+      if (c + 2 < nchunks) {
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          tma_chunk(tmap, st0 + static_cast<uint32_t>(sg) * kTmaStageBytes, bar, k0, j0 + (c + 2) * T);
+        }
+        issued = c + 3;
+      }
+    }
+    bool drained = true;
+    for (int c = waited; c < issued; ++c)
+      drained = mbar_wait_bounded(bar0 + 8u * static_cast<uint32_t>(c & 1),
+                                  static_cast<uint32_t>((c >> 1) & 1)) && drained;
+    drained = __all_sync(0xffffffffu, drained);
+    if (timed_out || !drained) {
+      if (lane == 0) atomicAdd(timeouts, 1ull);
+      if (a.run) {
+        a.smin = -inf_v<float>();
+        a.how = LANE_VIOLATED;
+        a.run = false;
+      }
+      if (b.run) {
+        b.smin = -inf_v<float>();
+        b.how = LANE_VIOLATED;
+        b.run = false;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && drained) {
+      mbar_inval(bar0);
+      mbar_inval(bar0 + 8u);
+    }
+  }
+}
+
 // Disturbance component of Philox word w with half-range a: the binary32
 // copy (top 24 bits, a 2^-23 folded in) or the binary64 value, exactly as the
 // sampler stores them.

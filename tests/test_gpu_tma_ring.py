@@ -217,3 +217,105 @@ def test_tma_auto_takes_large_launches_only(R, orc, params):
             a1, m1, _ = res[(N, R.TMA_NEVER)]
             np.testing.assert_array_equal(a0, a1)
             _same(m0, m1)
+
+
+# ------------------------------------------- two candidates per thread --
+@pytest.mark.parametrize("N,H", [(1000, 203), (4096, 600), (36, 65)])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_recheck"])
+@pytest.mark.parametrize("unc", [0.0, 0.1])
+@pytest.mark.parametrize("early", [0, 1, 2])
+def test_tma_pairs_equal_single_lanes(R, orc, params, N, H, prec, unc, early):
+    """Two candidates per thread on the TMA ring (RRG_TMA_ALWAYS with
+    RRG_PAIR_ALWAYS) against one per thread on the per-lane ring: identical
+    flags, P and min slacks (every one without an early exit, the admissible
+    candidates' with one); 13 rows leave the last pair with one candidate."""
+    p = R.FP32 if prec == "fp32" else R.FP32_RECHECK
+    kappas = np.linspace(0.0, 1.0, 13)
+    x_t = orc.equilibrium(params, 100.0) * np.array([1.0, 1.03, 1.0])
+    with R.Governor(params, _cfg(R, N, H, precision=p, early_exit=early, param_unc_rel=unc)) as g:
+        g.sample_scenarios(5, 2)
+        g.set_tma(R.TMA_NEVER)
+        g.set_pairing(R.PAIR_NEVER)
+        a0, m0, P0 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        g.set_tma(R.TMA_ALWAYS)
+        g.set_pairing(R.PAIR_ALWAYS)
+        g.reset_stats()
+        a1, m1, P1 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        st = g.stats()
+    assert st["wait_timeouts"] == 0
+    assert st["lane_steps_paired"] > 0
+    assert st["lane_steps_tma"] == st["lane_steps"] - st["lane_steps_fp64"]
+    np.testing.assert_array_equal(a1, a0)
+    np.testing.assert_array_equal(P1, P0)
+    if early == 0:
+        _same(m1, m0)
+    else:
+        _same(m1[a0 == 1], m0[a0 == 1])
+
+
+@pytest.mark.parametrize("unc", [0.0, 0.1])
+def test_tma_pairs_decide_like_the_oracle(R, orc, params, unc):
+    N, H, seed, upd = 1000, 203, 3, 4
+    kappas = np.linspace(0.0, 0.06, 25) if unc else np.linspace(0.09, 0.115, 26)
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, _cfg(R, N, H, max_candidates=32, early_exit=R.EXIT_LANE, param_unc_rel=unc)) as g:
+        g.set_tma(R.TMA_ALWAYS)
+        g.set_pairing(R.PAIR_ALWAYS)
+        g.sample_scenarios(seed, upd)
+        adm, _, P = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        assert g.stats()["lane_steps_paired"] > 0
+    d = orc.sample_disturbances(seed, upd, N, H, inputs.DIST_AMP)
+    mult = orc.sample_param_multipliers(seed, upd, N, unc, MASK) if unc else None
+    with orc.param_multipliers(mult):
+        a_o, _, P_o, _ = orc.eval_candidates(params, orc.cfg(H=H, N=N, early_exit=0), x_t, 100.0, 250.0,
+                                             kappas, d, want_P=True, nthreads=NTH)
+    np.testing.assert_array_equal(adm, a_o)
+    np.testing.assert_array_equal(P, P_o)
+
+
+@pytest.mark.parametrize("probe", [0, 20])
+def test_tma_pairs_in_searches_and_closed_loop(R, orc, params, probe):
+    """Searches (pipelined rounds keep single lanes, the rounds after them
+    pair) and the closed loop give the same results with pairs on the TMA
+    ring as with single lanes on the per-lane ring, and the oracle's joint
+    bisection."""
+    N, H, seed, upd = 1024, 500, 3, 7
+    cases = [(100.0, 250.0, orc.equilibrium(params, 100.0)),
+             (180.0, 90.0, orc.equilibrium(params, 180.0) * np.array([1.02, 0.99, 1.01]))]
+    r_seq = np.array([250.0] * 2 + [120.0] * 2)
+    out, loops = {}, {}
+    with R.Governor(params, _cfg(R, N, H, max_candidates=64, probe_steps=probe)) as g:
+        for tma, pair in ((R.TMA_ALWAYS, R.PAIR_ALWAYS), (R.TMA_NEVER, R.PAIR_NEVER)):
+            g.set_tma(tma)
+            g.set_pairing(pair)
+            g.sample_scenarios(seed, upd)
+            out[tma] = [g.step(x_t, r, v_prev) for v_prev, r, x_t in cases]
+            loops[tma] = g.closed_loop(orc.equilibrium(params, 100.0), 100.0, r_seq, 9, 0, inputs.DIST_AMP)
+            assert g.stats()["wait_timeouts"] == 0
+    assert out[R.TMA_ALWAYS] == out[R.TMA_NEVER]
+    for a, c in zip(loops[R.TMA_ALWAYS], loops[R.TMA_NEVER]):
+        np.testing.assert_array_equal(np.asarray(a), np.asarray(c))
+    d = orc.sample_disturbances(seed, upd, N, H, inputs.DIST_AMP)
+    for (v_prev, r, x_t), (_, k, f) in zip(cases, out[R.TMA_ALWAYS]):
+        assert (k, f) == orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, v_prev, r, 12, d, nthreads=NTH)
+
+
+def test_tma_pairs_wait_timeout(R, orc, params):
+    """The injected timeout with pairs: counted, nothing admissible, and the
+    handle recovers."""
+    N, H = 1000, 100
+    kappas = np.linspace(0.0, 0.2, 7)
+    x_t = orc.equilibrium(params, 100.0)
+    with R.Governor(params, _cfg(R, N, H, early_exit=R.EXIT_LANE)) as g:
+        g.set_tma(R.TMA_ALWAYS)
+        g.set_pairing(R.PAIR_ALWAYS)
+        g.sample_scenarios(1, 1)
+        a0, _, P0 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        g.set_injection(R.INJECT_TMA_NO_COPY)
+        g.reset_stats()
+        a1, _, P1 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+        assert g.stats()["wait_timeouts"] > 0 and not a1.any() and not P1.any()
+        g.set_injection(0)
+        a2, _, P2 = g.eval_candidates(x_t, 100.0, 250.0, kappas, want_P=True)
+    np.testing.assert_array_equal(a2, a0)
+    np.testing.assert_array_equal(P2, P0)
