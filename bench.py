@@ -103,14 +103,14 @@ SWEEP_CASE = (100.0, 150.0)     # v_prev, r_t: x_t at the equilibrium of v_prev
 # rollout's sources are the ones profiled: the trajectory loops and model
 # (rrg_lane.cuh, rrg_device.cuh), the rollout kernels and their dispatch in
 # rrg_kernels.cu, and the Launch struct (sha1 of each region)
-TRAFFIC_PER_LAUNCH = (433920 + 24625152 + 35840 + 35840) / 4
+TRAFFIC_PER_LAUNCH = (433664 + 24614656 + 35840 + 35584) / 4
 TRAFFIC_SOURCES = (
-    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "6974a9bcf1f03779f0a0b2b8b315615007072de0"),
+    ("paper_2510_08288_gb300/csrc/rrg_lane.cuh", None, None, "bb86588f91e49ec177d60d8ba804f8f0da51ccab"),
     ("paper_2510_08288_gb300/csrc/rrg_device.cuh", None, None, "1ef24ed4a16f67f78ee586ee6229fd831974dc8e"),
     ("paper_2510_08288_gb300/csrc/rrg_kernels.cu", "// Where a rollout lane takes its disturbances from.",
-     "// Binary64 re-run of the trajectories", "a84c48ddcffea78ff0046eb2a42f5af85977e10a"),
+     "// Binary64 re-run of the trajectories", "69650da0e7a4601cab97766b63f3c5ad23e6b113"),
     ("paper_2510_08288_gb300/csrc/rrg_internal.h", "struct Launch {", "\n};\n",
-     "b6965d96ced6990869710984b1659f342995ad8b"),
+     "fb4621135eb51875cc90e855eb357a809ab05b13"),
 )
 
 
@@ -130,7 +130,7 @@ def source_region(rel, begin, end):
 # one pass over the three launches of the first timed update).  Each round
 # reads the array once per candidate that is still running (tile-major order;
 # the 3.9 GB array does not fit in L2), up to 16 times the algorithmic bytes.
-SWEEP_TRAFFIC_64K = (7910840064 + 3330816 + 19834391552 + 548352 + 51305616640 + 654592) / 3
+SWEEP_TRAFFIC_64K = (7911768832 + 3319040 + 19845668096 + 436992 + 51305741824 + 906496) / 3
 # warp instructions per trajectory-step of the TMA-ring kernel there (22.50 G
 # over 6.56 G lane-steps in the same capture)
 TMA_INSTR_PER_STEP = 110
@@ -142,13 +142,13 @@ TMA_INSTR_PER_STEP = 110
 # the 3.8 MB of checkpoints and lane minima stay in L2 during the launch),
 # valid while the forward kernel, its launch, the step and the Launch struct
 # are the ones profiled
-ADJ_TRAFFIC_PER_LAUNCH = 49196544 + 4864
+ADJ_TRAFFIC_PER_LAUNCH = 49196544 + 4096
 ADJ_TRAFFIC_SOURCES = (
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', 'b726a6442e28e5a458abb23e2651863f42659404'),
     ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
     ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
-    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, '6974a9bcf1f03779f0a0b2b8b315615007072de0'),
-    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', 'b6965d96ced6990869710984b1659f342995ad8b'),
+    ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, 'bb86588f91e49ec177d60d8ba804f8f0da51ccab'),
+    ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', 'fb4621135eb51875cc90e855eb357a809ab05b13'),
 )
 
 
