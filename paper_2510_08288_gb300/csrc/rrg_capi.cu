@@ -67,6 +67,11 @@ struct rrg_ctx {
   uint64_t cl_key_seed = 0, cl_key_t0 = 0;
   uint64_t cl_per = 0, cl_rl_per = 0, cl_rd_per = 0;
   bool cl_conditional = false;  // the cached graph uses a conditional node
+  // the captured search of rrg_step (fixed io_dev / flag_dev pointers),
+  // discarded whenever the launch descriptor changes (fill_launch)
+  cudaGraphExec_t st_exec = nullptr;
+  uint64_t st_per = 0, st_rl_per = 0, st_rd_per = 0;
+  bool st_refused = false;      // the graph API refused: rrg_step launches directly
   SearchState* st = nullptr;
   double* cand_kappa = nullptr;
   double* cand_v = nullptr;
@@ -199,6 +204,7 @@ void free_all(rrg_ctx* h) {
   for (auto& pr : h->ev_roll) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto& pr : h->ev_rec) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (h->cl_exec) cudaGraphExecDestroy(h->cl_exec);
+  if (h->st_exec) cudaGraphExecDestroy(h->st_exec);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -206,6 +212,11 @@ void free_all(rrg_ctx* h) {
 }
 
 void fill_launch(rrg_ctx* h) {
+  if (h->st_exec) {  // the captured step graph holds the old descriptor
+    cudaGraphExecDestroy(h->st_exec);
+    h->st_exec = nullptr;
+  }
+  h->st_refused = false;  // a new descriptor may capture where the old one did not
   Launch& L = h->L;
   const rrg_config& c = h->cfg;
   L.stream = h->stream;
@@ -893,6 +904,112 @@ int rrg_slack_error(rrg_handle h, const double* x_t, double v_prev, double r_t,
   return RRG_OK;
 }
 
+// The search of rrg_step, captured once on the handle's fixed io pointers:
+// with a pipelined search the rounds after the pipelined pair sit in a
+// conditional node (as in the closed-loop graph), else, or if the graph API
+// refuses a step, the plain sequence.  Sets the host counters one replay adds
+// (the conditional body's are added on the device when it runs); nullptr if
+// nothing could be captured.
+cudaGraphExec_t capture_step(rrg_ctx* h) {
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  double* io = h->io_dev;
+  const uint64_t l0 = h->launches, r0 = h->rollout_launches, d0 = h->rounds;
+  auto end_capture = [&]() {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(h->stream, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+  };
+  cudaGraph_t G = nullptr;
+  if (search_pipelined(h->scfg, h->cfg.horizon)) {
+    bool ok = cudaGraphCreate(&G, 0) == cudaSuccess;
+    cudaGraphConditionalHandle hc = 0;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&hc, G, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+    std::vector<cudaGraphNode_t> sinks;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, G, nullptr, nullptr, 0, mode) == cudaSuccess;
+    if (ok) {
+      h->capturing = true;
+      h->L.cond = hc;
+      extra_round_counts(h, &h->L.cond_launches, &h->L.cond_rollouts, &h->L.cond_rounds);
+      ok = enqueue_search(h, io + IO_X, io + IO_R, nullptr, io + IO_V, io + IO_OUT, io + IO_OUT + 1,
+                          h->flag_dev, -1, false) == RRG_OK;
+      h->L.cond = 0ull;
+      h->capturing = false;
+      h->st_per = h->launches - l0;
+      h->st_rl_per = h->rollout_launches - r0;
+      h->st_rd_per = h->rounds - d0;
+      if (ok) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        ok = cudaStreamGetCaptureInfo(h->stream, &st, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+             nd > 0;
+        if (ok) sinks.assign(deps, deps + nd);
+      }
+      cudaGraph_t g1 = nullptr;
+      ok = (cudaStreamEndCapture(h->stream, &g1) == cudaSuccess) && ok;
+    }
+    if (ok) {
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = hc;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cn = nullptr;
+      ok = cudaGraphAddNode(&cn, G, sinks.data(), nullptr, sinks.size(), &cp) == cudaSuccess;
+      cudaGraph_t body = ok ? cp.conditional.phGraph_out[0] : nullptr;
+      if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, mode) == cudaSuccess;
+      if (ok) {
+        h->capturing = true;
+        ok = enqueue_extra_rounds(h, io + IO_OUT, io + IO_OUT + 1, h->flag_dev) == RRG_OK;
+        h->capturing = false;
+        ok = (cudaStreamEndCapture(h->stream, &body) == cudaSuccess) && ok;
+      }
+    }
+    if (!ok) {
+      end_capture();
+      if (G) cudaGraphDestroy(G);
+      G = nullptr;
+    }
+    h->launches = l0;
+    h->rollout_launches = r0;
+    h->rounds = d0;
+  }
+  if (!G) {
+    if (cudaStreamBeginCapture(h->stream, mode) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    h->capturing = true;
+    const int rc = enqueue_search(h, io + IO_X, io + IO_R, nullptr, io + IO_V, io + IO_OUT, io + IO_OUT + 1,
+                                  h->flag_dev);
+    h->capturing = false;
+    h->st_per = h->launches - l0;
+    h->st_rl_per = h->rollout_launches - r0;
+    h->st_rd_per = h->rounds - d0;
+    h->launches = l0;
+    h->rollout_launches = r0;
+    h->rounds = d0;
+    const cudaError_t ce = cudaStreamEndCapture(h->stream, &G);
+    if (rc != RRG_OK || ce != cudaSuccess) {
+      if (G) cudaGraphDestroy(G);
+      end_capture();
+      return nullptr;
+    }
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ce = cudaGraphInstantiate(&ex, G, 0);
+  cudaGraphDestroy(G);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return ex;
+}
+
 int rrg_step(rrg_handle h, const double* x_t, double r_t, double v_prev, double* v_t,
              double* kappa, int32_t* flags) {
   if (!h) return RRG_EINVAL;
@@ -903,9 +1020,23 @@ int rrg_step(rrg_handle h, const double* x_t, double r_t, double v_prev, double*
   h->io_h[IO_R] = r_t;
   h->io_h[IO_V] = v_prev;
   CK(cudaMemcpyAsync(h->io_dev, h->io_h, 5 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  int rc = enqueue_search(h, h->io_dev + IO_X, h->io_dev + IO_R, nullptr, h->io_dev + IO_V,
-                          h->io_dev + IO_OUT, h->io_dev + IO_OUT + 1, h->flag_dev);
-  if (rc != RRG_OK) return rc;
+  // the search as one graph replay (its launch gaps cost about 50 us per
+  // update when enqueued kernel by kernel), except while the library times
+  // rollout launches (profiling), which needs the direct launches' events
+  if (!h->profiling && !h->st_exec && !h->st_refused) {
+    h->st_exec = capture_step(h);
+    h->st_refused = h->st_exec == nullptr;
+  }
+  if (!h->profiling && h->st_exec) {
+    CK(cudaGraphLaunch(h->st_exec, h->stream));
+    h->launches += h->st_per;
+    h->rollout_launches += h->st_rl_per;
+    h->rounds += h->st_rd_per;
+  } else {
+    int rc = enqueue_search(h, h->io_dev + IO_X, h->io_dev + IO_R, nullptr, h->io_dev + IO_V,
+                            h->io_dev + IO_OUT, h->io_dev + IO_OUT + 1, h->flag_dev);
+    if (rc != RRG_OK) return rc;
+  }
   CK(cudaMemcpyAsync(h->io_h + IO_OUT, h->io_dev + IO_OUT, 2 * sizeof(double),
                      cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->flag_h, h->flag_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
@@ -1003,6 +1134,10 @@ int rrg_closed_loop_dev(rrg_handle h, const double* x0, double v0, const double*
     if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    if (h->st_exec) {
+      cudaGraphExecDestroy(h->st_exec);
+      h->st_exec = nullptr;
+    }
     if (h->tma_ok && !encode_scenario_map(&h->tmap[1], h->d32b, h->cfg.n_scenarios, h->cfg.horizon)) {
       h->tma_ok = false;  // the rings fall back to per-lane asynchronous copies
       h->L.tmap = nullptr;

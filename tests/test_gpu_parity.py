@@ -634,3 +634,37 @@ def test_closed_loop_graph_runs_remaining_rounds_when_needed(R, orc, params, m, 
     vo, ko, fo, xo = orc.closed_loop(params, orc.cfg(H=H, N=N), x0, 100.0, r_seq, 2, 0, amp, amp, search=0)
     np.testing.assert_array_equal(runs[1][1], ko)
     np.testing.assert_array_equal(runs[1][2], fo)
+
+
+@pytest.mark.parametrize("kind,probe", [("spec", 0), ("spec", 32), ("spec", 128), ("ksection", 0), ("bisect", 0)])
+def test_step_graph_equals_direct_launches(R, orc, params, kind, probe):
+    """rrg_step replays its search as a captured graph (with a pipelined search
+    the rounds after the pipelined pair sit in a conditional node); with the
+    library's rollout timing on it launches directly.  Both give the same
+    results on a sequence of inputs, the graph is rebuilt after a shape
+    change, and each equals the oracle's joint bisection (Alg. 1)."""
+    N, H, seed = 512, 300, 4
+    search = {"spec": R.SEARCH_SPEC_BISECT, "ksection": R.SEARCH_KSECTION, "bisect": R.SEARCH_BISECT}[kind]
+    cases = [(100.0, 250.0, orc.equilibrium(params, 100.0)),
+             (180.0, 90.0, orc.equilibrium(params, 180.0) * np.array([1.02, 0.99, 1.01])),
+             (60.0, 280.0, orc.equilibrium(params, 60.0)),
+             (250.0, 260.0, orc.equilibrium(params, 250.0))]
+    cfg = _cfg(R, N, H, search=search, precision=R.FP32_RECHECK, max_candidates=64, probe_steps=probe,
+               recheck_eps_rel=1e-6)
+    res = {}
+    with R.Governor(params, cfg) as g:
+        for mode in ("graph", "direct", "graph_after_retune"):
+            g.set_profiling(mode == "direct")
+            if mode == "graph_after_retune" and kind == "spec":
+                g.set_tuning(16, probe)
+            out = []
+            for t, (v_prev, r, x_t) in enumerate(cases):
+                g.sample_scenarios(seed, t)
+                out.append(g.step(x_t, r, v_prev))
+            res[mode] = out
+        g.set_profiling(False)
+    assert res["graph"] == res["direct"] == res["graph_after_retune"]
+    if kind != "ksection":
+        for t, ((v_prev, r, x_t), (_, k, f)) in enumerate(zip(cases, res["graph"])):
+            d = orc.sample_disturbances(seed, t, N, H, inputs.DIST_AMP)
+            assert (k, f) == orc.bisect_joint(params, orc.cfg(H=H, N=N), x_t, v_prev, r, 12, d)
