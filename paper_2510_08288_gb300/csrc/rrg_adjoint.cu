@@ -340,13 +340,12 @@ adjoint_forward_kernel(const Launch L, const DT* __restrict__ d, int checkpoint,
 // slot's lanes; out[i * kOutStride + 0] = g, [1], [2] = k*, j* (as long long).
 constexpr int kOutStride = kAdjOutStride;
 
-__global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
-                                      const int* __restrict__ lane_arg, int N, double* out) {
-  __shared__ double sv[256];
-  __shared__ int sk[256];
-  const int i = blockIdx.x;
-  const double* lm = lane_min + static_cast<size_t>(i) * N;
-  const int* la = lane_arg + static_cast<size_t>(i) * N;
+// The argmin of slot i by the whole block (blockDim a power of two, at most
+// the shared arrays' size): the smallest lane minimum, and among equal ones
+// the smallest k, which the reduction order cannot change; written to
+// o[0..2] by thread 0, visible to the block after its closing barrier.
+__device__ void block_argmin(const double* __restrict__ lm, const int* __restrict__ la, int N, double* o,
+                             double* sv, int* sk) {
   double best = INFINITY;
   int bk = 0x7fffffff;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -356,10 +355,10 @@ __global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
   sv[threadIdx.x] = best;
   sk[threadIdx.x] = bk;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      const double s = sv[threadIdx.x + o];
-      const int kk = sk[threadIdx.x + o];
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double s = sv[threadIdx.x + w];
+      const int kk = sk[threadIdx.x + w];
       if (s < sv[threadIdx.x] || (s == sv[threadIdx.x] && kk < sk[threadIdx.x])) {
         sv[threadIdx.x] = s;
         sk[threadIdx.x] = kk;
@@ -368,11 +367,20 @@ __global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double* o = out + static_cast<size_t>(i) * kOutStride;
     long long kj[2] = {sk[0], (sk[0] >= 0 && sk[0] < N) ? la[sk[0]] : 0};
     o[0] = sv[0];
     memcpy(o + 1, kj, sizeof kj);
   }
+  __syncthreads();
+}
+
+__global__ void adjoint_argmin_kernel(const double* __restrict__ lane_min,
+                                      const int* __restrict__ lane_arg, int N, double* out) {
+  __shared__ double sv[256];
+  __shared__ int sk[256];
+  const int i = blockIdx.x;
+  block_argmin(lane_min + static_cast<size_t>(i) * N, lane_arg + static_cast<size_t>(i) * N, N,
+               out + static_cast<size_t>(i) * kOutStride, sv, sk);
 }
 
 // Values stored per step of the recomputed trajectory: x_j and the three
@@ -392,12 +400,21 @@ constexpr int kRevThreads = 128;
 // out[0] = dg/dkappa, out[1..3] = dg/dx_t, out[4..4+NPARAM) = dg/dtheta.
 template <typename T, typename DT>
 __global__ void __launch_bounds__(kRevThreads)
-adjoint_reverse_kernel(const Launch L, const DT* __restrict__ d, double v_prev, double r,
+adjoint_reverse_kernel(const Launch L, const DT* __restrict__ d,
                        int checkpoint, const double* __restrict__ ckpt, T* __restrict__ seg_all,
-                       double* __restrict__ out_all, int slot0) {
+                       double* __restrict__ out_all, int slot0, const double* __restrict__ lane_min,
+                       const int* __restrict__ lane_arg) {
   const int i = slot0 + static_cast<int>(blockIdx.x);  // candidate slot
   const int N = L.N, H = L.H;
+  // the inputs of the candidate set-up the forward pass ran on
+  const double v_prev = L.st->v_prev, r = L.st->r;
   double* o = out_all + static_cast<size_t>(i) * kOutStride;
+  if (lane_min != nullptr) {
+    // the argmin first, by this block (one launch fewer than a separate pass)
+    __shared__ double sv[kRevThreads];
+    __shared__ int sk[kRevThreads];
+    block_argmin(lane_min + static_cast<size_t>(i) * N, lane_arg + static_cast<size_t>(i) * N, N, o, sv, sk);
+  }
   long long kj[2];
   memcpy(kj, o + 1, sizeof kj);
   double* out = o + 3;
@@ -548,7 +565,7 @@ bool reads32(const Launch& L, bool fp64) { return !fp64 && L.precision != RRG_FP
 
 cudaError_t launch_adjoint_forward(const Launch& L, bool fp64, int m, int checkpoint, double* ckpt,
                                    double* lane_min, int* lane_arg, double* d_out,
-                                   cudaEvent_t fwd_begin, cudaEvent_t fwd_end) {
+                                   cudaEvent_t fwd_begin, cudaEvent_t fwd_end, bool argmin) {
   // one warp per block until blocks of 128 threads would fill every SM:
   // each scenario is one dependent chain, so spreading them over SMs costs
   // nothing
@@ -575,23 +592,23 @@ cudaError_t launch_adjoint_forward(const Launch& L, bool fp64, int m, int checkp
     e = cudaEventRecord(fwd_end, L.stream);
     if (e != cudaSuccess) return e;
   }
-  adjoint_argmin_kernel<<<m, 256, 0, L.stream>>>(lane_min, lane_arg, L.N, d_out);
+  if (argmin) adjoint_argmin_kernel<<<m, 256, 0, L.stream>>>(lane_min, lane_arg, L.N, d_out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_reverse(const Launch& L, bool fp64, int slot0, int count, double v_prev,
-                                   double r, int checkpoint, const double* ckpt, void* seg,
-                                   double* d_out) {
+cudaError_t launch_adjoint_reverse(const Launch& L, bool fp64, int slot0, int count, int checkpoint,
+                                   const double* ckpt, void* seg, double* d_out, const double* lane_min,
+                                   const int* lane_arg) {
   if (count < 1 || slot0 < 0) return cudaErrorInvalidConfiguration;
   if (fp64)
     adjoint_reverse_kernel<double, double><<<count, kRevThreads, 0, L.stream>>>(
-        L, L.d64, v_prev, r, checkpoint, ckpt, static_cast<double*>(seg), d_out, slot0);
+        L, L.d64, checkpoint, ckpt, static_cast<double*>(seg), d_out, slot0, lane_min, lane_arg);
   else if (reads32(L, fp64))
     adjoint_reverse_kernel<float, float><<<count, kRevThreads, 0, L.stream>>>(
-        L, L.d32, v_prev, r, checkpoint, ckpt, static_cast<float*>(seg), d_out, slot0);
+        L, L.d32, checkpoint, ckpt, static_cast<float*>(seg), d_out, slot0, lane_min, lane_arg);
   else
     adjoint_reverse_kernel<float, double><<<count, kRevThreads, 0, L.stream>>>(
-        L, L.d64, v_prev, r, checkpoint, ckpt, static_cast<float*>(seg), d_out, slot0);
+        L, L.d64, checkpoint, ckpt, static_cast<float*>(seg), d_out, slot0, lane_min, lane_arg);
   return cudaGetLastError();
 }
 

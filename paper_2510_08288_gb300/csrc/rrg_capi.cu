@@ -57,6 +57,8 @@ struct rrg_ctx {
   double* adj_seg = nullptr;
   size_t adj_seg_cap = 0;
   double* adj_out = nullptr;   // [0] g, [1..2] k*, j* (as long long), [3..] gradient
+  double* adj_out_h = nullptr;  // pinned host copies of adj_out and the steady-state flags
+  int32_t* adj_ss_h = nullptr;
   // binary32-vs-binary64 slack error per lane (allocated on first use)
   void* err_buf = nullptr;
   size_t err_cap = 0;
@@ -72,6 +74,13 @@ struct rrg_ctx {
   cudaGraphExec_t st_exec = nullptr;
   uint64_t st_per = 0, st_rl_per = 0, st_rd_per = 0;
   bool st_refused = false;      // the graph API refused: rrg_step launches directly
+  // the captured gradient call (rrg_slack_gradients), keyed by its shape and
+  // the adjoint buffers
+  cudaGraphExec_t ad_exec = nullptr;
+  int ad_m = 0, ad_ck = 0, ad_prec = -1;
+  const void* ad_key[5] = {};
+  uint64_t ad_per = 0, ad_rl_per = 0;
+  bool ad_refused = false;
   SearchState* st = nullptr;
   double* cand_kappa = nullptr;
   double* cand_v = nullptr;
@@ -205,6 +214,9 @@ void free_all(rrg_ctx* h) {
   for (auto& pr : h->ev_rec) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (h->cl_exec) cudaGraphExecDestroy(h->cl_exec);
   if (h->st_exec) cudaGraphExecDestroy(h->st_exec);
+  if (h->ad_exec) cudaGraphExecDestroy(h->ad_exec);
+  if (h->adj_out_h) cudaFreeHost(h->adj_out_h);
+  if (h->adj_ss_h) cudaFreeHost(h->adj_ss_h);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -217,6 +229,11 @@ void fill_launch(rrg_ctx* h) {
     h->st_exec = nullptr;
   }
   h->st_refused = false;  // a new descriptor may capture where the old one did not
+  if (h->ad_exec) {
+    cudaGraphExecDestroy(h->ad_exec);
+    h->ad_exec = nullptr;
+  }
+  h->ad_refused = false;
   Launch& L = h->L;
   const rrg_config& c = h->cfg;
   L.stream = h->stream;
@@ -520,23 +537,37 @@ int adj_buffers(rrg_ctx* h, size_t M, int checkpoint) {
     CK(grow(&h->adj_out, &c3, static_cast<size_t>(h->cfg.max_candidates) * kAdjOutStride));
     h->adj_lane_cap = M * N;
   }
+  // pinned staging of the results: a pageable destination would make each
+  // read a staged copy
+  if (!h->adj_out_h)
+    CK(cudaMallocHost(reinterpret_cast<void**>(&h->adj_out_h),
+                      static_cast<size_t>(h->cfg.max_candidates) * kAdjOutStride * sizeof(double)));
+  if (!h->adj_ss_h)
+    CK(cudaMallocHost(reinterpret_cast<void**>(&h->adj_ss_h),
+                      static_cast<size_t>(h->cfg.max_candidates) * sizeof(int32_t)));
   return RRG_OK;
 }
 
-// Enqueues the candidate set-up of m kappas, the binary64 scenario fill if
-// the gradient reads it, the forward pass and the argmin (no sync).
-int adj_enqueue_forward(rrg_ctx* h, const double* x_t, double v_prev, double r_t, const double* kappas,
-                        int m, int checkpoint, int precision) {
-  int rc = adj_buffers(h, static_cast<size_t>(m), checkpoint);
-  if (rc != RRG_OK) return rc;
+// The inputs of an adjoint call into io_dev (x_t, r_t, v_prev) and kap_dev
+// (the m kappas), from the pinned staging.
+int adj_upload(rrg_ctx* h, const double* x_t, double v_prev, double r_t, const double* kappas, int m) {
   double* kap_h = h->io_h + IO_LEN;
   std::memcpy(h->io_h + IO_X, x_t, 3 * sizeof(double));
+  h->io_h[IO_R] = r_t;
+  h->io_h[IO_V] = v_prev;
   std::memcpy(kap_h, kappas, static_cast<size_t>(m) * sizeof(double));
   CK(cudaMemcpyAsync(h->io_dev, h->io_h, IO_LEN * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->kap_dev, kap_h, m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  return RRG_OK;
+}
+
+// Enqueues the candidate set-up of the m uploaded kappas (v_prev and r read
+// on the device), the binary64 scenario fill if the gradient reads it, the
+// forward pass and the argmin (no sync; buffers sized by adj_buffers).
+int adj_enqueue_forward_kernels(rrg_ctx* h, int m, int checkpoint, int precision, bool argmin) {
   const Launch& L = h->L;
   // candidate set-up (kappas, setpoints, rollout constants, steady-state check)
-  CK(launch_eval_prepare(L, h->io_dev + IO_X, v_prev, r_t, h->kap_dev, m));
+  CK(launch_eval_prepare(L, h->io_dev + IO_X, 0.0, 0.0, h->kap_dev, m, h->io_dev + IO_V, h->io_dev + IO_R));
   CK(launch_prepare(L, m));
   h->launches += 2;
   const bool use32 = precision == RRG_FP32 && h->cfg.precision != RRG_FP64 && !h->cfg.scenarios_in_register;
@@ -553,32 +584,75 @@ int adj_enqueue_forward(rrg_ctx* h, const double* x_t, double v_prev, double r_t
     ea = eb = nullptr;
   }
   CK(launch_adjoint_forward(L, precision == RRG_FP64, m, checkpoint, h->adj_ckpt, h->adj_lane_min,
-                            h->adj_lane_arg, h->adj_out, ea, eb));
+                            h->adj_lane_arg, h->adj_out, ea, eb, argmin));
   if (ea) h->ev_roll.emplace_back(ea, eb);
-  h->launches += 2;
+  h->launches += argmin ? 2 : 1;
   h->rollout_launches += 1;
   return RRG_OK;
 }
 
-int adj_enqueue_reverse(rrg_ctx* h, int slot0, int count, double v_prev, double r_t, int checkpoint,
-                        int precision) {
-  CK(launch_adjoint_reverse(h->L, precision == RRG_FP64, slot0, count, v_prev, r_t, checkpoint,
-                            h->adj_ckpt, h->adj_seg, h->adj_out));
+int adj_enqueue_forward(rrg_ctx* h, const double* x_t, double v_prev, double r_t, const double* kappas,
+                        int m, int checkpoint, int precision, bool argmin = true) {
+  int rc = adj_buffers(h, static_cast<size_t>(m), checkpoint);
+  if (rc == RRG_OK) rc = adj_upload(h, x_t, v_prev, r_t, kappas, m);
+  if (rc == RRG_OK) rc = adj_enqueue_forward_kernels(h, m, checkpoint, precision, argmin);
+  return rc;
+}
+
+// with_argmin: the reverse sweep finds each slot's argmin itself (after a
+// forward pass enqueued without its argmin pass).
+int adj_enqueue_reverse(rrg_ctx* h, int slot0, int count, int checkpoint, int precision,
+                        bool with_argmin = false) {
+  CK(launch_adjoint_reverse(h->L, precision == RRG_FP64, slot0, count, checkpoint, h->adj_ckpt, h->adj_seg,
+                            h->adj_out, with_argmin ? h->adj_lane_min : nullptr,
+                            with_argmin ? h->adj_lane_arg : nullptr));
   h->launches += 1;
   return RRG_OK;
+}
+
+// The kernels of one gradient call (set-up, forward pass, reverse sweeps with
+// their argmin) captured as a graph on the handle's fixed buffers; sets the
+// host counters one replay adds.  nullptr if the capture fails.
+cudaGraphExec_t capture_gradient(rrg_ctx* h, int m, int checkpoint, int precision) {
+  const uint64_t l0 = h->launches, r0 = h->rollout_launches;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  h->capturing = true;
+  int rc = adj_enqueue_forward_kernels(h, m, checkpoint, precision, false);
+  if (rc == RRG_OK) rc = adj_enqueue_reverse(h, 0, m, checkpoint, precision, true);
+  h->capturing = false;
+  h->ad_per = h->launches - l0;
+  h->ad_rl_per = h->rollout_launches - r0;
+  h->launches = l0;
+  h->rollout_launches = r0;
+  cudaGraph_t G = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(h->stream, &G);
+  if (rc != RRG_OK || ce != cudaSuccess) {
+    if (G) cudaGraphDestroy(G);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ci = cudaGraphInstantiate(&ex, G, 0);
+  cudaGraphDestroy(G);
+  if (ci != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return ex;
 }
 
 // Reads slots 0..m-1 of the adjoint's output (and the steady-state flags)
 // after the stream drained.
 int adj_read(rrg_ctx* h, int m, std::vector<double>* out, std::vector<int32_t>* ss) {
-  out->resize(static_cast<size_t>(m) * kAdjOutStride);
-  CK(cudaMemcpyAsync(out->data(), h->adj_out, out->size() * sizeof(double), cudaMemcpyDeviceToHost,
-                     h->stream));
-  if (ss) {
-    ss->resize(static_cast<size_t>(m));
-    CK(cudaMemcpyAsync(ss->data(), h->cand_ss, m * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
-  }
+  const size_t n = static_cast<size_t>(m) * kAdjOutStride;
+  CK(cudaMemcpyAsync(h->adj_out_h, h->adj_out, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (ss) CK(cudaMemcpyAsync(h->adj_ss_h, h->cand_ss, m * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  out->assign(h->adj_out_h, h->adj_out_h + n);
+  if (ss) ss->assign(h->adj_ss_h, h->adj_ss_h + m);
   return RRG_OK;
 }
 
@@ -1308,10 +1382,36 @@ int rrg_slack_gradients(rrg_handle h, const double* x_t, double v_prev, double r
   if (precision != RRG_FP64 && precision != RRG_FP32)
     return set_err(h, RRG_EINVAL, "precision must be RRG_FP64 or RRG_FP32");
   DeviceGuard gd(h->device);
-  int rc = adj_enqueue_forward(h, x_t, v_prev, r_t, kappas, m, checkpoint, precision);
+  int rc = adj_buffers(h, static_cast<size_t>(m), checkpoint);
+  if (rc == RRG_OK) rc = adj_upload(h, x_t, v_prev, r_t, kappas, m);
   if (rc != RRG_OK) return rc;
-  rc = adj_enqueue_reverse(h, 0, m, v_prev, r_t, checkpoint, precision);
-  if (rc != RRG_OK) return rc;
+  // the kernels as one graph replay (as rrg_step), except while the library
+  // times rollout launches; the graph is keyed by the call's shape and the
+  // adjoint buffers (which adj_buffers may have reallocated)
+  const void* key[5] = {h->adj_ckpt, h->adj_seg, h->adj_lane_min, h->adj_lane_arg, h->adj_out};
+  if (h->ad_exec && (h->ad_m != m || h->ad_ck != checkpoint || h->ad_prec != precision ||
+                     std::memcmp(key, h->ad_key, sizeof key) != 0)) {
+    cudaGraphExecDestroy(h->ad_exec);
+    h->ad_exec = nullptr;
+    h->ad_refused = false;
+  }
+  if (!h->profiling && !h->ad_exec && !h->ad_refused) {
+    h->ad_exec = capture_gradient(h, m, checkpoint, precision);
+    h->ad_refused = h->ad_exec == nullptr;
+    h->ad_m = m;
+    h->ad_ck = checkpoint;
+    h->ad_prec = precision;
+    std::memcpy(h->ad_key, key, sizeof key);
+  }
+  if (!h->profiling && h->ad_exec) {
+    CK(cudaGraphLaunch(h->ad_exec, h->stream));
+    h->launches += h->ad_per;
+    h->rollout_launches += h->ad_rl_per;
+  } else {
+    rc = adj_enqueue_forward_kernels(h, m, checkpoint, precision, false);
+    if (rc == RRG_OK) rc = adj_enqueue_reverse(h, 0, m, checkpoint, precision, true);
+    if (rc != RRG_OK) return rc;
+  }
   std::vector<double> out;
   std::vector<int32_t> ss;
   rc = adj_read(h, m, &out, ss_ok ? &ss : nullptr);
@@ -1420,7 +1520,7 @@ int rrg_newton_search(rrg_handle h, const double* x_t, double r_t, double v_prev
   // argmin is the constraint's early dip, so its reverse sweep is short;
   // the admissible end's minimum often comes late in the horizon), and a
   // Newton step from there; the secant through both ends' values guards it
-  rc = adj_enqueue_reverse(h, jhi, 1, v_prev, r_t, checkpoint, precision);
+  rc = adj_enqueue_reverse(h, jhi, 1, checkpoint, precision);
   if (rc != RRG_OK) return rc;
   rc = adj_read(h, G + 1, &out, nullptr);
   if (rc != RRG_OK) return rc;

@@ -372,8 +372,11 @@ cudaError_t launch_search_mid(const Launch& L);
 // Candidate set-up for the slots the last search kernel chose: one block per
 // candidate (the binary64 equilibrium solves spread over the SMs).
 cudaError_t launch_prepare(const Launch& L, int width);
+// d_vp / d_r (optional): read v_prev and r on the device instead (a captured
+// graph replayed with new inputs).
 cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
-                                const double* d_kappas, int m);
+                                const double* d_kappas, int m, const double* d_vp = nullptr,
+                                const double* d_r = nullptr);
 cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d_min_slack);
 // Tensor map of a binary32 scenario array [3][H][N] for the TMA ring (boxes
 // of 32 scenarios x one chunk of steps x 3 components); false when N is not a
@@ -407,12 +410,16 @@ cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, d
 // Discrete adjoint of the min-slack objective (rrg_adjoint.cu), for the m
 // candidate slots the last candidate set-up prepared; layouts in the file.
 constexpr int kAdjOutStride = 3 + 4 + RRG_NPARAM;
+// argmin = false: the argmin pass is left to the reverse sweep (lane_min /
+// lane_arg given to launch_adjoint_reverse), one launch fewer.
 cudaError_t launch_adjoint_forward(const Launch& L, bool fp64, int m, int checkpoint, double* ckpt,
                                    double* lane_min, int* lane_arg, double* d_out,
-                                   cudaEvent_t fwd_begin, cudaEvent_t fwd_end);
-cudaError_t launch_adjoint_reverse(const Launch& L, bool fp64, int slot0, int count, double v_prev,
-                                   double r, int checkpoint, const double* ckpt, void* seg,
-                                   double* d_out);
+                                   cudaEvent_t fwd_begin, cudaEvent_t fwd_end, bool argmin = true);
+// The reverse sweeps read v_prev and r from the search state the candidate
+// set-up wrote.
+cudaError_t launch_adjoint_reverse(const Launch& L, bool fp64, int slot0, int count, int checkpoint,
+                                   const double* ckpt, void* seg, double* d_out,
+                                   const double* lane_min = nullptr, const int* lane_arg = nullptr);
 
 // Binary32-vs-binary64 slack error of every trajectory of the m candidates
 // the last eval_prepare + prepare set up (rrg_error.cu): per lane o = i N + k

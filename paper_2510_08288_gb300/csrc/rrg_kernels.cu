@@ -1296,12 +1296,13 @@ cudaError_t launch_search_next(const Launch& L, double* d_v_t, double* d_kappa, 
 // Explicit candidates (rrg_eval_candidates).
 __global__ void __launch_bounds__(kSearchThreads)
 eval_prepare_kernel(const Launch L, const double* __restrict__ d_x, double v_prev, double r,
-                    const double* __restrict__ d_kappas, int m) {
+                    const double* __restrict__ d_kappas, int m, const double* __restrict__ d_vp,
+                    const double* __restrict__ d_r) {
   SearchState* s = L.st;
   if (threadIdx.x == 0) {
     s->x[0] = d_x[0]; s->x[1] = d_x[1]; s->x[2] = d_x[2];
-    s->v_prev = v_prev;
-    s->r = r;
+    s->v_prev = d_vp != nullptr ? *d_vp : v_prev;
+    s->r = d_r != nullptr ? *d_r : r;
     s->m = m;
     s->done = 0;
     s->invalid = 0;
@@ -1324,8 +1325,8 @@ __global__ void eval_finish_kernel(const Launch L, int m, uint8_t* adm, double* 
 }
 
 cudaError_t launch_eval_prepare(const Launch& L, const double* d_x, double v_prev, double r,
-                                const double* d_kappas, int m) {
-  eval_prepare_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, v_prev, r, d_kappas, m);
+                                const double* d_kappas, int m, const double* d_vp, const double* d_r) {
+  eval_prepare_kernel<<<1, kSearchThreads, 0, L.stream>>>(L, d_x, v_prev, r, d_kappas, m, d_vp, d_r);
   return cudaGetLastError();
 }
 
