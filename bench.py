@@ -142,10 +142,10 @@ TMA_INSTR_PER_STEP = 110
 # the 3.8 MB of checkpoints and lane minima stay in L2 during the launch),
 # valid while the forward kernel, its launch, the step and the Launch struct
 # are the ones profiled
-ADJ_TRAFFIC_PER_LAUNCH = 49196544 + 4096
+ADJ_TRAFFIC_PER_LAUNCH = 49196288 + 3328
 ADJ_TRAFFIC_SOURCES = (
-    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', 'b726a6442e28e5a458abb23e2651863f42659404'),
-    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', '8c78a02e6d8a05f0b94d85067ed95aa0249042f4'),
+    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'constexpr int kFwdRing = 8;', '__global__ void adjoint_argmin_kernel', 'dd5593761eb2e7fa9699a30371ebecad854ba470'),
+    ('paper_2510_08288_gb300/csrc/rrg_adjoint.cu', 'cudaError_t launch_adjoint_forward(', 'adjoint_argmin_kernel<<<', 'a97cb6582368d4a124a1b7416784f62ca4ea66c5'),
     ('paper_2510_08288_gb300/csrc/rrg_device.cuh', None, None, '1ef24ed4a16f67f78ee586ee6229fd831974dc8e'),
     ('paper_2510_08288_gb300/csrc/rrg_lane.cuh', None, None, 'bb86588f91e49ec177d60d8ba804f8f0da51ccab'),
     ('paper_2510_08288_gb300/csrc/rrg_internal.h', 'struct Launch {', '\n};\n', 'fb4621135eb51875cc90e855eb357a809ab05b13'),
