@@ -102,3 +102,49 @@ def test_closed_loop_window_crosses_the_first_level_change():
     assert bench.window_start(5, 990) == 10             # the window stays inside the run
     c = bench.workload_config(115, 5, 20)
     assert "timed updates [115, 135)" in c["workload"] and "[110, 115) warm up" in c["workload"]
+
+
+def test_sweep_issue_ceiling_follows_the_kernel_that_ran():
+    """The sweep line's issue ceiling is the one of the kernel that fed most of
+    the top row's steps: the TMA ring (110 instructions per trajectory-step)
+    or the register ring (114)."""
+    tma = bench.sweep_ceiling({"tma_step_fraction": 1.0})
+    regs = bench.sweep_ceiling({"tma_step_fraction": 0.0})
+    assert abs(tma - bench.FLOPS_PER_STEP / (2.0 * bench.TMA_INSTR_PER_STEP)) < 1e-12
+    assert abs(regs - bench.ISSUE_CEILING) < 1e-12
+    assert tma > regs
+
+
+def test_batch_kernel_names():
+    assert bench.batch_kernel_name((bench.BATCH_PAIR_VARIANT, 32, 8)).startswith("batch_rollout_warp_pair_kernel<8>")
+    assert bench.batch_kernel_name((7, 32, 16)) == "batch_rollout_warp_kernel<16>"
+    assert bench.batch_kernel_name((3, 128, 16)) == "batch_rollout_kernel<128, 16>"
+
+
+def test_apply_tma_leaves_handles_without_a_tma_ring_alone():
+    """--tma auto|always on a handle that has no TMA ring (n_scenarios not a
+    multiple of 4) keeps it off instead of failing; never is always set."""
+    class FakeR:
+        TMA_NEVER, TMA_AUTO, TMA_ALWAYS = 0, 1, 2
+
+    class FakeGov:
+        def __init__(self, available):
+            self.mode = FakeR.TMA_AUTO if available else FakeR.TMA_NEVER
+            self.calls = []
+
+        def get_tma(self):
+            return self.mode
+
+        def set_tma(self, mode):
+            self.calls.append(mode)
+            self.mode = mode
+
+    g = FakeGov(available=False)
+    bench.apply_tma(FakeR, g, FakeR.TMA_ALWAYS)
+    assert g.calls == [] and g.get_tma() == FakeR.TMA_NEVER
+    bench.apply_tma(FakeR, g, FakeR.TMA_NEVER)
+    assert g.calls == [FakeR.TMA_NEVER]
+    g = FakeGov(available=True)
+    bench.apply_tma(FakeR, g, FakeR.TMA_ALWAYS)
+    assert g.calls == [FakeR.TMA_ALWAYS]
+    assert bench.TMA_MODES == ("never", "auto", "always") and len(bench.TMA_NAMES) == 3
