@@ -63,6 +63,9 @@ PROBE_STEPS = 128
 # stage points of 6, the RK4 combination of 18, the disturbance add of 3, and
 # output, slack, running min and the finiteness accumulator of 6
 FLOPS_PER_STEP = 141
+# MUFU operations per binary32 trajectory step: per right-hand side the power
+# term's lg2 and ex2 and the torque term's reciprocal, 4 evaluations per step
+MUFU_PER_STEP = 12
 # instructions a warp issues per trajectory step in the register-ring loop
 # (ncu: instructions executed by the 65,536-scenario sweep's rollout launches
 # at 32,768 scenarios over their lane-steps / 32, parametric and nominal
@@ -807,7 +810,10 @@ def run_gpu(args):
                          "frac_of_issue_ceiling": frac_of(frac_of(achieved, peak), ISSUE_CEILING),
                          "measured_units": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
                                             "mufu_ex2_tops": peaks[2],
-                                            "frac_of_measured_fp32": achieved / peaks[0]},
+                                            "frac_of_measured_fp32": achieved / peaks[0],
+                                            "mufu_per_traj_step": MUFU_PER_STEP,
+                                            "frac_of_measured_mufu": achieved / FLOPS_PER_STEP * MUFU_PER_STEP
+                                            / peaks[2]},
                          "latency": {"cycles_per_step": step_cycles, "chain_cycles_per_step": chain_cycles,
                                      "frac": frac_of(chain_cycles, step_cycles),
                                      "basis": "rollout time per update (direct launches) over the %d-step "
@@ -1520,6 +1526,7 @@ def run_sweep(args):
         torch.cuda.empty_cache()
     clk = clocks.stop()
     peak, peak_src = fp32_peak(clk)
+    unit_peaks = R.rrg_alu_peaks()   # measured FP32 FMA, FP64 FMA, MUFU throughput
     for row in rows:
         row["rollout_frac"] = frac_of(row["rollout_tflops"], peak)
     top = rows[-1]
@@ -1551,7 +1558,12 @@ def run_sweep(args):
                      "n_scenarios": top["n_scenarios"],
                      "peak_source": peak_src,
                      "issue_ceiling": sweep_ceiling(top),
-                     "frac_of_issue_ceiling": frac_of(top["rollout_frac"], sweep_ceiling(top))},
+                     "frac_of_issue_ceiling": frac_of(top["rollout_frac"], sweep_ceiling(top)),
+                     "measured_units": {"fp32_fma_tflops": unit_peaks[0], "mufu_ex2_tops": unit_peaks[2],
+                                        "frac_of_measured_fp32": top["rollout_tflops"] / unit_peaks[0],
+                                        "mufu_per_traj_step": MUFU_PER_STEP,
+                                        "frac_of_measured_mufu": top["rollout_tflops"] / FLOPS_PER_STEP
+                                        * MUFU_PER_STEP / unit_peaks[2]}},
         "cpu_baseline": cpu, "sweep": rows, "clocks": clk,
         "gpu_launches": top["gpu_launches"],
         "fp32_error": fp32_err,
