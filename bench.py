@@ -851,15 +851,23 @@ BATCH_METRIC = "RG updates/s (instance updates, batched) & trajectory-steps/s; F
 
 
 BATCH_PAIR_VARIANT = 8   # warp tiles of two candidates per thread
+BATCH_SPLIT_VARIANT = 9  # warp tiles of 16 scenarios, two lanes per trajectory
 
 
 def batch_kernel_name(variant):
     """The rollout kernel of a batch variant (index, lanes per tile, prefetch)."""
     if variant[0] == BATCH_PAIR_VARIANT:
         return "batch_rollout_warp_pair_kernel<%d> (two candidates per thread)" % variant[2]
+    if variant[0] == BATCH_SPLIT_VARIANT:
+        return "batch_rollout_split_kernel<%d> (two lanes per trajectory)" % variant[2]
     if variant[1] == 32:
         return "batch_rollout_warp_kernel<%d>" % variant[2]
     return "batch_rollout_kernel<%d, %d>" % (variant[1], variant[2])
+
+
+def batch_ceiling(variant):
+    """Issue ceiling of a batch variant's rollout (fraction of the FP32 peak), or None."""
+    return None if variant[0] == BATCH_SPLIT_VARIANT else ISSUE_CEILING
 
 
 def batch_config(S, W, K, variant):
@@ -1072,8 +1080,10 @@ def run_batch(args):
                      "timing": "%d direct-launch updates after the timed ones" % K2,
                      "flops_per_traj_step": FLOPS_PER_STEP,
                      "peak_source": peak_src,
-                     "issue_ceiling": ISSUE_CEILING,
-                     "frac_of_issue_ceiling": frac_of(frac_of(achieved, peak), ISSUE_CEILING)},
+                     # the one-lane loop's ceiling (its instructions per step were
+                     # counted); none for the two-lane split, whose were not
+                     "issue_ceiling": batch_ceiling(variant),
+                     "frac_of_issue_ceiling": frac_of(frac_of(achieved, peak), batch_ceiling(variant))},
         "autotune_rollout_ms": [float(x) for x in tune_ms] if tune_ms is not None else None,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": st["launches"],
         "rechecked_trajectories": st["rechecked"],

@@ -659,11 +659,14 @@ RRG_API int rrg_step_latency(rrg_handle h, double v, int steps, double *cycles_p
  * RRG_FP32_RECHECK; no parametric uncertainty (otherwise RRG_ENOTIMPL).  Each
  * instance's result equals rrg_step's for the same inputs and scenarios. */
 #define RRG_BATCH_MAX_INSTANCES 1024
-#define RRG_BATCH_VARIANTS 9   /* rollout variants: lanes per tile {64, 128,
+#define RRG_BATCH_VARIANTS 10  /* rollout variants: lanes per tile {64, 128,
                                   256} x disturbance prefetch depth {8, 16},
                                   then warp tiles (32 lanes, each warp takes its
                                   own) x {8, 16}, then warp tiles of two
-                                  candidates per thread (prefetch 8) */
+                                  candidates per thread (prefetch 8), then warp
+                                  tiles of 16 scenarios at two lanes per
+                                  trajectory (prefetch 8; tile_lanes reports
+                                  16) */
 typedef struct rrg_batch_ctx *rrg_batch_handle;
 
 /* cfg as for rrg_create (n_scenarios and horizon are ignored); n_scenarios

@@ -525,8 +525,196 @@ __global__ void __launch_bounds__(128) batch_rollout_warp_pair_kernel(const BLau
   }
 }
 
-// Binary64 re-run (disturbances regenerated from the Philox counters) over
-// steps 0..jlast of each listed lane.
+// ---------------------------------------------------------------------------
+// Two lanes per trajectory (warp-cooperative): the lanes 2q and 2q + 1 of a
+// warp carry scenario q of a 16-scenario tile.  Both hold the whole state and
+// form the same stage points and RK4 combination; of each right-hand side,
+// role 0 evaluates the two linear flow derivatives (d_ca, d_sm) and role 1 the
+// compressor-speed derivative with its power term and reciprocal (d_w), and
+// the pair swaps them with two shuffles.  Each component is the expression of
+// fc3_rhs_fast, so the trajectory equals the one-lane rollout bit for bit.
+// The warp issues both roles' instructions for half as many trajectories, and
+// the swap sits on every stage's dependency chain: the autotuner measures it
+// against the one-lane variants.
+__device__ __forceinline__ void fc3_rhs_split(const RhsU<float>& U, const RhsC<float>& C, int role,
+                                              float z_ca, float z_w, float z_sm, float w, float x_pw,
+                                              float& d_ca, float& d_w, float& d_sm) {
+  float v0, v1 = 0.0f;
+  if (role == 0) {
+    v0 = U.a1 * z_sm + (C.c_ca - U.a12 * z_ca);
+    v1 = U.g_w * z_w + ((C.c_sm + U.b3 * z_ca) - U.g_sm * z_sm);
+  } else {
+    const float W_cp = U.a_w * z_w + (C.W_r - U.a_p * z_sm);
+    const float f = torque_factor<float>(U, pow_m1<float>(x_pw, U.e, U.pws), w);
+    v0 = (C.e0 - U.e2 * z_w) - W_cp * f;
+  }
+  const float o0 = __shfl_xor_sync(0xffffffffu, v0, 1);
+  const float o1 = __shfl_xor_sync(0xffffffffu, v1, 1);
+  d_ca = role == 0 ? v0 : o0;
+  d_sm = role == 0 ? v1 : o1;
+  d_w = role == 0 ? o0 : v0;
+}
+
+// rk4_step_fast with the split right-hand side (the same stage points and
+// combination, in the same order).  Called by all 32 lanes.
+__device__ __forceinline__ void rk4_step_split(const RhsU<float>& U, const RhsC<float>& C,
+                                               const StepC<float>& S, int role, float& q_ca, float& w,
+                                               float& q_sm, float& w_abs, float e_ca, float e_w,
+                                               float e_sm) {
+  const float dt = S.dt, h2 = S.h2, h6 = S.h6, g2 = S.g2, g1 = S.g1;
+  const float x1 = q_sm * U.inv_p_atm + C.x_r;
+  float a1, b1, c1, a2, b2, c2, a3, b3, c3, a4, b4, c4;
+  fc3_rhs_split(U, C, role, q_ca, w, q_sm, w_abs, x1, a1, b1, c1);
+  fc3_rhs_split(U, C, role, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, w_abs + h2 * b1, x1 + g2 * c1,
+                a2, b2, c2);
+  fc3_rhs_split(U, C, role, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, w_abs + h2 * b2, x1 + g2 * c2,
+                a3, b3, c3);
+  const float p_ca = (q_ca + e_ca) + h6 * (a1 + 2.0f * (a2 + a3));
+  const float p_w = (w + e_w) + h6 * (b1 + 2.0f * (b2 + b3));
+  const float p_sm = (q_sm + e_sm) + h6 * (c1 + 2.0f * (c2 + c3));
+  const float p_wa = p_w + C.r_w;
+  fc3_rhs_split(U, C, role, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, w_abs + dt * b3, x1 + g1 * c3,
+                a4, b4, c4);
+  q_ca = p_ca + h6 * a4;
+  w = p_w + h6 * b4;
+  q_sm = p_sm + h6 * c4;
+  w_abs = p_wa + h6 * b4;
+}
+
+// run_lane (steps 1..H from step 0) for a lane pair: the same blocks of PF
+// steps, block tests, finiteness rule, band tracking and dead-flag use, so the
+// decisions and the min slack of a trajectory that does not violate equal
+// run_lane's.  The warp steps together while any of its pairs runs (the
+// shuffles need every lane); a pair that has stopped, or a lane past the
+// instance's scenarios (on = false), keeps stepping without recording.
+template <int PF>
+__device__ __forceinline__ float run_lane_split(const RhsU<float>& K, const RhsC<float>& C,
+                                                const float* __restrict__ d, int k, bool on, int N, int H,
+                                                int role, float& q_ca, float& w, float& q_sm, float& w_abs,
+                                                float dt, float thr, const volatile int32_t* dead,
+                                                unsigned* steps, float band, int* jlast) {
+  float smin = inf_v<float>();
+  int j = 0, jl = -1, j_stop = 0;
+  bool run = on;
+  {
+    const float s0 = checked_slack<float>(C, q_ca, w, q_sm);
+    smin = fmin(smin, s0);
+    if (s0 < band) jl = 0;
+    if (s0 < thr) run = false;
+  }
+  const StepC<float> S = step_consts<float>(K, dt);
+  const size_t HN = static_cast<size_t>(H) * N;
+  const float* pf = d + (on ? k : 0);  // in bounds for every lane
+  float r0[PF], r1[PF], r2[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    if (u < H) {
+      r0[u] = __ldg(pf);
+      r1[u] = __ldg(pf + HN);
+      r2[u] = __ldg(pf + 2 * HN);
+    } else {
+      r0[u] = r1[u] = r2[u] = 0.0f;
+    }
+    pf += N;
+  }
+  while (j + PF <= H && __any_sync(0xffffffffu, run)) {
+    const int dead_now = (run && dead != nullptr) ? *dead : 0;
+    float nf = 0.0f, bmin = inf_v<float>();
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const float e0 = r0[u], e1 = r1[u], e2 = r2[u];
+      if (j + PF < H) {
+        r0[u] = __ldg(pf);
+        r1[u] = __ldg(pf + HN);
+        r2[u] = __ldg(pf + 2 * HN);
+      }
+      pf += N;
+      rk4_step_split(K, C, S, role, q_ca, w, q_sm, w_abs, e0, e1, e2);
+      ++j;
+      const float s = C.y_scale * (q_sm - q_ca) + C.s_off;
+      bmin = fmin(bmin, s);
+      nf = fma_rn(s, 0.0f, nf);
+    }
+    if (run) {
+      nf = fma_rn(q_ca, 0.0f, fma_rn(w, 0.0f, fma_rn(q_sm, 0.0f, nf)));
+      if (nf != nf) bmin = -inf_v<float>();
+      smin = fmin(smin, bmin);
+      if (bmin < band) jl = j;
+      j_stop = j;
+      if (smin < thr || (dead_now != 0 && j < H)) run = false;
+    }
+  }
+  const float* dp = d + static_cast<size_t>(j) * N + (on ? k : 0);
+  while (j < H && __any_sync(0xffffffffu, run)) {
+    const float e0 = __ldg(dp), e1 = __ldg(dp + HN), e2 = __ldg(dp + 2 * HN);
+    dp += N;
+    rk4_step_split(K, C, S, role, q_ca, w, q_sm, w_abs, e0, e1, e2);
+    ++j;
+    if (run) {
+      const float s = checked_slack<float>(C, q_ca, w, q_sm);
+      smin = fmin(smin, s);
+      if (s < band) jl = j;
+      j_stop = j;
+      if (s < thr) run = false;
+    }
+  }
+  *steps = static_cast<unsigned>(j_stop);
+  *jlast = jl;
+  return smin;
+}
+
+// A warp tile of 16 scenarios of candidate slot (s, i), two lanes each:
+// batch_tile's classification and reduction with role 0's lanes as the
+// trajectories (role 1's take no part in the flags, the min or the step
+// count).  Called by all 32 lanes; returns are warp-uniform.
+template <int PF>
+__device__ __forceinline__ void batch_tile_split(const BLaunch& B, int s, int i, int k, int role) {
+  const BInst I = B.inst[s];
+  const size_t slot = static_cast<size_t>(s) * B.c.M + i;
+  if (!B.cand_ss[slot]) return;
+  volatile int32_t* dead = B.cand_dead + slot;
+  const bool cand_stop = B.c.early_exit == RRG_EXIT_CANDIDATE;
+  if (cand_stop) {
+    const int dead0 = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? *dead : 0, 0);
+    if (dead0) return;
+  }
+  const bool on = k < I.N;
+  const float eps = static_cast<float>(B.c.eps_abs);
+  const float thr = B.c.early_exit != RRG_EXIT_NONE ? -eps : -inf_v<float>();
+  const BState& st = B.st[s];
+  const double p_atm = B.params[P_P_ATM];
+  const RhsC<float> C = B.cand_c32[slot];
+  float q_ca, w, q_sm, w_abs;
+  start_state<float>(C, st.x, p_atm, q_ca, w, q_sm, w_abs);
+  const float* d = (st.cur ? B.d32b : B.d32) + I.off;
+  unsigned steps = 0;
+  int jlast = -1;
+  const float smin = run_lane_split<PF>(B.u32, C, d, k, on, I.N, I.H, role, q_ca, w, q_sm, w_abs,
+                                        static_cast<float>(B.c.dt), thr, cand_stop ? dead : nullptr, &steps,
+                                        eps, &jlast);
+  const bool mine = on && role == 0;
+  if (cand_stop && mine && smin < thr) *dead = 1;
+  batch_reduce(B, slot, k, mine, smin, mine ? steps : 0u, jlast, eps, dead);
+}
+
+// Warp tiles of 16 scenarios at two lanes per trajectory.
+template <int PF>
+__global__ void __launch_bounds__(128) batch_rollout_split_kernel(const BLaunch B) {
+  const uint32_t total = B.queue[1];
+  const int lane = static_cast<int>(threadIdx.x & 31);
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(B.queue, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) return;
+    int s = 0, i = 0, b = 0;
+    if (lane == 0) tile_of(B, t, 16, &s, &i, &b);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    batch_tile_split<PF>(B, s, i, b * 16 + (lane >> 1), lane & 1);
+  }
+}
 __global__ void __launch_bounds__(64) batch_recheck_kernel(const BLaunch B) {
   const uint32_t count = min(*B.recheck_count, static_cast<uint32_t>(B.recheck_cap));
   const double p_atm = B.params[P_P_ATM];
@@ -682,15 +870,16 @@ struct Variant {
   void (*kernel)(const BLaunch);
 };
 // tile = 32: warp tiles (CTAs of 4 warps, no CTA barrier); rows = 2: two
-// candidates per thread
+// candidates per thread; tile = 16: warp tiles of 16 scenarios, two lanes
+// per trajectory
 const Variant kVariants[RRG_BATCH_VARIANTS] = {
     {64, 8, 1, batch_rollout_kernel<64, 8>},   {64, 16, 1, batch_rollout_kernel<64, 16>},
     {128, 8, 1, batch_rollout_kernel<128, 8>}, {128, 16, 1, batch_rollout_kernel<128, 16>},
     {256, 8, 1, batch_rollout_kernel<256, 8>}, {256, 16, 1, batch_rollout_kernel<256, 16>},
     {32, 8, 1, batch_rollout_warp_kernel<8>},  {32, 16, 1, batch_rollout_warp_kernel<16>},
-    {32, 8, 2, batch_rollout_warp_pair_kernel<8>},
+    {32, 8, 2, batch_rollout_warp_pair_kernel<8>}, {16, 8, 1, batch_rollout_split_kernel<8>},
 };
-constexpr int block_threads(int tile) { return tile == 32 ? 128 : tile; }
+constexpr int block_threads(int tile) { return tile <= 32 ? 128 : tile; }
 
 }  // namespace
 }  // namespace rrg

@@ -577,7 +577,7 @@ def rrg_alu_peaks():
 
 
 # ---------------------------------------------------------------- batched --
-BATCH_VARIANTS = 9
+BATCH_VARIANTS = 10
 BATCH_MAX_WIDTHS = 24
 
 

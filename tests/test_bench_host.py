@@ -119,6 +119,9 @@ def test_batch_kernel_names():
     assert bench.batch_kernel_name((bench.BATCH_PAIR_VARIANT, 32, 8)).startswith("batch_rollout_warp_pair_kernel<8>")
     assert bench.batch_kernel_name((7, 32, 16)) == "batch_rollout_warp_kernel<16>"
     assert bench.batch_kernel_name((3, 128, 16)) == "batch_rollout_kernel<128, 16>"
+    assert bench.batch_kernel_name((bench.BATCH_SPLIT_VARIANT, 16, 8)).startswith("batch_rollout_split_kernel<8>")
+    assert bench.batch_ceiling((bench.BATCH_SPLIT_VARIANT, 16, 8)) is None
+    assert bench.batch_ceiling((7, 32, 16)) == bench.ISSUE_CEILING
 
 
 def test_apply_tma_leaves_handles_without_a_tma_ring_alone():

@@ -295,3 +295,48 @@ def test_batch_pair_tiles_match_single_tiles_and_oracle(R, orc, params, width, k
         else:
             k_o, f_o = _oracle(orc, params, "ksection", x[s], b["v_prev"][s], b["r"][s], d, N, H, 7)
         assert (k[s], f[s]) == (k_o, f_o), s
+
+
+SPLIT_VARIANT = 9  # warp tiles of 16 scenarios, two lanes per trajectory
+
+
+@pytest.mark.parametrize("early", ["none", "lane", "candidate"])
+@pytest.mark.parametrize("kind", ["spec", "ksection"])
+def test_batch_split_tiles_match_single_tiles_and_oracle(R, orc, params, early, kind):
+    """Two lanes per trajectory (role 0 the linear flow derivatives, role 1
+    the compressor speed's, swapped by shuffles): every instance's v_t, kappa
+    and flags equal the one-lane warp tiles' and the oracle's, for scenario
+    counts that leave a ragged 16-scenario tile and horizons shorter than the
+    prefetch block; without early exit both count the same lane-steps."""
+    S, seed, upd = 9, 7, 3
+    b, x = _problem(orc, params, S, 5, N_lo=1, N_hi=300, H_lo=1, H_hi=250)
+    ex = {"none": R.EXIT_NONE, "lane": R.EXIT_LANE, "candidate": R.EXIT_CANDIDATE}[early]
+    if kind == "spec":
+        cfg = _cfg(R, 64, R.SEARCH_SPEC_BISECT, n_bisect=12, recheck_eps_rel=1e-6, early_exit=ex)
+    else:
+        cfg = _cfg(R, 7, R.SEARCH_KSECTION, recheck_eps_rel=1e-6, early_exit=ex)
+    out, steps = {}, {}
+    with R.BatchGovernor(params, cfg, b["N"], b["H"]) as g:
+        if kind == "spec":
+            g.set_width(7)
+        for var in (7, SPLIT_VARIANT):
+            g.set_variant(var)
+            assert g.get_variant()[0] == var
+            g.reset_stats()
+            out[var] = g.step(x, b["r"], b["v_prev"], seed, upd)
+            st = g.stats()
+            steps[var] = st["lane_steps"] - st["lane_steps_fp64"]
+        assert g.get_variant()[1] == 16
+    for a, c in zip(out[7], out[SPLIT_VARIANT]):
+        np.testing.assert_array_equal(a, c)
+    if early == "none":
+        assert steps[7] == steps[SPLIT_VARIANT] > 0
+    v, k, f = out[SPLIT_VARIANT]
+    for s in range(S):
+        N, H = int(b["N"][s]), int(b["H"][s])
+        d = orc.sample_disturbances(seed + s, upd, N, H, inputs.DIST_AMP)
+        if kind == "spec":
+            k_o, f_o = orc.bisect_joint(params, orc.cfg(H=H, N=N), x[s], b["v_prev"][s], b["r"][s], 12, d)
+        else:
+            k_o, f_o = _oracle(orc, params, "ksection", x[s], b["v_prev"][s], b["r"][s], d, N, H, 7)
+        assert (k[s], f[s]) == (k_o, f_o), s
