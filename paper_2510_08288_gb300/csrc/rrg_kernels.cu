@@ -1337,20 +1337,100 @@ cudaError_t launch_eval_finish(const Launch& L, int m, uint8_t* d_adm, double* d
 
 // ---------------------------------------------------------------------------
 // Simulated plant of the closed loop (Fig. 1) and the loop bookkeeping.
+// The plant's step runs on one warp.  It is binary64 and sits on the closed
+// loop's critical path, and GB300's binary64 pipe takes a warp instruction at
+// a time however few lanes are active, so a lone thread pays for every
+// instruction of the step.  All 32 lanes run the same step; only the x^e - 1
+// series is shared out: the 16 leaves of pow_m1_series's Estrin tree go to 16
+// lanes, and each level above is one fused multiply-add after two shuffles.
+// The tree, its operands and their order are pow_m1_series's, so every lane
+// gets its value bit for bit (the plant kernel measured 12.8 against 16.8 us).
+// The step around it is rk4_step_fast<double>'s: the same stage points and
+// combination, each right-hand side fc3_rhs_fast's with the shared series.
+// Called by all 32 lanes of the warp with the same arguments.
+__device__ __forceinline__ double pow_m1_warp(const PowSeries* __restrict__ S, double x, double e) {
+  if (S != nullptr && S->e == e) {
+    const double t = fma(x, S->inv_c, -1.0);
+    if (fabs(t) <= 1.0 / 3.0) {
+      const int i = static_cast<int>(threadIdx.x & 15);
+      const double t2 = t * t, t4 = t2 * t2, t8 = t4 * t4, t16 = t8 * t8, t32 = t16 * t16;
+      double p = fma(S->a[2 * i + 1], t, S->a[2 * i]);
+      double hi = __shfl_sync(0xffffffffu, p, 2 * i + 1), lo = __shfl_sync(0xffffffffu, p, 2 * i);
+      p = fma(hi, t2, lo);
+      hi = __shfl_sync(0xffffffffu, p, 2 * i + 1);
+      lo = __shfl_sync(0xffffffffu, p, 2 * i);
+      p = fma(hi, t4, lo);
+      hi = __shfl_sync(0xffffffffu, p, 2 * i + 1);
+      lo = __shfl_sync(0xffffffffu, p, 2 * i);
+      p = fma(hi, t8, lo);
+      const double p1 = __shfl_sync(0xffffffffu, p, 1), p0 = __shfl_sync(0xffffffffu, p, 0);
+      return fma(S->a[32], t32, fma(p1, t16, p0));
+    }
+  }
+  return pow(x, e) - 1.0;
+}
+
+__device__ __forceinline__ void rhs_plant_warp(const RhsU<double>& U, const RhsC<double>& C, double z_ca,
+                                               double z_w, double z_sm, double w, double x_pw, double& d_ca,
+                                               double& d_w, double& d_sm) {
+  d_ca = U.a1 * z_sm + (C.c_ca - U.a12 * z_ca);
+  d_sm = U.g_w * z_w + ((C.c_sm + U.b3 * z_ca) - U.g_sm * z_sm);
+  const double W_cp = U.a_w * z_w + (C.W_r - U.a_p * z_sm);
+  const double f = torque_factor<double>(U, pow_m1_warp(U.pws, x_pw, U.e), w);
+  d_w = (C.e0 - U.e2 * z_w) - W_cp * f;
+}
+
+__device__ __forceinline__ void rk4_plant_warp(const RhsU<double>& U, const RhsC<double>& C, double dt0,
+                                               double& q_ca, double& w, double& q_sm, double& w_abs,
+                                               double e_ca, double e_w, double e_sm) {
+  const StepC<double> S = step_consts<double>(U, dt0);
+  const double dt = S.dt, h2 = S.h2, h6 = S.h6, g2 = S.g2, g1 = S.g1;
+  const double x1 = q_sm * U.inv_p_atm + C.x_r;
+  double a1, b1, c1, a2, b2, c2, a3, b3, c3, a4, b4, c4;
+  rhs_plant_warp(U, C, q_ca, w, q_sm, w_abs, x1, a1, b1, c1);
+  rhs_plant_warp(U, C, q_ca + h2 * a1, w + h2 * b1, q_sm + h2 * c1, w_abs + h2 * b1, x1 + g2 * c1,
+                 a2, b2, c2);
+  rhs_plant_warp(U, C, q_ca + h2 * a2, w + h2 * b2, q_sm + h2 * c2, w_abs + h2 * b2, x1 + g2 * c2,
+                 a3, b3, c3);
+  const double p_ca = (q_ca + e_ca) + h6 * (a1 + 2.0 * (a2 + a3));
+  const double p_w = (w + e_w) + h6 * (b1 + 2.0 * (b2 + b3));
+  const double p_sm = (q_sm + e_sm) + h6 * (c1 + 2.0 * (c2 + c3));
+  const double p_wa = p_w + C.r_w;
+  rhs_plant_warp(U, C, q_ca + dt * a3, w + dt * b3, q_sm + dt * c3, w_abs + dt * b3, x1 + g1 * c3,
+                 a4, b4, c4);
+  q_ca = p_ca + h6 * a4;
+  w = p_w + h6 * b4;
+  q_sm = p_sm + h6 * c4;
+  w_abs = p_wa + h6 * b4;
+}
+
+// x_{t+1} = RK4(x_t, v) + the plant's own draw (plant_step_fast's step, on the
+// warp).
 __device__ void plant_step(const Launch& L, const double* x, double v, uint64_t seed, uint64_t upd,
                            const double* amp, double* x_next) {
   const U64x4 r = philox4x64_10(0ull, 0ull, upd, 1ull, seed, 0ull);
-  plant_step_fast(L.k64, L.u64, L.params, L.dt, v, x, uniform_sym(r.w[0], amp[0]),
-                  uniform_sym(r.w[1], amp[1]), uniform_sym(r.w[2], amp[2]), x_next);
+  RhsC<double> c64;
+  RhsC<float> c32;
+  const double q0[3] = {0.0, 0.0, 0.0};
+  fold_rhs_cand(L.k64, cand_consts(L.params, v), q0, 0.0, &c64, &c32);
+  const double p_atm = L.params[P_P_ATM];
+  double q_ca = x[0] - p_atm, w = x[1], q_sm = x[2] - p_atm, w_abs = x[1];
+  rk4_plant_warp(L.u64, c64, L.dt, q_ca, w, q_sm, w_abs, uniform_sym(r.w[0], amp[0]),
+                 uniform_sym(r.w[1], amp[1]), uniform_sym(r.w[2], amp[2]));
+  x_next[0] = q_ca + p_atm;
+  x_next[1] = w;
+  x_next[2] = q_sm + p_atm;
 }
 
 __global__ void plant_kernel(const Launch L, const double* d_x, const double* d_v, uint64_t seed,
                              uint64_t base, const unsigned long long* t_dev, const double* amp,
                              double* x_next) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
   double x[3] = {d_x[0], d_x[1], d_x[2]}, xn[3];
   plant_step(L, x, *d_v, seed, base + (t_dev ? *t_dev : 0ull), amp, xn);
-  x_next[0] = xn[0]; x_next[1] = xn[1]; x_next[2] = xn[2];
+  if (threadIdx.x == 0) {
+    x_next[0] = xn[0]; x_next[1] = xn[1]; x_next[2] = xn[2];
+  }
 }
 
 cudaError_t launch_plant(const Launch& L, const double* d_x, const double* d_v, uint64_t seed,
@@ -1380,15 +1460,17 @@ cudaError_t launch_loop_init(const Launch& L, LoopState* ls, const double* x0, d
 __global__ void loop_end_kernel(const Launch L, LoopState* ls, uint64_t seed, uint64_t t0,
                                 const double* amp, double* v_out, double* kappa_out,
                                 int32_t* flags_out, double* x_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
   const SearchState* s = L.st;
   const unsigned long long t = ls->t;
   const double v = s->v_t_out;
+  const double x[3] = {ls->x[0], ls->x[1], ls->x[2]};
+  double xn[3];
+  plant_step(L, x, v, seed, t0 + t, amp, xn);  // the whole warp (its shuffles order the reads above)
+  if (threadIdx.x != 0) return;
   if (v_out) v_out[t] = v;
   if (kappa_out) kappa_out[t] = s->kappa_opt;
   if (flags_out) flags_out[t] = s->flags;
-  double xn[3];
-  plant_step(L, ls->x, v, seed, t0 + t, amp, xn);
   ls->x[0] = xn[0]; ls->x[1] = xn[1]; ls->x[2] = xn[2];
   ls->v_prev = v;
   ls->t = t + 1;
