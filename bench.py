@@ -441,6 +441,49 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- GPU side --
+def e2e_loop_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning, tma=1):
+    """The timed updates [W, T) as one rrg_closed_loop_dev call each (plant
+    state on the device, as in the timed value) on a fresh handle: every
+    update copies its r_t in from pinned host memory, and its v_t, kappa,
+    flags and x_{t+1} out to pinned host memory, and waits for them."""
+    import numpy as np
+    import torch
+    g2 = R.Governor(p, cfg, stream)
+    g2.set_tuning(*tuning)
+    apply_tma(R, g2, tma)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_r = torch.zeros(T, dtype=torch.float64, device=dev)
+    d_v, d_k = torch.zeros_like(d_r), torch.zeros_like(d_r)
+    d_f = torch.zeros(T, dtype=torch.int32, device=dev)
+    d_x = torch.zeros(3 * (T + 1), dtype=torch.float64, device=dev)
+    h_r = torch.tensor(r_seq[:T], dtype=torch.float64).pin_memory()
+    h_out = torch.zeros(6, dtype=torch.float64).pin_memory()   # v, kappa, x_{t+1}[3], flags
+    h_f = torch.zeros(1, dtype=torch.int32).pin_memory()
+    d_r[:W].copy_(h_r[:W])
+    R.rrg_closed_loop_dev(g2.h, x0, V0, d_r, W, seed, 0, amp, True, d_v, d_k, d_f, d_x)
+    torch.cuda.synchronize()
+    e2e_s, kap = 0.0, []
+    with torch.cuda.stream(stream):
+        for t in range(W, T):
+            flush.fill_(float(t))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_r[t:t + 1].copy_(h_r[t:t + 1], non_blocking=True)
+            R.rrg_closed_loop_dev(g2.h, None, 0.0, d_r, 1, seed, 0, amp, True, d_v, d_k, d_f, d_x)
+            h_out[0:1].copy_(d_v[t:t + 1], non_blocking=True)
+            h_out[1:2].copy_(d_k[t:t + 1], non_blocking=True)
+            h_out[2:5].copy_(d_x[3 * (t + 1):3 * (t + 2)], non_blocking=True)
+            h_f.copy_(d_f[t:t + 1], non_blocking=True)
+            stream.synchronize()
+            e2e_s += time.perf_counter() - t0
+            kap.append(float(h_out[1]))
+    g2.close()
+    K = T - W
+    return {"value": K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 8 + 8 + 24 + 4,
+            "call": "rrg_closed_loop_dev, one update per call, plant state on the device",
+            "kappa_equal_to_device_run": bool(np.all(np.array(kap) == kap_dev[W:T]))}
+
+
 def e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, W, T, flush, kap_dev, tuning, tma=1):
     """The timed updates [W, T) again through the host-buffer entry points
     (rrg_sample_scenarios, rrg_step, rrg_plant_step) on a fresh handle, after
@@ -747,10 +790,12 @@ def run_gpu(args):
     out = None
     if rank == 0:
         # e2e: the same updates through the host-buffer C ABI, on a fresh handle
-        e2e = None
+        e2e = e2e_loop = None
         if not args.no_e2e:
             e2e = e2e_run(R, p, cfg, stream, x0, r_seq, seed, amp, S0, T, flush, kap_dev, (tune_m, tune_probe),
                           TMA_MODES.index(args.tma))
+            e2e_loop = e2e_loop_run(R, p, cfg, stream, x0, r_seq, seed, amp, S0, T, flush, kap_dev,
+                                    (tune_m, tune_probe), TMA_MODES.index(args.tma))
 
         # plain FP64 bisection on the same GPU over the same timed updates,
         # timed the same way (CUDA events around each update, L2 flushed in
@@ -821,6 +866,7 @@ def run_gpu(args):
                                               "chain: rrg_step_latency, one warp, same right-hand side" % HZ}},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_device_loop": e2e_loop,
             "direct_launches": {"value": world * K / direct_s, "unit": UNIT, "ms_per_step": 1e3 * direct_s / K,
                                 "gpu_launches": std["launches"], "kappa_equal_to_graph_replay": direct_same},
             "scenarios_in_register": {"value": world * K / reg_s, "unit": UNIT, "ms_per_step": 1e3 * reg_s / K,
